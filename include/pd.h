@@ -1,0 +1,201 @@
+/*
+ * pd.h -- C ABI of the GB300 PIC-DSMC particle pipeline.
+ *
+ * The library advances the 2D3V particle-in-cell / direct-simulation Monte
+ * Carlo model of W. Yang et al., "The role of double ionization on the
+ * generation of doubly charged ions in copper vacuum arcs" (arXiv:2109.00214):
+ * electrons, Cu, Cu+ and Cu2+ super-particles (Cu2+ labelled by the channel
+ * that made it, Sec. 2.3), electron-impact DSMC collisions with five channels
+ * including the four-stage double-ionization scheme of Sec. 2.2, the
+ * electrostatic push, fixed-point charge deposition (Eq. (9)-(10)) and the
+ * Poisson solve (Eq. (8)).  Every step of the pipeline runs in this library's
+ * CUDA kernels on the stream the caller supplies.
+ *
+ * Conventions
+ *   - Every call returns pd_status; PD_OK is 0.  Nothing is thrown across
+ *     the ABI.  After a failing call, pd_last_error() gives a message.
+ *   - Kernels report failures (capacity exhausted, a bounded wait that ran
+ *     out) through a sticky device error word; it is read at the next call
+ *     that synchronises (pd_synchronize, pd_get_*), which then fails.
+ *   - Ownership: the caller owns the device workspace (any device
+ *     allocation, e.g. a torch tensor), the CUDA stream and every host
+ *     buffer.  The library keeps only small host metadata, freed by
+ *     pd_destroy.  It never allocates device memory itself.
+ *   - Units are SI unless a name ends in _eV.  Geometry: axial index iz along
+ *     z (cathode at z = 0, anode at z = L = nz dz), radial index ir along r
+ *     (axis at r = 0); in the Cartesian periodic mode the same two indices
+ *     are the two in-plane axes.  Cell index = iz * nr + ir.
+ *   - Species codes: 0 e, 1 Cu, 2 Cu+, 3 Cu2+ from Cu+ -> Cu2+ (label SW),
+ *     4 Cu2+ from Cu -> Cu2+ (label DI).  Channels: 0 elastic e-Cu,
+ *     1 excitation e-Cu, 2 ionization Cu -> Cu+, 3 double ionization
+ *     Cu -> Cu2+, 4 ionization Cu+ -> Cu2+.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PD_OK = 0,
+    PD_ERR_ARG = 1,        /* invalid argument or configuration */
+    PD_ERR_CAPACITY = 2,   /* particle capacity or id space exhausted */
+    PD_ERR_CUDA = 3,       /* a CUDA runtime call failed */
+    PD_ERR_TIMEOUT = 4,    /* a bounded device wait ran out */
+    PD_ERR_NONFINITE = 5,  /* NaN/Inf met where a finite value is required */
+    PD_ERR_STATE = 6       /* call not valid in the current state */
+} pd_status;
+
+enum { PD_GEOM_RZ = 0, PD_GEOM_XY_PERIODIC = 1 };
+enum { PD_FIELD_NONE = 0, PD_FIELD_POISSON = 1, PD_FIELD_EXTERNAL = 2 };
+enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI = 4, PD_NSP = 5 };
+enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4, PD_NCH = 5 };
+
+#define PD_CONFIG_VERSION 1u
+
+/* Run parameters (Sec. 2.3 gives: 50 nm cells, 1 fs electron step, heavy step
+ * ten times longer, W = 100, 2.9 kV through R = 1 kOhm with C = 1 pF, a 200 nm
+ * tip with field enhancement 35, neutral flux 3 % of the electron flux). */
+typedef struct pd_config {
+    uint32_t struct_size;      /* sizeof(pd_config); checked */
+    uint32_t version;          /* PD_CONFIG_VERSION */
+    int32_t geometry;          /* PD_GEOM_* */
+    int32_t nz, nr;            /* cells along z and r; nz * nr < 2^24 */
+    double dz, dr;             /* cell size (m) */
+    double depth;              /* Cartesian cell depth (m); unused in r-z */
+    double dt;                 /* electron time step (s) */
+    int32_t heavy_subcycle;    /* heavies move every this many electron steps */
+    double weight;             /* physical particles per super-particle */
+    uint32_t seed, run;        /* Philox key */
+    int32_t field_mode;        /* PD_FIELD_*; PD_FIELD_POISSON needs r-z */
+    int32_t inject_on;         /* cathode emission each step (r-z only) */
+    int32_t di_on;             /* double-ionization channel on */
+    int32_t di_split_mode;     /* 0: cos chi = R, 1: cos^2 chi = R (stage 4) */
+    double coll_dt_scale;      /* collision time step / electron time step */
+    double V0, R_ohm, C_farad; /* external circuit */
+    double beta, tip_radius, work_function, neutral_ratio, neutral_T;
+    double poisson_tol;        /* relative residual |b - A phi| / |b| */
+    int32_t poisson_max_cycles;
+    int32_t reserved0;
+    int64_t capacity;          /* particle slots */
+} pd_config;
+
+/* Scalars of the current state (Sec. 3: arc current and voltage, Eq. (21)
+ * ionization degree and mean charge, cathode erosion). */
+typedef struct pd_scalars {
+    double t;                  /* simulated time (s) */
+    double V;                  /* anode voltage (V) */
+    double I_gap;              /* gap current of the last step (A) */
+    double gamma;              /* ionization degree, Eq. (21), q <= 2 */
+    double Qbar;               /* mean ion charge, Eq. (21) */
+    double erosion;            /* cathode erosion: net Cu mass / charge (kg/C) */
+    double mass;               /* net Cu mass leaving the cathode (kg) */
+    double charge;             /* net charge through the cathode (C) */
+    double sgmax[2];           /* NTC majorants (sigma g)_max, (e,Cu), (e,Cu+) */
+    double poisson_relres;     /* last solve's relative residual */
+    double poisson_cycles;     /* last solve's multigrid cycles */
+    double absorbed_energy[3]; /* J absorbed at cathode, anode, outer wall */
+    int64_t n_particles;       /* live particles */
+    int64_t count[PD_NSP];     /* live particles per species */
+    int64_t step;              /* electron steps taken */
+} pd_scalars;
+
+/* counters: events per channel [5], null candidates, candidates whose target
+ * was already ionized this step, accepted candidates below threshold, NTC
+ * majorant violations, isotropic-sampling fallbacks, candidates in total,
+ * electrons emitted, neutrals emitted, absorbed [electrode 3][species 5]. */
+#define PD_NCOUNTERS 28
+
+typedef struct pd_sim pd_sim;
+
+/* Defaults: the paper's run parameters on a 64 x 64 r-z grid over the 6 um
+ * gap (Sec. 2.3). */
+pd_status pd_config_default(pd_config* cfg);
+
+/* Device workspace bytes pd_create needs for cfg. */
+pd_status pd_workspace_size(const pd_config* cfg, size_t* bytes);
+
+/* Create a simulation in a caller-owned device workspace (at least
+ * pd_workspace_size bytes, 256-byte aligned) on stream `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  The current CUDA device
+ * must be the workspace's device.  The simulation starts empty (vacuum,
+ * Sec. 2.3), with zero cross sections and no field. */
+pd_status pd_create(const pd_config* cfg, void* dev_workspace, size_t bytes, void* cuda_stream,
+                    pd_sim** out);
+
+/* Integrated cross section of one channel (Sec. 2.3, Fig. 1 of the paper) as
+ * n >= 2 points (E_eV ascending, sigma_m2) in host memory, copied.  The table
+ * is resampled by linear interpolation onto the library's grid (64 points per
+ * octave from 2^-10 eV to 2^15 eV) and is zero below threshold_eV, which is
+ * also the energy the channel removes (Eq. (6), dE = -E_th).  Recomputes the
+ * NTC majorants.  Synchronous with respect to the host. */
+pd_status pd_set_cross_section(pd_sim* sim, int channel, const double* E_eV, const double* sigma_m2,
+                               int n, double threshold_eV);
+
+/* Append n particles given on the host in cell-relative form: species code,
+ * cell indices iz, ir, offsets pz, pr in [0, 1) inside the cell, velocities
+ * vz, vr, vt (m/s).  Ids are assigned in order.  Copied (synchronous). */
+pd_status pd_load_particles(pd_sim* sim, int64_t n, const uint8_t* species, const int32_t* iz,
+                            const int32_t* ir, const float* pz, const float* pr, const float* vz,
+                            const float* vr, const float* vt);
+
+/* Same, with all nine arrays in device memory (asynchronous on the stream;
+ * the arrays must stay valid until the stream reaches the copy). */
+pd_status pd_load_particles_device(pd_sim* sim, int64_t n, const uint8_t* species, const int32_t* iz,
+                                   const int32_t* ir, const float* pz, const float* pr, const float* vz,
+                                   const float* vr, const float* vt);
+
+/* External node field (field_mode PD_FIELD_EXTERNAL), host arrays of
+ * (nz+1)*(nr+1) nodes in r-z or nz*nr in the periodic mode, row-major in iz. */
+pd_status pd_set_field(pd_sim* sim, const double* Ez, const double* Er);
+
+/* Switch cathode emission (FN electrons + neutrals, Sec. 2.3) on or off. */
+pd_status pd_inject_cathode(pd_sim* sim, int enable);
+
+/* Advance n_steps electron steps: inject -> push + deposit -> sort ->
+ * collide + spawn -> circuit -> Poisson -> E.  Asynchronous on the stream. */
+pd_status pd_step(pd_sim* sim, int64_t n_steps);
+
+/* Wait for the stream and report a device-side error if one was raised. */
+pd_status pd_synchronize(pd_sim* sim);
+
+/* Diagnostics (synchronise). */
+pd_status pd_get_scalars(pd_sim* sim, pd_scalars* out);
+pd_status pd_get_counters(pd_sim* sim, uint64_t* out /* PD_NCOUNTERS */);
+/* Slots in use (live + dead); size for pd_get_particles. */
+pd_status pd_particle_slots(pd_sim* sim, int64_t* slots);
+/* Copy every slot to host arrays of pd_particle_slots() entries; dead slots
+ * have species 255.  Order is the device order (cell-sorted, not by id). */
+pd_status pd_get_particles(pd_sim* sim, uint32_t* id, uint8_t* species, int32_t* iz, int32_t* ir,
+                           float* pz, float* pr, float* vz, float* vr, float* vt);
+/* Fixed-point node charge (units of e * 2^-32 per super-particle) of the
+ * electrons and of the heavies. */
+pd_status pd_get_rho(pd_sim* sim, int64_t* rho_e, int64_t* rho_h);
+pd_status pd_get_phi(pd_sim* sim, double* phi);
+pd_status pd_get_field(pd_sim* sim, double* Ez, double* Er);
+/* Number density (m^-3) of one species on the nodes (CIC / node volume). */
+pd_status pd_get_density_map(pd_sim* sim, int species, double* out);
+/* Kinetic-energy histogram (eV) of one species on [e_lo_eV, e_hi_eV). */
+pd_status pd_get_energy_spectrum(pd_sim* sim, int species, double e_lo_eV, double e_hi_eV, int nbins,
+                                 uint64_t* out);
+
+/* Per-kernel CUDA-event timing of the launches pd_step makes (for
+ * measurement).  enable != 0 starts recording; pd_profile_read synchronises
+ * and returns, per kernel id, total milliseconds and launch counts, then
+ * clears.  Kernel ids: see pd_kernel_name. */
+#define PD_NKERNELS 12
+pd_status pd_profile_enable(pd_sim* sim, int enable);
+pd_status pd_profile_read(pd_sim* sim, double* ms /* PD_NKERNELS */, uint64_t* launches /* PD_NKERNELS */);
+const char* pd_kernel_name(int kernel_id);
+
+const char* pd_last_error(const pd_sim* sim);
+void pd_destroy(pd_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

@@ -40,11 +40,13 @@ typedef double real;
 #define R_(x) ((double)(x))
 #define OR_SQRT sqrt
 #define OR_FLOOR floor
+#define OR_NEXTAFTER nextafter
 #else
 typedef float real;
 #define R_(x) ((float)(x))
 #define OR_SQRT sqrtf
 #define OR_FLOOR floorf
+#define OR_NEXTAFTER nextafterf
 #endif
 
 /* ------------------------------------------------------------------ */
@@ -271,7 +273,7 @@ static void compute_sgmax(or_sim* S) {
         }
         best *= 1.0 + 1e-6;
         real f = R_(best);
-        if ((double)f < best) f = nextafter(f, INFINITY);
+        if ((double)f < best) f = OR_NEXTAFTER(f, INFINITY);
         S->sgmax[k] = f;
     }
 }

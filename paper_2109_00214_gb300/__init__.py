@@ -1,0 +1,391 @@
+"""Python binding of libpd.so (include/pd.h): argument marshalling only.
+
+Every step of the particle pipeline runs in the library's CUDA kernels; this
+module only fills the C structs, passes torch tensors' device pointers and
+CUDA streams, and copies host arrays in and out.  Importing it loads the
+compiled library and fails loudly if it is missing: there is no fallback.
+
+The functions keep the C names (pd_create, pd_step, ...).  ``Simulation`` is
+a small convenience holder of a workspace tensor and a pd_sim handle.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "config_from_dict",
+           "pd_config_default", "pd_workspace_size", "pd_create", "pd_set_cross_section",
+           "pd_load_particles", "pd_load_particles_device", "pd_set_field", "pd_inject_cathode",
+           "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots",
+           "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
+           "pd_get_energy_spectrum", "pd_profile_enable", "pd_profile_read", "pd_kernel_name",
+           "pd_last_error", "pd_destroy", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
+
+PD_NCOUNTERS = 28
+PD_NKERNELS = 12
+GEOM = {"rz": 0, "xy_periodic": 1}
+COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
+                  "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
+                 + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
+                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")])
+STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CAPACITY", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
+          5: "PD_ERR_NONFINITE", 6: "PD_ERR_STATE"}
+
+
+class PdConfig(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("version", C.c_uint32), ("geometry", C.c_int32),
+        ("nz", C.c_int32), ("nr", C.c_int32), ("dz", C.c_double), ("dr", C.c_double),
+        ("depth", C.c_double), ("dt", C.c_double), ("heavy_subcycle", C.c_int32),
+        ("weight", C.c_double), ("seed", C.c_uint32), ("run", C.c_uint32),
+        ("field_mode", C.c_int32), ("inject_on", C.c_int32), ("di_on", C.c_int32),
+        ("di_split_mode", C.c_int32), ("coll_dt_scale", C.c_double), ("V0", C.c_double),
+        ("R_ohm", C.c_double), ("C_farad", C.c_double), ("beta", C.c_double),
+        ("tip_radius", C.c_double), ("work_function", C.c_double), ("neutral_ratio", C.c_double),
+        ("neutral_T", C.c_double), ("poisson_tol", C.c_double), ("poisson_max_cycles", C.c_int32),
+        ("reserved0", C.c_int32), ("capacity", C.c_int64),
+    ]
+
+
+class PdScalars(C.Structure):
+    _fields_ = [
+        ("t", C.c_double), ("V", C.c_double), ("I_gap", C.c_double), ("gamma", C.c_double),
+        ("Qbar", C.c_double), ("erosion", C.c_double), ("mass", C.c_double), ("charge", C.c_double),
+        ("sgmax", C.c_double * 2), ("poisson_relres", C.c_double), ("poisson_cycles", C.c_double),
+        ("absorbed_energy", C.c_double * 3), ("n_particles", C.c_int64), ("count", C.c_int64 * 5),
+        ("step", C.c_int64),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class PdError(RuntimeError):
+    pass
+
+
+_L = None
+P = C.c_void_p
+Dp = C.POINTER(C.c_double)
+
+_SIGS = {
+    "pd_config_default": (C.c_int, [C.POINTER(PdConfig)]),
+    "pd_workspace_size": (C.c_int, [C.POINTER(PdConfig), C.POINTER(C.c_size_t)]),
+    "pd_create": (C.c_int, [C.POINTER(PdConfig), P, C.c_size_t, P, C.POINTER(P)]),
+    "pd_set_cross_section": (C.c_int, [P, C.c_int, Dp, Dp, C.c_int, C.c_double]),
+    "pd_load_particles": (C.c_int, [P, C.c_int64, P, P, P, P, P, P, P, P]),
+    "pd_load_particles_device": (C.c_int, [P, C.c_int64, P, P, P, P, P, P, P, P]),
+    "pd_set_field": (C.c_int, [P, Dp, Dp]),
+    "pd_inject_cathode": (C.c_int, [P, C.c_int]),
+    "pd_step": (C.c_int, [P, C.c_int64]),
+    "pd_synchronize": (C.c_int, [P]),
+    "pd_get_scalars": (C.c_int, [P, C.POINTER(PdScalars)]),
+    "pd_get_counters": (C.c_int, [P, P]),
+    "pd_particle_slots": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "pd_get_particles": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
+    "pd_get_rho": (C.c_int, [P, P, P]),
+    "pd_get_phi": (C.c_int, [P, Dp]),
+    "pd_get_field": (C.c_int, [P, Dp, Dp]),
+    "pd_get_density_map": (C.c_int, [P, C.c_int, Dp]),
+    "pd_get_energy_spectrum": (C.c_int, [P, C.c_int, C.c_double, C.c_double, C.c_int, P]),
+    "pd_profile_enable": (C.c_int, [P, C.c_int]),
+    "pd_profile_read": (C.c_int, [P, Dp, P]),
+    "pd_kernel_name": (C.c_char_p, [C.c_int]),
+    "pd_last_error": (C.c_char_p, [P]),
+    "pd_destroy": (None, [P]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def load_library(path=None, build_if_missing=True):
+    """Load libpd.so (building it with nvcc if it is absent or stale)."""
+    global _L
+    if _L is not None:
+        return _L
+    if path is None:
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+    if not os.path.exists(path):
+        raise PdError(f"CUDA library {path} is missing; build it with paper_2109_00214_gb300/build.py")
+    L = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _L = L
+    return L
+
+
+def _lib():
+    return _L if _L is not None else load_library()
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data)
+
+
+def _dp(a):
+    return a.ctypes.data_as(Dp)
+
+
+def _check(h, r, what):
+    if r != 0:
+        msg = _lib().pd_last_error(h) if h else b""
+        raise PdError(f"{what}: {STATUS.get(r, r)}: {msg.decode() if msg else ''}")
+
+
+def config_from_dict(d):
+    c = PdConfig()
+    _check(None, _lib().pd_config_default(C.byref(c)), "pd_config_default")
+    c.geometry = GEOM[d["geometry"]]
+    c.nz, c.nr = d["nz"], d["nr"]
+    c.dz, c.dr, c.depth, c.dt = d["dz"], d["dr"], d.get("depth", 1.0), d["dt"]
+    c.heavy_subcycle = d["heavy_subcycle"]
+    c.weight = d["weight"]
+    c.seed, c.run = d["seed"], d.get("run", 0)
+    c.field_mode = d["field_on"]
+    c.inject_on, c.di_on = d["inject_on"], d["di_on"]
+    c.di_split_mode = d.get("di_split_mode", 0)
+    c.coll_dt_scale = d.get("coll_dt_scale", 1.0)
+    c.V0, c.R_ohm, c.C_farad = d["V0"], d["R_ohm"], d["C_farad"]
+    c.beta, c.tip_radius, c.work_function = d["beta"], d["tip_radius"], d["work_function"]
+    c.neutral_ratio, c.neutral_T = d["neutral_ratio"], d["neutral_T"]
+    c.poisson_tol = d.get("poisson_tol", 1e-8)
+    c.poisson_max_cycles = d.get("poisson_max_cycles", 60)
+    c.capacity = d["capacity"]
+    return c
+
+
+# ---- thin wrappers with the C names --------------------------------------
+def pd_config_default():
+    c = PdConfig()
+    _check(None, _lib().pd_config_default(C.byref(c)), "pd_config_default")
+    return c
+
+
+def pd_workspace_size(cfg):
+    n = C.c_size_t(0)
+    _check(None, _lib().pd_workspace_size(C.byref(cfg), C.byref(n)), "pd_workspace_size")
+    return n.value
+
+
+def pd_create(cfg, workspace_ptr, nbytes, stream_ptr):
+    h = P()
+    _check(None, _lib().pd_create(C.byref(cfg), P(workspace_ptr), nbytes, P(stream_ptr), C.byref(h)),
+           "pd_create")
+    return h
+
+
+def pd_set_cross_section(h, ch, E, sig, threshold):
+    E = np.ascontiguousarray(E, np.float64)
+    sig = np.ascontiguousarray(sig, np.float64)
+    _check(h, _lib().pd_set_cross_section(h, int(ch), _dp(E), _dp(sig), len(E), float(threshold)),
+           "pd_set_cross_section")
+
+
+def pd_load_particles(h, parts):
+    n = len(parts["species"])
+    a = [np.ascontiguousarray(parts["species"], np.uint8), np.ascontiguousarray(parts["iz"], np.int32),
+         np.ascontiguousarray(parts["ir"], np.int32)]
+    a += [np.ascontiguousarray(parts[k], np.float32) for k in ("pz", "pr", "vz", "vr", "vt")]
+    _check(h, _lib().pd_load_particles(h, n, *[_ptr(x) for x in a]), "pd_load_particles")
+
+
+def pd_load_particles_device(h, n, ptrs):
+    """ptrs: device pointers (int) of species u8, iz i32, ir i32, pz, pr, vz, vr, vt f32."""
+    _check(h, _lib().pd_load_particles_device(h, int(n), *[P(p) for p in ptrs]), "pd_load_particles_device")
+
+
+def pd_set_field(h, Ez, Er):
+    Ez = np.ascontiguousarray(Ez, np.float64).ravel()
+    Er = np.ascontiguousarray(Er, np.float64).ravel()
+    _check(h, _lib().pd_set_field(h, _dp(Ez), _dp(Er)), "pd_set_field")
+
+
+def pd_inject_cathode(h, enable):
+    _check(h, _lib().pd_inject_cathode(h, int(enable)), "pd_inject_cathode")
+
+
+def pd_step(h, n):
+    _check(h, _lib().pd_step(h, int(n)), "pd_step")
+
+
+def pd_synchronize(h):
+    _check(h, _lib().pd_synchronize(h), "pd_synchronize")
+
+
+def pd_get_scalars(h):
+    s = PdScalars()
+    _check(h, _lib().pd_get_scalars(h, C.byref(s)), "pd_get_scalars")
+    return s.as_dict()
+
+
+def pd_get_counters(h):
+    a = np.zeros(PD_NCOUNTERS, np.uint64)
+    _check(h, _lib().pd_get_counters(h, _ptr(a)), "pd_get_counters")
+    return dict(zip(COUNTER_NAMES, (int(x) for x in a)))
+
+
+def pd_particle_slots(h):
+    n = C.c_int64(0)
+    _check(h, _lib().pd_particle_slots(h, C.byref(n)), "pd_particle_slots")
+    return n.value
+
+
+def pd_get_particles(h, live_only=True):
+    n = pd_particle_slots(h)
+    out = dict(id=np.zeros(n, np.uint32), species=np.zeros(n, np.uint8), iz=np.zeros(n, np.int32),
+               ir=np.zeros(n, np.int32))
+    for k in ("pz", "pr", "vz", "vr", "vt"):
+        out[k] = np.zeros(n, np.float32)
+    keys = ("id", "species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
+    _check(h, _lib().pd_get_particles(h, *[_ptr(out[k]) for k in keys]), "pd_get_particles")
+    if live_only:
+        m = out["species"] != 255
+        out = {k: v[m] for k, v in out.items()}
+    return out
+
+
+def pd_get_rho(h, nodes):
+    a = np.zeros(nodes, np.int64)
+    b = np.zeros(nodes, np.int64)
+    _check(h, _lib().pd_get_rho(h, _ptr(a), _ptr(b)), "pd_get_rho")
+    return a, b
+
+
+def pd_get_phi(h, nodes):
+    a = np.zeros(nodes)
+    _check(h, _lib().pd_get_phi(h, _dp(a)), "pd_get_phi")
+    return a
+
+
+def pd_get_field(h, nodes):
+    a = np.zeros(nodes)
+    b = np.zeros(nodes)
+    _check(h, _lib().pd_get_field(h, _dp(a), _dp(b)), "pd_get_field")
+    return a, b
+
+
+def pd_get_density_map(h, species, nodes):
+    a = np.zeros(nodes)
+    _check(h, _lib().pd_get_density_map(h, int(species), _dp(a)), "pd_get_density_map")
+    return a
+
+
+def pd_get_energy_spectrum(h, species, lo, hi, nbins):
+    a = np.zeros(nbins, np.uint64)
+    _check(h, _lib().pd_get_energy_spectrum(h, int(species), float(lo), float(hi), int(nbins), _ptr(a)),
+           "pd_get_energy_spectrum")
+    return a
+
+
+def pd_profile_enable(h, on):
+    _check(h, _lib().pd_profile_enable(h, int(on)), "pd_profile_enable")
+
+
+def pd_profile_read(h):
+    ms = np.zeros(PD_NKERNELS)
+    n = np.zeros(PD_NKERNELS, np.uint64)
+    _check(h, _lib().pd_profile_read(h, _dp(ms), _ptr(n)), "pd_profile_read")
+    return {pd_kernel_name(k): (float(ms[k]), int(n[k])) for k in range(PD_NKERNELS)}
+
+
+def pd_kernel_name(k):
+    return _lib().pd_kernel_name(int(k)).decode()
+
+
+KERNEL_NAMES = ["inject", "push", "scan_bins", "scatter", "ncand", "scan_cand", "collide", "finalize",
+                "poisson", "efield", "memset", "other"]
+
+
+def pd_last_error(h):
+    return _lib().pd_last_error(h).decode()
+
+
+def pd_destroy(h):
+    _lib().pd_destroy(h)
+
+
+class Simulation:
+    """A pd_sim in a torch-allocated device workspace on a torch stream."""
+
+    def __init__(self, cfg_dict, xs=None, device="cuda", stream=None):
+        import torch
+        load_library()
+        self.cfg_dict = dict(cfg_dict)
+        self.cfg = config_from_dict(cfg_dict)
+        self.nbytes = pd_workspace_size(self.cfg)
+        self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.ws.device)
+        self.h = pd_create(self.cfg, self.ws.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        rz = cfg_dict["geometry"] == "rz"
+        self.nzn = cfg_dict["nz"] + (1 if rz else 0)
+        self.nrn = cfg_dict["nr"] + (1 if rz else 0)
+        self.nodes = self.nzn * self.nrn
+        if xs is not None:
+            self.set_cross_sections(xs)
+
+    def set_cross_sections(self, xs):
+        for ch, (E, s, th) in xs.items():
+            pd_set_cross_section(self.h, ch, E, s, th)
+
+    def load(self, parts):
+        pd_load_particles(self.h, parts)
+
+    def load_device(self, t):
+        """t: dict of torch CUDA tensors (species u8, iz, ir i32, pz, pr, vz, vr, vt f32)."""
+        keys = ("species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
+        pd_load_particles_device(self.h, t["species"].numel(), [t[k].data_ptr() for k in keys])
+
+    def set_field(self, Ez, Er):
+        pd_set_field(self.h, Ez, Er)
+
+    def step(self, n=1):
+        pd_step(self.h, n)
+
+    def synchronize(self):
+        pd_synchronize(self.h)
+
+    def scalars(self):
+        return pd_get_scalars(self.h)
+
+    def counters(self):
+        return pd_get_counters(self.h)
+
+    def particles(self, live_only=True):
+        return pd_get_particles(self.h, live_only)
+
+    def rho(self):
+        a, b = pd_get_rho(self.h, self.nodes)
+        return a.reshape(self.nzn, self.nrn), b.reshape(self.nzn, self.nrn)
+
+    def phi(self):
+        return pd_get_phi(self.h, self.nodes).reshape(self.nzn, self.nrn)
+
+    def field(self):
+        a, b = pd_get_field(self.h, self.nodes)
+        return a.reshape(self.nzn, self.nrn), b.reshape(self.nzn, self.nrn)
+
+    def density_map(self, species):
+        return pd_get_density_map(self.h, species, self.nodes).reshape(self.nzn, self.nrn)
+
+    def energy_spectrum(self, species, lo=0.0, hi=500.0, nbins=100):
+        return pd_get_energy_spectrum(self.h, species, lo, hi, nbins)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,886 @@
+// pd_capi.cu -- the C ABI (include/pd.h): workspace layout, constants,
+// step orchestration and diagnostics.  Host code; every pipeline step runs
+// in the kernels of pd_particles.cu, pd_collide.cu and pd_field.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd.h"
+#include "pd_field.h"
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+using namespace pd;
+
+namespace {
+
+// CODATA 2018
+constexpr double QE = 1.602176634e-19;
+constexpr double ME = 9.1093837015e-31;
+constexpr double AMU = 1.66053906660e-27;
+constexpr double M_CU = 63.546 * AMU;
+constexpr double KB = 1.380649e-23;
+constexpr double PI = 3.14159265358979323846;
+constexpr int ZQ[NSP] = {-1, 0, 1, 2, 2};
+
+double species_mass(int s) { return s == SP_E ? ME : M_CU; }
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t total = 0;
+    size_t A[7], B[7];
+    size_t count, off, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E, phi, xsE, xs, ck, ray, hist,
+        spc, state, field;
+    uint32_t nbins_pad, ncell_pad;
+    size_t field_bytes;
+};
+
+Layout make_layout(const pd_config& c) {
+    Layout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t r = o;
+        o = align256(o + bytes);
+        return r;
+    };
+    const uint64_t cap = (uint64_t)c.capacity;
+    for (int k = 0; k < 7; ++k) L.A[k] = take(cap * 4);
+    for (int k = 0; k < 7; ++k) L.B[k] = take(cap * 4);
+    const uint64_t ncell = (uint64_t)c.nz * c.nr;
+    L.nbins_pad = scan_padded(ncell * NSP);
+    L.ncell_pad = scan_padded(ncell);
+    L.count = take((size_t)L.nbins_pad * 4);
+    L.off = take(((size_t)L.nbins_pad + 1) * 4);
+    const size_t npart = (size_t)std::max(L.nbins_pad, L.ncell_pad) / SCAN_TILE + 1;
+    L.partial = take(npart * 4);
+    L.nc = take(ncell * 8);
+    L.cand = take((size_t)L.ncell_pad * 4);
+    L.cand_off = take(((size_t)L.ncell_pad + 1) * 4);
+    L.active = take(ncell * 4);
+    const uint64_t nodes = c.geometry == PD_GEOM_RZ ? (uint64_t)(c.nz + 1) * (c.nr + 1) : ncell;
+    L.rho_e = take(nodes * 8);
+    L.rho_h = take(nodes * 8);
+    L.diag = take(nodes * 8);
+    L.E = take(nodes * 8);
+    L.phi = take(nodes * 8);
+    L.xsE = take(XS_N * 4);
+    L.xs = take(NCH * XS_N * 4);
+    L.ck = take(2 * (size_t)c.nr * 4);
+    L.ray = take(1024 * 4);
+    L.hist = take(4096 * 8);
+    L.spc = take(NSP * 8);
+    L.state = take(sizeof(DevState));
+    L.field_bytes = c.field_mode == PD_FIELD_POISSON ? field_workspace_bytes(c.nz, c.nr) : 0;
+    L.field = take(L.field_bytes);
+    L.total = o;
+    return L;
+}
+
+const char* const KNAMES[PD_NKERNELS] = {"inject",  "push",     "scan_bins", "scatter", "ncand",  "scan_cand",
+                                         "collide", "finalize", "poisson",   "efield",  "memset", "other"};
+enum { K_INJECT, K_PUSH, K_SCAN_BINS, K_SCATTER, K_NCAND, K_SCAN_CAND, K_COLLIDE, K_FINALIZE, K_POISSON, K_EFIELD,
+       K_MEMSET, K_OTHER };
+
+}  // namespace
+
+struct pd_sim {
+    pd_config cfg;
+    Layout L;
+    cudaStream_t stream;
+    char* ws;
+    int sms;
+    Particles A, B;
+    uint32_t *count, *off, *partial, *cand, *cand_off, *active;
+    uint2* nc;
+    long long *rho_e, *rho_h, *diag;
+    float2* E;
+    double* phi;
+    float *xsE, *xs, *ck, *ray;
+    unsigned long long *hist, *spc;
+    DevState* st;
+    FieldSolver field;
+    // host copies
+    float h_xsE[XS_N];
+    float h_xs[NCH][XS_N];
+    double eth[NCH];
+    CollConsts cc;
+    InjectConsts ic;
+    float h_ray[1024];
+    int64_t step;
+    bool primed;
+    int inject_on;
+    std::string err;
+    // profiling
+    bool prof;
+    struct Rec {
+        int k;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    uint64_t launches[PD_NKERNELS];
+};
+
+namespace {
+
+pd_status fail(pd_sim* s, pd_status code, const std::string& msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+pd_status cuda_fail(pd_sim* s, cudaError_t e, const char* where) {
+    return fail(s, PD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+    } while (0)
+
+cudaEvent_t take_event(pd_sim* s) {
+    if (s->pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = s->pool.back();
+    s->pool.pop_back();
+    return e;
+}
+
+struct Timed {
+    pd_sim* s;
+    int k;
+    cudaEvent_t b;
+    Timed(pd_sim* s_, int k_) : s(s_), k(k_), b(nullptr) {
+        s->launches[k] += 1;
+        if (s->prof) {
+            cudaEvent_t a = take_event(s);
+            b = take_event(s);
+            cudaEventRecord(a, s->stream);
+            s->recs.push_back({k, a, b});
+        }
+    }
+    ~Timed() {
+        if (b) cudaEventRecord(b, s->stream);
+    }
+};
+
+KParams kparams(const pd_sim* s, int heavy_step) {
+    KParams P;
+    const pd_config& c = s->cfg;
+    P.geom = c.geometry == PD_GEOM_RZ ? 0 : 1;
+    P.nz = c.nz;
+    P.nr = c.nr;
+    P.nzn = P.geom == 0 ? c.nz + 1 : c.nz;
+    P.nrn = P.geom == 0 ? c.nr + 1 : c.nr;
+    P.ncell = (uint32_t)c.nz * (uint32_t)c.nr;
+    P.seed = c.seed;
+    P.run = c.run;
+    P.step = (uint32_t)s->step;
+    P.heavy_step = heavy_step;
+    P.field_on = c.field_mode != PD_FIELD_NONE;
+    P.capacity = (unsigned long long)c.capacity;
+    P.weight = c.weight;
+    for (int k = 0; k < NSP; ++k) P.masses[k] = species_mass(k);
+    return P;
+}
+
+PushConsts push_consts(const pd_config& c) {
+    PushConsts pc;
+    const double dte = c.dt, dth = c.dt * c.heavy_subcycle;
+    for (int sp = 0; sp < NSP; ++sp) {
+        const double dts = sp == SP_E ? dte : dth;
+        pc.qmdt[sp] = (float)((double)ZQ[sp] * QE / species_mass(sp) * dts);
+        pc.dtz[sp] = (float)(dts / c.dz);
+        pc.dtr[sp] = (float)(dts / c.dr);
+        pc.mass_w[sp] = 0.0f;
+    }
+    return pc;
+}
+
+double cell_volume(const pd_config& c, int j) {
+    if (c.geometry == PD_GEOM_RZ) return PI * (double)(2 * j + 1) * c.dr * c.dr * c.dz;
+    return c.dz * c.dr * c.depth;
+}
+
+// Verboncoeur node volumes (linear hat in r); half axial extent on electrodes
+double node_volume(const pd_config& c, int i, int j) {
+    if (c.geometry != PD_GEOM_RZ) return c.dz * c.dr * c.depth;
+    const double dz = c.dz, dr = c.dr;
+    const int N = c.nr;
+    double v;
+    if (j == 0) v = PI * dz * dr * dr / 3.0;
+    else if (j == N) v = 2.0 * PI * dz * dr * dr * ((double)N / 2.0 - 1.0 / 6.0);
+    else v = 2.0 * PI * dz * dr * dr * (double)j;
+    if (i == 0 || i == c.nz) v *= 0.5;
+    return v;
+}
+
+double mr_class() { return ME * M_CU / (ME + M_CU); }
+
+// NTC majorants from the float tables (see pd_set_cross_section), then the
+// per-row factors c_k(j) = W (sigma g)_max dt_coll / V_cell(j).
+void update_collision_consts(pd_sim* s) {
+    const double mr = mr_class();
+    CollConsts& cc = s->cc;
+    cc.kmr = (float)(0.5 * mr / QE);
+    cc.a_e = (float)(mr / ME);
+    cc.a_t = (float)(mr / M_CU);
+    for (int ch = 0; ch < NCH; ++ch) cc.kth[ch] = (float)(2.0 * s->eth[ch] * QE / mr);
+    cc.di_split_mode = s->cfg.di_split_mode;
+    const double kd = (double)cc.kmr;
+    const int ch0[2] = {CH_EL, CH_SW}, nch[2] = {4, 1};
+    for (int k = 0; k < 2; ++k) {
+        double best = 0.0;
+        float prev = 0.0f;
+        for (int q = 0; q < XS_N; ++q) {
+            float sT = 0.0f;
+            for (int c = 0; c < nch[k]; ++c) sT = sT + s->h_xs[ch0[k] + c][q];
+            if (q > 0) {
+                const float smax = sT > prev ? sT : prev;
+                const double g = std::sqrt((double)s->h_xsE[q] / kd);
+                const double cand = (double)smax * g;
+                if (cand > best) best = cand;
+            }
+            prev = sT;
+        }
+        best *= 1.0 + 1e-6;
+        float f = (float)best;
+        if ((double)f < best) f = std::nextafter(f, INFINITY);
+        cc.sgmax[k] = f;
+    }
+}
+
+pd_status upload_ck(pd_sim* s) {
+    const pd_config& c = s->cfg;
+    std::vector<float> ck(2 * (size_t)c.nr);
+    const double dtc = c.dt * c.coll_dt_scale;
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < c.nr; ++j)
+            ck[(size_t)k * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[k] * dtc / cell_volume(c, j));
+    CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
+pd_status read_state(pd_sim* s, DevState* out) {
+    CK(cudaMemcpyAsync(out, s->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
+pd_status check_device_error(pd_sim* s, const DevState& d) {
+    if (d.error & ERR_CAPACITY) return fail(s, PD_ERR_CAPACITY, "particle capacity exhausted");
+    if (d.error & ERR_IDS) return fail(s, PD_ERR_CAPACITY, "particle id space exhausted");
+    if (d.error & ERR_TIMEOUT) return fail(s, PD_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (d.error & ERR_NONFINITE) return fail(s, PD_ERR_NONFINITE, "non-finite value in the field solve");
+    if (d.error & ERR_BOUNDS) return fail(s, PD_ERR_CAPACITY, "spawn exceeded its reserved slots");
+    return PD_OK;
+}
+
+pd_status sync_check(pd_sim* s, DevState* d) {
+    pd_status r = read_state(s, d);
+    if (r != PD_OK) return r;
+    return check_device_error(s, *d);
+}
+
+pd_status validate(const pd_config* c, std::string& msg) {
+    if (!c) { msg = "null config"; return PD_ERR_ARG; }
+    if (c->struct_size != sizeof(pd_config) || c->version != PD_CONFIG_VERSION) {
+        msg = "pd_config size/version mismatch";
+        return PD_ERR_ARG;
+    }
+    if (c->geometry != PD_GEOM_RZ && c->geometry != PD_GEOM_XY_PERIODIC) { msg = "bad geometry"; return PD_ERR_ARG; }
+    if (c->nz < 2 || c->nr < 2 || (int64_t)c->nz * c->nr >= (1 << 24)) { msg = "grid must be >= 2x2 and < 2^24 cells"; return PD_ERR_ARG; }
+    if (!(c->dz > 0) || !(c->dr > 0) || !(c->dt > 0) || !(c->weight > 0)) { msg = "dz, dr, dt, weight must be > 0"; return PD_ERR_ARG; }
+    if (c->geometry == PD_GEOM_XY_PERIODIC && !(c->depth > 0)) { msg = "depth must be > 0"; return PD_ERR_ARG; }
+    if (c->heavy_subcycle < 1) { msg = "heavy_subcycle must be >= 1"; return PD_ERR_ARG; }
+    if (c->capacity < 1 || c->capacity > 0xFFFFFFFFll) { msg = "capacity must be in [1, 2^32)"; return PD_ERR_ARG; }
+    if (c->field_mode < 0 || c->field_mode > 2) { msg = "bad field_mode"; return PD_ERR_ARG; }
+    if (c->field_mode == PD_FIELD_POISSON && c->geometry != PD_GEOM_RZ) { msg = "Poisson field needs r-z"; return PD_ERR_ARG; }
+    if (c->field_mode == PD_FIELD_POISSON && !field_grid_ok(c->nz, c->nr)) { msg = "Poisson multigrid needs nz, nr = m * 2^k with m <= 8"; return PD_ERR_ARG; }
+    if (!(c->coll_dt_scale >= 0)) { msg = "coll_dt_scale must be >= 0"; return PD_ERR_ARG; }
+    if (c->geometry == PD_GEOM_RZ && c->inject_on) {
+        if (!(c->tip_radius > 0) || c->tip_radius / c->dr > 63) { msg = "tip must span 1..63 cells"; return PD_ERR_ARG; }
+    }
+    return PD_OK;
+}
+
+void setup_injection(pd_sim* s) {
+    const pd_config& c = s->cfg;
+    InjectConsts& ic = s->ic;
+    std::memset(&ic, 0, sizeof(ic));
+    const double dr = c.dr, rt = c.tip_radius;
+    const float rtip_cells = (float)(rt / dr);
+    int n = 0;
+    for (int j = 0; (double)j * dr < rt && j < c.nr && j < 64; ++j) {
+        const double rhi = std::fmin((j + 1) * dr, rt), rlo = j * dr;
+        ic.area[j] = PI * (rhi * rhi - rlo * rlo);
+        ic.lo[j] = (float)j;
+        ic.hi[j] = (j + 1) * dr <= rt ? (float)(j + 1) : rtip_cells;
+        n = j + 1;
+    }
+    ic.ntip = n;
+    ic.dt = c.dt;
+    ic.weight = c.weight;
+    ic.beta = c.beta;
+    ic.work = c.work_function;
+    ic.ratio = c.neutral_ratio;
+    ic.vth = (float)std::sqrt(KB * c.neutral_T / M_CU);
+    for (int k = 0; k < 1024; ++k) s->h_ray[k] = (float)std::sqrt(-2.0 * std::log(1.0 - (double)k / 1024.0));
+}
+
+int grid_for(pd_sim* s, int per_sm) { return s->sms * per_sm; }
+
+pd_status prime(pd_sim* s) {
+    const pd_config& c = s->cfg;
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    KParams P = kparams(s, 1);
+    CK(cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream));
+    CK(cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream));
+    {
+        Timed t(s, K_OTHER);
+        launch_deposit(s->A, s->rho_e, s->rho_h, s->st, P, grid_for(s, 8), s->stream);
+    }
+    if (c.field_mode == PD_FIELD_POISSON) {
+        Timed t(s, K_POISSON);
+        field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->st, s->stream);
+    }
+    CK(cudaGetLastError());
+    s->primed = true;
+    return PD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_config_default(pd_config* c) {
+    if (!c) return PD_ERR_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->struct_size = sizeof(pd_config);
+    c->version = PD_CONFIG_VERSION;
+    c->geometry = PD_GEOM_RZ;
+    c->nz = 64;
+    c->nr = 64;
+    c->dz = 6e-6 / 64;
+    c->dr = 6e-6 / 64;
+    c->depth = 1.0;
+    c->dt = 1e-15;
+    c->heavy_subcycle = 10;
+    c->weight = 100.0;
+    c->seed = 1;
+    c->run = 0;
+    c->field_mode = PD_FIELD_POISSON;
+    c->inject_on = 1;
+    c->di_on = 1;
+    c->di_split_mode = 0;
+    c->coll_dt_scale = 1.0;
+    c->V0 = 2.9e3;
+    c->R_ohm = 1e3;
+    c->C_farad = 1e-12;
+    c->beta = 35.0;
+    c->tip_radius = 100e-9;
+    c->work_function = 4.5;
+    c->neutral_ratio = 0.03;
+    c->neutral_T = 2000.0;
+    c->poisson_tol = 1e-8;
+    c->poisson_max_cycles = 60;
+    c->capacity = 1 << 16;
+    return PD_OK;
+}
+
+pd_status pd_workspace_size(const pd_config* c, size_t* bytes) {
+    std::string msg;
+    pd_status r = validate(c, msg);
+    if (r != PD_OK) return r;
+    if (!bytes) return PD_ERR_ARG;
+    *bytes = make_layout(*c).total;
+    return PD_OK;
+}
+
+pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd_sim** out) {
+    if (!out) return PD_ERR_ARG;
+    *out = nullptr;
+    std::string msg;
+    pd_status r = validate(c, msg);
+    if (r != PD_OK) {
+        std::fprintf(stderr, "pd_create: %s\n", msg.c_str());
+        return r;
+    }
+    Layout L = make_layout(*c);
+    if (!ws || bytes < L.total || ((uintptr_t)ws & 255)) return PD_ERR_ARG;
+    pd_sim* s = new (std::nothrow) pd_sim();
+    if (!s) return PD_ERR_ARG;
+    s->cfg = *c;
+    s->L = L;
+    s->stream = (cudaStream_t)stream;
+    s->ws = (char*)ws;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        delete s;
+        return PD_ERR_CUDA;
+    }
+    char* w = s->ws;
+    auto P32 = [&](size_t o) { return (uint32_t*)(w + o); };
+    auto PF = [&](size_t o) { return (float*)(w + o); };
+    s->A = Particles{P32(L.A[0]), PF(L.A[1]), PF(L.A[2]), PF(L.A[3]), PF(L.A[4]), PF(L.A[5]), P32(L.A[6])};
+    s->B = Particles{P32(L.B[0]), PF(L.B[1]), PF(L.B[2]), PF(L.B[3]), PF(L.B[4]), PF(L.B[5]), P32(L.B[6])};
+    s->count = P32(L.count);
+    s->off = P32(L.off);
+    s->partial = P32(L.partial);
+    s->nc = (uint2*)(w + L.nc);
+    s->cand = P32(L.cand);
+    s->cand_off = P32(L.cand_off);
+    s->active = P32(L.active);
+    s->rho_e = (long long*)(w + L.rho_e);
+    s->rho_h = (long long*)(w + L.rho_h);
+    s->diag = (long long*)(w + L.diag);
+    s->E = (float2*)(w + L.E);
+    s->phi = (double*)(w + L.phi);
+    s->xsE = PF(L.xsE);
+    s->xs = PF(L.xs);
+    s->ck = PF(L.ck);
+    s->ray = PF(L.ray);
+    s->hist = (unsigned long long*)(w + L.hist);
+    s->spc = (unsigned long long*)(w + L.spc);
+    s->st = (DevState*)(w + L.state);
+    for (int k = 0; k < XS_N; ++k) {
+        const int ex = XS_EMIN_EXP + k / XS_SUB, j = k % XS_SUB;
+        s->h_xsE[k] = (float)std::ldexp(1.0 + (double)j / XS_SUB, ex);
+    }
+    std::memset(s->h_xs, 0, sizeof(s->h_xs));
+    for (int k = 0; k < NCH; ++k) s->eth[k] = 0.0;
+    update_collision_consts(s);
+    setup_injection(s);
+    s->inject_on = c->inject_on && c->geometry == PD_GEOM_RZ;
+    s->step = 0;
+    s->primed = false;
+    s->prof = false;
+    std::memset(s->launches, 0, sizeof(s->launches));
+    // zero everything but the two particle buffers
+    const size_t z0 = L.count;
+    e = cudaMemsetAsync(w + z0, 0, L.total - z0, s->stream);
+    DevState d;
+    std::memset(&d, 0, sizeof(d));
+    d.V = c->V0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->st, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->xsE, s->h_xsE, sizeof(s->h_xsE), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->ray, s->h_ray, sizeof(s->h_ray), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "pd_create: %s\n", cudaGetErrorString(e));
+        delete s;
+        return PD_ERR_CUDA;
+    }
+    if (c->field_mode == PD_FIELD_POISSON) {
+        if (field_init(s->field, *c, w + L.field, L.field_bytes, s->stream) != 0) {
+            delete s;
+            return PD_ERR_CUDA;
+        }
+    }
+    pd_status ur = upload_ck(s);
+    if (ur != PD_OK) {
+        delete s;
+        return ur;
+    }
+    *out = s;
+    return PD_OK;
+}
+
+pd_status pd_set_cross_section(pd_sim* s, int ch, const double* E, const double* sig, int n, double threshold) {
+    if (!s) return PD_ERR_ARG;
+    if (ch < 0 || ch >= NCH || n < 2 || !E || !sig) return fail(s, PD_ERR_ARG, "bad cross-section arguments");
+    for (int a = 0; a + 1 < n; ++a)
+        if (!(E[a + 1] > E[a])) return fail(s, PD_ERR_ARG, "cross-section energies must ascend");
+    for (int k = 0; k < XS_N; ++k) {
+        const double e = (double)s->h_xsE[k];
+        double v;
+        if (e <= E[0]) v = sig[0];
+        else if (e >= E[n - 1]) v = sig[n - 1];
+        else {
+            int a = 0;
+            while (E[a + 1] <= e) ++a;
+            const double t = (e - E[a]) / (E[a + 1] - E[a]);
+            v = sig[a] + t * (sig[a + 1] - sig[a]);
+        }
+        if (e < threshold) v = 0.0;
+        if (ch == CH_DI && !s->cfg.di_on) v = 0.0;
+        s->h_xs[ch][k] = (float)v;
+    }
+    s->eth[ch] = threshold;
+    update_collision_consts(s);
+    CK(cudaMemcpyAsync(s->xs + (size_t)ch * XS_N, s->h_xs[ch], XS_N * 4, cudaMemcpyHostToDevice, s->stream));
+    return upload_ck(s);
+}
+
+pd_status pd_load_particles(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                            const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
+    if (!s) return PD_ERR_ARG;
+    if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
+    if (n == 0) return PD_OK;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    if (d.n_slots + (uint64_t)n > (uint64_t)s->cfg.capacity) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if ((uint64_t)d.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    std::vector<uint32_t> key(n), id(n);
+    for (int64_t q = 0; q < n; ++q) {
+        if (sp[q] >= NSP || iz[q] < 0 || iz[q] >= s->cfg.nz || ir[q] < 0 || ir[q] >= s->cfg.nr ||
+            !(pz[q] >= 0.0f && pz[q] < 1.0f) || !(pr[q] >= 0.0f && pr[q] < 1.0f))
+            return fail(s, PD_ERR_ARG, "particle " + std::to_string(q) + " out of range");
+        key[q] = ((uint32_t)sp[q] << 24) | ((uint32_t)iz[q] * (uint32_t)s->cfg.nr + (uint32_t)ir[q]);
+        id[q] = d.id_next + (uint32_t)q;
+    }
+    const size_t o = d.n_slots;
+    CK(cudaMemcpyAsync(s->A.key + o, key.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.pz + o, pz, n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.pr + o, pr, n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vz + o, vz, n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vr + o, vr, n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vt + o, vt, n * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.id + o, id.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
+    d.n_slots += (uint64_t)n;
+    d.id_next += (uint32_t)n;
+    CK(cudaMemcpyAsync(&s->st->n_slots, &d.n_slots, 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->st->id_next, &d.id_next, 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->primed = false;
+    return PD_OK;
+}
+
+pd_status pd_load_particles_device(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                                   const float* pz, const float* pr, const float* vz, const float* vr,
+                                   const float* vt) {
+    if (!s) return PD_ERR_ARG;
+    if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
+    if (n == 0) return PD_OK;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    if (d.n_slots + (uint64_t)n > (uint64_t)s->cfg.capacity) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if ((uint64_t)d.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    const size_t o = d.n_slots;
+    unsigned int bad = 0;
+    unsigned int* dbad = &s->st->load_bad;
+    CK(cudaMemsetAsync(dbad, 0, 4, s->stream));
+    launch_pack_keys(sp, iz, ir, pz, pr, n, s->cfg.nz, s->cfg.nr, d.id_next, s->A.key + o, s->A.id + o, dbad,
+                     grid_for(s, 8), s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(s->A.pz + o, pz, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.pr + o, pr, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vz + o, vz, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vr + o, vr, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vt + o, vt, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (bad) return fail(s, PD_ERR_ARG, "a device particle is out of range");
+    d.n_slots += (uint64_t)n;
+    d.id_next += (uint32_t)n;
+    CK(cudaMemcpyAsync(&s->st->n_slots, &d.n_slots, 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->st->id_next, &d.id_next, 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->primed = false;
+    return PD_OK;
+}
+
+pd_status pd_set_field(pd_sim* s, const double* Ez, const double* Er) {
+    if (!s || !Ez || !Er) return PD_ERR_ARG;
+    const pd_config& c = s->cfg;
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    std::vector<float2> h(nodes);
+    for (size_t k = 0; k < nodes; ++k) h[k] = make_float2((float)Ez[k], (float)Er[k]);
+    CK(cudaMemcpyAsync(s->E, h.data(), nodes * 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
+pd_status pd_inject_cathode(pd_sim* s, int enable) {
+    if (!s) return PD_ERR_ARG;
+    if (enable && s->cfg.geometry != PD_GEOM_RZ) return fail(s, PD_ERR_ARG, "injection needs r-z");
+    s->inject_on = enable ? 1 : 0;
+    return PD_OK;
+}
+
+pd_status pd_step(pd_sim* s, int64_t n_steps) {
+    if (!s) return PD_ERR_ARG;
+    if (n_steps < 0) return fail(s, PD_ERR_ARG, "n_steps < 0");
+    const pd_config& c = s->cfg;
+    if (!s->primed) {
+        pd_status r = prime(s);
+        if (r != PD_OK) return r;
+    }
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    const PushConsts pc = push_consts(c);
+    const uint32_t ncell = (uint32_t)c.nz * (uint32_t)c.nr;
+    const uint32_t nbins = ncell * NSP;
+    const int gpart = grid_for(s, 8);
+    for (int64_t it = 0; it < n_steps; ++it) {
+        const int heavy = (s->step % c.heavy_subcycle) == 0;
+        const KParams P = kparams(s, heavy);
+        if (s->inject_on) {
+            Timed t(s, K_INJECT);
+            launch_inject(s->A, s->E, s->st, P, s->ic, s->ray, s->stream);
+        }
+        {
+            Timed t(s, K_MEMSET);
+            cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
+            if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
+        }
+        {
+            Timed t(s, K_PUSH);
+            launch_push(s->A, s->E, s->rho_e, s->rho_h, s->count, s->st, P, pc, gpart, s->stream);
+        }
+        {
+            Timed t(s, K_SCAN_BINS);
+            launch_scan(s->count, s->off, s->partial, s->L.nbins_pad, s->stream);
+        }
+        {
+            Timed t(s, K_SCATTER);
+            launch_scatter(s->A, s->B, s->off, s->count, s->st, P, gpart, s->stream);
+        }
+        std::swap(s->A, s->B);
+        {
+            Timed t(s, K_NCAND);
+            launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, 8), s->stream);
+        }
+        {
+            Timed t(s, K_SCAN_CAND);
+            launch_scan(s->cand, s->cand_off, s->partial, s->L.ncell_pad, s->stream);
+        }
+        {
+            Timed t(s, K_COLLIDE);
+            launch_collide(s->A, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P,
+                           s->cc, nbins, grid_for(s, 16), s->stream);
+        }
+        {
+            Timed t(s, K_FINALIZE);
+            launch_finalize(s->off, nbins, s->cand_off, ncell, s->st, P, c.dt, c.V0, c.R_ohm, c.C_farad,
+                            c.geometry == PD_GEOM_RZ, s->stream);
+        }
+        if (c.field_mode == PD_FIELD_POISSON) {
+            Timed t(s, K_POISSON);
+            field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->st, s->stream);
+        }
+        s->step += 1;
+    }
+    CK(cudaGetLastError());
+    return PD_OK;
+}
+
+pd_status pd_synchronize(pd_sim* s) {
+    if (!s) return PD_ERR_ARG;
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status pd_get_scalars(pd_sim* s, pd_scalars* out) {
+    if (!s || !out) return PD_ERR_ARG;
+    CK(cudaMemsetAsync(s->spc, 0, NSP * 8, s->stream));
+    launch_species_count(s->A, s->st, s->spc, grid_for(s, 4), s->stream);
+    unsigned long long cnt[NSP];
+    CK(cudaMemcpyAsync(cnt, s->spc, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    std::memset(out, 0, sizeof(*out));
+    const pd_config& c = s->cfg;
+    out->t = (double)s->step * c.dt;
+    out->V = d.V;
+    out->I_gap = d.I_gap;
+    const double n0 = (double)cnt[SP_CU], n1 = (double)cnt[SP_CUP], n2 = (double)(cnt[SP_CU2_SW] + cnt[SP_CU2_DI]);
+    const double ions = n1 + n2, all = n0 + ions;
+    out->gamma = all > 0 ? ions / all : 0.0;
+    out->Qbar = ions > 0 ? (n1 + 2.0 * n2) / ions : 0.0;
+    double heavy_back = 0;
+    for (int sp = 1; sp < NSP; ++sp) heavy_back += (double)d.ctr[C_ABS + 0 * NSP + sp];
+    out->mass = M_CU * c.weight * ((double)d.ctr[C_EMIT_CU] - heavy_back);
+    out->charge = d.charge_cathode;
+    out->erosion = out->charge != 0 ? out->mass / out->charge : 0.0;
+    out->sgmax[0] = s->cc.sgmax[0];
+    out->sgmax[1] = s->cc.sgmax[1];
+    out->poisson_relres = d.relres;
+    out->poisson_cycles = d.cycles;
+    for (int k = 0; k < 3; ++k) out->absorbed_energy[k] = d.absorbed_energy[k];
+    int64_t tot = 0;
+    for (int sp = 0; sp < NSP; ++sp) {
+        out->count[sp] = (int64_t)cnt[sp];
+        tot += (int64_t)cnt[sp];
+    }
+    out->n_particles = tot;
+    out->step = s->step;
+    return PD_OK;
+}
+
+pd_status pd_get_counters(pd_sim* s, uint64_t* out) {
+    if (!s || !out) return PD_ERR_ARG;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    for (int k = 0; k < NCOUNTERS; ++k) out[k] = d.ctr[k];
+    return PD_OK;
+}
+
+pd_status pd_particle_slots(pd_sim* s, int64_t* slots) {
+    if (!s || !slots) return PD_ERR_ARG;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    *slots = (int64_t)d.n_slots;
+    return PD_OK;
+}
+
+pd_status pd_get_particles(pd_sim* s, uint32_t* id, uint8_t* sp, int32_t* iz, int32_t* ir, float* pz, float* pr,
+                           float* vz, float* vr, float* vt) {
+    if (!s) return PD_ERR_ARG;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    const size_t n = d.n_slots;
+    if (n == 0) return PD_OK;
+    std::vector<uint32_t> key(n);
+    CK(cudaMemcpyAsync(key.data(), s->A.key, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(id, s->A.id, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(pz, s->A.pz, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(pr, s->A.pr, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vz, s->A.vz, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vr, s->A.vr, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(vt, s->A.vt, n * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (size_t q = 0; q < n; ++q) {
+        if (key[q] == DEAD) {
+            sp[q] = 255;
+            iz[q] = -1;
+            ir[q] = -1;
+            continue;
+        }
+        const uint32_t cell = key[q] & 0xFFFFFFu;
+        sp[q] = (uint8_t)(key[q] >> 24);
+        iz[q] = (int32_t)(cell / (uint32_t)s->cfg.nr);
+        ir[q] = (int32_t)(cell % (uint32_t)s->cfg.nr);
+    }
+    return PD_OK;
+}
+
+pd_status pd_get_rho(pd_sim* s, int64_t* rho_e, int64_t* rho_h) {
+    if (!s) return PD_ERR_ARG;
+    const pd_config& c = s->cfg;
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    if (rho_e) CK(cudaMemcpyAsync(rho_e, s->rho_e, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    if (rho_h) CK(cudaMemcpyAsync(rho_h, s->rho_h, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status pd_get_phi(pd_sim* s, double* phi) {
+    if (!s || !phi) return PD_ERR_ARG;
+    const pd_config& c = s->cfg;
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    CK(cudaMemcpyAsync(phi, s->phi, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status pd_get_field(pd_sim* s, double* Ez, double* Er) {
+    if (!s || !Ez || !Er) return PD_ERR_ARG;
+    const pd_config& c = s->cfg;
+    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    std::vector<float2> h(nodes);
+    CK(cudaMemcpyAsync(h.data(), s->E, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    for (size_t k = 0; k < nodes; ++k) {
+        Ez[k] = h[k].x;
+        Er[k] = h[k].y;
+    }
+    return PD_OK;
+}
+
+pd_status pd_get_density_map(pd_sim* s, int species, double* out) {
+    if (!s || !out || species < 0 || species >= NSP) return PD_ERR_ARG;
+    const pd_config& c = s->cfg;
+    const int nzn = c.geometry == PD_GEOM_RZ ? c.nz + 1 : c.nz, nrn = c.geometry == PD_GEOM_RZ ? c.nr + 1 : c.nr;
+    const size_t nodes = (size_t)nzn * nrn;
+    CK(cudaMemsetAsync(s->diag, 0, nodes * 8, s->stream));
+    launch_density(s->A, s->st, kparams(s, 1), species, s->diag, grid_for(s, 8), s->stream);
+    std::vector<long long> h(nodes);
+    CK(cudaMemcpyAsync(h.data(), s->diag, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    for (int i = 0; i < nzn; ++i)
+        for (int j = 0; j < nrn; ++j) {
+            const size_t k = (size_t)i * nrn + j;
+            out[k] = c.weight * (double)h[k] / 4294967296.0 / node_volume(c, i, j);
+        }
+    return PD_OK;
+}
+
+pd_status pd_get_energy_spectrum(pd_sim* s, int species, double lo, double hi, int nbins, uint64_t* out) {
+    if (!s || !out || species < 0 || species >= NSP || nbins < 1 || nbins > 4096 || !(hi > lo))
+        return PD_ERR_ARG;
+    CK(cudaMemsetAsync(s->hist, 0, (size_t)nbins * 8, s->stream));
+    launch_spectrum(s->A, s->st, kparams(s, 1), species, lo, hi, nbins, s->hist, grid_for(s, 8), s->stream);
+    CK(cudaMemcpyAsync(out, s->hist, (size_t)nbins * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status pd_profile_enable(pd_sim* s, int enable) {
+    if (!s) return PD_ERR_ARG;
+    s->prof = enable != 0;
+    if (s->prof && s->pool.empty()) {
+        for (int k = 0; k < 8192; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) break;
+            s->pool.push_back(e);
+        }
+    }
+    return PD_OK;
+}
+
+pd_status pd_profile_read(pd_sim* s, double* ms, uint64_t* launches) {
+    if (!s) return PD_ERR_ARG;
+    CK(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < PD_NKERNELS; ++k) {
+        if (ms) ms[k] = 0.0;
+        if (launches) launches[k] = s->launches[k];
+        s->launches[k] = 0;
+    }
+    for (auto& r : s->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && ms) ms[r.k] += t;
+        s->pool.push_back(r.a);
+        s->pool.push_back(r.b);
+    }
+    s->recs.clear();
+    return PD_OK;
+}
+
+const char* pd_kernel_name(int k) { return (k >= 0 && k < PD_NKERNELS) ? KNAMES[k] : "?"; }
+
+const char* pd_last_error(const pd_sim* s) { return s ? s->err.c_str() : "null simulation"; }
+
+void pd_destroy(pd_sim* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (auto& r : s->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : s->pool) cudaEventDestroy(e);
+    field_free(s->field);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,525 @@
+// pd_collide.cu -- DSMC electron-impact collisions and cathode injection.
+//
+// Collisions (Sec. 2.1 Eq. (4)-(7), Sec. 2.2 Eq. (11)-(20)) in no-time-counter
+// form, per cell and pair class k in {(e, Cu), (e, Cu+)}:
+//   k_ncand    N_cand = floor(N_e N_t c_k(r) + R), c_k = W (sigma g)_max dt_coll / V_cell,
+//              one thread per cell; cells with candidates go to an active list.
+//   k_collide  one warp per active cell.  Candidate m draws from the stream
+//              (cell, step, k<<28 | m): the electron and target ranks (in
+//              ascending-id order inside the cell, found by a warp radix
+//              select), the acceptance number and the channel number.  Lane 0
+//              applies the kinematics.  Spawned electrons go to the slots
+//              reserved for the cell at n_alive + 2 * (candidates of the
+//              cells before it); unused reserved slots are marked dead.
+//   k_finalize slot / id bookkeeping and the RC circuit update.
+// Compiled with -fmad=false (decision arithmetic is rounded op by op).
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+namespace pd {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct V3 {
+    float x, y, z;
+};
+
+// sigma(eps): linear interpolation on the grid E_k = 2^e (1 + j/64); the
+// bracketing index comes from the exponent and top six mantissa bits of eps.
+__device__ __forceinline__ float xs_lookup(const float* __restrict__ E, const float* __restrict__ s, float eps) {
+    if (!(eps < E[XS_N - 1])) return 0.0f;
+    int k;
+    if (eps < E[0]) {
+        k = 0;
+        eps = E[0];
+    } else {
+        const uint32_t b = __float_as_uint(eps);
+        k = ((int)(b >> 23) - 127 - XS_EMIN_EXP) * XS_SUB + (int)((b >> 17) & 63u);
+    }
+    const float t = (eps - E[k]) / (E[k + 1] - E[k]);
+    return s[k] + t * (s[k + 1] - s[k]);
+}
+
+// isotropic unit vector, Marsaglia (1972)
+__device__ V3 iso_dir(Stream& st, uint32_t& fb) {
+    for (int a = 0; a < 64; ++a) {
+        const float u1 = 2.0f * st.u01() - 1.0f;
+        const float u2 = 2.0f * st.u01() - 1.0f;
+        const float s = u1 * u1 + u2 * u2;
+        if (s < 1.0f) {
+            const float q = 2.0f * sqrtf(1.0f - s);
+            return V3{u1 * q, u2 * q, 1.0f - 2.0f * s};
+        }
+    }
+    ++fb;
+    return V3{0.0f, 0.0f, 1.0f};
+}
+
+// uniform azimuth (cos, sin) from a point of the unit disc
+__device__ void azimuth(Stream& st, float& c, float& s, uint32_t& fb) {
+    for (int a = 0; a < 64; ++a) {
+        const float u1 = 2.0f * st.u01() - 1.0f;
+        const float u2 = 2.0f * st.u01() - 1.0f;
+        const float q = u1 * u1 + u2 * u2;
+        if (q < 1.0f && q > 0.0f) {
+            const float r = sqrtf(q);
+            c = u1 / r;
+            s = u2 / r;
+            return;
+        }
+    }
+    ++fb;
+    c = 1.0f;
+    s = 0.0f;
+}
+
+// Eq. (6): |u'|^2 = |u|^2 - 2 E_th / m_r (kth); Eq. (7) isotropic direction;
+// Eq. (5): v1 += (u' - u) m_r/m1, v2 -= (u' - u) m_r/m2.
+__device__ bool binary_scatter(Stream& st, V3& v1, V3& v2, float kth, float a1, float a2, uint32_t& fb) {
+    const V3 u{v1.x - v2.x, v1.y - v2.y, v1.z - v2.z};
+    const float g2 = (u.x * u.x + u.y * u.y) + u.z * u.z;
+    const float up2 = g2 - kth;
+    if (up2 < 0.0f) return false;
+    const float gp = sqrtf(up2);
+    const V3 n = iso_dir(st, fb);
+    const V3 du{gp * n.x - u.x, gp * n.y - u.y, gp * n.z - u.z};
+    v1.x = v1.x + du.x * a1;
+    v1.y = v1.y + du.y * a1;
+    v1.z = v1.z + du.z * a1;
+    v2.x = v2.x - du.x * a2;
+    v2.y = v2.y - du.y * a2;
+    v2.z = v2.z - du.z * a2;
+    return true;
+}
+
+// Eq. (15)-(20): v5 = cos(chi) |v| R^T(theta, phi) (sin chi cos psi,
+// sin chi sin psi, cos chi); v6 = v - v5; theta, phi from the components of v.
+__device__ void rectangle_split(Stream& st, const V3& v, V3& v5, V3& v6, int mode, uint32_t& fb) {
+    float cchi = st.u01();
+    if (mode == 1) cchi = sqrtf(cchi);
+    const float schi = sqrtf(1.0f - cchi * cchi);
+    float cpsi, spsi;
+    azimuth(st, cpsi, spsi, fb);
+    const float vperp2 = v.x * v.x + v.y * v.y;
+    const float vmag2 = vperp2 + v.z * v.z;
+    const float vmag = sqrtf(vmag2), vperp = sqrtf(vperp2);
+    V3 w5{0.0f, 0.0f, 0.0f};
+    if (vmag > 0.0f) {
+        const float ct = v.z / vmag, sth = vperp / vmag;
+        float cp = 1.0f, sp = 0.0f;
+        if (vperp > 0.0f) {
+            cp = v.x / vperp;
+            sp = v.y / vperp;
+        }
+        const float a = cchi * vmag;
+        const float w1 = a * (schi * cpsi), w2 = a * (schi * spsi), w3 = a * cchi;
+        w5.x = (w1 * (ct * cp) - w2 * sp) + w3 * (sth * cp);
+        w5.y = (w1 * (ct * sp) + w2 * cp) + w3 * (sth * sp);
+        w5.z = w3 * ct - w1 * sth;
+    }
+    v5 = w5;
+    v6 = V3{v.x - w5.x, v.y - w5.y, v.z - w5.z};
+}
+
+// single-particle fixed-point CIC deposit of zq at (cell, pz, pr)
+__device__ void deposit1(long long* rho, const KParams& P, uint32_t cell, float pz, float pr, int zq) {
+    const int iz = (int)(cell / (uint32_t)P.nr);
+    const int ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+    const uint32_t wz = __float2uint_rn(pz * 65536.0f);
+    const uint32_t wr = __float2uint_rn(pr * 65536.0f);
+    const long long az = 65536 - (long long)wz, ar = 65536 - (long long)wr;
+    atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir)], (unsigned long long)(zq * az * ar));
+    atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir)], (unsigned long long)(zq * (long long)wz * ar));
+    atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir + 1)], (unsigned long long)(zq * az * (long long)wr));
+    atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir + 1)],
+              (unsigned long long)(zq * (long long)wz * (long long)wr));
+}
+
+// k-th smallest id of ids[0..N) and its position; the whole warp takes part
+__device__ uint32_t select_rank(const uint32_t* __restrict__ ids, uint32_t N, uint32_t rank, int lane) {
+    uint32_t prefix = 0, want = rank;
+    for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
+        uint32_t cnt = 0;
+        for (uint32_t q = lane; q < N; q += 32) {
+            const uint32_t id = ids[q];
+            cnt += ((id & hm) == prefix && !((id >> bit) & 1u)) ? 1u : 0u;
+        }
+        cnt = __reduce_add_sync(FULL, cnt);
+        if (want >= cnt) {
+            want -= cnt;
+            prefix |= 1u << bit;
+        }
+    }
+    uint32_t pos = 0xFFFFFFFFu;
+    for (uint32_t q = lane; q < N; q += 32)
+        if (ids[q] == prefix) pos = q;
+    return __reduce_min_sync(FULL, pos);
+}
+
+__global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
+                                               uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
+                                               KParams P) {
+    const uint32_t C = P.ncell;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); c0 < C; c0 += stride) {
+        const uint32_t c = c0 + lane;
+        uint32_t n0 = 0, n1 = 0;
+        if (c < C) {
+            const uint32_t Ne = off[c + 1] - off[c];
+            const uint32_t Ncu = off[C + c + 1] - off[C + c];
+            const uint32_t Ni = off[2 * C + c + 1] - off[2 * C + c];
+            if (Ne > 0 && (Ncu > 0 || Ni > 0)) {
+                const uint32_t j = c % (uint32_t)P.nr;
+                Stream s(c, P.step, SID_NCAND, P.seed, P.run);
+                const float R0 = s.u01();
+                const float R1 = s.u01();
+                const float x0 = ((float)Ne * (float)Ncu) * ck[j] + R0;
+                const float x1 = ((float)Ne * (float)Ni) * ck[P.nr + j] + R1;
+                n0 = (uint32_t)floorf(x0);
+                n1 = (uint32_t)floorf(x1);
+            }
+            nc[c] = make_uint2(n0, n1);
+            cand[c] = n0 + n1;
+        }
+        const bool act = c < C && (n0 + n1) > 0;
+        const unsigned m = __ballot_sync(FULL, act);
+        if (m) {
+            unsigned long long base = 0;
+            if (lane == __ffs(m) - 1) base = atomicAdd(&st->n_active, (unsigned long long)__popc(m));
+            base = __shfl_sync(FULL, base, __ffs(m) - 1);
+            if (act) {
+                unsigned lt;
+                asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+                active[base + __popc(m & lt)] = c;
+            }
+        }
+    }
+}
+
+struct CellCtx {
+    uint32_t cell;
+    unsigned long long slot0;        // first reserved spawn slot
+    uint32_t nres;                   // reserved slots
+    uint32_t id0;                    // id of the first reserved slot
+    uint32_t s;                      // spawned so far
+    uint32_t ev[NCH], nulls, consumed, thr, viol, fb;
+};
+
+__device__ bool spawn_electron(Particles& A, CellCtx& cx, const KParams& P, DevState* st, long long* rho_e,
+                               uint32_t cell, float pz, float pr, const V3& v) {
+    if (cx.s >= cx.nres) {
+        set_error(st, ERR_BOUNDS);
+        return false;
+    }
+    const unsigned long long slot = cx.slot0 + cx.s;
+    A.key[slot] = make_key(SP_E, cell);
+    A.pz[slot] = pz;
+    A.pr[slot] = pr;
+    A.vz[slot] = v.x;
+    A.vr[slot] = v.y;
+    A.vt[slot] = v.z;
+    A.id[slot] = cx.id0 + cx.s;
+    ++cx.s;
+    deposit1(rho_e, P, cell, pz, pr, -1);
+    return true;
+}
+
+// lane-0 part of one candidate after the pair is chosen
+__device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
+                                  float Racc, float Rch, const float* __restrict__ xsE, const float* __restrict__ xs,
+                                  const KParams& P, const CollConsts& cc, DevState* st, long long* rho_e,
+                                  long long* rho_h) {
+    const int ts = k == 0 ? SP_CU : SP_CUP;
+    const uint32_t tkey = A.key[it];
+    if ((int)key_species(tkey) != ts) {      // target already ionized this step
+        ++cx.consumed;
+        return;
+    }
+    V3 ve{A.vz[ie], A.vr[ie], A.vt[ie]};
+    V3 vt{A.vz[it], A.vr[it], A.vt[it]};
+    const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
+    const float g2 = (ux * ux + uy * uy) + uz * uz;
+    const float g = sqrtf(g2);
+    const float eps = g2 * cc.kmr;
+    const int ch0 = k == 0 ? CH_EL : CH_SW;
+    const int nch = k == 0 ? 4 : 1;
+    float cum[4];
+    float sT = 0.0f;
+    for (int q = 0; q < nch; ++q) {
+        sT = sT + xs_lookup(xsE, xs + (ch0 + q) * XS_N, eps);
+        cum[q] = sT;
+    }
+    const float sg = sT * g;
+    if (sg > cc.sgmax[k]) ++cx.viol;
+    if (!(Racc * cc.sgmax[k] < sg)) {
+        ++cx.nulls;
+        return;
+    }
+    const float r = Rch * sT;
+    int q = -1;
+    for (int a = 0; a < nch; ++a)
+        if (r < cum[a]) {
+            q = a;
+            break;
+        }
+    if (q < 0) {
+        q = nch - 1;
+        for (int a = nch - 1; a >= 0; --a)
+            if (cum[a] > (a ? cum[a - 1] : 0.0f)) {
+                q = a;
+                break;
+            }
+    }
+    const int ch = ch0 + q;
+    if (ch == CH_EL || ch == CH_EXC) {
+        if (!binary_scatter(rs, ve, vt, ch == CH_EL ? 0.0f : cc.kth[ch], cc.a_e, cc.a_t, cx.fb)) {
+            ++cx.thr;
+            return;
+        }
+        A.vz[ie] = ve.x; A.vr[ie] = ve.y; A.vt[ie] = ve.z;
+        A.vz[it] = vt.x; A.vr[it] = vt.y; A.vt[it] = vt.z;
+        ++cx.ev[ch];
+        return;
+    }
+    // Stage 1, Eq. (12): e + A -> e1 + A*, losing the threshold energy
+    if (!binary_scatter(rs, ve, vt, cc.kth[ch], cc.a_e, cc.a_t, cx.fb)) {
+        ++cx.thr;
+        return;
+    }
+    // Stage 2, Eq. (13): A* -> e2 + ion with the position and velocity of A*
+    V3 e2 = vt;
+    // Stage 3, Eq. (14): e1 + e2 elastic, equal masses
+    binary_scatter(rs, ve, e2, 0.0f, 0.5f, 0.5f, cx.fb);
+    const int new_sp = ch == CH_SI ? SP_CUP : (ch == CH_SW ? SP_CU2_SW : SP_CU2_DI);
+    const int dq = charge_of(new_sp) - charge_of(ts);
+    V3 keep = ve, e6{0.0f, 0.0f, 0.0f};
+    if (ch == CH_DI) {
+        // Stage 4, Eq. (15): e3 -> e5 + e6 (velocity rectangle)
+        V3 e5;
+        rectangle_split(rs, ve, e5, e6, cc.di_split_mode, cx.fb);
+        keep = e5;
+    }
+    A.vz[ie] = keep.x; A.vr[ie] = keep.y; A.vt[ie] = keep.z;
+    A.vz[it] = vt.x; A.vr[it] = vt.y; A.vt[it] = vt.z;
+    const uint32_t tcell = key_cell(tkey);
+    A.key[it] = make_key((uint32_t)new_sp, tcell);
+    const float tpz = A.pz[it], tpr = A.pr[it];
+    deposit1(rho_h, P, tcell, tpz, tpr, dq);
+    spawn_electron(A, cx, P, st, rho_e, tcell, tpz, tpr, e2);
+    if (ch == CH_DI) spawn_electron(A, cx, P, st, rho_e, key_cell(A.key[ie]), A.pz[ie], A.pr[ie], e6);
+    ++cx.ev[ch];
+}
+
+__global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __restrict__ off,
+                                                 const uint2* __restrict__ nc, const uint32_t* __restrict__ cand_off,
+                                                 const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
+                                                 long long* rho_h, const float* __restrict__ xsE,
+                                                 const float* __restrict__ xs, KParams P, CollConsts cc,
+                                                 uint32_t nbins) {
+    const unsigned long long n_active = st->n_active;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long warp0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    const uint32_t C = P.ncell;
+    const uint32_t n_alive = off[nbins];
+    const uint32_t id_next = st->id_next;
+    for (unsigned long long w = warp0; w < n_active; w += nwarps) {
+        const uint32_t c = active[w];
+        const uint2 n = nc[c];
+        CellCtx cx;
+        cx.cell = c;
+        cx.nres = 2u * (n.x + n.y);
+        cx.slot0 = (unsigned long long)n_alive + 2ull * cand_off[c];
+        cx.id0 = id_next + 2u * cand_off[c];
+        cx.s = 0;
+        for (int q = 0; q < NCH; ++q) cx.ev[q] = 0;
+        cx.nulls = cx.consumed = cx.thr = cx.viol = cx.fb = 0;
+        if (cx.slot0 + cx.nres > P.capacity) {
+            // no room for this cell's spawns: report, and leave its reserved
+            // slots (those that exist) dead
+            if (lane == 0) set_error(st, ERR_CAPACITY);
+            for (unsigned long long q = cx.slot0 + lane; q < P.capacity && q < cx.slot0 + cx.nres; q += 32)
+                A.key[q] = DEAD;
+            continue;
+        }
+        const uint32_t e_base = off[c];
+        const uint32_t Ne = off[c + 1] - e_base;
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t tb = (k == 0 ? C : 2 * C) + c;
+            const uint32_t t_base = off[tb];
+            const uint32_t Nt = off[tb + 1] - t_base;
+            const uint32_t ncand = k == 0 ? n.x : n.y;
+            for (uint32_t m = 0; m < ncand; ++m) {
+                Stream rs(c, P.step, sid_cand(k, m), P.seed, P.run);
+                const uint32_t i = rs.pick(Ne);
+                const uint32_t j = rs.pick(Nt);
+                const float Racc = rs.u01();
+                const float Rch = rs.u01();
+                const uint32_t pe = select_rank(A.id + e_base, Ne, i, lane);
+                const uint32_t pt = select_rank(A.id + t_base, Nt, j, lane);
+                if (pe >= Ne || pt >= Nt) {       // ids not unique: corrupt state, never index with it
+                    if (lane == 0) set_error(st, ERR_BOUNDS);
+                    continue;
+                }
+                if (lane == 0)
+                    process_candidate(A, cx, rs, k, e_base + pe, t_base + pt, Racc, Rch, xsE, xs, P, cc, st, rho_e,
+                                      rho_h);
+                __syncwarp();
+            }
+        }
+        const uint32_t s = __shfl_sync(FULL, cx.s, 0);
+        for (uint32_t q = s + lane; q < cx.nres; q += 32) A.key[cx.slot0 + q] = DEAD;
+        if (lane == 0) {
+            for (int q = 0; q < NCH; ++q)
+                if (cx.ev[q]) atomicAdd(&st->ctr[C_EV + q], (unsigned long long)cx.ev[q]);
+            if (cx.nulls) atomicAdd(&st->ctr[C_NULL], (unsigned long long)cx.nulls);
+            if (cx.consumed) atomicAdd(&st->ctr[C_CONSUMED], (unsigned long long)cx.consumed);
+            if (cx.thr) atomicAdd(&st->ctr[C_THR], (unsigned long long)cx.thr);
+            if (cx.viol) atomicAdd(&st->ctr[C_VIOL], (unsigned long long)cx.viol);
+            if (cx.fb) atomicAdd(&st->ctr[C_ISOFB], (unsigned long long)cx.fb);
+        }
+    }
+}
+
+__global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, const uint32_t* __restrict__ cand_off,
+                           uint32_t ncell, DevState* st, KParams P, double dt, double V0, double R_ohm,
+                           double C_farad, int circuit) {
+    const unsigned long long T = cand_off[ncell];
+    unsigned long long ns = (unsigned long long)off[nbins] + 2ull * T;
+    if (ns > P.capacity) {
+        set_error(st, ERR_CAPACITY);
+        ns = P.capacity;
+    }
+    st->n_slots = ns;
+    if ((unsigned long long)st->id_next + 2ull * T > 0xFFFFFFFFull) set_error(st, ERR_IDS);
+    st->id_next += (uint32_t)(2ull * T);
+    st->ctr[C_CAND] += T;
+    st->n_active = 0;
+    if (circuit) {
+        // C dV/dt = (V0 - V)/R - I_gap; the gap current leaves the anode node
+        const double I = -st->anode_charge_step / dt;
+        st->I_gap = I;
+        st->V += dt / C_farad * ((V0 - st->V) / R_ohm - I);
+        st->anode_charge_step = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------
+// cathode injection (Sec. 2.3): FN electrons from the tip and neutrals at
+// a fixed fraction of the electron flux; one block.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float rayleigh(const float* __restrict__ ray, float U) {
+    const float x = U * 1023.0f;
+    const int k = min((int)x, 1022);
+    const float t = x - (float)k;
+    return ray[k] + t * (ray[k + 1] - ray[k]);
+}
+
+__global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __restrict__ E, DevState* st, KParams P,
+                                                InjectConsts ic, const float* __restrict__ ray) {
+    __shared__ uint32_t ne_s[64], nn_s[64], pre_s[65];
+    const int t = threadIdx.x;
+    if (t < ic.ntip) {
+        const int j = t;
+        const double ezs = 0.5 * ((double)E[j].x + (double)E[j + 1].x);
+        const double F = ic.beta * (ezs < 0 ? -ezs : 0.0);
+        double J = 0.0;
+        if (F > 0.0) {
+            const double Afn = 1.541434e-6, Bfn = 6.830890e9;
+            J = Afn / ic.work * F * F * exp(-Bfn * ic.work * sqrt(ic.work) / F);
+        }
+        const double lam_e = J * ic.area[j] * ic.dt / (1.602176634e-19 * ic.weight);
+        const double lam_n = ic.ratio * lam_e;
+        Stream s((uint32_t)j, P.step, SID_INJ_COUNT, P.seed, P.run);
+        const double Re = (double)s.u01(), Rn = (double)s.u01();
+        ne_s[j] = (uint32_t)floor(lam_e + Re);
+        nn_s[j] = (uint32_t)floor(lam_n + Rn);
+    }
+    __syncthreads();
+    if (t == 0) {
+        uint32_t acc = 0;
+        for (int j = 0; j < ic.ntip; ++j) {
+            pre_s[j] = acc;
+            acc += ne_s[j] + nn_s[j];
+        }
+        pre_s[ic.ntip] = acc;
+    }
+    __syncthreads();
+    const uint32_t total = pre_s[ic.ntip];
+    const unsigned long long slot0 = st->n_slots;
+    const uint32_t id0 = st->id_next;
+    uint32_t emitted_e = 0, emitted_cu = 0;
+    uint32_t fb = 0;
+    for (uint32_t p = t; p < total; p += blockDim.x) {
+        int j = 0;
+        while (pre_s[j + 1] <= p) ++j;
+        const uint32_t loc = p - pre_s[j];
+        const bool is_e = loc < ne_s[j];
+        Stream sp((uint32_t)j, P.step, is_e ? sid_inj_e(loc) : sid_inj_cu(loc - ne_s[j]), P.seed, P.run);
+        const float U = sp.u01();
+        const float lo = ic.lo[j], hi = ic.hi[j];
+        const float rr = sqrtf(lo * lo + U * (hi * hi - lo * lo));
+        float pr = rr - lo;
+        if (pr >= 1.0f) pr = 0x1.fffffep-1f;
+        if (pr < 0.0f) pr = 0.0f;
+        float vz = 0.f, vr = 0.f, vt = 0.f;
+        if (!is_e) {
+            const float U1 = sp.u01(), U2 = sp.u01();
+            vz = ic.vth * rayleigh(ray, U1);
+            const float s = ic.vth * rayleigh(ray, U2);
+            float cp, sn;
+            azimuth(sp, cp, sn, fb);
+            vr = s * cp;
+            vt = s * sn;
+        }
+        const unsigned long long slot = slot0 + p;
+        if (slot >= P.capacity) {
+            set_error(st, ERR_CAPACITY);
+            continue;
+        }
+        A.key[slot] = make_key(is_e ? SP_E : SP_CU, (uint32_t)j);   // iz = 0
+        A.pz[slot] = 0.0f;
+        A.pr[slot] = pr;
+        A.vz[slot] = vz;
+        A.vr[slot] = vr;
+        A.vt[slot] = vt;
+        A.id[slot] = id0 + p;
+        if (is_e) ++emitted_e; else ++emitted_cu;
+    }
+    if (emitted_e) {
+        atomicAdd(&st->ctr[C_EMIT_E], (unsigned long long)emitted_e);
+        for (uint32_t q = 0; q < emitted_e; ++q) atomicAdd(&st->charge_cathode, 1.602176634e-19 * ic.weight);
+    }
+    if (emitted_cu) atomicAdd(&st->ctr[C_EMIT_CU], (unsigned long long)emitted_cu);
+    if (fb) atomicAdd(&st->ctr[C_ISOFB], (unsigned long long)fb);
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long ns = slot0 + total;
+        st->n_slots = ns > P.capacity ? P.capacity : ns;
+        st->id_next = id0 + total;
+    }
+}
+
+void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
+                  const KParams& P, int grid, cudaStream_t s) {
+    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, st, P);
+}
+void launch_collide(const Particles& A, const uint32_t* off, const uint2* nc, const uint32_t* cand_off,
+                    const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h, const float* xsE,
+                    const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins, int grid,
+                    cudaStream_t s) {
+    k_collide<<<grid, 128, 0, s>>>(A, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
+}
+void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, uint32_t ncell, DevState* st,
+                     const KParams& P, double dt, double V0, double R_ohm, double C_farad, int circuit,
+                     cudaStream_t s) {
+    k_finalize<<<1, 1, 0, s>>>(off, nbins, cand_off, ncell, st, P, dt, V0, R_ohm, C_farad, circuit);
+}
+void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts& ic,
+                   const float* ray, cudaStream_t s) {
+    k_inject<<<1, 256, 0, s>>>(A, E, st, P, ic, ray);
+}
+
+}  // namespace pd

@@ -1,0 +1,155 @@
+// pd_internal.cuh -- device-side definitions shared by the library's kernels.
+//
+// Particle store (structure of arrays, one slot per super-particle):
+//   key  u32  (species << 24) | cell, cell = iz * nr + ir; PD_DEAD for a free slot
+//   pz, pr    f32 offset inside the cell, in [0, 1)
+//   vz, vr, vt f32 velocity (m/s)
+//   id   u32  particle id (ascending id = canonical order inside a cell)
+// 28 bytes per particle.  Two copies (A, B): the counting sort scatters A
+// into B in (species, cell) order each step and the two are swapped.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pd {
+
+constexpr uint32_t DEAD = 0xFFFFFFFFu;
+constexpr int NSP = 5;
+constexpr int NCH = 5;
+constexpr int SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4;
+constexpr int CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4;
+
+// cross-section grid: 64 points per octave from 2^-10 eV over 25 octaves
+constexpr int XS_EMIN_EXP = -10;
+constexpr int XS_OCT = 25;
+constexpr int XS_SUB = 64;
+constexpr int XS_N = XS_OCT * XS_SUB + 1;
+
+// sticky device error bits
+constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_IDS = 8u, ERR_BOUNDS = 16u;
+
+// counter slots (see PD_NCOUNTERS in pd.h)
+constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
+              C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, NCOUNTERS = 28;
+
+// Device-resident scalars of one simulation.
+struct DevState {
+    unsigned long long n_slots;      // slots of buffer A in use (live + dead)
+    unsigned long long n_active;     // cells with collision candidates this step
+    unsigned int id_next;            // next particle id
+    unsigned int error;              // ERR_* bits
+    unsigned long long ctr[NCOUNTERS];
+    double absorbed_energy[3];
+    double charge_cathode;           // C through the cathode
+    double anode_charge_step;        // C arriving at the anode this step
+    double V;                        // anode voltage
+    double I_gap;                    // last step's gap current
+    double relres;                   // last Poisson relative residual
+    double cycles;                   // last Poisson cycles
+    unsigned int load_bad;           // set by a device load that met an out-of-range particle
+    unsigned int pad0;
+};
+
+// Per-species push constants (float, computed on the host in double then rounded).
+struct PushConsts {
+    float qmdt[NSP];                 // z e / m * dt_s
+    float dtz[NSP], dtr[NSP];        // dt_s / dz, dt_s / dr
+    float mass_w[NSP];               // unused in kernels; kept for layout stability
+};
+
+// Collision constants (float; see the host's derivation).
+struct CollConsts {
+    float kmr;                       // eps[eV] = g^2 * kmr
+    float a_e, a_t;                  // m_r / m_e, m_r / M
+    float kth[NCH];                  // 2 E_th e / m_r
+    float sgmax[2];                  // NTC majorants of the two pair classes
+    int di_split_mode;
+};
+
+struct Particles {
+    uint32_t* key;
+    float *pz, *pr, *vz, *vr, *vt;
+    uint32_t* id;
+};
+
+// Geometry / run parameters passed by value to the kernels.
+struct KParams {
+    int geom;                        // 0 r-z, 1 periodic
+    int nz, nr;
+    int nzn, nrn;                    // node grid
+    uint32_t ncell;                  // nz * nr
+    uint32_t seed, run;
+    uint32_t step;
+    int heavy_step;
+    int field_on;                    // gather E in the push
+    unsigned long long capacity;
+    double weight;
+    double masses[NSP];
+};
+
+// ---------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
+// multipliers 0xD2511F53, 0xCD9E8D57 and key increments 0x9E3779B9,
+// 0xBB67AE85.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Draw stream keyed by (subject, step, stream id); block counter in word 3.
+struct Stream {
+    uint4 ctr;
+    uint2 key;
+    uint4 buf;
+    int used;
+    __device__ __forceinline__ Stream(uint32_t subject, uint32_t step, uint32_t sid, uint32_t seed, uint32_t run)
+        : ctr(make_uint4(subject, step, sid, 0u)), key(make_uint2(seed, run)), buf(make_uint4(0, 0, 0, 0)), used(4) {}
+    __device__ __forceinline__ uint32_t next() {
+        if (used == 4) {
+            buf = philox4x32_10(ctr, key);
+            ctr.w += 1u;
+            used = 0;
+        }
+        const uint32_t v = used == 0 ? buf.x : used == 1 ? buf.y : used == 2 ? buf.z : buf.w;
+        ++used;
+        return v;
+    }
+    // uniform on [0, 1) from the top 24 bits
+    __device__ __forceinline__ float u01() { return __fmul_rn((float)(next() >> 8), 5.9604644775390625e-08f); }
+    // uniform integer in [0, n)
+    __device__ __forceinline__ uint32_t pick(uint32_t n) { return (uint32_t)(((unsigned long long)next() * n) >> 32); }
+};
+
+__host__ __device__ constexpr uint32_t sid_cand(int k, uint32_t m) { return ((uint32_t)k << 28) | m; }
+constexpr uint32_t SID_NCAND = 0xE0000000u;
+constexpr uint32_t SID_INJ_COUNT = 0xD0000000u;
+__host__ __device__ constexpr uint32_t sid_inj_e(uint32_t p) { return 0xD1000000u | p; }
+__host__ __device__ constexpr uint32_t sid_inj_cu(uint32_t p) { return 0xD2000000u | p; }
+
+__device__ __forceinline__ uint32_t key_species(uint32_t key) { return key >> 24; }
+__device__ __forceinline__ uint32_t key_cell(uint32_t key) { return key & 0xFFFFFFu; }
+__device__ __forceinline__ uint32_t make_key(uint32_t sp, uint32_t cell) { return (sp << 24) | cell; }
+
+__device__ __forceinline__ int charge_of(int sp) { return sp == SP_E ? -1 : (sp == SP_CU ? 0 : (sp == SP_CUP ? 1 : 2)); }
+
+// node index of (i, j); periodic wrap in the Cartesian mode
+__device__ __forceinline__ uint32_t node_of(const KParams& P, int i, int j) {
+    if (P.geom != 0) {
+        if (i >= P.nz) i -= P.nz;
+        if (j >= P.nr) j -= P.nr;
+        return (uint32_t)i * (uint32_t)P.nr + (uint32_t)j;
+    }
+    return (uint32_t)i * (uint32_t)P.nrn + (uint32_t)j;
+}
+
+__device__ __forceinline__ void set_error(DevState* st, uint32_t bits) { atomicOr(&st->error, bits); }
+
+}  // namespace pd

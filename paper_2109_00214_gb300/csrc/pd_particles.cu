@@ -1,0 +1,436 @@
+// pd_particles.cu -- particle streaming kernels of the time step.
+//
+//   k_push      Newton push (Sec. 2.1) with the field gathered by the CIC
+//               weights of Eq. (10), r-z rotation or periodic wrap, absorbing
+//               electrodes, fused with the fixed-point CIC charge deposit of
+//               Eq. (9)-(10) and the (species, cell) histogram for the sort.
+//   k_scatter   counting-sort scatter A -> B by (species, cell).
+//   k_scan_*    exclusive prefix sum of u32 (bin offsets, candidate offsets).
+//   k_deposit   deposit without moving (initial state).
+//   diagnostics species counts, density map, energy histogram.
+//
+// Compiled with -fmad=false: every float operation is rounded on its own, in
+// the order written, so results do not depend on contraction choices.
+#include "pd_internal.cuh"
+#include "pd_kernels.h"
+
+namespace pd {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// histogram increment with one atomic per distinct bin in the warp
+__device__ __forceinline__ void warp_count(uint32_t* count, uint32_t bin, bool on) {
+    const unsigned m = __ballot_sync(FULL, on);
+    if (!on) return;
+    const unsigned g = __match_any_sync(m, bin);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(g) - 1)) atomicAdd(&count[bin], (uint32_t)__popc(g));
+}
+
+// Fixed-point CIC deposit, Eq. (9)-(10): w = rn(f * 2^16) per axis, corner
+// weights (2^16 - w_z)(2^16 - w_r), w_z (2^16 - w_r), (2^16 - w_z) w_r, w_z w_r
+// (they sum to 2^32).  Lanes holding the same key (species and cell) are
+// summed first: each weight is split in 16-bit halves so the warp sums fit in
+// 32 bits, then one 64-bit atomic per node and group.
+__device__ __forceinline__ void warp_deposit(long long* rho, const KParams& P, uint32_t key, int iz, int ir,
+                                             float pz, float pr, int zq, bool on) {
+    const unsigned m = __ballot_sync(FULL, on);
+    if (!on) return;
+    const unsigned g = __match_any_sync(m, key);
+    const uint32_t wz = __float2uint_rn(pz * 65536.0f);
+    const uint32_t wr = __float2uint_rn(pr * 65536.0f);
+    const unsigned long long az = 65536u - wz, ar = 65536u - wr;
+    const unsigned long long W[4] = {az * ar, (unsigned long long)wz * ar, az * (unsigned long long)wr,
+                                     (unsigned long long)wz * wr};
+    const bool leader = (threadIdx.x & 31) == (unsigned)(__ffs(g) - 1);
+    const uint32_t nodes[4] = {node_of(P, iz, ir), node_of(P, iz + 1, ir), node_of(P, iz, ir + 1),
+                               node_of(P, iz + 1, ir + 1)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t hi = __reduce_add_sync(g, (uint32_t)(W[k] >> 16));
+        const uint32_t lo = __reduce_add_sync(g, (uint32_t)(W[k] & 0xFFFFu));
+        if (leader) {
+            const long long s = (long long)(((unsigned long long)hi << 16) + lo) * zq;
+            atomicAdd((unsigned long long*)&rho[nodes[k]], (unsigned long long)s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// push + gather + deposit + histogram
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_push(Particles A, const float2* __restrict__ E, long long* rho_e,
+                                              long long* rho_h, uint32_t* count, DevState* st, KParams P,
+                                              PushConsts pc) {
+    const unsigned long long n = st->n_slots;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
+         i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const bool valid = i < n;
+        uint32_t key = valid ? A.key[i] : DEAD;
+        const bool live = key != DEAD;
+        const int sp = (int)key_species(key);
+        uint32_t cell = key_cell(key);
+        const bool move = live && (sp == SP_E || P.heavy_step);
+        int iz = 0, ir = 0;
+        float pz = 0.f, pr = 0.f;
+        bool keep = live;
+        if (move) {
+            iz = (int)(cell / (uint32_t)P.nr);
+            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+            pz = A.pz[i];
+            pr = A.pr[i];
+            float vz = A.vz[i], vr = A.vr[i], vt = 0.f;
+            const bool rz = P.geom == 0;
+            if (rz) vt = A.vt[i];
+            if (P.field_on) {
+                const float gz = 1.0f - pz, gr = 1.0f - pr;
+                const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
+                const float2 e00 = E[node_of(P, iz, ir)], e10 = E[node_of(P, iz + 1, ir)];
+                const float2 e01 = E[node_of(P, iz, ir + 1)], e11 = E[node_of(P, iz + 1, ir + 1)];
+                const float ez = ((w00 * e00.x + w10 * e10.x) + w01 * e01.x) + w11 * e11.x;
+                const float er = ((w00 * e00.y + w10 * e10.y) + w01 * e01.y) + w11 * e11.y;
+                vz = vz + pc.qmdt[sp] * ez;
+                vr = vr + pc.qmdt[sp] * er;
+            }
+            const float z = pz + vz * pc.dtz[sp];
+            const float fz = floorf(z);
+            int niz = iz + (int)fz;
+            float npz = z - fz;
+            if (npz >= 1.0f) npz = 0x1.fffffep-1f;
+            int nir;
+            float npr;
+            if (rz) {
+                const float x = ((float)ir + pr) + vr * pc.dtr[sp];
+                const float y = vt * pc.dtr[sp];
+                const float rr = sqrtf(x * x + y * y);
+                float c = 1.0f, s = 0.0f;
+                if (rr > 0.0f) {
+                    c = x / rr;
+                    s = y / rr;
+                }
+                const float nvr = c * vr + s * vt;
+                const float nvt = c * vt - s * vr;
+                vr = nvr;
+                vt = nvt;
+                const float fr = floorf(rr);
+                nir = (int)fr;
+                npr = rr - fr;
+                if (npr >= 1.0f) npr = 0x1.fffffep-1f;
+            } else {
+                const float r = pr + vr * pc.dtr[sp];
+                const float fr = floorf(r);
+                nir = ir + (int)fr;
+                npr = r - fr;
+                if (npr >= 1.0f) npr = 0x1.fffffep-1f;
+                niz = ((niz % P.nz) + P.nz) % P.nz;
+                nir = ((nir % P.nr) + P.nr) % P.nr;
+            }
+            int electrode = -1;
+            if (rz) {
+                if (niz < 0) electrode = 0;
+                else if (niz >= P.nz) electrode = 1;
+                else if (nir >= P.nr) electrode = 2;
+            }
+            if (electrode >= 0) {
+                keep = false;
+                key = DEAD;
+                A.key[i] = DEAD;
+                const double v2 = (double)vz * vz + (double)vr * vr + (double)vt * vt;
+                const double ke = P.weight * (0.5 * P.masses[sp] * v2);
+                atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
+                atomicAdd(&st->absorbed_energy[electrode], ke);
+                const double qw = (double)charge_of(sp) * 1.602176634e-19 * P.weight;
+                if (electrode == 1) atomicAdd(&st->anode_charge_step, qw);
+                if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
+            } else {
+                cell = (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir;
+                key = make_key((uint32_t)sp, cell);
+                A.key[i] = key;
+                A.pz[i] = npz;
+                A.pr[i] = npr;
+                if (P.field_on || rz) {
+                    A.vz[i] = vz;
+                    A.vr[i] = vr;
+                }
+                if (rz) A.vt[i] = vt;
+                iz = niz;
+                ir = nir;
+                pz = npz;
+                pr = npr;
+            }
+        }
+        const int zq = charge_of(sp);
+        const bool dep = move && keep && zq != 0;
+        // electrons and heavies deposit into separate grids (heavies are held
+        // between their sub-cycled pushes)
+        warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, dep && sp == SP_E);
+        warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, dep && sp != SP_E);
+        warp_count(count, (uint32_t)sp * P.ncell + cell, keep);
+    }
+}
+
+// deposit of every live particle without moving (state before the first step)
+__global__ void __launch_bounds__(256) k_deposit(Particles A, long long* rho_e, long long* rho_h, DevState* st,
+                                                 KParams P) {
+    const unsigned long long n = st->n_slots;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
+         i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const uint32_t key = i < n ? A.key[i] : DEAD;
+        const bool live = key != DEAD;
+        const int sp = (int)key_species(key);
+        const uint32_t cell = key_cell(key);
+        int iz = 0, ir = 0;
+        float pz = 0.f, pr = 0.f;
+        const int zq = live ? charge_of(sp) : 0;
+        if (live && zq != 0) {
+            iz = (int)(cell / (uint32_t)P.nr);
+            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+            pz = A.pz[i];
+            pr = A.pr[i];
+        }
+        warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp == SP_E);
+        warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp != SP_E);
+    }
+}
+
+// ---------------------------------------------------------------------
+// counting-sort scatter: slot = off[bin] + (running count of the bin), the
+// bin counter counting back down to zero (ready for the next histogram)
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_scatter(Particles A, Particles B, const uint32_t* __restrict__ off,
+                                                 uint32_t* count, DevState* st, KParams P) {
+    const unsigned long long n = st->n_slots;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
+         i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const uint32_t key = i < n ? A.key[i] : DEAD;
+        const bool live = key != DEAD;
+        const unsigned m = __ballot_sync(FULL, live);
+        if (!live) continue;
+        const uint32_t bin = key_species(key) * P.ncell + key_cell(key);
+        const unsigned g = __match_any_sync(m, bin);
+        const int leader = __ffs(g) - 1;
+        const uint32_t cnt = (uint32_t)__popc(g);
+        uint32_t old = 0;
+        if (lane == leader) old = atomicSub(&count[bin], cnt);
+        old = __shfl_sync(g, old, leader);
+        const uint32_t slot = off[bin] + old - cnt + (uint32_t)__popc(g & lanemask_lt());
+        B.key[slot] = key;
+        B.pz[slot] = A.pz[i];
+        B.pr[slot] = A.pr[i];
+        B.vz[slot] = A.vz[i];
+        B.vr[slot] = A.vr[i];
+        B.vt[slot] = A.vt[i];
+        B.id[slot] = A.id[i];
+    }
+}
+
+// ---------------------------------------------------------------------
+// exclusive scan of u32 (input padded to a multiple of SCAN_TILE with zeros)
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t wbase = warp > 0 ? warp_sums[warp - 1] : 0u;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return wbase + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, uint32_t* partial) {
+    const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)blockIdx.x * SCAN_TILE) + threadIdx.x * 2;
+    const uint4 a = p[0], b = p[1];
+    uint32_t s = (a.x + a.y + a.z + a.w) + (b.x + b.y + b.z + b.w);
+    s = __reduce_add_sync(FULL, s);
+    __shared__ uint32_t ws[SCAN_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = threadIdx.x < SCAN_THREADS / 32 ? ws[threadIdx.x] : 0u;
+        t = __reduce_add_sync(FULL, t);
+        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of nb block sums in place, total to partial[nb]
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partial, uint32_t nb) {
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? partial[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nb) partial[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* __restrict__ in,
+                                                            const uint32_t* __restrict__ partial, uint32_t* out,
+                                                            uint32_t n, uint32_t nb) {
+    const size_t base = (size_t)blockIdx.x * SCAN_TILE + threadIdx.x * 8;
+    const uint4* p = reinterpret_cast<const uint4*>(in + base);
+    const uint4 a = p[0], b = p[1];
+    uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+    uint32_t tot;
+    uint32_t run = partial[blockIdx.x] + block_exclusive_scan(s, &tot);
+    uint32_t o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        o[k] = run;
+        run += v[k];
+    }
+    uint4* q = reinterpret_cast<uint4*>(out + base);
+    q[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    q[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = partial[nb];
+}
+
+// ---------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------
+__global__ void k_species_count(Particles A, DevState* st, unsigned long long* out) {
+    __shared__ unsigned long long c[NSP];
+    if (threadIdx.x < NSP) c[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long n = st->n_slots;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t key = A.key[i];
+        if (key != DEAD) atomicAdd(&c[key_species(key)], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x < NSP) atomicAdd(&out[threadIdx.x], c[threadIdx.x]);
+}
+
+__global__ void k_density(Particles A, DevState* st, KParams P, int species, long long* acc) {
+    const unsigned long long n = st->n_slots;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
+         i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const uint32_t key = i < n ? A.key[i] : DEAD;
+        const bool on = key != DEAD && (int)key_species(key) == species;
+        int iz = 0, ir = 0;
+        float pz = 0.f, pr = 0.f;
+        if (on) {
+            const uint32_t cell = key_cell(key);
+            iz = (int)(cell / (uint32_t)P.nr);
+            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+            pz = A.pz[i];
+            pr = A.pr[i];
+        }
+        warp_deposit(acc, P, key, iz, ir, pz, pr, 1, on);
+    }
+}
+
+__global__ void k_spectrum(Particles A, DevState* st, KParams P, int species, double lo, double hi, int nbins,
+                           unsigned long long* hist) {
+    const unsigned long long n = st->n_slots;
+    const double m = P.masses[species];
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t key = A.key[i];
+        if (key == DEAD || (int)key_species(key) != species) continue;
+        const double vz = A.vz[i], vr = A.vr[i], vt = A.vt[i];
+        const double v2 = vz * vz + vr * vr + vt * vt;
+        const double e = 0.5 * m * v2 / 1.602176634e-19;
+        if (e < lo || e >= hi) continue;
+        int b = (int)((e - lo) / (hi - lo) * nbins);
+        if (b >= nbins) b = nbins - 1;
+        atomicAdd(&hist[b], 1ull);
+    }
+}
+
+__global__ void k_pack_keys(const uint8_t* __restrict__ sp, const int32_t* __restrict__ iz,
+                            const int32_t* __restrict__ ir, const float* __restrict__ pz,
+                            const float* __restrict__ pr, long long n, int nz, int nr, uint32_t id0, uint32_t* key,
+                            uint32_t* id, unsigned int* bad) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int a = iz[q], b = ir[q];
+        const uint32_t s = sp[q];
+        const float fz = pz[q], fr = pr[q];
+        const bool ok = s < NSP && a >= 0 && a < nz && b >= 0 && b < nr && fz >= 0.0f && fz < 1.0f && fr >= 0.0f &&
+                        fr < 1.0f;
+        if (!ok) atomicOr(bad, 1u);
+        key[q] = ok ? make_key(s, (uint32_t)a * (uint32_t)nr + (uint32_t)b) : DEAD;
+        id[q] = id0 + (uint32_t)q;
+    }
+}
+
+// ---------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------
+void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* count,
+                 DevState* st, const KParams& P, const PushConsts& pc, int grid, cudaStream_t s) {
+    k_push<<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
+}
+void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
+                    int grid, cudaStream_t s) {
+    k_deposit<<<grid, 256, 0, s>>>(A, rho_e, rho_h, st, P);
+}
+void launch_scatter(const Particles& A, const Particles& B, const uint32_t* off, uint32_t* count, DevState* st,
+                    const KParams& P, int grid, cudaStream_t s) {
+    k_scatter<<<grid, 256, 0, s>>>(A, B, off, count, st, P);
+}
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
+    const uint32_t nb = n_padded / SCAN_TILE;
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, partial);
+    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb);
+    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
+}
+void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
+                      int64_t n, int nz, int nr, uint32_t id0, uint32_t* key, uint32_t* id, unsigned int* bad,
+                      int grid, cudaStream_t s) {
+    k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, id0, key, id, bad);
+}
+void launch_species_count(const Particles& A, DevState* st, unsigned long long* out, int grid, cudaStream_t s) {
+    k_species_count<<<grid, 256, 0, s>>>(A, st, out);
+}
+void launch_density(const Particles& A, DevState* st, const KParams& P, int species, long long* acc, int grid,
+                    cudaStream_t s) {
+    k_density<<<grid, 256, 0, s>>>(A, st, P, species, acc);
+}
+void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int species, double lo, double hi,
+                     int nbins, unsigned long long* hist, int grid, cudaStream_t s) {
+    k_spectrum<<<grid, 256, 0, s>>>(A, st, P, species, lo, hi, nbins, hist);
+}
+
+}  // namespace pd

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle on
+the same seeded inputs and Philox streams.
+
+Bar (from the method's determinism rules): event counts, labels (species
+codes), ids and int64 fixed-point charge bit-exact; FP32 particle state
+bit-exact as well where the field is shared (the float operations are the
+same, rounded one by one), which is stricter than the 1e-5 relative tolerance
+allowed for FP32 state; the Poisson potential within the solve tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+FLOATS = ("pz", "pr", "vz", "vr", "vt")
+
+
+@pytest.fixture(scope="module")
+def pd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2109_00214_gb300 as m
+    m.load_library()
+    return m
+
+
+def run_pair(pd, cfg, parts, xs, steps, field=None, fp64=False):
+    sim = pd.Simulation(cfg, xs)
+    o = oracle.Oracle(cfg, fp64=fp64)
+    o.set_cross_sections(xs)
+    if len(parts["species"]):
+        sim.load(parts)
+        o.load(parts)
+    if field is not None:
+        sim.set_field(*field)
+        o.set_field(*field)
+    o.prime()
+    sim.step(steps)
+    o.step(steps)
+    return sim, o
+
+
+def assert_same_particles(g, op, rtol=0.0):
+    order = np.argsort(g["id"], kind="stable")
+    assert len(g["id"]) == len(op["id"])
+    for k in ("id", "species", "iz", "ir"):
+        assert np.array_equal(g[k][order], op[k]), k
+    for k in FLOATS:
+        a = g[k][order].astype(np.float64)
+        b = op[k]
+        if rtol == 0.0:
+            bad = np.flatnonzero(a != b)
+            assert bad.size == 0, (k, bad[:5], a[bad[:5]], b[bad[:5]])
+        else:
+            assert np.allclose(a, b, rtol=rtol, atol=rtol * np.abs(b).max()), k
+
+
+def assert_same_counters(gc, oc, keys=None):
+    for k in keys or oc:
+        assert gc[k] == oc[k], (k, gc[k], oc[k])
+
+
+@pytest.mark.parametrize("nz,nr,total,scale,steps", [
+    (64, 64, 2e5, 3000.0, 4),      # stress: about one candidate per cell
+    (37, 53, 6e4, 20000.0, 3),     # ragged grid, dense collisions, many spawns
+    (64, 64, 2e5, 1.0, 5),         # the paper's dt: rare candidates
+])
+def test_microbench_bit_exact(pd, xs, nz, nr, total, scale, steps):
+    cfg, parts = synthetic.microbench(nz=nz, nr=nr, total=total, coll_scale=scale, seed=11)
+    sim, o = run_pair(pd, cfg, parts, xs, steps)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    if scale > 1:
+        assert gc["ev_di"] > 0 and gc["ev_sw"] > 0 and gc["ev_si"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+    ge, gh = sim.rho()
+    oe, oh = o.rho()
+    assert np.array_equal(ge, oe) and np.array_equal(gh, oh)
+    assert gc["ratio_viol"] == 0
+
+
+def test_microbench_di_off(pd, xs):
+    cfg, parts = synthetic.microbench(nz=32, nr=32, total=5e4, coll_scale=5000.0, seed=5)
+    cfg["di_on"] = 0
+    sim, o = run_pair(pd, cfg, parts, xs, 3)
+    gc = sim.counters()
+    assert gc["ev_di"] == 0
+    assert_same_counters(gc, o.counters())
+    assert_same_particles(sim.particles(), o.particles())
+
+
+def _rz_field(n, V0, seed=3):
+    rng = np.random.default_rng(seed)
+    Ez = np.full((n + 1, n + 1), -V0 / 6e-6) * (1 + 0.3 * rng.uniform(-1, 1, (n + 1, n + 1)))
+    Er = 2e8 * rng.uniform(-1, 1, (n + 1, n + 1))
+    Er[:, 0] = 0
+    return Ez, Er
+
+
+def test_rz_external_field_with_injection_bit_exact(pd, xs):
+    """r-z push with a shared external field, heavy sub-cycling (steps 0 and
+    10 move heavies), FN + neutral injection, absorbing walls and circuit."""
+    n = 64
+    cfg, parts = synthetic.rz_plume(n=n, total=6e4, seed=2)
+    cfg.update(field_on=2, inject_on=1, beta=60.0, coll_dt_scale=50.0)
+    field = _rz_field(n, cfg["V0"])
+    sim, o = run_pair(pd, cfg, parts, xs, 12, field=field)
+    gc, oc = sim.counters(), o.counters()
+    assert gc["emitted_e"] > 0 and gc["emitted_cu"] >= 0
+    assert sum(gc[k] for k in gc if k.startswith("abs_")) > 0
+    assert_same_counters(gc, oc)
+    assert_same_particles(sim.particles(), o.particles())
+    ge, gh = sim.rho()
+    oe, oh = o.rho()
+    assert np.array_equal(ge, oe) and np.array_equal(gh, oh)
+    gs, os_ = sim.scalars(), o.scalars()
+    for k in ("V", "I_gap", "gamma", "Qbar", "mass"):
+        assert gs[k] == pytest.approx(os_[k], rel=1e-12, abs=1e-300), k
+    assert gs["charge"] == pytest.approx(os_["charge"], rel=1e-12)
+
+
+def test_rz_poisson_matches_oracle(pd, xs):
+    """Self-consistent field: multigrid (GPU) vs conjugate gradients (CPU) on
+    the same fixed-point charge, to the solve tolerance."""
+    n = 64
+    cfg, parts = synthetic.rz_plume(n=n, total=8e4, seed=4)
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+    sim, o = run_pair(pd, cfg, parts, xs, 0)
+    sim.step(0)
+    gphi, ophi = sim.phi(), o.phi()
+    scale = np.abs(ophi).max()
+    assert np.abs(gphi - ophi).max() <= 1e-8 * scale
+    gs = sim.scalars()
+    assert gs["poisson_relres"] <= 1e-10
+    gEz, gEr = sim.field()
+    oEz, oEr = o.field()
+    assert np.allclose(gEz, oEz, rtol=1e-6, atol=1e-6 * np.abs(oEz).max())
+    assert np.allclose(gEr, oEr, rtol=1e-6, atol=1e-6 * np.abs(oEz).max())
+
+
+def test_rz_self_consistent_steps_track_oracle(pd, xs):
+    """A few self-consistent steps: the two field solves agree to ~1e-9, so
+    particle states agree to FP32 rounding and the counters stay equal."""
+    n = 64
+    cfg, parts = synthetic.rz_plume(n=n, total=3e4, seed=6)
+    cfg.update(field_on=1, inject_on=1, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+    sim, o = run_pair(pd, cfg, parts, xs, 5)
+    gc, oc = sim.counters(), o.counters()
+    for k in ("ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "emitted_e", "emitted_cu"):
+        assert abs(gc[k] - oc[k]) <= max(2, 0.01 * oc[k]), k
+    g, op = sim.particles(), o.particles()
+    assert abs(len(g["id"]) - len(op["id"])) <= max(4, 0.001 * len(op["id"]))
+
+
+def test_empty_and_capacity(pd, xs):
+    cfg, parts = synthetic.microbench(nz=16, nr=16, total=2e3, seed=1)
+    sim = pd.Simulation(dict(cfg, capacity=4096), xs)
+    sim.step(3)                                   # empty domain steps fine
+    assert sim.counters()["cand_total"] == 0
+    small = dict(cfg, capacity=100)
+    sim2 = pd.Simulation(small, xs)
+    with pytest.raises(pd.PdError):
+        sim2.load(parts)                          # more particles than slots
+    # a capacity that the spawns overrun is reported, not written past
+    cfg3, parts3 = synthetic.microbench(nz=16, nr=16, total=3e3, coll_scale=2e5, seed=2)
+    sim3 = pd.Simulation(dict(cfg3, capacity=len(parts3["species"]) + 8), xs)
+    sim3.load(parts3)
+    sim3.step(2)
+    with pytest.raises(pd.PdError, match="CAPACITY"):
+        sim3.synchronize()
+
+
+def test_species_diagnostics_match_oracle(pd, xs):
+    n = 32
+    cfg, parts = synthetic.rz_plume(n=n, total=2e4, seed=9)
+    cfg.update(field_on=0, inject_on=0, coll_dt_scale=200.0)
+    sim, o = run_pair(pd, cfg, parts, xs, 3)
+    for sp in (0, 1, 2, 3, 4):
+        assert np.array_equal(sim.energy_spectrum(sp, 0, 200, 40), o.energy_spectrum(sp, 0, 200, 40))
+        assert np.allclose(sim.density_map(sp), o.density_map(sp), rtol=1e-12, atol=0)
+    gs, os_ = sim.scalars(), o.scalars()
+    assert gs["gamma"] == pytest.approx(os_["gamma"], rel=1e-14)
+    assert gs["Qbar"] == pytest.approx(os_["Qbar"], rel=1e-14)
