@@ -303,7 +303,8 @@ int field_init(FieldSolver& fs, const pd_config& c, void* ws, size_t bytes, cuda
                 else if (j == c.nr) verb = 2.0 * PI_ * dz * dr * dr * ((double)c.nr / 2.0 - 1.0 / 6.0);
                 else verb = 2.0 * PI_ * dz * dr * dr * (double)j;
                 vb[j] = verb;
-                fvv[j] = bb[j] * L.dz / verb;   // Vfv / Vverb, Vfv = A dz
+                const double A = bb[j] * L.dz;  // radial extent area of the control volume
+                fvv[j] = A * L.dz / verb;       // Vfv / Vverb, Vfv = A dz
             }
             fs.fv_over_verb = (double*)take(fvv.size() * 8);
             fs.verb_base = (double*)take(vb.size() * 8);
