@@ -325,18 +325,23 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* __re
 // ---------------------------------------------------------------------
 // diagnostics
 // ---------------------------------------------------------------------
+// live particles per species: per-warp ballot counts, one atomic per warp
+// and species at the end
 __global__ void k_species_count(Particles A, DevState* st, unsigned long long* out) {
-    __shared__ unsigned long long c[NSP];
-    if (threadIdx.x < NSP) c[threadIdx.x] = 0;
-    __syncthreads();
     const unsigned long long n = st->n_slots;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t key = A.key[i];
-        if (key != DEAD) atomicAdd(&c[key_species(key)], 1ull);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long c[NSP] = {0, 0, 0, 0, 0};
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
+         i0 += stride) {
+        const unsigned long long i = i0 + lane;
+        const uint32_t sp = i < n ? key_species(A.key[i]) : 255u;
+#pragma unroll
+        for (int s = 0; s < NSP; ++s) c[s] += (unsigned)__popc(__ballot_sync(FULL, sp == (uint32_t)s));
     }
-    __syncthreads();
-    if (threadIdx.x < NSP) atomicAdd(&out[threadIdx.x], c[threadIdx.x]);
+    if (lane == 0)
+        for (int s = 0; s < NSP; ++s)
+            if (c[s]) atomicAdd(&out[s], c[s]);
 }
 
 __global__ void k_density(Particles A, DevState* st, KParams P, int species, long long* acc) {
