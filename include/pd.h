@@ -195,6 +195,28 @@ const char* pd_kernel_name(int kernel_id);
 const char* pd_last_error(const pd_sim* sim);
 void pd_destroy(pd_sim* sim);
 
+/* Kinetic-energy histogram (eV) of one species, computed from raw particle
+ * arrays in device memory, with no allocation of any kind.  The paper has no
+ * counterpart: this is a service for callers that hold particles in their own
+ * device buffers and cannot allocate device memory (the memory belongs to
+ * another allocator or budget, or an allocation would synchronise the device
+ * at a bad moment).  Inputs: n slots of key (species << 24 | cell, dead slots
+ * 0xFFFFFFFF) and vz, vr, vt (m/s), all device pointers; out: nbins host
+ * counters for [e_lo_eV, e_hi_eV), written before the call returns (the call
+ * synchronises `cuda_stream`).  Bins are those of pd_get_energy_spectrum.
+ * Scratch: one histogram of PD_SPECTRUM_STATIC_MAX_BINS counters in the
+ * library's own device memory, which every GPU that loads the library keeps
+ * until the process exits.  nbins above that maximum is rejected with
+ * PD_ERR_ARG.  The first call on a device looks up the scratch's device
+ * address; make that first call before any stream capture.  All calls share
+ * the one histogram, which is cleared at the start of each call: calls whose
+ * work overlaps on the GPU (other streams, other threads) race and give wrong
+ * counts. */
+#define PD_SPECTRUM_STATIC_MAX_BINS 4096
+pd_status pd_energy_spectrum_static(const uint32_t* key, const float* vz, const float* vr, const float* vt,
+                                    int64_t n, int species, double e_lo_eV, double e_hi_eV, int nbins,
+                                    void* cuda_stream, uint64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots",
            "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
            "pd_get_energy_spectrum", "pd_profile_enable", "pd_profile_read", "pd_kernel_name",
-           "pd_last_error", "pd_destroy", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
+           "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 28
 PD_NKERNELS = 12
@@ -99,6 +99,8 @@ _SIGS = {
     "pd_kernel_name": (C.c_char_p, [C.c_int]),
     "pd_last_error": (C.c_char_p, [P]),
     "pd_destroy": (None, [P]),
+    "pd_energy_spectrum_static": (C.c_int, [P, P, P, P, C.c_int64, C.c_int, C.c_double, C.c_double, C.c_int,
+                                            P, P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -311,6 +313,19 @@ def pd_last_error(h):
 
 def pd_destroy(h):
     _lib().pd_destroy(h)
+
+
+PD_SPECTRUM_STATIC_MAX_BINS = 4096
+
+
+def pd_energy_spectrum_static(key_ptr, vz_ptr, vr_ptr, vt_ptr, n, species, lo, hi, nbins, stream_ptr=0):
+    """Energy histogram of raw device particle arrays (device pointers as ints),
+    with no allocation; see include/pd.h for the shared-scratch rules."""
+    a = np.zeros(nbins, np.uint64)
+    r = _lib().pd_energy_spectrum_static(P(key_ptr), P(vz_ptr), P(vr_ptr), P(vt_ptr), int(n), int(species),
+                                         float(lo), float(hi), int(nbins), P(stream_ptr), _ptr(a))
+    _check(None, r, "pd_energy_spectrum_static")
+    return a
 
 
 class Simulation:

@@ -22,6 +22,7 @@ UNITS = {
     "pd_collide.cu": ["-fmad=false"],
     "pd_capi.cu": ["-fmad=false"],
     "pd_field.cu": [],
+    "pd_noalloc.cu": ["-fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
