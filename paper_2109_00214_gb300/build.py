@@ -23,6 +23,7 @@ UNITS = {
     "pd_capi.cu": ["-fmad=false"],
     "pd_field.cu": [],
     "pd_noalloc.cu": ["-fmad=false"],
+    "pd_stream.cu": ["-fmad=false"],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -48,7 +48,7 @@ Layout make_layout(const pd_config& c) {
         o = align256(o + bytes);
         return r;
     };
-    const uint64_t cap = (uint64_t)c.capacity;
+    const uint64_t cap = ((uint64_t)c.capacity + 3) & ~3ull;   // slot arrays move in groups of four
     for (int k = 0; k < 7; ++k) L.A[k] = take(cap * 4);
     for (int k = 0; k < 7; ++k) L.B[k] = take(cap * 4);
     const uint64_t ncell = (uint64_t)c.nz * c.nr;
@@ -181,6 +181,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.nzn = P.geom == 0 ? c.nz + 1 : c.nz;
     P.nrn = P.geom == 0 ? c.nr + 1 : c.nr;
     P.ncell = (uint32_t)c.nz * (uint32_t)c.nr;
+    P.inv_nr = 1.0f / (float)c.nr;
     P.seed = c.seed;
     P.run = c.run;
     P.step = (uint32_t)s->step;

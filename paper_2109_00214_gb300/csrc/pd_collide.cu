@@ -157,6 +157,57 @@ __device__ uint32_t select_rank(const uint32_t* __restrict__ ids, uint32_t N, ui
     return __reduce_min_sync(FULL, pos);
 }
 
+// Register-cached id list of one cell and species: element lane + 32 k in
+// ids[k], for lists of up to 32 * RC ids (one coalesced load per cell).
+constexpr int RC = 8;
+
+struct IdList {
+    uint32_t ids[RC];
+    const uint32_t* base;
+    uint32_t n;
+    bool cached;
+};
+
+__device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ base, uint32_t n, int lane) {
+    L.base = base;
+    L.n = n;
+    L.cached = n <= 32u * RC;
+    if (L.cached) {
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            const uint32_t q = (uint32_t)lane + 32u * k;
+            L.ids[k] = q < n ? base[q] : 0u;
+        }
+    }
+}
+
+// select_rank on a register-cached list (same result as select_rank)
+__device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
+    if (!L.cached) return select_rank(L.base, L.n, rank, lane);
+    uint32_t prefix = 0, want = rank;
+    for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            const uint32_t q = (uint32_t)lane + 32u * k;
+            cnt += (q < L.n && (L.ids[k] & hm) == prefix && !((L.ids[k] >> bit) & 1u)) ? 1u : 0u;
+        }
+        cnt = __reduce_add_sync(FULL, cnt);
+        if (want >= cnt) {
+            want -= cnt;
+            prefix |= 1u << bit;
+        }
+    }
+    uint32_t pos = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < RC; ++k) {
+        const uint32_t q = (uint32_t)lane + 32u * k;
+        if (q < L.n && L.ids[k] == prefix) pos = q;
+    }
+    return __reduce_min_sync(FULL, pos);
+}
+
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
                                                uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
                                                KParams P) {
@@ -346,19 +397,24 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
         }
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
+        IdList el;
+        load_ids(el, A.id + e_base, Ne, lane);
         for (int k = 0; k < 2; ++k) {
             const uint32_t tb = (k == 0 ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
             const uint32_t Nt = off[tb + 1] - t_base;
             const uint32_t ncand = k == 0 ? n.x : n.y;
+            if (ncand == 0) continue;
+            IdList tl;
+            load_ids(tl, A.id + t_base, Nt, lane);
             for (uint32_t m = 0; m < ncand; ++m) {
                 Stream rs(c, P.step, sid_cand(k, m), P.seed, P.run);
                 const uint32_t i = rs.pick(Ne);
                 const uint32_t j = rs.pick(Nt);
                 const float Racc = rs.u01();
                 const float Rch = rs.u01();
-                const uint32_t pe = select_rank(A.id + e_base, Ne, i, lane);
-                const uint32_t pt = select_rank(A.id + t_base, Nt, j, lane);
+                const uint32_t pe = select_rank_list(el, i, lane);
+                const uint32_t pt = select_rank_list(tl, j, lane);
                 if (pe >= Ne || pt >= Nt) {       // ids not unique: corrupt state, never index with it
                     if (lane == 0) set_error(st, ERR_BOUNDS);
                     continue;

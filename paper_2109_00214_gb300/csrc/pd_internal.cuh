@@ -78,6 +78,7 @@ struct KParams {
     int nz, nr;
     int nzn, nrn;                    // node grid
     uint32_t ncell;                  // nz * nr
+    float inv_nr;                    // 1 / nr (cell decoding estimate)
     uint32_t seed, run;
     uint32_t step;
     int heavy_step;

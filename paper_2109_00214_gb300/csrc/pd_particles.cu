@@ -1,10 +1,5 @@
-// pd_particles.cu -- particle streaming kernels of the time step.
+// pd_particles.cu -- scans, the initial deposit and diagnostics.
 //
-//   k_push      Newton push (Sec. 2.1) with the field gathered by the CIC
-//               weights of Eq. (10), r-z rotation or periodic wrap, absorbing
-//               electrodes, fused with the fixed-point CIC charge deposit of
-//               Eq. (9)-(10) and the (species, cell) histogram for the sort.
-//   k_scatter   counting-sort scatter A -> B by (species, cell).
 //   k_scan_*    exclusive prefix sum of u32 (bin offsets, candidate offsets).
 //   k_deposit   deposit without moving (initial state).
 //   diagnostics species counts, density map, energy histogram.
@@ -13,171 +8,13 @@
 // the order written, so results do not depend on contraction choices.
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
+#include "pd_warp.cuh"
 
 namespace pd {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
 
-// histogram increment with one atomic per distinct bin in the warp
-__device__ __forceinline__ void warp_count(uint32_t* count, uint32_t bin, bool on) {
-    const unsigned m = __ballot_sync(FULL, on);
-    if (!on) return;
-    const unsigned g = __match_any_sync(m, bin);
-    if ((threadIdx.x & 31) == (unsigned)(__ffs(g) - 1)) atomicAdd(&count[bin], (uint32_t)__popc(g));
-}
-
-// Fixed-point CIC deposit, Eq. (9)-(10): w = rn(f * 2^16) per axis, corner
-// weights (2^16 - w_z)(2^16 - w_r), w_z (2^16 - w_r), (2^16 - w_z) w_r, w_z w_r
-// (they sum to 2^32).  Lanes holding the same key (species and cell) are
-// summed first: each weight is split in 16-bit halves so the warp sums fit in
-// 32 bits, then one 64-bit atomic per node and group.
-__device__ __forceinline__ void warp_deposit(long long* rho, const KParams& P, uint32_t key, int iz, int ir,
-                                             float pz, float pr, int zq, bool on) {
-    const unsigned m = __ballot_sync(FULL, on);
-    if (!on) return;
-    const unsigned g = __match_any_sync(m, key);
-    const uint32_t wz = __float2uint_rn(pz * 65536.0f);
-    const uint32_t wr = __float2uint_rn(pr * 65536.0f);
-    const unsigned long long az = 65536u - wz, ar = 65536u - wr;
-    const unsigned long long W[4] = {az * ar, (unsigned long long)wz * ar, az * (unsigned long long)wr,
-                                     (unsigned long long)wz * wr};
-    const bool leader = (threadIdx.x & 31) == (unsigned)(__ffs(g) - 1);
-    const uint32_t nodes[4] = {node_of(P, iz, ir), node_of(P, iz + 1, ir), node_of(P, iz, ir + 1),
-                               node_of(P, iz + 1, ir + 1)};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t hi = __reduce_add_sync(g, (uint32_t)(W[k] >> 16));
-        const uint32_t lo = __reduce_add_sync(g, (uint32_t)(W[k] & 0xFFFFu));
-        if (leader) {
-            const long long s = (long long)(((unsigned long long)hi << 16) + lo) * zq;
-            atomicAdd((unsigned long long*)&rho[nodes[k]], (unsigned long long)s);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------
-// push + gather + deposit + histogram
-// ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_push(Particles A, const float2* __restrict__ E, long long* rho_e,
-                                              long long* rho_h, uint32_t* count, DevState* st, KParams P,
-                                              PushConsts pc) {
-    const unsigned long long n = st->n_slots;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
-         i0 += stride) {
-        const unsigned long long i = i0 + lane;
-        const bool valid = i < n;
-        uint32_t key = valid ? A.key[i] : DEAD;
-        const bool live = key != DEAD;
-        const int sp = (int)key_species(key);
-        uint32_t cell = key_cell(key);
-        const bool move = live && (sp == SP_E || P.heavy_step);
-        int iz = 0, ir = 0;
-        float pz = 0.f, pr = 0.f;
-        bool keep = live;
-        if (move) {
-            iz = (int)(cell / (uint32_t)P.nr);
-            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
-            pz = A.pz[i];
-            pr = A.pr[i];
-            float vz = A.vz[i], vr = A.vr[i], vt = 0.f;
-            const bool rz = P.geom == 0;
-            if (rz) vt = A.vt[i];
-            if (P.field_on) {
-                const float gz = 1.0f - pz, gr = 1.0f - pr;
-                const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
-                const float2 e00 = E[node_of(P, iz, ir)], e10 = E[node_of(P, iz + 1, ir)];
-                const float2 e01 = E[node_of(P, iz, ir + 1)], e11 = E[node_of(P, iz + 1, ir + 1)];
-                const float ez = ((w00 * e00.x + w10 * e10.x) + w01 * e01.x) + w11 * e11.x;
-                const float er = ((w00 * e00.y + w10 * e10.y) + w01 * e01.y) + w11 * e11.y;
-                vz = vz + pc.qmdt[sp] * ez;
-                vr = vr + pc.qmdt[sp] * er;
-            }
-            const float z = pz + vz * pc.dtz[sp];
-            const float fz = floorf(z);
-            int niz = iz + (int)fz;
-            float npz = z - fz;
-            if (npz >= 1.0f) npz = 0x1.fffffep-1f;
-            int nir;
-            float npr;
-            if (rz) {
-                const float x = ((float)ir + pr) + vr * pc.dtr[sp];
-                const float y = vt * pc.dtr[sp];
-                const float rr = sqrtf(x * x + y * y);
-                float c = 1.0f, s = 0.0f;
-                if (rr > 0.0f) {
-                    c = x / rr;
-                    s = y / rr;
-                }
-                const float nvr = c * vr + s * vt;
-                const float nvt = c * vt - s * vr;
-                vr = nvr;
-                vt = nvt;
-                const float fr = floorf(rr);
-                nir = (int)fr;
-                npr = rr - fr;
-                if (npr >= 1.0f) npr = 0x1.fffffep-1f;
-            } else {
-                const float r = pr + vr * pc.dtr[sp];
-                const float fr = floorf(r);
-                nir = ir + (int)fr;
-                npr = r - fr;
-                if (npr >= 1.0f) npr = 0x1.fffffep-1f;
-                niz = ((niz % P.nz) + P.nz) % P.nz;
-                nir = ((nir % P.nr) + P.nr) % P.nr;
-            }
-            int electrode = -1;
-            if (rz) {
-                if (niz < 0) electrode = 0;
-                else if (niz >= P.nz) electrode = 1;
-                else if (nir >= P.nr) electrode = 2;
-            }
-            if (electrode >= 0) {
-                keep = false;
-                key = DEAD;
-                A.key[i] = DEAD;
-                const double v2 = (double)vz * vz + (double)vr * vr + (double)vt * vt;
-                const double ke = P.weight * (0.5 * P.masses[sp] * v2);
-                atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
-                atomicAdd(&st->absorbed_energy[electrode], ke);
-                const double qw = (double)charge_of(sp) * 1.602176634e-19 * P.weight;
-                if (electrode == 1) atomicAdd(&st->anode_charge_step, qw);
-                if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
-            } else {
-                cell = (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir;
-                key = make_key((uint32_t)sp, cell);
-                A.key[i] = key;
-                A.pz[i] = npz;
-                A.pr[i] = npr;
-                if (P.field_on || rz) {
-                    A.vz[i] = vz;
-                    A.vr[i] = vr;
-                }
-                if (rz) A.vt[i] = vt;
-                iz = niz;
-                ir = nir;
-                pz = npz;
-                pr = npr;
-            }
-        }
-        const int zq = charge_of(sp);
-        const bool dep = move && keep && zq != 0;
-        // electrons and heavies deposit into separate grids (heavies are held
-        // between their sub-cycled pushes)
-        warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, dep && sp == SP_E);
-        warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, dep && sp != SP_E);
-        warp_count(count, (uint32_t)sp * P.ncell + cell, keep);
-    }
-}
-
-// deposit of every live particle without moving (state before the first step)
 __global__ void __launch_bounds__(256) k_deposit(Particles A, long long* rho_e, long long* rho_h, DevState* st,
                                                  KParams P) {
     const unsigned long long n = st->n_slots;
@@ -201,40 +38,6 @@ __global__ void __launch_bounds__(256) k_deposit(Particles A, long long* rho_e, 
         }
         warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp == SP_E);
         warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp != SP_E);
-    }
-}
-
-// ---------------------------------------------------------------------
-// counting-sort scatter: slot = off[bin] + (running count of the bin), the
-// bin counter counting back down to zero (ready for the next histogram)
-// ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scatter(Particles A, Particles B, const uint32_t* __restrict__ off,
-                                                 uint32_t* count, DevState* st, KParams P) {
-    const unsigned long long n = st->n_slots;
-    const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
-         i0 += stride) {
-        const unsigned long long i = i0 + lane;
-        const uint32_t key = i < n ? A.key[i] : DEAD;
-        const bool live = key != DEAD;
-        const unsigned m = __ballot_sync(FULL, live);
-        if (!live) continue;
-        const uint32_t bin = key_species(key) * P.ncell + key_cell(key);
-        const unsigned g = __match_any_sync(m, bin);
-        const int leader = __ffs(g) - 1;
-        const uint32_t cnt = (uint32_t)__popc(g);
-        uint32_t old = 0;
-        if (lane == leader) old = atomicSub(&count[bin], cnt);
-        old = __shfl_sync(g, old, leader);
-        const uint32_t slot = off[bin] + old - cnt + (uint32_t)__popc(g & lanemask_lt());
-        B.key[slot] = key;
-        B.pz[slot] = A.pz[i];
-        B.pr[slot] = A.pr[i];
-        B.vz[slot] = A.vz[i];
-        B.vr[slot] = A.vr[i];
-        B.vt[slot] = A.vt[i];
-        B.id[slot] = A.id[i];
     }
 }
 
@@ -403,17 +206,9 @@ __global__ void k_pack_keys(const uint8_t* __restrict__ sp, const int32_t* __res
 // ---------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------
-void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* count,
-                 DevState* st, const KParams& P, const PushConsts& pc, int grid, cudaStream_t s) {
-    k_push<<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
-}
 void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
                     int grid, cudaStream_t s) {
     k_deposit<<<grid, 256, 0, s>>>(A, rho_e, rho_h, st, P);
-}
-void launch_scatter(const Particles& A, const Particles& B, const uint32_t* off, uint32_t* count, DevState* st,
-                    const KParams& P, int grid, cudaStream_t s) {
-    k_scatter<<<grid, 256, 0, s>>>(A, B, off, count, st, P);
 }
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
     const uint32_t nb = n_padded / SCAN_TILE;
