@@ -34,9 +34,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E, phi, xsE, xs, ck, ray, hist,
+    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E, phi, xsE, xs, ck, ray, hist,
         spc, state, field;
-    uint32_t nbins_pad, ncell_pad;
+    uint32_t nbins_pad, ncell_pad, words_pad;
     size_t field_bytes;
 };
 
@@ -54,9 +54,16 @@ Layout make_layout(const pd_config& c) {
     const uint64_t ncell = (uint64_t)c.nz * c.nr;
     L.nbins_pad = scan_padded(ncell * NSP);
     L.ncell_pad = scan_padded(ncell);
-    L.count = take((size_t)L.nbins_pad * 4);
-    L.off = take(((size_t)L.nbins_pad + 1) * 4);
-    const size_t npart = (size_t)std::max(L.nbins_pad, L.ncell_pad) / SCAN_TILE + 1;
+    L.words_pad = scan_padded(cap / 32 + 1);
+    L.count = take((size_t)L.nbins_pad * 4);               // movers into each bin (cursor in the scatter)
+    L.off = take(((size_t)L.nbins_pad + 1) * 4);           // bin offsets, two copies (previous / new)
+    L.off2 = take(((size_t)L.nbins_pad + 1) * 4);
+    L.outc = take((size_t)L.nbins_pad * 4);                // movers out of each bin
+    L.stay = take((size_t)L.nbins_pad * 4);                // particles that stay in each bin
+    L.cntb = take((size_t)L.nbins_pad * 4);                // new bin counts (scan input)
+    L.mv = take((size_t)L.words_pad * 4);                  // mover bit mask of the sorted slots
+    L.mvx = take(((size_t)L.words_pad + 1) * 4);           // its popcount prefix
+    const size_t npart = (size_t)std::max(std::max(L.nbins_pad, L.ncell_pad), L.words_pad) / SCAN_TILE + 1;
     L.partial = take(npart * 4);
     L.nc = take(ncell * 8);
     L.cand = take((size_t)L.ncell_pad * 4);
@@ -95,7 +102,8 @@ struct pd_sim {
     char* ws;
     int sms;
     Particles A, B;
-    uint32_t *count, *off, *partial, *cand, *cand_off, *active;
+    uint32_t *count, *off, *off2, *outc, *stay, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active;
+    bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
     uint2* nc;
     long long *rho_e, *rho_h, *diag;
     float2* E;
@@ -187,6 +195,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.step = (uint32_t)s->step;
     P.heavy_step = heavy_step;
     P.field_on = c.field_mode != PD_FIELD_NONE;
+    P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)c.capacity;
     P.weight = c.weight;
     for (int k = 0; k < NSP; ++k) P.masses[k] = species_mass(k);
@@ -438,6 +447,13 @@ pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd
     s->B = Particles{P32(L.B[0]), PF(L.B[1]), PF(L.B[2]), PF(L.B[3]), PF(L.B[4]), PF(L.B[5]), P32(L.B[6])};
     s->count = P32(L.count);
     s->off = P32(L.off);
+    s->off2 = P32(L.off2);
+    s->outc = P32(L.outc);
+    s->stay = P32(L.stay);
+    s->cntb = P32(L.cntb);
+    s->mv = P32(L.mv);
+    s->mvx = P32(L.mvx);
+    s->sorted_valid = false;
     s->partial = P32(L.partial);
     s->nc = (uint2*)(w + L.nc);
     s->cand = P32(L.cand);
@@ -639,17 +655,24 @@ pd_status pd_step(pd_sim* s, int64_t n_steps) {
         }
         {
             Timed t(s, K_PUSH);
-            launch_push(s->A, s->E, s->rho_e, s->rho_h, s->count, s->st, P, pc, gpart, s->stream);
+            launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, pc,
+                        gpart, s->stream);
         }
         {
             Timed t(s, K_SCAN_BINS);
-            launch_scan(s->count, s->off, s->partial, s->L.nbins_pad, s->stream);
+            launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
+                            grid_for(s, 8), s->stream);
+            launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
+            if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
         }
         {
             Timed t(s, K_SCATTER);
-            launch_scatter(s->A, s->B, s->off, s->count, s->st, P, gpart, s->stream);
+            launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P, gpart,
+                           s->stream);
         }
         std::swap(s->A, s->B);
+        std::swap(s->off, s->off2);
+        s->sorted_valid = true;
         {
             Timed t(s, K_NCAND);
             launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, 8), s->stream);
@@ -765,7 +788,7 @@ pd_status pd_get_particles(pd_sim* s, uint32_t* id, uint8_t* sp, int32_t* iz, in
             continue;
         }
         const uint32_t cell = key[q] & 0xFFFFFFu;
-        sp[q] = (uint8_t)(key[q] >> 24);
+        sp[q] = (uint8_t)((key[q] >> 24) & 7u);
         iz[q] = (int32_t)(cell / (uint32_t)s->cfg.nr);
         ir[q] = (int32_t)(cell % (uint32_t)s->cfg.nr);
     }

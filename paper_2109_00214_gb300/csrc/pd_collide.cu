@@ -284,7 +284,7 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
                                   long long* rho_h) {
     const int ts = k == 0 ? SP_CU : SP_CUP;
     const uint32_t tkey = A.key[it];
-    if ((int)key_species(tkey) != ts) {      // target already ionized this step
+    if ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts) {   // target already ionized this step
         ++cx.consumed;
         return;
     }
@@ -355,7 +355,7 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     A.vz[ie] = keep.x; A.vr[ie] = keep.y; A.vt[ie] = keep.z;
     A.vz[it] = vt.x; A.vr[it] = vt.y; A.vt[it] = vt.z;
     const uint32_t tcell = key_cell(tkey);
-    A.key[it] = make_key((uint32_t)new_sp, tcell);
+    A.key[it] = converted_key((uint32_t)new_sp, (uint32_t)ts, tcell);
     const float tpz = A.pz[it], tpr = A.pr[it];
     deposit1(rho_h, P, tcell, tpz, tpr, dq);
     spawn_electron(A, cx, P, st, rho_e, tcell, tpz, tpr, e2);

@@ -83,6 +83,7 @@ struct KParams {
     uint32_t step;
     int heavy_step;
     int field_on;                    // gather E in the push
+    int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
     double weight;
     double masses[NSP];
@@ -135,9 +136,19 @@ constexpr uint32_t SID_INJ_COUNT = 0xD0000000u;
 __host__ __device__ constexpr uint32_t sid_inj_e(uint32_t p) { return 0xD1000000u | p; }
 __host__ __device__ constexpr uint32_t sid_inj_cu(uint32_t p) { return 0xD2000000u | p; }
 
-__device__ __forceinline__ uint32_t key_species(uint32_t key) { return key >> 24; }
+// Key layout: bits 0-23 cell, 24-26 species, 27-29 species before a
+// conversion in this step's collisions, 31 "converted" flag (the sort needs
+// the bin a particle was sorted under).  DEAD (all ones) is never a valid key.
+constexpr uint32_t KEY_FLAG = 0x80000000u;
+__device__ __forceinline__ uint32_t key_species(uint32_t key) { return (key >> 24) & 7u; }
+__device__ __forceinline__ uint32_t key_sorted_species(uint32_t key) {
+    return (key & KEY_FLAG) ? ((key >> 27) & 7u) : ((key >> 24) & 7u);
+}
 __device__ __forceinline__ uint32_t key_cell(uint32_t key) { return key & 0xFFFFFFu; }
 __device__ __forceinline__ uint32_t make_key(uint32_t sp, uint32_t cell) { return (sp << 24) | cell; }
+__device__ __forceinline__ uint32_t converted_key(uint32_t new_sp, uint32_t old_sp, uint32_t cell) {
+    return KEY_FLAG | (old_sp << 27) | (new_sp << 24) | cell;
+}
 
 __device__ __forceinline__ int charge_of(int sp) { return sp == SP_E ? -1 : (sp == SP_CU ? 0 : (sp == SP_CUP ? 1 : 2)); }
 

@@ -9,15 +9,22 @@ constexpr uint32_t SCAN_TILE = SCAN_THREADS * 8;   // elements per scan block
 
 inline uint32_t scan_padded(uint64_t n) { return (uint32_t)((n + SCAN_TILE - 1) / SCAN_TILE * SCAN_TILE); }
 
-void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* count,
-                 DevState* st, const KParams& P, const PushConsts& pc, int grid, cudaStream_t s);
+// push + deposit + mover bookkeeping (see pd_stream.cu)
+void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
+                 uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
+                 const KParams& P, const PushConsts& pc, int grid, cudaStream_t s);
+void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
+                     uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s);
 void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
                     int grid, cudaStream_t s);
-void launch_scatter(const Particles& A, const Particles& B, const uint32_t* off, uint32_t* count, DevState* st,
-                    const KParams& P, int grid, cudaStream_t s);
+void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
+                    const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
+                    DevState* st, const KParams& P, int grid, cudaStream_t s);
 // exclusive scan of n_padded (multiple of SCAN_TILE) u32; out has n_padded + 1
 // entries, out[n_padded] = total; partial needs n_padded / SCAN_TILE + 1 entries
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
+// the same over the population counts of the input words
+void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
 void launch_species_count(const Particles& A, DevState* st, unsigned long long* out, int grid, cudaStream_t s);
 void launch_density(const Particles& A, DevState* st, const KParams& P, int species, long long* acc, int grid,
                     cudaStream_t s);

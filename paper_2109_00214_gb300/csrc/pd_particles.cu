@@ -72,9 +72,18 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return wbase + x - v;
 }
 
+// scan input transform: the value itself, or its population count (a scan
+// of bit masks counts set bits)
+template <bool POPC>
+__device__ __forceinline__ uint4 scan_tf(uint4 v) {
+    if (POPC) return make_uint4(__popc(v.x), __popc(v.y), __popc(v.z), __popc(v.w));
+    return v;
+}
+
+template <bool POPC>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, uint32_t* partial) {
     const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)blockIdx.x * SCAN_TILE) + threadIdx.x * 2;
-    const uint4 a = p[0], b = p[1];
+    const uint4 a = scan_tf<POPC>(p[0]), b = scan_tf<POPC>(p[1]);
     uint32_t s = (a.x + a.y + a.z + a.w) + (b.x + b.y + b.z + b.w);
     s = __reduce_add_sync(FULL, s);
     __shared__ uint32_t ws[SCAN_THREADS / 32];
@@ -101,12 +110,13 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partial, uint3
     if (threadIdx.x == 0) partial[nb] = carry;
 }
 
+template <bool POPC>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* __restrict__ in,
                                                             const uint32_t* __restrict__ partial, uint32_t* out,
                                                             uint32_t n, uint32_t nb) {
     const size_t base = (size_t)blockIdx.x * SCAN_TILE + threadIdx.x * 8;
     const uint4* p = reinterpret_cast<const uint4*>(in + base);
-    const uint4 a = p[0], b = p[1];
+    const uint4 a = scan_tf<POPC>(p[0]), b = scan_tf<POPC>(p[1]);
     uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     uint32_t s = 0;
 #pragma unroll
@@ -212,9 +222,15 @@ void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevS
 }
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
     const uint32_t nb = n_padded / SCAN_TILE;
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, partial);
+    k_scan_reduce<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial);
     k_scan_partials<<<1, 1024, 0, s>>>(partial, nb);
-    k_scan_down<<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
+    k_scan_down<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
+}
+void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
+    const uint32_t nb = n_padded / SCAN_TILE;
+    k_scan_reduce<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial);
+    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb);
+    k_scan_down<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
 }
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
                       int64_t n, int nz, int nr, uint32_t id0, uint32_t* key, uint32_t* id, unsigned int* bad,

@@ -1,18 +1,27 @@
-// pd_stream.cu -- the two particle-streaming kernels of the step.
+// pd_stream.cu -- the particle-streaming kernels of the step.
 //
 //   k_push4     Newton push (Sec. 2.1) with the field gathered by the CIC
 //               weights of Eq. (10), r-z rotation or periodic wrap, absorbing
 //               walls, fused with the fixed-point CIC deposit of Eq. (9)-(10)
-//               and the (species, cell) histogram for the sort.
-//   k_scatter4  counting-sort scatter A -> B by (species, cell).
+//               and the bookkeeping of the cell sort.
+//   k_bincount  new bin counts = sorted counts - movers out + movers in.
+//   k_scatter4  the sort itself, A -> B in (species, cell) order.
 //
-// Both move four consecutive particles per thread with 128-bit loads issued
-// before any of them is used, so that each warp keeps 512 B per array in
-// flight: the kernels are bound by HBM latency and bandwidth, not by the
-// arithmetic.  Slot arrays are padded to a multiple of four.
+// The sort exploits that a step moves few particles out of their (species,
+// cell) bin.  Slots [0, n_sorted) hold the previous step's sorted order.  A
+// particle there that stays in its bin ("stayer") goes to
+//     new_off[b] + (p - old_off[b]) - (movers in [old_off[b], p)),
+// computed from a bit mask of movers and its popcount prefix: no atomics, and
+// the stayers of a warp land on consecutive slots.  Movers, spawned and
+// injected particles (slots >= n_sorted) take slots after the stayers of
+// their new bin through one atomic cursor per bin, aggregated over the warp.
+// With no previous order (after a load) everything is a mover and this is a
+// plain counting sort.
 //
-// Compiled with -fmad=false: every float operation is rounded on its own, in
-// the order written, as in the reference formulas of the method.
+// Both streaming kernels move four consecutive particles per thread with
+// 128-bit loads issued before use.  Slot arrays are padded to a multiple of
+// four.  Compiled with -fmad=false: every float operation is rounded on its
+// own, in the order written.
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
 #include "pd_warp.cuh"
@@ -27,7 +36,7 @@ __device__ __forceinline__ T pick5(const T (&a)[NSP], int sp) {
 __device__ __forceinline__ float lane_of(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ uint32_t lane_of(const uint4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
-// cell -> (iz, ir) without an integer division: float estimate, then fix by one
+// cell -> (iz, ir) without an integer division: float estimate, then fix
 __device__ __forceinline__ void decode_cell(uint32_t cell, const KParams& P, int& iz, int& ir) {
     int q = (int)((float)cell * P.inv_nr);
     int r = (int)cell - q * P.nr;
@@ -48,11 +57,15 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return i;
 }
 
+constexpr uint32_t NOBIN = 0xFFFFFFFFu;
+
 template <bool RZ, bool FIELD>
 __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
-                                               long long* rho_h, uint32_t* count, DevState* st, KParams P,
-                                               PushConsts pc) {
+                                               long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
+                                               uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
+                                               DevState* st, KParams P, PushConsts pc) {
     const uint32_t n = (uint32_t)st->n_slots;
+    const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -77,11 +90,12 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
         }
         uint32_t ko[4];
         float zo[4], ro[4], vzo[4], vro[4], vto[4];
-        bool moved_any = false;
+        bool moved_any = false, key_changed = false;
+        uint32_t nib = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t i = 4u * g + (uint32_t)q;
-            uint32_t key = (gv && i < n) ? lane_of(K, q) : DEAD;
+            const uint32_t key_in = (gv && i < n) ? lane_of(K, q) : DEAD;
             float pz = lane_of(Z, q), pr = lane_of(R, q);
             float vz = lane_of(VZ, q), vr = lane_of(VR, q), vt = lane_of(VT, q);
             ko[q] = lane_of(K, q);
@@ -90,9 +104,12 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
             vzo[q] = vz;
             vro[q] = vr;
             vto[q] = vt;
-            const bool live = key != DEAD;
-            const int sp = (int)key_species(key);
-            uint32_t cell = key_cell(key);
+            const bool live = key_in != DEAD;
+            const int sp = (int)key_species(key_in);
+            const uint32_t cell_in = key_cell(key_in);
+            const bool in_sorted = live && i < n_sorted;
+            const uint32_t old_bin = in_sorted ? key_sorted_species(key_in) * P.ncell + cell_in : NOBIN;
+            uint32_t cell = cell_in;
             const bool move = live && (sp == SP_E || P.heavy_step);
             bool keep = live;
             int iz = 0, ir = 0;
@@ -149,8 +166,6 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 }
                 if (electrode >= 0) {
                     keep = false;
-                    key = DEAD;
-                    ko[q] = DEAD;
                     const double v2 = (double)vz * vz + (double)vr * vr + (double)vt * vt;
                     const double ke = P.weight * (0.5 * pick5(P.masses, sp) * v2);
                     atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
@@ -160,8 +175,6 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                     if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
                 } else {
                     cell = (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir;
-                    key = make_key((uint32_t)sp, cell);
-                    ko[q] = key;
                     zo[q] = npz;
                     ro[q] = npr;
                     vzo[q] = vz;
@@ -173,34 +186,74 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                     pr = npr;
                 }
             }
+            const uint32_t key = keep ? make_key((uint32_t)sp, cell) : DEAD;
+            if (live) {
+                key_changed |= key != key_in;
+                ko[q] = key;
+            }
+            const uint32_t new_bin = keep ? (uint32_t)sp * P.ncell + cell : NOBIN;
+            const bool mover = in_sorted && new_bin != old_bin;
+            const bool in_mover = keep && (!in_sorted || new_bin != old_bin);
+            nib |= (mover ? 1u : 0u) << q;
+            if (mover) atomicAdd(&out_cnt[old_bin], 1u);
+            warp_count(in_cnt, new_bin, in_mover);
             const int zq = charge_of(sp);
             const bool dep = move && keep && zq != 0;
             // electrons and heavies deposit into separate grids (heavies are
             // held between their sub-cycled pushes)
-            warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, dep && sp == SP_E);
-            warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, dep && sp != SP_E);
-            warp_count(count, (uint32_t)sp * P.ncell + cell, keep);
-        }
-        if (gv && moved_any) {
-            key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
-            pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
-            pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
-            if (FIELD || RZ) {
-                vz4[g] = make_float4(vzo[0], vzo[1], vzo[2], vzo[3]);
-                vr4[g] = make_float4(vro[0], vro[1], vro[2], vro[3]);
+            if (__any_sync(FULL_MASK, dep)) {
+                long long* rho = sp == SP_E ? rho_e : rho_h;
+                warp_deposit(rho, P, key, iz, ir, pz, pr, zq, dep);
             }
-            if (RZ) vt4[g] = make_float4(vto[0], vto[1], vto[2], vto[3]);
+        }
+        // mover bits: particle 4g+q is bit (4g+q) % 32 of word (4g+q) / 32
+        uint32_t word = nib << (4 * (lane & 7));
+        word |= __shfl_xor_sync(FULL_MASK, word, 1);
+        word |= __shfl_xor_sync(FULL_MASK, word, 2);
+        word |= __shfl_xor_sync(FULL_MASK, word, 4);
+        if ((lane & 7) == 0 && gv) mv[(g0 >> 3) + (lane >> 3)] = word;
+        if (gv && (moved_any || key_changed)) {
+            key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
+            if (moved_any) {
+                pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
+                pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
+                if (FIELD || RZ) {
+                    vz4[g] = make_float4(vzo[0], vzo[1], vzo[2], vzo[3]);
+                    vr4[g] = make_float4(vro[0], vro[1], vro[2], vro[3]);
+                }
+                if (RZ) vt4[g] = make_float4(vto[0], vto[1], vto[2], vto[3]);
+            }
         }
     }
 }
 
-// Counting-sort scatter.  All seven arrays of four particles are loaded
-// first; then per particle: its bin offset and, for each group of lanes with
-// the same bin, one atomic that reserves the group's slots (the bin counter
-// counts back down to zero, ready for the next histogram).
-__global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, const uint32_t* __restrict__ off,
-                                                  uint32_t* count, DevState* st, KParams P) {
+// cnt[b] = (sorted count of b) - out[b] + in[b]; stay[b] = sorted - out; out := 0
+__global__ void __launch_bounds__(256) k_bincount(const uint32_t* __restrict__ old_off, uint32_t* out_cnt,
+                                                  const uint32_t* __restrict__ in_cnt, uint32_t* cnt, uint32_t* stay,
+                                                  uint32_t nbins_pad, int use_prev) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins_pad; b += gridDim.x * blockDim.x) {
+        const uint32_t sorted = use_prev ? old_off[b + 1] - old_off[b] : 0u;
+        const uint32_t s = sorted - out_cnt[b];
+        stay[b] = s;
+        cnt[b] = s + in_cnt[b];
+        out_cnt[b] = 0u;
+    }
+}
+
+// movers strictly before slot p (p < n_sorted)
+__device__ __forceinline__ uint32_t movers_before(const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
+                                                  uint32_t p) {
+    const uint32_t w = p >> 5;
+    return mvx[w] + (uint32_t)__popc(mv[w] & ((1u << (p & 31u)) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, const uint32_t* __restrict__ old_off,
+                                                  const uint32_t* __restrict__ new_off,
+                                                  const uint32_t* __restrict__ stay, uint32_t* in_cnt,
+                                                  const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
+                                                  uint32_t nbins, DevState* st, KParams P) {
     const uint32_t n = (uint32_t)st->n_slots;
+    const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -210,6 +263,7 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
         const bool gv = g < nv;
         uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
         float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
+        uint32_t mw = 0, mx = 0;
         if (gv) {
             K = reinterpret_cast<const uint4*>(A.key)[g];
             Z = reinterpret_cast<const float4*>(A.pz)[g];
@@ -218,51 +272,73 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
             VR = reinterpret_cast<const float4*>(A.vr)[g];
             VT = reinterpret_cast<const float4*>(A.vt)[g];
             ID = reinterpret_cast<const uint4*>(A.id)[g];
-        }
-        uint32_t bin[4], grp[4], base[4], old[4];
-        bool lv[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t key = (gv && 4u * g + (uint32_t)q < n) ? lane_of(K, q) : DEAD;
-            lv[q] = key != DEAD;
-            bin[q] = lv[q] ? key_species(key) * P.ncell + key_cell(key) : 0u;
-            base[q] = lv[q] ? off[bin[q]] : 0u;
+            if (4u * g < n_sorted) {
+                mw = mv[g >> 3];
+                mx = mvx[g >> 3];
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const unsigned m = __ballot_sync(FULL_MASK, lv[q]);
-            grp[q] = lv[q] ? __match_any_sync(m, bin[q]) : 0u;
-            old[q] = 0;
-            if (lv[q] && lane == __ffs(grp[q]) - 1) old[q] = atomicSub(&count[bin[q]], (uint32_t)__popc(grp[q]));
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!lv[q]) continue;
-            const uint32_t o = __shfl_sync(grp[q], old[q], __ffs(grp[q]) - 1);
-            const uint32_t slot = base[q] + o - (uint32_t)__popc(grp[q]) + (uint32_t)__popc(grp[q] & lt);
-            B.key[slot] = lane_of(K, q);
-            B.pz[slot] = lane_of(Z, q);
-            B.pr[slot] = lane_of(R, q);
-            B.vz[slot] = lane_of(VZ, q);
-            B.vr[slot] = lane_of(VR, q);
-            B.vt[slot] = lane_of(VT, q);
-            B.id[slot] = lane_of(ID, q);
+            const uint32_t i = 4u * g + (uint32_t)q;
+            const uint32_t key = (gv && i < n) ? lane_of(K, q) : DEAD;
+            const bool live = key != DEAD;
+            const uint32_t b = live ? key_species(key) * P.ncell + key_cell(key) : 0u;
+            const bool stayer = live && i < n_sorted && !((mw >> (i & 31u)) & 1u);
+            const bool mover = live && !stayer;
+            uint32_t slot = 0;
+            if (stayer) {
+                const uint32_t o = old_off[b];
+                const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
+                slot = new_off[b] + (i - o) - (before - movers_before(mv, mvx, o));
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, mover);
+            if (mover) {
+                const unsigned grp = __match_any_sync(m, b);
+                const int leader = __ffs(grp) - 1;
+                const uint32_t cnt = (uint32_t)__popc(grp);
+                uint32_t old = 0;
+                if (lane == leader) old = atomicSub(&in_cnt[b], cnt);
+                old = __shfl_sync(grp, old, leader);
+                slot = new_off[b] + stay[b] + old - cnt + (uint32_t)__popc(grp & lt);
+            }
+            if (live && slot >= n) {        // inconsistent bookkeeping: report, never write out of range
+                set_error(st, ERR_BOUNDS);
+                continue;
+            }
+            if (live) {
+                B.key[slot] = key;
+                B.pz[slot] = lane_of(Z, q);
+                B.pr[slot] = lane_of(R, q);
+                B.vz[slot] = lane_of(VZ, q);
+                B.vr[slot] = lane_of(VR, q);
+                B.vt[slot] = lane_of(VT, q);
+                B.id[slot] = lane_of(ID, q);
+            }
         }
     }
 }
 
-void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* count,
-                 DevState* st, const KParams& P, const PushConsts& pc, int grid, cudaStream_t s) {
+void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
+                 uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
+                 const KParams& P, const PushConsts& pc, int grid, cudaStream_t s) {
     const bool rz = P.geom == 0, field = P.field_on != 0;
-    if (rz && field) k_push4<true, true><<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
-    else if (rz) k_push4<true, false><<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
-    else if (field) k_push4<false, true><<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
-    else k_push4<false, false><<<grid, 256, 0, s>>>(A, E, rho_e, rho_h, count, st, P, pc);
+#define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, old_off, nbins, st, P, pc
+    if (rz && field) k_push4<true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    else if (rz) k_push4<true, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    else if (field) k_push4<false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    else k_push4<false, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+#undef PD_PUSH_ARGS
 }
 
-void launch_scatter(const Particles& A, const Particles& B, const uint32_t* off, uint32_t* count, DevState* st,
-                    const KParams& P, int grid, cudaStream_t s) {
-    k_scatter4<<<grid, 256, 0, s>>>(A, B, off, count, st, P);
+void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
+                     uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s) {
+    k_bincount<<<grid, 256, 0, s>>>(old_off, out_cnt, in_cnt, cnt, stay, nbins_pad, use_prev);
+}
+
+void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
+                    const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
+                    DevState* st, const KParams& P, int grid, cudaStream_t s) {
+    k_scatter4<<<grid, 256, 0, s>>>(A, B, old_off, new_off, stay, in_cnt, mv, mvx, nbins, st, P);
 }
 
 }  // namespace pd
