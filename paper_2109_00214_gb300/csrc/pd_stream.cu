@@ -14,14 +14,16 @@
 // computed from a bit mask of movers and its popcount prefix: no atomics, and
 // the stayers of a warp land on consecutive slots.  Movers, spawned and
 // injected particles (slots >= n_sorted) take slots after the stayers of
-// their new bin through one atomic cursor per bin, aggregated over the warp.
-// With no previous order (after a load) everything is a mover and this is a
-// plain counting sort.
+// their new bin through one atomic cursor per bin.  With no previous order
+// (after a load) everything is a mover and this is a plain counting sort.
 //
-// Both streaming kernels move four consecutive particles per thread with
-// 128-bit loads issued before use.  Slot arrays are padded to a multiple of
-// four.  Compiled with -fmad=false: every float operation is rounded on its
-// own, in the order written.
+// Each thread moves four consecutive particles with 128-bit loads issued
+// before use.  Sorted input means the four usually share a cell, so counts,
+// slot claims and deposited charge are merged over runs of equal keys inside
+// the thread (no warp-wide collectives on the common path), and the push
+// arithmetic is done for all four and selected, without divergent branches.
+// Slot arrays are padded to a multiple of four.  Compiled with -fmad=false:
+// every float operation is rounded on its own, in the order written.
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
 #include "pd_warp.cuh"
@@ -36,25 +38,37 @@ __device__ __forceinline__ T pick5(const T (&a)[NSP], int sp) {
 __device__ __forceinline__ float lane_of(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ uint32_t lane_of(const uint4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
-// cell -> (iz, ir) without an integer division: float estimate, then fix
+// cell -> (iz, ir) without an integer division: the float estimate is within
+// one of the quotient for cell < 2^24 and nr >= 2; fix it without branches
 __device__ __forceinline__ void decode_cell(uint32_t cell, const KParams& P, int& iz, int& ir) {
     int q = (int)((float)cell * P.inv_nr);
     int r = (int)cell - q * P.nr;
-    while (r < 0) {
-        q -= 1;
-        r += P.nr;
-    }
-    while (r >= P.nr) {
-        q += 1;
-        r -= P.nr;
-    }
+    const int lo = r < 0 ? 1 : 0, hi = r >= P.nr ? 1 : 0;
+    q += hi - lo;
+    r += (lo - hi) * P.nr;
     iz = q;
     ir = r;
 }
 
-__device__ __forceinline__ int wrap(int i, int n) {
-    if ((unsigned)i >= (unsigned)n) i = ((i % n) + n) % n;
+// periodic wrap of an index that moved by at most one period
+__device__ __forceinline__ int wrap1(int i, int n) {
+    i += i < 0 ? n : 0;
+    i -= i >= n ? n : 0;
     return i;
+}
+
+// Runs of equal keys among the "on" entries of four consecutive particles:
+// link[q] = particle q continues the run of q-1; len[q] = length of the run
+// that starts at q (0 if q does not start one).
+__device__ __forceinline__ void runs4(const bool (&on)[4], const uint32_t (&key)[4], bool (&link)[4],
+                                      uint32_t (&len)[4]) {
+    link[0] = false;
+#pragma unroll
+    for (int q = 1; q < 4; ++q) link[q] = on[q] && on[q - 1] && key[q] == key[q - 1];
+    const uint32_t c3 = 0, c2 = link[3] ? 1u + c3 : 0u, c1 = link[2] ? 1u + c2 : 0u, c0 = link[1] ? 1u + c1 : 0u;
+    const uint32_t c[4] = {c0, c1, c2, c3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) len[q] = (on[q] && !link[q]) ? 1u + c[q] : 0u;
 }
 
 constexpr uint32_t NOBIN = 0xFFFFFFFFu;
@@ -67,7 +81,6 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
     const uint32_t n = (uint32_t)st->n_slots;
     const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
-    const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     uint4* key4 = reinterpret_cast<uint4*>(A.key);
     float4* pz4 = reinterpret_cast<float4*>(A.pz);
@@ -75,8 +88,7 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
     float4* vz4 = reinterpret_cast<float4*>(A.vz);
     float4* vr4 = reinterpret_cast<float4*>(A.vr);
     float4* vt4 = reinterpret_cast<float4*>(A.vt);
-    for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < nv; g0 += stride) {
-        const uint32_t g = g0 + lane;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x % 32u < nv; g += stride) {
         const bool gv = g < nv;
         uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD);
         float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
@@ -88,141 +100,178 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
             VR = vr4[g];
             if (RZ) VT = vt4[g];
         }
-        uint32_t ko[4];
-        float zo[4], ro[4], vzo[4], vro[4], vto[4];
-        bool moved_any = false, key_changed = false;
-        uint32_t nib = 0;
+        uint32_t ko[4], key[4], newbin[4], oldbin[4];
+        float zo[4], ro[4], vzo[4], vro[4], vto[4], dz_[4], dr_[4];
+        int sp_[4], iz_[4], ir_[4], wall_[4];
+        bool keep[4], mover[4], inmv[4], dep[4], absd[4], moved[4];
+        uint32_t flags = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t i = 4u * g + (uint32_t)q;
             const uint32_t key_in = (gv && i < n) ? lane_of(K, q) : DEAD;
-            float pz = lane_of(Z, q), pr = lane_of(R, q);
+            const float pz = lane_of(Z, q), pr = lane_of(R, q);
             float vz = lane_of(VZ, q), vr = lane_of(VR, q), vt = lane_of(VT, q);
-            ko[q] = lane_of(K, q);
-            zo[q] = pz;
-            ro[q] = pr;
-            vzo[q] = vz;
-            vro[q] = vr;
-            vto[q] = vt;
             const bool live = key_in != DEAD;
-            const int sp = (int)key_species(key_in);
-            const uint32_t cell_in = key_cell(key_in);
+            const int sp = live ? (int)key_species(key_in) : 0;
             const bool in_sorted = live && i < n_sorted;
-            const uint32_t old_bin = in_sorted ? key_sorted_species(key_in) * P.ncell + cell_in : NOBIN;
-            uint32_t cell = cell_in;
+            oldbin[q] = in_sorted ? key_sorted_species(key_in) * P.ncell + key_cell(key_in) : NOBIN;
             const bool move = live && (sp == SP_E || P.heavy_step);
-            bool keep = live;
-            int iz = 0, ir = 0;
-            if (move) {
-                moved_any = true;
-                decode_cell(cell, P, iz, ir);
-                const float qmdt = pick5(pc.qmdt, sp), dtz = pick5(pc.dtz, sp), dtr = pick5(pc.dtr, sp);
-                if (FIELD) {
-                    const float gz = 1.0f - pz, gr = 1.0f - pr;
-                    const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
-                    const float2 e00 = E[node_of(P, iz, ir)], e10 = E[node_of(P, iz + 1, ir)];
-                    const float2 e01 = E[node_of(P, iz, ir + 1)], e11 = E[node_of(P, iz + 1, ir + 1)];
-                    const float ez = ((w00 * e00.x + w10 * e10.x) + w01 * e01.x) + w11 * e11.x;
-                    const float er = ((w00 * e00.y + w10 * e10.y) + w01 * e01.y) + w11 * e11.y;
-                    vz = vz + qmdt * ez;
-                    vr = vr + qmdt * er;
-                }
-                const float z = pz + vz * dtz;
-                const float fz = floorf(z);
-                int niz = iz + (int)fz;
-                float npz = z - fz;
-                if (npz >= 1.0f) npz = 0x1.fffffep-1f;
-                int nir;
-                float npr;
-                int electrode = -1;
-                if (RZ) {
-                    const float x = ((float)ir + pr) + vr * dtr;
-                    const float y = vt * dtr;
-                    const float rr = sqrtf(x * x + y * y);
-                    float c = 1.0f, s = 0.0f;
-                    if (rr > 0.0f) {
-                        c = x / rr;
-                        s = y / rr;
-                    }
-                    const float nvr = c * vr + s * vt;
-                    const float nvt = c * vt - s * vr;
-                    vr = nvr;
-                    vt = nvt;
-                    const float fr = floorf(rr);
-                    nir = (int)fr;
-                    npr = rr - fr;
-                    if (npr >= 1.0f) npr = 0x1.fffffep-1f;
-                    if (niz < 0) electrode = 0;
-                    else if (niz >= P.nz) electrode = 1;
-                    else if (nir >= P.nr) electrode = 2;
-                } else {
-                    const float r = pr + vr * dtr;
-                    const float fr = floorf(r);
-                    nir = ir + (int)fr;
-                    npr = r - fr;
-                    if (npr >= 1.0f) npr = 0x1.fffffep-1f;
-                    niz = wrap(niz, P.nz);
-                    nir = wrap(nir, P.nr);
-                }
-                if (electrode >= 0) {
-                    keep = false;
-                    const double v2 = (double)vz * vz + (double)vr * vr + (double)vt * vt;
-                    const double ke = P.weight * (0.5 * pick5(P.masses, sp) * v2);
-                    atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
-                    atomicAdd(&st->absorbed_energy[electrode], ke);
-                    const double qw = (double)charge_of(sp) * 1.602176634e-19 * P.weight;
-                    if (electrode == 1) atomicAdd(&st->anode_charge_step, qw);
-                    if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
-                } else {
-                    cell = (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir;
-                    zo[q] = npz;
-                    ro[q] = npr;
-                    vzo[q] = vz;
-                    vro[q] = vr;
-                    vto[q] = vt;
-                    iz = niz;
-                    ir = nir;
-                    pz = npz;
-                    pr = npr;
-                }
+            const uint32_t cell_in = move ? key_cell(key_in) : 0u;   // dead lanes read a valid node
+            int iz, ir;
+            decode_cell(cell_in, P, iz, ir);
+            const float qmdt = pick5(pc.qmdt, sp), dtz = pick5(pc.dtz, sp), dtr = pick5(pc.dtr, sp);
+            if (FIELD) {
+                const float gz = 1.0f - pz, gr = 1.0f - pr;
+                const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
+                const float2 e00 = E[node_of(P, iz, ir)], e10 = E[node_of(P, iz + 1, ir)];
+                const float2 e01 = E[node_of(P, iz, ir + 1)], e11 = E[node_of(P, iz + 1, ir + 1)];
+                const float ez = ((w00 * e00.x + w10 * e10.x) + w01 * e01.x) + w11 * e11.x;
+                const float er = ((w00 * e00.y + w10 * e10.y) + w01 * e01.y) + w11 * e11.y;
+                vz = vz + qmdt * ez;
+                vr = vr + qmdt * er;
             }
-            const uint32_t key = keep ? make_key((uint32_t)sp, cell) : DEAD;
-            if (live) {
-                key_changed |= key != key_in;
-                ko[q] = key;
+            const float z = pz + vz * dtz;
+            const float fz = floorf(z);
+            int niz = iz + (int)fz;
+            float npz = z - fz;
+            npz = npz >= 1.0f ? 0x1.fffffep-1f : npz;
+            int nir;
+            float npr;
+            bool out = false;
+            if (RZ) {
+                const float x = ((float)ir + pr) + vr * dtr;
+                const float y = vt * dtr;
+                const float rr = sqrtf(x * x + y * y);
+                const bool pos = rr > 0.0f;
+                const float c = pos ? x / rr : 1.0f, s = pos ? y / rr : 0.0f;
+                const float nvr = c * vr + s * vt;
+                const float nvt = c * vt - s * vr;
+                vr = nvr;
+                vt = nvt;
+                const float fr = floorf(rr);
+                nir = (int)fr;
+                npr = rr - fr;
+                npr = npr >= 1.0f ? 0x1.fffffep-1f : npr;
+                out = niz < 0 || niz >= P.nz || nir >= P.nr;
+                // cathode (z = 0) before anode (z = L) before the outer wall (r = R)
+                wall_[q] = niz < 0 ? 0 : (niz >= P.nz ? 1 : 2);
+            } else {
+                wall_[q] = 0;
+                const float r = pr + vr * dtr;
+                const float fr = floorf(r);
+                nir = ir + (int)fr;
+                npr = r - fr;
+                npr = npr >= 1.0f ? 0x1.fffffep-1f : npr;
+                // a particle crosses at most one period per step (|v dt| < one domain)
+                niz = wrap1(niz, P.nz);
+                nir = wrap1(nir, P.nr);
             }
-            const uint32_t new_bin = keep ? (uint32_t)sp * P.ncell + cell : NOBIN;
-            const bool mover = in_sorted && new_bin != old_bin;
-            const bool in_mover = keep && (!in_sorted || new_bin != old_bin);
-            nib |= (mover ? 1u : 0u) << q;
-            if (mover) atomicAdd(&out_cnt[old_bin], 1u);
-            warp_count(in_cnt, new_bin, in_mover);
-            const int zq = charge_of(sp);
-            const bool dep = move && keep && zq != 0;
-            // electrons and heavies deposit into separate grids (heavies are
-            // held between their sub-cycled pushes)
-            if (__any_sync(FULL_MASK, dep)) {
-                long long* rho = sp == SP_E ? rho_e : rho_h;
-                warp_deposit(rho, P, key, iz, ir, pz, pr, zq, dep);
+            const bool absorbed = move && out;
+            const bool kp = live && !absorbed;
+            const uint32_t cell = move ? (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir : key_cell(key_in);
+            const uint32_t k = kp ? make_key((uint32_t)sp, cell) : DEAD;
+            const uint32_t nb = kp ? (uint32_t)sp * P.ncell + cell : NOBIN;
+            const bool mvq = in_sorted && nb != oldbin[q];
+            const bool inq = kp && (!in_sorted || nb != oldbin[q]);
+            const bool mk = move && kp;
+            ko[q] = live ? k : lane_of(K, q);
+            key[q] = k;
+            newbin[q] = nb;
+            keep[q] = kp;
+            mover[q] = mvq;
+            inmv[q] = inq;
+            absd[q] = absorbed;
+            moved[q] = mk;
+            zo[q] = mk ? npz : pz;
+            ro[q] = mk ? npr : pr;
+            vzo[q] = move ? vz : lane_of(VZ, q);
+            vro[q] = move ? vr : lane_of(VR, q);
+            vto[q] = move ? vt : lane_of(VT, q);
+            dz_[q] = zo[q];
+            dr_[q] = ro[q];
+            sp_[q] = sp;
+            iz_[q] = mk ? niz : iz;
+            ir_[q] = mk ? nir : ir;
+            dep[q] = mk && charge_of(sp) != 0;
+            flags |= (absorbed ? 1u : 0u) | (mvq ? 2u : 0u) | (inq ? 4u : 0u) | (dep[q] ? 8u : 0u) |
+                     ((live && k != lane_of(K, q)) || mk ? 16u : 0u);
+        }
+        const uint32_t wflags = __reduce_or_sync(FULL_MASK, flags);
+        if (RZ && (wflags & 1u)) {  // absorbed at an electrode or the outer wall: ledgers
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!absd[q]) continue;
+                const int sp = sp_[q];
+                const int electrode = wall_[q];
+                const double v2 = (double)vzo[q] * vzo[q] + (double)vro[q] * vro[q] + (double)vto[q] * vto[q];
+                const double ke = P.weight * (0.5 * pick5(P.masses, sp) * v2);
+                atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
+                atomicAdd(&st->absorbed_energy[electrode], ke);
+                const double qw = (double)charge_of(sp) * 1.602176634e-19 * P.weight;
+                if (electrode == 1) atomicAdd(&st->anode_charge_step, qw);
+                if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
             }
         }
-        // mover bits: particle 4g+q is bit (4g+q) % 32 of word (4g+q) / 32
-        uint32_t word = nib << (4 * (lane & 7));
-        word |= __shfl_xor_sync(FULL_MASK, word, 1);
-        word |= __shfl_xor_sync(FULL_MASK, word, 2);
-        word |= __shfl_xor_sync(FULL_MASK, word, 4);
-        if ((lane & 7) == 0 && gv) mv[(g0 >> 3) + (lane >> 3)] = word;
-        if (gv && (moved_any || key_changed)) {
-            key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
-            if (moved_any) {
-                pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
-                pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
-                if (FIELD || RZ) {
-                    vz4[g] = make_float4(vzo[0], vzo[1], vzo[2], vzo[3]);
-                    vr4[g] = make_float4(vro[0], vro[1], vro[2], vro[3]);
-                }
-                if (RZ) vt4[g] = make_float4(vto[0], vto[1], vto[2], vto[3]);
+        if (wflags & 2u) {          // movers out of their sorted bin
+            uint32_t nib = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (mover[q]) atomicAdd(&out_cnt[oldbin[q]], 1u);
+                nib |= (mover[q] ? 1u : 0u) << q;
             }
+            if (nib) atomicOr(&mv[g >> 3], nib << (4u * (g & 7u)));
+        }
+        if (wflags & 4u) {          // movers into their new bin (all particles after a load)
+            bool link[4];
+            uint32_t len[4];
+            runs4(inmv, newbin, link, len);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (len[q]) atomicAdd(&in_cnt[newbin[q]], len[q]);
+        }
+        if (wflags & 8u) {          // fixed-point CIC deposit, merged over runs of one key
+            bool link[4];
+            uint32_t len[4];
+            runs4(dep, key, link, len);
+            unsigned long long W[4][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t wz = __float2uint_rn(dz_[q] * 65536.0f);
+                const uint32_t wr = __float2uint_rn(dr_[q] * 65536.0f);
+                const unsigned long long az = 65536u - wz, ar = 65536u - wr;
+                W[q][0] = dep[q] ? az * ar : 0ull;
+                W[q][1] = dep[q] ? (unsigned long long)wz * ar : 0ull;
+                W[q][2] = dep[q] ? az * (unsigned long long)wr : 0ull;
+                W[q][3] = dep[q] ? (unsigned long long)wz * wr : 0ull;
+            }
+            // accumulate each run into its first particle (runs are contiguous)
+#pragma unroll
+            for (int q = 3; q >= 1; --q)
+                if (link[q])
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) W[q - 1][c] += W[q][c];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!len[q]) continue;
+                const long long zq = charge_of(sp_[q]);
+                long long* rho = sp_[q] == SP_E ? rho_e : rho_h;
+                const int iz = iz_[q], ir = ir_[q];
+                atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir)], (unsigned long long)(zq * (long long)W[q][0]));
+                atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir)], (unsigned long long)(zq * (long long)W[q][1]));
+                atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir + 1)], (unsigned long long)(zq * (long long)W[q][2]));
+                atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir + 1)],
+                          (unsigned long long)(zq * (long long)W[q][3]));
+            }
+        }
+        if (gv && (flags & 16u)) {
+            key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
+            pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
+            pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
+            if (FIELD || RZ) {
+                vz4[g] = make_float4(vzo[0], vzo[1], vzo[2], vzo[3]);
+                vr4[g] = make_float4(vro[0], vro[1], vro[2], vro[3]);
+            }
+            if (RZ) vt4[g] = make_float4(vto[0], vto[1], vto[2], vto[3]);
         }
     }
 }
@@ -255,65 +304,66 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
     const uint32_t n = (uint32_t)st->n_slots;
     const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
-    const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
-    const unsigned lt = lanemask_lt();
-    for (uint32_t g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < nv; g0 += stride) {
-        const uint32_t g = g0 + lane;
-        const bool gv = g < nv;
-        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
-        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
-        uint32_t mw = 0, mx = 0;
-        if (gv) {
-            K = reinterpret_cast<const uint4*>(A.key)[g];
-            Z = reinterpret_cast<const float4*>(A.pz)[g];
-            R = reinterpret_cast<const float4*>(A.pr)[g];
-            VZ = reinterpret_cast<const float4*>(A.vz)[g];
-            VR = reinterpret_cast<const float4*>(A.vr)[g];
-            VT = reinterpret_cast<const float4*>(A.vt)[g];
-            ID = reinterpret_cast<const uint4*>(A.id)[g];
-            if (4u * g < n_sorted) {
-                mw = mv[g >> 3];
-                mx = mvx[g >> 3];
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nv; g += stride) {
+        const uint4 K = reinterpret_cast<const uint4*>(A.key)[g];
+        const float4 Z = reinterpret_cast<const float4*>(A.pz)[g];
+        const float4 R = reinterpret_cast<const float4*>(A.pr)[g];
+        const float4 VZ = reinterpret_cast<const float4*>(A.vz)[g];
+        const float4 VR = reinterpret_cast<const float4*>(A.vr)[g];
+        const float4 VT = reinterpret_cast<const float4*>(A.vt)[g];
+        const uint4 ID = reinterpret_cast<const uint4*>(A.id)[g];
+        const bool sorted_part = 4u * g < n_sorted;
+        const uint32_t mw = sorted_part ? mv[g >> 3] : 0u;
+        const uint32_t mx = sorted_part ? mvx[g >> 3] : 0u;
+        uint32_t key[4], bin[4], slot[4];
+        bool live[4], mover[4];
+        bool any_mover = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = 4u * g + (uint32_t)q;
+            key[q] = i < n ? lane_of(K, q) : DEAD;
+            live[q] = key[q] != DEAD;
+            bin[q] = live[q] ? key_species(key[q]) * P.ncell + key_cell(key[q]) : 0u;
+            const bool stayer = live[q] && i < n_sorted && !((mw >> (i & 31u)) & 1u);
+            mover[q] = live[q] && !stayer;
+            any_mover |= mover[q];
+            slot[q] = 0;
+            if (stayer) {
+                const uint32_t o = old_off[bin[q]];
+                const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
+                slot[q] = new_off[bin[q]] + (i - o) - (before - movers_before(mv, mvx, o));
+            }
+        }
+        if (any_mover) {            // claim slots after the stayers, one atomic per run of one bin
+            bool link[4];
+            uint32_t len[4];
+            runs4(mover, bin, link, len);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (len[q]) {
+                    const uint32_t old = atomicSub(&in_cnt[bin[q]], len[q]);
+                    slot[q] = new_off[bin[q]] + stay[bin[q]] + old - len[q];
+                } else if (link[q]) {
+                    slot[q] = (q > 0 ? slot[q > 0 ? q - 1 : 0] : 0u) + 1u;
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t i = 4u * g + (uint32_t)q;
-            const uint32_t key = (gv && i < n) ? lane_of(K, q) : DEAD;
-            const bool live = key != DEAD;
-            const uint32_t b = live ? key_species(key) * P.ncell + key_cell(key) : 0u;
-            const bool stayer = live && i < n_sorted && !((mw >> (i & 31u)) & 1u);
-            const bool mover = live && !stayer;
-            uint32_t slot = 0;
-            if (stayer) {
-                const uint32_t o = old_off[b];
-                const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
-                slot = new_off[b] + (i - o) - (before - movers_before(mv, mvx, o));
-            }
-            const unsigned m = __ballot_sync(FULL_MASK, mover);
-            if (mover) {
-                const unsigned grp = __match_any_sync(m, b);
-                const int leader = __ffs(grp) - 1;
-                const uint32_t cnt = (uint32_t)__popc(grp);
-                uint32_t old = 0;
-                if (lane == leader) old = atomicSub(&in_cnt[b], cnt);
-                old = __shfl_sync(grp, old, leader);
-                slot = new_off[b] + stay[b] + old - cnt + (uint32_t)__popc(grp & lt);
-            }
-            if (live && slot >= n) {        // inconsistent bookkeeping: report, never write out of range
+            if (!live[q]) continue;
+            if (slot[q] >= n) {     // inconsistent bookkeeping: report, never write out of range
                 set_error(st, ERR_BOUNDS);
                 continue;
             }
-            if (live) {
-                B.key[slot] = key;
-                B.pz[slot] = lane_of(Z, q);
-                B.pr[slot] = lane_of(R, q);
-                B.vz[slot] = lane_of(VZ, q);
-                B.vr[slot] = lane_of(VR, q);
-                B.vt[slot] = lane_of(VT, q);
-                B.id[slot] = lane_of(ID, q);
-            }
+            const uint32_t s = slot[q];
+            B.key[s] = key[q];
+            B.pz[s] = lane_of(Z, q);
+            B.pr[s] = lane_of(R, q);
+            B.vz[s] = lane_of(VZ, q);
+            B.vr[s] = lane_of(VR, q);
+            B.vt[s] = lane_of(VT, q);
+            B.id[s] = lane_of(ID, q);
         }
     }
 }
