@@ -652,6 +652,9 @@ pd_status pd_step(pd_sim* s, int64_t n_steps) {
             Timed t(s, K_MEMSET);
             cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
             if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
+            // mover bits are OR-ed in by the push: start from zero
+            const size_t words = (size_t)(std::min<int64_t>(c.capacity, 0xFFFFFFFFll) + 127) / 32;
+            cudaMemsetAsync(s->mv, 0, std::min<size_t>(words, s->L.words_pad) * 4, s->stream);
         }
         {
             Timed t(s, K_PUSH);

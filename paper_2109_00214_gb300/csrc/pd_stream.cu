@@ -332,7 +332,9 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
             if (stayer) {
                 const uint32_t o = old_off[bin[q]];
                 const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
-                slot[q] = new_off[bin[q]] + (i - o) - (before - movers_before(mv, mvx, o));
+                const uint32_t r = (i - o) - (before - movers_before(mv, mvx, o));
+                if (r >= stay[bin[q]]) set_error(st, ERR_BOUNDS);   // stayer outside its bin's range
+                slot[q] = new_off[bin[q]] + r;
             }
         }
         if (any_mover) {            // claim slots after the stayers, one atomic per run of one bin
@@ -343,6 +345,7 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
             for (int q = 0; q < 4; ++q) {
                 if (len[q]) {
                     const uint32_t old = atomicSub(&in_cnt[bin[q]], len[q]);
+                    if (old < len[q]) set_error(st, ERR_BOUNDS);      // more movers than counted
                     slot[q] = new_off[bin[q]] + stay[bin[q]] + old - len[q];
                 } else if (link[q]) {
                     slot[q] = (q > 0 ? slot[q > 0 ? q - 1 : 0] : 0u) + 1u;
