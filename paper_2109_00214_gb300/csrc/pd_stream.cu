@@ -296,37 +296,59 @@ __device__ __forceinline__ uint32_t movers_before(const uint32_t* __restrict__ m
     return mvx[w] + (uint32_t)__popc(mv[w] & ((1u << (p & 31u)) - 1u));
 }
 
-__global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, const uint32_t* __restrict__ old_off,
-                                                  const uint32_t* __restrict__ new_off,
-                                                  const uint32_t* __restrict__ stay, uint32_t* in_cnt,
-                                                  const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
-                                                  uint32_t nbins, DevState* st, KParams P) {
+// Staging window of the scatter: a block's stayers land on a nearly
+// contiguous range of slots (its own particles plus the movers other blocks
+// insert between its bins); stayers within SCATTER_WIN slots of the block's
+// first one go through shared memory and are written out in slot order.
+constexpr int SCATTER_THREADS = 256;
+constexpr uint32_t SCATTER_WIN = 1536;
+
+__global__ void __launch_bounds__(SCATTER_THREADS) k_scatter4(Particles A, Particles B,
+                                                              const uint32_t* __restrict__ old_off,
+                                                              const uint32_t* __restrict__ new_off,
+                                                              const uint32_t* __restrict__ stay, uint32_t* in_cnt,
+                                                              const uint32_t* __restrict__ mv,
+                                                              const uint32_t* __restrict__ mvx, uint32_t nbins,
+                                                              DevState* st, KParams P) {
+    __shared__ uint32_t s_key[SCATTER_WIN], s_id[SCATTER_WIN];
+    __shared__ float s_pz[SCATTER_WIN], s_pr[SCATTER_WIN], s_vz[SCATTER_WIN], s_vr[SCATTER_WIN], s_vt[SCATTER_WIN];
+    __shared__ uint32_t s_base;
     const uint32_t n = (uint32_t)st->n_slots;
     const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < nv; g += stride) {
-        const uint4 K = reinterpret_cast<const uint4*>(A.key)[g];
-        const float4 Z = reinterpret_cast<const float4*>(A.pz)[g];
-        const float4 R = reinterpret_cast<const float4*>(A.pr)[g];
-        const float4 VZ = reinterpret_cast<const float4*>(A.vz)[g];
-        const float4 VR = reinterpret_cast<const float4*>(A.vr)[g];
-        const float4 VT = reinterpret_cast<const float4*>(A.vt)[g];
-        const uint4 ID = reinterpret_cast<const uint4*>(A.id)[g];
-        const bool sorted_part = 4u * g < n_sorted;
+    for (uint32_t k = threadIdx.x; k < SCATTER_WIN; k += blockDim.x) s_key[k] = DEAD;
+    if (threadIdx.x == 0) s_base = 0xFFFFFFFFu;
+    __syncthreads();
+    for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < nv; g0 += stride) {
+        const uint32_t g = g0 + threadIdx.x;
+        const bool gv = g < nv;
+        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
+        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
+        if (gv) {
+            K = reinterpret_cast<const uint4*>(A.key)[g];
+            Z = reinterpret_cast<const float4*>(A.pz)[g];
+            R = reinterpret_cast<const float4*>(A.pr)[g];
+            VZ = reinterpret_cast<const float4*>(A.vz)[g];
+            VR = reinterpret_cast<const float4*>(A.vr)[g];
+            VT = reinterpret_cast<const float4*>(A.vt)[g];
+            ID = reinterpret_cast<const uint4*>(A.id)[g];
+        }
+        const bool sorted_part = gv && 4u * g < n_sorted;
         const uint32_t mw = sorted_part ? mv[g >> 3] : 0u;
         const uint32_t mx = sorted_part ? mvx[g >> 3] : 0u;
         uint32_t key[4], bin[4], slot[4];
-        bool live[4], mover[4];
+        bool live[4], mover[4], stays[4];
         bool any_mover = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t i = 4u * g + (uint32_t)q;
-            key[q] = i < n ? lane_of(K, q) : DEAD;
+            key[q] = (gv && i < n) ? lane_of(K, q) : DEAD;
             live[q] = key[q] != DEAD;
             bin[q] = live[q] ? key_species(key[q]) * P.ncell + key_cell(key[q]) : 0u;
             const bool stayer = live[q] && i < n_sorted && !((mw >> (i & 31u)) & 1u);
             mover[q] = live[q] && !stayer;
+            stays[q] = stayer;
             any_mover |= mover[q];
             slot[q] = 0;
             if (stayer) {
@@ -352,6 +374,15 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
                 }
             }
         }
+        // the block's first stayer slot anchors the staging window
+        uint32_t my_min = 0xFFFFFFFFu;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (stays[q] && slot[q] < my_min) my_min = slot[q];
+        my_min = __reduce_min_sync(FULL_MASK, my_min);
+        if ((threadIdx.x & 31) == 0 && my_min != 0xFFFFFFFFu) atomicMin(&s_base, my_min);
+        __syncthreads();
+        const uint32_t base = s_base;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (!live[q]) continue;
@@ -360,14 +391,44 @@ __global__ void __launch_bounds__(256) k_scatter4(Particles A, Particles B, cons
                 continue;
             }
             const uint32_t s = slot[q];
-            B.key[s] = key[q];
-            B.pz[s] = lane_of(Z, q);
-            B.pr[s] = lane_of(R, q);
-            B.vz[s] = lane_of(VZ, q);
-            B.vr[s] = lane_of(VR, q);
-            B.vt[s] = lane_of(VT, q);
-            B.id[s] = lane_of(ID, q);
+            const uint32_t w = s - base;
+            if (stays[q] && w < SCATTER_WIN) {
+                s_key[w] = key[q];
+                s_pz[w] = lane_of(Z, q);
+                s_pr[w] = lane_of(R, q);
+                s_vz[w] = lane_of(VZ, q);
+                s_vr[w] = lane_of(VR, q);
+                s_vt[w] = lane_of(VT, q);
+                s_id[w] = lane_of(ID, q);
+            } else {
+                B.key[s] = key[q];
+                B.pz[s] = lane_of(Z, q);
+                B.pr[s] = lane_of(R, q);
+                B.vz[s] = lane_of(VZ, q);
+                B.vr[s] = lane_of(VR, q);
+                B.vt[s] = lane_of(VT, q);
+                B.id[s] = lane_of(ID, q);
+            }
         }
+        __syncthreads();
+        // write the window out in slot order: consecutive threads, consecutive slots
+        if (base != 0xFFFFFFFFu) {
+            for (uint32_t e = threadIdx.x; e < SCATTER_WIN; e += blockDim.x) {
+                const uint32_t k = s_key[e];
+                if (k == DEAD) continue;
+                const uint32_t s = base + e;
+                B.key[s] = k;
+                B.pz[s] = s_pz[e];
+                B.pr[s] = s_pr[e];
+                B.vz[s] = s_vz[e];
+                B.vr[s] = s_vr[e];
+                B.vt[s] = s_vt[e];
+                B.id[s] = s_id[e];
+                s_key[e] = DEAD;
+            }
+        }
+        if (threadIdx.x == 0) s_base = 0xFFFFFFFFu;
+        __syncthreads();
     }
 }
 
@@ -391,7 +452,7 @@ void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t*
 void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
                     const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
                     DevState* st, const KParams& P, int grid, cudaStream_t s) {
-    k_scatter4<<<grid, 256, 0, s>>>(A, B, old_off, new_off, stay, in_cnt, mv, mvx, nbins, st, P);
+    k_scatter4<<<grid, SCATTER_THREADS, 0, s>>>(A, B, old_off, new_off, stay, in_cnt, mv, mvx, nbins, st, P);
 }
 
 }  // namespace pd
