@@ -52,8 +52,8 @@ def parse():
     p.add_argument("--total", type=float, default=1e8)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-rows", type=int, default=256, help="rows of cells in the CPU-baseline sample")
-    p.add_argument("--cpu-steps", type=int, default=4)
+    p.add_argument("--cpu-rows", type=int, default=512, help="rows of cells in the CPU-baseline sample")
+    p.add_argument("--cpu-steps", type=int, default=10)
     return p.parse_args()
 
 
