@@ -169,8 +169,10 @@ pd_status pd_get_counters(pd_sim* sim, uint64_t* out /* PD_NCOUNTERS */);
 /* Slots in use (live + dead); size for pd_get_particles. */
 pd_status pd_particle_slots(pd_sim* sim, int64_t* slots);
 /* Copy every slot to host arrays of pd_particle_slots() entries; dead slots
- * have species 255.  Order is the device order (cell-sorted, not by id). */
-pd_status pd_get_particles(pd_sim* sim, uint32_t* id, uint8_t* species, int32_t* iz, int32_t* ir,
+ * have species 255 and run -1.  Order is the device order (cell-sorted, not
+ * by id).  `run` (may be NULL) receives the run of each particle; iz, ir are
+ * local to that run. */
+pd_status pd_get_particles(pd_sim* sim, uint32_t* id, int32_t* run, uint8_t* species, int32_t* iz, int32_t* ir,
                            float* pz, float* pr, float* vz, float* vr, float* vt);
 /* Fixed-point node charge (units of e * 2^-32 per super-particle) of the
  * electrons and of the heavies. */
@@ -194,6 +196,51 @@ const char* pd_kernel_name(int kernel_id);
 
 const char* pd_last_error(const pd_sim* sim);
 void pd_destroy(pd_sim* sim);
+
+/* ---------------------------------------------------------------------
+ * Ensembles: several independent breakdown runs (e.g. seeds x gap voltages,
+ * each with its own grid, particle load, weight, circuit and emission)
+ * advanced together.  Every kernel launch of a step covers all runs: their
+ * cells and nodes are laid end to end in one index space (cells of run r
+ * start at its cell_base, nodes at its node_base) and the particle store is
+ * shared.  Each run evolves exactly as the same run would alone (its Philox
+ * key is its own (seed, run) and draws are keyed by its local cells).  The
+ * runs must agree on geometry, dt, heavy_subcycle, field_mode,
+ * coll_dt_scale, di_on and di_split_mode; at most 128 runs and 2^24 cells in
+ * total.  pd_sim functions apply to an ensemble (the single-run getters
+ * report run 0; grids returned by pd_get_rho/phi/field are the runs' grids
+ * end to end).
+ * --------------------------------------------------------------------- */
+typedef struct pd_sim pd_ensemble;
+pd_status pd_ensemble_workspace_size(const pd_config* cfgs, int n_runs, size_t* bytes);
+pd_status pd_ensemble_create(const pd_config* cfgs, int n_runs, void* dev_workspace, size_t bytes,
+                             void* cuda_stream, pd_ensemble** out);
+pd_status pd_ensemble_step(pd_ensemble* ens, int64_t n_steps);
+pd_status pd_ensemble_get_scalars(pd_ensemble* ens, int run, pd_scalars* out);
+pd_status pd_run_count(pd_sim* sim, int* n_runs);
+/* first global cell and node of a run */
+pd_status pd_run_layout(pd_sim* sim, int run, int64_t* cell_base, int64_t* node_base);
+pd_status pd_get_run_counters(pd_sim* sim, int run, uint64_t* out /* PD_NCOUNTERS */);
+pd_status pd_get_run_density_map(pd_sim* sim, int run, int species, double* out);
+pd_status pd_get_run_energy_spectrum(pd_sim* sim, int run, int species, double e_lo_eV, double e_hi_eV,
+                                     int nbins, uint64_t* out);
+/* loads into one run (iz, ir local to the run); see pd_load_particles */
+pd_status pd_load_particles_run(pd_sim* sim, int run, int64_t n, const uint8_t* species, const int32_t* iz,
+                                const int32_t* ir, const float* pz, const float* pr, const float* vz,
+                                const float* vr, const float* vt);
+pd_status pd_load_particles_device_run(pd_sim* sim, int run, int64_t n, const uint8_t* species,
+                                       const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
+                                       const float* vz, const float* vr, const float* vt);
+
+/* CUDA-graph stepping.  When enabled, pd_step captures G steps (G = the heavy
+ * sub-cycle rounded up to an even number) once into a graph and replays it
+ * with one launch per G steps; the step counter that keys the random streams
+ * lives on the device, so replays draw fresh numbers.  The Poisson solve then
+ * runs exactly `poisson_cycles` multigrid cycles per step with no host
+ * synchronisation (runs that reach their tolerance earlier skip the rest);
+ * the achieved residual is reported in pd_scalars.  Steps not aligned to G
+ * run eagerly.  Changing cross sections or emission drops the graph. */
+pd_status pd_set_graph_mode(pd_sim* sim, int enable, int poisson_cycles);
 
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle
  * arrays in device memory, with no allocation of any kind.  The paper has no

@@ -21,7 +21,10 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots",
            "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
            "pd_get_energy_spectrum", "pd_profile_enable", "pd_profile_read", "pd_kernel_name",
-           "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
+           "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "Ensemble", "pd_ensemble_workspace_size",
+           "pd_ensemble_create", "pd_ensemble_step", "pd_ensemble_get_scalars", "pd_run_count", "pd_run_layout",
+           "pd_get_run_counters", "pd_get_run_density_map", "pd_get_run_energy_spectrum", "pd_load_particles_run",
+           "pd_load_particles_device_run", "pd_set_graph_mode", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 28
 PD_NKERNELS = 12
@@ -88,7 +91,19 @@ _SIGS = {
     "pd_get_scalars": (C.c_int, [P, C.POINTER(PdScalars)]),
     "pd_get_counters": (C.c_int, [P, P]),
     "pd_particle_slots": (C.c_int, [P, C.POINTER(C.c_int64)]),
-    "pd_get_particles": (C.c_int, [P, P, P, P, P, P, P, P, P, P]),
+    "pd_get_particles": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
+    "pd_ensemble_workspace_size": (C.c_int, [C.POINTER(PdConfig), C.c_int, C.POINTER(C.c_size_t)]),
+    "pd_ensemble_create": (C.c_int, [C.POINTER(PdConfig), C.c_int, P, C.c_size_t, P, C.POINTER(P)]),
+    "pd_ensemble_step": (C.c_int, [P, C.c_int64]),
+    "pd_ensemble_get_scalars": (C.c_int, [P, C.c_int, C.POINTER(PdScalars)]),
+    "pd_run_count": (C.c_int, [P, C.POINTER(C.c_int)]),
+    "pd_run_layout": (C.c_int, [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "pd_get_run_counters": (C.c_int, [P, C.c_int, P]),
+    "pd_get_run_density_map": (C.c_int, [P, C.c_int, C.c_int, Dp]),
+    "pd_get_run_energy_spectrum": (C.c_int, [P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, P]),
+    "pd_load_particles_run": (C.c_int, [P, C.c_int, C.c_int64, P, P, P, P, P, P, P, P]),
+    "pd_load_particles_device_run": (C.c_int, [P, C.c_int, C.c_int64, P, P, P, P, P, P, P, P]),
+    "pd_set_graph_mode": (C.c_int, [P, C.c_int, C.c_int]),
     "pd_get_rho": (C.c_int, [P, P, P]),
     "pd_get_phi": (C.c_int, [P, Dp]),
     "pd_get_field": (C.c_int, [P, Dp, Dp]),
@@ -243,16 +258,90 @@ def pd_particle_slots(h):
 
 def pd_get_particles(h, live_only=True):
     n = pd_particle_slots(h)
-    out = dict(id=np.zeros(n, np.uint32), species=np.zeros(n, np.uint8), iz=np.zeros(n, np.int32),
-               ir=np.zeros(n, np.int32))
+    out = dict(id=np.zeros(n, np.uint32), run=np.zeros(n, np.int32), species=np.zeros(n, np.uint8),
+               iz=np.zeros(n, np.int32), ir=np.zeros(n, np.int32))
     for k in ("pz", "pr", "vz", "vr", "vt"):
         out[k] = np.zeros(n, np.float32)
-    keys = ("id", "species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
+    keys = ("id", "run", "species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
     _check(h, _lib().pd_get_particles(h, *[_ptr(out[k]) for k in keys]), "pd_get_particles")
     if live_only:
         m = out["species"] != 255
         out = {k: v[m] for k, v in out.items()}
     return out
+
+
+def pd_ensemble_workspace_size(cfgs):
+    arr = (PdConfig * len(cfgs))(*cfgs)
+    n = C.c_size_t(0)
+    _check(None, _lib().pd_ensemble_workspace_size(arr, len(cfgs), C.byref(n)), "pd_ensemble_workspace_size")
+    return n.value
+
+
+def pd_ensemble_create(cfgs, workspace_ptr, nbytes, stream_ptr):
+    arr = (PdConfig * len(cfgs))(*cfgs)
+    h = P()
+    _check(None, _lib().pd_ensemble_create(arr, len(cfgs), P(workspace_ptr), nbytes, P(stream_ptr), C.byref(h)),
+           "pd_ensemble_create")
+    return h
+
+
+def pd_ensemble_step(h, n):
+    _check(h, _lib().pd_ensemble_step(h, int(n)), "pd_ensemble_step")
+
+
+def pd_ensemble_get_scalars(h, run):
+    s = PdScalars()
+    _check(h, _lib().pd_ensemble_get_scalars(h, int(run), C.byref(s)), "pd_ensemble_get_scalars")
+    return s.as_dict()
+
+
+def pd_run_count(h):
+    n = C.c_int(0)
+    _check(h, _lib().pd_run_count(h, C.byref(n)), "pd_run_count")
+    return n.value
+
+
+def pd_run_layout(h, run):
+    a = C.c_int64(0)
+    b = C.c_int64(0)
+    _check(h, _lib().pd_run_layout(h, int(run), C.byref(a), C.byref(b)), "pd_run_layout")
+    return a.value, b.value
+
+
+def pd_get_run_counters(h, run):
+    a = np.zeros(PD_NCOUNTERS, np.uint64)
+    _check(h, _lib().pd_get_run_counters(h, int(run), _ptr(a)), "pd_get_run_counters")
+    return dict(zip(COUNTER_NAMES, (int(x) for x in a)))
+
+
+def pd_get_run_density_map(h, run, species, nodes):
+    a = np.zeros(nodes)
+    _check(h, _lib().pd_get_run_density_map(h, int(run), int(species), _dp(a)), "pd_get_run_density_map")
+    return a
+
+
+def pd_get_run_energy_spectrum(h, run, species, lo, hi, nbins):
+    a = np.zeros(nbins, np.uint64)
+    _check(h, _lib().pd_get_run_energy_spectrum(h, int(run), int(species), float(lo), float(hi), int(nbins),
+                                                 _ptr(a)), "pd_get_run_energy_spectrum")
+    return a
+
+
+def pd_load_particles_run(h, run, parts):
+    n = len(parts["species"])
+    a = [np.ascontiguousarray(parts["species"], np.uint8), np.ascontiguousarray(parts["iz"], np.int32),
+         np.ascontiguousarray(parts["ir"], np.int32)]
+    a += [np.ascontiguousarray(parts[k], np.float32) for k in ("pz", "pr", "vz", "vr", "vt")]
+    _check(h, _lib().pd_load_particles_run(h, int(run), n, *[_ptr(x) for x in a]), "pd_load_particles_run")
+
+
+def pd_load_particles_device_run(h, run, n, ptrs):
+    _check(h, _lib().pd_load_particles_device_run(h, int(run), int(n), *[P(p) for p in ptrs]),
+           "pd_load_particles_device_run")
+
+
+def pd_set_graph_mode(h, enable, poisson_cycles=4):
+    _check(h, _lib().pd_set_graph_mode(h, int(enable), int(poisson_cycles)), "pd_set_graph_mode")
 
 
 def pd_get_rho(h, nodes):
@@ -404,3 +493,66 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Ensemble(Simulation):
+    """Several independent runs advanced together (one launch per kernel for
+    all runs).  `cfg_dicts` is a list of run configurations."""
+
+    def __init__(self, cfg_dicts, xs=None, device="cuda", stream=None):
+        import torch
+        load_library()
+        self.cfg_dicts = [dict(c) for c in cfg_dicts]
+        self.cfg_dict = self.cfg_dicts[0]
+        self.cfgs = [config_from_dict(c) for c in cfg_dicts]
+        self.nbytes = pd_ensemble_workspace_size(self.cfgs)
+        self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.ws.device)
+        self.h = pd_ensemble_create(self.cfgs, self.ws.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        self.R = len(cfg_dicts)
+        self.run_nodes = []
+        for c in cfg_dicts:
+            rz = c["geometry"] == "rz"
+            self.run_nodes.append(((c["nz"] + (1 if rz else 0)), (c["nr"] + (1 if rz else 0))))
+        self.nodes = sum(a * b for a, b in self.run_nodes)
+        self.nzn, self.nrn = self.run_nodes[0]
+        if xs is not None:
+            self.set_cross_sections(xs)
+
+    def load_run(self, run, parts):
+        pd_load_particles_run(self.h, run, parts)
+
+    def load_run_device(self, run, t):
+        keys = ("species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
+        pd_load_particles_device_run(self.h, run, t["species"].numel(), [t[k].data_ptr() for k in keys])
+
+    def run_scalars(self, run):
+        return pd_ensemble_get_scalars(self.h, run)
+
+    def run_counters(self, run):
+        return pd_get_run_counters(self.h, run)
+
+    def run_slice(self, arr, run):
+        """The part of a concatenated node array (rho, phi, field) that belongs to one run."""
+        _, nb = pd_run_layout(self.h, run)
+        a, b = self.run_nodes[run]
+        return np.asarray(arr).ravel()[nb:nb + a * b].reshape(a, b)
+
+    def run_density_map(self, run, species):
+        a, b = self.run_nodes[run]
+        return pd_get_run_density_map(self.h, run, species, a * b).reshape(a, b)
+
+    def run_energy_spectrum(self, run, species, lo=0.0, hi=500.0, nbins=100):
+        return pd_get_run_energy_spectrum(self.h, run, species, lo, hi, nbins)
+
+    def rho(self):
+        return pd_get_rho(self.h, self.nodes)
+
+    def phi(self):
+        return pd_get_phi(self.h, self.nodes)
+
+    def field(self):
+        return pd_get_field(self.h, self.nodes)
+
+    def set_graph_mode(self, enable, poisson_cycles=4):
+        pd_set_graph_mode(self.h, enable, poisson_cycles)

@@ -1,11 +1,19 @@
 // pd_capi.cu -- the C ABI (include/pd.h): workspace layout, constants,
 // step orchestration and diagnostics.  Host code; every pipeline step runs
-// in the kernels of pd_particles.cu, pd_collide.cu and pd_field.cu.
+// in the kernels of pd_stream.cu, pd_particles.cu, pd_collide.cu and
+// pd_field.cu.
+//
+// A simulation holds R >= 1 independent runs (an ensemble).  Their cells and
+// nodes are laid end to end in one global index space, so that each kernel
+// launch advances every run: the sort, scans and candidate machinery see one
+// big set of (species, cell) bins; per-particle kernels look up the run of a
+// cell and take its constants from a small table.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -26,21 +34,27 @@ constexpr double M_CU = 63.546 * AMU;
 constexpr double KB = 1.380649e-23;
 constexpr double PI = 3.14159265358979323846;
 constexpr int ZQ[NSP] = {-1, 0, 1, 2, 2};
+constexpr int MAX_RUNS = MAX_RUNS_SMEM;
 
 double species_mass(int s) { return s == SP_E ? ME : M_CU; }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+size_t run_nodes(const pd_config& c) {
+    return c.geometry == PD_GEOM_RZ ? (size_t)(c.nz + 1) * (c.nr + 1) : (size_t)c.nz * c.nr;
+}
+
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E, phi, xsE, xs, ck, ray, hist,
-        spc, state, field;
+    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E,
+        phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field;
     uint32_t nbins_pad, ncell_pad, words_pad;
+    uint64_t cap, ncell, nodes, ck_len;
     size_t field_bytes;
 };
 
-Layout make_layout(const pd_config& c) {
+Layout make_layout(const std::vector<pd_config>& cf) {
     Layout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -48,10 +62,24 @@ Layout make_layout(const pd_config& c) {
         o = align256(o + bytes);
         return r;
     };
-    const uint64_t cap = ((uint64_t)c.capacity + 3) & ~3ull;   // slot arrays move in groups of four
+    const int R = (int)cf.size();
+    uint64_t cap = 0, ncell = 0, nodes = 0, ckl = 0;
+    std::vector<int> nz(R), nr(R);
+    for (int r = 0; r < R; ++r) {
+        cap += (uint64_t)cf[r].capacity;
+        ncell += (uint64_t)cf[r].nz * cf[r].nr;
+        nodes += run_nodes(cf[r]);
+        ckl += 2ull * cf[r].nr;
+        nz[r] = cf[r].nz;
+        nr[r] = cf[r].nr;
+    }
+    cap = (cap + 3) & ~3ull;   // slot arrays move in groups of four
+    L.cap = cap;
+    L.ncell = ncell;
+    L.nodes = nodes;
+    L.ck_len = ckl;
     for (int k = 0; k < 7; ++k) L.A[k] = take(cap * 4);
     for (int k = 0; k < 7; ++k) L.B[k] = take(cap * 4);
-    const uint64_t ncell = (uint64_t)c.nz * c.nr;
     L.nbins_pad = scan_padded(ncell * NSP);
     L.ncell_pad = scan_padded(ncell);
     L.words_pad = scan_padded(cap / 32 + 1);
@@ -69,7 +97,6 @@ Layout make_layout(const pd_config& c) {
     L.cand = take((size_t)L.ncell_pad * 4);
     L.cand_off = take(((size_t)L.ncell_pad + 1) * 4);
     L.active = take(ncell * 4);
-    const uint64_t nodes = c.geometry == PD_GEOM_RZ ? (uint64_t)(c.nz + 1) * (c.nr + 1) : ncell;
     L.rho_e = take(nodes * 8);
     L.rho_h = take(nodes * 8);
     L.diag = take(nodes * 8);
@@ -77,12 +104,17 @@ Layout make_layout(const pd_config& c) {
     L.phi = take(nodes * 8);
     L.xsE = take(XS_N * 4);
     L.xs = take(NCH * XS_N * 4);
-    L.ck = take(2 * (size_t)c.nr * 4);
+    L.ck = take(ckl * 4);
     L.ray = take(1024 * 4);
     L.hist = take(4096 * 8);
     L.spc = take(NSP * 8);
     L.state = take(sizeof(DevState));
-    L.field_bytes = c.field_mode == PD_FIELD_POISSON ? field_workspace_bytes(c.nz, c.nr) : 0;
+    L.rs = take(R * sizeof(RunState));
+    L.runs = take(R * sizeof(RunInfo));
+    L.cell_run = take(ncell * 2);
+    L.circ = take(R * sizeof(RunCircuit));
+    L.ic = take(R * sizeof(InjectConsts));
+    L.field_bytes = cf[0].field_mode == PD_FIELD_POISSON ? field_workspace_bytes(nz, nr) : 0;
     L.field = take(L.field_bytes);
     L.total = o;
     return L;
@@ -96,7 +128,8 @@ enum { K_INJECT, K_PUSH, K_SCAN_BINS, K_SCATTER, K_NCAND, K_SCAN_CAND, K_COLLIDE
 }  // namespace
 
 struct pd_sim {
-    pd_config cfg;
+    std::vector<pd_config> cfgs;
+    int R;
     Layout L;
     cudaStream_t stream;
     char* ws;
@@ -111,18 +144,32 @@ struct pd_sim {
     float *xsE, *xs, *ck, *ray;
     unsigned long long *hist, *spc;
     DevState* st;
+    RunState* rs;
+    RunInfo* runs_dev;
+    uint16_t* cell_run;
+    RunCircuit* circ_dev;
+    InjectConsts* ic_dev;
+    std::vector<RunInfo> runs;
+    std::vector<uint32_t> node_base;
     FieldSolver field;
     // host copies
     float h_xsE[XS_N];
     float h_xs[NCH][XS_N];
     double eth[NCH];
     CollConsts cc;
-    InjectConsts ic;
+    std::vector<InjectConsts> ic;
     float h_ray[1024];
     int64_t step;
     bool primed;
-    int inject_on;
     std::string err;
+    // CUDA graph of G steps (G = lcm(2, heavy_subcycle))
+    bool graph_on;
+    int graph_cycles;
+    cudaGraphExec_t gexec;
+    int64_t graph_steps;
+    uint64_t graph_launches[PD_NKERNELS];
+    bool any_inject;
+    std::vector<uint16_t> h_cell_run;
     // profiling
     bool prof;
     struct Rec {
@@ -145,9 +192,9 @@ pd_status cuda_fail(pd_sim* s, cudaError_t e, const char* where) {
     return fail(s, PD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define CK(call)                                          \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
     } while (0)
 
@@ -162,13 +209,14 @@ cudaEvent_t take_event(pd_sim* s) {
     return e;
 }
 
+// launch accounting and (when profiling, outside graph capture) CUDA events
 struct Timed {
     pd_sim* s;
     int k;
     cudaEvent_t b;
-    Timed(pd_sim* s_, int k_) : s(s_), k(k_), b(nullptr) {
+    Timed(pd_sim* s_, int k_, bool capturing = false) : s(s_), k(k_), b(nullptr) {
         s->launches[k] += 1;
-        if (s->prof) {
+        if (s->prof && !capturing) {
             cudaEvent_t a = take_event(s);
             b = take_event(s);
             cudaEventRecord(a, s->stream);
@@ -182,37 +230,20 @@ struct Timed {
 
 KParams kparams(const pd_sim* s, int heavy_step) {
     KParams P;
-    const pd_config& c = s->cfg;
+    const pd_config& c = s->cfgs[0];
     P.geom = c.geometry == PD_GEOM_RZ ? 0 : 1;
-    P.nz = c.nz;
-    P.nr = c.nr;
-    P.nzn = P.geom == 0 ? c.nz + 1 : c.nz;
-    P.nrn = P.geom == 0 ? c.nr + 1 : c.nr;
-    P.ncell = (uint32_t)c.nz * (uint32_t)c.nr;
-    P.inv_nr = 1.0f / (float)c.nr;
-    P.seed = c.seed;
-    P.run = c.run;
+    P.nruns = s->R;
+    P.ncell = (uint32_t)s->L.ncell;
     P.step = (uint32_t)s->step;
     P.heavy_step = heavy_step;
     P.field_on = c.field_mode != PD_FIELD_NONE;
     P.use_prev = s->sorted_valid ? 1 : 0;
-    P.capacity = (unsigned long long)c.capacity;
-    P.weight = c.weight;
+    P.capacity = (unsigned long long)s->L.cap;
     for (int k = 0; k < NSP; ++k) P.masses[k] = species_mass(k);
+    P.runs = s->runs_dev;
+    P.cell_run = s->cell_run;
+    P.rs = s->rs;
     return P;
-}
-
-PushConsts push_consts(const pd_config& c) {
-    PushConsts pc;
-    const double dte = c.dt, dth = c.dt * c.heavy_subcycle;
-    for (int sp = 0; sp < NSP; ++sp) {
-        const double dts = sp == SP_E ? dte : dth;
-        pc.qmdt[sp] = (float)((double)ZQ[sp] * QE / species_mass(sp) * dts);
-        pc.dtz[sp] = (float)(dts / c.dz);
-        pc.dtr[sp] = (float)(dts / c.dr);
-        pc.mass_w[sp] = 0.0f;
-    }
-    return pc;
 }
 
 double cell_volume(const pd_config& c, int j) {
@@ -235,8 +266,7 @@ double node_volume(const pd_config& c, int i, int j) {
 
 double mr_class() { return ME * M_CU / (ME + M_CU); }
 
-// NTC majorants from the float tables (see pd_set_cross_section), then the
-// per-row factors c_k(j) = W (sigma g)_max dt_coll / V_cell(j).
+// NTC majorants from the float tables (see pd_set_cross_section)
 void update_collision_consts(pd_sim* s) {
     const double mr = mr_class();
     CollConsts& cc = s->cc;
@@ -244,7 +274,7 @@ void update_collision_consts(pd_sim* s) {
     cc.a_e = (float)(mr / ME);
     cc.a_t = (float)(mr / M_CU);
     for (int ch = 0; ch < NCH; ++ch) cc.kth[ch] = (float)(2.0 * s->eth[ch] * QE / mr);
-    cc.di_split_mode = s->cfg.di_split_mode;
+    cc.di_split_mode = s->cfgs[0].di_split_mode;
     const double kd = (double)cc.kmr;
     const int ch0[2] = {CH_EL, CH_SW}, nch[2] = {4, 1};
     for (int k = 0; k < 2; ++k) {
@@ -268,13 +298,17 @@ void update_collision_consts(pd_sim* s) {
     }
 }
 
+// per-row factors c_k(j) = W (sigma g)_max dt_coll / V_cell(j) of every run
 pd_status upload_ck(pd_sim* s) {
-    const pd_config& c = s->cfg;
-    std::vector<float> ck(2 * (size_t)c.nr);
-    const double dtc = c.dt * c.coll_dt_scale;
-    for (int k = 0; k < 2; ++k)
-        for (int j = 0; j < c.nr; ++j)
-            ck[(size_t)k * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[k] * dtc / cell_volume(c, j));
+    std::vector<float> ck(s->L.ck_len);
+    for (int r = 0; r < s->R; ++r) {
+        const pd_config& c = s->cfgs[r];
+        const double dtc = c.dt * c.coll_dt_scale;
+        const uint32_t base = s->runs[r].ck_base;
+        for (int k = 0; k < 2; ++k)
+            for (int j = 0; j < c.nr; ++j)
+                ck[base + (size_t)k * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[k] * dtc / cell_volume(c, j));
+    }
     CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return PD_OK;
@@ -291,7 +325,7 @@ pd_status check_device_error(pd_sim* s, const DevState& d) {
     if (d.error & ERR_IDS) return fail(s, PD_ERR_CAPACITY, "particle id space exhausted");
     if (d.error & ERR_TIMEOUT) return fail(s, PD_ERR_TIMEOUT, "a bounded device wait ran out");
     if (d.error & ERR_NONFINITE) return fail(s, PD_ERR_NONFINITE, "non-finite value in the field solve");
-    if (d.error & ERR_BOUNDS) return fail(s, PD_ERR_CAPACITY, "spawn exceeded its reserved slots");
+    if (d.error & ERR_BOUNDS) return fail(s, PD_ERR_CAPACITY, "inconsistent slot bookkeeping (reported, not written)");
     return PD_OK;
 }
 
@@ -301,7 +335,13 @@ pd_status sync_check(pd_sim* s, DevState* d) {
     return check_device_error(s, *d);
 }
 
-pd_status validate(const pd_config* c, std::string& msg) {
+pd_status read_run(pd_sim* s, int run, RunState* out) {
+    CK(cudaMemcpyAsync(out, s->rs + run, sizeof(RunState), cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status validate_one(const pd_config* c, std::string& msg) {
     if (!c) { msg = "null config"; return PD_ERR_ARG; }
     if (c->struct_size != sizeof(pd_config) || c->version != PD_CONFIG_VERSION) {
         msg = "pd_config size/version mismatch";
@@ -323,10 +363,33 @@ pd_status validate(const pd_config* c, std::string& msg) {
     return PD_OK;
 }
 
-void setup_injection(pd_sim* s) {
-    const pd_config& c = s->cfg;
-    InjectConsts& ic = s->ic;
+// runs of one simulation share everything that is not per-run geometry,
+// weight, seed, circuit or emission
+pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
+    if (!cfgs || n < 1 || n > MAX_RUNS) { msg = "need 1.." + std::to_string(MAX_RUNS) + " runs"; return PD_ERR_ARG; }
+    uint64_t cells = 0, cap = 0;
+    for (int r = 0; r < n; ++r) {
+        pd_status e = validate_one(&cfgs[r], msg);
+        if (e != PD_OK) return e;
+        const pd_config &a = cfgs[0], &b = cfgs[r];
+        if (b.geometry != a.geometry || b.dt != a.dt || b.heavy_subcycle != a.heavy_subcycle ||
+            b.field_mode != a.field_mode || b.coll_dt_scale != a.coll_dt_scale || b.di_on != a.di_on ||
+            b.di_split_mode != a.di_split_mode) {
+            msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale or double-ionization settings";
+            return PD_ERR_ARG;
+        }
+        cells += (uint64_t)b.nz * b.nr;
+        cap += (uint64_t)b.capacity;
+    }
+    if (cells >= (1u << 24)) { msg = "all runs together must have < 2^24 cells"; return PD_ERR_ARG; }
+    if (cap > 0xFFFFFFF0ull) { msg = "all runs together must have < 2^32 slots"; return PD_ERR_ARG; }
+    return PD_OK;
+}
+
+InjectConsts make_injection(const pd_config& c) {
+    InjectConsts ic;
     std::memset(&ic, 0, sizeof(ic));
+    if (c.geometry != PD_GEOM_RZ || !c.inject_on) return ic;
     const double dr = c.dr, rt = c.tip_radius;
     const float rtip_cells = (float)(rt / dr);
     int n = 0;
@@ -344,92 +407,161 @@ void setup_injection(pd_sim* s) {
     ic.work = c.work_function;
     ic.ratio = c.neutral_ratio;
     ic.vth = (float)std::sqrt(KB * c.neutral_T / M_CU);
-    for (int k = 0; k < 1024; ++k) s->h_ray[k] = (float)std::sqrt(-2.0 * std::log(1.0 - (double)k / 1024.0));
+    return ic;
 }
 
 int grid_for(pd_sim* s, int per_sm) { return s->sms * per_sm; }
 
+size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
+
 pd_status prime(pd_sim* s) {
-    const pd_config& c = s->cfg;
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
     KParams P = kparams(s, 1);
-    CK(cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream));
-    CK(cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream));
+    CK(cudaMemsetAsync(s->rho_e, 0, total_nodes(s) * 8, s->stream));
+    CK(cudaMemsetAsync(s->rho_h, 0, total_nodes(s) * 8, s->stream));
     {
         Timed t(s, K_OTHER);
         launch_deposit(s->A, s->rho_e, s->rho_h, s->st, P, grid_for(s, 8), s->stream);
     }
-    if (c.field_mode == PD_FIELD_POISSON) {
+    if (s->cfgs[0].field_mode == PD_FIELD_POISSON) {
         Timed t(s, K_POISSON);
-        field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->st, s->stream);
+        if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream))
+            return fail(s, PD_ERR_CUDA, "field solve failed");
+        field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->stream);
     }
     CK(cudaGetLastError());
     s->primed = true;
     return PD_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-pd_status pd_config_default(pd_config* c) {
-    if (!c) return PD_ERR_ARG;
-    std::memset(c, 0, sizeof(*c));
-    c->struct_size = sizeof(pd_config);
-    c->version = PD_CONFIG_VERSION;
-    c->geometry = PD_GEOM_RZ;
-    c->nz = 64;
-    c->nr = 64;
-    c->dz = 6e-6 / 64;
-    c->dr = 6e-6 / 64;
-    c->depth = 1.0;
-    c->dt = 1e-15;
-    c->heavy_subcycle = 10;
-    c->weight = 100.0;
-    c->seed = 1;
-    c->run = 0;
-    c->field_mode = PD_FIELD_POISSON;
-    c->inject_on = 1;
-    c->di_on = 1;
-    c->di_split_mode = 0;
-    c->coll_dt_scale = 1.0;
-    c->V0 = 2.9e3;
-    c->R_ohm = 1e3;
-    c->C_farad = 1e-12;
-    c->beta = 35.0;
-    c->tip_radius = 100e-9;
-    c->work_function = 4.5;
-    c->neutral_ratio = 0.03;
-    c->neutral_T = 2000.0;
-    c->poisson_tol = 1e-8;
-    c->poisson_max_cycles = 60;
-    c->capacity = 1 << 16;
+// one electron step, issued on the stream; `capturing` when recorded into a graph
+pd_status issue_step(pd_sim* s, bool capturing) {
+    const pd_config& c = s->cfgs[0];
+    const int heavy = (s->step % c.heavy_subcycle) == 0;
+    const KParams P = kparams(s, heavy);
+    const uint32_t nbins = (uint32_t)s->L.ncell * NSP;
+    const int gpart = grid_for(s, 8);
+    const size_t nodes = total_nodes(s);
+    if (s->any_inject) {
+        Timed t(s, K_INJECT, capturing);
+        launch_inject(s->A, s->E, s->st, P, s->ic_dev, s->ray, s->stream);
+    }
+    {
+        Timed t(s, K_MEMSET, capturing);
+        cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
+        if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
+        // mover bits are OR-ed in by the push: start from zero
+        cudaMemsetAsync(s->mv, 0, (size_t)s->L.words_pad * 4, s->stream);
+    }
+    {
+        Timed t(s, K_PUSH, capturing);
+        launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, gpart,
+                    s->stream);
+    }
+    {
+        Timed t(s, K_SCAN_BINS, capturing);
+        launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev, grid_for(s, 8),
+                        s->stream);
+        launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
+        if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
+    }
+    {
+        Timed t(s, K_SCATTER, capturing);
+        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P, gpart,
+                       s->stream);
+    }
+    std::swap(s->A, s->B);
+    std::swap(s->off, s->off2);
+    s->sorted_valid = true;
+    {
+        Timed t(s, K_NCAND, capturing);
+        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, 8), s->stream);
+    }
+    {
+        Timed t(s, K_SCAN_CAND, capturing);
+        launch_scan(s->cand, s->cand_off, s->partial, s->L.ncell_pad, s->stream);
+    }
+    {
+        Timed t(s, K_COLLIDE, capturing);
+        launch_collide(s->A, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P, s->cc,
+                       nbins, grid_for(s, 16), s->stream);
+    }
+    {
+        Timed t(s, K_FINALIZE, capturing);
+        launch_finalize(s->off, nbins, s->cand_off, s->st, P, s->circ_dev, c.dt, c.geometry == PD_GEOM_RZ, s->stream);
+    }
+    if (c.field_mode == PD_FIELD_POISSON) {
+        {
+            Timed t(s, K_POISSON, capturing);
+            const bool host_check = !capturing && !s->graph_on;
+            if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, host_check ? 1 : 0,
+                            s->graph_cycles, s->stream))
+                return fail(s, PD_ERR_CUDA, "field solve failed");
+        }
+        {
+            Timed t(s, K_EFIELD, capturing);
+            field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->stream);
+        }
+    }
+    s->step += 1;
     return PD_OK;
 }
 
-pd_status pd_workspace_size(const pd_config* c, size_t* bytes) {
-    std::string msg;
-    pd_status r = validate(c, msg);
+int graph_period(const pd_sim* s) {
+    const int h = s->cfgs[0].heavy_subcycle;
+    return (h % 2 == 0) ? h : 2 * h;   // whole heavy cycles, even (buffers swap every step)
+}
+
+pd_status drop_graph(pd_sim* s) {
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return PD_OK;
+}
+
+// capture G steps into one executable graph (the first step of the capture
+// must be a multiple of G and the sorted order must already exist)
+pd_status build_graph(pd_sim* s) {
+    drop_graph(s);
+    const int G = graph_period(s);
+    cudaGraph_t g = nullptr;
+    uint64_t before[PD_NKERNELS];
+    std::memcpy(before, s->launches, sizeof(before));
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t step0 = s->step;
+    pd_status r = PD_OK;
+    for (int k = 0; k < G && r == PD_OK; ++k) r = issue_step(s, true);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    s->step = step0;           // capture only recorded the steps
+    for (int k = 0; k < PD_NKERNELS; ++k) {   // launches of one replay
+        s->graph_launches[k] = s->launches[k] - before[k];
+        s->launches[k] = before[k];
+    }
     if (r != PD_OK) return r;
-    if (!bytes) return PD_ERR_ARG;
-    *bytes = make_layout(*c).total;
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGraphInstantiate");
+    s->graph_steps = G;
     return PD_OK;
 }
 
-pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd_sim** out) {
+pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, void* stream, pd_sim** out) {
     if (!out) return PD_ERR_ARG;
     *out = nullptr;
     std::string msg;
-    pd_status r = validate(c, msg);
-    if (r != PD_OK) {
+    pd_status v = validate(cfgs, n, msg);
+    if (v != PD_OK) {
         std::fprintf(stderr, "pd_create: %s\n", msg.c_str());
-        return r;
+        return v;
     }
-    Layout L = make_layout(*c);
+    std::vector<pd_config> cf(cfgs, cfgs + n);
+    Layout L = make_layout(cf);
     if (!ws || bytes < L.total || ((uintptr_t)ws & 255)) return PD_ERR_ARG;
     pd_sim* s = new (std::nothrow) pd_sim();
     if (!s) return PD_ERR_ARG;
-    s->cfg = *c;
+    s->cfgs = cf;
+    s->R = n;
     s->L = L;
     s->stream = (cudaStream_t)stream;
     s->ws = (char*)ws;
@@ -471,6 +603,11 @@ pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd
     s->hist = (unsigned long long*)(w + L.hist);
     s->spc = (unsigned long long*)(w + L.spc);
     s->st = (DevState*)(w + L.state);
+    s->rs = (RunState*)(w + L.rs);
+    s->runs_dev = (RunInfo*)(w + L.runs);
+    s->cell_run = (uint16_t*)(w + L.cell_run);
+    s->circ_dev = (RunCircuit*)(w + L.circ);
+    s->ic_dev = (InjectConsts*)(w + L.ic);
     for (int k = 0; k < XS_N; ++k) {
         const int ex = XS_EMIN_EXP + k / XS_SUB, j = k % XS_SUB;
         s->h_xsE[k] = (float)std::ldexp(1.0 + (double)j / XS_SUB, ex);
@@ -478,35 +615,90 @@ pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd
     std::memset(s->h_xs, 0, sizeof(s->h_xs));
     for (int k = 0; k < NCH; ++k) s->eth[k] = 0.0;
     update_collision_consts(s);
-    setup_injection(s);
-    s->inject_on = c->inject_on && c->geometry == PD_GEOM_RZ;
+    for (int k = 0; k < 1024; ++k) s->h_ray[k] = (float)std::sqrt(-2.0 * std::log(1.0 - (double)k / 1024.0));
+    // run tables
+    s->runs.resize(n);
+    s->node_base.resize(n);
+    std::vector<RunCircuit> circ(n);
+    std::vector<uint16_t> cell_run(L.ncell);
+    std::vector<RunState> rs(n);
+    s->ic.resize(n);
+    uint32_t cb = 0, nb = 0, kb = 0;
+    for (int r = 0; r < n; ++r) {
+        const pd_config& c = cf[r];
+        RunInfo& RI = s->runs[r];
+        std::memset(&RI, 0, sizeof(RI));
+        RI.nz = c.nz;
+        RI.nr = c.nr;
+        RI.nzn = c.geometry == PD_GEOM_RZ ? c.nz + 1 : c.nz;
+        RI.nrn = c.geometry == PD_GEOM_RZ ? c.nr + 1 : c.nr;
+        RI.inv_nr = 1.0f / (float)c.nr;
+        RI.cell_base = cb;
+        RI.node_base = nb;
+        RI.ncell = (uint32_t)c.nz * (uint32_t)c.nr;
+        RI.seed = c.seed;
+        RI.run = c.run;
+        RI.ck_base = kb;
+        const double dte = c.dt, dth = c.dt * c.heavy_subcycle;
+        for (int sp = 0; sp < NSP; ++sp) {
+            const double dts = sp == SP_E ? dte : dth;
+            RI.qmdt[sp] = (float)((double)ZQ[sp] * QE / species_mass(sp) * dts);
+            RI.dtz[sp] = (float)(dts / c.dz);
+            RI.dtr[sp] = (float)(dts / c.dr);
+        }
+        RI.weight = c.weight;
+        for (uint32_t q = 0; q < RI.ncell; ++q) cell_run[cb + q] = (uint16_t)r;
+        s->node_base[r] = nb;
+        cb += RI.ncell;
+        nb += (uint32_t)run_nodes(c);
+        kb += 2u * (uint32_t)c.nr;
+        circ[r] = RunCircuit{c.V0, c.R_ohm, c.C_farad};
+        std::memset(&rs[r], 0, sizeof(RunState));
+        rs[r].V = c.V0;
+        s->ic[r] = make_injection(c);
+    }
+    s->any_inject = false;
+    for (int r = 0; r < n; ++r) s->any_inject = s->any_inject || s->ic[r].ntip > 0;
+    s->h_cell_run = cell_run;
+    std::memset(s->graph_launches, 0, sizeof(s->graph_launches));
     s->step = 0;
     s->primed = false;
     s->prof = false;
+    s->graph_on = false;
+    s->graph_cycles = 4;
+    s->gexec = nullptr;
+    s->graph_steps = 0;
     std::memset(s->launches, 0, sizeof(s->launches));
     // zero everything but the two particle buffers
     const size_t z0 = L.count;
     e = cudaMemsetAsync(w + z0, 0, L.total - z0, s->stream);
-    DevState d;
-    std::memset(&d, 0, sizeof(d));
-    d.V = c->V0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->st, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->xsE, s->h_xsE, sizeof(s->h_xsE), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->ray, s->h_ray, sizeof(s->h_ray), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->runs_dev, s->runs.data(), n * sizeof(RunInfo), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->cell_run, cell_run.data(), cell_run.size() * 2, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->circ_dev, circ.data(), n * sizeof(RunCircuit), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->rs, rs.data(), n * sizeof(RunState), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ic_dev, s->ic.data(), n * sizeof(InjectConsts), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         std::fprintf(stderr, "pd_create: %s\n", cudaGetErrorString(e));
         delete s;
         return PD_ERR_CUDA;
     }
-    if (c->field_mode == PD_FIELD_POISSON) {
-        if (field_init(s->field, *c, w + L.field, L.field_bytes, s->stream) != 0) {
+    if (cf[0].field_mode == PD_FIELD_POISSON) {
+        if (field_init(s->field, cf, s->node_base, s->phi, w + L.field, L.field_bytes, s->stream) != 0) {
+            field_free(s->field);
             delete s;
             return PD_ERR_CUDA;
         }
     }
     pd_status ur = upload_ck(s);
     if (ur != PD_OK) {
+        field_free(s->field);
         delete s;
         return ur;
     }
@@ -514,49 +706,28 @@ pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd
     return PD_OK;
 }
 
-pd_status pd_set_cross_section(pd_sim* s, int ch, const double* E, const double* sig, int n, double threshold) {
+pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                    const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
-    if (ch < 0 || ch >= NCH || n < 2 || !E || !sig) return fail(s, PD_ERR_ARG, "bad cross-section arguments");
-    for (int a = 0; a + 1 < n; ++a)
-        if (!(E[a + 1] > E[a])) return fail(s, PD_ERR_ARG, "cross-section energies must ascend");
-    for (int k = 0; k < XS_N; ++k) {
-        const double e = (double)s->h_xsE[k];
-        double v;
-        if (e <= E[0]) v = sig[0];
-        else if (e >= E[n - 1]) v = sig[n - 1];
-        else {
-            int a = 0;
-            while (E[a + 1] <= e) ++a;
-            const double t = (e - E[a]) / (E[a + 1] - E[a]);
-            v = sig[a] + t * (sig[a + 1] - sig[a]);
-        }
-        if (e < threshold) v = 0.0;
-        if (ch == CH_DI && !s->cfg.di_on) v = 0.0;
-        s->h_xs[ch][k] = (float)v;
-    }
-    s->eth[ch] = threshold;
-    update_collision_consts(s);
-    CK(cudaMemcpyAsync(s->xs + (size_t)ch * XS_N, s->h_xs[ch], XS_N * 4, cudaMemcpyHostToDevice, s->stream));
-    return upload_ck(s);
-}
-
-pd_status pd_load_particles(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
-                            const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
-    if (!s) return PD_ERR_ARG;
+    if (run < 0 || run >= s->R) return fail(s, PD_ERR_ARG, "bad run index");
     if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
     if (n == 0) return PD_OK;
     DevState d;
     pd_status r = sync_check(s, &d);
     if (r != PD_OK) return r;
-    if (d.n_slots + (uint64_t)n > (uint64_t)s->cfg.capacity) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
-    if ((uint64_t)d.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    RunState rs;
+    r = read_run(s, run, &rs);
+    if (r != PD_OK) return r;
+    if (d.n_slots + (uint64_t)n > s->L.cap) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if ((uint64_t)rs.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    const RunInfo& RI = s->runs[run];
     std::vector<uint32_t> key(n), id(n);
     for (int64_t q = 0; q < n; ++q) {
-        if (sp[q] >= NSP || iz[q] < 0 || iz[q] >= s->cfg.nz || ir[q] < 0 || ir[q] >= s->cfg.nr ||
+        if (sp[q] >= NSP || iz[q] < 0 || iz[q] >= RI.nz || ir[q] < 0 || ir[q] >= RI.nr ||
             !(pz[q] >= 0.0f && pz[q] < 1.0f) || !(pr[q] >= 0.0f && pr[q] < 1.0f))
             return fail(s, PD_ERR_ARG, "particle " + std::to_string(q) + " out of range");
-        key[q] = ((uint32_t)sp[q] << 24) | ((uint32_t)iz[q] * (uint32_t)s->cfg.nr + (uint32_t)ir[q]);
-        id[q] = d.id_next + (uint32_t)q;
+        key[q] = ((uint32_t)sp[q] << 24) | (RI.cell_base + (uint32_t)iz[q] * (uint32_t)RI.nr + (uint32_t)ir[q]);
+        id[q] = rs.id_next + (uint32_t)q;
     }
     const size_t o = d.n_slots;
     CK(cudaMemcpyAsync(s->A.key + o, key.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
@@ -567,30 +738,34 @@ pd_status pd_load_particles(pd_sim* s, int64_t n, const uint8_t* sp, const int32
     CK(cudaMemcpyAsync(s->A.vt + o, vt, n * 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->A.id + o, id.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
     d.n_slots += (uint64_t)n;
-    d.id_next += (uint32_t)n;
+    rs.id_next += (uint32_t)n;
     CK(cudaMemcpyAsync(&s->st->n_slots, &d.n_slots, 8, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(&s->st->id_next, &d.id_next, 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->rs[run].id_next, &rs.id_next, 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->primed = false;
     return PD_OK;
 }
 
-pd_status pd_load_particles_device(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
-                                   const float* pz, const float* pr, const float* vz, const float* vr,
-                                   const float* vt) {
+pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                      const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
+    if (run < 0 || run >= s->R) return fail(s, PD_ERR_ARG, "bad run index");
     if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
     if (n == 0) return PD_OK;
     DevState d;
     pd_status r = sync_check(s, &d);
     if (r != PD_OK) return r;
-    if (d.n_slots + (uint64_t)n > (uint64_t)s->cfg.capacity) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
-    if ((uint64_t)d.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    RunState rs;
+    r = read_run(s, run, &rs);
+    if (r != PD_OK) return r;
+    if (d.n_slots + (uint64_t)n > s->L.cap) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if ((uint64_t)rs.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
+    const RunInfo& RI = s->runs[run];
     const size_t o = d.n_slots;
     unsigned int bad = 0;
     unsigned int* dbad = &s->st->load_bad;
     CK(cudaMemsetAsync(dbad, 0, 4, s->stream));
-    launch_pack_keys(sp, iz, ir, pz, pr, n, s->cfg.nz, s->cfg.nr, d.id_next, s->A.key + o, s->A.id + o, dbad,
+    launch_pack_keys(sp, iz, ir, pz, pr, n, RI.nz, RI.nr, RI.cell_base, rs.id_next, s->A.key + o, s->A.id + o, dbad,
                      grid_for(s, 8), s->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(s->A.pz + o, pz, n * 4, cudaMemcpyDeviceToDevice, s->stream));
@@ -602,125 +777,25 @@ pd_status pd_load_particles_device(pd_sim* s, int64_t n, const uint8_t* sp, cons
     CK(cudaStreamSynchronize(s->stream));
     if (bad) return fail(s, PD_ERR_ARG, "a device particle is out of range");
     d.n_slots += (uint64_t)n;
-    d.id_next += (uint32_t)n;
+    rs.id_next += (uint32_t)n;
     CK(cudaMemcpyAsync(&s->st->n_slots, &d.n_slots, 8, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(&s->st->id_next, &d.id_next, 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->rs[run].id_next, &rs.id_next, 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->primed = false;
     return PD_OK;
 }
 
-pd_status pd_set_field(pd_sim* s, const double* Ez, const double* Er) {
-    if (!s || !Ez || !Er) return PD_ERR_ARG;
-    const pd_config& c = s->cfg;
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
-    std::vector<float2> h(nodes);
-    for (size_t k = 0; k < nodes; ++k) h[k] = make_float2((float)Ez[k], (float)Er[k]);
-    CK(cudaMemcpyAsync(s->E, h.data(), nodes * 8, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
-    return PD_OK;
-}
-
-pd_status pd_inject_cathode(pd_sim* s, int enable) {
-    if (!s) return PD_ERR_ARG;
-    if (enable && s->cfg.geometry != PD_GEOM_RZ) return fail(s, PD_ERR_ARG, "injection needs r-z");
-    s->inject_on = enable ? 1 : 0;
-    return PD_OK;
-}
-
-pd_status pd_step(pd_sim* s, int64_t n_steps) {
-    if (!s) return PD_ERR_ARG;
-    if (n_steps < 0) return fail(s, PD_ERR_ARG, "n_steps < 0");
-    const pd_config& c = s->cfg;
-    if (!s->primed) {
-        pd_status r = prime(s);
-        if (r != PD_OK) return r;
-    }
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
-    const PushConsts pc = push_consts(c);
-    const uint32_t ncell = (uint32_t)c.nz * (uint32_t)c.nr;
-    const uint32_t nbins = ncell * NSP;
-    const int gpart = grid_for(s, 8);
-    for (int64_t it = 0; it < n_steps; ++it) {
-        const int heavy = (s->step % c.heavy_subcycle) == 0;
-        const KParams P = kparams(s, heavy);
-        if (s->inject_on) {
-            Timed t(s, K_INJECT);
-            launch_inject(s->A, s->E, s->st, P, s->ic, s->ray, s->stream);
-        }
-        {
-            Timed t(s, K_MEMSET);
-            cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
-            if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
-            // mover bits are OR-ed in by the push: start from zero
-            const size_t words = (size_t)(std::min<int64_t>(c.capacity, 0xFFFFFFFFll) + 127) / 32;
-            cudaMemsetAsync(s->mv, 0, std::min<size_t>(words, s->L.words_pad) * 4, s->stream);
-        }
-        {
-            Timed t(s, K_PUSH);
-            launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, pc,
-                        gpart, s->stream);
-        }
-        {
-            Timed t(s, K_SCAN_BINS);
-            launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
-                            grid_for(s, 8), s->stream);
-            launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
-            if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
-        }
-        {
-            Timed t(s, K_SCATTER);
-            launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P, gpart,
-                           s->stream);
-        }
-        std::swap(s->A, s->B);
-        std::swap(s->off, s->off2);
-        s->sorted_valid = true;
-        {
-            Timed t(s, K_NCAND);
-            launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, 8), s->stream);
-        }
-        {
-            Timed t(s, K_SCAN_CAND);
-            launch_scan(s->cand, s->cand_off, s->partial, s->L.ncell_pad, s->stream);
-        }
-        {
-            Timed t(s, K_COLLIDE);
-            launch_collide(s->A, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P,
-                           s->cc, nbins, grid_for(s, 16), s->stream);
-        }
-        {
-            Timed t(s, K_FINALIZE);
-            launch_finalize(s->off, nbins, s->cand_off, ncell, s->st, P, c.dt, c.V0, c.R_ohm, c.C_farad,
-                            c.geometry == PD_GEOM_RZ, s->stream);
-        }
-        if (c.field_mode == PD_FIELD_POISSON) {
-            Timed t(s, K_POISSON);
-            field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->st, s->stream);
-        }
-        s->step += 1;
-    }
-    CK(cudaGetLastError());
-    return PD_OK;
-}
-
-pd_status pd_synchronize(pd_sim* s) {
-    if (!s) return PD_ERR_ARG;
-    DevState d;
-    return sync_check(s, &d);
-}
-
-pd_status pd_get_scalars(pd_sim* s, pd_scalars* out) {
-    if (!s || !out) return PD_ERR_ARG;
+pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
+    if (!s || !out || run < 0 || run >= s->R) return PD_ERR_ARG;
     CK(cudaMemsetAsync(s->spc, 0, NSP * 8, s->stream));
-    launch_species_count(s->A, s->st, s->spc, grid_for(s, 4), s->stream);
+    launch_species_count(s->A, s->st, kparams(s, 1), run, s->spc, grid_for(s, 4), s->stream);
     unsigned long long cnt[NSP];
     CK(cudaMemcpyAsync(cnt, s->spc, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
-    DevState d;
-    pd_status r = sync_check(s, &d);
+    RunState d;
+    pd_status r = read_run(s, run, &d);
     if (r != PD_OK) return r;
     std::memset(out, 0, sizeof(*out));
-    const pd_config& c = s->cfg;
+    const pd_config& c = s->cfgs[run];
     out->t = (double)s->step * c.dt;
     out->V = d.V;
     out->I_gap = d.I_gap;
@@ -748,14 +823,244 @@ pd_status pd_get_scalars(pd_sim* s, pd_scalars* out) {
     return PD_OK;
 }
 
-pd_status pd_get_counters(pd_sim* s, uint64_t* out) {
-    if (!s || !out) return PD_ERR_ARG;
+pd_status run_density(pd_sim* s, int run, int species, double* out) {
+    if (!s || !out || species < 0 || species >= NSP || run < 0 || run >= s->R) return PD_ERR_ARG;
+    const pd_config& c = s->cfgs[run];
+    const RunInfo& RI = s->runs[run];
+    const size_t nodes = total_nodes(s);
+    CK(cudaMemsetAsync(s->diag, 0, nodes * 8, s->stream));
+    launch_density(s->A, s->st, kparams(s, 1), run, species, s->diag, grid_for(s, 8), s->stream);
+    const size_t rn = run_nodes(c);
+    std::vector<long long> h(rn);
+    CK(cudaMemcpyAsync(h.data(), s->diag + RI.node_base, rn * 8, cudaMemcpyDeviceToHost, s->stream));
     DevState d;
     pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    for (int i = 0; i < RI.nzn; ++i)
+        for (int j = 0; j < RI.nrn; ++j) {
+            const size_t k = (size_t)i * RI.nrn + j;
+            out[k] = c.weight * (double)h[k] / 4294967296.0 / node_volume(c, i, j);
+        }
+    return PD_OK;
+}
+
+pd_status run_spectrum(pd_sim* s, int run, int species, double lo, double hi, int nbins, uint64_t* out) {
+    if (!s || !out || species < 0 || species >= NSP || nbins < 1 || nbins > 4096 || !(hi > lo) || run < 0 ||
+        run >= s->R)
+        return PD_ERR_ARG;
+    CK(cudaMemsetAsync(s->hist, 0, (size_t)nbins * 8, s->stream));
+    launch_spectrum(s->A, s->st, kparams(s, 1), run, species, lo, hi, nbins, s->hist, grid_for(s, 8), s->stream);
+    CK(cudaMemcpyAsync(out, s->hist, (size_t)nbins * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    return sync_check(s, &d);
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_config_default(pd_config* c) {
+    if (!c) return PD_ERR_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->struct_size = sizeof(pd_config);
+    c->version = PD_CONFIG_VERSION;
+    c->geometry = PD_GEOM_RZ;
+    c->nz = 64;
+    c->nr = 64;
+    c->dz = 6e-6 / 64;
+    c->dr = 6e-6 / 64;
+    c->depth = 1.0;
+    c->dt = 1e-15;
+    c->heavy_subcycle = 10;
+    c->weight = 100.0;
+    c->seed = 1;
+    c->run = 0;
+    c->field_mode = PD_FIELD_POISSON;
+    c->inject_on = 1;
+    c->di_on = 1;
+    c->di_split_mode = 0;
+    c->coll_dt_scale = 1.0;
+    c->V0 = 2.9e3;
+    c->R_ohm = 1e3;
+    c->C_farad = 1e-12;
+    c->beta = 35.0;
+    c->tip_radius = 100e-9;
+    c->work_function = 4.5;
+    c->neutral_ratio = 0.03;
+    c->neutral_T = 2000.0;
+    c->poisson_tol = 1e-8;
+    c->poisson_max_cycles = 60;
+    c->capacity = 1 << 16;
+    return PD_OK;
+}
+
+pd_status pd_ensemble_workspace_size(const pd_config* cfgs, int n, size_t* bytes) {
+    std::string msg;
+    pd_status r = validate(cfgs, n, msg);
+    if (r != PD_OK) return r;
+    if (!bytes) return PD_ERR_ARG;
+    *bytes = make_layout(std::vector<pd_config>(cfgs, cfgs + n)).total;
+    return PD_OK;
+}
+
+pd_status pd_workspace_size(const pd_config* c, size_t* bytes) { return pd_ensemble_workspace_size(c, 1, bytes); }
+
+pd_status pd_ensemble_create(const pd_config* cfgs, int n, void* ws, size_t bytes, void* stream, pd_ensemble** out) {
+    return create_common(cfgs, n, ws, bytes, stream, out);
+}
+
+pd_status pd_create(const pd_config* c, void* ws, size_t bytes, void* stream, pd_sim** out) {
+    return create_common(c, 1, ws, bytes, stream, out);
+}
+
+pd_status pd_run_count(pd_sim* s, int* n) {
+    if (!s || !n) return PD_ERR_ARG;
+    *n = s->R;
+    return PD_OK;
+}
+
+pd_status pd_run_layout(pd_sim* s, int run, int64_t* cell_base, int64_t* node_base) {
+    if (!s || run < 0 || run >= s->R) return PD_ERR_ARG;
+    if (cell_base) *cell_base = s->runs[run].cell_base;
+    if (node_base) *node_base = s->runs[run].node_base;
+    return PD_OK;
+}
+
+pd_status pd_set_cross_section(pd_sim* s, int ch, const double* E, const double* sig, int n, double threshold) {
+    if (!s) return PD_ERR_ARG;
+    if (ch < 0 || ch >= NCH || n < 2 || !E || !sig) return fail(s, PD_ERR_ARG, "bad cross-section arguments");
+    for (int a = 0; a + 1 < n; ++a)
+        if (!(E[a + 1] > E[a])) return fail(s, PD_ERR_ARG, "cross-section energies must ascend");
+    for (int k = 0; k < XS_N; ++k) {
+        const double e = (double)s->h_xsE[k];
+        double v;
+        if (e <= E[0]) v = sig[0];
+        else if (e >= E[n - 1]) v = sig[n - 1];
+        else {
+            int a = 0;
+            while (E[a + 1] <= e) ++a;
+            const double t = (e - E[a]) / (E[a + 1] - E[a]);
+            v = sig[a] + t * (sig[a + 1] - sig[a]);
+        }
+        if (e < threshold) v = 0.0;
+        if (ch == CH_DI && !s->cfgs[0].di_on) v = 0.0;
+        s->h_xs[ch][k] = (float)v;
+    }
+    s->eth[ch] = threshold;
+    update_collision_consts(s);
+    drop_graph(s);
+    CK(cudaMemcpyAsync(s->xs + (size_t)ch * XS_N, s->h_xs[ch], XS_N * 4, cudaMemcpyHostToDevice, s->stream));
+    return upload_ck(s);
+}
+
+pd_status pd_load_particles(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                            const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
+    return load_host(s, 0, n, sp, iz, ir, pz, pr, vz, vr, vt);
+}
+
+pd_status pd_load_particles_run(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz,
+                                const int32_t* ir, const float* pz, const float* pr, const float* vz, const float* vr,
+                                const float* vt) {
+    return load_host(s, run, n, sp, iz, ir, pz, pr, vz, vr, vt);
+}
+
+pd_status pd_load_particles_device(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                                   const float* pz, const float* pr, const float* vz, const float* vr,
+                                   const float* vt) {
+    return load_device(s, 0, n, sp, iz, ir, pz, pr, vz, vr, vt);
+}
+
+pd_status pd_load_particles_device_run(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz,
+                                       const int32_t* ir, const float* pz, const float* pr, const float* vz,
+                                       const float* vr, const float* vt) {
+    return load_device(s, run, n, sp, iz, ir, pz, pr, vz, vr, vt);
+}
+
+pd_status pd_set_field(pd_sim* s, const double* Ez, const double* Er) {
+    if (!s || !Ez || !Er) return PD_ERR_ARG;
+    const size_t nodes = total_nodes(s);
+    std::vector<float2> h(nodes);
+    for (size_t k = 0; k < nodes; ++k) h[k] = make_float2((float)Ez[k], (float)Er[k]);
+    CK(cudaMemcpyAsync(s->E, h.data(), nodes * 8, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
+pd_status pd_inject_cathode(pd_sim* s, int enable) {
+    if (!s) return PD_ERR_ARG;
+    if (enable && s->cfgs[0].geometry != PD_GEOM_RZ) return fail(s, PD_ERR_ARG, "injection needs r-z");
+    for (int r = 0; r < s->R; ++r) {
+        pd_config c = s->cfgs[r];
+        c.inject_on = enable ? 1 : 0;
+        s->ic[r] = make_injection(c);
+    }
+    s->any_inject = false;
+    for (int r = 0; r < s->R; ++r) s->any_inject = s->any_inject || s->ic[r].ntip > 0;
+    drop_graph(s);
+    CK(cudaMemcpyAsync(s->ic_dev, s->ic.data(), s->R * sizeof(InjectConsts), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
+pd_status pd_set_graph_mode(pd_sim* s, int enable, int poisson_cycles) {
+    if (!s || poisson_cycles < 0) return PD_ERR_ARG;
+    drop_graph(s);
+    s->graph_on = enable != 0;
+    s->graph_cycles = poisson_cycles > 0 ? poisson_cycles : 4;
+    return PD_OK;
+}
+
+pd_status pd_step(pd_sim* s, int64_t n_steps) {
+    if (!s) return PD_ERR_ARG;
+    if (n_steps < 0) return fail(s, PD_ERR_ARG, "n_steps < 0");
+    if (!s->primed) {
+        drop_graph(s);
+        pd_status r = prime(s);
+        if (r != PD_OK) return r;
+    }
+    int64_t left = n_steps;
+    while (left > 0) {
+        const int G = graph_period(s);
+        if (s->graph_on && s->sorted_valid && s->step % G == 0 && left >= G) {
+            if (!s->gexec) {
+                pd_status r = build_graph(s);
+                if (r != PD_OK) return r;
+            }
+            CK(cudaGraphLaunch(s->gexec, s->stream));
+            for (int k = 0; k < PD_NKERNELS; ++k) s->launches[k] += s->graph_launches[k];
+            s->step += G;
+            left -= G;
+            continue;
+        }
+        pd_status r = issue_step(s, false);
+        if (r != PD_OK) return r;
+        --left;
+    }
+    CK(cudaGetLastError());
+    return PD_OK;
+}
+
+pd_status pd_ensemble_step(pd_ensemble* s, int64_t n_steps) { return pd_step(s, n_steps); }
+
+pd_status pd_synchronize(pd_sim* s) {
+    if (!s) return PD_ERR_ARG;
+    DevState d;
+    return sync_check(s, &d);
+}
+
+pd_status pd_get_scalars(pd_sim* s, pd_scalars* out) { return run_scalars(s, 0, out); }
+pd_status pd_ensemble_get_scalars(pd_ensemble* s, int run, pd_scalars* out) { return run_scalars(s, run, out); }
+
+pd_status pd_get_run_counters(pd_sim* s, int run, uint64_t* out) {
+    if (!s || !out || run < 0 || run >= s->R) return PD_ERR_ARG;
+    RunState d;
+    pd_status r = read_run(s, run, &d);
     if (r != PD_OK) return r;
     for (int k = 0; k < NCOUNTERS; ++k) out[k] = d.ctr[k];
     return PD_OK;
 }
+
+pd_status pd_get_counters(pd_sim* s, uint64_t* out) { return pd_get_run_counters(s, 0, out); }
 
 pd_status pd_particle_slots(pd_sim* s, int64_t* slots) {
     if (!s || !slots) return PD_ERR_ARG;
@@ -766,8 +1071,8 @@ pd_status pd_particle_slots(pd_sim* s, int64_t* slots) {
     return PD_OK;
 }
 
-pd_status pd_get_particles(pd_sim* s, uint32_t* id, uint8_t* sp, int32_t* iz, int32_t* ir, float* pz, float* pr,
-                           float* vz, float* vr, float* vt) {
+pd_status pd_get_particles(pd_sim* s, uint32_t* id, int32_t* run, uint8_t* sp, int32_t* iz, int32_t* ir, float* pz,
+                           float* pr, float* vz, float* vr, float* vt) {
     if (!s) return PD_ERR_ARG;
     DevState d;
     pd_status r = sync_check(s, &d);
@@ -775,6 +1080,7 @@ pd_status pd_get_particles(pd_sim* s, uint32_t* id, uint8_t* sp, int32_t* iz, in
     const size_t n = d.n_slots;
     if (n == 0) return PD_OK;
     std::vector<uint32_t> key(n);
+    std::vector<uint16_t> cell_run;
     CK(cudaMemcpyAsync(key.data(), s->A.key, n * 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(id, s->A.id, n * 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(pz, s->A.pz, n * 4, cudaMemcpyDeviceToHost, s->stream));
@@ -788,20 +1094,24 @@ pd_status pd_get_particles(pd_sim* s, uint32_t* id, uint8_t* sp, int32_t* iz, in
             sp[q] = 255;
             iz[q] = -1;
             ir[q] = -1;
+            if (run) run[q] = -1;
             continue;
         }
-        const uint32_t cell = key[q] & 0xFFFFFFu;
+        const uint32_t g = key[q] & 0xFFFFFFu;
+        const int rr = s->h_cell_run[g];
+        const RunInfo& RI = s->runs[rr];
+        const uint32_t lc = g - RI.cell_base;
         sp[q] = (uint8_t)((key[q] >> 24) & 7u);
-        iz[q] = (int32_t)(cell / (uint32_t)s->cfg.nr);
-        ir[q] = (int32_t)(cell % (uint32_t)s->cfg.nr);
+        iz[q] = (int32_t)(lc / (uint32_t)RI.nr);
+        ir[q] = (int32_t)(lc % (uint32_t)RI.nr);
+        if (run) run[q] = rr;
     }
     return PD_OK;
 }
 
 pd_status pd_get_rho(pd_sim* s, int64_t* rho_e, int64_t* rho_h) {
     if (!s) return PD_ERR_ARG;
-    const pd_config& c = s->cfg;
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    const size_t nodes = total_nodes(s);
     if (rho_e) CK(cudaMemcpyAsync(rho_e, s->rho_e, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
     if (rho_h) CK(cudaMemcpyAsync(rho_h, s->rho_h, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
     DevState d;
@@ -810,17 +1120,14 @@ pd_status pd_get_rho(pd_sim* s, int64_t* rho_e, int64_t* rho_h) {
 
 pd_status pd_get_phi(pd_sim* s, double* phi) {
     if (!s || !phi) return PD_ERR_ARG;
-    const pd_config& c = s->cfg;
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
-    CK(cudaMemcpyAsync(phi, s->phi, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(phi, s->phi, total_nodes(s) * 8, cudaMemcpyDeviceToHost, s->stream));
     DevState d;
     return sync_check(s, &d);
 }
 
 pd_status pd_get_field(pd_sim* s, double* Ez, double* Er) {
     if (!s || !Ez || !Er) return PD_ERR_ARG;
-    const pd_config& c = s->cfg;
-    const size_t nodes = (size_t)(c.geometry == PD_GEOM_RZ ? (c.nz + 1) * (c.nr + 1) : c.nz * c.nr);
+    const size_t nodes = total_nodes(s);
     std::vector<float2> h(nodes);
     CK(cudaMemcpyAsync(h.data(), s->E, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
     DevState d;
@@ -833,34 +1140,17 @@ pd_status pd_get_field(pd_sim* s, double* Ez, double* Er) {
     return PD_OK;
 }
 
-pd_status pd_get_density_map(pd_sim* s, int species, double* out) {
-    if (!s || !out || species < 0 || species >= NSP) return PD_ERR_ARG;
-    const pd_config& c = s->cfg;
-    const int nzn = c.geometry == PD_GEOM_RZ ? c.nz + 1 : c.nz, nrn = c.geometry == PD_GEOM_RZ ? c.nr + 1 : c.nr;
-    const size_t nodes = (size_t)nzn * nrn;
-    CK(cudaMemsetAsync(s->diag, 0, nodes * 8, s->stream));
-    launch_density(s->A, s->st, kparams(s, 1), species, s->diag, grid_for(s, 8), s->stream);
-    std::vector<long long> h(nodes);
-    CK(cudaMemcpyAsync(h.data(), s->diag, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
-    DevState d;
-    pd_status r = sync_check(s, &d);
-    if (r != PD_OK) return r;
-    for (int i = 0; i < nzn; ++i)
-        for (int j = 0; j < nrn; ++j) {
-            const size_t k = (size_t)i * nrn + j;
-            out[k] = c.weight * (double)h[k] / 4294967296.0 / node_volume(c, i, j);
-        }
-    return PD_OK;
+pd_status pd_get_density_map(pd_sim* s, int species, double* out) { return run_density(s, 0, species, out); }
+pd_status pd_get_run_density_map(pd_sim* s, int run, int species, double* out) {
+    return run_density(s, run, species, out);
 }
 
 pd_status pd_get_energy_spectrum(pd_sim* s, int species, double lo, double hi, int nbins, uint64_t* out) {
-    if (!s || !out || species < 0 || species >= NSP || nbins < 1 || nbins > 4096 || !(hi > lo))
-        return PD_ERR_ARG;
-    CK(cudaMemsetAsync(s->hist, 0, (size_t)nbins * 8, s->stream));
-    launch_spectrum(s->A, s->st, kparams(s, 1), species, lo, hi, nbins, s->hist, grid_for(s, 8), s->stream);
-    CK(cudaMemcpyAsync(out, s->hist, (size_t)nbins * 8, cudaMemcpyDeviceToHost, s->stream));
-    DevState d;
-    return sync_check(s, &d);
+    return run_spectrum(s, 0, species, lo, hi, nbins, out);
+}
+pd_status pd_get_run_energy_spectrum(pd_sim* s, int run, int species, double lo, double hi, int nbins,
+                                     uint64_t* out) {
+    return run_spectrum(s, run, species, lo, hi, nbins, out);
 }
 
 pd_status pd_profile_enable(pd_sim* s, int enable) {
@@ -901,6 +1191,7 @@ const char* pd_last_error(const pd_sim* s) { return s ? s->err.c_str() : "null s
 void pd_destroy(pd_sim* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    drop_graph(s);
     for (auto& r : s->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

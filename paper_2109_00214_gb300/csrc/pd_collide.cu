@@ -121,17 +121,17 @@ __device__ void rectangle_split(Stream& st, const V3& v, V3& v5, V3& v6, int mod
     v6 = V3{v.x - w5.x, v.y - w5.y, v.z - w5.z};
 }
 
-// single-particle fixed-point CIC deposit of zq at (cell, pz, pr)
-__device__ void deposit1(long long* rho, const KParams& P, uint32_t cell, float pz, float pr, int zq) {
-    const int iz = (int)(cell / (uint32_t)P.nr);
-    const int ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+// single-particle fixed-point CIC deposit of zq at (local cell, pz, pr) of run RI
+__device__ void deposit1(long long* rho, const RunInfo& RI, int geom, uint32_t lcell, float pz, float pr, int zq) {
+    const int iz = (int)(lcell / (uint32_t)RI.nr);
+    const int ir = (int)(lcell - (uint32_t)iz * (uint32_t)RI.nr);
     const uint32_t wz = __float2uint_rn(pz * 65536.0f);
     const uint32_t wr = __float2uint_rn(pr * 65536.0f);
     const long long az = 65536 - (long long)wz, ar = 65536 - (long long)wr;
-    atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir)], (unsigned long long)(zq * az * ar));
-    atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir)], (unsigned long long)(zq * (long long)wz * ar));
-    atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir + 1)], (unsigned long long)(zq * az * (long long)wr));
-    atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir + 1)],
+    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)], (unsigned long long)(zq * az * ar));
+    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir)], (unsigned long long)(zq * (long long)wz * ar));
+    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir + 1)], (unsigned long long)(zq * az * (long long)wr));
+    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir + 1)],
               (unsigned long long)(zq * (long long)wz * (long long)wr));
 }
 
@@ -222,12 +222,14 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
             const uint32_t Ncu = off[C + c + 1] - off[C + c];
             const uint32_t Ni = off[2 * C + c + 1] - off[2 * C + c];
             if (Ne > 0 && (Ncu > 0 || Ni > 0)) {
-                const uint32_t j = c % (uint32_t)P.nr;
-                Stream s(c, P.step, SID_NCAND, P.seed, P.run);
+                const RunInfo& RI = P.runs[run_of(P, c)];
+                const uint32_t lc = c - RI.cell_base;
+                const uint32_t j = lc % (uint32_t)RI.nr;
+                Stream s(lc, st->step, SID_NCAND, RI.seed, RI.run);
                 const float R0 = s.u01();
                 const float R1 = s.u01();
-                const float x0 = ((float)Ne * (float)Ncu) * ck[j] + R0;
-                const float x1 = ((float)Ne * (float)Ni) * ck[P.nr + j] + R1;
+                const float x0 = ((float)Ne * (float)Ncu) * ck[RI.ck_base + j] + R0;
+                const float x1 = ((float)Ne * (float)Ni) * ck[RI.ck_base + RI.nr + j] + R1;
                 n0 = (uint32_t)floorf(x0);
                 n1 = (uint32_t)floorf(x1);
             }
@@ -250,7 +252,9 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
 }
 
 struct CellCtx {
-    uint32_t cell;
+    uint32_t cell;                   // global cell
+    const RunInfo* RI;
+    int geom;
     unsigned long long slot0;        // first reserved spawn slot
     uint32_t nres;                   // reserved slots
     uint32_t id0;                    // id of the first reserved slot
@@ -258,14 +262,14 @@ struct CellCtx {
     uint32_t ev[NCH], nulls, consumed, thr, viol, fb;
 };
 
-__device__ bool spawn_electron(Particles& A, CellCtx& cx, const KParams& P, DevState* st, long long* rho_e,
-                               uint32_t cell, float pz, float pr, const V3& v) {
+__device__ bool spawn_electron(Particles& A, CellCtx& cx, DevState* st, long long* rho_e, uint32_t gcell, float pz,
+                               float pr, const V3& v) {
     if (cx.s >= cx.nres) {
         set_error(st, ERR_BOUNDS);
         return false;
     }
     const unsigned long long slot = cx.slot0 + cx.s;
-    A.key[slot] = make_key(SP_E, cell);
+    A.key[slot] = make_key(SP_E, gcell);
     A.pz[slot] = pz;
     A.pr[slot] = pr;
     A.vz[slot] = v.x;
@@ -273,15 +277,14 @@ __device__ bool spawn_electron(Particles& A, CellCtx& cx, const KParams& P, DevS
     A.vt[slot] = v.z;
     A.id[slot] = cx.id0 + cx.s;
     ++cx.s;
-    deposit1(rho_e, P, cell, pz, pr, -1);
+    deposit1(rho_e, *cx.RI, cx.geom, gcell - cx.RI->cell_base, pz, pr, -1);
     return true;
 }
 
 // lane-0 part of one candidate after the pair is chosen
 __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
                                   float Racc, float Rch, const float* __restrict__ xsE, const float* __restrict__ xs,
-                                  const KParams& P, const CollConsts& cc, DevState* st, long long* rho_e,
-                                  long long* rho_h) {
+                                  const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h) {
     const int ts = k == 0 ? SP_CU : SP_CUP;
     const uint32_t tkey = A.key[it];
     if ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts) {   // target already ionized this step
@@ -357,9 +360,9 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     const uint32_t tcell = key_cell(tkey);
     A.key[it] = converted_key((uint32_t)new_sp, (uint32_t)ts, tcell);
     const float tpz = A.pz[it], tpr = A.pr[it];
-    deposit1(rho_h, P, tcell, tpz, tpr, dq);
-    spawn_electron(A, cx, P, st, rho_e, tcell, tpz, tpr, e2);
-    if (ch == CH_DI) spawn_electron(A, cx, P, st, rho_e, key_cell(A.key[ie]), A.pz[ie], A.pr[ie], e6);
+    deposit1(rho_h, *cx.RI, cx.geom, tcell - cx.RI->cell_base, tpz, tpr, dq);
+    spawn_electron(A, cx, st, rho_e, tcell, tpz, tpr, e2);
+    if (ch == CH_DI) spawn_electron(A, cx, st, rho_e, key_cell(A.key[ie]), A.pz[ie], A.pr[ie], e6);
     ++cx.ev[ch];
 }
 
@@ -375,15 +378,20 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t C = P.ncell;
     const uint32_t n_alive = off[nbins];
-    const uint32_t id_next = st->id_next;
     for (unsigned long long w = warp0; w < n_active; w += nwarps) {
         const uint32_t c = active[w];
         const uint2 n = nc[c];
+        const int r = run_of(P, c);
+        const RunInfo* RI = &P.runs[r];
+        const uint32_t lc = c - RI->cell_base;
         CellCtx cx;
         cx.cell = c;
+        cx.RI = RI;
+        cx.geom = P.geom;
         cx.nres = 2u * (n.x + n.y);
         cx.slot0 = (unsigned long long)n_alive + 2ull * cand_off[c];
-        cx.id0 = id_next + 2u * cand_off[c];
+        // ids: the run's next id plus twice the candidates of the run's earlier cells
+        cx.id0 = P.rs[r].id_next + 2u * (cand_off[c] - cand_off[RI->cell_base]);
         cx.s = 0;
         for (int q = 0; q < NCH; ++q) cx.ev[q] = 0;
         cx.nulls = cx.consumed = cx.thr = cx.viol = cx.fb = 0;
@@ -408,7 +416,7 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
             IdList tl;
             load_ids(tl, A.id + t_base, Nt, lane);
             for (uint32_t m = 0; m < ncand; ++m) {
-                Stream rs(c, P.step, sid_cand(k, m), P.seed, P.run);
+                Stream rs(lc, st->step, sid_cand(k, m), RI->seed, RI->run);
                 const uint32_t i = rs.pick(Ne);
                 const uint32_t j = rs.pick(Nt);
                 const float Racc = rs.u01();
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
                     continue;
                 }
                 if (lane == 0)
-                    process_candidate(A, cx, rs, k, e_base + pe, t_base + pt, Racc, Rch, xsE, xs, P, cc, st, rho_e,
+                    process_candidate(A, cx, rs, k, e_base + pe, t_base + pt, Racc, Rch, xsE, xs, cc, st, rho_e,
                                       rho_h);
                 __syncwarp();
             }
@@ -428,43 +436,54 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
         const uint32_t s = __shfl_sync(FULL, cx.s, 0);
         for (uint32_t q = s + lane; q < cx.nres; q += 32) A.key[cx.slot0 + q] = DEAD;
         if (lane == 0) {
+            RunState& rsv = P.rs[r];
             for (int q = 0; q < NCH; ++q)
-                if (cx.ev[q]) atomicAdd(&st->ctr[C_EV + q], (unsigned long long)cx.ev[q]);
-            if (cx.nulls) atomicAdd(&st->ctr[C_NULL], (unsigned long long)cx.nulls);
-            if (cx.consumed) atomicAdd(&st->ctr[C_CONSUMED], (unsigned long long)cx.consumed);
-            if (cx.thr) atomicAdd(&st->ctr[C_THR], (unsigned long long)cx.thr);
-            if (cx.viol) atomicAdd(&st->ctr[C_VIOL], (unsigned long long)cx.viol);
-            if (cx.fb) atomicAdd(&st->ctr[C_ISOFB], (unsigned long long)cx.fb);
+                if (cx.ev[q]) atomicAdd(&rsv.ctr[C_EV + q], (unsigned long long)cx.ev[q]);
+            if (cx.nulls) atomicAdd(&rsv.ctr[C_NULL], (unsigned long long)cx.nulls);
+            if (cx.consumed) atomicAdd(&rsv.ctr[C_CONSUMED], (unsigned long long)cx.consumed);
+            if (cx.thr) atomicAdd(&rsv.ctr[C_THR], (unsigned long long)cx.thr);
+            if (cx.viol) atomicAdd(&rsv.ctr[C_VIOL], (unsigned long long)cx.viol);
+            if (cx.fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)cx.fb);
         }
     }
 }
 
+// slot / id bookkeeping of the step and the RC circuit of each run
 __global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, const uint32_t* __restrict__ cand_off,
-                           uint32_t ncell, DevState* st, KParams P, double dt, double V0, double R_ohm,
-                           double C_farad, int circuit) {
-    const unsigned long long T = cand_off[ncell];
-    unsigned long long ns = (unsigned long long)off[nbins] + 2ull * T;
-    if (ns > P.capacity) {
-        set_error(st, ERR_CAPACITY);
-        ns = P.capacity;
+                           DevState* st, KParams P, const RunCircuit* __restrict__ circ, double dt, int circuit) {
+    const uint32_t C = P.ncell;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long T = cand_off[C];
+        unsigned long long ns = (unsigned long long)off[nbins] + 2ull * T;
+        if (ns > P.capacity) {
+            set_error(st, ERR_CAPACITY);
+            ns = P.capacity;
+        }
+        st->n_slots = ns;
+        st->n_active = 0;
     }
-    st->n_slots = ns;
-    if ((unsigned long long)st->id_next + 2ull * T > 0xFFFFFFFFull) set_error(st, ERR_IDS);
-    st->id_next += (uint32_t)(2ull * T);
-    st->ctr[C_CAND] += T;
-    st->n_active = 0;
-    if (circuit) {
-        // C dV/dt = (V0 - V)/R - I_gap; the gap current leaves the anode node
-        const double I = -st->anode_charge_step / dt;
-        st->I_gap = I;
-        st->V += dt / C_farad * ((V0 - st->V) / R_ohm - I);
-        st->anode_charge_step = 0.0;
+    // the step is over for every kernel that draws from it
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->step += 1u;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.nruns; r += gridDim.x * blockDim.x) {
+        const RunInfo& RI = P.runs[r];
+        RunState& rs = P.rs[r];
+        const unsigned long long T = cand_off[RI.cell_base + RI.ncell] - cand_off[RI.cell_base];
+        if ((unsigned long long)rs.id_next + 2ull * T > 0xFFFFFFFFull) set_error(st, ERR_IDS);
+        rs.id_next += (uint32_t)(2ull * T);
+        rs.ctr[C_CAND] += T;
+        if (circuit) {
+            // C dV/dt = (V0 - V)/R - I_gap; the gap current leaves the anode node
+            const double I = -rs.anode_charge_step / dt;
+            rs.I_gap = I;
+            rs.V += dt / circ[r].C_farad * ((circ[r].V0 - rs.V) / circ[r].R_ohm - I);
+            rs.anode_charge_step = 0.0;
+        }
     }
 }
 
 // ---------------------------------------------------------------------
 // cathode injection (Sec. 2.3): FN electrons from the tip and neutrals at
-// a fixed fraction of the electron flux; one block.
+// a fixed fraction of the electron flux; one block per run.
 // ---------------------------------------------------------------------
 __device__ __forceinline__ float rayleigh(const float* __restrict__ ray, float U) {
     const float x = U * 1023.0f;
@@ -474,12 +493,18 @@ __device__ __forceinline__ float rayleigh(const float* __restrict__ ray, float U
 }
 
 __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __restrict__ E, DevState* st, KParams P,
-                                                InjectConsts ic, const float* __restrict__ ray) {
+                                                const InjectConsts* __restrict__ icv, const float* __restrict__ ray) {
     __shared__ uint32_t ne_s[64], nn_s[64], pre_s[65];
+    __shared__ unsigned long long slot0_s;
+    const int run = blockIdx.x;
+    const InjectConsts& ic = icv[run];
+    const RunInfo& RI = P.runs[run];
+    RunState& rs = P.rs[run];
+    if (ic.ntip == 0) return;
     const int t = threadIdx.x;
     if (t < ic.ntip) {
         const int j = t;
-        const double ezs = 0.5 * ((double)E[j].x + (double)E[j + 1].x);
+        const double ezs = 0.5 * ((double)E[node_of(RI, 0, 0, j)].x + (double)E[node_of(RI, 0, 0, j + 1)].x);
         const double F = ic.beta * (ezs < 0 ? -ezs : 0.0);
         double J = 0.0;
         if (F > 0.0) {
@@ -488,7 +513,7 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
         }
         const double lam_e = J * ic.area[j] * ic.dt / (1.602176634e-19 * ic.weight);
         const double lam_n = ic.ratio * lam_e;
-        Stream s((uint32_t)j, P.step, SID_INJ_COUNT, P.seed, P.run);
+        Stream s((uint32_t)j, st->step, SID_INJ_COUNT, RI.seed, RI.run);
         const double Re = (double)s.u01(), Rn = (double)s.u01();
         ne_s[j] = (uint32_t)floor(lam_e + Re);
         nn_s[j] = (uint32_t)floor(lam_n + Rn);
@@ -501,11 +526,12 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
             acc += ne_s[j] + nn_s[j];
         }
         pre_s[ic.ntip] = acc;
+        slot0_s = acc ? atomicAdd(&st->n_slots, (unsigned long long)acc) : 0ull;
     }
     __syncthreads();
     const uint32_t total = pre_s[ic.ntip];
-    const unsigned long long slot0 = st->n_slots;
-    const uint32_t id0 = st->id_next;
+    const unsigned long long slot0 = slot0_s;
+    const uint32_t id0 = rs.id_next;
     uint32_t emitted_e = 0, emitted_cu = 0;
     uint32_t fb = 0;
     for (uint32_t p = t; p < total; p += blockDim.x) {
@@ -513,7 +539,7 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
         while (pre_s[j + 1] <= p) ++j;
         const uint32_t loc = p - pre_s[j];
         const bool is_e = loc < ne_s[j];
-        Stream sp((uint32_t)j, P.step, is_e ? sid_inj_e(loc) : sid_inj_cu(loc - ne_s[j]), P.seed, P.run);
+        Stream sp((uint32_t)j, st->step, is_e ? sid_inj_e(loc) : sid_inj_cu(loc - ne_s[j]), RI.seed, RI.run);
         const float U = sp.u01();
         const float lo = ic.lo[j], hi = ic.hi[j];
         const float rr = sqrtf(lo * lo + U * (hi * hi - lo * lo));
@@ -535,7 +561,7 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
             set_error(st, ERR_CAPACITY);
             continue;
         }
-        A.key[slot] = make_key(is_e ? SP_E : SP_CU, (uint32_t)j);   // iz = 0
+        A.key[slot] = make_key(is_e ? SP_E : SP_CU, RI.cell_base + (uint32_t)j);   // iz = 0
         A.pz[slot] = 0.0f;
         A.pr[slot] = pr;
         A.vz[slot] = vz;
@@ -545,16 +571,15 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
         if (is_e) ++emitted_e; else ++emitted_cu;
     }
     if (emitted_e) {
-        atomicAdd(&st->ctr[C_EMIT_E], (unsigned long long)emitted_e);
-        for (uint32_t q = 0; q < emitted_e; ++q) atomicAdd(&st->charge_cathode, 1.602176634e-19 * ic.weight);
+        atomicAdd(&rs.ctr[C_EMIT_E], (unsigned long long)emitted_e);
+        for (uint32_t q = 0; q < emitted_e; ++q) atomicAdd(&rs.charge_cathode, 1.602176634e-19 * ic.weight);
     }
-    if (emitted_cu) atomicAdd(&st->ctr[C_EMIT_CU], (unsigned long long)emitted_cu);
-    if (fb) atomicAdd(&st->ctr[C_ISOFB], (unsigned long long)fb);
+    if (emitted_cu) atomicAdd(&rs.ctr[C_EMIT_CU], (unsigned long long)emitted_cu);
+    if (fb) atomicAdd(&rs.ctr[C_ISOFB], (unsigned long long)fb);
     __syncthreads();
     if (t == 0) {
-        unsigned long long ns = slot0 + total;
-        st->n_slots = ns > P.capacity ? P.capacity : ns;
-        st->id_next = id0 + total;
+        rs.id_next = id0 + total;
+        if (slot0 + total > P.capacity) atomicMin(&st->n_slots, P.capacity);
     }
 }
 
@@ -568,14 +593,13 @@ void launch_collide(const Particles& A, const uint32_t* off, const uint2* nc, co
                     cudaStream_t s) {
     k_collide<<<grid, 128, 0, s>>>(A, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
 }
-void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, uint32_t ncell, DevState* st,
-                     const KParams& P, double dt, double V0, double R_ohm, double C_farad, int circuit,
-                     cudaStream_t s) {
-    k_finalize<<<1, 1, 0, s>>>(off, nbins, cand_off, ncell, st, P, dt, V0, R_ohm, C_farad, circuit);
+void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
+                     const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {
+    k_finalize<<<1, 256, 0, s>>>(off, nbins, cand_off, st, P, circ, dt, circuit);
 }
-void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts& ic,
+void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts* ic,
                    const float* ray, cudaStream_t s) {
-    k_inject<<<1, 256, 0, s>>>(A, E, st, P, ic, ray);
+    k_inject<<<P.nruns, 256, 0, s>>>(A, E, st, P, ic, ray);
 }
 
 }  // namespace pd

@@ -1,5 +1,5 @@
 // pd_field.cu -- Poisson solve of Eq. (8), read as lap(phi) = -rho/eps0, by
-// geometric multigrid on the r-z node grid, and E = -grad(phi).
+// geometric multigrid on the r-z node grid of every run, and E = -grad(phi).
 //
 // Discretisation (finite volumes around each node (i, j)):
 //   ap_j (phi_{j+1} - phi_j) + am_j (phi_{j-1} - phi_j)
@@ -12,9 +12,13 @@
 // Multigrid: V(2,2) cycles with red-black Gauss-Seidel, residual restriction
 // by full weighting of the integrated residuals (weights 1, 1/2, 1/4),
 // bilinear prolongation, coefficients rediscretised on each level, and a
-// single-block Gauss-Seidel solve on the coarsest level.  Double precision;
-// the cycle stops once |b - A phi| / |b| <= tol (checked on the host between
-// cycles).
+// single-block Gauss-Seidel solve on the coarsest level.  Double precision.
+//
+// Batched over runs: each level operation is one launch with blockIdx.y = run
+// (runs of different sizes and depths; a block whose run has no such level,
+// or has converged, returns at once).  Per-run residual norms and converged
+// flags stay on the device.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -27,11 +31,11 @@ namespace {
 constexpr double QE_ = 1.602176634e-19;
 constexpr double EPS0_ = 8.8541878128e-12;
 constexpr double PI_ = 3.14159265358979323846;
+constexpr int RED_BLOCKS = 64;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
 void level_dims(int nz, int nr, int* nzs, int* nrs, int& nlev) {
-    nlev = 0;
     nzs[0] = nz;
     nrs[0] = nr;
     nlev = 1;
@@ -42,6 +46,17 @@ void level_dims(int nz, int nr, int* nzs, int* nrs, int& nlev) {
         ++nlev;
     }
 }
+
+size_t run_bytes(int nz, int nr) {
+    int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
+    level_dims(nz, nr, a, b, n);
+    size_t t = 0;
+    for (int l = 0; l < n; ++l) {
+        const size_t nodes = (size_t)(a[l] + 1) * (b[l] + 1);
+        t += 3 * al(nodes * 8) + 3 * al((size_t)(b[l] + 1) * 8);
+    }
+    return t + 2 * al((size_t)(nr + 1) * 8);
+}
 }  // namespace
 
 bool field_grid_ok(int nz, int nr) {
@@ -50,41 +65,51 @@ bool field_grid_ok(int nz, int nr) {
     return (a[n - 1] + 1) * (b[n - 1] + 1) <= 1024 && a[n - 1] >= 2 && b[n - 1] >= 2;
 }
 
-size_t field_workspace_bytes(int nz, int nr) {
-    int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
-    level_dims(nz, nr, a, b, n);
+size_t field_workspace_bytes(const std::vector<int>& nz, const std::vector<int>& nr) {
     size_t t = 0;
-    for (int l = 0; l < n; ++l) {
-        const size_t nodes = (size_t)(a[l] + 1) * (b[l] + 1);
-        t += 3 * al(nodes * 8) + 3 * al((size_t)(b[l] + 1) * 8);
-    }
-    t += 2 * al((size_t)(nr + 1) * 8) + al(4096 * 8);
+    const size_t R = nz.size();
+    for (size_t r = 0; r < R; ++r) t += run_bytes(nz[r], nr[r]);
+    t += al(R * MG_MAX_LEVELS * sizeof(MGLevel)) + al(R * 4) * 3 + al(R * RED_BLOCKS * 2 * 8) + al(R * 8) * 2 +
+         al(R * 16);
     return t;
 }
 
 // ------------------------------------------------------------------
-// kernels
+// kernels (blockIdx.y = run)
 // ------------------------------------------------------------------
+__device__ __forceinline__ bool level_active(const int* nlev, const int* done, int r, int l, bool coarsest) {
+    if (done && done[r]) return false;
+    const int n = nlev[r];
+    return coarsest ? (l == n - 1) : (l < n - 1);
+}
+
 __global__ void k_rhs(const long long* rho_e, const long long* rho_h, const double* fv_over_verb,
-                      const double* verb_base, MGLevel L, double qw, const DevState* st, double* phi) {
+                      const double* verb_base, const int* fvb_off, const MGLevel* lev, const RunInfo* runs,
+                      const RunState* rs, double* phi) {
+    const int run = blockIdx.y;
+    const MGLevel L = lev[run * MG_MAX_LEVELS];
+    const RunInfo& RI = runs[run];
     const int W = L.nr + 1;
     const int n = (L.nz + 1) * W;
-    const double V = st->V;
+    const double V = rs[run].V;
+    const double qw = QE_ * RI.weight / 4294967296.0;
+    const int fo = fvb_off[run];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W, j = k - i * W;
+        const uint32_t g = RI.node_base + (uint32_t)k;
         if (i == 0) {
-            phi[k] = 0.0;
+            phi[g] = 0.0;
             L.f[k] = 0.0;
             continue;
         }
         if (i == L.nz) {
-            phi[k] = V;
+            phi[g] = V;
             L.f[k] = 0.0;
             continue;
         }
         // rho_ij (C/m^3) = q W rho_int 2^-32 / V_verb; rhs = rho Vfv / eps0
-        const double rho = qw * (double)(rho_e[k] + rho_h[k]) / verb_base[j];
-        double v = rho * (fv_over_verb[j] * verb_base[j]) / EPS0_;
+        const double rho = qw * (double)(rho_e[g] + rho_h[g]) / verb_base[fo + j];
+        double v = rho * (fv_over_verb[fo + j] * verb_base[fo + j]) / EPS0_;
         if (i == L.nz - 1) v += L.b[j] * V;
         L.f[k] = v;
     }
@@ -103,7 +128,10 @@ __device__ __forceinline__ double apply_A(const MGLevel& L, const double* x, int
 
 // red-black Gauss-Seidel on the interior rows; Dirichlet neighbours are part
 // of f (level 0) or zero (corrections)
-__global__ void k_smooth(MGLevel L, int color) {
+__global__ void k_smooth(const MGLevel* lev, const int* nlev, const int* done, int l, int color) {
+    const int run = blockIdx.y;
+    if (!level_active(nlev, done, run, l, false)) return;
+    const MGLevel L = lev[run * MG_MAX_LEVELS + l];
     const int W = L.nr + 1;
     const int n = (L.nz - 1) * W;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -119,17 +147,23 @@ __global__ void k_smooth(MGLevel L, int color) {
     }
 }
 
-__global__ void k_residual(MGLevel L, double* red) {
-    const int W = L.nr + 1;
-    const int n = (L.nz - 1) * W;
+// residual of level l; with `red`, per-block partial sums of r^2 and f^2
+__global__ void k_residual(const MGLevel* lev, const int* nlev, const int* done, int l, double* red) {
+    const int run = blockIdx.y;
+    const bool act = red ? (nlev[run] > 0) : level_active(nlev, done, run, l, false);
     double acc = 0.0, accb = 0.0;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const int i = 1 + q / W, j = q - (i - 1) * W;
-        const int k = i * W + j;
-        const double r = L.f[k] - apply_A(L, L.x, i, j);
-        L.r[k] = r;
-        acc += r * r;
-        accb += L.f[k] * L.f[k];
+    if (act) {
+        const MGLevel L = lev[run * MG_MAX_LEVELS + l];
+        const int W = L.nr + 1;
+        const int n = (L.nz - 1) * W;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+            const int i = 1 + q / W, j = q - (i - 1) * W;
+            const int k = i * W + j;
+            const double r = L.f[k] - apply_A(L, L.x, i, j);
+            L.r[k] = r;
+            acc += r * r;
+            accb += L.f[k] * L.f[k];
+        }
     }
     if (red) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -149,15 +183,43 @@ __global__ void k_residual(MGLevel L, double* red) {
                 t += sa[q];
                 tb += sb[q];
             }
-            red[2 * blockIdx.x] = t;
-            red[2 * blockIdx.x + 1] = tb;
+            red[(run * RED_BLOCKS + blockIdx.x) * 2] = t;
+            red[(run * RED_BLOCKS + blockIdx.x) * 2 + 1] = tb;
         }
     }
 }
 
+// per run: relres = |r| / |b|, converged flag, bookkeeping
+__global__ void k_norms(const double* red, double* bnorm, int* done, const double* tol, RunState* rs, int nruns,
+                        int cycle, int first) {
+    const int run = blockIdx.x * blockDim.x + threadIdx.x;
+    if (run >= nruns) return;
+    double a = 0, b = 0;
+    for (int q = 0; q < RED_BLOCKS; ++q) {
+        a += red[(run * RED_BLOCKS + q) * 2];
+        b += red[(run * RED_BLOCKS + q) * 2 + 1];
+    }
+    const double rn = sqrt(a), bn = sqrt(b);
+    if (first) done[run] = 0;
+    if (done[run]) return;
+    bnorm[run] = bn;
+    const double rel = bn > 0 ? rn / bn : 0.0;
+    rs[run].relres = rel;
+    rs[run].cycles = (double)cycle;
+    if (!(rel == rel) || !(bn == bn)) {
+        done[run] = 2;              // non-finite: stop this run
+        return;
+    }
+    if (bn == 0.0 || rel <= tol[run]) done[run] = 1;
+}
+
 // coarse rhs = sum of the fine integrated residuals over the coarse control
 // volume (full weighting scaled by 4); zero initial coarse correction
-__global__ void k_restrict(MGLevel F, MGLevel Cl) {
+__global__ void k_restrict(const MGLevel* lev, const int* nlev, const int* done, int l) {
+    const int run = blockIdx.y;
+    if (!level_active(nlev, done, run, l, false)) return;
+    const MGLevel F = lev[run * MG_MAX_LEVELS + l];
+    const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
     const int Wc = Cl.nr + 1, Wf = F.nr + 1;
     const int n = (Cl.nz + 1) * Wc;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -183,7 +245,11 @@ __global__ void k_restrict(MGLevel F, MGLevel Cl) {
     }
 }
 
-__global__ void k_prolong(MGLevel F, MGLevel Cl) {
+__global__ void k_prolong(const MGLevel* lev, const int* nlev, const int* done, int l) {
+    const int run = blockIdx.y;
+    if (!level_active(nlev, done, run, l, false)) return;
+    const MGLevel F = lev[run * MG_MAX_LEVELS + l];
+    const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
     const int Wc = Cl.nr + 1, Wf = F.nr + 1;
     const int n = (F.nz - 1) * Wf;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -195,8 +261,13 @@ __global__ void k_prolong(MGLevel F, MGLevel Cl) {
     }
 }
 
-// coarsest level: Gauss-Seidel sweeps in one block
-__global__ void __launch_bounds__(1024) k_coarse(MGLevel L, int sweeps) {
+// coarsest level of each run whose hierarchy ends at level l: Gauss-Seidel
+// sweeps in one block (blockIdx.x = run)
+__global__ void __launch_bounds__(1024) k_coarse(const MGLevel* lev, const int* nlev, const int* done, int l,
+                                                 int sweeps) {
+    const int run = blockIdx.x;
+    if (!level_active(nlev, done, run, l, true)) return;
+    const MGLevel L = lev[run * MG_MAX_LEVELS + l];
     const int W = L.nr + 1;
     const int n = (L.nz - 1) * W;
     for (int it = 0; it < sweeps; ++it) {
@@ -219,25 +290,29 @@ __global__ void __launch_bounds__(1024) k_coarse(MGLevel L, int sweeps) {
 
 // E = -grad(phi): central inside, one-sided at the electrodes, E_r = 0 on the
 // axis and at r = R
-__global__ void k_efield(const double* phi, int nz, int nr, double dz, double dr, float2* E) {
+__global__ void k_efield(const double* phi, const RunInfo* runs, const double* dzr, float2* E) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int nz = RI.nz, nr = RI.nr;
+    const double dz = dzr[2 * run], dr = dzr[2 * run + 1];
     const int W = nr + 1;
     const int n = (nz + 1) * W;
+    const double* p = phi + RI.node_base;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W, j = k - i * W;
         double ez, er;
-        if (i == 0) ez = -(phi[k + W] - phi[k]) / dz;
-        else if (i == nz) ez = -(phi[k] - phi[k - W]) / dz;
-        else ez = -(phi[k + W] - phi[k - W]) / (2.0 * dz);
+        if (i == 0) ez = -(p[k + W] - p[k]) / dz;
+        else if (i == nz) ez = -(p[k] - p[k - W]) / dz;
+        else ez = -(p[k + W] - p[k - W]) / (2.0 * dz);
         if (j == 0 || j == nr) er = 0.0;
-        else er = -(phi[k + 1] - phi[k - 1]) / (2.0 * dr);
-        E[k] = make_float2((float)ez, (float)er);
+        else er = -(p[k + 1] - p[k - 1]) / (2.0 * dr);
+        E[RI.node_base + k] = make_float2((float)ez, (float)er);
     }
 }
 
-__global__ void k_record(DevState* st, double relres, double cycles, int bad) {
-    st->relres = relres;
-    st->cycles = cycles;
-    if (bad) atomicOr(&st->error, ERR_NONFINITE);
+__global__ void k_flag_nonfinite(const int* done, int nruns, DevState* st) {
+    for (int r = threadIdx.x; r < nruns; r += blockDim.x)
+        if (done[r] == 2) atomicOr(&st->error, ERR_NONFINITE);
 }
 
 // ------------------------------------------------------------------
@@ -248,9 +323,9 @@ static int blocks_for(int n) {
     return b < 1 ? 1 : (b > 1216 ? 1216 : b);
 }
 
-int field_init(FieldSolver& fs, const pd_config& c, void* ws, size_t bytes, cudaStream_t s) {
-    int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
-    level_dims(c.nz, c.nr, a, b, n);
+int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::vector<uint32_t>& node_base,
+               double* phi, void* ws, size_t bytes, cudaStream_t s) {
+    const int R = (int)cfgs.size();
     char* w = (char*)ws;
     size_t o = 0;
     auto take = [&](size_t sz) {
@@ -258,130 +333,170 @@ int field_init(FieldSolver& fs, const pd_config& c, void* ws, size_t bytes, cuda
         o += al(sz);
         return p;
     };
-    fs.nlev = n;
-    fs.nz = c.nz;
-    fs.nr = c.nr;
-    fs.weight = c.weight;
-    fs.tol = c.poisson_tol;
-    fs.max_cycles = c.poisson_max_cycles > 0 ? c.poisson_max_cycles : 60;
-    fs.V0 = c.V0;
-    for (int l = 0; l < n; ++l) {
-        MGLevel& L = fs.lev[l];
-        L.nz = a[l];
-        L.nr = b[l];
-        L.dz = c.dz * (double)(1 << l);
-        L.dr = c.dr * (double)(1 << l);
-        const size_t nodes = (size_t)(L.nz + 1) * (L.nr + 1);
-        L.x = (double*)take(nodes * 8);
-        L.f = (double*)take(nodes * 8);
-        L.r = (double*)take(nodes * 8);
-        L.ap = (double*)take((size_t)(L.nr + 1) * 8);
-        L.am = (double*)take((size_t)(L.nr + 1) * 8);
-        L.b = (double*)take((size_t)(L.nr + 1) * 8);
-        std::vector<double> ap(L.nr + 1), am(L.nr + 1), bb(L.nr + 1);
-        const double R = L.nr * L.dr;
-        for (int j = 0; j <= L.nr; ++j) {
-            const double rp = (j + 0.5) * L.dr, rm = (j - 0.5) * L.dr;
-            ap[j] = j < L.nr ? 2.0 * PI_ * rp * L.dz / L.dr : 0.0;
-            am[j] = j > 0 ? 2.0 * PI_ * rm * L.dz / L.dr : 0.0;
-            double A;
-            if (j == 0) A = PI_ * (0.5 * L.dr) * (0.5 * L.dr);
-            else if (j == L.nr) A = PI_ * (R * R - (R - 0.5 * L.dr) * (R - 0.5 * L.dr));
-            else A = 2.0 * PI_ * j * L.dr * L.dr;
-            bb[j] = A / L.dz;
-        }
-        cudaMemcpyAsync(L.ap, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(L.am, am.data(), am.size() * 8, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(L.b, bb.data(), bb.size() * 8, cudaMemcpyHostToDevice, s);
-        cudaMemsetAsync(L.x, 0, nodes * 8, s);
-        if (l == 0) {
-            std::vector<double> fvv(L.nr + 1), vb(L.nr + 1);
+    fs.nruns = R;
+    fs.nlev.assign(R, 0);
+    fs.host_lev.assign((size_t)R * MG_MAX_LEVELS, MGLevel{});
+    fs.max_levels = 0;
+    fs.max_nodes0 = 0;
+    fs.max_cycles = cfgs[0].poisson_max_cycles > 0 ? cfgs[0].poisson_max_cycles : 60;
+    std::vector<double> fvv_all, vb_all, tol(R), dzr(2 * (size_t)R);
+    std::vector<int> fvb_off(R);
+    for (int r = 0; r < R; ++r) {
+        const pd_config& c = cfgs[r];
+        int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
+        level_dims(c.nz, c.nr, a, b, n);
+        fs.nlev[r] = n;
+        fs.max_levels = std::max(fs.max_levels, n);
+        fs.max_nodes0 = std::max(fs.max_nodes0, (c.nz + 1) * (c.nr + 1));
+        tol[r] = c.poisson_tol;
+        dzr[2 * r] = c.dz;
+        dzr[2 * r + 1] = c.dr;
+        for (int l = 0; l < n; ++l) {
+            MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
+            L.nz = a[l];
+            L.nr = b[l];
+            const double dz = c.dz * (double)(1 << l), dr = c.dr * (double)(1 << l);
+            const size_t nodes = (size_t)(L.nz + 1) * (L.nr + 1);
+            L.x = l == 0 ? phi + node_base[r] : (double*)take(nodes * 8);
+            L.f = (double*)take(nodes * 8);
+            L.r = (double*)take(nodes * 8);
+            L.ap = (double*)take((size_t)(L.nr + 1) * 8);
+            L.am = (double*)take((size_t)(L.nr + 1) * 8);
+            L.b = (double*)take((size_t)(L.nr + 1) * 8);
+            std::vector<double> ap(L.nr + 1), am(L.nr + 1), bb(L.nr + 1);
+            const double Rr = L.nr * dr;
             for (int j = 0; j <= L.nr; ++j) {
-                const double dz = c.dz, dr = c.dr;
-                double verb;
-                if (j == 0) verb = PI_ * dz * dr * dr / 3.0;
-                else if (j == c.nr) verb = 2.0 * PI_ * dz * dr * dr * ((double)c.nr / 2.0 - 1.0 / 6.0);
-                else verb = 2.0 * PI_ * dz * dr * dr * (double)j;
-                vb[j] = verb;
-                const double A = bb[j] * L.dz;  // radial extent area of the control volume
-                fvv[j] = A * L.dz / verb;       // Vfv / Vverb, Vfv = A dz
+                const double rp = (j + 0.5) * dr, rm = (j - 0.5) * dr;
+                ap[j] = j < L.nr ? 2.0 * PI_ * rp * dz / dr : 0.0;
+                am[j] = j > 0 ? 2.0 * PI_ * rm * dz / dr : 0.0;
+                double A;
+                if (j == 0) A = PI_ * (0.5 * dr) * (0.5 * dr);
+                else if (j == L.nr) A = PI_ * (Rr * Rr - (Rr - 0.5 * dr) * (Rr - 0.5 * dr));
+                else A = 2.0 * PI_ * j * dr * dr;
+                bb[j] = A / dz;
             }
-            fs.fv_over_verb = (double*)take(fvv.size() * 8);
-            fs.verb_base = (double*)take(vb.size() * 8);
-            cudaMemcpyAsync(fs.fv_over_verb, fvv.data(), fvv.size() * 8, cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(fs.verb_base, vb.data(), vb.size() * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(L.ap, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(L.am, am.data(), am.size() * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(L.b, bb.data(), bb.size() * 8, cudaMemcpyHostToDevice, s);
+            if (l > 0) cudaMemsetAsync(L.x, 0, nodes * 8, s);
+            if (l == 0) {
+                fvb_off[r] = (int)fvv_all.size();
+                for (int j = 0; j <= L.nr; ++j) {
+                    double verb;
+                    if (j == 0) verb = PI_ * c.dz * c.dr * c.dr / 3.0;
+                    else if (j == c.nr) verb = 2.0 * PI_ * c.dz * c.dr * c.dr * ((double)c.nr / 2.0 - 1.0 / 6.0);
+                    else verb = 2.0 * PI_ * c.dz * c.dr * c.dr * (double)j;
+                    const double A = bb[j] * dz;      // radial extent area of the control volume
+                    vb_all.push_back(verb);
+                    fvv_all.push_back(A * dz / verb);  // Vfv / Vverb, Vfv = A dz
+                }
+            }
         }
     }
-    fs.red = (double*)take(4096 * 8);
+    fs.fv_over_verb = (double*)take(fvv_all.size() * 8);
+    fs.verb_base = (double*)take(vb_all.size() * 8);
+    fs.lev = (MGLevel*)take((size_t)R * MG_MAX_LEVELS * sizeof(MGLevel));
+    fs.nlev_dev = (int*)take((size_t)R * 4);
+    fs.fvb_off = (int*)take((size_t)R * 4);
+    fs.done = (int*)take((size_t)R * 4);
+    fs.red = (double*)take((size_t)R * RED_BLOCKS * 2 * 8);
+    fs.bnorm = (double*)take((size_t)R * 8);
+    fs.tol = (double*)take((size_t)R * 8);
+    fs.dzr = (double*)take((size_t)R * 16);
     if (o > bytes) return 1;
-    if (!fs.host_red && cudaMallocHost(&fs.host_red, 4096 * 8) != cudaSuccess) return 1;
+    cudaMemcpyAsync(fs.dzr, dzr.data(), (size_t)R * 16, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.fv_over_verb, fvv_all.data(), fvv_all.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.verb_base, vb_all.data(), vb_all.size() * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.lev, fs.host_lev.data(), fs.host_lev.size() * sizeof(MGLevel), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.nlev_dev, fs.nlev.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.fvb_off, fvb_off.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(fs.tol, tol.data(), (size_t)R * 8, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(fs.done, 0, (size_t)R * 4, s);
+    if (!fs.host_done && cudaMallocHost(&fs.host_done, (size_t)R * 4) != cudaSuccess) return 1;
     return cudaStreamSynchronize(s) == cudaSuccess ? 0 : 1;
 }
 
 void field_free(FieldSolver& fs) {
-    if (fs.host_red) cudaFreeHost(fs.host_red);
-    fs.host_red = nullptr;
+    if (fs.host_done) cudaFreeHost(fs.host_done);
+    fs.host_done = nullptr;
 }
 
-static void vcycle(FieldSolver& fs, int l, cudaStream_t s) {
-    MGLevel& L = fs.lev[l];
-    const int n = (L.nz + 1) * (L.nr + 1);
-    if (l == fs.nlev - 1) {
-        k_coarse<<<1, 1024, 0, s>>>(L, 200);
-        return;
+static int level_blocks(const FieldSolver& fs, int l) {
+    int mx = 0;
+    for (int r = 0; r < fs.nruns; ++r)
+        if (l < fs.nlev[r]) {
+            const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
+            mx = std::max(mx, (L.nz + 1) * (L.nr + 1));
+        }
+    return blocks_for(mx);
+}
+
+static void vcycle(FieldSolver& fs, cudaStream_t s) {
+    const int R = fs.nruns;
+    // down: smooth, residual, restrict; the coarsest level of each run is solved directly
+    for (int l = 0; l < fs.max_levels; ++l) {
+        const dim3 g(level_blocks(fs, l), R);
+        for (int it = 0; it < 2; ++it) {
+            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
+            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
+        }
+        k_residual<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, nullptr);
+        if (l + 1 < fs.max_levels) {
+            const dim3 gc(level_blocks(fs, l + 1), R);
+            k_restrict<<<gc, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
+        }
+        k_coarse<<<R, 1024, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 200);
     }
-    for (int it = 0; it < 2; ++it) {
-        k_smooth<<<blocks_for(n / 2), 256, 0, s>>>(L, 0);
-        k_smooth<<<blocks_for(n / 2), 256, 0, s>>>(L, 1);
-    }
-    k_residual<<<blocks_for(n), 256, 0, s>>>(L, nullptr);
-    MGLevel& Cl = fs.lev[l + 1];
-    k_restrict<<<blocks_for((Cl.nz + 1) * (Cl.nr + 1)), 256, 0, s>>>(L, Cl);
-    vcycle(fs, l + 1, s);
-    k_prolong<<<blocks_for(n), 256, 0, s>>>(L, Cl);
-    for (int it = 0; it < 2; ++it) {
-        k_smooth<<<blocks_for(n / 2), 256, 0, s>>>(L, 1);
-        k_smooth<<<blocks_for(n / 2), 256, 0, s>>>(L, 0);
+    // up: prolong, smooth
+    for (int l = fs.max_levels - 2; l >= 0; --l) {
+        const dim3 g(level_blocks(fs, l), R);
+        k_prolong<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
+        for (int it = 0; it < 2; ++it) {
+            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
+            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
+        }
     }
 }
 
-static int residual_norms(FieldSolver& fs, cudaStream_t s, double* rn, double* bn) {
-    MGLevel& L = fs.lev[0];
-    const int n = (L.nz + 1) * (L.nr + 1);
-    const int nb = blocks_for(n) > 2048 ? 2048 : blocks_for(n);
-    k_residual<<<nb, 256, 0, s>>>(L, fs.red);
-    if (cudaMemcpyAsync(fs.host_red, fs.red, (size_t)nb * 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) return 1;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
-    double a = 0, b = 0;
-    for (int q = 0; q < nb; ++q) {
-        a += fs.host_red[2 * q];
-        b += fs.host_red[2 * q + 1];
-    }
-    *rn = std::sqrt(a);
-    *bn = std::sqrt(b);
-    return 0;
+static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStream_t s) {
+    const int R = fs.nruns;
+    const dim3 g(RED_BLOCKS, R);
+    k_residual<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, nullptr, 0, fs.red);
+    k_norms<<<(R + 127) / 128, 128, 0, s>>>(fs.red, fs.bnorm, fs.done, fs.tol, rs, R, cycle, first);
 }
 
-int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E, DevState* st,
-                cudaStream_t s) {
-    MGLevel& L0 = fs.lev[0];
-    L0.x = phi;   // solve in place; the previous solution is the initial guess
-    const int n = (L0.nz + 1) * (L0.nr + 1);
-    const double qw = QE_ * fs.weight / 4294967296.0;
-    k_rhs<<<blocks_for(n), 256, 0, s>>>(rho_e, rho_h, fs.fv_over_verb, fs.verb_base, L0, qw, st, phi);
-    double rn = 0, bn = 0;
-    if (residual_norms(fs, s, &rn, &bn)) return 1;
-    int cyc = 0;
-    bool bad = !std::isfinite(rn) || !std::isfinite(bn);
-    while (!bad && bn > 0 && rn > fs.tol * bn && cyc < fs.max_cycles) {
-        vcycle(fs, 0, s);
-        ++cyc;
-        if (residual_norms(fs, s, &rn, &bn)) return 1;
-        bad = !std::isfinite(rn);
+int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
+                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s) {
+    (void)E;
+    const int R = fs.nruns;
+    const dim3 g0(blocks_for(fs.max_nodes0), R);
+    k_rhs<<<g0, 256, 0, s>>>(rho_e, rho_h, fs.fv_over_verb, fs.verb_base, fs.fvb_off, fs.lev, runs, rs, phi);
+    norms(fs, rs, 0, 1, s);
+    if (host_check) {
+        for (int cyc = 1; cyc <= fs.max_cycles; ++cyc) {
+            if (cudaMemcpyAsync(fs.host_done, fs.done, (size_t)R * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return 1;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
+            bool all = true;
+            for (int r = 0; r < R; ++r) all = all && fs.host_done[r] != 0;
+            if (all) break;
+            vcycle(fs, s);
+            norms(fs, rs, cyc, 0, s);
+        }
+    } else {
+        for (int cyc = 1; cyc <= cycles; ++cyc) {
+            vcycle(fs, s);
+            norms(fs, rs, cyc, 0, s);
+        }
     }
-    k_efield<<<blocks_for(n), 256, 0, s>>>(phi, L0.nz, L0.nr, L0.dz, L0.dr, E);
-    k_record<<<1, 1, 0, s>>>(st, bn > 0 ? rn / bn : 0.0, (double)cyc, bad ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+// E for every run (separate so the caller can time it)
+void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, cudaStream_t s) {
+    const dim3 g(blocks_for(fs.max_nodes0), fs.nruns);
+    k_efield<<<g, 256, 0, s>>>(phi, runs, fs.dzr, E);
+    k_flag_nonfinite<<<1, 128, 0, s>>>(fs.done, fs.nruns, st);
 }
 
 }  // namespace pd

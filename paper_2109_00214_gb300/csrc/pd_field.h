@@ -1,6 +1,9 @@
-// pd_field.h -- Poisson solve (Eq. (8)) and E = -grad(phi) on the r-z node grid.
+// pd_field.h -- Poisson solve (Eq. (8)) and E = -grad(phi) on the r-z node
+// grids of all runs of a simulation, batched.
 #pragma once
 #include <cstddef>
+#include <vector>
+
 #include "pd.h"
 #include "pd_internal.cuh"
 
@@ -8,32 +11,50 @@ namespace pd {
 
 constexpr int MG_MAX_LEVELS = 12;
 
+// one level of one run
 struct MGLevel {
     int nz, nr;              // cells
-    double dz, dr;
     double *x, *f, *r;       // (nz+1)(nr+1) nodes each
     double *ap, *am, *b;     // per radial node j: radial face and axial coefficients
 };
 
 struct FieldSolver {
-    int nlev = 0;
-    MGLevel lev[MG_MAX_LEVELS];
-    double* fv_over_verb = nullptr;   // per radial node: finite-volume / Verboncoeur volume
-    double* verb_base = nullptr;      // per radial node: Verboncoeur volume of an interior row
-    double* red = nullptr;            // reduction scratch
-    double* host_red = nullptr;       // pinned host copy
-    double weight = 0, tol = 1e-8, V0 = 0;
+    int nruns = 0;
+    int max_levels = 0;                 // deepest hierarchy over the runs
+    std::vector<int> nlev;              // levels of each run
+    std::vector<MGLevel> host_lev;      // [run * MG_MAX_LEVELS + l]
+    MGLevel* lev = nullptr;             // device copy of host_lev
+    int* nlev_dev = nullptr;            // [nruns]
+    double* fv_over_verb = nullptr;     // per run and radial node: finite-volume / Verboncoeur volume
+    double* verb_base = nullptr;        // per run and radial node: Verboncoeur volume of an interior row
+    int* fvb_off = nullptr;             // [nruns] offset of a run's radial tables
+    double* red = nullptr;              // [nruns][RED_BLOCKS][2] partial norms
+    double* bnorm = nullptr;            // [nruns]
+    int* done = nullptr;                // [nruns] converged flags
+    int* host_done = nullptr;           // pinned copy
+    double* tol = nullptr;              // [nruns]
     int max_cycles = 60;
-    int nz = 0, nr = 0;
+    int max_nodes0 = 0;                 // largest level-0 node count
+    double* dzr = nullptr;              // [nruns][2] cell sizes dz, dr
 };
 
 bool field_grid_ok(int nz, int nr);
-size_t field_workspace_bytes(int nz, int nr);
-int field_init(FieldSolver& fs, const pd_config& c, void* ws, size_t bytes, cudaStream_t s);
-// rho_e + rho_h (fixed point) -> phi (warm-started from its current value) -> E;
-// the anode potential is DevState::V.  Records relres / cycles in DevState.
+// bytes for the runs' grids (cells per run)
+size_t field_workspace_bytes(const std::vector<int>& nz, const std::vector<int>& nr);
+// phi: the simulation's node potential, runs laid end to end at node_base
+int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::vector<uint32_t>& node_base,
+               double* phi, void* ws, size_t bytes, cudaStream_t s);
 void field_free(FieldSolver& fs);
+// rho_e + rho_h (fixed point) -> phi (warm-started from its current value) -> E
+// for every run; the anode potential of each run is RunState::V.  With
+// host_check, V-cycles run until every run reaches its tolerance (the host
+// reads the flags between cycles); otherwise exactly `cycles` V-cycles are
+// issued with no host synchronisation (runs already converged skip them),
+// so the solve can be captured in a CUDA graph.  Records relres / cycles.
 int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
-                DevState* st, cudaStream_t s);
+                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s);
+
+// E = -grad(phi) of every run; flags runs whose solve met a non-finite value
+void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, cudaStream_t s);
 
 }  // namespace pd

@@ -32,12 +32,18 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
               C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, NCOUNTERS = 28;
 
-// Device-resident scalars of one simulation.
+// Device-resident scalars shared by all runs of a simulation.
 struct DevState {
     unsigned long long n_slots;      // slots of buffer A in use (live + dead)
     unsigned long long n_active;     // cells with collision candidates this step
-    unsigned int id_next;            // next particle id
     unsigned int error;              // ERR_* bits
+    unsigned int load_bad;           // set by a device load that met an out-of-range particle
+    unsigned int step;               // electron step index (Philox counter word), advanced by finalize
+    unsigned int pad0;
+};
+
+// Device-resident scalars of one run (an ensemble holds several runs).
+struct RunState {
     unsigned long long ctr[NCOUNTERS];
     double absorbed_energy[3];
     double charge_cathode;           // C through the cathode
@@ -46,15 +52,21 @@ struct DevState {
     double I_gap;                    // last step's gap current
     double relres;                   // last Poisson relative residual
     double cycles;                   // last Poisson cycles
-    unsigned int load_bad;           // set by a device load that met an out-of-range particle
+    unsigned int id_next;            // next particle id of the run
     unsigned int pad0;
 };
 
-// Per-species push constants (float, computed on the host in double then rounded).
-struct PushConsts {
+// Per-run constants.  The runs' cells and nodes are laid end to end in one
+// global index space: global cell = cell_base + iz * nr + ir.
+struct RunInfo {
+    int nz, nr, nzn, nrn;            // cells and nodes along z and r
+    float inv_nr;                    // 1 / nr (cell decoding estimate)
+    uint32_t cell_base, node_base, ncell;
+    uint32_t seed, run;              // Philox key of the run
+    uint32_t ck_base;                // c_k(j) of the run at ck[ck_base + k * nr + j]
     float qmdt[NSP];                 // z e / m * dt_s
     float dtz[NSP], dtr[NSP];        // dt_s / dz, dt_s / dr
-    float mass_w[NSP];               // unused in kernels; kept for layout stability
+    double weight;
 };
 
 // Collision constants (float; see the host's derivation).
@@ -72,22 +84,23 @@ struct Particles {
     uint32_t* id;
 };
 
-// Geometry / run parameters passed by value to the kernels.
+// Launch-wide parameters passed by value to the kernels.
 struct KParams {
     int geom;                        // 0 r-z, 1 periodic
-    int nz, nr;
-    int nzn, nrn;                    // node grid
-    uint32_t ncell;                  // nz * nr
-    float inv_nr;                    // 1 / nr (cell decoding estimate)
-    uint32_t seed, run;
+    int nruns;
+    uint32_t ncell;                  // cells of all runs
     uint32_t step;
     int heavy_step;
     int field_on;                    // gather E in the push
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
-    double weight;
     double masses[NSP];
+    const RunInfo* runs;             // [nruns]
+    const uint16_t* cell_run;        // run of each global cell (nruns > 1)
+    RunState* rs;                    // [nruns]
 };
+
+constexpr int MAX_RUNS_SMEM = 128;   // kernels stage up to this many RunInfo in shared memory
 
 // ---------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the 4x32 S-box with
@@ -152,14 +165,20 @@ __device__ __forceinline__ uint32_t converted_key(uint32_t new_sp, uint32_t old_
 
 __device__ __forceinline__ int charge_of(int sp) { return sp == SP_E ? -1 : (sp == SP_CU ? 0 : (sp == SP_CUP ? 1 : 2)); }
 
-// node index of (i, j); periodic wrap in the Cartesian mode
-__device__ __forceinline__ uint32_t node_of(const KParams& P, int i, int j) {
-    if (P.geom != 0) {
-        if (i >= P.nz) i -= P.nz;
-        if (j >= P.nr) j -= P.nr;
-        return (uint32_t)i * (uint32_t)P.nr + (uint32_t)j;
+// global node index of local node (i, j) of a run; periodic wrap in the
+// Cartesian mode
+__device__ __forceinline__ uint32_t node_of(const RunInfo& R, int geom, int i, int j) {
+    if (geom != 0) {
+        if (i >= R.nz) i -= R.nz;
+        if (j >= R.nr) j -= R.nr;
+        return R.node_base + (uint32_t)i * (uint32_t)R.nr + (uint32_t)j;
     }
-    return (uint32_t)i * (uint32_t)P.nrn + (uint32_t)j;
+    return R.node_base + (uint32_t)i * (uint32_t)R.nrn + (uint32_t)j;
+}
+
+// run of a global cell
+__device__ __forceinline__ int run_of(const KParams& P, uint32_t gcell) {
+    return P.nruns == 1 ? 0 : (int)P.cell_run[gcell];
 }
 
 __device__ __forceinline__ void set_error(DevState* st, uint32_t bits) { atomicOr(&st->error, bits); }

@@ -9,32 +9,48 @@ constexpr uint32_t SCAN_TILE = SCAN_THREADS * 8;   // elements per scan block
 
 inline uint32_t scan_padded(uint64_t n) { return (uint32_t)((n + SCAN_TILE - 1) / SCAN_TILE * SCAN_TILE); }
 
+// external circuit of one run
+struct RunCircuit {
+    double V0, R_ohm, C_farad;
+};
+
+// cathode injection constants of one run (ntip = 0: emission off)
+struct InjectConsts {
+    int ntip;                 // tip cells (r index 0 .. ntip-1)
+    double area[64];          // emitting area of each tip cell (m^2)
+    float lo[64], hi[64];     // radial extent of each tip cell in cell units
+    double dt, weight, beta, work, ratio;
+    float vth;                // thermal speed of the neutrals
+};
+
 // push + deposit + mover bookkeeping (see pd_stream.cu)
 void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
                  uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
-                 const KParams& P, const PushConsts& pc, int grid, cudaStream_t s);
+                 const KParams& P, int grid, cudaStream_t s);
 void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
                      uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s);
-void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
-                    int grid, cudaStream_t s);
 void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
                     const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
                     DevState* st, const KParams& P, int grid, cudaStream_t s);
+void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
+                    int grid, cudaStream_t s);
 // exclusive scan of n_padded (multiple of SCAN_TILE) u32; out has n_padded + 1
 // entries, out[n_padded] = total; partial needs n_padded / SCAN_TILE + 1 entries
 void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
 // the same over the population counts of the input words
 void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
-void launch_species_count(const Particles& A, DevState* st, unsigned long long* out, int grid, cudaStream_t s);
-void launch_density(const Particles& A, DevState* st, const KParams& P, int species, long long* acc, int grid,
-                    cudaStream_t s);
-void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int species, double lo, double hi,
+// diagnostics of one run
+void launch_species_count(const Particles& A, DevState* st, const KParams& P, int run, unsigned long long* out,
+                          int grid, cudaStream_t s);
+void launch_density(const Particles& A, DevState* st, const KParams& P, int run, int species, long long* acc,
+                    int grid, cudaStream_t s);
+void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int run, int species, double lo, double hi,
                      int nbins, unsigned long long* hist, int grid, cudaStream_t s);
 
-// device-array load: keys and ids of n new particles; *bad set on a bad input
+// device-array load: keys and ids of n new particles of one run; *bad set on a bad input
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
-                      int64_t n, int nz, int nr, uint32_t id0, uint32_t* key, uint32_t* id, unsigned int* bad,
-                      int grid, cudaStream_t s);
+                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t* key, uint32_t* id,
+                      unsigned int* bad, int grid, cudaStream_t s);
 
 // collisions
 void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
@@ -43,21 +59,11 @@ void launch_collide(const Particles& A, const uint32_t* off, const uint2* nc, co
                     const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h, const float* xsE,
                     const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins, int grid,
                     cudaStream_t s);
-void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, uint32_t ncell, DevState* st,
-                     const KParams& P, double dt, double V0, double R_ohm, double C_farad, int circuit,
-                     cudaStream_t s);
+void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
+                     const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 
-// cathode injection
-struct InjectConsts {
-    int ntip;                 // tip cells (r index 0 .. ntip-1)
-    double area[64];          // emitting area of each tip cell (m^2)
-    float lo[64], hi[64];     // radial extent of each tip cell in cell units
-    double dt, weight, beta, work, ratio;
-    float vth;                // thermal speed of the neutrals
-};
-void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts& ic,
+// cathode injection, one block per run
+void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts* ic,
                    const float* ray, cudaStream_t s);
 
-// field
-struct FieldSolver;
 }  // namespace pd

@@ -15,6 +15,7 @@ namespace pd {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 
+// deposit of every live particle without moving (state before the first step)
 __global__ void __launch_bounds__(256) k_deposit(Particles A, long long* rho_e, long long* rho_h, DevState* st,
                                                  KParams P) {
     const unsigned long long n = st->n_slots;
@@ -25,19 +26,23 @@ __global__ void __launch_bounds__(256) k_deposit(Particles A, long long* rho_e, 
         const unsigned long long i = i0 + lane;
         const uint32_t key = i < n ? A.key[i] : DEAD;
         const bool live = key != DEAD;
-        const int sp = (int)key_species(key);
-        const uint32_t cell = key_cell(key);
+        const int sp = live ? (int)key_species(key) : 0;
+        const uint32_t gcell = live ? key_cell(key) : 0u;
+        const RunInfo& RI = P.runs[run_of(P, gcell)];
         int iz = 0, ir = 0;
         float pz = 0.f, pr = 0.f;
         const int zq = live ? charge_of(sp) : 0;
         if (live && zq != 0) {
-            iz = (int)(cell / (uint32_t)P.nr);
-            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+            const uint32_t lc = gcell - RI.cell_base;
+            iz = (int)(lc / (uint32_t)RI.nr);
+            ir = (int)(lc - (uint32_t)iz * (uint32_t)RI.nr);
             pz = A.pz[i];
             pr = A.pr[i];
         }
-        warp_deposit(rho_e, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp == SP_E);
-        warp_deposit(rho_h, P, key, iz, ir, pz, pr, zq, live && zq != 0 && sp != SP_E);
+        // group lanes by key, which fixes the run, species and cell
+        const uint32_t k = live ? make_key((uint32_t)sp, gcell) : DEAD;
+        warp_deposit(rho_e, RI, P.geom, k, iz, ir, pz, pr, zq, live && zq != 0 && sp == SP_E);
+        warp_deposit(rho_h, RI, P.geom, k, iz, ir, pz, pr, zq, live && zq != 0 && sp != SP_E);
     }
 }
 
@@ -138,17 +143,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* __re
 // ---------------------------------------------------------------------
 // diagnostics
 // ---------------------------------------------------------------------
-// live particles per species: per-warp ballot counts, one atomic per warp
-// and species at the end
-__global__ void k_species_count(Particles A, DevState* st, unsigned long long* out) {
+// particle slot i belongs to run `run` (cells [cell_base, cell_base + ncell))
+__device__ __forceinline__ bool in_run(uint32_t key, const RunInfo& RI) {
+    if (key == DEAD) return false;
+    const uint32_t c = key_cell(key);
+    return c >= RI.cell_base && c < RI.cell_base + RI.ncell;
+}
+
+// live particles of one run per species: per-warp ballot counts, one atomic
+// per warp and species at the end
+__global__ void k_species_count(Particles A, DevState* st, KParams P, int run, unsigned long long* out) {
     const unsigned long long n = st->n_slots;
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const RunInfo RI = P.runs[run];
     unsigned long long c[NSP] = {0, 0, 0, 0, 0};
     for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
          i0 += stride) {
         const unsigned long long i = i0 + lane;
-        const uint32_t sp = i < n ? key_species(A.key[i]) : 255u;
+        const uint32_t key = i < n ? A.key[i] : DEAD;
+        const uint32_t sp = in_run(key, RI) ? key_species(key) : 255u;
 #pragma unroll
         for (int s = 0; s < NSP; ++s) c[s] += (unsigned)__popc(__ballot_sync(FULL, sp == (uint32_t)s));
     }
@@ -157,36 +171,38 @@ __global__ void k_species_count(Particles A, DevState* st, unsigned long long* o
             if (c[s]) atomicAdd(&out[s], c[s]);
 }
 
-__global__ void k_density(Particles A, DevState* st, KParams P, int species, long long* acc) {
+__global__ void k_density(Particles A, DevState* st, KParams P, int run, int species, long long* acc) {
     const unsigned long long n = st->n_slots;
     const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const RunInfo RI = P.runs[run];
     for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
          i0 += stride) {
         const unsigned long long i = i0 + lane;
         const uint32_t key = i < n ? A.key[i] : DEAD;
-        const bool on = key != DEAD && (int)key_species(key) == species;
+        const bool on = in_run(key, RI) && (int)key_species(key) == species;
         int iz = 0, ir = 0;
         float pz = 0.f, pr = 0.f;
         if (on) {
-            const uint32_t cell = key_cell(key);
-            iz = (int)(cell / (uint32_t)P.nr);
-            ir = (int)(cell - (uint32_t)iz * (uint32_t)P.nr);
+            const uint32_t lc = key_cell(key) - RI.cell_base;
+            iz = (int)(lc / (uint32_t)RI.nr);
+            ir = (int)(lc - (uint32_t)iz * (uint32_t)RI.nr);
             pz = A.pz[i];
             pr = A.pr[i];
         }
-        warp_deposit(acc, P, key, iz, ir, pz, pr, 1, on);
+        warp_deposit(acc, RI, P.geom, on ? make_key((uint32_t)species, key_cell(key)) : DEAD, iz, ir, pz, pr, 1, on);
     }
 }
 
-__global__ void k_spectrum(Particles A, DevState* st, KParams P, int species, double lo, double hi, int nbins,
-                           unsigned long long* hist) {
+__global__ void k_spectrum(Particles A, DevState* st, KParams P, int run, int species, double lo, double hi,
+                           int nbins, unsigned long long* hist) {
     const unsigned long long n = st->n_slots;
     const double m = P.masses[species];
+    const RunInfo RI = P.runs[run];
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t key = A.key[i];
-        if (key == DEAD || (int)key_species(key) != species) continue;
+        if (!in_run(key, RI) || (int)key_species(key) != species) continue;
         const double vz = A.vz[i], vr = A.vr[i], vt = A.vt[i];
         const double v2 = vz * vz + vr * vr + vt * vt;
         const double e = 0.5 * m * v2 / 1.602176634e-19;
@@ -199,8 +215,8 @@ __global__ void k_spectrum(Particles A, DevState* st, KParams P, int species, do
 
 __global__ void k_pack_keys(const uint8_t* __restrict__ sp, const int32_t* __restrict__ iz,
                             const int32_t* __restrict__ ir, const float* __restrict__ pz,
-                            const float* __restrict__ pr, long long n, int nz, int nr, uint32_t id0, uint32_t* key,
-                            uint32_t* id, unsigned int* bad) {
+                            const float* __restrict__ pr, long long n, int nz, int nr, uint32_t cell_base, uint32_t id0,
+                            uint32_t* key, uint32_t* id, unsigned int* bad) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const int a = iz[q], b = ir[q];
         const uint32_t s = sp[q];
@@ -208,7 +224,7 @@ __global__ void k_pack_keys(const uint8_t* __restrict__ sp, const int32_t* __res
         const bool ok = s < NSP && a >= 0 && a < nz && b >= 0 && b < nr && fz >= 0.0f && fz < 1.0f && fr >= 0.0f &&
                         fr < 1.0f;
         if (!ok) atomicOr(bad, 1u);
-        key[q] = ok ? make_key(s, (uint32_t)a * (uint32_t)nr + (uint32_t)b) : DEAD;
+        key[q] = ok ? make_key(s, cell_base + (uint32_t)a * (uint32_t)nr + (uint32_t)b) : DEAD;
         id[q] = id0 + (uint32_t)q;
     }
 }
@@ -233,20 +249,21 @@ void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint
     k_scan_down<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
 }
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
-                      int64_t n, int nz, int nr, uint32_t id0, uint32_t* key, uint32_t* id, unsigned int* bad,
-                      int grid, cudaStream_t s) {
-    k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, id0, key, id, bad);
+                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t* key, uint32_t* id,
+                      unsigned int* bad, int grid, cudaStream_t s) {
+    k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, cell_base, id0, key, id, bad);
 }
-void launch_species_count(const Particles& A, DevState* st, unsigned long long* out, int grid, cudaStream_t s) {
-    k_species_count<<<grid, 256, 0, s>>>(A, st, out);
+void launch_species_count(const Particles& A, DevState* st, const KParams& P, int run, unsigned long long* out,
+                          int grid, cudaStream_t s) {
+    k_species_count<<<grid, 256, 0, s>>>(A, st, P, run, out);
 }
-void launch_density(const Particles& A, DevState* st, const KParams& P, int species, long long* acc, int grid,
-                    cudaStream_t s) {
-    k_density<<<grid, 256, 0, s>>>(A, st, P, species, acc);
+void launch_density(const Particles& A, DevState* st, const KParams& P, int run, int species, long long* acc,
+                    int grid, cudaStream_t s) {
+    k_density<<<grid, 256, 0, s>>>(A, st, P, run, species, acc);
 }
-void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int species, double lo, double hi,
+void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int run, int species, double lo, double hi,
                      int nbins, unsigned long long* hist, int grid, cudaStream_t s) {
-    k_spectrum<<<grid, 256, 0, s>>>(A, st, P, species, lo, hi, nbins, hist);
+    k_spectrum<<<grid, 256, 0, s>>>(A, st, P, run, species, lo, hi, nbins, hist);
 }
 
 }  // namespace pd

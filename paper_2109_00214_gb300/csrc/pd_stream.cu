@@ -38,14 +38,14 @@ __device__ __forceinline__ T pick5(const T (&a)[NSP], int sp) {
 __device__ __forceinline__ float lane_of(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ uint32_t lane_of(const uint4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
-// cell -> (iz, ir) without an integer division: the float estimate is within
-// one of the quotient for cell < 2^24 and nr >= 2; fix it without branches
-__device__ __forceinline__ void decode_cell(uint32_t cell, const KParams& P, int& iz, int& ir) {
-    int q = (int)((float)cell * P.inv_nr);
-    int r = (int)cell - q * P.nr;
-    const int lo = r < 0 ? 1 : 0, hi = r >= P.nr ? 1 : 0;
+// local cell -> (iz, ir) without an integer division: the float estimate is
+// within one of the quotient for cell < 2^24 and nr >= 2; fix it without branches
+__device__ __forceinline__ void decode_cell(uint32_t cell, int nr, float inv_nr, int& iz, int& ir) {
+    int q = (int)((float)cell * inv_nr);
+    int r = (int)cell - q * nr;
+    const int lo = r < 0 ? 1 : 0, hi = r >= nr ? 1 : 0;
     q += hi - lo;
-    r += (lo - hi) * P.nr;
+    r += (lo - hi) * nr;
     iz = q;
     ir = r;
 }
@@ -77,11 +77,15 @@ template <bool RZ, bool FIELD>
 __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
                                                uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
-                                               DevState* st, KParams P, PushConsts pc) {
+                                               DevState* st, KParams P) {
+    __shared__ RunInfo s_runs[MAX_RUNS_SMEM];
+    for (int r = threadIdx.x; r < P.nruns; r += blockDim.x) s_runs[r] = P.runs[r];
+    __syncthreads();
     const uint32_t n = (uint32_t)st->n_slots;
     const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
     const uint32_t stride = gridDim.x * blockDim.x;
+    const int geom = RZ ? 0 : 1;
     uint4* key4 = reinterpret_cast<uint4*>(A.key);
     float4* pz4 = reinterpret_cast<float4*>(A.pz);
     float4* pr4 = reinterpret_cast<float4*>(A.pr);
@@ -91,40 +95,43 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x % 32u < nv; g += stride) {
         const bool gv = g < nv;
         uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD);
-        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
+        float4 Z = make_float4(0, 0, 0, 0), R4 = Z, VZ = Z, VR = Z, VT = Z;
         if (gv) {
             K = key4[g];
             Z = pz4[g];
-            R = pr4[g];
+            R4 = pr4[g];
             VZ = vz4[g];
             VR = vr4[g];
             if (RZ) VT = vt4[g];
         }
         uint32_t ko[4], key[4], newbin[4], oldbin[4];
-        float zo[4], ro[4], vzo[4], vro[4], vto[4], dz_[4], dr_[4];
-        int sp_[4], iz_[4], ir_[4], wall_[4];
-        bool keep[4], mover[4], inmv[4], dep[4], absd[4], moved[4];
+        float zo[4], ro[4], vzo[4], vro[4], vto[4];
+        int sp_[4], iz_[4], ir_[4], wall_[4], run_[4];
+        bool mover[4], inmv[4], dep[4], absd[4];
         uint32_t flags = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t i = 4u * g + (uint32_t)q;
             const uint32_t key_in = (gv && i < n) ? lane_of(K, q) : DEAD;
-            const float pz = lane_of(Z, q), pr = lane_of(R, q);
+            const float pz = lane_of(Z, q), pr = lane_of(R4, q);
             float vz = lane_of(VZ, q), vr = lane_of(VR, q), vt = lane_of(VT, q);
             const bool live = key_in != DEAD;
             const int sp = live ? (int)key_species(key_in) : 0;
+            const uint32_t gcell_in = live ? key_cell(key_in) : 0u;
+            const int r = live ? run_of(P, gcell_in) : 0;
+            const RunInfo& RI = s_runs[r];
             const bool in_sorted = live && i < n_sorted;
-            oldbin[q] = in_sorted ? key_sorted_species(key_in) * P.ncell + key_cell(key_in) : NOBIN;
+            oldbin[q] = in_sorted ? key_sorted_species(key_in) * P.ncell + gcell_in : NOBIN;
             const bool move = live && (sp == SP_E || P.heavy_step);
-            const uint32_t cell_in = move ? key_cell(key_in) : 0u;   // dead lanes read a valid node
+            const uint32_t lcell = move ? gcell_in - RI.cell_base : 0u;   // dead lanes read a valid node
             int iz, ir;
-            decode_cell(cell_in, P, iz, ir);
-            const float qmdt = pick5(pc.qmdt, sp), dtz = pick5(pc.dtz, sp), dtr = pick5(pc.dtr, sp);
+            decode_cell(lcell, RI.nr, RI.inv_nr, iz, ir);
+            const float qmdt = RI.qmdt[sp], dtz = RI.dtz[sp], dtr = RI.dtr[sp];
             if (FIELD) {
                 const float gz = 1.0f - pz, gr = 1.0f - pr;
                 const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
-                const float2 e00 = E[node_of(P, iz, ir)], e10 = E[node_of(P, iz + 1, ir)];
-                const float2 e01 = E[node_of(P, iz, ir + 1)], e11 = E[node_of(P, iz + 1, ir + 1)];
+                const float2 e00 = E[node_of(RI, geom, iz, ir)], e10 = E[node_of(RI, geom, iz + 1, ir)];
+                const float2 e01 = E[node_of(RI, geom, iz, ir + 1)], e11 = E[node_of(RI, geom, iz + 1, ir + 1)];
                 const float ez = ((w00 * e00.x + w10 * e10.x) + w01 * e01.x) + w11 * e11.x;
                 const float er = ((w00 * e00.y + w10 * e10.y) + w01 * e01.y) + w11 * e11.y;
                 vz = vz + qmdt * ez;
@@ -152,44 +159,42 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 nir = (int)fr;
                 npr = rr - fr;
                 npr = npr >= 1.0f ? 0x1.fffffep-1f : npr;
-                out = niz < 0 || niz >= P.nz || nir >= P.nr;
+                out = niz < 0 || niz >= RI.nz || nir >= RI.nr;
                 // cathode (z = 0) before anode (z = L) before the outer wall (r = R)
-                wall_[q] = niz < 0 ? 0 : (niz >= P.nz ? 1 : 2);
+                wall_[q] = niz < 0 ? 0 : (niz >= RI.nz ? 1 : 2);
             } else {
                 wall_[q] = 0;
-                const float r = pr + vr * dtr;
-                const float fr = floorf(r);
+                const float rr = pr + vr * dtr;
+                const float fr = floorf(rr);
                 nir = ir + (int)fr;
-                npr = r - fr;
+                npr = rr - fr;
                 npr = npr >= 1.0f ? 0x1.fffffep-1f : npr;
                 // a particle crosses at most one period per step (|v dt| < one domain)
-                niz = wrap1(niz, P.nz);
-                nir = wrap1(nir, P.nr);
+                niz = wrap1(niz, RI.nz);
+                nir = wrap1(nir, RI.nr);
             }
             const bool absorbed = move && out;
             const bool kp = live && !absorbed;
-            const uint32_t cell = move ? (uint32_t)niz * (uint32_t)P.nr + (uint32_t)nir : key_cell(key_in);
-            const uint32_t k = kp ? make_key((uint32_t)sp, cell) : DEAD;
-            const uint32_t nb = kp ? (uint32_t)sp * P.ncell + cell : NOBIN;
+            const uint32_t gcell =
+                move ? RI.cell_base + (uint32_t)niz * (uint32_t)RI.nr + (uint32_t)nir : gcell_in;
+            const uint32_t k = kp ? make_key((uint32_t)sp, gcell) : DEAD;
+            const uint32_t nb = kp ? (uint32_t)sp * P.ncell + gcell : NOBIN;
             const bool mvq = in_sorted && nb != oldbin[q];
             const bool inq = kp && (!in_sorted || nb != oldbin[q]);
             const bool mk = move && kp;
             ko[q] = live ? k : lane_of(K, q);
             key[q] = k;
             newbin[q] = nb;
-            keep[q] = kp;
             mover[q] = mvq;
             inmv[q] = inq;
             absd[q] = absorbed;
-            moved[q] = mk;
             zo[q] = mk ? npz : pz;
             ro[q] = mk ? npr : pr;
             vzo[q] = move ? vz : lane_of(VZ, q);
             vro[q] = move ? vr : lane_of(VR, q);
             vto[q] = move ? vt : lane_of(VT, q);
-            dz_[q] = zo[q];
-            dr_[q] = ro[q];
             sp_[q] = sp;
+            run_[q] = r;
             iz_[q] = mk ? niz : iz;
             ir_[q] = mk ? nir : ir;
             dep[q] = mk && charge_of(sp) != 0;
@@ -203,13 +208,14 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 if (!absd[q]) continue;
                 const int sp = sp_[q];
                 const int electrode = wall_[q];
+                RunState& rs = P.rs[run_[q]];
                 const double v2 = (double)vzo[q] * vzo[q] + (double)vro[q] * vro[q] + (double)vto[q] * vto[q];
-                const double ke = P.weight * (0.5 * pick5(P.masses, sp) * v2);
-                atomicAdd(&st->ctr[C_ABS + electrode * NSP + sp], 1ull);
-                atomicAdd(&st->absorbed_energy[electrode], ke);
-                const double qw = (double)charge_of(sp) * 1.602176634e-19 * P.weight;
-                if (electrode == 1) atomicAdd(&st->anode_charge_step, qw);
-                if (electrode == 0) atomicAdd(&st->charge_cathode, qw);
+                const double ke = s_runs[run_[q]].weight * (0.5 * pick5(P.masses, sp) * v2);
+                atomicAdd(&rs.ctr[C_ABS + electrode * NSP + sp], 1ull);
+                atomicAdd(&rs.absorbed_energy[electrode], ke);
+                const double qw = (double)charge_of(sp) * 1.602176634e-19 * s_runs[run_[q]].weight;
+                if (electrode == 1) atomicAdd(&rs.anode_charge_step, qw);
+                if (electrode == 0) atomicAdd(&rs.charge_cathode, qw);
             }
         }
         if (wflags & 2u) {          // movers out of their sorted bin
@@ -236,8 +242,8 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
             unsigned long long W[4][4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t wz = __float2uint_rn(dz_[q] * 65536.0f);
-                const uint32_t wr = __float2uint_rn(dr_[q] * 65536.0f);
+                const uint32_t wz = __float2uint_rn(zo[q] * 65536.0f);
+                const uint32_t wr = __float2uint_rn(ro[q] * 65536.0f);
                 const unsigned long long az = 65536u - wz, ar = 65536u - wr;
                 W[q][0] = dep[q] ? az * ar : 0ull;
                 W[q][1] = dep[q] ? (unsigned long long)wz * ar : 0ull;
@@ -255,11 +261,15 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 if (!len[q]) continue;
                 const long long zq = charge_of(sp_[q]);
                 long long* rho = sp_[q] == SP_E ? rho_e : rho_h;
+                const RunInfo& RI = s_runs[run_[q]];
                 const int iz = iz_[q], ir = ir_[q];
-                atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir)], (unsigned long long)(zq * (long long)W[q][0]));
-                atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir)], (unsigned long long)(zq * (long long)W[q][1]));
-                atomicAdd((unsigned long long*)&rho[node_of(P, iz, ir + 1)], (unsigned long long)(zq * (long long)W[q][2]));
-                atomicAdd((unsigned long long*)&rho[node_of(P, iz + 1, ir + 1)],
+                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)],
+                          (unsigned long long)(zq * (long long)W[q][0]));
+                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir)],
+                          (unsigned long long)(zq * (long long)W[q][1]));
+                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir + 1)],
+                          (unsigned long long)(zq * (long long)W[q][2]));
+                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir + 1)],
                           (unsigned long long)(zq * (long long)W[q][3]));
             }
         }
@@ -434,9 +444,9 @@ __global__ void __launch_bounds__(SCATTER_THREADS) k_scatter4(Particles A, Parti
 
 void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
                  uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
-                 const KParams& P, const PushConsts& pc, int grid, cudaStream_t s) {
+                 const KParams& P, int grid, cudaStream_t s) {
     const bool rz = P.geom == 0, field = P.field_on != 0;
-#define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, old_off, nbins, st, P, pc
+#define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, old_off, nbins, st, P
     if (rz && field) k_push4<true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
     else if (rz) k_push4<true, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
     else if (field) k_push4<false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);

@@ -24,8 +24,9 @@ __device__ __forceinline__ void warp_count(uint32_t* count, uint32_t bin, bool o
 // weights (2^16 - w_z)(2^16 - w_r), w_z (2^16 - w_r), (2^16 - w_z) w_r, w_z w_r
 // (they sum to 2^32).  Lanes holding the same key (species and cell) are
 // summed first: each weight is split in 16-bit halves so the warp sums fit in
-// 32 bits, then one 64-bit atomic per node and group.
-__device__ __forceinline__ void warp_deposit(long long* rho, const KParams& P, uint32_t key, int iz, int ir,
+// 32 bits, then one 64-bit atomic per node and group.  (iz, ir) are local to
+// the run RI.
+__device__ __forceinline__ void warp_deposit(long long* rho, const RunInfo& RI, int geom, uint32_t key, int iz, int ir,
                                              float pz, float pr, int zq, bool on) {
     const unsigned m = __ballot_sync(FULL_MASK, on);
     if (!on) return;
@@ -36,8 +37,8 @@ __device__ __forceinline__ void warp_deposit(long long* rho, const KParams& P, u
     const unsigned long long W[4] = {az * ar, (unsigned long long)wz * ar, az * (unsigned long long)wr,
                                      (unsigned long long)wz * wr};
     const bool leader = (threadIdx.x & 31) == (unsigned)(__ffs(g) - 1);
-    const uint32_t nodes[4] = {node_of(P, iz, ir), node_of(P, iz + 1, ir), node_of(P, iz, ir + 1),
-                               node_of(P, iz + 1, ir + 1)};
+    const uint32_t nodes[4] = {node_of(RI, geom, iz, ir), node_of(RI, geom, iz + 1, ir), node_of(RI, geom, iz, ir + 1),
+                               node_of(RI, geom, iz + 1, ir + 1)};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t hi = __reduce_add_sync(g, (uint32_t)(W[k] >> 16));
