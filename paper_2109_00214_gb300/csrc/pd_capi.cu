@@ -168,6 +168,7 @@ struct pd_sim {
     cudaGraphExec_t gexec;
     int64_t graph_steps;
     uint64_t graph_launches[PD_NKERNELS];
+    cudaStream_t capture_stream;
     bool any_inject;
     std::vector<uint16_t> h_cell_run;
     // profiling
@@ -189,6 +190,7 @@ pd_status fail(pd_sim* s, pd_status code, const std::string& msg) {
 }
 
 pd_status cuda_fail(pd_sim* s, cudaError_t e, const char* where) {
+    (void)cudaGetLastError();   // reported here: do not leave it to the caller's next CUDA call
     return fail(s, PD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -240,6 +242,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
     for (int k = 0; k < NSP; ++k) P.masses[k] = species_mass(k);
+    P.run0 = s->runs[0];
     P.runs = s->runs_dev;
     P.cell_run = s->cell_run;
     P.rs = s->rs;
@@ -527,11 +530,22 @@ pd_status build_graph(pd_sim* s) {
     cudaGraph_t g = nullptr;
     uint64_t before[PD_NKERNELS];
     std::memcpy(before, s->launches, sizeof(before));
-    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    // record on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    if (!s->capture_stream) CK(cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking));
+    CK(cudaStreamSynchronize(s->stream));
+    cudaStream_t user = s->stream;
+    s->stream = s->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        s->stream = user;
+        return cuda_fail(s, e, "cudaStreamBeginCapture");
+    }
     const int64_t step0 = s->step;
     pd_status r = PD_OK;
     for (int k = 0; k < G && r == PD_OK; ++k) r = issue_step(s, true);
-    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    e = cudaStreamEndCapture(s->stream, &g);
+    s->stream = user;
     s->step = step0;           // capture only recorded the steps
     for (int k = 0; k < PD_NKERNELS; ++k) {   // launches of one replay
         s->graph_launches[k] = s->launches[k] - before[k];
@@ -667,6 +681,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->graph_on = false;
     s->graph_cycles = 4;
     s->gexec = nullptr;
+    s->capture_stream = nullptr;
     s->graph_steps = 0;
     std::memset(s->launches, 0, sizeof(s->launches));
     // zero everything but the two particle buffers
@@ -1192,6 +1207,7 @@ void pd_destroy(pd_sim* s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
     drop_graph(s);
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     for (auto& r : s->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

@@ -95,6 +95,7 @@ struct KParams {
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
     double masses[NSP];
+    RunInfo run0;                    // runs[0] by value (the one run of a single simulation)
     const RunInfo* runs;             // [nruns]
     const uint16_t* cell_run;        // run of each global cell (nruns > 1)
     RunState* rs;                    // [nruns]

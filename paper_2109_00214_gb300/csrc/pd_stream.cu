@@ -73,14 +73,23 @@ __device__ __forceinline__ void runs4(const bool (&on)[4], const uint32_t (&key)
 
 constexpr uint32_t NOBIN = 0xFFFFFFFFu;
 
-template <bool RZ, bool FIELD>
+// per-species constant: shared-memory table (ensembles) or kernel parameter
+// (one run, selected without dynamic indexing)
+template <bool MULTI>
+__device__ __forceinline__ float spc(const float (&a)[NSP], int sp) {
+    return MULTI ? a[sp] : pick5(a, sp);
+}
+
+template <bool RZ, bool FIELD, bool MULTI>
 __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
                                                uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
                                                DevState* st, KParams P) {
-    __shared__ RunInfo s_runs[MAX_RUNS_SMEM];
-    for (int r = threadIdx.x; r < P.nruns; r += blockDim.x) s_runs[r] = P.runs[r];
-    __syncthreads();
+    __shared__ RunInfo s_runs[MULTI ? MAX_RUNS_SMEM : 1];
+    if (MULTI) {
+        for (int r = threadIdx.x; r < P.nruns; r += blockDim.x) s_runs[r] = P.runs[r];
+        __syncthreads();
+    }
     const uint32_t n = (uint32_t)st->n_slots;
     const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
     const uint32_t nv = (n + 3u) >> 2;
@@ -119,14 +128,14 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
             const int sp = live ? (int)key_species(key_in) : 0;
             const uint32_t gcell_in = live ? key_cell(key_in) : 0u;
             const int r = live ? run_of(P, gcell_in) : 0;
-            const RunInfo& RI = s_runs[r];
+            const RunInfo& RI = MULTI ? s_runs[r] : P.run0;
             const bool in_sorted = live && i < n_sorted;
             oldbin[q] = in_sorted ? key_sorted_species(key_in) * P.ncell + gcell_in : NOBIN;
             const bool move = live && (sp == SP_E || P.heavy_step);
             const uint32_t lcell = move ? gcell_in - RI.cell_base : 0u;   // dead lanes read a valid node
             int iz, ir;
             decode_cell(lcell, RI.nr, RI.inv_nr, iz, ir);
-            const float qmdt = RI.qmdt[sp], dtz = RI.dtz[sp], dtr = RI.dtr[sp];
+            const float qmdt = spc<MULTI>(RI.qmdt, sp), dtz = spc<MULTI>(RI.dtz, sp), dtr = spc<MULTI>(RI.dtr, sp);
             if (FIELD) {
                 const float gz = 1.0f - pz, gr = 1.0f - pr;
                 const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
@@ -210,10 +219,11 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 const int electrode = wall_[q];
                 RunState& rs = P.rs[run_[q]];
                 const double v2 = (double)vzo[q] * vzo[q] + (double)vro[q] * vro[q] + (double)vto[q] * vto[q];
-                const double ke = s_runs[run_[q]].weight * (0.5 * pick5(P.masses, sp) * v2);
+                const double w = MULTI ? s_runs[run_[q]].weight : P.run0.weight;
+                const double ke = w * (0.5 * pick5(P.masses, sp) * v2);
                 atomicAdd(&rs.ctr[C_ABS + electrode * NSP + sp], 1ull);
                 atomicAdd(&rs.absorbed_energy[electrode], ke);
-                const double qw = (double)charge_of(sp) * 1.602176634e-19 * s_runs[run_[q]].weight;
+                const double qw = (double)charge_of(sp) * 1.602176634e-19 * w;
                 if (electrode == 1) atomicAdd(&rs.anode_charge_step, qw);
                 if (electrode == 0) atomicAdd(&rs.charge_cathode, qw);
             }
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __rest
                 if (!len[q]) continue;
                 const long long zq = charge_of(sp_[q]);
                 long long* rho = sp_[q] == SP_E ? rho_e : rho_h;
-                const RunInfo& RI = s_runs[run_[q]];
+                const RunInfo& RI = MULTI ? s_runs[run_[q]] : P.run0;
                 const int iz = iz_[q], ir = ir_[q];
                 atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)],
                           (unsigned long long)(zq * (long long)W[q][0]));
@@ -447,10 +457,17 @@ void launch_push(const Particles& A, const float2* E, long long* rho_e, long lon
                  const KParams& P, int grid, cudaStream_t s) {
     const bool rz = P.geom == 0, field = P.field_on != 0;
 #define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, old_off, nbins, st, P
-    if (rz && field) k_push4<true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
-    else if (rz) k_push4<true, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
-    else if (field) k_push4<false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
-    else k_push4<false, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    if (P.nruns > 1) {
+        if (rz && field) k_push4<true, true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else if (rz) k_push4<true, false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else if (field) k_push4<false, true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else k_push4<false, false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    } else {
+        if (rz && field) k_push4<true, true, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else if (rz) k_push4<true, false, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else if (field) k_push4<false, true, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+        else k_push4<false, false, false><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
+    }
 #undef PD_PUSH_ARGS
 }
 
