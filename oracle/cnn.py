@@ -1,0 +1,192 @@
+"""CPU oracle of the learned Poisson warm start -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests may import this module.  Plain numpy in float64, written from
+the definitions below; it shares nothing with the CUDA library.
+
+The warm start is not part of the paper's method: it predicts the potential
+of Eq. (8) from the charge density so that the multigrid solve starts close
+to its answer.  Definitions used here (and by the library):
+
+Training pair of one r-z run (node arrays of shape (nz + 1, nr + 1)):
+    rho_max = max |rho|,  L = nz dz (the gap),  z_i = i dz
+    x = rho / rho_max                                  (0 where rho_max = 0)
+    phi_L = V z / L          (the charge-free solution of Eq. (8): linear in z)
+    t = (phi - phi_L) eps0 / (rho_max L^2)
+and the warm start built from a prediction y of t:
+    phi_0 = phi_L + y rho_max L^2 / eps0.
+
+Network: six 3 x 3 convolutions over the node grid, output the size of the
+input (zero padding), channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
+after the first five, one bias per output channel:
+    a_l[p, co] = b_l[co] + sum_{dy, dx, ci} W_l[tap(dy, dx), co, ci] h_{l-1}[p + (dy, dx), ci]
+    h_l = relu(a_l) (l < 6),  y = a_6,  tap(dy, dx) = 3 (dy + 1) + (dx + 1)
+with h_{l-1} = 0 outside the grid (cross-correlation, as in deep-learning
+convolutions).  Parameter vector: for l = 1..6 in order, W_l as
+[tap][co][ci] followed by b_l[co].
+
+Loss: mean over the batch and the nodes of (y - t)^2.
+
+Adam (Kingma and Ba, ICLR 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2)
+g^2, w -= lr (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps) at step k = 1, 2, ...
+
+bf16 mirror: with `bf16=True` the values are rounded to bfloat16 (round to
+nearest, ties to even) where the library stores bfloat16 -- the weights
+every layer uses, the activations h_1..h_5 and the loss gradients with
+respect to a_1..a_5 -- so that the two sides differ only by the order of
+their float sums.
+"""
+import numpy as np
+
+CH = 32
+LAYERS = ((1, CH), (CH, CH), (CH, CH), (CH, CH), (CH, CH), (CH, 1))   # (c_in, c_out)
+EPS0 = 8.8541878128e-12
+
+
+def layer_sizes():
+    """(weights, biases) counts of the six layers."""
+    return [(9 * co * ci, co) for ci, co in LAYERS]
+
+
+def n_params():
+    return sum(w + b for w, b in layer_sizes())
+
+
+def unpack(params):
+    """Parameter vector -> list of (W [9, co, ci], b [co]) per layer."""
+    params = np.asarray(params, dtype=np.float64)
+    out, o = [], 0
+    for ci, co in LAYERS:
+        W = params[o:o + 9 * co * ci].reshape(9, co, ci)
+        o += 9 * co * ci
+        b = params[o:o + co]
+        o += co
+        out.append((W, b))
+    assert o == params.size
+    return out
+
+
+def pack(layers):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers])
+
+
+def init_params(seed):
+    """He-normal weights, zero biases (a seeded starting point)."""
+    rng = np.random.default_rng(seed)
+    layers = []
+    for ci, co in LAYERS:
+        W = rng.standard_normal((9, co, ci)) * np.sqrt(2.0 / (9 * ci))
+        layers.append((W, np.zeros(co)))
+    return pack(layers)
+
+
+def round_bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return (r.astype(np.uint32)).view(np.float32).astype(np.float64)
+
+
+def shift(h, dy, dx):
+    """s[b, i, j, :] = h[b, i + dy, j + dx, :], zero outside the grid."""
+    B, H, W, C = h.shape
+    s = np.zeros_like(h)
+    i0, i1 = max(0, -dy), min(H, H - dy)
+    j0, j1 = max(0, -dx), min(W, W - dx)
+    s[:, i0:i1, j0:j1, :] = h[:, i0 + dy:i1 + dy, j0 + dx:j1 + dx, :]
+    return s
+
+
+TAPS = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
+def conv(h, W, b):
+    """a[p, co] = b[co] + sum_tap sum_ci W[tap, co, ci] h[p + tap, ci]."""
+    a = np.zeros(h.shape[:3] + (W.shape[1],)) + b
+    for tap, (dy, dx) in enumerate(TAPS):
+        a += shift(h, dy, dx) @ W[tap].T
+    return a
+
+
+def forward(params, x, bf16=False):
+    """x [B, H, W] -> (y [B, H, W], list of layer inputs h_0..h_5)."""
+    layers = unpack(params)
+    rnd = round_bf16 if bf16 else (lambda v: v)
+    h = np.asarray(x, dtype=np.float64)[..., None]
+    hs = [h]
+    for l, (W, b) in enumerate(layers):
+        a = conv(h, rnd(W), b)
+        if l < 5:
+            h = rnd(np.maximum(a, 0.0))
+            hs.append(h)
+        else:
+            y = a[..., 0]
+    return y, hs
+
+
+def loss(params, x, t, bf16=False):
+    y, _ = forward(params, x, bf16)
+    return float(np.mean((y - np.asarray(t, dtype=np.float64)) ** 2))
+
+
+def loss_and_grad(params, x, t, bf16=False):
+    """Mean squared error and its gradient by back-propagation, in the
+    parameter-vector layout."""
+    layers = unpack(params)
+    rnd = round_bf16 if bf16 else (lambda v: v)
+    y, hs = forward(params, x, bf16)
+    t = np.asarray(t, dtype=np.float64)
+    N = y.size
+    L = float(np.mean((y - t) ** 2))
+    g = (2.0 / N) * (y - t)[..., None]          # dL/da_6
+    grads = [None] * 6
+    for l in range(5, -1, -1):
+        W, _ = layers[l]
+        Wr = rnd(W)
+        h = hs[l]                                # input of layer l
+        gW = np.zeros_like(W)
+        for tap, (dy, dx) in enumerate(TAPS):
+            # dL/dW[tap, co, ci] = sum_p g[p, co] h[p + tap, ci]
+            gW[tap] = np.einsum("bijc,bijd->cd", g, shift(h, dy, dx))
+        gb = g.sum(axis=(0, 1, 2))
+        grads[l] = (gW, gb)
+        if l == 0:
+            break
+        # dL/dh[q, ci] = sum_tap sum_co W[tap, co, ci] g[q - tap, co]
+        gh = np.zeros(h.shape)
+        for tap, (dy, dx) in enumerate(TAPS):
+            gh += shift(g, -dy, -dx) @ Wr[tap]
+        g = rnd(gh * (h > 0.0))                  # through the ReLU of layer l - 1
+    return L, pack(grads)
+
+
+def adam_step(params, grad, m, v, k, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step k (1-based); returns new (params, m, v)."""
+    m = b1 * m + (1.0 - b1) * grad
+    v = b2 * v + (1.0 - b2) * grad * grad
+    mh = m / (1.0 - b1 ** k)
+    vh = v / (1.0 - b2 ** k)
+    return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def training_pair(rho, phi, V, dz):
+    """(x, t) of one run from its node density rho (C/m^3) and potential phi
+    (V), arrays of shape (nz + 1, nr + 1)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    nz = rho.shape[0] - 1
+    L = nz * dz
+    z = np.arange(nz + 1)[:, None] * dz
+    rmax = np.abs(rho).max()
+    if rmax == 0.0:
+        return np.zeros_like(rho), np.zeros_like(rho)
+    return rho / rmax, (phi - V * z / L) * EPS0 / (rmax * L * L)
+
+
+def warm_start(y, rho_max, V, dz):
+    """phi_0 from a prediction y of t."""
+    y = np.asarray(y, dtype=np.float64)
+    nz = y.shape[0] - 1
+    L = nz * dz
+    z = np.arange(nz + 1)[:, None] * dz
+    return V * z / L + y * rho_max * L * L / EPS0
