@@ -12,6 +12,14 @@ Metric: particle-updates/s (particles advanced by push + sort + collide per
 second).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload ensemble [--steps K] [--warmup W]
+
+--workload ensemble times the batched breakdown ensemble instead: 64 r-z runs
+(8 seeds x gap voltages 2-10 kV, grids 64^2..256^2 cells, 1e5..2e6 particles
+each, self-consistent Poisson field), advanced as one
+ensemble under a CUDA graph with autotuned launch shapes, against the plain
+method (the same 64 runs as separate simulations, one after another), both
+with every Poisson solve at or below the same relative residual.
 
 --impl reference times the CPU oracle (the plain restatement of the method)
 on a bounded sample of the same workload on this machine's host cores.
@@ -54,7 +62,15 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=512, help="rows of cells in the CPU-baseline sample")
     p.add_argument("--cpu-steps", type=int, default=10)
-    return p.parse_args()
+    p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble"])
+    p.add_argument("--no-autotune", action="store_true")
+    a = p.parse_args()
+    if a.workload == "ensemble":
+        if "--steps" not in sys.argv:
+            a.steps = 40
+        if "--warmup" not in sys.argv:
+            a.warmup = 10
+    return a
 
 
 def dist_setup(args):
@@ -202,11 +218,188 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+ENS_METRIC = "wall time per ensemble step at equal Poisson residual (64 breakdown runs)"
+
+
+def ensemble_updates(c0, c1, steps, heavy_subcycle):
+    """particle updates of `steps` steps: electrons every step, heavies on
+    their sub-cycle steps (mean of the start and end populations)"""
+    ne = 0.5 * (c0[0] + c1[0])
+    nh = 0.5 * (sum(c0[1:]) + sum(c1[1:]))
+    return steps * ne + (steps / heavy_subcycle) * nh
+
+
+def run_ensemble(args, ws, rank, local):
+    """Batched ensemble (one launch per kernel for all runs, CUDA graph,
+    autotuned shapes) against the plain method (one simulation per run, run
+    after run), at equal Poisson residual."""
+    import torch
+    import paper_2109_00214_gb300 as pd
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pd.load_library()
+    all_runs = synthetic.ensemble_breakdown()
+    runs = all_runs[rank::ws]                   # replicas: runs split across ranks, no collective
+    xs = synthetic.standin_cross_sections()
+    cfgs = [c for c, _ in runs]
+    R = len(runs)
+    tol = max(c["poisson_tol"] for c in cfgs)
+    G = 2 * cfgs[0]["heavy_subcycle"] if cfgs[0]["heavy_subcycle"] % 2 else cfgs[0]["heavy_subcycle"]
+    W = -(-args.warmup // G) * G
+    K = -(-args.steps // G) * G
+    hs = cfgs[0]["heavy_subcycle"]
+    keys = ("species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
+
+    def counts(get):
+        c = np.zeros(5)
+        for r in range(R):
+            c += np.array(get(r)["count"], dtype=np.float64)
+        return c
+
+    def timed(stream, fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        barrier(ws)
+        return e0.elapsed_time(e1), (t1 - t0) * 1e3
+
+    # ---- plain method: one simulation per run, run after run --------------
+    sims = []
+    for cfg, parts in runs:
+        sm = pd.Simulation(cfg, xs, device=dev)
+        sm.load_device({k: torch.from_numpy(parts[k]).to(dev) for k in keys})
+        sims.append(sm)
+    for sm in sims:
+        sm.step(W)
+    torch.cuda.synchronize()
+    c0 = counts(lambda r: sims[r].scalars())
+    plain_ms, plain_wall = timed(sims[0].stream, lambda: [sm.step(K) for sm in sims])
+    plain_sc = [sm.scalars() for sm in sims]
+    c1 = counts(lambda r: plain_sc[r])
+    plain_upd = ensemble_updates(c0, c1, K, hs)
+    plain_relres = max(sc["poisson_relres_max"] for sc in plain_sc)
+    plain_launches = 0
+    for sm in sims:
+        sm.close()
+    del sims
+    torch.cuda.empty_cache()
+
+    # ---- batched ensemble ---------------------------------------------------
+    ens = pd.Ensemble(cfgs, xs, device=dev)
+    for r, (_, parts) in enumerate(runs):
+        ens.load_run_device(r, {k: torch.from_numpy(parts[k]).to(dev) for k in keys})
+    tuning = None
+    if not args.no_autotune:
+        tuning = ens.autotune(2)
+    # eager warm-up with host-checked solves; per-kernel times of the last G steps
+    done = int(ens.run_scalars(0)["step"])      # steps the autotuner took
+    ens.step(W + (G - (done + W) % G) % G)      # end on a multiple of the graph period
+    ens.synchronize()
+    pd.pd_profile_read(ens.h)
+    pd.pd_profile_enable(ens.h, 1)
+    ens.step(G)
+    prof = pd.pd_profile_read(ens.h)
+    pd.pd_profile_enable(ens.h, 0)
+    cyc = max(ens.run_scalars(r)["poisson_cycles"] for r in range(R))
+    # graph mode: a fixed cycle count; raised until every solve of the timed
+    # steps reaches the tolerance
+    cycles = int(cyc) + 1
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if ws == 1 else str(local)
+    out_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    for attempt in range(4):
+        ens.set_graph_mode(1, cycles)
+        ens.step(G)                              # capture + one replay, untimed
+        ens.synchronize()
+        pd.pd_profile_read(ens.h)
+        c0 = counts(ens.run_scalars)
+        sampler = ClockSampler(gpu_index if gpu_index.isdigit() else local,
+                               os.path.join(out_dir, f"clocks_ensemble_rank{rank}.csv"))
+        ens_ms, ens_wall = timed(ens.stream, lambda: ens.step(K))
+        clocks = sampler.stop()
+        launches = int(sum(n for _, n in pd.pd_profile_read(ens.h).values()))
+        sc = [ens.run_scalars(r) for r in range(R)]
+        relres = max(x["poisson_relres_max"] for x in sc)
+        if relres <= tol:
+            break
+        cycles += 2
+    c1 = counts(lambda r: sc[r])
+    ens_upd = ensemble_updates(c0, c1, K, hs)
+    nparts = int(sum(c1))
+    ens.close()
+    del ens
+    torch.cuda.empty_cache()
+
+    # ---- end to end: host loads, K graph steps, per-run scalars back ------
+    e2e = None
+    if not args.no_e2e:
+        ens2 = pd.Ensemble(cfgs, xs, device=dev)
+        if tuning:
+            ens2.set_tuning(**tuning)
+        ens2.set_graph_mode(1, cycles)
+
+        def e2e_run():
+            for r, (_, parts) in enumerate(runs):
+                ens2.load_run(r, parts)
+            ens2.step(K)
+            return [ens2.run_scalars(r) for r in range(R)]
+        _, wall = timed(ens2.stream, e2e_run)
+        h2d = sum(25 * len(p["species"]) for _, p in runs)
+        e2e = {"value": max_over_ranks(ws, wall, dev) / K, "unit": "ms/step",
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": R * 256 / K}
+        ens2.close()
+        del ens2
+        torch.cuda.empty_cache()
+
+    ens_ms_max = max_over_ranks(ws, ens_ms, dev)
+    plain_ms_max = max_over_ranks(ws, plain_ms, dev)
+    upd_all = sum_over_ranks(ws, ens_upd, dev)
+    if rank == 0:
+        grids = {}
+        for c in cfgs:
+            grids[c["nz"]] = grids.get(c["nz"], 0) + 1
+        line = {"metric": ENS_METRIC, "value": ens_ms_max / K, "unit": "ms/step", "n_gpus": ws, "steps": K,
+                "warmup": W, "ms_per_step": ens_ms_max / K, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"batched breakdown ensemble: {len(all_runs)} r-z runs (8 seeds x "
+                                       f"{len(synthetic.ENSEMBLE_VOLTS_KV)} gap voltages 2-10 kV), grids "
+                                       f"{sorted(grids)} cells per side, 1e5..2e6 particles per run, "
+                                       f"Poisson to relres <= {tol:g}, plume start without cathode emission, dt = 1 fs",
+                           "runs_per_gpu": R, "grid_histogram": grids, "particles_per_gpu": nparts,
+                           "parallelism": f"runs split over {ws} replicas" if ws > 1 else "single",
+                           "l2": "particle store larger than L2; no flush"},
+                "batched": {"ms_per_step": ens_ms_max / K, "wall_ms_per_step": ens_wall / K,
+                            "poisson_cycles_fixed": cycles, "poisson_relres_max": relres,
+                            "particle_updates_per_s": upd_all / (ens_ms_max * 1e-3), "tuning": tuning,
+                            "eager_kernels_ms_per_step": {k: v[0] / G for k, v in prof.items() if v[1]}},
+                "plain": {"ms_per_step": plain_ms_max / K, "wall_ms_per_step": plain_wall / K,
+                          "poisson_relres_max": plain_relres,
+                          "particle_updates_per_s": sum_over_ranks(ws, plain_upd, dev) / (plain_ms_max * 1e-3),
+                          "method": "one simulation per run, stepped run after run, host-checked multigrid"},
+                "equal_residual": bool(relres <= tol and plain_relres <= tol),
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "ensemble":
+        run_ensemble(args, ws, rank, local)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     import torch
     import paper_2109_00214_gb300 as pd

@@ -98,6 +98,8 @@ typedef struct pd_scalars {
     double sgmax[2];           /* NTC majorants (sigma g)_max, (e,Cu), (e,Cu+) */
     double poisson_relres;     /* last solve's relative residual */
     double poisson_cycles;     /* last solve's multigrid cycles */
+    double poisson_relres_max; /* largest final relative residual of the solves
+                                  issued by the latest pd_step call */
     double absorbed_energy[3]; /* J absorbed at cathode, anode, outer wall */
     int64_t n_particles;       /* live particles */
     int64_t count[PD_NSP];     /* live particles per species */
@@ -178,6 +180,11 @@ pd_status pd_get_particles(pd_sim* sim, uint32_t* id, int32_t* run, uint8_t* spe
  * electrons and of the heavies. */
 pd_status pd_get_rho(pd_sim* sim, int64_t* rho_e, int64_t* rho_h);
 pd_status pd_get_phi(pd_sim* sim, double* phi);
+/* Training pairs of the Poisson solve (Eq. (8)): node charge density
+ * rho = e W (rho_e + rho_h) 2^-32 / V_node in C/m^3 (V_node: Verboncoeur's
+ * node volumes in r-z, dz dr depth in the Cartesian mode) and the node
+ * potential phi in V, both host arrays of all runs' nodes end to end. */
+pd_status pd_get_rho_phi(pd_sim* sim, double* rho, double* phi);
 pd_status pd_get_field(pd_sim* sim, double* Ez, double* Er);
 /* Number density (m^-3) of one species on the nodes (CIC / node volume). */
 pd_status pd_get_density_map(pd_sim* sim, int species, double* out);
@@ -241,6 +248,49 @@ pd_status pd_load_particles_device_run(pd_sim* sim, int run, int64_t n, const ui
  * the achieved residual is reported in pd_scalars.  Steps not aligned to G
  * run eagerly.  Changing cross sections or emission drops the graph. */
 pd_status pd_set_graph_mode(pd_sim* sim, int enable, int poisson_cycles);
+
+/* Launch shapes of the step's kernels.  Every one of these kernels walks its
+ * work with a grid-stride loop and writes results that do not depend on the
+ * order in which threads run (integer atomics, per-cell work, canonical id
+ * order), so a shape changes speed only, never a result.  Grids are given
+ * in blocks per SM (1..64); mg_threads is the block size of the multigrid
+ * level kernels (a multiple of 32 in 64..1024) and mg_max_blocks caps their
+ * blocks per run and level (1..65535).  pd_set_tuning validates and drops
+ * a captured graph. */
+typedef struct pd_tuning {
+    int push_blocks_per_sm;     /* push + gather + deposit (256 threads) */
+    int bincount_blocks_per_sm; /* sort: bin counts (256 threads) */
+    int scatter_blocks_per_sm;  /* sort: scatter (256 threads) */
+    int ncand_blocks_per_sm;    /* NTC candidate counts (256 threads) */
+    int collide_blocks_per_sm;  /* collisions (128 threads) */
+    int mg_threads;
+    int mg_max_blocks;
+} pd_tuning;
+pd_status pd_get_tuning(pd_sim* sim, pd_tuning* out);
+pd_status pd_set_tuning(pd_sim* sim, const pd_tuning* t);
+
+/* Autotuner: picks each pd_tuning entry in turn (coordinate descent over a
+ * fixed candidate list per entry) by timing its kernel with CUDA events over
+ * `steps_per_trial` eager steps after one untimed step per candidate, keeps
+ * the fastest and leaves it set; `out` (may be null) receives the choice.
+ * The trial steps are real steps: the simulation advances by every step the
+ * tuner takes (pd_scalars.step counts them).  steps_per_trial in 1..64.
+ * Per-kernel profile records taken before the call are discarded. */
+pd_status pd_autotune(pd_sim* sim, int steps_per_trial, pd_tuning* out);
+
+/* Checkpoint and resume.  pd_save synchronises and writes the whole state of
+ * a simulation or ensemble to a file: its configs, cross-section tables, the
+ * particle slots in their sorted order with the bin offsets, node charge,
+ * potential and field, every run's counters, ledgers and circuit state, and
+ * the step counter.  pd_load reads such a file into a simulation created
+ * with the same configs (compared field by field); pd_step then continues
+ * exactly as the saved simulation would have, with bit-identical results.
+ * Launch shapes, graph mode and profiling are not saved.  Errors: PD_ERR_ARG
+ * for an unreadable, truncated or foreign file or different configs, and
+ * PD_ERR_CAPACITY when the saved slots exceed the capacity; a failed load
+ * can leave the simulation's state partly overwritten. */
+pd_status pd_save(pd_sim* sim, const char* path);
+pd_status pd_load(pd_sim* sim, const char* path);
 
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle
  * arrays in device memory, with no allocation of any kind.  The paper has no

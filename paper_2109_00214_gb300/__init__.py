@@ -24,7 +24,8 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "Ensemble", "pd_ensemble_workspace_size",
            "pd_ensemble_create", "pd_ensemble_step", "pd_ensemble_get_scalars", "pd_run_count", "pd_run_layout",
            "pd_get_run_counters", "pd_get_run_density_map", "pd_get_run_energy_spectrum", "pd_load_particles_run",
-           "pd_load_particles_device_run", "pd_set_graph_mode", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
+           "pd_load_particles_device_run", "pd_set_graph_mode", "PdTuning", "pd_get_tuning",
+           "pd_set_tuning", "pd_autotune", "pd_save", "pd_load", "pd_get_rho_phi", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 28
 PD_NKERNELS = 12
@@ -57,6 +58,7 @@ class PdScalars(C.Structure):
         ("t", C.c_double), ("V", C.c_double), ("I_gap", C.c_double), ("gamma", C.c_double),
         ("Qbar", C.c_double), ("erosion", C.c_double), ("mass", C.c_double), ("charge", C.c_double),
         ("sgmax", C.c_double * 2), ("poisson_relres", C.c_double), ("poisson_cycles", C.c_double),
+        ("poisson_relres_max", C.c_double),
         ("absorbed_energy", C.c_double * 3), ("n_particles", C.c_int64), ("count", C.c_int64 * 5),
         ("step", C.c_int64),
     ]
@@ -67,6 +69,17 @@ class PdScalars(C.Structure):
             v = getattr(self, name)
             d[name] = list(v) if hasattr(v, "__len__") else v
         return d
+
+
+class PdTuning(C.Structure):
+    _fields_ = [
+        ("push_blocks_per_sm", C.c_int32), ("bincount_blocks_per_sm", C.c_int32),
+        ("scatter_blocks_per_sm", C.c_int32), ("ncand_blocks_per_sm", C.c_int32),
+        ("collide_blocks_per_sm", C.c_int32), ("mg_threads", C.c_int32), ("mg_max_blocks", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 class PdError(RuntimeError):
@@ -104,6 +117,12 @@ _SIGS = {
     "pd_load_particles_run": (C.c_int, [P, C.c_int, C.c_int64, P, P, P, P, P, P, P, P]),
     "pd_load_particles_device_run": (C.c_int, [P, C.c_int, C.c_int64, P, P, P, P, P, P, P, P]),
     "pd_set_graph_mode": (C.c_int, [P, C.c_int, C.c_int]),
+    "pd_get_tuning": (C.c_int, [P, C.POINTER(PdTuning)]),
+    "pd_set_tuning": (C.c_int, [P, C.POINTER(PdTuning)]),
+    "pd_autotune": (C.c_int, [P, C.c_int, C.POINTER(PdTuning)]),
+    "pd_save": (C.c_int, [P, C.c_char_p]),
+    "pd_load": (C.c_int, [P, C.c_char_p]),
+    "pd_get_rho_phi": (C.c_int, [P, Dp, Dp]),
     "pd_get_rho": (C.c_int, [P, P, P]),
     "pd_get_phi": (C.c_int, [P, Dp]),
     "pd_get_field": (C.c_int, [P, Dp, Dp]),
@@ -344,6 +363,44 @@ def pd_set_graph_mode(h, enable, poisson_cycles=4):
     _check(h, _lib().pd_set_graph_mode(h, int(enable), int(poisson_cycles)), "pd_set_graph_mode")
 
 
+def pd_get_tuning(h):
+    t = PdTuning()
+    _check(h, _lib().pd_get_tuning(h, C.byref(t)), "pd_get_tuning")
+    return t.as_dict()
+
+
+def pd_set_tuning(h, **kw):
+    """Change some launch shapes (keys of PdTuning); the others keep their values."""
+    t = PdTuning()
+    _check(h, _lib().pd_get_tuning(h, C.byref(t)), "pd_get_tuning")
+    for k, v in kw.items():
+        if k not in t.as_dict():
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    _check(h, _lib().pd_set_tuning(h, C.byref(t)), "pd_set_tuning")
+
+
+def pd_autotune(h, steps_per_trial=2):
+    t = PdTuning()
+    _check(h, _lib().pd_autotune(h, int(steps_per_trial), C.byref(t)), "pd_autotune")
+    return t.as_dict()
+
+
+def pd_save(h, path):
+    _check(h, _lib().pd_save(h, os.fsencode(path)), "pd_save")
+
+
+def pd_load(h, path):
+    _check(h, _lib().pd_load(h, os.fsencode(path)), "pd_load")
+
+
+def pd_get_rho_phi(h, nodes):
+    rho = np.zeros(nodes)
+    phi = np.zeros(nodes)
+    _check(h, _lib().pd_get_rho_phi(h, _dp(rho), _dp(phi)), "pd_get_rho_phi")
+    return rho, phi
+
+
 def pd_get_rho(h, nodes):
     a = np.zeros(nodes, np.int64)
     b = np.zeros(nodes, np.int64)
@@ -459,6 +516,25 @@ class Simulation:
 
     def scalars(self):
         return pd_get_scalars(self.h)
+
+    def tuning(self):
+        return pd_get_tuning(self.h)
+
+    def save(self, path):
+        pd_save(self.h, path)
+
+    def restore(self, path):
+        pd_load(self.h, path)
+
+    def rho_phi(self):
+        """Node charge density (C/m^3) and potential (V), the Poisson training pairs."""
+        return pd_get_rho_phi(self.h, self.nodes)
+
+    def set_tuning(self, **kw):
+        pd_set_tuning(self.h, **kw)
+
+    def autotune(self, steps_per_trial=2):
+        return pd_autotune(self.h, steps_per_trial)
 
     def counters(self):
         return pd_get_counters(self.h)

@@ -180,6 +180,7 @@ struct pd_sim {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     uint64_t launches[PD_NKERNELS];
+    pd_tuning tune;
 };
 
 namespace {
@@ -415,6 +416,31 @@ InjectConsts make_injection(const pd_config& c) {
 
 int grid_for(pd_sim* s, int per_sm) { return s->sms * per_sm; }
 
+pd_tuning default_tuning() {
+    pd_tuning t;
+    t.push_blocks_per_sm = 8;
+    t.bincount_blocks_per_sm = 8;
+    t.scatter_blocks_per_sm = 8;
+    t.ncand_blocks_per_sm = 8;
+    t.collide_blocks_per_sm = 16;
+    t.mg_threads = 256;
+    t.mg_max_blocks = 1216;
+    return t;
+}
+
+bool tuning_ok(const pd_tuning& t) {
+    auto bps = [](int v) { return v >= 1 && v <= 64; };
+    return bps(t.push_blocks_per_sm) && bps(t.bincount_blocks_per_sm) && bps(t.scatter_blocks_per_sm) &&
+           bps(t.ncand_blocks_per_sm) && bps(t.collide_blocks_per_sm) && t.mg_threads >= 64 &&
+           t.mg_threads <= 1024 && t.mg_threads % 32 == 0 && t.mg_max_blocks >= 1 && t.mg_max_blocks <= 65535;
+}
+
+void apply_tuning(pd_sim* s, const pd_tuning& t) {
+    s->tune = t;
+    s->field.threads = t.mg_threads;
+    s->field.max_blocks = t.mg_max_blocks;
+}
+
 size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
 
 pd_status prime(pd_sim* s) {
@@ -429,7 +455,7 @@ pd_status prime(pd_sim* s) {
         Timed t(s, K_POISSON);
         if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream))
             return fail(s, PD_ERR_CUDA, "field solve failed");
-        field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->stream);
+        field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
     }
     CK(cudaGetLastError());
     s->primed = true;
@@ -442,7 +468,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     const int heavy = (s->step % c.heavy_subcycle) == 0;
     const KParams P = kparams(s, heavy);
     const uint32_t nbins = (uint32_t)s->L.ncell * NSP;
-    const int gpart = grid_for(s, 8);
+    const int gpart = grid_for(s, s->tune.push_blocks_per_sm);
     const size_t nodes = total_nodes(s);
     if (s->any_inject) {
         Timed t(s, K_INJECT, capturing);
@@ -462,22 +488,23 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     }
     {
         Timed t(s, K_SCAN_BINS, capturing);
-        launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev, grid_for(s, 8),
-                        s->stream);
+        launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
+                        grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
         launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
         if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
     }
     {
         Timed t(s, K_SCATTER, capturing);
-        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P, gpart,
-                       s->stream);
+        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P,
+                       grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
     }
     std::swap(s->A, s->B);
     std::swap(s->off, s->off2);
     s->sorted_valid = true;
     {
         Timed t(s, K_NCAND, capturing);
-        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, 8), s->stream);
+        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, s->tune.ncand_blocks_per_sm),
+                     s->stream);
     }
     {
         Timed t(s, K_SCAN_CAND, capturing);
@@ -485,8 +512,8 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     }
     {
         Timed t(s, K_COLLIDE, capturing);
-        launch_collide(s->A, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P, s->cc,
-                       nbins, grid_for(s, 16), s->stream);
+        launch_collide(s->A, s->B, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P,
+                       s->cc, nbins, grid_for(s, s->tune.collide_blocks_per_sm), s->stream);
     }
     {
         Timed t(s, K_FINALIZE, capturing);
@@ -502,7 +529,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
         }
         {
             Timed t(s, K_EFIELD, capturing);
-            field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->stream);
+            field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
         }
     }
     s->step += 1;
@@ -512,6 +539,89 @@ pd_status issue_step(pd_sim* s, bool capturing) {
 int graph_period(const pd_sim* s) {
     const int h = s->cfgs[0].heavy_subcycle;
     return (h % 2 == 0) ? h : 2 * h;   // whole heavy cycles, even (buffers swap every step)
+}
+
+// ---- checkpoint file: a header, then the sections in a fixed order ----
+constexpr char CKPT_MAGIC[8] = {'P', 'D', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t CKPT_VERSION = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, nruns;
+    uint32_t cfg_size, runstate_size, devstate_size, sorted_valid;
+    uint32_t primed, pad0;
+    int64_t step;
+    uint64_t n_slots, n_off, nodes, cap;
+};
+
+bool same_config(const pd_config& a, const pd_config& b) {
+    return a.struct_size == b.struct_size && a.version == b.version && a.geometry == b.geometry && a.nz == b.nz &&
+           a.nr == b.nr && a.dz == b.dz && a.dr == b.dr && a.depth == b.depth && a.dt == b.dt &&
+           a.heavy_subcycle == b.heavy_subcycle && a.weight == b.weight && a.seed == b.seed && a.run == b.run &&
+           a.field_mode == b.field_mode && a.inject_on == b.inject_on && a.di_on == b.di_on &&
+           a.di_split_mode == b.di_split_mode && a.coll_dt_scale == b.coll_dt_scale && a.V0 == b.V0 &&
+           a.R_ohm == b.R_ohm && a.C_farad == b.C_farad && a.beta == b.beta && a.tip_radius == b.tip_radius &&
+           a.work_function == b.work_function && a.neutral_ratio == b.neutral_ratio &&
+           a.neutral_T == b.neutral_T && a.poisson_tol == b.poisson_tol &&
+           a.poisson_max_cycles == b.poisson_max_cycles && a.capacity == b.capacity;
+}
+
+struct File {
+    std::FILE* f;
+    explicit File(std::FILE* f_) : f(f_) {}
+    ~File() {
+        if (f) std::fclose(f);
+    }
+    bool put(const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+    bool get(void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+};
+
+// device range <-> file through a bounded host buffer
+pd_status dev_to_file(pd_sim* s, File& F, const void* dev, size_t bytes) {
+    std::vector<char> h(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t o = 0; o < bytes; o += h.size()) {
+        const size_t n = std::min(h.size(), bytes - o);
+        CK(cudaMemcpyAsync(h.data(), (const char*)dev + o, n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        if (!F.put(h.data(), n)) return fail(s, PD_ERR_ARG, "checkpoint write failed");
+    }
+    return PD_OK;
+}
+
+pd_status file_to_dev(pd_sim* s, File& F, void* dev, size_t bytes) {
+    std::vector<char> h(std::min<size_t>(bytes, (size_t)64 << 20));
+    for (size_t o = 0; o < bytes; o += h.size()) {
+        const size_t n = std::min(h.size(), bytes - o);
+        if (!F.get(h.data(), n)) return fail(s, PD_ERR_ARG, "checkpoint file is truncated");
+        CK(cudaMemcpyAsync((char*)dev + o, h.data(), n, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return PD_OK;
+}
+
+void fill_event_pool(pd_sim* s) {
+    if (!s->pool.empty() || !s->recs.empty()) return;
+    for (int k = 0; k < 8192; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        s->pool.push_back(e);
+    }
+}
+
+// synchronise, add the recorded kernel times per kernel id into ms (may be
+// null) and return the events to the pool
+pd_status collect_profile(pd_sim* s, double* ms) {
+    CK(cudaStreamSynchronize(s->stream));
+    if (ms)
+        for (int k = 0; k < PD_NKERNELS; ++k) ms[k] = 0.0;
+    for (auto& r : s->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && ms) ms[r.k] += t;
+        s->pool.push_back(r.a);
+        s->pool.push_back(r.b);
+    }
+    s->recs.clear();
+    return PD_OK;
 }
 
 pd_status drop_graph(pd_sim* s) {
@@ -680,6 +790,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->prof = false;
     s->graph_on = false;
     s->graph_cycles = 4;
+    s->tune = default_tuning();
     s->gexec = nullptr;
     s->capture_stream = nullptr;
     s->graph_steps = 0;
@@ -827,6 +938,7 @@ pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
     out->sgmax[1] = s->cc.sgmax[1];
     out->poisson_relres = d.relres;
     out->poisson_cycles = d.cycles;
+    out->poisson_relres_max = d.relres_max;
     for (int k = 0; k < 3; ++k) out->absorbed_energy[k] = d.absorbed_energy[k];
     int64_t tot = 0;
     for (int sp = 0; sp < NSP; ++sp) {
@@ -1028,6 +1140,8 @@ pd_status pd_set_graph_mode(pd_sim* s, int enable, int poisson_cycles) {
 pd_status pd_step(pd_sim* s, int64_t n_steps) {
     if (!s) return PD_ERR_ARG;
     if (n_steps < 0) return fail(s, PD_ERR_ARG, "n_steps < 0");
+    // RunState::relres_max of every run restarts with this call
+    CK(cudaMemset2DAsync(&s->rs[0].relres_max, sizeof(RunState), 0, sizeof(double), (size_t)s->R, s->stream));
     if (!s->primed) {
         drop_graph(s);
         pd_status r = prime(s);
@@ -1140,6 +1254,121 @@ pd_status pd_get_phi(pd_sim* s, double* phi) {
     return sync_check(s, &d);
 }
 
+pd_status pd_get_rho_phi(pd_sim* s, double* rho, double* phi) {
+    if (!s || !rho || !phi) return PD_ERR_ARG;
+    const size_t nodes = total_nodes(s);
+    std::vector<long long> he(nodes), hh(nodes);
+    CK(cudaMemcpyAsync(he.data(), s->rho_e, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(hh.data(), s->rho_h, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(phi, s->phi, nodes * 8, cudaMemcpyDeviceToHost, s->stream));
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    for (int run = 0; run < s->R; ++run) {
+        const pd_config& c = s->cfgs[run];
+        const RunInfo& RI = s->runs[run];
+        for (int i = 0; i < RI.nzn; ++i)
+            for (int j = 0; j < RI.nrn; ++j) {
+                const size_t k = RI.node_base + (size_t)i * RI.nrn + j;
+                rho[k] = QE * c.weight * (double)(he[k] + hh[k]) / 4294967296.0 / node_volume(c, i, j);
+            }
+    }
+    return PD_OK;
+}
+
+pd_status pd_save(pd_sim* s, const char* path) {
+    if (!s || !path) return PD_ERR_ARG;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    File F(std::fopen(path, "wb"));
+    if (!F.f) return fail(s, PD_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, CKPT_MAGIC, 8);
+    h.version = CKPT_VERSION;
+    h.nruns = (uint32_t)s->R;
+    h.cfg_size = sizeof(pd_config);
+    h.runstate_size = sizeof(RunState);
+    h.devstate_size = sizeof(DevState);
+    h.sorted_valid = s->sorted_valid ? 1u : 0u;
+    h.primed = s->primed ? 1u : 0u;
+    h.step = s->step;
+    h.n_slots = d.n_slots;
+    h.n_off = (uint64_t)s->L.nbins_pad + 1;
+    h.nodes = total_nodes(s);
+    h.cap = s->L.cap;
+    bool ok = F.put(&h, sizeof(h)) && F.put(s->cfgs.data(), s->cfgs.size() * sizeof(pd_config)) &&
+              F.put(s->h_xs, sizeof(s->h_xs)) && F.put(s->eth, sizeof(s->eth)) && F.put(&d, sizeof(d));
+    if (!ok) return fail(s, PD_ERR_ARG, "checkpoint write failed");
+    const size_t nodes = (size_t)h.nodes, n = (size_t)h.n_slots;
+    const void* arrays[7] = {s->A.key, s->A.pz, s->A.pr, s->A.vz, s->A.vr, s->A.vt, s->A.id};
+    if ((r = dev_to_file(s, F, s->rs, (size_t)s->R * sizeof(RunState))) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->off, (size_t)h.n_off * 4)) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->rho_e, nodes * 8)) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->rho_h, nodes * 8)) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->E, nodes * 8)) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->phi, nodes * 8)) != PD_OK) return r;
+    for (int a = 0; a < 7; ++a)
+        if ((r = dev_to_file(s, F, arrays[a], n * 4)) != PD_OK) return r;
+    if (std::fflush(F.f) != 0) return fail(s, PD_ERR_ARG, "checkpoint write failed");
+    return PD_OK;
+}
+
+pd_status pd_load(pd_sim* s, const char* path) {
+    if (!s || !path) return PD_ERR_ARG;
+    DevState cur;
+    pd_status r = sync_check(s, &cur);
+    if (r != PD_OK) return r;
+    File F(std::fopen(path, "rb"));
+    if (!F.f) return fail(s, PD_ERR_ARG, std::string("cannot open ") + path);
+    CkptHeader h;
+    if (!F.get(&h, sizeof(h)) || std::memcmp(h.magic, CKPT_MAGIC, 8) != 0 || h.version != CKPT_VERSION)
+        return fail(s, PD_ERR_ARG, "not a checkpoint of this library version");
+    if (h.nruns != (uint32_t)s->R || h.cfg_size != sizeof(pd_config) || h.runstate_size != sizeof(RunState) ||
+        h.devstate_size != sizeof(DevState) || h.n_off != (uint64_t)s->L.nbins_pad + 1 ||
+        h.nodes != total_nodes(s) || h.cap != s->L.cap)
+        return fail(s, PD_ERR_ARG, "checkpoint was written by a simulation of another shape");
+    if (h.n_slots > s->L.cap) return fail(s, PD_ERR_CAPACITY, "checkpoint holds more slots than the capacity");
+    std::vector<pd_config> cf(s->R);
+    if (!F.get(cf.data(), cf.size() * sizeof(pd_config))) return fail(s, PD_ERR_ARG, "checkpoint file is truncated");
+    for (int k = 0; k < s->R; ++k)
+        if (!same_config(cf[k], s->cfgs[k])) return fail(s, PD_ERR_ARG, "checkpoint configs differ from this simulation's");
+    float xs[NCH][XS_N];
+    double eth[NCH];
+    DevState d;
+    if (!F.get(xs, sizeof(xs)) || !F.get(eth, sizeof(eth)) || !F.get(&d, sizeof(d)))
+        return fail(s, PD_ERR_ARG, "checkpoint file is truncated");
+    if (d.n_slots != h.n_slots) return fail(s, PD_ERR_ARG, "inconsistent checkpoint");
+    drop_graph(s);
+    const size_t nodes = (size_t)h.nodes, n = (size_t)h.n_slots;
+    void* arrays[7] = {s->A.key, s->A.pz, s->A.pr, s->A.vz, s->A.vr, s->A.vt, s->A.id};
+    if ((r = file_to_dev(s, F, s->rs, (size_t)s->R * sizeof(RunState))) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->off, (size_t)h.n_off * 4)) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->rho_e, nodes * 8)) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->rho_h, nodes * 8)) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->E, nodes * 8)) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->phi, nodes * 8)) != PD_OK) return r;
+    for (int a = 0; a < 7; ++a)
+        if ((r = file_to_dev(s, F, arrays[a], n * 4)) != PD_OK) return r;
+    // slots past the saved ones are free
+    CK(cudaMemsetAsync(s->A.key + n, 0xFF, (size_t)(s->L.cap - n) * 4, s->stream));
+    std::memcpy(s->h_xs, xs, sizeof(xs));
+    std::memcpy(s->eth, eth, sizeof(eth));
+    update_collision_consts(s);
+    CK(cudaMemcpyAsync(s->xs, s->h_xs, sizeof(s->h_xs), cudaMemcpyHostToDevice, s->stream));
+    d.error = 0;
+    d.load_bad = 0;
+    CK(cudaMemcpyAsync(s->st, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream));
+    r = upload_ck(s);
+    if (r != PD_OK) return r;
+    s->step = h.step;
+    s->sorted_valid = h.sorted_valid != 0;
+    s->primed = h.primed != 0;
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
 pd_status pd_get_field(pd_sim* s, double* Ez, double* Er) {
     if (!s || !Ez || !Er) return PD_ERR_ARG;
     const size_t nodes = total_nodes(s);
@@ -1171,32 +1400,105 @@ pd_status pd_get_run_energy_spectrum(pd_sim* s, int run, int species, double lo,
 pd_status pd_profile_enable(pd_sim* s, int enable) {
     if (!s) return PD_ERR_ARG;
     s->prof = enable != 0;
-    if (s->prof && s->pool.empty()) {
-        for (int k = 0; k < 8192; ++k) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) break;
-            s->pool.push_back(e);
-        }
-    }
+    if (s->prof) fill_event_pool(s);
     return PD_OK;
 }
 
 pd_status pd_profile_read(pd_sim* s, double* ms, uint64_t* launches) {
     if (!s) return PD_ERR_ARG;
-    CK(cudaStreamSynchronize(s->stream));
     for (int k = 0; k < PD_NKERNELS; ++k) {
-        if (ms) ms[k] = 0.0;
         if (launches) launches[k] = s->launches[k];
         s->launches[k] = 0;
     }
-    for (auto& r : s->recs) {
-        float t = 0.f;
-        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && ms) ms[r.k] += t;
-        s->pool.push_back(r.a);
-        s->pool.push_back(r.b);
-    }
-    s->recs.clear();
+    return collect_profile(s, ms);
+}
+
+pd_status pd_get_tuning(pd_sim* s, pd_tuning* out) {
+    if (!s || !out) return PD_ERR_ARG;
+    *out = s->tune;
     return PD_OK;
+}
+
+pd_status pd_set_tuning(pd_sim* s, const pd_tuning* t) {
+    if (!s || !t) return PD_ERR_ARG;
+    if (!tuning_ok(*t)) return fail(s, PD_ERR_ARG, "launch shape out of range");
+    drop_graph(s);
+    apply_tuning(s, *t);
+    return PD_OK;
+}
+
+pd_status pd_autotune(pd_sim* s, int steps_per_trial, pd_tuning* out) {
+    if (!s) return PD_ERR_ARG;
+    if (steps_per_trial < 1 || steps_per_trial > 64) return fail(s, PD_ERR_ARG, "steps_per_trial must be in 1..64");
+    if (!s->primed) {
+        pd_status r = prime(s);
+        if (r != PD_OK) return r;
+    }
+    drop_graph(s);
+    const bool prof0 = s->prof;
+    fill_event_pool(s);
+    pd_status r = collect_profile(s, nullptr);      // earlier records are discarded
+    uint64_t launches0[PD_NKERNELS];
+    std::memcpy(launches0, s->launches, sizeof(launches0));
+    struct Knob {
+        int* v;
+        int kernel;
+        std::vector<int> cand;
+    };
+    pd_tuning t = s->tune;
+    std::vector<Knob> knobs = {
+        {&t.push_blocks_per_sm, K_PUSH, {2, 4, 6, 8, 12, 16, 24, 32}},
+        {&t.bincount_blocks_per_sm, K_SCAN_BINS, {2, 4, 8, 16}},
+        {&t.scatter_blocks_per_sm, K_SCATTER, {2, 4, 6, 8, 12, 16}},
+        {&t.ncand_blocks_per_sm, K_NCAND, {2, 4, 8, 16}},
+        {&t.collide_blocks_per_sm, K_COLLIDE, {4, 8, 16, 32}},
+    };
+    if (s->cfgs[0].field_mode == PD_FIELD_POISSON) {
+        knobs.push_back({&t.mg_threads, K_POISSON, {64, 128, 256, 512}});
+        knobs.push_back({&t.mg_max_blocks, K_POISSON, {76, 152, 304, 608, 1216}});
+    }
+    // time the knob's kernel for one value: an untimed step, then
+    // steps_per_trial profiled ones
+    auto trial = [&](int kid, double* ms) -> pd_status {
+        apply_tuning(s, t);
+        s->prof = false;
+        pd_status q = issue_step(s, false);
+        s->prof = true;
+        for (int k = 0; k < steps_per_trial && q == PD_OK; ++k) q = issue_step(s, false);
+        s->prof = false;
+        double acc[PD_NKERNELS];
+        const pd_status c = collect_profile(s, acc);
+        if (q != PD_OK) return q;
+        if (c != PD_OK) return c;
+        DevState d;
+        q = sync_check(s, &d);
+        *ms = acc[kid];
+        return q;
+    };
+    for (size_t kn = 0; kn < knobs.size() && r == PD_OK; ++kn) {
+        Knob& K = knobs[kn];
+        // the current value first: another must beat it by 2 % to replace it
+        std::vector<int> order = {*K.v};
+        for (int v : K.cand)
+            if (v != *K.v) order.push_back(v);
+        int best = *K.v;
+        double best_ms = 0.0;
+        for (size_t q = 0; q < order.size() && r == PD_OK; ++q) {
+            *K.v = order[q];
+            double ms = 0.0;
+            r = trial(K.kernel, &ms);
+            if (r == PD_OK && (q == 0 || ms < 0.98 * best_ms)) {
+                best = order[q];
+                best_ms = ms;
+            }
+        }
+        *K.v = best;
+    }
+    apply_tuning(s, t);
+    std::memcpy(s->launches, launches0, sizeof(launches0));
+    s->prof = prof0;
+    if (out) *out = s->tune;
+    return r;
 }
 
 const char* pd_kernel_name(int k) { return (k >= 0 && k < PD_NKERNELS) ? KNAMES[k] : "?"; }

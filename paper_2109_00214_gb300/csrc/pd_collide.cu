@@ -164,13 +164,94 @@ constexpr int RC = 8;
 struct IdList {
     uint32_t ids[RC];
     const uint32_t* base;
+    const uint32_t* table;           // rank -> position of a long list, or null
     uint32_t n;
     bool cached;
 };
 
-__device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ base, uint32_t n, int lane) {
+// Scratch for the rank tables of long lists: four u32 arrays indexed by slot.
+// They are the sort's other buffer, unused between the scatter and the next
+// step's scatter; a list at slots [b, b + n) uses [b, b + n) of each.
+struct RankScratch {
+    uint32_t *ka, *va, *kb, *vb;
+};
+
+// Rank table of ids[0..n) (unique): position of the r-th smallest id at
+// table[r].  Stable LSD radix sort of (id, position) pairs by 4-bit digits,
+// one warp, digit ranks from ballots; only the digits below the highest set
+// bit of any id are sorted.  Returns the buffer that holds the table.
+__device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t n, uint32_t* ka, uint32_t* va,
+                                      uint32_t* kb, uint32_t* vb, int lane) {
+    uint32_t orv = 0;
+    for (uint32_t q = lane; q < n; q += 32) {
+        const uint32_t x = ids[q];
+        ka[q] = x;
+        va[q] = q;
+        orv |= x;
+    }
+    orv = __reduce_or_sync(FULL, orv);
+    const int passes = (32 - __clz((int)orv) + 3) / 4;
+    uint32_t *sk = ka, *sv = va, *dk = kb, *dv = vb;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    __syncwarp();
+    for (int p = 0; p < passes; ++p) {
+        const int sh = 4 * p;
+        // lane v < 16 counts digit v
+        uint32_t cnt = 0;
+        for (uint32_t q0 = 0; q0 < n; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            const uint32_t d = q < n ? (sk[q] >> sh) & 15u : 16u;
+#pragma unroll
+            for (uint32_t v = 0; v < 16; ++v) {
+                const unsigned m = __ballot_sync(FULL, d == v);
+                if ((uint32_t)lane == v) cnt += (uint32_t)__popc(m);
+            }
+        }
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t base = x - cnt;          // lane v: first destination of digit v
+        for (uint32_t q0 = 0; q0 < n; q0 += 32) {
+            const uint32_t q = q0 + lane;
+            const bool in = q < n;
+            const uint32_t key = in ? sk[q] : 0u, val = in ? sv[q] : 0u;
+            const uint32_t d = in ? (key >> sh) & 15u : 16u;
+            uint32_t dst = 0;
+#pragma unroll
+            for (uint32_t v = 0; v < 16; ++v) {
+                const unsigned m = __ballot_sync(FULL, d == v);
+                const uint32_t b = __shfl_sync(FULL, base, (int)v);
+                if (d == v) dst = b + (uint32_t)__popc(m & lt);
+                if ((uint32_t)lane == v) base += (uint32_t)__popc(m);
+            }
+            if (in) {
+                dk[dst] = key;
+                dv[dst] = val;
+            }
+        }
+        __syncwarp();
+        uint32_t* t = sk;
+        sk = dk;
+        dk = t;
+        t = sv;
+        sv = dv;
+        dv = t;
+    }
+    return sv;
+}
+
+// ids of one cell and species at slots [slot0, slot0 + n); `lookups` rank
+// selections will follow: long lists get a rank table when that pays
+__device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
+                                         uint32_t lookups, const RankScratch& S, int lane) {
+    const uint32_t* base = ids + slot0;
     L.base = base;
     L.n = n;
+    L.table = nullptr;
     L.cached = n <= 32u * RC;
     if (L.cached) {
 #pragma unroll
@@ -178,11 +259,14 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
             const uint32_t q = (uint32_t)lane + 32u * k;
             L.ids[k] = q < n ? base[q] : 0u;
         }
+    } else if (lookups >= 2) {
+        L.table = rank_table(base, n, S.ka + slot0, S.va + slot0, S.kb + slot0, S.vb + slot0, lane);
     }
 }
 
-// select_rank on a register-cached list (same result as select_rank)
+// position of the rank-th smallest id of the list (same result as select_rank)
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
+    if (L.table) return L.table[rank];
     if (!L.cached) return select_rank(L.base, L.n, rank, lane);
     uint32_t prefix = 0, want = rank;
     for (int bit = 31; bit >= 0; --bit) {
@@ -366,7 +450,7 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     ++cx.ev[ch];
 }
 
-__global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                  const uint2* __restrict__ nc, const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
                                                  long long* rho_h, const float* __restrict__ xsE,
@@ -406,7 +490,7 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
         IdList el;
-        load_ids(el, A.id + e_base, Ne, lane);
+        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, lane);
         for (int k = 0; k < 2; ++k) {
             const uint32_t tb = (k == 0 ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
@@ -414,7 +498,7 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, const uint32_t* __
             const uint32_t ncand = k == 0 ? n.x : n.y;
             if (ncand == 0) continue;
             IdList tl;
-            load_ids(tl, A.id + t_base, Nt, lane);
+            load_ids(tl, A.id, t_base, Nt, ncand, S, lane);
             for (uint32_t m = 0; m < ncand; ++m) {
                 Stream rs(lc, st->step, sid_cand(k, m), RI->seed, RI->run);
                 const uint32_t i = rs.pick(Ne);
@@ -587,11 +671,12 @@ void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* can
                   const KParams& P, int grid, cudaStream_t s) {
     k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, st, P);
 }
-void launch_collide(const Particles& A, const uint32_t* off, const uint2* nc, const uint32_t* cand_off,
-                    const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h, const float* xsE,
-                    const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins, int grid,
-                    cudaStream_t s) {
-    k_collide<<<grid, 128, 0, s>>>(A, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
+                    const uint32_t* cand_off, const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h,
+                    const float* xsE, const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins,
+                    int grid, cudaStream_t s) {
+    const RankScratch S{B.key, B.id, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr)};
+    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {

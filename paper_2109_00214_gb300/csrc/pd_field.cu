@@ -11,8 +11,10 @@
 //
 // Multigrid: V(2,2) cycles with red-black Gauss-Seidel, residual restriction
 // by full weighting of the integrated residuals (weights 1, 1/2, 1/4),
-// bilinear prolongation, coefficients rediscretised on each level, and a
-// single-block Gauss-Seidel solve on the coarsest level.  Double precision.
+// bilinear prolongation, coefficients rediscretised on each level, and an
+// exact solve on the coarsest level: the inverse of its operator, formed on
+// the host once, applied by one block (Gauss-Seidel sweeps instead when the
+// coarsest level has more than MG_DIRECT_MAX unknowns).  Double precision.
 //
 // Batched over runs: each level operation is one launch with blockIdx.y = run
 // (runs of different sizes and depths; a block whose run has no such level,
@@ -47,6 +49,9 @@ void level_dims(int nz, int nr, int* nzs, int* nrs, int& nlev) {
     }
 }
 
+// unknowns of the coarsest level (interior rows, all radial nodes)
+int coarse_unknowns(const int* a, const int* b, int n) { return (a[n - 1] - 1) * (b[n - 1] + 1); }
+
 size_t run_bytes(int nz, int nr) {
     int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
     level_dims(nz, nr, a, b, n);
@@ -55,6 +60,8 @@ size_t run_bytes(int nz, int nr) {
         const size_t nodes = (size_t)(a[l] + 1) * (b[l] + 1);
         t += 3 * al(nodes * 8) + 3 * al((size_t)(b[l] + 1) * 8);
     }
+    const size_t m = (size_t)coarse_unknowns(a, b, n);
+    if (m <= (size_t)MG_DIRECT_MAX) t += al(m * m * 8);
     return t + 2 * al((size_t)(nr + 1) * 8);
 }
 }  // namespace
@@ -70,7 +77,7 @@ size_t field_workspace_bytes(const std::vector<int>& nz, const std::vector<int>&
     const size_t R = nz.size();
     for (size_t r = 0; r < R; ++r) t += run_bytes(nz[r], nr[r]);
     t += al(R * MG_MAX_LEVELS * sizeof(MGLevel)) + al(R * 4) * 3 + al(R * RED_BLOCKS * 2 * 8) + al(R * 8) * 2 +
-         al(R * 16);
+         al(R * 16) + al(R * sizeof(double*));
     return t;
 }
 
@@ -261,15 +268,28 @@ __global__ void k_prolong(const MGLevel* lev, const int* nlev, const int* done, 
     }
 }
 
-// coarsest level of each run whose hierarchy ends at level l: Gauss-Seidel
-// sweeps in one block (blockIdx.x = run)
-__global__ void __launch_bounds__(1024) k_coarse(const MGLevel* lev, const int* nlev, const int* done, int l,
-                                                 int sweeps) {
+// coarsest level of each run whose hierarchy ends at level l (blockIdx.x =
+// run): x = A^-1 f with the stored inverse (transposed: column v of A^-1 at
+// inv[v * m]), or Gauss-Seidel sweeps when the run has none
+__global__ void __launch_bounds__(256) k_coarse(const MGLevel* lev, const int* nlev, const int* done,
+                                                const double* const* inv, int l, int sweeps) {
     const int run = blockIdx.x;
     if (!level_active(nlev, done, run, l, true)) return;
     const MGLevel L = lev[run * MG_MAX_LEVELS + l];
     const int W = L.nr + 1;
     const int n = (L.nz - 1) * W;
+    const double* Ai = inv[run];
+    if (Ai) {
+        __shared__ double f[MG_DIRECT_MAX];
+        for (int q = threadIdx.x; q < n; q += blockDim.x) f[q] = L.f[W + q];
+        __syncthreads();
+        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+            double acc = 0.0;
+            for (int v = 0; v < n; ++v) acc += Ai[(size_t)v * n + u] * f[v];
+            L.x[W + u] = acc;
+        }
+        return;
+    }
     for (int it = 0; it < sweeps; ++it) {
         for (int color = 0; color < 2; ++color) {
             for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -310,22 +330,80 @@ __global__ void k_efield(const double* phi, const RunInfo* runs, const double* d
     }
 }
 
-__global__ void k_flag_nonfinite(const int* done, int nruns, DevState* st) {
-    for (int r = threadIdx.x; r < nruns; r += blockDim.x)
+__global__ void k_solve_epilogue(const int* done, int nruns, DevState* st, RunState* rs) {
+    for (int r = threadIdx.x; r < nruns; r += blockDim.x) {
         if (done[r] == 2) atomicOr(&st->error, ERR_NONFINITE);
+        const double rel = rs[r].relres;
+        if (!(rel <= rs[r].relres_max)) rs[r].relres_max = rel;   // NaN propagates
+    }
 }
 
 // ------------------------------------------------------------------
 // host
 // ------------------------------------------------------------------
-static int blocks_for(int n) {
-    int b = (n + 255) / 256;
-    return b < 1 ? 1 : (b > 1216 ? 1216 : b);
+static int blocks_for(const FieldSolver& fs, int n) {
+    int b = (n + fs.threads - 1) / fs.threads;
+    return b < 1 ? 1 : (b > fs.max_blocks ? fs.max_blocks : b);
+}
+
+// Inverse of the coarsest operator by Gauss-Jordan elimination with partial
+// pivoting; unknown u = (i - 1) (nr + 1) + j for interior rows i and radial
+// nodes j, the rows of the smoother's equation.  Stored transposed.
+static bool invert_coarse(int nz, int nr, const std::vector<double>& ap, const std::vector<double>& am,
+                          const std::vector<double>& bb, std::vector<double>& out) {
+    const int W = nr + 1, m = (nz - 1) * W;
+    std::vector<double> A((size_t)m * m, 0.0), X((size_t)m * m, 0.0);
+    for (int u = 0; u < m; ++u) {
+        const int i = 1 + u / W, j = u % W;
+        A[(size_t)u * m + u] = ap[j] + am[j] + 2.0 * bb[j];
+        if (j < nr) A[(size_t)u * m + u + 1] = -ap[j];
+        if (j > 0) A[(size_t)u * m + u - 1] = -am[j];
+        if (i + 1 < nz) A[(size_t)u * m + u + W] = -bb[j];
+        if (i - 1 > 0) A[(size_t)u * m + u - W] = -bb[j];
+        X[(size_t)u * m + u] = 1.0;
+    }
+    for (int c = 0; c < m; ++c) {
+        int p = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(A[(size_t)r * m + c]) > std::fabs(A[(size_t)p * m + c])) p = r;
+        if (!(std::fabs(A[(size_t)p * m + c]) > 0.0)) return false;
+        if (p != c)
+            for (int k = 0; k < m; ++k) {
+                std::swap(A[(size_t)p * m + k], A[(size_t)c * m + k]);
+                std::swap(X[(size_t)p * m + k], X[(size_t)c * m + k]);
+            }
+        const double d = A[(size_t)c * m + c];
+        for (int k = 0; k < m; ++k) {
+            A[(size_t)c * m + k] /= d;
+            X[(size_t)c * m + k] /= d;
+        }
+        for (int r = 0; r < m; ++r) {
+            if (r == c) continue;
+            const double f = A[(size_t)r * m + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < m; ++k) {
+                A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+                X[(size_t)r * m + k] -= f * X[(size_t)c * m + k];
+            }
+        }
+    }
+    out.assign((size_t)m * m, 0.0);
+    for (int u = 0; u < m; ++u)
+        for (int v = 0; v < m; ++v) out[(size_t)v * m + u] = X[(size_t)u * m + v];
+    return true;
 }
 
 int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::vector<uint32_t>& node_base,
                double* phi, void* ws, size_t bytes, cudaStream_t s) {
     const int R = (int)cfgs.size();
+    {
+        std::vector<int> nz(R), nr(R);
+        for (int r = 0; r < R; ++r) {
+            nz[r] = cfgs[r].nz;
+            nr[r] = cfgs[r].nr;
+        }
+        if (field_workspace_bytes(nz, nr) > bytes) return 1;   // checked before anything is written
+    }
     char* w = (char*)ws;
     size_t o = 0;
     auto take = [&](size_t sz) {
@@ -341,6 +419,7 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
     fs.max_cycles = cfgs[0].poisson_max_cycles > 0 ? cfgs[0].poisson_max_cycles : 60;
     std::vector<double> fvv_all, vb_all, tol(R), dzr(2 * (size_t)R);
     std::vector<int> fvb_off(R);
+    std::vector<double*> inv(R, nullptr);
     for (int r = 0; r < R; ++r) {
         const pd_config& c = cfgs[r];
         int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
@@ -375,6 +454,13 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
                 else A = 2.0 * PI_ * j * dr * dr;
                 bb[j] = A / dz;
             }
+            if (l == n - 1 && coarse_unknowns(a, b, n) <= MG_DIRECT_MAX) {
+                const int m = coarse_unknowns(a, b, n);
+                std::vector<double> Ai;
+                if (!invert_coarse(L.nz, L.nr, ap, am, bb, Ai)) return 1;
+                inv[r] = (double*)take((size_t)m * m * 8);
+                cudaMemcpyAsync(inv[r], Ai.data(), Ai.size() * 8, cudaMemcpyHostToDevice, s);
+            }
             cudaMemcpyAsync(L.ap, ap.data(), ap.size() * 8, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(L.am, am.data(), am.size() * 8, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(L.b, bb.data(), bb.size() * 8, cudaMemcpyHostToDevice, s);
@@ -403,7 +489,9 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
     fs.bnorm = (double*)take((size_t)R * 8);
     fs.tol = (double*)take((size_t)R * 8);
     fs.dzr = (double*)take((size_t)R * 16);
+    fs.inv = (double**)take((size_t)R * sizeof(double*));
     if (o > bytes) return 1;
+    cudaMemcpyAsync(fs.inv, inv.data(), (size_t)R * sizeof(double*), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.dzr, dzr.data(), (size_t)R * 16, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.fv_over_verb, fvv_all.data(), fvv_all.size() * 8, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.verb_base, vb_all.data(), vb_all.size() * 8, cudaMemcpyHostToDevice, s);
@@ -428,7 +516,7 @@ static int level_blocks(const FieldSolver& fs, int l) {
             const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
             mx = std::max(mx, (L.nz + 1) * (L.nr + 1));
         }
-    return blocks_for(mx);
+    return blocks_for(fs, mx);
 }
 
 static void vcycle(FieldSolver& fs, cudaStream_t s) {
@@ -437,23 +525,23 @@ static void vcycle(FieldSolver& fs, cudaStream_t s) {
     for (int l = 0; l < fs.max_levels; ++l) {
         const dim3 g(level_blocks(fs, l), R);
         for (int it = 0; it < 2; ++it) {
-            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
-            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
+            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
+            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
         }
-        k_residual<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, nullptr);
+        k_residual<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, nullptr);
         if (l + 1 < fs.max_levels) {
             const dim3 gc(level_blocks(fs, l + 1), R);
-            k_restrict<<<gc, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
+            k_restrict<<<gc, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
         }
-        k_coarse<<<R, 1024, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 200);
+        k_coarse<<<R, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, fs.inv, l, 200);
     }
     // up: prolong, smooth
     for (int l = fs.max_levels - 2; l >= 0; --l) {
         const dim3 g(level_blocks(fs, l), R);
-        k_prolong<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
+        k_prolong<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
         for (int it = 0; it < 2; ++it) {
-            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
-            k_smooth<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
+            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
+            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
         }
     }
 }
@@ -461,6 +549,8 @@ static void vcycle(FieldSolver& fs, cudaStream_t s) {
 static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStream_t s) {
     const int R = fs.nruns;
     const dim3 g(RED_BLOCKS, R);
+    // fixed shape: the summation order of the norms (and so the cycle count)
+    // does not depend on the tuned block size
     k_residual<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, nullptr, 0, fs.red);
     k_norms<<<(R + 127) / 128, 128, 0, s>>>(fs.red, fs.bnorm, fs.done, fs.tol, rs, R, cycle, first);
 }
@@ -469,8 +559,8 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
                 const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s) {
     (void)E;
     const int R = fs.nruns;
-    const dim3 g0(blocks_for(fs.max_nodes0), R);
-    k_rhs<<<g0, 256, 0, s>>>(rho_e, rho_h, fs.fv_over_verb, fs.verb_base, fs.fvb_off, fs.lev, runs, rs, phi);
+    const dim3 g0(blocks_for(fs, fs.max_nodes0), R);
+    k_rhs<<<g0, fs.threads, 0, s>>>(rho_e, rho_h, fs.fv_over_verb, fs.verb_base, fs.fvb_off, fs.lev, runs, rs, phi);
     norms(fs, rs, 0, 1, s);
     if (host_check) {
         for (int cyc = 1; cyc <= fs.max_cycles; ++cyc) {
@@ -493,10 +583,11 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
 }
 
 // E for every run (separate so the caller can time it)
-void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, cudaStream_t s) {
-    const dim3 g(blocks_for(fs.max_nodes0), fs.nruns);
-    k_efield<<<g, 256, 0, s>>>(phi, runs, fs.dzr, E);
-    k_flag_nonfinite<<<1, 128, 0, s>>>(fs.done, fs.nruns, st);
+void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, RunState* rs,
+                  cudaStream_t s) {
+    const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    k_efield<<<g, fs.threads, 0, s>>>(phi, runs, fs.dzr, E);
+    k_solve_epilogue<<<1, 128, 0, s>>>(fs.done, fs.nruns, st, rs);
 }
 
 }  // namespace pd

@@ -10,6 +10,7 @@
 namespace pd {
 
 constexpr int MG_MAX_LEVELS = 12;
+constexpr int MG_DIRECT_MAX = 256;      // coarsest levels up to this many unknowns are solved by their inverse
 
 // one level of one run
 struct MGLevel {
@@ -36,6 +37,9 @@ struct FieldSolver {
     int max_cycles = 60;
     int max_nodes0 = 0;                 // largest level-0 node count
     double* dzr = nullptr;              // [nruns][2] cell sizes dz, dr
+    double** inv = nullptr;             // [nruns] inverse of the coarsest operator (transposed), or null
+    int threads = 256;                  // threads per block of the level kernels (64..1024, a multiple of 32)
+    int max_blocks = 1216;              // cap on blocks per run and level (grid-stride loops beyond it)
 };
 
 bool field_grid_ok(int nz, int nr);
@@ -55,6 +59,8 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
                 const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s);
 
 // E = -grad(phi) of every run; flags runs whose solve met a non-finite value
-void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, cudaStream_t s);
+// and folds each run's final residual into RunState::relres_max
+void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, RunState* rs,
+                  cudaStream_t s);
 
 }  // namespace pd

@@ -52,6 +52,7 @@ struct RunState {
     double I_gap;                    // last step's gap current
     double relres;                   // last Poisson relative residual
     double cycles;                   // last Poisson cycles
+    double relres_max;               // largest final residual of the solves since it was last cleared
     unsigned int id_next;            // next particle id of the run
     unsigned int pad0;
 };

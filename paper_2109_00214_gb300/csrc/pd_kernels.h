@@ -55,10 +55,11 @@ void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, c
 // collisions
 void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
                   const KParams& P, int grid, cudaStream_t s);
-void launch_collide(const Particles& A, const uint32_t* off, const uint2* nc, const uint32_t* cand_off,
-                    const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h, const float* xsE,
-                    const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins, int grid,
-                    cudaStream_t s);
+// B: the other particle buffer, used as scratch (free until the next scatter)
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
+                    const uint32_t* cand_off, const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h,
+                    const float* xsE, const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins,
+                    int grid, cudaStream_t s);
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 

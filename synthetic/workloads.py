@@ -228,3 +228,34 @@ def rate_cell(n_e=200000, n_t=100000, Te_eV=10.0, seed=3, depth=1e-6, dt=1e-15,
                       inject_on=0, coll_dt_scale=coll_scale,
                       capacity=n_e * 3 + n_t + (1 << 16), max_cand_per_step=1 << 22)
     return cfg, concat_loads([le, lt])
+
+
+ENSEMBLE_GRIDS = (64, 96, 128, 192, 256)
+ENSEMBLE_VOLTS_KV = (2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 10.0)
+
+
+def ensemble_breakdown(seeds=range(1, 9), volts_kV=ENSEMBLE_VOLTS_KV, grids=ENSEMBLE_GRIDS,
+                       n_lo=1e5, n_hi=2e6, emission=False):
+    """Ensemble of independent breakdown runs, seeds x gap voltages (run index
+    = seed position * len(volts_kV) + voltage position).  Each run draws, from
+    a numpy Philox generator keyed by its run index, its grid N (N x N cells,
+    one of `grids`) and its particle count, log-uniform in [n_lo, n_hi]; its
+    initial load is the near-cathode plume of `rz_plume` scaled to that grid
+    and count.  Field: the self-consistent Poisson solve.  Cathode emission is
+    off unless `emission`: the plume's charge noise puts 1e10-1e11 V/m on the
+    cathode, and with the tip enhancement of 35 the Fowler-Nordheim count per
+    step then outgrows any capacity within a few steps on the coarser runs.
+    Returns a list of (config, particles)."""
+    out = []
+    seeds = list(seeds)
+    for si, seed in enumerate(seeds):
+        for vi, kv in enumerate(volts_kV):
+            run = si * len(volts_kV) + vi
+            pick = np.random.Generator(np.random.Philox(key=run))
+            n = int(grids[int(pick.integers(0, len(grids)))])
+            count = float(math.exp(pick.uniform(math.log(n_lo), math.log(n_hi))))
+            cfg, parts = rz_plume(n=n, total=count, seed=1000 * int(seed) + run)
+            cfg.update(seed=int(seed), run=run, V0=kv * 1e3, field_on=1, inject_on=int(bool(emission)),
+                       capacity=int(1.25 * count) + (1 << 16))
+            out.append((cfg, parts))
+    return out

@@ -28,8 +28,11 @@ def _runs(field_on, sizes=(32, 48, 64), volts=(2.0e3, 5.0e3, 2.9e3)):
     runs = []
     for k, (n, V) in enumerate(zip(sizes, volts)):
         cfg, parts = synthetic.rz_plume(n=n, total=1.5e4 * (k + 1), seed=10 + k)
-        cfg.update(field_on=field_on, inject_on=1, beta=60.0, coll_dt_scale=50.0, V0=V, run=k,
-                   poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+        # with the self-consistent field the charge noise of these small loads
+        # (a few 1e4 heavy-weight particles) reaches 1e11 V/m at the cathode:
+        # no tip enhancement there, or Fowler-Nordheim emission runs away
+        cfg.update(field_on=field_on, inject_on=1, beta=60.0 if field_on == 2 else 1.0, coll_dt_scale=50.0, V0=V,
+                   run=k, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
         runs.append((cfg, parts))
     return runs
 
@@ -128,3 +131,43 @@ def test_batched_multigrid_matches_oracle_per_run(pd, xs):
         ophi = o.phi()
         assert np.abs(ens.run_slice(phi, k) - ophi).max() <= 1e-8 * np.abs(ophi).max(), k
         assert ens.run_scalars(k)["poisson_relres"] <= 1e-10
+
+
+def test_autotuned_shapes_leave_results_unchanged(pd, xs):
+    """Every tuned kernel walks its work with a grid-stride loop and writes
+    order-independent results, so the autotuner's trial steps (real steps,
+    under many launch shapes) must give exactly what default shapes give."""
+    runs = _runs(field_on=1)
+    a = _ensemble(pd, runs, xs)
+    b = _ensemble(pd, runs, xs)
+    chosen = b.autotune(1)
+    taken = int(b.run_scalars(0)["step"])
+    assert taken > 10
+    assert chosen == b.tuning()
+    b.set_tuning(push_blocks_per_sm=3, scatter_blocks_per_sm=5, collide_blocks_per_sm=7, mg_threads=96,
+                 mg_max_blocks=9)
+    b.step(3)
+    a.step(taken + 3)
+    ga, gb = _split(a, a.particles()), _split(b, b.particles())
+    for k in range(a.R):
+        for key in ("id", "species", "iz", "ir") + FLOATS:
+            assert np.array_equal(ga[k][key], gb[k][key]), (k, key)
+        assert a.run_counters(k) == b.run_counters(k)
+        assert abs(a.run_scalars(k)["V"] - b.run_scalars(k)["V"]) <= 1e-9 * abs(a.run_scalars(k)["V"])
+
+
+def test_graph_mode_reports_the_worst_residual(pd, xs):
+    runs = _runs(field_on=1)
+    tol = runs[0][0]["poisson_tol"]
+    ens = _ensemble(pd, runs, xs)
+    ens.step(10)
+    ens.set_graph_mode(1, 1)                 # one V-cycle per step: short of the tolerance
+    ens.step(10)
+    worst = [ens.run_scalars(k)["poisson_relres_max"] for k in range(ens.R)]
+    assert max(worst) > tol
+    for k in range(ens.R):
+        assert worst[k] >= ens.run_scalars(k)["poisson_relres"]
+    ens.set_graph_mode(1, 40)                # enough cycles: every solve converges
+    ens.step(10)
+    for k in range(ens.R):
+        assert ens.run_scalars(k)["poisson_relres_max"] <= tol

@@ -64,6 +64,23 @@ def assert_same_counters(gc, oc, keys=None):
         assert gc[k] == oc[k], (k, gc[k], oc[k])
 
 
+@pytest.mark.parametrize("n_e,n_t,ncells,scale", [
+    (6000, 3000, 4, 3.0),          # 1500 e / 750 Cu per cell: rank tables, ~30 candidates per cell
+    (20000, 9000, 1, 0.3),         # one cell of 29000 particles
+    (700, 300, 2, 1.0),            # long electron lists, mostly single lookups: the scan select
+])
+def test_dense_cells_bit_exact(pd, xs, n_e, n_t, ncells, scale):
+    """Cells whose id lists exceed the register-cached length: the canonical
+    (ascending id) pair choice must still match the oracle exactly."""
+    cfg, parts = synthetic.rate_cell(n_e=n_e, n_t=n_t, Te_eV=30.0, seed=5, coll_scale=scale, ncells=ncells)
+    cfg.update(nz=2, nr=max(2, ncells))     # the library's grids are at least 2 x 2: a second, empty row
+    sim, o = run_pair(pd, cfg, parts, xs, 3)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["cand_total"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
 @pytest.mark.parametrize("nz,nr,total,scale,steps", [
     (64, 64, 2e5, 3000.0, 4),      # stress: about one candidate per cell
     (37, 53, 6e4, 20000.0, 3),     # ragged grid, dense collisions, many spawns
@@ -123,12 +140,16 @@ def test_rz_external_field_with_injection_bit_exact(pd, xs):
     assert gs["charge"] == pytest.approx(os_["charge"], rel=1e-12)
 
 
-def test_rz_poisson_matches_oracle(pd, xs):
+@pytest.mark.parametrize("n,nr", [
+    (64, 64),      # coarsest level 8 x 8 cells: solved by its stored inverse
+    (96, 96),      # 6 x 6
+    (64, 320),     # R = 5 L: coarsest 8 x 40 cells, 287 unknowns: Gauss-Seidel sweeps
+])
+def test_rz_poisson_matches_oracle(pd, xs, n, nr):
     """Self-consistent field: multigrid (GPU) vs conjugate gradients (CPU) on
     the same fixed-point charge, to the solve tolerance."""
-    n = 64
     cfg, parts = synthetic.rz_plume(n=n, total=8e4, seed=4)
-    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+    cfg.update(nr=nr, field_on=1, inject_on=0, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
     sim, o = run_pair(pd, cfg, parts, xs, 0)
     sim.step(0)
     gphi, ophi = sim.phi(), o.phi()
