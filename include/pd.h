@@ -292,6 +292,59 @@ pd_status pd_autotune(pd_sim* sim, int steps_per_trial, pd_tuning* out);
 pd_status pd_save(pd_sim* sim, const char* path);
 pd_status pd_load(pd_sim* sim, const char* path);
 
+/* ---- Learned warm start of the Poisson solve (Eq. (8)) -------------------
+ *
+ * A six-layer convolutional network predicts the space-charge part of the
+ * potential from the charge density; the multigrid solve then starts from
+ * that prediction instead of the previous step's potential and still runs
+ * to the configured residual.  Definitions (node arrays of one r-z run,
+ * (nz + 1) x (nr + 1), L = nz dz the gap, z_i = i dz):
+ *   rho_max = max |rho|,  x = rho / rho_max  (x = 0 when rho_max = 0)
+ *   t = (phi - V z / L) eps0 / (rho_max L^2)            (training target)
+ *   phi_0 = V z / L + y rho_max L^2 / eps0              (warm start from y ~ t)
+ * Network: 3 x 3 convolutions, zero padding, channels 1 -> 32 -> 32 -> 32 ->
+ * 32 -> 32 -> 1, ReLU after the first five, a bias per output channel.
+ * Parameters (PD_NET_NPARAMS floats): for each layer in order its weights
+ * W[tap][c_out][c_in], tap = 3 (dy + 1) + (dx + 1) for the input node at
+ * (i + dy, j + dx), then its biases.  Layers compute with bfloat16 weights
+ * and activations and float accumulation; the optimiser keeps float master
+ * weights.  Loss: mean over samples and nodes of (y - t)^2; optimiser: Adam. */
+#define PD_NET_NPARAMS 37601
+typedef struct pd_net pd_net;
+
+/* Device workspace for a network that processes up to max_nodes nodes per
+ * call (the sum over the samples of a batch of (nz + 1)(nr + 1)). */
+pd_status pd_net_workspace_size(int64_t max_nodes, size_t* bytes);
+pd_status pd_net_create(int64_t max_nodes, void* dev_workspace, size_t bytes, void* cuda_stream, pd_net** out);
+void pd_net_destroy(pd_net* net);
+/* Host float arrays of PD_NET_NPARAMS values; set resets the optimiser. */
+pd_status pd_net_set_params(pd_net* net, const float* params);
+pd_status pd_net_get_params(pd_net* net, float* params);
+/* Inference on a batch of B samples of H x W nodes stored one after another
+ * (x, y: device float arrays of B H W values). */
+pd_status pd_net_forward(pd_net* net, const float* x, int B, int H, int W, float* y);
+/* Forward and back-propagation of the loss against targets t (device,
+ * B H W floats): *loss (host, may be null) receives the loss and grads
+ * (host, PD_NET_NPARAMS floats, may be null) the gradient; the gradient is
+ * also kept for pd_net_adam.  Synchronises when loss or grads is given. */
+pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, int H, int W, double* loss,
+                           float* grads);
+/* One Adam step (b1, b2, eps as in Kingma and Ba) with the gradient of the
+ * last pd_net_loss_grad. */
+pd_status pd_net_adam(pd_net* net, float lr, float b1, float b2, float eps);
+
+/* Training pairs (x, t) of every run of a simulation from its current
+ * charge and potential (call after a step), written to device float arrays
+ * laid out like the node arrays of pd_get_phi. */
+pd_status pd_warmstart_pairs(pd_sim* sim, float* x, float* t);
+
+/* Starting point of each Poisson solve: PD_WARM_PREVIOUS (default: the
+ * previous step's potential), PD_WARM_COLD (the charge-free potential
+ * V z / L) or PD_WARM_LEARNED (phi_0 from `net`, which must stay alive and
+ * hold at least the simulation's node count).  r-z Poisson mode only. */
+enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2 };
+pd_status pd_set_warm_start(pd_sim* sim, int mode, pd_net* net);
+
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle
  * arrays in device memory, with no allocation of any kind.  The paper has no
  * counterpart: this is a service for callers that hold particles in their own

@@ -169,6 +169,22 @@ def adam_step(params, grad, m, v, k, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def node_density(rho_int, weight, dz, dr, nz, nr):
+    """Node charge density (C/m^3) of an r-z run from its fixed-point node
+    charge (units of e 2^-32 per super-particle, electrons plus heavies):
+    Verboncoeur's node volumes -- axis pi dz dr^2 / 3, interior 2 pi dz dr^2 j,
+    outer wall 2 pi dz dr^2 (nr / 2 - 1 / 6) -- halved on the electrode rows."""
+    j = np.arange(nr + 1, dtype=np.float64)
+    vol = 2.0 * np.pi * dz * dr * dr * j
+    vol[0] = np.pi * dz * dr * dr / 3.0
+    vol[nr] = 2.0 * np.pi * dz * dr * dr * (nr / 2.0 - 1.0 / 6.0)
+    vol = np.tile(vol, (nz + 1, 1))
+    vol[0] *= 0.5
+    vol[nz] *= 0.5
+    q = np.asarray(rho_int, dtype=np.float64).reshape(nz + 1, nr + 1)
+    return 1.602176634e-19 * weight * q / 2.0 ** 32 / vol
+
+
 def training_pair(rho, phi, V, dz):
     """(x, t) of one run from its node density rho (C/m^3) and potential phi
     (V), arrays of shape (nz + 1, nr + 1)."""

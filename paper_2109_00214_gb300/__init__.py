@@ -25,7 +25,10 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_ensemble_create", "pd_ensemble_step", "pd_ensemble_get_scalars", "pd_run_count", "pd_run_layout",
            "pd_get_run_counters", "pd_get_run_density_map", "pd_get_run_energy_spectrum", "pd_load_particles_run",
            "pd_load_particles_device_run", "pd_set_graph_mode", "PdTuning", "pd_get_tuning",
-           "pd_set_tuning", "pd_autotune", "pd_save", "pd_load", "pd_get_rho_phi", "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
+           "pd_set_tuning", "pd_autotune", "pd_save", "pd_load", "pd_get_rho_phi", "Net", "PD_NET_NPARAMS", "pd_net_workspace_size",
+           "pd_net_create", "pd_net_destroy", "pd_net_set_params", "pd_net_get_params", "pd_net_forward",
+           "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
+           "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 28
 PD_NKERNELS = 12
@@ -123,6 +126,16 @@ _SIGS = {
     "pd_save": (C.c_int, [P, C.c_char_p]),
     "pd_load": (C.c_int, [P, C.c_char_p]),
     "pd_get_rho_phi": (C.c_int, [P, Dp, Dp]),
+    "pd_net_workspace_size": (C.c_int, [C.c_int64, C.POINTER(C.c_size_t)]),
+    "pd_net_create": (C.c_int, [C.c_int64, P, C.c_size_t, P, C.POINTER(P)]),
+    "pd_net_destroy": (None, [P]),
+    "pd_net_set_params": (C.c_int, [P, P]),
+    "pd_net_get_params": (C.c_int, [P, P]),
+    "pd_net_forward": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, P]),
+    "pd_net_loss_grad": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, Dp, P]),
+    "pd_net_adam": (C.c_int, [P, C.c_float, C.c_float, C.c_float, C.c_float]),
+    "pd_warmstart_pairs": (C.c_int, [P, P, P]),
+    "pd_set_warm_start": (C.c_int, [P, C.c_int, P]),
     "pd_get_rho": (C.c_int, [P, P, P]),
     "pd_get_phi": (C.c_int, [P, Dp]),
     "pd_get_field": (C.c_int, [P, Dp, Dp]),
@@ -401,6 +414,71 @@ def pd_get_rho_phi(h, nodes):
     return rho, phi
 
 
+PD_NET_NPARAMS = 37601
+WARM_MODES = {"previous": 0, "cold": 1, "learned": 2}
+
+
+def pd_net_workspace_size(max_nodes):
+    n = C.c_size_t(0)
+    _check(None, _lib().pd_net_workspace_size(int(max_nodes), C.byref(n)), "pd_net_workspace_size")
+    return n.value
+
+
+def pd_net_create(max_nodes, ws_ptr, nbytes, stream_ptr):
+    h = P()
+    _check(None, _lib().pd_net_create(int(max_nodes), P(ws_ptr), int(nbytes), P(stream_ptr), C.byref(h)),
+           "pd_net_create")
+    return h
+
+
+def pd_net_destroy(h):
+    _lib().pd_net_destroy(h)
+
+
+def _net_check(h, r, what):
+    if r != 0:
+        raise PdError(f"{what}: {STATUS.get(r, r)}")
+
+
+def pd_net_set_params(h, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != PD_NET_NPARAMS:
+        raise ValueError("need PD_NET_NPARAMS parameters")
+    _net_check(h, _lib().pd_net_set_params(h, _ptr(a)), "pd_net_set_params")
+
+
+def pd_net_get_params(h):
+    a = np.zeros(PD_NET_NPARAMS, np.float32)
+    _net_check(h, _lib().pd_net_get_params(h, _ptr(a)), "pd_net_get_params")
+    return a
+
+
+def pd_net_forward(h, x_ptr, B, H, W, y_ptr):
+    _net_check(h, _lib().pd_net_forward(h, P(x_ptr), int(B), int(H), int(W), P(y_ptr)), "pd_net_forward")
+
+
+def pd_net_loss_grad(h, x_ptr, t_ptr, B, H, W, want_loss=True, want_grads=False):
+    loss = C.c_double(0.0)
+    g = np.zeros(PD_NET_NPARAMS, np.float32) if want_grads else None
+    _net_check(h, _lib().pd_net_loss_grad(h, P(x_ptr), P(t_ptr), int(B), int(H), int(W),
+                                         C.byref(loss) if want_loss else None,
+                                         _ptr(g) if want_grads else None), "pd_net_loss_grad")
+    return (loss.value if want_loss else None), g
+
+
+def pd_net_adam(h, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    _net_check(h, _lib().pd_net_adam(h, float(lr), float(b1), float(b2), float(eps)), "pd_net_adam")
+
+
+def pd_warmstart_pairs(h, x_ptr, t_ptr):
+    _check(h, _lib().pd_warmstart_pairs(h, P(x_ptr), P(t_ptr)), "pd_warmstart_pairs")
+
+
+def pd_set_warm_start(h, mode, net_h=None):
+    m = WARM_MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(h, _lib().pd_set_warm_start(h, m, net_h), "pd_set_warm_start")
+
+
 def pd_get_rho(h, nodes):
     a = np.zeros(nodes, np.int64)
     b = np.zeros(nodes, np.int64)
@@ -474,6 +552,55 @@ def pd_energy_spectrum_static(key_ptr, vz_ptr, vr_ptr, vt_ptr, n, species, lo, h
     return a
 
 
+class Net:
+    """The warm-start network (pd_net) in a torch-allocated device workspace."""
+
+    def __init__(self, max_nodes, params=None, device="cuda", stream=None):
+        import torch
+        load_library()
+        self.max_nodes = int(max_nodes)
+        self.nbytes = pd_net_workspace_size(self.max_nodes)
+        self.ws = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.ws.device)
+        self.h = pd_net_create(self.max_nodes, self.ws.data_ptr(), self.nbytes, self.stream.cuda_stream)
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        pd_net_set_params(self.h, params)
+
+    def params(self):
+        return pd_net_get_params(self.h)
+
+    def forward(self, x):
+        """x: torch CUDA float tensor [B, H, W] -> y (same shape)."""
+        import torch
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        B, H, W = x.shape
+        pd_net_forward(self.h, x.data_ptr(), B, H, W, y.data_ptr())
+        return y
+
+    def loss_grad(self, x, t, want_grads=False):
+        x, t = x.contiguous(), t.contiguous()
+        B, H, W = x.shape
+        return pd_net_loss_grad(self.h, x.data_ptr(), t.data_ptr(), B, H, W, True, want_grads)
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        pd_net_adam(self.h, lr, b1, b2, eps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pd_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Simulation:
     """A pd_sim in a torch-allocated device workspace on a torch stream."""
 
@@ -522,6 +649,19 @@ class Simulation:
 
     def save(self, path):
         pd_save(self.h, path)
+
+    def warmstart_pairs(self):
+        """(x, t) training pairs of the current state as torch CUDA tensors
+        over all nodes (runs end to end)."""
+        import torch
+        x = torch.empty(self.nodes, dtype=torch.float32, device=self.ws.device)
+        t = torch.empty(self.nodes, dtype=torch.float32, device=self.ws.device)
+        pd_warmstart_pairs(self.h, x.data_ptr(), t.data_ptr())
+        return x, t
+
+    def set_warm_start(self, mode, net=None):
+        self._warm_net = net          # keep the network alive while it is in use
+        pd_set_warm_start(self.h, mode, net.h if net is not None else None)
 
     def restore(self, path):
         pd_load(self.h, path)

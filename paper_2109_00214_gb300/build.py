@@ -24,6 +24,7 @@ UNITS = {
     "pd_field.cu": [],
     "pd_noalloc.cu": ["-fmad=false"],
     "pd_stream.cu": ["-fmad=false"],
+    "pd_net.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -21,6 +21,7 @@
 #include "pd_field.h"
 #include "pd_internal.cuh"
 #include "pd_kernels.h"
+#include "pd_net.h"
 
 using namespace pd;
 
@@ -48,7 +49,7 @@ struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
     size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E,
-        phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field;
+        phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base;
     uint32_t nbins_pad, ncell_pad, words_pad;
     uint64_t cap, ncell, nodes, ck_len;
     size_t field_bytes;
@@ -116,6 +117,10 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.ic = take(R * sizeof(InjectConsts));
     L.field_bytes = cf[0].field_mode == PD_FIELD_POISSON ? field_workspace_bytes(nz, nr) : 0;
     L.field = take(L.field_bytes);
+    L.wsx = take(nodes * 4);                               // warm start: network input and output
+    L.wsy = take(nodes * 4);
+    L.rmax = take(R * 8);
+    L.grp_base = take(R * 4);
     L.total = o;
     return L;
 }
@@ -181,6 +186,16 @@ struct pd_sim {
     std::vector<cudaEvent_t> pool;
     uint64_t launches[PD_NKERNELS];
     pd_tuning tune;
+    // warm start of the Poisson solve
+    int warm_mode;
+    pd_net* warm_net;
+    struct Group {
+        int B, H, W, first;   // runs of one grid shape; their node bases at grp_base[first ..]
+    };
+    std::vector<Group> groups;
+    float *wsx, *wsy;
+    double* rmax;
+    uint32_t* grp_base;
 };
 
 namespace {
@@ -443,6 +458,21 @@ void apply_tuning(pd_sim* s, const pd_tuning& t) {
 
 size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
 
+// starting point of the next Poisson solve (PD_WARM_PREVIOUS: phi as it is)
+pd_status warm_start(pd_sim* s) {
+    if (s->warm_mode == PD_WARM_COLD) {
+        warm_apply(s->field, nullptr, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+    } else if (s->warm_mode == PD_WARM_LEARNED) {
+        warm_inputs(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rmax, s->wsx, s->stream);
+        for (const auto& g : s->groups)
+            if (net_forward_at(s->warm_net, s->wsx, s->wsy, g.B, g.H, g.W, s->grp_base + g.first,
+                               (int64_t)total_nodes(s), s->stream))
+                return PD_ERR_CUDA;
+        warm_apply(s->field, s->wsy, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+    }
+    return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ERR_CUDA;
+}
+
 pd_status prime(pd_sim* s) {
     KParams P = kparams(s, 1);
     CK(cudaMemsetAsync(s->rho_e, 0, total_nodes(s) * 8, s->stream));
@@ -453,6 +483,7 @@ pd_status prime(pd_sim* s) {
     }
     if (s->cfgs[0].field_mode == PD_FIELD_POISSON) {
         Timed t(s, K_POISSON);
+        if (warm_start(s) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
         if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream))
             return fail(s, PD_ERR_CUDA, "field solve failed");
         field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
@@ -522,6 +553,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     if (c.field_mode == PD_FIELD_POISSON) {
         {
             Timed t(s, K_POISSON, capturing);
+            if (warm_start(s) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
             const bool host_check = !capturing && !s->graph_on;
             if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, host_check ? 1 : 0,
                             s->graph_cycles, s->stream))
@@ -732,6 +764,12 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->cell_run = (uint16_t*)(w + L.cell_run);
     s->circ_dev = (RunCircuit*)(w + L.circ);
     s->ic_dev = (InjectConsts*)(w + L.ic);
+    s->wsx = PF(L.wsx);
+    s->wsy = PF(L.wsy);
+    s->rmax = (double*)(w + L.rmax);
+    s->grp_base = P32(L.grp_base);
+    s->warm_mode = PD_WARM_PREVIOUS;
+    s->warm_net = nullptr;
     for (int k = 0; k < XS_N; ++k) {
         const int ex = XS_EMIN_EXP + k / XS_SUB, j = k % XS_SUB;
         s->h_xsE[k] = (float)std::ldexp(1.0 + (double)j / XS_SUB, ex);
@@ -1273,6 +1311,54 @@ pd_status pd_get_rho_phi(pd_sim* s, double* rho, double* phi) {
                 rho[k] = QE * c.weight * (double)(he[k] + hh[k]) / 4294967296.0 / node_volume(c, i, j);
             }
     }
+    return PD_OK;
+}
+
+pd_status pd_warmstart_pairs(pd_sim* s, float* x, float* t) {
+    if (!s || !x || !t) return PD_ERR_ARG;
+    if (s->cfgs[0].field_mode != PD_FIELD_POISSON) return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
+    if (!s->primed) {
+        pd_status r = prime(s);
+        if (r != PD_OK) return r;
+    }
+    warm_inputs(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rmax, x, s->stream);
+    warm_targets(s->field, s->phi, s->runs_dev, s->rs, s->rmax, t, s->stream);
+    CK(cudaGetLastError());
+    return PD_OK;
+}
+
+pd_status pd_set_warm_start(pd_sim* s, int mode, pd_net* net) {
+    if (!s) return PD_ERR_ARG;
+    if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED)
+        return fail(s, PD_ERR_ARG, "bad warm-start mode");
+    if (mode != PD_WARM_PREVIOUS && s->cfgs[0].field_mode != PD_FIELD_POISSON)
+        return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
+    if (mode == PD_WARM_LEARNED) {
+        if (!net) return fail(s, PD_ERR_ARG, "learned warm start needs a network");
+        if (net_max_nodes(net) < (int64_t)total_nodes(s))
+            return fail(s, PD_ERR_ARG, "network holds fewer nodes than the simulation");
+        // batches of runs of one grid shape
+        std::vector<pd_sim::Group> groups;
+        std::vector<uint32_t> bases;
+        std::vector<int> done(s->R, 0);
+        for (int r = 0; r < s->R; ++r) {
+            if (done[r]) continue;
+            pd_sim::Group g{0, s->cfgs[r].nz + 1, s->cfgs[r].nr + 1, (int)bases.size()};
+            for (int q = r; q < s->R; ++q)
+                if (!done[q] && s->cfgs[q].nz == s->cfgs[r].nz && s->cfgs[q].nr == s->cfgs[r].nr) {
+                    bases.push_back(s->node_base[q]);
+                    done[q] = 1;
+                    ++g.B;
+                }
+            groups.push_back(g);
+        }
+        CK(cudaMemcpyAsync(s->grp_base, bases.data(), bases.size() * 4, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        s->groups = groups;
+    }
+    drop_graph(s);
+    s->warm_mode = mode;
+    s->warm_net = mode == PD_WARM_LEARNED ? net : nullptr;
     return PD_OK;
 }
 

@@ -590,4 +590,92 @@ void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float
     k_solve_epilogue<<<1, 128, 0, s>>>(fs.done, fs.nruns, st, rs);
 }
 
+// ------------------------------------------------------------------
+// warm start
+// ------------------------------------------------------------------
+__device__ __forceinline__ double node_rho(const long long* rho_e, const long long* rho_h, const double* verb_base,
+                                           int fo, const RunInfo& RI, int i, int j, uint32_t g) {
+    const double qw = QE_ * RI.weight / 4294967296.0;
+    double vol = verb_base[fo + j];
+    if (i == 0 || i == RI.nz) vol *= 0.5;
+    return qw * (double)(rho_e[g] + rho_h[g]) / vol;
+}
+
+__global__ void k_warm_rmax(const long long* rho_e, const long long* rho_h, const double* verb_base,
+                            const int* fvb_off, const RunInfo* runs, unsigned long long* rmax_bits) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int W = RI.nr + 1, n = (RI.nz + 1) * W;
+    double m = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = k / W, j = k - i * W;
+        m = fmax(m, fabs(node_rho(rho_e, rho_h, verb_base, fvb_off[run], RI, i, j, RI.node_base + (uint32_t)k)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&rmax_bits[run], (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_warm_x(const long long* rho_e, const long long* rho_h, const double* verb_base, const int* fvb_off,
+                         const RunInfo* runs, const double* rmax, float* x) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int W = RI.nr + 1, n = (RI.nz + 1) * W;
+    const double rm = rmax[run];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = k / W, j = k - i * W;
+        const uint32_t g = RI.node_base + (uint32_t)k;
+        x[g] = rm > 0.0 ? (float)(node_rho(rho_e, rho_h, verb_base, fvb_off[run], RI, i, j, g) / rm) : 0.0f;
+    }
+}
+
+__global__ void k_warm_apply(const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
+                             const double* dzr, double* phi) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int W = RI.nr + 1, n = (RI.nz - 1) * W;
+    const double V = rs[run].V, L = RI.nz * dzr[2 * run];
+    const double s = y ? rmax[run] * L * L / EPS0_ : 0.0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int i = 1 + q / W;
+        const uint32_t g = RI.node_base + (uint32_t)(W + q);
+        const double lap = V * (double)i / (double)RI.nz;
+        phi[g] = y ? lap + (double)y[g] * s : lap;
+    }
+}
+
+__global__ void k_warm_targets(const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
+                               const double* dzr, float* t) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int W = RI.nr + 1, n = (RI.nz + 1) * W;
+    const double V = rs[run].V, L = RI.nz * dzr[2 * run], rm = rmax[run];
+    const double s = rm > 0.0 ? EPS0_ / (rm * L * L) : 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int i = k / W;
+        const uint32_t g = RI.node_base + (uint32_t)k;
+        t[g] = (float)((phi[g] - V * (double)i / (double)RI.nz) * s);
+    }
+}
+
+void warm_inputs(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
+                 double* rmax, float* x, cudaStream_t s) {
+    const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    cudaMemsetAsync(rmax, 0, (size_t)fs.nruns * 8, s);
+    k_warm_rmax<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.verb_base, fs.fvb_off, runs, (unsigned long long*)rmax);
+    k_warm_x<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.verb_base, fs.fvb_off, runs, rmax, x);
+}
+
+void warm_apply(FieldSolver& fs, const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
+                double* phi, cudaStream_t s) {
+    const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    k_warm_apply<<<g, fs.threads, 0, s>>>(y, runs, rs, rmax, fs.dzr, phi);
+}
+
+void warm_targets(FieldSolver& fs, const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
+                  float* t, cudaStream_t s) {
+    const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    k_warm_targets<<<g, fs.threads, 0, s>>>(phi, runs, rs, rmax, fs.dzr, t);
+}
+
 }  // namespace pd

@@ -63,4 +63,16 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
 void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, RunState* rs,
                   cudaStream_t s);
 
+// Warm start of the solve (see pd_set_warm_start): rmax[run] = max |rho| of
+// the run's nodes (C/m^3, Verboncoeur volumes, halved on the electrode rows)
+// and x = rho / rmax at the run's nodes
+void warm_inputs(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
+                 double* rmax, float* x, cudaStream_t s);
+// interior rows of phi := V z / L + y rmax L^2 / eps0 (y = null: V z / L)
+void warm_apply(FieldSolver& fs, const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
+                double* phi, cudaStream_t s);
+// training targets t = (phi - V z / L) eps0 / (rmax L^2) at every node
+void warm_targets(FieldSolver& fs, const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
+                  float* t, cudaStream_t s);
+
 }  // namespace pd

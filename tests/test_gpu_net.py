@@ -1,0 +1,164 @@
+"""The warm-start network on the GPU against the float64 oracle (oracle/cnn.py,
+in its bfloat16 mirror): forward pass, loss, every parameter's gradient and
+Adam; the training pairs of a simulation against the oracle's; and the
+Poisson warm-start modes (the solve still reaches its tolerance from any
+starting point).
+
+Tolerances: both sides round the same values to bfloat16 and differ in the
+order of their float sums (about 1e-6 relative), which now and then moves a
+value across a bfloat16 rounding boundary (one unit in the 8th bit).  Such
+flips stay rare and isolated, so the norms agree to ~1e-4; the bounds below
+leave a factor of ten or more."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def pd(torch):
+    import paper_2109_00214_gb300 as m
+    m.load_library()
+    return m
+
+
+def _params(seed):
+    p = cnn.init_params(seed)
+    rng = np.random.default_rng(seed + 100)
+    o = 0
+    for nw, nb in cnn.layer_sizes():
+        p[o + nw:o + nw + nb] = 0.05 * rng.standard_normal(nb)
+        o += nw + nb
+    return p.astype(np.float32)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 21, 37), (1, 8, 16), (3, 5, 3)])
+def test_forward_loss_and_gradients_match_the_oracle(pd, torch, B, H, W):
+    rng = np.random.default_rng(B * 1000 + H * 10 + W)
+    p = _params(B + H + W)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    t = (0.1 * rng.standard_normal((B, H, W))).astype(np.float32)
+    net = pd.Net(B * H * W, params=p)
+    xd = torch.from_numpy(x).cuda()
+    td = torch.from_numpy(t).cuda()
+    y = net.forward(xd).cpu().numpy()
+    p64 = p.astype(np.float64)
+    yo, _ = cnn.forward(p64, x, bf16=True)
+    assert _rel(y, yo) <= 2e-3
+    loss, g = net.loss_grad(xd, td, want_grads=True)
+    lo, go = cnn.loss_and_grad(p64, x, t, bf16=True)
+    assert loss == pytest.approx(lo, rel=2e-3)
+    o = 0
+    for l, (nw, nb) in enumerate(cnn.layer_sizes()):
+        assert _rel(g[o:o + nw], go[o:o + nw]) <= 1e-2, ("weights", l)
+        assert _rel(g[o + nw:o + nw + nb], go[o + nw:o + nw + nb]) <= 1e-2, ("biases", l)
+        o += nw + nb
+    net.close()
+
+
+def test_gradient_check_fails_for_a_wrong_gradient(pd, torch):
+    """The comparison above has teeth: the GPU gradient is far from the
+    oracle's gradient of a perturbed problem (targets shifted)."""
+    rng = np.random.default_rng(3)
+    B, H, W = 1, 12, 20
+    p = _params(5)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    t = (0.1 * rng.standard_normal((B, H, W))).astype(np.float32)
+    net = pd.Net(B * H * W, params=p)
+    _, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), want_grads=True)
+    _, go = cnn.loss_and_grad(p.astype(np.float64), x, t + 0.05, bf16=True)
+    assert _rel(g, go) > 0.05
+    net.close()
+
+
+def test_adam_matches_the_oracle(pd, torch):
+    rng = np.random.default_rng(4)
+    B, H, W = 2, 10, 18
+    p = _params(6)
+    net = pd.Net(B * H * W, params=p)
+    w = p.astype(np.float64)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for k in (1, 2, 3):
+        x = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+        t = torch.from_numpy((0.1 * rng.standard_normal((B, H, W))).astype(np.float32)).cuda()
+        _, g = net.loss_grad(x, t, want_grads=True)
+        net.adam(lr=1e-3)
+        w, m, v = cnn.adam_step(w, g.astype(np.float64), m, v, k, lr=1e-3)
+        assert np.abs(net.params() - w).max() <= 1e-6
+    net.close()
+
+
+def test_training_lowers_the_loss(pd, torch):
+    rng = np.random.default_rng(8)
+    B, H, W = 4, 33, 33
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    x = np.stack([np.exp(-((ii - rng.uniform(5, 28)) ** 2 + (jj - rng.uniform(5, 28)) ** 2) / 20.0)
+                  for _ in range(B)]).astype(np.float32)
+    t = (0.3 * x + 0.1 * np.roll(x, 2, axis=1)).astype(np.float32)
+    net = pd.Net(B * H * W, params=_params(9))
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    l0, _ = net.loss_grad(xd, td)
+    for _ in range(150):
+        net.loss_grad(xd, td, want_grads=False)
+        net.adam(lr=2e-3)
+    l1, _ = net.loss_grad(xd, td)
+    assert l1 < 0.2 * l0
+    net.close()
+
+
+def _plume(n=32, total=2e4, seed=21):
+    cfg, parts = synthetic.rz_plume(n=n, total=total, seed=seed)
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+    return cfg, parts
+
+
+def test_training_pairs_match_the_oracle(pd, torch, xs):
+    cfg, parts = _plume()
+    sim = pd.Simulation(cfg, xs)
+    sim.load(parts)
+    sim.step(0)
+    x, t = (a.cpu().numpy().astype(np.float64).reshape(sim.nzn, sim.nrn) for a in sim.warmstart_pairs())
+    o = oracle.Oracle(cfg, fp64=True)
+    o.set_cross_sections(xs)
+    o.load(parts)
+    o.prime()
+    rho = cnn.node_density(sum(o.rho()), cfg["weight"], cfg["dz"], cfg["dr"], cfg["nz"], cfg["nr"])
+    xo, to = cnn.training_pair(rho, o.phi().reshape(sim.nzn, sim.nrn), cfg["V0"], cfg["dz"])
+    assert np.abs(x - xo).max() <= 1e-6
+    assert np.abs(t - to).max() <= 1e-5 * np.abs(to).max()
+    assert np.abs(to).max() > 0
+
+
+def test_warm_start_modes_reach_the_tolerance(pd, torch, xs):
+    cfg, parts = _plume(n=64, total=6e4)
+    net = pd.Net((cfg["nz"] + 1) * (cfg["nr"] + 1), params=_params(10))
+    cycles = {}
+    for mode in ("previous", "cold", "learned"):
+        sim = pd.Simulation(cfg, xs)
+        sim.load(parts)
+        sim.step(2)
+        sim.set_warm_start(mode, net if mode == "learned" else None)
+        sim.step(1)
+        sc = sim.scalars()
+        assert sc["poisson_relres"] <= cfg["poisson_tol"], mode
+        cycles[mode] = sc["poisson_cycles"]
+        sim.close()
+    assert cycles["cold"] >= cycles["previous"]
+    net.close()

@@ -127,18 +127,14 @@ def test_training_pairs_follow_eq8_linearity(xs):
     o.load(parts)
     o.prime()
     n = cfg["nz"] + 1
-    rho_int = sum(o.rho()).reshape(n, -1).astype(np.float64)
+    rho_int = sum(o.rho()).astype(np.float64)
     phi = o.phi().reshape(n, -1)
-    # node density with Verboncoeur's volumes (axis, interior, outer; half on the electrodes)
-    dz, dr, nr = cfg["dz"], cfg["dr"], cfg["nr"]
-    j = np.arange(nr + 1, dtype=np.float64)
-    vol = 2 * np.pi * dz * dr * dr * j
-    vol[0] = np.pi * dz * dr * dr / 3
-    vol[nr] = 2 * np.pi * dz * dr * dr * (nr / 2 - 1 / 6)
-    vol = np.tile(vol, (n, 1))
-    vol[0] *= 0.5
-    vol[-1] *= 0.5
-    rho = 1.602176634e-19 * cfg["weight"] * rho_int / 2.0 ** 32 / vol
+    dz = cfg["dz"]
+    rho = cnn.node_density(rho_int, cfg["weight"], dz, cfg["dr"], cfg["nz"], cfg["nr"])
+    # the volumes sum to the cylinder: a uniform density is returned as given
+    vol = 1.602176634e-19 * cfg["weight"] / 2.0 ** 32 / cnn.node_density(np.ones(rho.size), cfg["weight"], dz,
+                                                                       cfg["dr"], cfg["nz"], cfg["nr"])
+    assert vol.sum() == pytest.approx(np.pi * (cfg["nr"] * cfg["dr"]) ** 2 * cfg["nz"] * dz, rel=1e-12)
     x, t = cnn.training_pair(rho, phi, cfg["V0"], dz)
     assert np.abs(x).max() == pytest.approx(1.0)
     assert np.abs(t).max() > 0
