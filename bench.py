@@ -13,6 +13,14 @@ second).  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload ensemble [--steps K] [--warmup W]
+  python bench.py --workload warmstart
+
+--workload warmstart trains the warm-start network on (rho, phi) pairs taken
+every 2 steps from plume runs on 256^2 and 512^2 grids (runs split 90/10 into
+training and held-out runs) and compares, on the held-out runs, the multigrid
+cycles and step time to the residual tolerance from three starting points:
+the charge-free potential (cold), the previous step's potential, and the
+network's prediction.
 
 --workload ensemble times the batched breakdown ensemble instead: 64 r-z runs
 (8 seeds x gap voltages 2-10 kV, grids 64^2..256^2 cells, 1e5..2e6 particles
@@ -62,8 +70,14 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=512, help="rows of cells in the CPU-baseline sample")
     p.add_argument("--cpu-steps", type=int, default=10)
-    p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble"])
+    p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble", "warmstart"])
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--ws-sizes", default="256,512", help="grid sizes of the warm-start runs")
+    p.add_argument("--ws-runs", type=int, default=10, help="runs per grid size (the last one is held out)")
+    p.add_argument("--ws-pairs", type=int, default=500, help="pairs per run, one every 2 steps")
+    p.add_argument("--ws-particles", type=float, default=4e6, help="particles of a 512^2 run (scaled by area)")
+    p.add_argument("--ws-iters", type=int, default=3000)
+    p.add_argument("--ws-eval-steps", type=int, default=30)
     a = p.parse_args()
     if a.workload == "ensemble":
         if "--steps" not in sys.argv:
@@ -389,14 +403,115 @@ def run_ensemble(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+WS_METRIC = "Poisson multigrid cycles per step to relres 1e-8: cold vs previous-step vs learned warm start"
+
+
+def run_warmstart(args, ws, rank, local):
+    import torch
+    import paper_2109_00214_gb300 as pd
+    from paper_2109_00214_gb300 import warmstart as W
+    import synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pd.load_library()
+    xs = synthetic.standin_cross_sections()
+    sizes = [int(v) for v in args.ws_sizes.split(",")]
+    kinds = ("absolute", "delta")
+    t0 = time.perf_counter()
+    sets = {k: [] for k in kinds}
+    held = {k: {} for k in kinds}
+    evals = {}
+    for n in sizes:
+        total = args.ws_particles * (n / 512.0) ** 2
+        runs = []
+        for k in range(args.ws_runs):
+            cfg, parts = synthetic.rz_plume(n=n, total=total, seed=100 * n + k + 1)
+            cfg.update(field_on=1, inject_on=0, run=k, V0=1e3 * (2 + (k % 8)), poisson_tol=1e-8)
+            runs.append((cfg, parts))
+        train_runs, test_runs = runs[:-1], runs[-1:]
+        tr = W.collect_pairs([c for c, _ in train_runs], [p for _, p in train_runs], xs, args.ws_pairs,
+                             kinds=kinds, device=dev)
+        te = W.collect_pairs([c for c, _ in test_runs], [p for _, p in test_runs], xs, args.ws_pairs,
+                             kinds=kinds, device=dev)
+        for k in kinds:
+            sets[k].append((tr[k][0].flatten(0, 1), tr[k][1].flatten(0, 1)))
+            held[k][n] = (te[k][0].flatten(0, 1), te[k][1].flatten(0, 1))
+        evals[n] = test_runs[0]
+        del tr, te
+    t_data = time.perf_counter() - t0
+    # mini-batches of about 5.3e5 nodes (8 grids of 257^2, 2 of 513^2), at most 16 grids
+    batch = [int(min(16, max(1, round(5.3e5 / (n + 1) ** 2)))) for n in sizes]
+    max_nodes = max(b * (n + 1) ** 2 for b, n in zip(batch, sizes))
+    rng = np.random.default_rng(1)
+    p0 = []
+    for ci, co in ((1, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1)):
+        p0.append(rng.standard_normal(9 * co * ci) * np.sqrt(2.0 / (9 * ci)))
+        p0.append(np.zeros(co))
+    p0 = np.concatenate(p0).astype(np.float32)
+    nets, train_info = {}, {}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for k in kinds:
+        net = pd.Net(max_nodes, params=p0, device=dev)
+        torch.cuda.synchronize()
+        e0.record(net.stream)
+        hist = W.train(net, sets[k], args.ws_iters, batch, lr=1e-3, lr_final=5e-5,
+                       log_every=max(1, args.ws_iters // 10))
+        e1.record(net.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tl = {str(n): {"test_loss": W.test_loss(net, *held[k][n], batch=b),
+                       "test_target_mean_square": float(torch.mean(held[k][n][1].double() ** 2).item())}
+              for n, b in zip(sizes, batch)}
+        train_info[k] = {"loss_history": hist, "train_ms": ms, "ms_per_iter": ms / max(args.ws_iters, 1),
+                         "held_out": tl}
+        nets["learned" if k == "absolute" else "learned_delta"] = net
+    modes = ("previous", "cold", "learned", "learned_delta")
+    results = {str(n): W.compare_starts(*evals[n], xs, nets, args.ws_eval_steps, modes=modes, device=dev)
+               for n in sizes}
+    # inference time on the largest grid
+    n = max(sizes)
+    net = nets["learned"]
+    x1 = held["absolute"][n][0][:1].contiguous()
+    for _ in range(3):
+        net.forward(x1)
+    e0.record(net.stream)
+    for _ in range(20):
+        net.forward(x1)
+    e1.record(net.stream)
+    torch.cuda.synchronize()
+    infer_ms = e0.elapsed_time(e1) / 20
+    flops = 2.0 * (n + 1) ** 2 * (9 * 32 * 2 + 4 * 9 * 32 * 32)
+    big = results[str(n)]
+    best = min(("learned", "learned_delta"), key=lambda m: big[m]["cycles_per_step"])
+    if rank == 0:
+        line = {"metric": WS_METRIC, "value": big[best]["cycles_per_step"], "unit": "cycles/step",
+                "n_gpus": ws, "steps": args.ws_eval_steps, "warmup": 2,
+                "ms_per_step": big[best]["ms_per_step"], "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 (network), f64 (solve)", "data": "synthetic",
+                "config": {"workload": f"learned Poisson warm start: {len(sizes)} x {args.ws_runs} plume runs on "
+                                       f"{sizes} grids, {args.ws_pairs} (rho, phi) pairs per run every 2 steps, "
+                                       f"90/10 train/held-out split by run; 6 x conv3x3 (32 ch), bf16 weights, "
+                                       f"fp32 accumulation; evaluated on the held-out {n}^2 run",
+                           "pairs_per_kind": int(sum(x.shape[0] for x, _ in sets["absolute"]) +
+                                                 sum(h[0].shape[0] for h in held["absolute"].values())),
+                           "train_iters": args.ws_iters, "batch": batch, "value_mode": best},
+                "results": results, "training": train_info, "data_s": t_data,
+                "inference": {"grid": n, "ms": infer_ms, "tflops": flops / (infer_ms * 1e-3) / 1e12}}
+        print(json.dumps(line), flush=True)
+    for net in nets.values():
+        net.close()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "ensemble":
-        run_ensemble(args, ws, rank, local)
+    if args.workload in ("ensemble", "warmstart"):
+        (run_ensemble if args.workload == "ensemble" else run_warmstart)(args, ws, rank, local)
         if ws > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -294,14 +294,19 @@ pd_status pd_load(pd_sim* sim, const char* path);
 
 /* ---- Learned warm start of the Poisson solve (Eq. (8)) -------------------
  *
- * A six-layer convolutional network predicts the space-charge part of the
- * potential from the charge density; the multigrid solve then starts from
- * that prediction instead of the previous step's potential and still runs
- * to the configured residual.  Definitions (node arrays of one r-z run,
- * (nz + 1) x (nr + 1), L = nz dz the gap, z_i = i dz):
- *   rho_max = max |rho|,  x = rho / rho_max  (x = 0 when rho_max = 0)
- *   t = (phi - V z / L) eps0 / (rho_max L^2)            (training target)
- *   phi_0 = V z / L + y rho_max L^2 / eps0              (warm start from y ~ t)
+ * A six-layer convolutional network predicts the potential from the charge
+ * density so that the multigrid solve starts closer to its answer; the solve
+ * still runs to the configured residual.  Node arrays of one r-z run are
+ * (nz + 1) x (nr + 1); z_i = i dz, L = nz dz; rho in C/m^3 (Verboncoeur's
+ * node volumes, halved on the electrode rows).  Two formulations:
+ *   absolute (PD_WARM_LEARNED): d = rho, base = V z / L;
+ *   delta (PD_WARM_LEARNED_DELTA): d = rho - rho', base = phi' + (V - V') z / L,
+ *     where rho', phi', V' belong to the previous solve;
+ * and, for both, with m = max |d| over the run's nodes:
+ *   x = d / m  (x = 0 when m = 0)                       (network input)
+ *   t = (phi - base) eps0 / (m dz^2)                    (training target)
+ *   phi_0 = base + y m dz^2 / eps0                      (warm start from y ~ t)
+ * (dz^2 makes t the potential in grid units of the unit-spacing Laplacian.)
  * Network: 3 x 3 convolutions, zero padding, channels 1 -> 32 -> 32 -> 32 ->
  * 32 -> 32 -> 1, ReLU after the first five, a bias per output channel.
  * Parameters (PD_NET_NPARAMS floats): for each layer in order its weights
@@ -333,16 +338,21 @@ pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, i
  * last pd_net_loss_grad. */
 pd_status pd_net_adam(pd_net* net, float lr, float b1, float b2, float eps);
 
-/* Training pairs (x, t) of every run of a simulation from its current
- * charge and potential (call after a step), written to device float arrays
- * laid out like the node arrays of pd_get_phi. */
-pd_status pd_warmstart_pairs(pd_sim* sim, float* x, float* t);
+/* Training pairs (x, t) of every run from the most recent solve (kind
+ * PD_PAIRS_ABSOLUTE) or from the two most recent solves (PD_PAIRS_DELTA),
+ * written to device float arrays laid out like the node arrays of
+ * pd_get_phi.  PD_ERR_STATE until enough solves have run since the
+ * simulation was created or loaded (one, or two for delta pairs). */
+enum { PD_PAIRS_ABSOLUTE = 0, PD_PAIRS_DELTA = 1 };
+pd_status pd_warmstart_pairs(pd_sim* sim, int kind, float* x, float* t);
 
 /* Starting point of each Poisson solve: PD_WARM_PREVIOUS (default: the
  * previous step's potential), PD_WARM_COLD (the charge-free potential
- * V z / L) or PD_WARM_LEARNED (phi_0 from `net`, which must stay alive and
- * hold at least the simulation's node count).  r-z Poisson mode only. */
-enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2 };
+ * V z / L), PD_WARM_LEARNED or PD_WARM_LEARNED_DELTA (phi_0 from `net`,
+ * which must stay alive and hold at least the simulation's node count; the
+ * delta form falls back to the previous potential on the first solve after
+ * create or load).  r-z Poisson mode only.  Drops a captured graph. */
+enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2, PD_WARM_LEARNED_DELTA = 3 };
 pd_status pd_set_warm_start(pd_sim* sim, int mode, pd_net* net);
 
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle

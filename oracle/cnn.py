@@ -7,13 +7,18 @@ The warm start is not part of the paper's method: it predicts the potential
 of Eq. (8) from the charge density so that the multigrid solve starts close
 to its answer.  Definitions used here (and by the library):
 
-Training pair of one r-z run (node arrays of shape (nz + 1, nr + 1)):
-    rho_max = max |rho|,  L = nz dz (the gap),  z_i = i dz
-    x = rho / rho_max                                  (0 where rho_max = 0)
-    phi_L = V z / L          (the charge-free solution of Eq. (8): linear in z)
-    t = (phi - phi_L) eps0 / (rho_max L^2)
+Training pair of one r-z run (node arrays of shape (nz + 1, nr + 1)),
+z_i = i dz, L = nz dz (the gap), absolute form:
+    d = rho,  base = V z / L     (the charge-free solution of Eq. (8): linear in z)
+delta form, against the previous solve (rho', phi', V'):
+    d = rho - rho',  base = phi' + (V - V') z / L
+and for both, with m = max |d|:
+    x = d / m                                          (0 where m = 0)
+    t = (phi - base) eps0 / (m dz^2)
 and the warm start built from a prediction y of t:
-    phi_0 = phi_L + y rho_max L^2 / eps0.
+    phi_0 = base + y m dz^2 / eps0.
+Dividing by dz^2 gives the potential in grid units of the unit-spacing
+Laplacian, the scale a convolution over the grid sees.
 
 Network: six 3 x 3 convolutions over the node grid, output the size of the
 input (zero padding), channels 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU
@@ -185,24 +190,29 @@ def node_density(rho_int, weight, dz, dr, nz, nr):
     return 1.602176634e-19 * weight * q / 2.0 ** 32 / vol
 
 
-def training_pair(rho, phi, V, dz):
+def training_pair(rho, phi, V, dz, rho_prev=None, phi_prev=None, V_prev=0.0):
     """(x, t) of one run from its node density rho (C/m^3) and potential phi
-    (V), arrays of shape (nz + 1, nr + 1)."""
+    (V), arrays of shape (nz + 1, nr + 1); the delta form when rho_prev and
+    phi_prev (the previous solve's) are given."""
     rho = np.asarray(rho, dtype=np.float64)
     phi = np.asarray(phi, dtype=np.float64)
     nz = rho.shape[0] - 1
-    L = nz * dz
-    z = np.arange(nz + 1)[:, None] * dz
-    rmax = np.abs(rho).max()
-    if rmax == 0.0:
+    zL = (np.arange(nz + 1)[:, None] / nz) * np.ones_like(rho)
+    if rho_prev is None:
+        d, base = rho, V * zL
+    else:
+        d = rho - np.asarray(rho_prev, dtype=np.float64)
+        base = np.asarray(phi_prev, dtype=np.float64) + (V - V_prev) * zL
+    m = np.abs(d).max()
+    if m == 0.0:
         return np.zeros_like(rho), np.zeros_like(rho)
-    return rho / rmax, (phi - V * z / L) * EPS0 / (rmax * L * L)
+    return d / m, (phi - base) * EPS0 / (m * dz * dz)
 
 
-def warm_start(y, rho_max, V, dz):
-    """phi_0 from a prediction y of t."""
+def warm_start(y, m, V, dz, phi_prev=None, V_prev=0.0):
+    """phi_0 (interior and electrode rows alike) from a prediction y of t."""
     y = np.asarray(y, dtype=np.float64)
     nz = y.shape[0] - 1
-    L = nz * dz
-    z = np.arange(nz + 1)[:, None] * dz
-    return V * z / L + y * rho_max * L * L / EPS0
+    zL = (np.arange(nz + 1)[:, None] / nz) * np.ones_like(y)
+    base = V * zL if phi_prev is None else np.asarray(phi_prev, dtype=np.float64) + (V - V_prev) * zL
+    return base + y * m * dz * dz / EPS0

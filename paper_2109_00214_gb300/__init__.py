@@ -134,7 +134,7 @@ _SIGS = {
     "pd_net_forward": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, P]),
     "pd_net_loss_grad": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, Dp, P]),
     "pd_net_adam": (C.c_int, [P, C.c_float, C.c_float, C.c_float, C.c_float]),
-    "pd_warmstart_pairs": (C.c_int, [P, P, P]),
+    "pd_warmstart_pairs": (C.c_int, [P, C.c_int, P, P]),
     "pd_set_warm_start": (C.c_int, [P, C.c_int, P]),
     "pd_get_rho": (C.c_int, [P, P, P]),
     "pd_get_phi": (C.c_int, [P, Dp]),
@@ -415,7 +415,8 @@ def pd_get_rho_phi(h, nodes):
 
 
 PD_NET_NPARAMS = 37601
-WARM_MODES = {"previous": 0, "cold": 1, "learned": 2}
+WARM_MODES = {"previous": 0, "cold": 1, "learned": 2, "learned_delta": 3}
+PAIR_KINDS = {"absolute": 0, "delta": 1}
 
 
 def pd_net_workspace_size(max_nodes):
@@ -470,8 +471,9 @@ def pd_net_adam(h, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     _net_check(h, _lib().pd_net_adam(h, float(lr), float(b1), float(b2), float(eps)), "pd_net_adam")
 
 
-def pd_warmstart_pairs(h, x_ptr, t_ptr):
-    _check(h, _lib().pd_warmstart_pairs(h, P(x_ptr), P(t_ptr)), "pd_warmstart_pairs")
+def pd_warmstart_pairs(h, kind, x_ptr, t_ptr):
+    k = PAIR_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _check(h, _lib().pd_warmstart_pairs(h, k, P(x_ptr), P(t_ptr)), "pd_warmstart_pairs")
 
 
 def pd_set_warm_start(h, mode, net_h=None):
@@ -650,13 +652,13 @@ class Simulation:
     def save(self, path):
         pd_save(self.h, path)
 
-    def warmstart_pairs(self):
-        """(x, t) training pairs of the current state as torch CUDA tensors
-        over all nodes (runs end to end)."""
+    def warmstart_pairs(self, kind="absolute"):
+        """(x, t) training pairs ("absolute" or "delta") of the latest solves
+        as torch CUDA tensors over all nodes (runs end to end)."""
         import torch
         x = torch.empty(self.nodes, dtype=torch.float32, device=self.ws.device)
         t = torch.empty(self.nodes, dtype=torch.float32, device=self.ws.device)
-        pd_warmstart_pairs(self.h, x.data_ptr(), t.data_ptr())
+        pd_warmstart_pairs(self.h, kind, x.data_ptr(), t.data_ptr())
         return x, t
 
     def set_warm_start(self, mode, net=None):

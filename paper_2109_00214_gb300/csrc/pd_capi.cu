@@ -49,7 +49,8 @@ struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
     size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E,
-        phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base;
+        phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
+        rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
     uint64_t cap, ncell, nodes, ck_len;
     size_t field_bytes;
@@ -121,6 +122,11 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.wsy = take(nodes * 4);
     L.rmax = take(R * 8);
     L.grp_base = take(R * 4);
+    L.rho_last = take(nodes * 8);                          // solve history of the warm start
+    L.rho_prev = take(nodes * 8);
+    L.phi_prev = take(nodes * 8);
+    L.V_last = take(R * 8);
+    L.V_prev = take(R * 8);
     L.total = o;
     return L;
 }
@@ -196,6 +202,8 @@ struct pd_sim {
     float *wsx, *wsy;
     double* rmax;
     uint32_t* grp_base;
+    WarmHistory whist;
+    int64_t solves;          // Poisson solves since create / load (history depth)
 };
 
 namespace {
@@ -458,18 +466,22 @@ void apply_tuning(pd_sim* s, const pd_tuning& t) {
 
 size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
 
-// starting point of the next Poisson solve (PD_WARM_PREVIOUS: phi as it is)
+// before each Poisson solve: the solve history, then the starting point
+// (PD_WARM_PREVIOUS: phi as it is)
 pd_status warm_start(pd_sim* s) {
+    warm_history(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rs, s->phi, s->whist, s->stream);
+    const bool delta = s->warm_mode == PD_WARM_LEARNED_DELTA;
     if (s->warm_mode == PD_WARM_COLD) {
-        warm_apply(s->field, nullptr, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
-    } else if (s->warm_mode == PD_WARM_LEARNED) {
-        warm_inputs(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rmax, s->wsx, s->stream);
+        warm_apply(s->field, nullptr, s->whist, false, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+    } else if (s->warm_mode == PD_WARM_LEARNED || (delta && s->solves >= 1)) {
+        warm_inputs(s->field, s->whist, delta, s->runs_dev, s->rmax, s->wsx, s->stream);
         for (const auto& g : s->groups)
             if (net_forward_at(s->warm_net, s->wsx, s->wsy, g.B, g.H, g.W, s->grp_base + g.first,
                                (int64_t)total_nodes(s), s->stream))
                 return PD_ERR_CUDA;
-        warm_apply(s->field, s->wsy, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+        warm_apply(s->field, s->wsy, s->whist, delta, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
     }
+    s->solves += 1;
     return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ERR_CUDA;
 }
 
@@ -770,6 +782,9 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->grp_base = P32(L.grp_base);
     s->warm_mode = PD_WARM_PREVIOUS;
     s->warm_net = nullptr;
+    s->whist = WarmHistory{(double*)(w + L.rho_last), (double*)(w + L.rho_prev), (double*)(w + L.phi_prev),
+                          (double*)(w + L.V_last), (double*)(w + L.V_prev)};
+    s->solves = 0;
     for (int k = 0; k < XS_N; ++k) {
         const int ex = XS_EMIN_EXP + k / XS_SUB, j = k % XS_SUB;
         s->h_xsE[k] = (float)std::ldexp(1.0 + (double)j / XS_SUB, ex);
@@ -1314,26 +1329,30 @@ pd_status pd_get_rho_phi(pd_sim* s, double* rho, double* phi) {
     return PD_OK;
 }
 
-pd_status pd_warmstart_pairs(pd_sim* s, float* x, float* t) {
-    if (!s || !x || !t) return PD_ERR_ARG;
+pd_status pd_warmstart_pairs(pd_sim* s, int kind, float* x, float* t) {
+    if (!s || !x || !t || (kind != PD_PAIRS_ABSOLUTE && kind != PD_PAIRS_DELTA)) return PD_ERR_ARG;
     if (s->cfgs[0].field_mode != PD_FIELD_POISSON) return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
     if (!s->primed) {
         pd_status r = prime(s);
         if (r != PD_OK) return r;
     }
-    warm_inputs(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rmax, x, s->stream);
-    warm_targets(s->field, s->phi, s->runs_dev, s->rs, s->rmax, t, s->stream);
+    if (s->solves < (kind == PD_PAIRS_DELTA ? 2 : 1))
+        return fail(s, PD_ERR_STATE, "not enough solves since create or load for these pairs");
+    const bool delta = kind == PD_PAIRS_DELTA;
+    warm_inputs(s->field, s->whist, delta, s->runs_dev, s->rmax, x, s->stream);
+    warm_targets(s->field, s->phi, s->whist, delta, s->runs_dev, s->rmax, t, s->stream);
     CK(cudaGetLastError());
     return PD_OK;
 }
 
 pd_status pd_set_warm_start(pd_sim* s, int mode, pd_net* net) {
     if (!s) return PD_ERR_ARG;
-    if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED)
+    if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED && mode != PD_WARM_LEARNED_DELTA)
         return fail(s, PD_ERR_ARG, "bad warm-start mode");
     if (mode != PD_WARM_PREVIOUS && s->cfgs[0].field_mode != PD_FIELD_POISSON)
         return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
-    if (mode == PD_WARM_LEARNED) {
+    const bool learned = mode == PD_WARM_LEARNED || mode == PD_WARM_LEARNED_DELTA;
+    if (learned) {
         if (!net) return fail(s, PD_ERR_ARG, "learned warm start needs a network");
         if (net_max_nodes(net) < (int64_t)total_nodes(s))
             return fail(s, PD_ERR_ARG, "network holds fewer nodes than the simulation");
@@ -1358,7 +1377,7 @@ pd_status pd_set_warm_start(pd_sim* s, int mode, pd_net* net) {
     }
     drop_graph(s);
     s->warm_mode = mode;
-    s->warm_net = mode == PD_WARM_LEARNED ? net : nullptr;
+    s->warm_net = learned ? net : nullptr;
     return PD_OK;
 }
 
@@ -1449,6 +1468,7 @@ pd_status pd_load(pd_sim* s, const char* path) {
     r = upload_ck(s);
     if (r != PD_OK) return r;
     s->step = h.step;
+    s->solves = 0;            // the warm-start history is not part of the checkpoint
     s->sorted_valid = h.sorted_valid != 0;
     s->primed = h.primed != 0;
     CK(cudaStreamSynchronize(s->stream));

@@ -593,6 +593,7 @@ void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float
 // ------------------------------------------------------------------
 // warm start
 // ------------------------------------------------------------------
+// node density of the current fixed-point charge (C/m^3)
 __device__ __forceinline__ double node_rho(const long long* rho_e, const long long* rho_h, const double* verb_base,
                                            int fo, const RunInfo& RI, int i, int j, uint32_t g) {
     const double qw = QE_ * RI.weight / 4294967296.0;
@@ -601,81 +602,118 @@ __device__ __forceinline__ double node_rho(const long long* rho_e, const long lo
     return qw * (double)(rho_e[g] + rho_h[g]) / vol;
 }
 
-__global__ void k_warm_rmax(const long long* rho_e, const long long* rho_h, const double* verb_base,
-                            const int* fvb_off, const RunInfo* runs, unsigned long long* rmax_bits) {
+// history shift at the start of a solve: rho_prev := rho_last, phi_prev :=
+// phi, V_prev := V_last; then rho_last := current density, V_last := V
+__global__ void k_warm_history(const long long* rho_e, const long long* rho_h, const double* verb_base,
+                               const int* fvb_off, const RunInfo* runs, const RunState* rs, const double* phi,
+                               WarmHistory h) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const int W = RI.nr + 1, n = (RI.nz + 1) * W;
-    double m = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W, j = k - i * W;
-        m = fmax(m, fabs(node_rho(rho_e, rho_h, verb_base, fvb_off[run], RI, i, j, RI.node_base + (uint32_t)k)));
+        const uint32_t g = RI.node_base + (uint32_t)k;
+        h.rho_prev[g] = h.rho_last[g];
+        h.phi_prev[g] = phi[g];
+        h.rho_last[g] = node_rho(rho_e, rho_h, verb_base, fvb_off[run], RI, i, j, g);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h.V_prev[run] = h.V_last[run];
+        h.V_last[run] = rs[run].V;
+    }
+}
+
+// d = rho_last - ref (ref null: 0); rmax[run] = max |d|
+__global__ void k_warm_rmax(const double* rho_last, const double* ref, const RunInfo* runs,
+                            unsigned long long* rmax_bits) {
+    const int run = blockIdx.y;
+    const RunInfo& RI = runs[run];
+    const int n = (RI.nz + 1) * (RI.nr + 1);
+    double m = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t g = RI.node_base + (uint32_t)k;
+        m = fmax(m, fabs(rho_last[g] - (ref ? ref[g] : 0.0)));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
     // non-negative doubles order like their bit patterns
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&rmax_bits[run], (unsigned long long)__double_as_longlong(m));
 }
 
-__global__ void k_warm_x(const long long* rho_e, const long long* rho_h, const double* verb_base, const int* fvb_off,
-                         const RunInfo* runs, const double* rmax, float* x) {
+__global__ void k_warm_x(const double* rho_last, const double* ref, const RunInfo* runs, const double* rmax,
+                         float* x) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
-    const int W = RI.nr + 1, n = (RI.nz + 1) * W;
+    const int n = (RI.nz + 1) * (RI.nr + 1);
     const double rm = rmax[run];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int i = k / W, j = k - i * W;
         const uint32_t g = RI.node_base + (uint32_t)k;
-        x[g] = rm > 0.0 ? (float)(node_rho(rho_e, rho_h, verb_base, fvb_off[run], RI, i, j, g) / rm) : 0.0f;
+        x[g] = rm > 0.0 ? (float)((rho_last[g] - (ref ? ref[g] : 0.0)) / rm) : 0.0f;
     }
+}
+
+// the potential the prediction is added to: V z / L, or with a reference
+// phi_ref + (V - V_ref) z / L
+__device__ __forceinline__ double warm_base(const double* phi_ref, double V, double V_ref, uint32_t g, int i,
+                                            int nz) {
+    return phi_ref ? phi_ref[g] + (V - V_ref) * (double)i / (double)nz : V * (double)i / (double)nz;
 }
 
 __global__ void k_warm_apply(const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
-                             const double* dzr, double* phi) {
+                             const double* dzr, const double* phi_ref, const double* V_ref, double* phi) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const int W = RI.nr + 1, n = (RI.nz - 1) * W;
-    const double V = rs[run].V, L = RI.nz * dzr[2 * run];
-    const double s = y ? rmax[run] * L * L / EPS0_ : 0.0;
+    const double V = rs[run].V, Vr = V_ref ? V_ref[run] : 0.0, dz = dzr[2 * run];
+    const double sc = y ? rmax[run] * dz * dz / EPS0_ : 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const int i = 1 + q / W;
         const uint32_t g = RI.node_base + (uint32_t)(W + q);
-        const double lap = V * (double)i / (double)RI.nz;
-        phi[g] = y ? lap + (double)y[g] * s : lap;
+        const double base = warm_base(phi_ref, V, Vr, g, i, RI.nz);
+        phi[g] = y ? base + (double)y[g] * sc : base;
     }
 }
 
-__global__ void k_warm_targets(const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
-                               const double* dzr, float* t) {
+__global__ void k_warm_targets(const double* phi, const RunInfo* runs, const double* V_last, const double* rmax,
+                               const double* dzr, const double* phi_ref, const double* V_ref, float* t) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const int W = RI.nr + 1, n = (RI.nz + 1) * W;
-    const double V = rs[run].V, L = RI.nz * dzr[2 * run], rm = rmax[run];
-    const double s = rm > 0.0 ? EPS0_ / (rm * L * L) : 0.0;
+    const double V = V_last[run], Vr = V_ref ? V_ref[run] : 0.0, dz = dzr[2 * run], rm = rmax[run];
+    const double sc = rm > 0.0 ? EPS0_ / (rm * dz * dz) : 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W;
         const uint32_t g = RI.node_base + (uint32_t)k;
-        t[g] = (float)((phi[g] - V * (double)i / (double)RI.nz) * s);
+        t[g] = (float)((phi[g] - warm_base(phi_ref, V, Vr, g, i, RI.nz)) * sc);
     }
 }
 
-void warm_inputs(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
-                 double* rmax, float* x, cudaStream_t s) {
+void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
+                  const RunState* rs, const double* phi, const WarmHistory& h, cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    k_warm_history<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.verb_base, fs.fvb_off, runs, rs, phi, h);
+}
+
+void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,
+                 cudaStream_t s) {
+    const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
+    const double* ref = delta ? h.rho_prev : nullptr;
     cudaMemsetAsync(rmax, 0, (size_t)fs.nruns * 8, s);
-    k_warm_rmax<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.verb_base, fs.fvb_off, runs, (unsigned long long*)rmax);
-    k_warm_x<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.verb_base, fs.fvb_off, runs, rmax, x);
+    k_warm_rmax<<<g, fs.threads, 0, s>>>(h.rho_last, ref, runs, (unsigned long long*)rmax);
+    k_warm_x<<<g, fs.threads, 0, s>>>(h.rho_last, ref, runs, rmax, x);
 }
 
-void warm_apply(FieldSolver& fs, const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
-                double* phi, cudaStream_t s) {
+void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, bool delta, const RunInfo* runs,
+                const RunState* rs, const double* rmax, double* phi, cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    k_warm_apply<<<g, fs.threads, 0, s>>>(y, runs, rs, rmax, fs.dzr, phi);
+    k_warm_apply<<<g, fs.threads, 0, s>>>(y, runs, rs, rmax, fs.dzr, delta ? h.phi_prev : nullptr,
+                                          delta ? h.V_prev : nullptr, phi);
 }
 
-void warm_targets(FieldSolver& fs, const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
-                  float* t, cudaStream_t s) {
+void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, bool delta, const RunInfo* runs,
+                  const double* rmax, float* t, cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    k_warm_targets<<<g, fs.threads, 0, s>>>(phi, runs, rs, rmax, fs.dzr, t);
+    k_warm_targets<<<g, fs.threads, 0, s>>>(phi, runs, h.V_last, rmax, fs.dzr, delta ? h.phi_prev : nullptr,
+                                            delta ? h.V_prev : nullptr, t);
 }
 
 }  // namespace pd

@@ -63,16 +63,29 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
 void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float2* E, DevState* st, RunState* rs,
                   cudaStream_t s);
 
-// Warm start of the solve (see pd_set_warm_start): rmax[run] = max |rho| of
-// the run's nodes (C/m^3, Verboncoeur volumes, halved on the electrode rows)
-// and x = rho / rmax at the run's nodes
-void warm_inputs(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
-                 double* rmax, float* x, cudaStream_t s);
-// interior rows of phi := V z / L + y rmax L^2 / eps0 (y = null: V z / L)
-void warm_apply(FieldSolver& fs, const float* y, const RunInfo* runs, const RunState* rs, const double* rmax,
-                double* phi, cudaStream_t s);
-// training targets t = (phi - V z / L) eps0 / (rmax L^2) at every node
-void warm_targets(FieldSolver& fs, const double* phi, const RunInfo* runs, const RunState* rs, const double* rmax,
-                  float* t, cudaStream_t s);
+// Warm start of the solve (see pd_set_warm_start).  History kept across
+// solves, per node (C/m^3 and V) and per run (V):
+struct WarmHistory {
+    double* rho_last;   // density of the most recent solve
+    double* rho_prev;   // density of the solve before it
+    double* phi_prev;   // potential of the solve before the most recent one
+    double* V_last;     // [runs] anode voltage of the most recent solve
+    double* V_prev;     // [runs] of the one before
+};
+// at the start of every solve: shift the history and record the current
+// density (Verboncoeur volumes, halved on the electrode rows) and voltage
+void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
+                  const RunState* rs, const double* phi, const WarmHistory& h, cudaStream_t s);
+// d = rho_last (- rho_prev when delta); rmax[run] = max |d|; x = d / rmax
+void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,
+                 cudaStream_t s);
+// interior rows of phi := base + y rmax dz^2 / eps0, base = V z / L or, with
+// delta, phi_prev + (V - V_prev) z / L (y = null: the base alone)
+void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, bool delta, const RunInfo* runs,
+                const RunState* rs, const double* rmax, double* phi, cudaStream_t s);
+// training targets t = (phi - base) eps0 / (rmax dz^2) at every node, with
+// the voltages of the history (call after a solve)
+void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, bool delta, const RunInfo* runs,
+                  const double* rmax, float* t, cudaStream_t s);
 
 }  // namespace pd

@@ -146,15 +146,48 @@ def test_training_pairs_match_the_oracle(pd, torch, xs):
     assert np.abs(to).max() > 0
 
 
+def test_delta_pairs_match_the_oracle(pd, torch, xs):
+    """Pairs of two consecutive solves (load + solve, one step + solve).  One
+    step moves the particles identically on both sides (the two potentials
+    differ by far less than a float rounding of the push), so the charge is
+    bit-identical and the potentials agree to the solve tolerance."""
+    cfg, parts = _plume()
+    cfg.update(poisson_tol=1e-12, oracle_poisson_tol=1e-13)
+    # a quarter of the load in the row at the anode: the charge it absorbs in
+    # the step drives the circuit, so the anode voltage of the two solves differs
+    parts = {k: v.copy() for k, v in parts.items()}
+    parts["iz"][::4] = cfg["nz"] - 1
+    sim = pd.Simulation(cfg, xs)
+    sim.load(parts)
+    sim.step(0)
+    with pytest.raises(pd.PdError):
+        sim.warmstart_pairs("delta")          # one solve only
+    sim.step(1)
+    x, t = (a.cpu().numpy().astype(np.float64).reshape(sim.nzn, sim.nrn) for a in sim.warmstart_pairs("delta"))
+    o = oracle.Oracle(cfg, fp64=False)
+    o.set_cross_sections(xs)
+    o.load(parts)
+    o.prime()
+    grid = (cfg["weight"], cfg["dz"], cfg["dr"], cfg["nz"], cfg["nr"])
+    rho1, phi1, V1 = cnn.node_density(sum(o.rho()), *grid), o.phi().reshape(sim.nzn, sim.nrn), cfg["V0"]
+    o.step(1)
+    rho2, phi2, V2 = cnn.node_density(sum(o.rho()), *grid), o.phi().reshape(sim.nzn, sim.nrn), o.scalars()["V"]
+    assert V2 != V1
+    xo, to = cnn.training_pair(rho2, phi2, V2, cfg["dz"], rho_prev=rho1, phi_prev=phi1, V_prev=V1)
+    assert np.abs(xo).max() == pytest.approx(1.0)
+    assert np.abs(x - xo).max() <= 1e-6
+    assert np.abs(t - to).max() <= 1e-3 * np.abs(to).max()
+
+
 def test_warm_start_modes_reach_the_tolerance(pd, torch, xs):
     cfg, parts = _plume(n=64, total=6e4)
     net = pd.Net((cfg["nz"] + 1) * (cfg["nr"] + 1), params=_params(10))
     cycles = {}
-    for mode in ("previous", "cold", "learned"):
+    for mode in ("previous", "cold", "learned", "learned_delta"):
         sim = pd.Simulation(cfg, xs)
         sim.load(parts)
         sim.step(2)
-        sim.set_warm_start(mode, net if mode == "learned" else None)
+        sim.set_warm_start(mode, net if mode.startswith("learned") else None)
         sim.step(1)
         sc = sim.scalars()
         assert sc["poisson_relres"] <= cfg["poisson_tol"], mode

@@ -116,38 +116,60 @@ def test_bf16_mirror_is_close_to_exact():
     assert np.linalg.norm(gb - g) <= 0.05 * np.linalg.norm(g)
 
 
+def _solved(cfg, xs, parts=None, V=None):
+    c = dict(cfg)
+    if V is not None:
+        c["V0"] = V
+    o = oracle.Oracle(c, fp64=True)
+    o.set_cross_sections(xs)
+    if parts is not None:
+        o.load(parts)
+    o.prime()
+    n = c["nz"] + 1
+    rho = cnn.node_density(sum(o.rho()).astype(np.float64), c["weight"], c["dz"], c["dr"], c["nz"], c["nr"])
+    return rho, o.phi().reshape(n, -1)
+
+
 def test_training_pairs_follow_eq8_linearity(xs):
     """Through the oracle's Poisson solve: a charge-free gap gives t = 0, the
-    target is invariant to scaling the charge, and the warm start built from
-    the exact target reproduces the potential."""
+    target is invariant to scaling the charge, the warm start built from the
+    exact target reproduces the potential, and the delta pair of two states
+    equals the absolute pair of their charge difference."""
     cfg, parts = synthetic.rz_plume(n=16, total=6e3, seed=9)
-    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-12, oracle_poisson_tol=1e-13)
-    o = oracle.Oracle(cfg, fp64=True)
-    o.set_cross_sections(xs)
-    o.load(parts)
-    o.prime()
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-13, oracle_poisson_tol=1e-13)
     n = cfg["nz"] + 1
-    rho_int = sum(o.rho()).astype(np.float64)
-    phi = o.phi().reshape(n, -1)
-    dz = cfg["dz"]
-    rho = cnn.node_density(rho_int, cfg["weight"], dz, cfg["dr"], cfg["nz"], cfg["nr"])
+    dz, V = cfg["dz"], cfg["V0"]
+    rho, phi = _solved(cfg, xs, parts)
     # the volumes sum to the cylinder: a uniform density is returned as given
     vol = 1.602176634e-19 * cfg["weight"] / 2.0 ** 32 / cnn.node_density(np.ones(rho.size), cfg["weight"], dz,
                                                                        cfg["dr"], cfg["nz"], cfg["nr"])
     assert vol.sum() == pytest.approx(np.pi * (cfg["nr"] * cfg["dr"]) ** 2 * cfg["nz"] * dz, rel=1e-12)
-    x, t = cnn.training_pair(rho, phi, cfg["V0"], dz)
+    x, t = cnn.training_pair(rho, phi, V, dz)
     assert np.abs(x).max() == pytest.approx(1.0)
     assert np.abs(t).max() > 0
-    x2, t2 = cnn.training_pair(3.0 * rho, cfg["V0"] * np.arange(n)[:, None] / (n - 1) + 3.0 * (
-        phi - cfg["V0"] * np.arange(n)[:, None] / (n - 1)), cfg["V0"], dz)
+    zV = V * np.arange(n)[:, None] / (n - 1)
+    x2, t2 = cnn.training_pair(3.0 * rho, zV + 3.0 * (phi - zV), V, dz)
     assert np.allclose(x2, x) and np.allclose(t2, t, rtol=1e-12, atol=1e-15)
-    phi0 = cnn.warm_start(t, np.abs(rho).max(), cfg["V0"], dz)
-    assert np.allclose(phi0, phi, rtol=1e-12, atol=1e-9 * cfg["V0"])
-    _, tz = cnn.training_pair(np.zeros_like(rho), phi, cfg["V0"], dz)
+    phi0 = cnn.warm_start(t, np.abs(rho).max(), V, dz)
+    assert np.allclose(phi0, phi, rtol=1e-12, atol=1e-9 * V)
+    _, tz = cnn.training_pair(np.zeros_like(rho), phi, V, dz)
     assert not tz.any()
-    o0 = oracle.Oracle(dict(cfg), fp64=True)
-    o0.set_cross_sections(xs)
-    o0.prime()
-    phiL = o0.phi().reshape(n, -1)
-    _, tl = cnn.training_pair(rho, phiL, cfg["V0"], dz)
+    rho0, phiL = _solved(cfg, xs)
+    assert not rho0.any()
+    _, tl = cnn.training_pair(rho, phiL, V, dz)
     assert np.abs(tl).max() <= 1e-9 * np.abs(t).max()
+    # a second state: half of the particles, another voltage
+    half = {k: v[::2] for k, v in parts.items()}
+    rho_b, phi_b = _solved(cfg, xs, half, V=1.7e3)
+    xd, td = cnn.training_pair(rho, phi, V, dz, rho_prev=rho_b, phi_prev=phi_b, V_prev=1.7e3)
+    # the charge difference is the other half of the particles (integer
+    # deposits add exactly); solved alone with the anode grounded it gives,
+    # by the linearity of Eq. (8), the same pair
+    odd = {k: v[1::2] for k, v in parts.items()}
+    rho_o, phi_o = _solved(cfg, xs, odd, V=0.0)
+    m = np.abs(rho - rho_b).max()
+    assert np.allclose(rho - rho_b, rho_o, rtol=1e-12, atol=1e-12 * m)
+    xa, ta = cnn.training_pair(rho_o, phi_o, 0.0, dz)
+    assert np.allclose(xd, xa, rtol=1e-10, atol=1e-12)
+    assert np.allclose(td, ta, rtol=1e-7, atol=1e-7 * np.abs(ta).max())
+    assert np.allclose(cnn.warm_start(td, m, V, dz, phi_prev=phi_b, V_prev=1.7e3), phi, rtol=1e-12, atol=1e-9 * V)
