@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=10)
     p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble", "warmstart"])
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="ensemble: skip the one-simulation-per-run arm")
     p.add_argument("--ws-sizes", default="256,512", help="grid sizes of the warm-start runs")
     p.add_argument("--ws-runs", type=int, default=10, help="runs per grid size (the last one is held out)")
     p.add_argument("--ws-pairs", type=int, default=500, help="pairs per run, one every 2 steps")
@@ -287,25 +288,27 @@ def run_ensemble(args, ws, rank, local):
         return e0.elapsed_time(e1), (t1 - t0) * 1e3
 
     # ---- plain method: one simulation per run, run after run --------------
-    sims = []
-    for cfg, parts in runs:
-        sm = pd.Simulation(cfg, xs, device=dev)
-        sm.load_device({k: torch.from_numpy(parts[k]).to(dev) for k in keys})
-        sims.append(sm)
-    for sm in sims:
-        sm.step(W)
-    torch.cuda.synchronize()
-    c0 = counts(lambda r: sims[r].scalars())
-    plain_ms, plain_wall = timed(sims[0].stream, lambda: [sm.step(K) for sm in sims])
-    plain_sc = [sm.scalars() for sm in sims]
-    c1 = counts(lambda r: plain_sc[r])
-    plain_upd = ensemble_updates(c0, c1, K, hs)
-    plain_relres = max(sc["poisson_relres_max"] for sc in plain_sc)
-    plain_launches = 0
-    for sm in sims:
-        sm.close()
-    del sims
-    torch.cuda.empty_cache()
+    plain_ms = plain_wall = plain_upd = None
+    plain_relres = None
+    sims = [] if not args.no_plain else None
+    if sims is not None:
+        for cfg, parts in runs:
+            sm = pd.Simulation(cfg, xs, device=dev)
+            sm.load_device({k: torch.from_numpy(parts[k]).to(dev) for k in keys})
+            sims.append(sm)
+        for sm in sims:
+            sm.step(W)
+        torch.cuda.synchronize()
+        c0 = counts(lambda r: sims[r].scalars())
+        plain_ms, plain_wall = timed(sims[0].stream, lambda: [sm.step(K) for sm in sims])
+        plain_sc = [sm.scalars() for sm in sims]
+        c1 = counts(lambda r: plain_sc[r])
+        plain_upd = ensemble_updates(c0, c1, K, hs)
+        plain_relres = max(sc["poisson_relres_max"] for sc in plain_sc)
+        for sm in sims:
+            sm.close()
+        del sims
+        torch.cuda.empty_cache()
 
     # ---- batched ensemble ---------------------------------------------------
     ens = pd.Ensemble(cfgs, xs, device=dev)
@@ -374,7 +377,7 @@ def run_ensemble(args, ws, rank, local):
         torch.cuda.empty_cache()
 
     ens_ms_max = max_over_ranks(ws, ens_ms, dev)
-    plain_ms_max = max_over_ranks(ws, plain_ms, dev)
+    plain_ms_max = max_over_ranks(ws, plain_ms, dev) if plain_ms is not None else None
     upd_all = sum_over_ranks(ws, ens_upd, dev)
     if rank == 0:
         grids = {}
@@ -394,11 +397,12 @@ def run_ensemble(args, ws, rank, local):
                             "poisson_cycles_fixed": cycles, "poisson_relres_max": relres,
                             "particle_updates_per_s": upd_all / (ens_ms_max * 1e-3), "tuning": tuning,
                             "eager_kernels_ms_per_step": {k: v[0] / G for k, v in prof.items() if v[1]}},
-                "plain": {"ms_per_step": plain_ms_max / K, "wall_ms_per_step": plain_wall / K,
-                          "poisson_relres_max": plain_relres,
-                          "particle_updates_per_s": sum_over_ranks(ws, plain_upd, dev) / (plain_ms_max * 1e-3),
-                          "method": "one simulation per run, stepped run after run, host-checked multigrid"},
-                "equal_residual": bool(relres <= tol and plain_relres <= tol),
+                "plain": None if plain_ms is None else {
+                    "ms_per_step": plain_ms_max / K, "wall_ms_per_step": plain_wall / K,
+                    "poisson_relres_max": plain_relres,
+                    "particle_updates_per_s": sum_over_ranks(ws, plain_upd, dev) / (plain_ms_max * 1e-3),
+                    "method": "one simulation per run, stepped run after run, host-checked multigrid"},
+                "equal_residual": bool(relres <= tol and (plain_relres is None or plain_relres <= tol)),
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
@@ -535,10 +539,12 @@ def main():
     sim.load_device(dtens)
     del dtens
     torch.cuda.synchronize()
+    tuning = None if args.no_autotune else sim.autotune(2)   # its trial steps are untimed warm-up
     sim.step(args.warmup)
     sim.synchronize()
     pd.pd_profile_read(sim.h)              # discard warm-up launch records
     pd.pd_profile_enable(sim.h, 1)
+    counters0 = sim.counters()
     n0 = sim.scalars()["n_particles"]
     stream = sim.stream
     e0 = torch.cuda.Event(enable_timing=True)
@@ -579,7 +585,8 @@ def main():
                 "launch_ms": per_launch_ms,
                 "share": prof[dom][0] / total_kernel_ms if total_kernel_ms > 0 else None,
                 "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}
-    counters = sim.counters()
+    counters1 = sim.counters()
+    counters = {k: counters1[k] - counters0[k] for k in counters1}   # events of the timed steps
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -588,6 +595,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         sim2 = pd.Simulation(cfg, xs, device=dev)
+        if tuning:
+            sim2.set_tuning(**tuning)
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -616,6 +625,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_desc(args.nz, args.nr, args.total), "nz": args.nz, "nr": args.nr,
                            "particles_per_gpu": int(n0), "parallelism": f"replicas x{ws}" if ws > 1 else "single",
+                           "tuning": tuning,
                            "l2": "inputs larger than L2 (28 B x particles resident in HBM); no flush"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,

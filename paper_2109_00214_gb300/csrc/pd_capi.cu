@@ -235,13 +235,14 @@ cudaEvent_t take_event(pd_sim* s) {
     return e;
 }
 
-// launch accounting and (when profiling, outside graph capture) CUDA events
+// launch accounting (`kernels` of the library's kernels the region launches)
+// and, when profiling outside graph capture, CUDA events around the region
 struct Timed {
     pd_sim* s;
     int k;
     cudaEvent_t b;
-    Timed(pd_sim* s_, int k_, bool capturing = false) : s(s_), k(k_), b(nullptr) {
-        s->launches[k] += 1;
+    Timed(pd_sim* s_, int k_, bool capturing, int kernels) : s(s_), k(k_), b(nullptr) {
+        s->launches[k] += (uint64_t)kernels;
         if (s->prof && !capturing) {
             cudaEvent_t a = take_event(s);
             b = take_event(s);
@@ -468,11 +469,13 @@ size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
 
 // before each Poisson solve: the solve history, then the starting point
 // (PD_WARM_PREVIOUS: phi as it is)
-pd_status warm_start(pd_sim* s) {
+pd_status warm_start(pd_sim* s, int* kernels) {
     warm_history(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rs, s->phi, s->whist, s->stream);
+    *kernels += 1;
     const bool delta = s->warm_mode == PD_WARM_LEARNED_DELTA;
     if (s->warm_mode == PD_WARM_COLD) {
         warm_apply(s->field, nullptr, s->whist, false, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+        *kernels += 1;
     } else if (s->warm_mode == PD_WARM_LEARNED || (delta && s->solves >= 1)) {
         warm_inputs(s->field, s->whist, delta, s->runs_dev, s->rmax, s->wsx, s->stream);
         for (const auto& g : s->groups)
@@ -480,6 +483,7 @@ pd_status warm_start(pd_sim* s) {
                                (int64_t)total_nodes(s), s->stream))
                 return PD_ERR_CUDA;
         warm_apply(s->field, s->wsy, s->whist, delta, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+        *kernels += 3 + 6 * (int)s->groups.size();   // rmax, x, apply; six layers per group
     }
     s->solves += 1;
     return cudaGetLastError() == cudaSuccess ? PD_OK : PD_ERR_CUDA;
@@ -490,14 +494,16 @@ pd_status prime(pd_sim* s) {
     CK(cudaMemsetAsync(s->rho_e, 0, total_nodes(s) * 8, s->stream));
     CK(cudaMemsetAsync(s->rho_h, 0, total_nodes(s) * 8, s->stream));
     {
-        Timed t(s, K_OTHER);
+        Timed t(s, K_OTHER, false, 1);
         launch_deposit(s->A, s->rho_e, s->rho_h, s->st, P, grid_for(s, 8), s->stream);
     }
     if (s->cfgs[0].field_mode == PD_FIELD_POISSON) {
-        Timed t(s, K_POISSON);
-        if (warm_start(s) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
-        if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream))
+        Timed t(s, K_POISSON, false, 2);   // + the warm start's and the solve's kernels, counted below
+        int nk = 0;
+        if (warm_start(s, &nk) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
+        if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream, &nk))
             return fail(s, PD_ERR_CUDA, "field solve failed");
+        s->launches[K_POISSON] += (uint64_t)nk;
         field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
     }
     CK(cudaGetLastError());
@@ -514,30 +520,30 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     const int gpart = grid_for(s, s->tune.push_blocks_per_sm);
     const size_t nodes = total_nodes(s);
     if (s->any_inject) {
-        Timed t(s, K_INJECT, capturing);
+        Timed t(s, K_INJECT, capturing, 1);
         launch_inject(s->A, s->E, s->st, P, s->ic_dev, s->ray, s->stream);
     }
     {
-        Timed t(s, K_MEMSET, capturing);
+        Timed t(s, K_MEMSET, capturing, 0);   // memsets, no kernels
         cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
         if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
         // mover bits are OR-ed in by the push: start from zero
         cudaMemsetAsync(s->mv, 0, (size_t)s->L.words_pad * 4, s->stream);
     }
     {
-        Timed t(s, K_PUSH, capturing);
+        Timed t(s, K_PUSH, capturing, 1);
         launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, gpart,
                     s->stream);
     }
     {
-        Timed t(s, K_SCAN_BINS, capturing);
+        Timed t(s, K_SCAN_BINS, capturing, P.use_prev ? 7 : 4);
         launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
                         grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
         launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
         if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
     }
     {
-        Timed t(s, K_SCATTER, capturing);
+        Timed t(s, K_SCATTER, capturing, 1);
         launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P,
                        grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
     }
@@ -545,34 +551,36 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     std::swap(s->off, s->off2);
     s->sorted_valid = true;
     {
-        Timed t(s, K_NCAND, capturing);
+        Timed t(s, K_NCAND, capturing, 1);
         launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, s->tune.ncand_blocks_per_sm),
                      s->stream);
     }
     {
-        Timed t(s, K_SCAN_CAND, capturing);
+        Timed t(s, K_SCAN_CAND, capturing, 3);
         launch_scan(s->cand, s->cand_off, s->partial, s->L.ncell_pad, s->stream);
     }
     {
-        Timed t(s, K_COLLIDE, capturing);
+        Timed t(s, K_COLLIDE, capturing, 1);
         launch_collide(s->A, s->B, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P,
                        s->cc, nbins, grid_for(s, s->tune.collide_blocks_per_sm), s->stream);
     }
     {
-        Timed t(s, K_FINALIZE, capturing);
+        Timed t(s, K_FINALIZE, capturing, 1);
         launch_finalize(s->off, nbins, s->cand_off, s->st, P, s->circ_dev, c.dt, c.geometry == PD_GEOM_RZ, s->stream);
     }
     if (c.field_mode == PD_FIELD_POISSON) {
         {
-            Timed t(s, K_POISSON, capturing);
-            if (warm_start(s) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
+            Timed t(s, K_POISSON, capturing, 0);
+            int nk = 0;
+            if (warm_start(s, &nk) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
             const bool host_check = !capturing && !s->graph_on;
             if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, host_check ? 1 : 0,
-                            s->graph_cycles, s->stream))
+                            s->graph_cycles, s->stream, &nk))
                 return fail(s, PD_ERR_CUDA, "field solve failed");
+            s->launches[K_POISSON] += (uint64_t)nk;
         }
         {
-            Timed t(s, K_EFIELD, capturing);
+            Timed t(s, K_EFIELD, capturing, 2);
             field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
         }
     }
@@ -1553,9 +1561,9 @@ pd_status pd_autotune(pd_sim* s, int steps_per_trial, pd_tuning* out) {
     };
     pd_tuning t = s->tune;
     std::vector<Knob> knobs = {
-        {&t.push_blocks_per_sm, K_PUSH, {2, 4, 6, 8, 12, 16, 24, 32}},
+        {&t.push_blocks_per_sm, K_PUSH, {2, 3, 4, 6, 8, 12, 16, 24}},
         {&t.bincount_blocks_per_sm, K_SCAN_BINS, {2, 4, 8, 16}},
-        {&t.scatter_blocks_per_sm, K_SCATTER, {2, 4, 6, 8, 12, 16}},
+        {&t.scatter_blocks_per_sm, K_SCATTER, {2, 3, 4, 6, 8, 12, 16}},
         {&t.ncand_blocks_per_sm, K_NCAND, {2, 4, 8, 16}},
         {&t.collide_blocks_per_sm, K_COLLIDE, {4, 8, 16, 32}},
     };

@@ -135,10 +135,11 @@ __device__ void deposit1(long long* rho, const RunInfo& RI, int geom, uint32_t l
               (unsigned long long)(zq * (long long)wz * (long long)wr));
 }
 
-// k-th smallest id of ids[0..N) and its position; the whole warp takes part
-__device__ uint32_t select_rank(const uint32_t* __restrict__ ids, uint32_t N, uint32_t rank, int lane) {
+// k-th smallest id of ids[0..N) and its position; the whole warp takes part.
+// Bits above `top` are zero in every id.
+__device__ uint32_t select_rank(const uint32_t* __restrict__ ids, uint32_t N, uint32_t rank, int lane, int top) {
     uint32_t prefix = 0, want = rank;
-    for (int bit = 31; bit >= 0; --bit) {
+    for (int bit = top; bit >= 0; --bit) {
         const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
         uint32_t cnt = 0;
         for (uint32_t q = lane; q < N; q += 32) {
@@ -166,7 +167,9 @@ struct IdList {
     const uint32_t* base;
     const uint32_t* table;           // rank -> position of a long list, or null
     uint32_t n;
+    int top;                         // highest set bit of any id (0 if none)
     bool cached;
+    bool sorted;                     // ids ascend with the position: rank = position
 };
 
 // Scratch for the rank tables of long lists: four u32 arrays indexed by slot.
@@ -176,64 +179,78 @@ struct RankScratch {
     uint32_t *ka, *va, *kb, *vb;
 };
 
+// 8-bit digit passes that sort ids whose highest set bit is `top`
+__device__ __forceinline__ int table_passes(int top) { return top / 8 + 1; }
+
 // Rank table of ids[0..n) (unique): position of the r-th smallest id at
-// table[r].  Stable LSD radix sort of (id, position) pairs by 4-bit digits,
-// one warp, digit ranks from ballots; only the digits below the highest set
-// bit of any id are sorted.  Returns the buffer that holds the table.
-__device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t n, uint32_t* ka, uint32_t* va,
-                                      uint32_t* kb, uint32_t* vb, int lane) {
-    uint32_t orv = 0;
+// table[r].  Stable LSD radix sort of (id, position) pairs by 8-bit digits
+// by one warp: per 32 ids, __match_any_sync groups equal digits, a group's
+// members take consecutive places after the digit's running offset (kept in
+// the warp's 256 shared-memory counters `cnt`) in lane order, and the
+// group's highest lane advances the offset.  Only the digits up to bit `top`
+// (the highest set bit of any id) are sorted.  Returns the buffer holding
+// the table.
+__device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t n, int top, uint32_t* ka,
+                                      uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* cnt, int lane) {
     for (uint32_t q = lane; q < n; q += 32) {
-        const uint32_t x = ids[q];
-        ka[q] = x;
+        ka[q] = ids[q];
         va[q] = q;
-        orv |= x;
     }
-    orv = __reduce_or_sync(FULL, orv);
-    const int passes = (32 - __clz((int)orv) + 3) / 4;
+    const int passes = table_passes(top);
     uint32_t *sk = ka, *sv = va, *dk = kb, *dv = vb;
     unsigned lt;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    __syncwarp();
     for (int p = 0; p < passes; ++p) {
-        const int sh = 4 * p;
-        // lane v < 16 counts digit v
-        uint32_t cnt = 0;
+        const int sh = 8 * p;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
+        __syncwarp();
+        // counts per digit
         for (uint32_t q0 = 0; q0 < n; q0 += 32) {
             const uint32_t q = q0 + lane;
-            const uint32_t d = q < n ? (sk[q] >> sh) & 15u : 16u;
-#pragma unroll
-            for (uint32_t v = 0; v < 16; ++v) {
-                const unsigned m = __ballot_sync(FULL, d == v);
-                if ((uint32_t)lane == v) cnt += (uint32_t)__popc(m);
-            }
+            const uint32_t d = q < n ? (sk[q] >> sh) & 255u : 256u;
+            const unsigned peers = __match_any_sync(FULL, d);
+            if (q < n && lane == 31 - __clz((int)peers)) cnt[d] += (uint32_t)__popc(peers);
+            __syncwarp();
         }
-        uint32_t x = cnt;
+        // exclusive scan of the 256 counts (8 per lane)
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = cnt[lane * 8 + k];
+            sum += c[k];
+        }
+        uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(FULL, x, o);
             if (lane >= o) x += y;
         }
-        uint32_t base = x - cnt;          // lane v: first destination of digit v
+        uint32_t run = x - sum;
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            cnt[lane * 8 + k] = run;
+            run += c[k];
+        }
+        __syncwarp();
+        // stable scatter
         for (uint32_t q0 = 0; q0 < n; q0 += 32) {
             const uint32_t q = q0 + lane;
             const bool in = q < n;
             const uint32_t key = in ? sk[q] : 0u, val = in ? sv[q] : 0u;
-            const uint32_t d = in ? (key >> sh) & 15u : 16u;
-            uint32_t dst = 0;
-#pragma unroll
-            for (uint32_t v = 0; v < 16; ++v) {
-                const unsigned m = __ballot_sync(FULL, d == v);
-                const uint32_t b = __shfl_sync(FULL, base, (int)v);
-                if (d == v) dst = b + (uint32_t)__popc(m & lt);
-                if ((uint32_t)lane == v) base += (uint32_t)__popc(m);
-            }
+            const uint32_t d = in ? (key >> sh) & 255u : 256u;
+            const unsigned peers = __match_any_sync(FULL, d);
+            const uint32_t b = in ? cnt[d] : 0u;
+            __syncwarp();
             if (in) {
+                if (lane == 31 - __clz((int)peers)) cnt[d] = b + (uint32_t)__popc(peers);
+                const uint32_t dst = b + (uint32_t)__popc(peers & lt);
                 dk[dst] = key;
                 dv[dst] = val;
             }
+            __syncwarp();
         }
-        __syncwarp();
         uint32_t* t = sk;
         sk = dk;
         dk = t;
@@ -245,31 +262,55 @@ __device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t
 }
 
 // ids of one cell and species at slots [slot0, slot0 + n); `lookups` rank
-// selections will follow: long lists get a rank table when that pays
+// selections will follow.  A long list gets a rank table when that is
+// cheaper: a bitwise select sweeps the list once per significant bit, the
+// table sort twice per 8-bit digit at several times the cost per sweep.
 __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
-                                         uint32_t lookups, const RankScratch& S, int lane) {
+                                         uint32_t lookups, const RankScratch& S, uint32_t* cnt, int lane) {
     const uint32_t* base = ids + slot0;
     L.base = base;
     L.n = n;
     L.table = nullptr;
     L.cached = n <= 32u * RC;
+    uint32_t orv = 0;
+    bool asc = true;
     if (L.cached) {
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             const uint32_t q = (uint32_t)lane + 32u * k;
             L.ids[k] = q < n ? base[q] : 0u;
+            orv |= L.ids[k];
         }
-    } else if (lookups >= 2) {
-        L.table = rank_table(base, n, S.ka + slot0, S.va + slot0, S.kb + slot0, S.vb + slot0, lane);
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            // element q + 1 is lane + 1 of the same row, or lane 0 of the next
+            const uint32_t q = (uint32_t)lane + 32u * k;
+            const uint32_t right = __shfl_down_sync(FULL, L.ids[k], 1);
+            const uint32_t wrap = __shfl_sync(FULL, k + 1 < RC ? L.ids[k + 1 < RC ? k + 1 : k] : 0u, 0);
+            const uint32_t next = lane == 31 ? wrap : right;
+            if (q + 1 < n && !(L.ids[k] < next)) asc = false;
+        }
+    } else {
+        for (uint32_t q = lane; q < n; q += 32) {
+            const uint32_t x = base[q];
+            orv |= x;
+            if (q + 1 < n && !(x < base[q + 1])) asc = false;
+        }
     }
+    orv = __reduce_or_sync(FULL, orv);
+    L.sorted = __all_sync(FULL, asc);
+    L.top = orv ? 31 - __clz((int)orv) : 0;
+    if (!L.cached && !L.sorted && lookups * (uint32_t)(L.top + 1) > 10u * (uint32_t)table_passes(L.top))
+        L.table = rank_table(base, n, L.top, S.ka + slot0, S.va + slot0, S.kb + slot0, S.vb + slot0, cnt, lane);
 }
 
 // position of the rank-th smallest id of the list (same result as select_rank)
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
+    if (L.sorted) return rank;
     if (L.table) return L.table[rank];
-    if (!L.cached) return select_rank(L.base, L.n, rank, lane);
+    if (!L.cached) return select_rank(L.base, L.n, rank, lane, L.top);
     uint32_t prefix = 0, want = rank;
-    for (int bit = 31; bit >= 0; --bit) {
+    for (int bit = L.top; bit >= 0; --bit) {
         const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
         uint32_t cnt = 0;
 #pragma unroll
@@ -366,17 +407,16 @@ __device__ bool spawn_electron(Particles& A, CellCtx& cx, DevState* st, long lon
 }
 
 // lane-0 part of one candidate after the pair is chosen
+// (tkey, ve, vt: the target's key and both velocities as they are now)
 __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
-                                  float Racc, float Rch, const float* __restrict__ xsE, const float* __restrict__ xs,
+                                  uint32_t tkey, V3 ve, V3 vt, float Racc, float Rch,
+                                  const float* __restrict__ xsE, const float* __restrict__ xs,
                                   const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h) {
     const int ts = k == 0 ? SP_CU : SP_CUP;
-    const uint32_t tkey = A.key[it];
     if ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts) {   // target already ionized this step
         ++cx.consumed;
         return;
     }
-    V3 ve{A.vz[ie], A.vr[ie], A.vt[ie]};
-    V3 vt{A.vz[it], A.vr[it], A.vt[it]};
     const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
     const float g2 = (ux * ux + uy * uy) + uz * uz;
     const float g = sqrtf(g2);
@@ -456,8 +496,10 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, con
                                                  long long* rho_h, const float* __restrict__ xsE,
                                                  const float* __restrict__ xs, KParams P, CollConsts cc,
                                                  uint32_t nbins) {
+    __shared__ uint32_t s_cnt[4][256];         // per-warp digit counters of the rank-table sort
     const unsigned long long n_active = st->n_active;
     const int lane = threadIdx.x & 31;
+    uint32_t* cnt = s_cnt[(threadIdx.x >> 5) & 3];
     const unsigned long long warp0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     const uint32_t C = P.ncell;
@@ -490,7 +532,7 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, con
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
         IdList el;
-        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, lane);
+        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, cnt, lane);
         for (int k = 0; k < 2; ++k) {
             const uint32_t tb = (k == 0 ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
@@ -498,22 +540,84 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, con
             const uint32_t ncand = k == 0 ? n.x : n.y;
             if (ncand == 0) continue;
             IdList tl;
-            load_ids(tl, A.id, t_base, Nt, ncand, S, lane);
-            for (uint32_t m = 0; m < ncand; ++m) {
-                Stream rs(lc, st->step, sid_cand(k, m), RI->seed, RI->run);
-                const uint32_t i = rs.pick(Ne);
-                const uint32_t j = rs.pick(Nt);
-                const float Racc = rs.u01();
-                const float Rch = rs.u01();
-                const uint32_t pe = select_rank_list(el, i, lane);
-                const uint32_t pt = select_rank_list(tl, j, lane);
-                if (pe >= Ne || pt >= Nt) {       // ids not unique: corrupt state, never index with it
-                    if (lane == 0) set_error(st, ERR_BOUNDS);
-                    continue;
+            load_ids(tl, A.id, t_base, Nt, ncand, S, cnt, lane);
+            // candidates in batches of 32: lane q draws candidate m0 + q's pair and
+            // prefetches its particles; lane 0 then applies them in order,
+            // re-reading a candidate whose particles an earlier candidate of
+            // the batch may have changed
+            for (uint32_t m0 = 0; m0 < ncand; m0 += 32) {
+                const uint32_t nb = min(32u, ncand - m0);
+                const bool has = (uint32_t)lane < nb;
+                uint32_t i = 0, j = 0;
+                float Racc = 0.0f, Rch = 0.0f;
+                if (has) {
+                    Stream rs(lc, st->step, sid_cand(k, m0 + lane), RI->seed, RI->run);
+                    i = rs.pick(Ne);
+                    j = rs.pick(Nt);
+                    Racc = rs.u01();
+                    Rch = rs.u01();
                 }
-                if (lane == 0)
-                    process_candidate(A, cx, rs, k, e_base + pe, t_base + pt, Racc, Rch, xsE, xs, cc, st, rho_e,
-                                      rho_h);
+                uint32_t pe = 0, pt = 0;
+                if (el.sorted) {
+                    pe = i;
+                } else if (el.table) {
+                    if (has) pe = el.table[i];
+                } else {
+                    for (uint32_t q = 0; q < nb; ++q) {
+                        const uint32_t p = select_rank_list(el, __shfl_sync(FULL, i, (int)q), lane);
+                        if ((uint32_t)lane == q) pe = p;
+                    }
+                }
+                if (tl.sorted) {
+                    pt = j;
+                } else if (tl.table) {
+                    if (has) pt = tl.table[j];
+                } else {
+                    for (uint32_t q = 0; q < nb; ++q) {
+                        const uint32_t p = select_rank_list(tl, __shfl_sync(FULL, j, (int)q), lane);
+                        if ((uint32_t)lane == q) pt = p;
+                    }
+                }
+                const bool ok = has && pe < Ne && pt < Nt;   // ids not unique: corrupt state, never index with it
+                if (has && !ok) set_error(st, ERR_BOUNDS);
+                const uint32_t ie = e_base + (ok ? pe : 0u), it = t_base + (ok ? pt : 0u);
+                uint32_t tkey = 0;
+                V3 ve{0.0f, 0.0f, 0.0f}, vt{0.0f, 0.0f, 0.0f};
+                if (ok) {
+                    tkey = A.key[it];
+                    ve = V3{A.vz[ie], A.vr[ie], A.vt[ie]};
+                    vt = V3{A.vz[it], A.vr[it], A.vt[it]};
+                }
+                // dirty: shares a particle with an earlier candidate of the batch
+                bool dirty = false;
+                for (uint32_t q = 0; q + 1 < nb; ++q) {
+                    const uint32_t e2 = __shfl_sync(FULL, ie, (int)q), t2 = __shfl_sync(FULL, it, (int)q);
+                    if (q < (uint32_t)lane && (e2 == ie || t2 == it)) dirty = true;
+                }
+                for (uint32_t q = 0; q < nb; ++q) {
+                    const bool okq = __shfl_sync(FULL, ok, (int)q);
+                    const bool dq = __shfl_sync(FULL, dirty, (int)q);
+                    const uint32_t ieq = __shfl_sync(FULL, ie, (int)q), itq = __shfl_sync(FULL, it, (int)q);
+                    uint32_t tkq = __shfl_sync(FULL, tkey, (int)q);
+                    V3 veq{__shfl_sync(FULL, ve.x, (int)q), __shfl_sync(FULL, ve.y, (int)q),
+                           __shfl_sync(FULL, ve.z, (int)q)};
+                    V3 vtq{__shfl_sync(FULL, vt.x, (int)q), __shfl_sync(FULL, vt.y, (int)q),
+                           __shfl_sync(FULL, vt.z, (int)q)};
+                    const float Ra = __shfl_sync(FULL, Racc, (int)q), Rc = __shfl_sync(FULL, Rch, (int)q);
+                    if (lane == 0 && okq) {
+                        if (dq) {
+                            tkq = A.key[itq];
+                            veq = V3{A.vz[ieq], A.vr[ieq], A.vt[ieq]};
+                            vtq = V3{A.vz[itq], A.vr[itq], A.vt[itq]};
+                        }
+                        // the candidate's stream after its four pair-choice draws
+                        Stream rs(lc, st->step, sid_cand(k, m0 + q), RI->seed, RI->run);
+                        rs.ctr.w = 1u;
+                        rs.used = 4;
+                        process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, Ra, Rc, xsE, xs, cc, st, rho_e,
+                                          rho_h);
+                    }
+                }
                 __syncwarp();
             }
         }

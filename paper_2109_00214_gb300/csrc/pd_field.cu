@@ -58,7 +58,7 @@ size_t run_bytes(int nz, int nr) {
     size_t t = 0;
     for (int l = 0; l < n; ++l) {
         const size_t nodes = (size_t)(a[l] + 1) * (b[l] + 1);
-        t += 3 * al(nodes * 8) + 3 * al((size_t)(b[l] + 1) * 8);
+        t += 4 * al(nodes * 8) + 3 * al((size_t)(b[l] + 1) * 8);
     }
     const size_t m = (size_t)coarse_unknowns(a, b, n);
     if (m <= (size_t)MG_DIRECT_MAX) t += al(m * m * 8);
@@ -133,24 +133,73 @@ __device__ __forceinline__ double apply_A(const MGLevel& L, const double* x, int
     return s;
 }
 
-// red-black Gauss-Seidel on the interior rows; Dirichlet neighbours are part
-// of f (level 0) or zero (corrections)
-__global__ void k_smooth(const MGLevel* lev, const int* nlev, const int* done, int l, int color) {
+// red-black Gauss-Seidel on the interior rows (Dirichlet neighbours are part
+// of f on level 0 and zero for the corrections): see k_smooth_pair
+
+// Two half-sweeps of red-black Gauss-Seidel in one launch: color c1 on a
+// tile and the ring of nodes around it, then color c2 on the tile, in shared
+// memory; reads `src`, writes the tile's interior-row nodes to `dst` (so no
+// block reads a value another block has already updated: the same result as
+// two separate half-sweeps).  Tile: SP_TI interior rows x SP_TJ radial nodes,
+// blockIdx.x = tile, blockIdx.y = run.
+constexpr int SP_TI = 8, SP_TJ = 32;
+
+__global__ void __launch_bounds__(256) k_smooth_pair(const MGLevel* lev, const int* nlev, const int* done, int l,
+                                                     int c1, int swap) {
+    __shared__ double xs[SP_TI + 4][SP_TJ + 4];
+    __shared__ double fsm[SP_TI + 2][SP_TJ + 2];
+    __shared__ double cap[SP_TJ + 2], cam[SP_TJ + 2], cb[SP_TJ + 2];
     const int run = blockIdx.y;
     if (!level_active(nlev, done, run, l, false)) return;
     const MGLevel L = lev[run * MG_MAX_LEVELS + l];
+    const double* src = swap ? L.x2 : L.x;
+    double* dst = swap ? L.x : L.x2;
     const int W = L.nr + 1;
-    const int n = (L.nz - 1) * W;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const int i = 1 + q / W, j = q - (i - 1) * W;
-        if (((i + j) & 1) != color) continue;
-        const int k = i * W + j;
-        double s = L.f[k];
-        if (j < L.nr) s += L.ap[j] * L.x[k + 1];
-        if (j > 0) s += L.am[j] * L.x[k - 1];
-        if (i + 1 < L.nz) s += L.b[j] * L.x[k + W];
-        if (i - 1 > 0) s += L.b[j] * L.x[k - W];
-        L.x[k] = s / (L.ap[j] + L.am[j] + 2.0 * L.b[j]);
+    const int tj = (W + SP_TJ - 1) / SP_TJ, ti = (L.nz - 1 + SP_TI - 1) / SP_TI;
+    if ((int)blockIdx.x >= ti * tj) return;
+    const int i0 = 1 + ((int)blockIdx.x / tj) * SP_TI, j0 = ((int)blockIdx.x % tj) * SP_TJ;
+    for (int q = threadIdx.x; q < (SP_TI + 4) * (SP_TJ + 4); q += blockDim.x) {
+        const int a = q / (SP_TJ + 4), c = q % (SP_TJ + 4);
+        const int i = i0 - 2 + a, j = j0 - 2 + c;
+        // only interior rows are read by the update (Dirichlet rows enter through f)
+        xs[a][c] = (i >= 1 && i <= L.nz - 1 && j >= 0 && j <= L.nr) ? src[i * W + j] : 0.0;
+    }
+    for (int q = threadIdx.x; q < (SP_TI + 2) * (SP_TJ + 2); q += blockDim.x) {
+        const int a = q / (SP_TJ + 2), c = q % (SP_TJ + 2);
+        const int i = i0 - 1 + a, j = j0 - 1 + c;
+        fsm[a][c] = (i >= 1 && i <= L.nz - 1 && j >= 0 && j <= L.nr) ? L.f[i * W + j] : 0.0;
+    }
+    for (int c = threadIdx.x; c < SP_TJ + 2; c += blockDim.x) {
+        const int j = j0 - 1 + c;
+        const bool in = j >= 0 && j <= L.nr;
+        cap[c] = in ? L.ap[j] : 0.0;
+        cam[c] = in ? L.am[j] : 0.0;
+        cb[c] = in ? L.b[j] : 0.0;
+    }
+    __syncthreads();
+    // node (i, j) of shared row a = i - i0 + 2, column c = j - j0 + 2
+    auto update = [&](int i, int j) {
+        const int a = i - i0 + 2, c = j - j0 + 2, cc = c - 1;
+        double s = fsm[a - 1][c - 1];
+        if (j < L.nr) s += cap[cc] * xs[a][c + 1];
+        if (j > 0) s += cam[cc] * xs[a][c - 1];
+        if (i + 1 < L.nz) s += cb[cc] * xs[a + 1][c];
+        if (i - 1 > 0) s += cb[cc] * xs[a - 1][c];
+        xs[a][c] = s / (cap[cc] + cam[cc] + 2.0 * cb[cc]);
+    };
+    for (int q = threadIdx.x; q < (SP_TI + 2) * (SP_TJ + 2); q += blockDim.x) {
+        const int i = i0 - 1 + q / (SP_TJ + 2), j = j0 - 1 + q % (SP_TJ + 2);
+        if (i >= 1 && i <= L.nz - 1 && j >= 0 && j <= L.nr && ((i + j) & 1) == c1) update(i, j);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < SP_TI * SP_TJ; q += blockDim.x) {
+        const int i = i0 + q / SP_TJ, j = j0 + q % SP_TJ;
+        if (i <= L.nz - 1 && j <= L.nr && ((i + j) & 1) != c1) update(i, j);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < SP_TI * SP_TJ; q += blockDim.x) {
+        const int i = i0 + q / SP_TJ, j = j0 + q % SP_TJ;
+        if (i <= L.nz - 1 && j <= L.nr) dst[i * W + j] = xs[i - i0 + 2][j - j0 + 2];
     }
 }
 
@@ -439,6 +488,7 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
             L.x = l == 0 ? phi + node_base[r] : (double*)take(nodes * 8);
             L.f = (double*)take(nodes * 8);
             L.r = (double*)take(nodes * 8);
+            L.x2 = (double*)take(nodes * 8);
             L.ap = (double*)take((size_t)(L.nr + 1) * 8);
             L.am = (double*)take((size_t)(L.nr + 1) * 8);
             L.b = (double*)take((size_t)(L.nr + 1) * 8);
@@ -519,15 +569,37 @@ static int level_blocks(const FieldSolver& fs, int l) {
     return blocks_for(fs, mx);
 }
 
+// kernels one V-cycle launches: per level 2 fused smoothing launches, a
+// residual and the coarsest solve, restriction below all but the deepest
+// level, and on the way up prolongation and 2 smoothing launches
+static int vcycle_kernels(const FieldSolver& fs) { return 8 * fs.max_levels - 4; }
+
+// tiles of k_smooth_pair on level l of the largest run there
+static int level_tiles(const FieldSolver& fs, int l) {
+    int mx = 1;
+    for (int r = 0; r < fs.nruns; ++r)
+        if (l < fs.nlev[r]) {
+            const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
+            const int t = ((L.nz - 1 + SP_TI - 1) / SP_TI) * ((L.nr + 1 + SP_TJ - 1) / SP_TJ);
+            mx = std::max(mx, t);
+        }
+    return mx;
+}
+
+// two red-black iterations (four half-sweeps) in two fused launches; the
+// second returns the values to x
+static void smooth2(FieldSolver& fs, int l, int c1, cudaStream_t s) {
+    const dim3 g(level_tiles(fs, l), fs.nruns);
+    k_smooth_pair<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, c1, 0);
+    k_smooth_pair<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, c1, 1);
+}
+
 static void vcycle(FieldSolver& fs, cudaStream_t s) {
     const int R = fs.nruns;
     // down: smooth, residual, restrict; the coarsest level of each run is solved directly
     for (int l = 0; l < fs.max_levels; ++l) {
         const dim3 g(level_blocks(fs, l), R);
-        for (int it = 0; it < 2; ++it) {
-            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
-            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
-        }
+        smooth2(fs, l, 0, s);
         k_residual<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, nullptr);
         if (l + 1 < fs.max_levels) {
             const dim3 gc(level_blocks(fs, l + 1), R);
@@ -539,10 +611,7 @@ static void vcycle(FieldSolver& fs, cudaStream_t s) {
     for (int l = fs.max_levels - 2; l >= 0; --l) {
         const dim3 g(level_blocks(fs, l), R);
         k_prolong<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
-        for (int it = 0; it < 2; ++it) {
-            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 1);
-            k_smooth<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, 0);
-        }
+        smooth2(fs, l, 1, s);
     }
 }
 
@@ -556,12 +625,13 @@ static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStrea
 }
 
 int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
-                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s) {
+                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s, int* kernels) {
     (void)E;
     const int R = fs.nruns;
     const dim3 g0(blocks_for(fs, fs.max_nodes0), R);
     k_rhs<<<g0, fs.threads, 0, s>>>(rho_e, rho_h, fs.fv_over_verb, fs.verb_base, fs.fvb_off, fs.lev, runs, rs, phi);
     norms(fs, rs, 0, 1, s);
+    if (kernels) *kernels += 3;
     if (host_check) {
         for (int cyc = 1; cyc <= fs.max_cycles; ++cyc) {
             if (cudaMemcpyAsync(fs.host_done, fs.done, (size_t)R * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -572,11 +642,13 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
             if (all) break;
             vcycle(fs, s);
             norms(fs, rs, cyc, 0, s);
+            if (kernels) *kernels += vcycle_kernels(fs) + 2;
         }
     } else {
         for (int cyc = 1; cyc <= cycles; ++cyc) {
             vcycle(fs, s);
             norms(fs, rs, cyc, 0, s);
+            if (kernels) *kernels += vcycle_kernels(fs) + 2;
         }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 1;

@@ -16,6 +16,7 @@ constexpr int MG_DIRECT_MAX = 256;      // coarsest levels up to this many unkno
 struct MGLevel {
     int nz, nr;              // cells
     double *x, *f, *r;       // (nz+1)(nr+1) nodes each
+    double* x2;              // the smoother's second buffer (interior rows)
     double *ap, *am, *b;     // per radial node j: radial face and axial coefficients
 };
 
@@ -56,7 +57,8 @@ void field_free(FieldSolver& fs);
 // issued with no host synchronisation (runs already converged skip them),
 // so the solve can be captured in a CUDA graph.  Records relres / cycles.
 int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
-                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s);
+                const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s,
+                int* kernels = nullptr);   // adds the number of kernels launched
 
 // E = -grad(phi) of every run; flags runs whose solve met a non-finite value
 // and folds each run's final residual into RunState::relres_max

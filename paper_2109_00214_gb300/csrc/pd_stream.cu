@@ -81,7 +81,7 @@ __device__ __forceinline__ float spc(const float (&a)[NSP], int sp) {
 }
 
 template <bool RZ, bool FIELD, bool MULTI>
-__global__ void __launch_bounds__(256) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
+__global__ void __launch_bounds__(256, 4) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
                                                uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
                                                DevState* st, KParams P) {
@@ -323,7 +323,7 @@ __device__ __forceinline__ uint32_t movers_before(const uint32_t* __restrict__ m
 constexpr int SCATTER_THREADS = 256;
 constexpr uint32_t SCATTER_WIN = 1536;
 
-__global__ void __launch_bounds__(SCATTER_THREADS) k_scatter4(Particles A, Particles B,
+__global__ void __launch_bounds__(SCATTER_THREADS, 4) k_scatter4(Particles A, Particles B,
                                                               const uint32_t* __restrict__ old_off,
                                                               const uint32_t* __restrict__ new_off,
                                                               const uint32_t* __restrict__ stay, uint32_t* in_cnt,
