@@ -194,6 +194,10 @@ BYTES_PER_PARTICLE = {
     "push": 32.0,      # read key, pz, pr, vz, vr (20 B); write key, pz, pr (12 B)
     "scatter": 56.0,   # read 7 x 4 B, write 7 x 4 B
 }
+# DRAM bytes per particle of the same kernels from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of a 2.49e7-particle launch, profiles/push_scatter_512x512_2.5e7_ncu.md),
+# scaled to a launch by its particle count; to be set to None when the kernels change
+TRAFFIC_PER_PARTICLE = {"push": 768.44e6 / 24898326, "scatter": 1365.81e6 / 24898326}
 
 
 def cpu_baseline(args, cfg_full, seed):
@@ -579,9 +583,12 @@ def main():
     bytes_per_launch = BYTES_PER_PARTICLE[dom] * 0.5 * (n0 + n1)
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     total_kernel_ms = sum(v[0] for v in prof.values())
+    tpp = TRAFFIC_PER_PARTICLE.get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "traffic": None, "algorithmic_bytes_per_launch": bytes_per_launch,
+                "traffic": tpp * 0.5 * (n0 + n1) if tpp else None,
+                "traffic_source": "ncu dram bytes per particle of a 2.49e7-particle launch, scaled" if tpp else None,
+                "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launch_ms": per_launch_ms,
                 "share": prof[dom][0] / total_kernel_ms if total_kernel_ms > 0 else None,
                 "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}

@@ -109,7 +109,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.ck = take(ckl * 4);
     L.ray = take(1024 * 4);
     L.hist = take(4096 * 8);
-    L.spc = take(NSP * 8);
+    L.spc = take((size_t)R * NSP * 8);                     // live particles per run and species
     L.state = take(sizeof(DevState));
     L.rs = take(R * sizeof(RunState));
     L.runs = take(R * sizeof(RunInfo));
@@ -204,6 +204,10 @@ struct pd_sim {
     uint32_t* grp_base;
     WarmHistory whist;
     int64_t solves;          // Poisson solves since create / load (history depth)
+    // species counts of all runs, cached until the particles change
+    uint64_t version;        // bumped by every call that changes the particles
+    uint64_t spc_version;    // version the cache was taken at (0: none)
+    std::vector<unsigned long long> spc_host;
 };
 
 namespace {
@@ -790,6 +794,8 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->grp_base = P32(L.grp_base);
     s->warm_mode = PD_WARM_PREVIOUS;
     s->warm_net = nullptr;
+    s->version = 1;
+    s->spc_version = 0;
     s->whist = WarmHistory{(double*)(w + L.rho_last), (double*)(w + L.rho_prev), (double*)(w + L.phi_prev),
                           (double*)(w + L.V_last), (double*)(w + L.V_prev)};
     s->solves = 0;
@@ -896,6 +902,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
 pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
                     const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
+    ++s->version;
     if (run < 0 || run >= s->R) return fail(s, PD_ERR_ARG, "bad run index");
     if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
     if (n == 0) return PD_OK;
@@ -936,6 +943,7 @@ pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int3
 pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
                       const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
+    ++s->version;
     if (run < 0 || run >= s->R) return fail(s, PD_ERR_ARG, "bad run index");
     if (n < 0) return fail(s, PD_ERR_ARG, "n < 0");
     if (n == 0) return PD_OK;
@@ -974,10 +982,17 @@ pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const in
 
 pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
     if (!s || !out || run < 0 || run >= s->R) return PD_ERR_ARG;
-    CK(cudaMemsetAsync(s->spc, 0, NSP * 8, s->stream));
-    launch_species_count(s->A, s->st, kparams(s, 1), run, s->spc, grid_for(s, 4), s->stream);
+    if (s->spc_version != s->version) {
+        // one pass counts every run (an ensemble's runs are read one after another)
+        s->spc_host.assign((size_t)s->R * NSP, 0ull);
+        CK(cudaMemsetAsync(s->spc, 0, (size_t)s->R * NSP * 8, s->stream));
+        launch_species_count_all(s->A, s->st, kparams(s, 1), s->spc, grid_for(s, 4), s->stream);
+        CK(cudaMemcpyAsync(s->spc_host.data(), s->spc, (size_t)s->R * NSP * 8, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        s->spc_version = s->version;
+    }
     unsigned long long cnt[NSP];
-    CK(cudaMemcpyAsync(cnt, s->spc, sizeof(cnt), cudaMemcpyDeviceToHost, s->stream));
+    for (int k = 0; k < NSP; ++k) cnt[k] = s->spc_host[(size_t)run * NSP + k];
     RunState d;
     pd_status r = read_run(s, run, &d);
     if (r != PD_OK) return r;
@@ -1200,6 +1215,7 @@ pd_status pd_set_graph_mode(pd_sim* s, int enable, int poisson_cycles) {
 
 pd_status pd_step(pd_sim* s, int64_t n_steps) {
     if (!s) return PD_ERR_ARG;
+    ++s->version;
     if (n_steps < 0) return fail(s, PD_ERR_ARG, "n_steps < 0");
     // RunState::relres_max of every run restarts with this call
     CK(cudaMemset2DAsync(&s->rs[0].relres_max, sizeof(RunState), 0, sizeof(double), (size_t)s->R, s->stream));
@@ -1430,6 +1446,7 @@ pd_status pd_save(pd_sim* s, const char* path) {
 
 pd_status pd_load(pd_sim* s, const char* path) {
     if (!s || !path) return PD_ERR_ARG;
+    ++s->version;
     DevState cur;
     pd_status r = sync_check(s, &cur);
     if (r != PD_OK) return r;
@@ -1543,6 +1560,7 @@ pd_status pd_set_tuning(pd_sim* s, const pd_tuning* t) {
 
 pd_status pd_autotune(pd_sim* s, int steps_per_trial, pd_tuning* out) {
     if (!s) return PD_ERR_ARG;
+    ++s->version;
     if (steps_per_trial < 1 || steps_per_trial > 64) return fail(s, PD_ERR_ARG, "steps_per_trial must be in 1..64");
     if (!s->primed) {
         pd_status r = prime(s);

@@ -34,6 +34,7 @@ constexpr double QE_ = 1.602176634e-19;
 constexpr double EPS0_ = 8.8541878128e-12;
 constexpr double PI_ = 3.14159265358979323846;
 constexpr int RED_BLOCKS = 64;
+constexpr int MAP_CHUNK = 256;      // items of one work-list entry
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -51,6 +52,22 @@ void level_dims(int nz, int nr, int* nzs, int* nrs, int& nlev) {
 
 // unknowns of the coarsest level (interior rows, all radial nodes)
 int coarse_unknowns(const int* a, const int* b, int n) { return (a[n - 1] - 1) * (b[n - 1] + 1); }
+
+constexpr int SP_TI = 8, SP_TJ = 32;   // smoother tile: interior rows x radial nodes
+
+int chunks(long long n) { return (int)((n + MAP_CHUNK - 1) / MAP_CHUNK); }
+int tiles_of(int nz, int nr) { return ((nz - 1 + SP_TI - 1) / SP_TI) * ((nr + 1 + SP_TJ - 1) / SP_TJ); }
+
+// work-list entries of one run (all levels that smooth)
+size_t run_tasks(int nz, int nr) {
+    int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
+    level_dims(nz, nr, a, b, n);
+    size_t t = 0;
+    for (int l = 0; l + 1 < n; ++l)
+        t += chunks((long long)(a[l] - 1) * (b[l] + 1)) + chunks((long long)(a[l + 1] + 1) * (b[l + 1] + 1)) +
+             tiles_of(a[l], b[l]);
+    return t;
+}
 
 size_t run_bytes(int nz, int nr) {
     int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
@@ -75,7 +92,12 @@ bool field_grid_ok(int nz, int nr) {
 size_t field_workspace_bytes(const std::vector<int>& nz, const std::vector<int>& nr) {
     size_t t = 0;
     const size_t R = nz.size();
-    for (size_t r = 0; r < R; ++r) t += run_bytes(nz[r], nr[r]);
+    size_t tasks = 0;
+    for (size_t r = 0; r < R; ++r) {
+        t += run_bytes(nz[r], nr[r]);
+        tasks += run_tasks(nz[r], nr[r]);
+    }
+    t += al(tasks * sizeof(int2) + 8);
     t += al(R * MG_MAX_LEVELS * sizeof(MGLevel)) + al(R * 4) * 3 + al(R * RED_BLOCKS * 2 * 8) + al(R * 8) * 2 +
          al(R * 16) + al(R * sizeof(double*));
     return t;
@@ -140,24 +162,22 @@ __device__ __forceinline__ double apply_A(const MGLevel& L, const double* x, int
 // tile and the ring of nodes around it, then color c2 on the tile, in shared
 // memory; reads `src`, writes the tile's interior-row nodes to `dst` (so no
 // block reads a value another block has already updated: the same result as
-// two separate half-sweeps).  Tile: SP_TI interior rows x SP_TJ radial nodes,
-// blockIdx.x = tile, blockIdx.y = run.
-constexpr int SP_TI = 8, SP_TJ = 32;
-
-__global__ void __launch_bounds__(256) k_smooth_pair(const MGLevel* lev, const int* nlev, const int* done, int l,
-                                                     int c1, int swap) {
+// two separate half-sweeps).  Tile: SP_TI interior rows x SP_TJ radial nodes;
+// the work list gives each block its (run, tile).
+__global__ void __launch_bounds__(256) k_smooth_pair(const MGLevel* lev, const int* done, int l, int c1, int swap,
+                                                     const int2* tasks) {
     __shared__ double xs[SP_TI + 4][SP_TJ + 4];
     __shared__ double fsm[SP_TI + 2][SP_TJ + 2];
     __shared__ double cap[SP_TJ + 2], cam[SP_TJ + 2], cb[SP_TJ + 2];
-    const int run = blockIdx.y;
-    if (!level_active(nlev, done, run, l, false)) return;
+    const int2 tk = tasks[blockIdx.x];
+    const int run = tk.x;
+    if (done[run]) return;
     const MGLevel L = lev[run * MG_MAX_LEVELS + l];
     const double* src = swap ? L.x2 : L.x;
     double* dst = swap ? L.x : L.x2;
     const int W = L.nr + 1;
-    const int tj = (W + SP_TJ - 1) / SP_TJ, ti = (L.nz - 1 + SP_TI - 1) / SP_TI;
-    if ((int)blockIdx.x >= ti * tj) return;
-    const int i0 = 1 + ((int)blockIdx.x / tj) * SP_TI, j0 = ((int)blockIdx.x % tj) * SP_TJ;
+    const int tj = (W + SP_TJ - 1) / SP_TJ;
+    const int i0 = 1 + (tk.y / tj) * SP_TI, j0 = (tk.y % tj) * SP_TJ;
     for (int q = threadIdx.x; q < (SP_TI + 4) * (SP_TJ + 4); q += blockDim.x) {
         const int a = q / (SP_TJ + 4), c = q % (SP_TJ + 4);
         const int i = i0 - 2 + a, j = j0 - 2 + c;
@@ -245,6 +265,21 @@ __global__ void k_residual(const MGLevel* lev, const int* nlev, const int* done,
     }
 }
 
+// residual of level l on the interior rows (work list of the level)
+__global__ void k_residual_tasks(const MGLevel* lev, const int* done, int l, const int2* tasks) {
+    const int2 tk = tasks[blockIdx.x];
+    const int run = tk.x;
+    if (done[run]) return;
+    const MGLevel L = lev[run * MG_MAX_LEVELS + l];
+    const int W = L.nr + 1;
+    const int n = min((L.nz - 1) * W, tk.y + MAP_CHUNK);
+    for (int q = tk.y + threadIdx.x; q < n; q += blockDim.x) {
+        const int i = 1 + q / W, j = q - (i - 1) * W;
+        const int k = i * W + j;
+        L.r[k] = L.f[k] - apply_A(L, L.x, i, j);
+    }
+}
+
 // per run: relres = |r| / |b|, converged flag, bookkeeping
 __global__ void k_norms(const double* red, double* bnorm, int* done, const double* tol, RunState* rs, int nruns,
                         int cycle, int first) {
@@ -271,14 +306,15 @@ __global__ void k_norms(const double* red, double* bnorm, int* done, const doubl
 
 // coarse rhs = sum of the fine integrated residuals over the coarse control
 // volume (full weighting scaled by 4); zero initial coarse correction
-__global__ void k_restrict(const MGLevel* lev, const int* nlev, const int* done, int l) {
-    const int run = blockIdx.y;
-    if (!level_active(nlev, done, run, l, false)) return;
+__global__ void k_restrict(const MGLevel* lev, const int* done, int l, const int2* tasks) {
+    const int2 tk = tasks[blockIdx.x];
+    const int run = tk.x;
+    if (done[run]) return;
     const MGLevel F = lev[run * MG_MAX_LEVELS + l];
     const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
     const int Wc = Cl.nr + 1, Wf = F.nr + 1;
-    const int n = (Cl.nz + 1) * Wc;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int n = min((Cl.nz + 1) * Wc, tk.y + MAP_CHUNK);
+    for (int k = tk.y + threadIdx.x; k < n; k += blockDim.x) {
         const int I = k / Wc, J = k - I * Wc;
         Cl.x[k] = 0.0;
         if (I == 0 || I == Cl.nz) {
@@ -301,14 +337,15 @@ __global__ void k_restrict(const MGLevel* lev, const int* nlev, const int* done,
     }
 }
 
-__global__ void k_prolong(const MGLevel* lev, const int* nlev, const int* done, int l) {
-    const int run = blockIdx.y;
-    if (!level_active(nlev, done, run, l, false)) return;
+__global__ void k_prolong(const MGLevel* lev, const int* done, int l, const int2* tasks) {
+    const int2 tk = tasks[blockIdx.x];
+    const int run = tk.x;
+    if (done[run]) return;
     const MGLevel F = lev[run * MG_MAX_LEVELS + l];
     const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
     const int Wc = Cl.nr + 1, Wf = F.nr + 1;
-    const int n = (F.nz - 1) * Wf;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int n = min((F.nz - 1) * Wf, tk.y + MAP_CHUNK);
+    for (int q = tk.y + threadIdx.x; q < n; q += blockDim.x) {
         const int i = 1 + q / Wf, j = q - (i - 1) * Wf;
         const int I0 = i >> 1, J0 = j >> 1;
         const int I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
@@ -540,7 +577,37 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
     fs.tol = (double*)take((size_t)R * 8);
     fs.dzr = (double*)take((size_t)R * 16);
     fs.inv = (double**)take((size_t)R * sizeof(double*));
+    // work lists, level by level
+    std::vector<int2> tasks;
+    for (int l = 0; l < MG_MAX_LEVELS; ++l) {
+        auto add = [&](int r, long long n, int step) {
+            for (long long q = 0; q < n; q += step) tasks.push_back(make_int2(r, (int)q));
+        };
+        fs.fine_off[l] = (int)tasks.size();
+        for (int r = 0; r < R; ++r)
+            if (l + 1 < fs.nlev[r]) {
+                const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
+                add(r, (long long)(L.nz - 1) * (L.nr + 1), MAP_CHUNK);
+            }
+        fs.fine_len[l] = (int)tasks.size() - fs.fine_off[l];
+        fs.coarse_off[l] = (int)tasks.size();
+        for (int r = 0; r < R; ++r)
+            if (l + 1 < fs.nlev[r]) {
+                const MGLevel& C = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l + 1];
+                add(r, (long long)(C.nz + 1) * (C.nr + 1), MAP_CHUNK);
+            }
+        fs.coarse_len[l] = (int)tasks.size() - fs.coarse_off[l];
+        fs.tile_off[l] = (int)tasks.size();
+        for (int r = 0; r < R; ++r)
+            if (l + 1 < fs.nlev[r]) {
+                const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
+                add(r, tiles_of(L.nz, L.nr), 1);
+            }
+        fs.tile_len[l] = (int)tasks.size() - fs.tile_off[l];
+    }
+    fs.tasks = (int2*)take(tasks.size() * sizeof(int2) + 8);
     if (o > bytes) return 1;
+    cudaMemcpyAsync(fs.tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.inv, inv.data(), (size_t)R * sizeof(double*), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.dzr, dzr.data(), (size_t)R * 16, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(fs.fv_over_verb, fvv_all.data(), fvv_all.size() * 8, cudaMemcpyHostToDevice, s);
@@ -559,60 +626,41 @@ void field_free(FieldSolver& fs) {
     fs.host_done = nullptr;
 }
 
-static int level_blocks(const FieldSolver& fs, int l) {
-    int mx = 0;
-    for (int r = 0; r < fs.nruns; ++r)
-        if (l < fs.nlev[r]) {
-            const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
-            mx = std::max(mx, (L.nz + 1) * (L.nr + 1));
-        }
-    return blocks_for(fs, mx);
-}
-
-// kernels one V-cycle launches: per level 2 fused smoothing launches, a
-// residual and the coarsest solve, restriction below all but the deepest
-// level, and on the way up prolongation and 2 smoothing launches
-static int vcycle_kernels(const FieldSolver& fs) { return 8 * fs.max_levels - 4; }
-
-// tiles of k_smooth_pair on level l of the largest run there
-static int level_tiles(const FieldSolver& fs, int l) {
-    int mx = 1;
-    for (int r = 0; r < fs.nruns; ++r)
-        if (l < fs.nlev[r]) {
-            const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
-            const int t = ((L.nz - 1 + SP_TI - 1) / SP_TI) * ((L.nr + 1 + SP_TJ - 1) / SP_TJ);
-            mx = std::max(mx, t);
-        }
-    return mx;
-}
 
 // two red-black iterations (four half-sweeps) in two fused launches; the
 // second returns the values to x
-static void smooth2(FieldSolver& fs, int l, int c1, cudaStream_t s) {
-    const dim3 g(level_tiles(fs, l), fs.nruns);
-    k_smooth_pair<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, c1, 0);
-    k_smooth_pair<<<g, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, c1, 1);
+static int smooth2(FieldSolver& fs, int l, int c1, cudaStream_t s) {
+    if (!fs.tile_len[l]) return 0;
+    const int2* t = fs.tasks + fs.tile_off[l];
+    k_smooth_pair<<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.done, l, c1, 0, t);
+    k_smooth_pair<<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.done, l, c1, 1, t);
+    return 2;
 }
 
-static void vcycle(FieldSolver& fs, cudaStream_t s) {
+// one V-cycle of every run that has not converged; returns the kernels launched
+static int vcycle(FieldSolver& fs, cudaStream_t s) {
     const int R = fs.nruns;
+    const int th = fs.threads;
+    int nk = 0;
     // down: smooth, residual, restrict; the coarsest level of each run is solved directly
     for (int l = 0; l < fs.max_levels; ++l) {
-        const dim3 g(level_blocks(fs, l), R);
-        smooth2(fs, l, 0, s);
-        k_residual<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, nullptr);
-        if (l + 1 < fs.max_levels) {
-            const dim3 gc(level_blocks(fs, l + 1), R);
-            k_restrict<<<gc, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
+        nk += smooth2(fs, l, 0, s);
+        if (fs.fine_len[l]) {
+            k_residual_tasks<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.fine_off[l]);
+            k_restrict<<<fs.coarse_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.coarse_off[l]);
+            nk += 2;
         }
         k_coarse<<<R, 256, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, fs.inv, l, 200);
+        ++nk;
     }
     // up: prolong, smooth
     for (int l = fs.max_levels - 2; l >= 0; --l) {
-        const dim3 g(level_blocks(fs, l), R);
-        k_prolong<<<g, fs.threads, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l);
-        smooth2(fs, l, 1, s);
+        if (!fs.fine_len[l]) continue;
+        k_prolong<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.fine_off[l]);
+        ++nk;
+        nk += smooth2(fs, l, 1, s);
     }
+    return nk;
 }
 
 static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStream_t s) {
@@ -640,15 +688,15 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
             bool all = true;
             for (int r = 0; r < R; ++r) all = all && fs.host_done[r] != 0;
             if (all) break;
-            vcycle(fs, s);
+            const int nk = vcycle(fs, s);
             norms(fs, rs, cyc, 0, s);
-            if (kernels) *kernels += vcycle_kernels(fs) + 2;
+            if (kernels) *kernels += nk + 2;
         }
     } else {
         for (int cyc = 1; cyc <= cycles; ++cyc) {
-            vcycle(fs, s);
+            const int nk = vcycle(fs, s);
             norms(fs, rs, cyc, 0, s);
-            if (kernels) *kernels += vcycle_kernels(fs) + 2;
+            if (kernels) *kernels += nk + 2;
         }
     }
     return cudaGetLastError() == cudaSuccess ? 0 : 1;

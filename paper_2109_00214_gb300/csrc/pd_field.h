@@ -39,6 +39,12 @@ struct FieldSolver {
     int max_nodes0 = 0;                 // largest level-0 node count
     double* dzr = nullptr;              // [nruns][2] cell sizes dz, dr
     double** inv = nullptr;             // [nruns] inverse of the coarsest operator (transposed), or null
+    // work lists of the per-cycle kernels: (run, first item) of each block,
+    // for every level l the runs that smooth there (l < levels - 1)
+    int2* tasks = nullptr;              // device copy of all lists
+    int fine_off[MG_MAX_LEVELS] = {}, fine_len[MG_MAX_LEVELS] = {};       // interior nodes of level l
+    int coarse_off[MG_MAX_LEVELS] = {}, coarse_len[MG_MAX_LEVELS] = {};   // all nodes of level l + 1
+    int tile_off[MG_MAX_LEVELS] = {}, tile_len[MG_MAX_LEVELS] = {};       // smoother tiles of level l
     int threads = 256;                  // threads per block of the level kernels (64..1024, a multiple of 32)
     int max_blocks = 1216;              // cap on blocks per run and level (grid-stride loops beyond it)
 };

@@ -40,8 +40,9 @@ void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t 
 // the same over the population counts of the input words
 void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
 // diagnostics of one run
-void launch_species_count(const Particles& A, DevState* st, const KParams& P, int run, unsigned long long* out,
-                          int grid, cudaStream_t s);
+// live particles of every run and species, out[run * NSP + species] (zeroed by the caller)
+void launch_species_count_all(const Particles& A, DevState* st, const KParams& P, unsigned long long* out, int grid,
+                              cudaStream_t s);
 void launch_density(const Particles& A, DevState* st, const KParams& P, int run, int species, long long* acc,
                     int grid, cudaStream_t s);
 void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int run, int species, double lo, double hi,

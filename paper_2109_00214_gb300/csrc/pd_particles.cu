@@ -152,23 +152,26 @@ __device__ __forceinline__ bool in_run(uint32_t key, const RunInfo& RI) {
 
 // live particles of one run per species: per-warp ballot counts, one atomic
 // per warp and species at the end
-__global__ void k_species_count(Particles A, DevState* st, KParams P, int run, unsigned long long* out) {
+// live particles per run and species, all runs in one pass: out[run * NSP + species]
+// (warp-aggregated shared-memory counters, one flush per block)
+__global__ void k_species_count_all(Particles A, DevState* st, KParams P, unsigned long long* out) {
+    __shared__ unsigned int cnt[MAX_RUNS_SMEM * NSP];
+    for (int q = threadIdx.x; q < P.nruns * NSP; q += blockDim.x) cnt[q] = 0u;
+    __syncthreads();
     const unsigned long long n = st->n_slots;
-    const int lane = threadIdx.x & 31;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    const RunInfo RI = P.runs[run];
-    unsigned long long c[NSP] = {0, 0, 0, 0, 0};
     for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n;
          i0 += stride) {
-        const unsigned long long i = i0 + lane;
+        const unsigned long long i = i0 + (threadIdx.x & 31);
         const uint32_t key = i < n ? A.key[i] : DEAD;
-        const uint32_t sp = in_run(key, RI) ? key_species(key) : 255u;
-#pragma unroll
-        for (int s = 0; s < NSP; ++s) c[s] += (unsigned)__popc(__ballot_sync(FULL, sp == (uint32_t)s));
+        const bool live = key != DEAD;
+        const uint32_t slot = live ? (uint32_t)run_of(P, key_cell(key)) * NSP + key_species(key) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(FULL, slot);
+        if (live && (threadIdx.x & 31) == 31 - __clz((int)peers)) atomicAdd(&cnt[slot], (unsigned)__popc(peers));
     }
-    if (lane == 0)
-        for (int s = 0; s < NSP; ++s)
-            if (c[s]) atomicAdd(&out[s], c[s]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < P.nruns * NSP; q += blockDim.x)
+        if (cnt[q]) atomicAdd(&out[q], (unsigned long long)cnt[q]);
 }
 
 __global__ void k_density(Particles A, DevState* st, KParams P, int run, int species, long long* acc) {
@@ -253,9 +256,9 @@ void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, c
                       unsigned int* bad, int grid, cudaStream_t s) {
     k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, cell_base, id0, key, id, bad);
 }
-void launch_species_count(const Particles& A, DevState* st, const KParams& P, int run, unsigned long long* out,
-                          int grid, cudaStream_t s) {
-    k_species_count<<<grid, 256, 0, s>>>(A, st, P, run, out);
+void launch_species_count_all(const Particles& A, DevState* st, const KParams& P, unsigned long long* out, int grid,
+                              cudaStream_t s) {
+    k_species_count_all<<<grid, 256, 0, s>>>(A, st, P, out);
 }
 void launch_density(const Particles& A, DevState* st, const KParams& P, int run, int species, long long* acc,
                     int grid, cudaStream_t s) {
