@@ -247,6 +247,17 @@ def pd_load_particles(h, parts):
     _check(h, _lib().pd_load_particles(h, n, *[_ptr(x) for x in a]), "pd_load_particles")
 
 
+def pd_load_particles_ptrs(h, n, ptrs):
+    """Host pointers (int; pinned memory loads fastest) of species u8, iz i32,
+    ir i32, pz, pr, vz, vr, vt f32."""
+    _check(h, _lib().pd_load_particles(h, int(n), *[P(p) for p in ptrs]), "pd_load_particles")
+
+
+def pd_load_particles_run_ptrs(h, run, n, ptrs):
+    """As pd_load_particles_ptrs, into one run of an ensemble."""
+    _check(h, _lib().pd_load_particles_run(h, int(run), int(n), *[P(p) for p in ptrs]), "pd_load_particles_run")
+
+
 def pd_load_particles_device(h, n, ptrs):
     """ptrs: device pointers (int) of species u8, iz i32, ir i32, pz, pr, vz, vr, vt f32."""
     _check(h, _lib().pd_load_particles_device(h, int(n), *[P(p) for p in ptrs]), "pd_load_particles_device")
@@ -646,6 +657,9 @@ class Simulation:
     def scalars(self):
         return pd_get_scalars(self.h)
 
+    def set_graph_mode(self, enable, poisson_cycles=4):
+        pd_set_graph_mode(self.h, enable, poisson_cycles)
+
     def tuning(self):
         return pd_get_tuning(self.h)
 
@@ -772,5 +786,3 @@ class Ensemble(Simulation):
     def field(self):
         return pd_get_field(self.h, self.nodes)
 
-    def set_graph_mode(self, enable, poisson_cycles=4):
-        pd_set_graph_mode(self.h, enable, poisson_cycles)

@@ -899,6 +899,13 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     return PD_OK;
 }
 
+pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
+                      const float* pz, const float* pr, const float* vz, const float* vr, const float* vt);
+
+// host arrays: copied straight to the device (fast from pinned memory) --
+// positions and velocities into their slots, species and cell indices into
+// the other particle buffer, free between steps -- and checked and packed
+// there by the device load
 pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
                     const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
@@ -909,35 +916,20 @@ pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int3
     DevState d;
     pd_status r = sync_check(s, &d);
     if (r != PD_OK) return r;
-    RunState rs;
-    r = read_run(s, run, &rs);
-    if (r != PD_OK) return r;
     if (d.n_slots + (uint64_t)n > s->L.cap) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
-    if ((uint64_t)rs.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
-    const RunInfo& RI = s->runs[run];
-    std::vector<uint32_t> key(n), id(n);
-    for (int64_t q = 0; q < n; ++q) {
-        if (sp[q] >= NSP || iz[q] < 0 || iz[q] >= RI.nz || ir[q] < 0 || ir[q] >= RI.nr ||
-            !(pz[q] >= 0.0f && pz[q] < 1.0f) || !(pr[q] >= 0.0f && pr[q] < 1.0f))
-            return fail(s, PD_ERR_ARG, "particle " + std::to_string(q) + " out of range");
-        key[q] = ((uint32_t)sp[q] << 24) | (RI.cell_base + (uint32_t)iz[q] * (uint32_t)RI.nr + (uint32_t)ir[q]);
-        id[q] = rs.id_next + (uint32_t)q;
-    }
-    const size_t o = d.n_slots;
-    CK(cudaMemcpyAsync(s->A.key + o, key.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.pz + o, pz, n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.pr + o, pr, n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vz + o, vz, n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vr + o, vr, n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vt + o, vt, n * 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.id + o, id.data(), n * 4, cudaMemcpyHostToDevice, s->stream));
-    d.n_slots += (uint64_t)n;
-    rs.id_next += (uint32_t)n;
-    CK(cudaMemcpyAsync(&s->st->n_slots, &d.n_slots, 8, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(&s->rs[run].id_next, &rs.id_next, 4, cudaMemcpyHostToDevice, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
-    s->primed = false;
-    return PD_OK;
+    const size_t o = d.n_slots, nb = (size_t)n * 4;
+    int32_t* diz = reinterpret_cast<int32_t*>(s->B.key + o);
+    int32_t* dir = reinterpret_cast<int32_t*>(s->B.id + o);
+    uint8_t* dsp = reinterpret_cast<uint8_t*>(s->B.pz + o);
+    CK(cudaMemcpyAsync(diz, iz, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dir, ir, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(dsp, sp, (size_t)n, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.pz + o, pz, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.pr + o, pr, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vz + o, vz, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vr + o, vr, nb, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->A.vt + o, vt, nb, cudaMemcpyHostToDevice, s->stream));
+    return load_device(s, run, n, dsp, diz, dir, s->A.pz + o, s->A.pr + o, s->A.vz + o, s->A.vr + o, s->A.vt + o);
 }
 
 pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
@@ -963,11 +955,10 @@ pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const in
     launch_pack_keys(sp, iz, ir, pz, pr, n, RI.nz, RI.nr, RI.cell_base, rs.id_next, s->A.key + o, s->A.id + o, dbad,
                      grid_for(s, 8), s->stream);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(s->A.pz + o, pz, n * 4, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.pr + o, pr, n * 4, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vz + o, vz, n * 4, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vr + o, vr, n * 4, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->A.vt + o, vt, n * 4, cudaMemcpyDeviceToDevice, s->stream));
+    const float* src[5] = {pz, pr, vz, vr, vt};
+    float* dst[5] = {s->A.pz + o, s->A.pr + o, s->A.vz + o, s->A.vr + o, s->A.vt + o};
+    for (int k = 0; k < 5; ++k)   // (a host load has already put them in place)
+        if (src[k] != dst[k]) CK(cudaMemcpyAsync(dst[k], src[k], n * 4, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(&bad, dbad, 4, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     if (bad) return fail(s, PD_ERR_ARG, "a device particle is out of range");

@@ -407,9 +407,35 @@ __device__ bool spawn_electron(Particles& A, CellCtx& cx, DevState* st, long lon
 }
 
 // lane-0 part of one candidate after the pair is chosen
-// (tkey, ve, vt: the target's key and both velocities as they are now)
+// cross sections of a pair: running sums cum[] of the class's channels at
+// the pair's relative energy, and sigma_T g
+struct PairEval {
+    float cum[4];
+    float sg;
+};
+
+__device__ __forceinline__ PairEval evaluate_pair(int k, const V3& ve, const V3& vt, const float* __restrict__ xsE,
+                                                  const float* __restrict__ xs, const CollConsts& cc) {
+    PairEval e;
+    const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
+    const float g2 = (ux * ux + uy * uy) + uz * uz;
+    const float g = sqrtf(g2);
+    const float eps = g2 * cc.kmr;
+    const int ch0 = k == 0 ? CH_EL : CH_SW;
+    const int nch = k == 0 ? 4 : 1;
+    float sT = 0.0f;
+    for (int q = 0; q < 4; ++q) {
+        if (q < nch) sT = sT + xs_lookup(xsE, xs + (ch0 + q) * XS_N, eps);
+        e.cum[q] = sT;
+    }
+    e.sg = sT * g;
+    return e;
+}
+
+// (tkey, ve, vt: the target's key and both velocities as they are now; ev:
+// evaluate_pair of ve, vt)
 __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
-                                  uint32_t tkey, V3 ve, V3 vt, float Racc, float Rch,
+                                  uint32_t tkey, V3 ve, V3 vt, const PairEval& ev, float Racc, float Rch,
                                   const float* __restrict__ xsE, const float* __restrict__ xs,
                                   const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h) {
     const int ts = k == 0 ? SP_CU : SP_CUP;
@@ -417,19 +443,11 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
         ++cx.consumed;
         return;
     }
-    const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
-    const float g2 = (ux * ux + uy * uy) + uz * uz;
-    const float g = sqrtf(g2);
-    const float eps = g2 * cc.kmr;
     const int ch0 = k == 0 ? CH_EL : CH_SW;
     const int nch = k == 0 ? 4 : 1;
-    float cum[4];
-    float sT = 0.0f;
-    for (int q = 0; q < nch; ++q) {
-        sT = sT + xs_lookup(xsE, xs + (ch0 + q) * XS_N, eps);
-        cum[q] = sT;
-    }
-    const float sg = sT * g;
+    const float* cum = ev.cum;
+    const float sT = cum[nch - 1];
+    const float sg = ev.sg;
     if (sg > cc.sgmax[k]) ++cx.viol;
     if (!(Racc * cc.sgmax[k] < sg)) {
         ++cx.nulls;
@@ -490,7 +508,7 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     ++cx.ev[ch];
 }
 
-__global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                  const uint2* __restrict__ nc, const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
                                                  long long* rho_h, const float* __restrict__ xsE,
@@ -588,6 +606,9 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, con
                     ve = V3{A.vz[ie], A.vr[ie], A.vt[ie]};
                     vt = V3{A.vz[it], A.vr[it], A.vt[it]};
                 }
+                // cross sections of every lane's pair, in parallel (redone by
+                // lane 0 for a pair an earlier candidate may have changed)
+                const PairEval ev = evaluate_pair(k, ve, vt, xsE, xs, cc);
                 // dirty: shares a particle with an earlier candidate of the batch
                 bool dirty = false;
                 for (uint32_t q = 0; q + 1 < nb; ++q) {
@@ -604,18 +625,23 @@ __global__ void __launch_bounds__(128) k_collide(Particles A, RankScratch S, con
                     V3 vtq{__shfl_sync(FULL, vt.x, (int)q), __shfl_sync(FULL, vt.y, (int)q),
                            __shfl_sync(FULL, vt.z, (int)q)};
                     const float Ra = __shfl_sync(FULL, Racc, (int)q), Rc = __shfl_sync(FULL, Rch, (int)q);
+                    PairEval evq;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) evq.cum[e] = __shfl_sync(FULL, ev.cum[e], (int)q);
+                    evq.sg = __shfl_sync(FULL, ev.sg, (int)q);
                     if (lane == 0 && okq) {
                         if (dq) {
                             tkq = A.key[itq];
                             veq = V3{A.vz[ieq], A.vr[ieq], A.vt[ieq]};
                             vtq = V3{A.vz[itq], A.vr[itq], A.vt[itq]};
+                            evq = evaluate_pair(k, veq, vtq, xsE, xs, cc);
                         }
                         // the candidate's stream after its four pair-choice draws
                         Stream rs(lc, st->step, sid_cand(k, m0 + q), RI->seed, RI->run);
                         rs.ctr.w = 1u;
                         rs.used = 4;
-                        process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, Ra, Rc, xsE, xs, cc, st, rho_e,
-                                          rho_h);
+                        process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, evq, Ra, Rc, xsE, xs, cc, st,
+                                          rho_e, rho_h);
                     }
                 }
                 __syncwarp();

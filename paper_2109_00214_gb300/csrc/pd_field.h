@@ -12,12 +12,23 @@ namespace pd {
 constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_DIRECT_MAX = 256;      // coarsest levels up to this many unknowns are solved by their inverse
 
-// one level of one run
+// one level of one run's correction multigrid (float)
 struct MGLevel {
     int nz, nr;              // cells
-    double *x, *f, *r;       // (nz+1)(nr+1) nodes each
-    double* x2;              // the smoother's second buffer (interior rows)
-    double *ap, *am, *b;     // per radial node j: radial face and axial coefficients
+    float *e, *e2, *f, *r;   // correction, the smoother's second buffer, right-hand side, residual (nodes)
+    float *ap, *am, *b;      // per radial node j: radial face and axial coefficients
+    float* dinv;             // 1 / (ap + am + 2 b)
+};
+
+// the double-precision problem of one run (level 0)
+struct MGTop {
+    int nz, nr;
+    double* phi;             // the run's potential (the simulation's phi at the run's node base)
+    double* bf;              // right-hand side b of the discrete Eq. (8) (nodes)
+    double *ap, *am, *b;     // coefficients per radial node
+    double* cr;              // b = (rho_e + rho_h) cr[j] on interior rows (plus the anode row's b V)
+    double* iv;              // 1 / Verboncoeur volume of an interior node at j
+    double idz, i2dz, i2dr;  // 1 / dz, 1 / (2 dz), 1 / (2 dr)
 };
 
 struct FieldSolver {
@@ -26,10 +37,9 @@ struct FieldSolver {
     std::vector<int> nlev;              // levels of each run
     std::vector<MGLevel> host_lev;      // [run * MG_MAX_LEVELS + l]
     MGLevel* lev = nullptr;             // device copy of host_lev
+    std::vector<MGTop> host_top;        // [run]
+    MGTop* top = nullptr;               // device copy
     int* nlev_dev = nullptr;            // [nruns]
-    double* fv_over_verb = nullptr;     // per run and radial node: finite-volume / Verboncoeur volume
-    double* verb_base = nullptr;        // per run and radial node: Verboncoeur volume of an interior row
-    int* fvb_off = nullptr;             // [nruns] offset of a run's radial tables
     double* red = nullptr;              // [nruns][RED_BLOCKS][2] partial norms
     double* bnorm = nullptr;            // [nruns]
     int* done = nullptr;                // [nruns] converged flags
@@ -37,8 +47,7 @@ struct FieldSolver {
     double* tol = nullptr;              // [nruns]
     int max_cycles = 60;
     int max_nodes0 = 0;                 // largest level-0 node count
-    double* dzr = nullptr;              // [nruns][2] cell sizes dz, dr
-    double** inv = nullptr;             // [nruns] inverse of the coarsest operator (transposed), or null
+    float** inv = nullptr;              // [nruns] inverse of the coarsest operator (transposed), or null
     // work lists of the per-cycle kernels: (run, first item) of each block,
     // for every level l the runs that smooth there (l < levels - 1)
     int2* tasks = nullptr;              // device copy of all lists
@@ -46,7 +55,7 @@ struct FieldSolver {
     int coarse_off[MG_MAX_LEVELS] = {}, coarse_len[MG_MAX_LEVELS] = {};   // all nodes of level l + 1
     int tile_off[MG_MAX_LEVELS] = {}, tile_len[MG_MAX_LEVELS] = {};       // smoother tiles of level l
     int threads = 256;                  // threads per block of the level kernels (64..1024, a multiple of 32)
-    int max_blocks = 1216;              // cap on blocks per run and level (grid-stride loops beyond it)
+    int max_blocks = 1216;              // cap on blocks per run of the once-per-solve node kernels
 };
 
 bool field_grid_ok(int nz, int nr);
@@ -58,8 +67,8 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
 void field_free(FieldSolver& fs);
 // rho_e + rho_h (fixed point) -> phi (warm-started from its current value) -> E
 // for every run; the anode potential of each run is RunState::V.  With
-// host_check, V-cycles run until every run reaches its tolerance (the host
-// reads the flags between cycles); otherwise exactly `cycles` V-cycles are
+// host_check, cycles run until every run reaches its tolerance (the host
+// reads the flags between cycles); otherwise exactly `cycles` cycles are
 // issued with no host synchronisation (runs already converged skip them),
 // so the solve can be captured in a CUDA graph.  Records relres / cycles.
 int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
