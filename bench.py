@@ -73,6 +73,7 @@ def parse():
     p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble", "warmstart"])
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="ensemble: skip the one-simulation-per-run arm")
+    p.add_argument("--ens-seeds", type=int, default=8, help="ensemble: seeds (runs = seeds x 8 voltages)")
     p.add_argument("--ws-sizes", default="256,512", help="grid sizes of the warm-start runs")
     p.add_argument("--ws-runs", type=int, default=10, help="runs per grid size (the last one is held out)")
     p.add_argument("--ws-pairs", type=int, default=500, help="pairs per run, one every 2 steps")
@@ -100,6 +101,12 @@ def dist_setup(args):
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return ws, rank, local
+
+
+def shard(items, rank, ws):
+    """The items rank `rank` of `ws` replicas takes (every ws-th, from its rank):
+    the ranks' shares partition the items."""
+    return items[rank::ws]
 
 
 def barrier(ws):
@@ -259,8 +266,8 @@ def run_ensemble(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pd.load_library()
-    all_runs = synthetic.ensemble_breakdown()
-    runs = all_runs[rank::ws]                   # replicas: runs split across ranks, no collective
+    all_runs = synthetic.ensemble_breakdown(seeds=range(1, args.ens_seeds + 1))
+    runs = shard(all_runs, rank, ws)            # replicas: runs split across ranks, no collective
     xs = synthetic.standin_cross_sections()
     cfgs = [c for c, _ in runs]
     R = len(runs)
