@@ -48,7 +48,7 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, rho_e, rho_h, diag, E,
+    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, mid, big, rho_e, rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
@@ -99,6 +99,8 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.cand = take((size_t)L.ncell_pad * 4);
     L.cand_off = take(((size_t)L.ncell_pad + 1) * 4);
     L.active = take(ncell * 4);
+    L.mid = take((size_t)rank_queue_max(cap, RANK_WARP_MAX) * 4);   // id lists queued for rank tables
+    L.big = take((size_t)rank_queue_max(cap, RANK_MID_MAX) * 4);
     L.rho_e = take(nodes * 8);
     L.rho_h = take(nodes * 8);
     L.diag = take(nodes * 8);
@@ -146,7 +148,7 @@ struct pd_sim {
     char* ws;
     int sms;
     Particles A, B;
-    uint32_t *count, *off, *off2, *outc, *stay, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active;
+    uint32_t *count, *off, *off2, *outc, *stay, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
     bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
     uint2* nc;
     long long *rho_e, *rho_h, *diag;
@@ -556,17 +558,18 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     s->sorted_valid = true;
     {
         Timed t(s, K_NCAND, capturing, 1);
-        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->st, P, grid_for(s, s->tune.ncand_blocks_per_sm),
-                     s->stream);
+        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->mid, s->big, s->st, P,
+                     grid_for(s, s->tune.ncand_blocks_per_sm), s->stream);
     }
     {
         Timed t(s, K_SCAN_CAND, capturing, 3);
         launch_scan(s->cand, s->cand_off, s->partial, s->L.ncell_pad, s->stream);
     }
     {
-        Timed t(s, K_COLLIDE, capturing, 1);
-        launch_collide(s->A, s->B, s->off, s->nc, s->cand_off, s->active, s->st, s->rho_e, s->rho_h, s->xsE, s->xs, P,
-                       s->cc, nbins, grid_for(s, s->tune.collide_blocks_per_sm), s->stream);
+        Timed t(s, K_COLLIDE, capturing, 3);
+        launch_collide(s->A, s->B, s->off, s->nc, s->cand_off, s->active, s->mid, s->big, s->st, s->rho_e, s->rho_h,
+                       s->xsE, s->xs, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
+                       s->stream);
     }
     {
         Timed t(s, K_FINALIZE, capturing, 1);
@@ -748,6 +751,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = collide_setup();
     if (e != cudaSuccess) {
         delete s;
         return PD_ERR_CUDA;
@@ -771,6 +775,8 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->cand = P32(L.cand);
     s->cand_off = P32(L.cand_off);
     s->active = P32(L.active);
+    s->mid = P32(L.mid);
+    s->big = P32(L.big);
     s->rho_e = (long long*)(w + L.rho_e);
     s->rho_h = (long long*)(w + L.rho_h);
     s->diag = (long long*)(w + L.diag);

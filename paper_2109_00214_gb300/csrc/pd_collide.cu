@@ -4,11 +4,13 @@
 // form, per cell and pair class k in {(e, Cu), (e, Cu+)}:
 //   k_ncand    N_cand = floor(N_e N_t c_k(r) + R), c_k = W (sigma g)_max dt_coll / V_cell,
 //              one thread per cell; cells with candidates go to an active list.
+//              Lists of more than RANK_WARP_MAX ids that active cells use
+//              are queued for k_rank_tables.
+//   k_rank_tables  rank tables of the queued lists, one block per list.
 //   k_collide  one warp per active cell.  Candidate m draws from the stream
 //              (cell, step, k<<28 | m): the electron and target ranks (in
-//              ascending-id order inside the cell, found by a warp radix
-//              select), the acceptance number and the channel number.  Lane 0
-//              applies the kinematics.  Spawned electrons go to the slots
+//              ascending-id order inside the cell), the acceptance number and
+//              the channel number.  Lane 0 applies the kinematics.  Spawned electrons go to the slots
 //              reserved for the cell at n_alive + 2 * (candidates of the
 //              cells before it); unused reserved slots are marked dead.
 //   k_finalize slot / id bookkeeping and the RC circuit update.
@@ -135,90 +137,93 @@ __device__ void deposit1(long long* rho, const RunInfo& RI, int geom, uint32_t l
               (unsigned long long)(zq * (long long)wz * (long long)wr));
 }
 
-// k-th smallest id of ids[0..N) and its position; the whole warp takes part.
-// Bits above `top` are zero in every id.
-__device__ uint32_t select_rank(const uint32_t* __restrict__ ids, uint32_t N, uint32_t rank, int lane, int top) {
-    uint32_t prefix = 0, want = rank;
-    for (int bit = top; bit >= 0; --bit) {
-        const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
-        uint32_t cnt = 0;
-        for (uint32_t q = lane; q < N; q += 32) {
-            const uint32_t id = ids[q];
-            cnt += ((id & hm) == prefix && !((id >> bit) & 1u)) ? 1u : 0u;
-        }
-        cnt = __reduce_add_sync(FULL, cnt);
-        if (want >= cnt) {
-            want -= cnt;
-            prefix |= 1u << bit;
-        }
-    }
-    uint32_t pos = 0xFFFFFFFFu;
-    for (uint32_t q = lane; q < N; q += 32)
-        if (ids[q] == prefix) pos = q;
-    return __reduce_min_sync(FULL, pos);
-}
+// Ranks inside a cell.  The candidate draws give ranks in ascending-id order;
+// the sorted slots hold a cell's particles in an order that depends on the
+// scatter's atomics, so each list the candidates use is mapped rank ->
+// position by one of:
+//   * ids already ascending with the position (rank = position);
+//   * up to 32 * RC ids with few lookups: a radix select over the ids held
+//     in registers, per lookup;
+//   * otherwise a rank table, position of the r-th smallest id at table[r],
+//     from a stable LSD radix sort of (id, position) pairs by 8-bit digits:
+//     by the cell's warp in its shared memory for lists up to RANK_WARP_MAX
+//     ids, by a block of k_rank_tables (before k_collide) for longer lists,
+//     in shared memory up to RANK_BLOCK_MAX ids and in the scratch buffers
+//     above that.
+// The table of the list at slots [b, b + n) is written to table[b, b + n).
 
 // Register-cached id list of one cell and species: element lane + 32 k in
 // ids[k], for lists of up to 32 * RC ids (one coalesced load per cell).
 constexpr int RC = 8;
+constexpr uint32_t RANK_BLOCK_MAX = 12288;      // longest list the large kernel sorts in shared memory
+constexpr int RT_THREADS = 1024;                // threads of a large-kernel block
+constexpr int RT_MID_THREADS = 256;             // threads of a mid-size-kernel block
+constexpr int RT_MID_BLOCKS_PER_SM = 5;
+constexpr uint32_t SENTINEL = 0xFFFFFFFFu;
 
 struct IdList {
     uint32_t ids[RC];
-    const uint32_t* base;
-    const uint32_t* table;           // rank -> position of a long list, or null
+    const uint32_t* table;           // rank -> position, or null
     uint32_t n;
     int top;                         // highest set bit of any id (0 if none)
     bool cached;
     bool sorted;                     // ids ascend with the position: rank = position
 };
 
-// Scratch for the rank tables of long lists: four u32 arrays indexed by slot.
-// They are the sort's other buffer, unused between the scatter and the next
-// step's scatter; a list at slots [b, b + n) uses [b, b + n) of each.
+// Scratch of the rank tables, arrays indexed by slot: two (key, value) pair
+// buffers and the tables.  They are the sort's other buffer, unused between
+// the scatter and the next step's scatter; a list at slots [b, b + n) uses
+// [b, b + n) of each.
 struct RankScratch {
-    uint32_t *ka, *va, *kb, *vb;
+    uint32_t *xk, *xv, *yk, *yv, *table;
 };
 
-// 8-bit digit passes that sort ids whose highest set bit is `top`
-__device__ __forceinline__ int table_passes(int top) { return top / 8 + 1; }
-
-// Rank table of ids[0..n) (unique): position of the r-th smallest id at
-// table[r].  Stable LSD radix sort of (id, position) pairs by 8-bit digits
-// by one warp: per 32 ids, __match_any_sync groups equal digits, a group's
-// members take consecutive places after the digit's running offset (kept in
-// the warp's 256 shared-memory counters `cnt`) in lane order, and the
-// group's highest lane advances the offset.  Only the digits up to bit `top`
-// (the highest set bit of any id) are sorted.  Returns the buffer holding
-// the table.
-__device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t n, int top, uint32_t* ka,
-                                      uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* cnt, int lane) {
-    for (uint32_t q = lane; q < n; q += 32) {
-        ka[q] = ids[q];
-        va[q] = q;
-    }
-    const int passes = table_passes(top);
-    uint32_t *sk = ka, *sv = va, *dk = kb, *dv = vb;
-    unsigned lt;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-    for (int p = 0; p < passes; ++p) {
-        const int sh = 8 * p;
+// One stable counting pass of an LSD radix sort over the pairs [0, n) by the
+// first nw warps of the group (one warp: BLOCK false; the whole block:
+// BLOCK true, all threads calling): warp w takes the w-th run of `seg`
+// pairs.  Keys come from sk, values from sv (null: the position itself);
+// the pairs go to (dk, dv) ordered by the digit (key >> sh) & 255, pairs of
+// equal digits keeping their order (dk null: values only).  Per 32 pairs,
+// __match_any_sync groups equal digits; a group's members take consecutive
+// places after the digit's running offset in lane order and the group's
+// highest lane advances it.  cnt: 256 counters per warp; tot: 256 (BLOCK).
+template <bool BLOCK>
+__device__ void radix_pass(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv, uint32_t n, int sh,
+                           int nw, uint32_t* cnt, uint32_t* tot, uint32_t tid, int lane, int w) {
+    const uint32_t seg = (n + 32u * nw - 1) / (32u * nw) * 32u;
+    const uint32_t q0 = min(n, (uint32_t)w * seg), q1 = min(n, q0 + seg);
+    uint32_t* c = cnt + (BLOCK ? w * 256 : 0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
+    for (int k = 0; k < 8; ++k) c[lane * 8 + k] = 0u;
+    __syncwarp();
+    for (uint32_t g = q0; g < q1; g += 32) {
+        const uint32_t q = g + lane;
+        const uint32_t d = q < q1 ? (sk[q] >> sh) & 255u : 256u;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (q < q1 && lane == 31 - __clz((int)peers)) c[d] += (uint32_t)__popc(peers);
         __syncwarp();
-        // counts per digit
-        for (uint32_t q0 = 0; q0 < n; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            const uint32_t d = q < n ? (sk[q] >> sh) & 255u : 256u;
-            const unsigned peers = __match_any_sync(FULL, d);
-            if (q < n && lane == 31 - __clz((int)peers)) cnt[d] += (uint32_t)__popc(peers);
-            __syncwarp();
+    }
+    // offsets: digit-major over the warps
+    if (BLOCK) {
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t run = 0;
+            for (int v = 0; v < nw; ++v) {
+                const uint32_t x = cnt[v * 256 + tid];
+                cnt[v * 256 + tid] = run;
+                run += x;
+            }
+            tot[tid] = run;
         }
-        // exclusive scan of the 256 counts (8 per lane)
-        uint32_t c[8], sum = 0;
+        __syncthreads();
+    }
+    if (!BLOCK || w == 0) {
+        uint32_t* t = BLOCK ? tot : c;
+        uint32_t cc[8], sum = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            c[k] = cnt[lane * 8 + k];
-            sum += c[k];
+            cc[k] = t[lane * 8 + k];
+            sum += cc[k];
         }
         uint32_t x = sum;
 #pragma unroll
@@ -230,50 +235,130 @@ __device__ const uint32_t* rank_table(const uint32_t* __restrict__ ids, uint32_t
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            cnt[lane * 8 + k] = run;
-            run += c[k];
+            t[lane * 8 + k] = run;
+            run += cc[k];
         }
         __syncwarp();
-        // stable scatter
-        for (uint32_t q0 = 0; q0 < n; q0 += 32) {
-            const uint32_t q = q0 + lane;
-            const bool in = q < n;
-            const uint32_t key = in ? sk[q] : 0u, val = in ? sv[q] : 0u;
-            const uint32_t d = in ? (key >> sh) & 255u : 256u;
-            const unsigned peers = __match_any_sync(FULL, d);
-            const uint32_t b = in ? cnt[d] : 0u;
-            __syncwarp();
-            if (in) {
-                if (lane == 31 - __clz((int)peers)) cnt[d] = b + (uint32_t)__popc(peers);
-                const uint32_t dst = b + (uint32_t)__popc(peers & lt);
-                dk[dst] = key;
-                dv[dst] = val;
-            }
-            __syncwarp();
-        }
-        uint32_t* t = sk;
-        sk = dk;
-        dk = t;
-        t = sv;
-        sv = dv;
-        dv = t;
     }
-    return sv;
+    if (BLOCK) {
+        __syncthreads();
+        if (tid < 256)
+            for (int v = 0; v < nw; ++v) cnt[v * 256 + tid] += tot[tid];
+        __syncthreads();
+    }
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    for (uint32_t g = q0; g < q1; g += 32) {
+        const uint32_t q = g + lane;
+        const bool in = q < q1;
+        const uint32_t key = in ? sk[q] : 0u, val = in ? (sv ? sv[q] : q) : 0u;
+        const uint32_t d = in ? (key >> sh) & 255u : 256u;
+        const unsigned peers = __match_any_sync(FULL, d);
+        const uint32_t b = in ? c[d] : 0u;
+        __syncwarp();
+        if (in) {
+            if (lane == 31 - __clz((int)peers)) c[d] = b + (uint32_t)__popc(peers);
+            const uint32_t dst = b + (uint32_t)__popc(peers & lt);
+            if (dk) dk[dst] = key;
+            dv[dst] = val;
+        }
+        __syncwarp();
+    }
+    if (BLOCK) __syncthreads();
+    else __syncwarp();
+}
+
+// Rank table of the n ids staged in xk (unique; highest set bit `top`):
+// the digits up to `top`, passes alternating between (yk, yv) and (xk, xv),
+// the last one writing the positions to table.
+template <bool BLOCK>
+__device__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uint32_t* yk, uint32_t* yv,
+                            uint32_t* table, int nw, uint32_t* cnt, uint32_t* tot, uint32_t tid, int lane, int w) {
+    const int passes = top / 8 + 1;
+    const uint32_t *sk = xk, *sv = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        const bool last = p + 1 == passes;
+        uint32_t* dk = last ? nullptr : ((p & 1) ? xk : yk);
+        uint32_t* dv = last ? table : ((p & 1) ? xv : yv);
+        radix_pass<BLOCK>(sk, sv, dk, dv, n, 8 * p, nw, cnt, tot, tid, lane, w);
+        sk = dk;
+        sv = dv;
+    }
+}
+
+// Rank tables of the lists that k_collide will use and k_ncand queued for
+// this kernel (entries cell << 2 | species bin 0..2; *nq of them, at most
+// max_q): one list per block at a time, NT threads, sorted in shared memory
+// up to MAXN ids and in the scratch buffers above that.  A list already in
+// ascending id order gets the identity.
+template <int NT, uint32_t MAXN>
+__global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__ ids, RankScratch S,
+                                                    const uint32_t* __restrict__ off, const uint32_t* __restrict__ q,
+                                                    const uint32_t* nq, uint32_t max_q, uint32_t C) {
+    constexpr int NWARPS = NT / 32;
+    extern __shared__ uint32_t s_buf[];                 // four arrays of MAXN
+    __shared__ uint32_t s_cnt[NWARPS * 256];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_or;
+    const uint32_t nb = min(*nq, max_q);             // an overflow is flagged by k_ncand
+    const uint32_t tid = threadIdx.x;
+    const int lane = (int)(tid & 31u), w = (int)(tid >> 5);
+    if (tid == 0) s_or = 0u;
+    __syncthreads();
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        const uint32_t e = q[b];
+        const uint32_t bin = (e & 3u) * C + (e >> 2);
+        const uint32_t slot0 = off[bin], n = off[bin + 1] - slot0;
+        const uint32_t* base = ids + slot0;
+        const bool in_smem = n <= MAXN;
+        uint32_t* xk = in_smem ? s_buf : S.xk + slot0;
+        uint32_t* xv = in_smem ? s_buf + MAXN : S.xv + slot0;
+        uint32_t* yk = in_smem ? s_buf + 2 * MAXN : S.yk + slot0;
+        uint32_t* yv = in_smem ? s_buf + 3 * MAXN : S.yv + slot0;
+        uint32_t* table = S.table + slot0;
+        uint32_t orv = 0;
+        for (uint32_t k = tid; k < n; k += NT) {
+            const uint32_t x = base[k];
+            xk[k] = x;
+            orv |= x;
+        }
+        orv = __reduce_or_sync(FULL, orv);
+        if (lane == 0 && orv) atomicOr(&s_or, orv);
+        __syncthreads();
+        bool asc = true;
+        for (uint32_t k = tid; k + 1 < n; k += NT)
+            if (!(xk[k] < xk[k + 1])) asc = false;
+        const uint32_t any = s_or;
+        if (__syncthreads_and(asc)) {
+            for (uint32_t r = tid; r < n; r += NT) table[r] = r;
+        } else {
+            const int top = any ? 31 - __clz((int)any) : 0;
+            const int nw = (int)min((uint32_t)NWARPS, (n + 255u) / 256u);
+            radix_table<true>(n, top, xk, xv, yk, yv, table, nw, s_cnt, s_tot, tid, lane, w);
+        }
+        if (tid == 0) s_or = 0u;
+        __syncthreads();
+    }
 }
 
 // ids of one cell and species at slots [slot0, slot0 + n); `lookups` rank
-// selections will follow.  A long list gets a rank table when that is
-// cheaper: a bitwise select sweeps the list once per significant bit, the
-// table sort twice per 8-bit digit at several times the cost per sweep.
+// selections will follow.  sbuf: the warp's four arrays of RANK_WARP_MAX and
+// its 256 counters.
 __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
-                                         uint32_t lookups, const RankScratch& S, uint32_t* cnt, int lane) {
+                                         uint32_t lookups, const RankScratch& S, uint32_t* sbuf, int lane) {
     const uint32_t* base = ids + slot0;
-    L.base = base;
     L.n = n;
     L.table = nullptr;
     L.cached = n <= 32u * RC;
-    uint32_t orv = 0;
+    L.sorted = false;
+    L.top = 0;
+    if (n > RANK_WARP_MAX) {         // table built by k_rank_tables
+        L.table = S.table + slot0;
+        return;
+    }
+    uint32_t* xk = sbuf;
     bool asc = true;
+    uint32_t orv = 0;
     if (L.cached) {
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
@@ -290,25 +375,43 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
             const uint32_t next = lane == 31 ? wrap : right;
             if (q + 1 < n && !(L.ids[k] < next)) asc = false;
         }
+        orv = __reduce_or_sync(FULL, orv);
+        L.top = orv ? 31 - __clz((int)orv) : 0;
+        L.sorted = __all_sync(FULL, asc);
+        // a select sweeps the list once per significant bit, per lookup
+        if (L.sorted || lookups * (uint32_t)(L.top + 1) <= 128u) return;
+#pragma unroll
+        for (int k = 0; k < RC; ++k) {
+            const uint32_t q = (uint32_t)lane + 32u * k;
+            if (q < n) xk[q] = L.ids[k];
+        }
     } else {
         for (uint32_t q = lane; q < n; q += 32) {
             const uint32_t x = base[q];
+            xk[q] = x;
             orv |= x;
-            if (q + 1 < n && !(x < base[q + 1])) asc = false;
         }
+        __syncwarp();
+        for (uint32_t q = lane; q + 1 < n; q += 32)
+            if (!(xk[q] < xk[q + 1])) asc = false;
+        orv = __reduce_or_sync(FULL, orv);
+        L.top = orv ? 31 - __clz((int)orv) : 0;
+        L.sorted = __all_sync(FULL, asc);
+        if (L.sorted) return;
     }
-    orv = __reduce_or_sync(FULL, orv);
-    L.sorted = __all_sync(FULL, asc);
-    L.top = orv ? 31 - __clz((int)orv) : 0;
-    if (!L.cached && !L.sorted && lookups * (uint32_t)(L.top + 1) > 10u * (uint32_t)table_passes(L.top))
-        L.table = rank_table(base, n, L.top, S.ka + slot0, S.va + slot0, S.kb + slot0, S.vb + slot0, cnt, lane);
+    __syncwarp();
+    uint32_t* table = S.table + slot0;
+    radix_table<false>(n, L.top, xk, sbuf + RANK_WARP_MAX, sbuf + 2 * RANK_WARP_MAX, sbuf + 3 * RANK_WARP_MAX, table,
+                       1, sbuf + 4 * RANK_WARP_MAX, nullptr, (uint32_t)lane, lane, 0);
+    L.table = table;                 // ordered for the warp by radix_pass's final __syncwarp
+    L.cached = false;
 }
 
-// position of the rank-th smallest id of the list (same result as select_rank)
+// position of the rank-th smallest id of the list
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
     if (L.sorted) return rank;
     if (L.table) return L.table[rank];
-    if (!L.cached) return select_rank(L.base, L.n, rank, lane, L.top);
+    // register-cached list: bitwise radix select
     uint32_t prefix = 0, want = rank;
     for (int bit = L.top; bit >= 0; --bit) {
         const uint32_t hm = bit == 31 ? 0u : (0xFFFFFFFFu << (bit + 1));
@@ -324,7 +427,7 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
             prefix |= 1u << bit;
         }
     }
-    uint32_t pos = 0xFFFFFFFFu;
+    uint32_t pos = SENTINEL;
 #pragma unroll
     for (int k = 0; k < RC; ++k) {
         const uint32_t q = (uint32_t)lane + 32u * k;
@@ -333,19 +436,22 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
     return __reduce_min_sync(FULL, pos);
 }
 
+// Heavy cells (a list the warp must sort or many candidates) go to the
+// front of `active`, the others to its back, so that k_collide starts them
+// first.
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
-                                               uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
-                                               KParams P) {
+                                               uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+                                               uint32_t* big, DevState* st, KParams P) {
     const uint32_t C = P.ncell;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); c0 < C; c0 += stride) {
         const uint32_t c = c0 + lane;
-        uint32_t n0 = 0, n1 = 0;
+        uint32_t n0 = 0, n1 = 0, Ne = 0, Ncu = 0, Ni = 0;
         if (c < C) {
-            const uint32_t Ne = off[c + 1] - off[c];
-            const uint32_t Ncu = off[C + c + 1] - off[C + c];
-            const uint32_t Ni = off[2 * C + c + 1] - off[2 * C + c];
+            Ne = off[c + 1] - off[c];
+            Ncu = off[C + c + 1] - off[C + c];
+            Ni = off[2 * C + c + 1] - off[2 * C + c];
             if (Ne > 0 && (Ncu > 0 || Ni > 0)) {
                 const RunInfo& RI = P.runs[run_of(P, c)];
                 const uint32_t lc = c - RI.cell_base;
@@ -362,15 +468,28 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
             cand[c] = n0 + n1;
         }
         const bool act = c < C && (n0 + n1) > 0;
-        const unsigned m = __ballot_sync(FULL, act);
-        if (m) {
-            unsigned long long base = 0;
-            if (lane == __ffs(m) - 1) base = atomicAdd(&st->n_active, (unsigned long long)__popc(m));
-            base = __shfl_sync(FULL, base, __ffs(m) - 1);
-            if (act) {
-                unsigned lt;
-                asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
-                active[base + __popc(m & lt)] = c;
+        const uint32_t RL = 32u * RC;
+        const bool heavy = act && (n0 + n1 > 32u || Ne > RL || (n0 > 0 && Ncu > RL) || (n1 > 0 && Ni > RL));
+        unsigned lt;
+        asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+        const unsigned mh = __ballot_sync(FULL, heavy), ml = __ballot_sync(FULL, act && !heavy);
+        uint32_t bh = 0, bl = 0;
+        if (mh && lane == __ffs(mh) - 1) bh = atomicAdd(&st->n_heavy, (uint32_t)__popc(mh));
+        if (ml && lane == __ffs(ml) - 1) bl = atomicAdd(&st->n_light, (uint32_t)__popc(ml));
+        if (mh) bh = __shfl_sync(FULL, bh, __ffs(mh) - 1);
+        if (ml) bl = __shfl_sync(FULL, bl, __ffs(ml) - 1);
+        if (heavy) active[bh + __popc(mh & lt)] = c;
+        else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
+        if (act) {
+            // the lists k_collide will rank that need a block's sort
+            const uint32_t len[3] = {Ne, n0 > 0 ? Ncu : 0u, n1 > 0 ? Ni : 0u};
+            for (uint32_t k = 0; k < 3; ++k) {
+                if (len[k] <= RANK_WARP_MAX) continue;
+                const bool large = len[k] > RANK_MID_MAX;
+                const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
+                if (x < rank_queue_max(P.capacity, large ? RANK_MID_MAX : RANK_WARP_MAX))
+                    (large ? big : mid)[x] = (c << 2) | k;
+                else set_error(st, ERR_BOUNDS);
             }
         }
     }
@@ -514,16 +633,19 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                                                  long long* rho_h, const float* __restrict__ xsE,
                                                  const float* __restrict__ xs, KParams P, CollConsts cc,
                                                  uint32_t nbins) {
-    __shared__ uint32_t s_cnt[4][256];         // per-warp digit counters of the rank-table sort
-    const unsigned long long n_active = st->n_active;
+    __shared__ uint32_t s_sort[4][4 * RANK_WARP_MAX + 256];   // per-warp rank-table sort
     const int lane = threadIdx.x & 31;
-    uint32_t* cnt = s_cnt[(threadIdx.x >> 5) & 3];
-    const unsigned long long warp0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
     const uint32_t C = P.ncell;
+    const uint32_t n_heavy = st->n_heavy, n_light = st->n_light;
     const uint32_t n_alive = off[nbins];
-    for (unsigned long long w = warp0; w < n_active; w += nwarps) {
-        const uint32_t c = active[w];
+    for (;;) {
+        // the next active cell, heavy ones first
+        uint32_t w = 0;
+        if (lane == 0) w = atomicAdd(&st->collide_next, 1u);
+        w = __shfl_sync(FULL, w, 0);
+        if (w >= n_heavy + n_light) break;
+        const uint32_t c = w < n_heavy ? active[w] : active[C - 1u - (w - n_heavy)];
         const uint2 n = nc[c];
         const int r = run_of(P, c);
         const RunInfo* RI = &P.runs[r];
@@ -550,7 +672,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
         IdList el;
-        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, cnt, lane);
+        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, sbuf, lane);
         for (int k = 0; k < 2; ++k) {
             const uint32_t tb = (k == 0 ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
@@ -558,7 +680,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             const uint32_t ncand = k == 0 ? n.x : n.y;
             if (ncand == 0) continue;
             IdList tl;
-            load_ids(tl, A.id, t_base, Nt, ncand, S, cnt, lane);
+            load_ids(tl, A.id, t_base, Nt, ncand, S, sbuf, lane);
             // candidates in batches of 32: lane q draws candidate m0 + q's pair and
             // prefetches its particles; lane 0 then applies them in order,
             // re-reading a candidate whose particles an earlier candidate of
@@ -674,7 +796,11 @@ __global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, con
             ns = P.capacity;
         }
         st->n_slots = ns;
-        st->n_active = 0;
+        st->n_heavy = 0;
+        st->n_light = 0;
+        st->n_mid = 0;
+        st->n_big = 0;
+        st->collide_next = 0;
     }
     // the step is over for every kernel that draws from it
     if (blockIdx.x == 0 && threadIdx.x == 0) st->step += 1u;
@@ -797,15 +923,31 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
     }
 }
 
-void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
-                  const KParams& P, int grid, cudaStream_t s) {
-    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, st, P);
+constexpr size_t RT_SMEM = (size_t)RANK_BLOCK_MAX * 4 * sizeof(uint32_t);
+constexpr size_t RT_MID_SMEM = (size_t)RANK_MID_MAX * 4 * sizeof(uint32_t);
+
+cudaError_t collide_setup() {
+    cudaError_t e = cudaFuncSetAttribute(k_rank_tables<RT_THREADS, RANK_BLOCK_MAX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_rank_tables<RT_MID_THREADS, RANK_MID_MAX>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_MID_SMEM);
+    return e;
+}
+void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+                  uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
+    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, mid, big, st, P);
 }
 void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
-                    const uint32_t* cand_off, const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h,
-                    const float* xsE, const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins,
-                    int grid, cudaStream_t s) {
-    const RankScratch S{B.key, B.id, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr)};
+                    const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
+                    DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
+                    const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s) {
+    const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
+                        reinterpret_cast<uint32_t*>(B.vz), B.id};
+    k_rank_tables<RT_MID_THREADS, RANK_MID_MAX><<<sms * RT_MID_BLOCKS_PER_SM, RT_MID_THREADS, RT_MID_SMEM, s>>>(
+        A.id, S, off, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
+    k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
+        A.id, S, off, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
     k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,

@@ -35,11 +35,13 @@ constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISO
 // Device-resident scalars shared by all runs of a simulation.
 struct DevState {
     unsigned long long n_slots;      // slots of buffer A in use (live + dead)
-    unsigned long long n_active;     // cells with collision candidates this step
+    unsigned int n_heavy;            // cells with collision candidates this step: heavy ones (long
+    unsigned int n_light;            // id lists or many candidates) and the others
     unsigned int error;              // ERR_* bits
     unsigned int load_bad;           // set by a device load that met an out-of-range particle
     unsigned int step;               // electron step index (Philox counter word), advanced by finalize
-    unsigned int pad0;
+    unsigned int n_mid, n_big;       // id lists queued for the two rank-table kernels this step
+    unsigned int collide_next;       // next active cell for k_collide's warps
 };
 
 // Device-resident scalars of one run (an ensemble holds several runs).

@@ -53,14 +53,25 @@ void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, c
                       int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t* key, uint32_t* id,
                       unsigned int* bad, int grid, cudaStream_t s);
 
-// collisions
-void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, DevState* st,
-                  const KParams& P, int grid, cudaStream_t s);
+// collisions.  The rank table of an id list of more than RANK_WARP_MAX ids
+// that the candidates of an active cell use is built before k_collide, by a
+// block of its own: lists up to RANK_MID_MAX ids by the mid-size kernel,
+// longer ones by the large one.  k_ncand queues them in `mid` and `big`;
+// rank_queue_max(cap, len) entries always suffice for lists longer than len
+// (the lists hold disjoint particles).
+constexpr uint32_t RANK_WARP_MAX = 512;
+constexpr uint32_t RANK_MID_MAX = 2048;
+__host__ __device__ inline uint32_t rank_queue_max(uint64_t cap, uint32_t len) { return (uint32_t)(cap / (len + 1) + 4); }
+// shared-memory attribute of the rank-table kernels (once per process and device)
+cudaError_t collide_setup();
+void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+                  uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s);
 // B: the other particle buffer, used as scratch (free until the next scatter)
+// the two rank-table kernels, then k_collide (three launches)
 void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
-                    const uint32_t* cand_off, const uint32_t* active, DevState* st, long long* rho_e, long long* rho_h,
-                    const float* xsE, const float* xs, const KParams& P, const CollConsts& cc, uint32_t nbins,
-                    int grid, cudaStream_t s);
+                    const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
+                    DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
+                    const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s);
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 

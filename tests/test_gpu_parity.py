@@ -64,15 +64,20 @@ def assert_same_counters(gc, oc, keys=None):
         assert gc[k] == oc[k], (k, gc[k], oc[k])
 
 
-@pytest.mark.parametrize("n_e,n_t,ncells,scale", [
-    (6000, 3000, 4, 3.0),          # 1500 e / 750 Cu per cell: rank tables, ~30 candidates per cell
-    (20000, 9000, 1, 0.3),         # one cell of 29000 particles
-    (700, 300, 2, 1.0),            # long electron lists, mostly single lookups: the scan select
+@pytest.mark.parametrize("n_e,n_t,ncells,scale,Te", [
+    (6000, 3000, 4, 3.0, 30.0),    # 1500 e / 750 Cu per cell: tables sorted by a block, ~30 candidates per cell
+    (20000, 9000, 1, 0.3, 30.0),   # one cell of 29000 particles: a block's sort in the scratch buffers
+    (700, 300, 2, 1.0, 30.0),      # 350 e per cell: tables sorted by the cell's warp
+    (2050, 1000, 4, 3.0, 300.0),   # about 512 e per cell (both sides of the warp / block split), many movers
+    (8200, 3000, 4, 1.0, 300.0),   # about 2050 e per cell (both sides of the mid-size / large block split)
+    (24600, 6000, 2, 0.1, 300.0),  # about 12300 e per cell (both sides of the shared-memory limit)
+    (800, 400, 4, 100.0, 300.0),   # 200 e / 100 Cu per cell, many lookups: tables of register-cached lists
 ])
-def test_dense_cells_bit_exact(pd, xs, n_e, n_t, ncells, scale):
+def test_dense_cells_bit_exact(pd, xs, n_e, n_t, ncells, scale, Te):
     """Cells whose id lists exceed the register-cached length: the canonical
-    (ascending id) pair choice must still match the oracle exactly."""
-    cfg, parts = synthetic.rate_cell(n_e=n_e, n_t=n_t, Te_eV=30.0, seed=5, coll_scale=scale, ncells=ncells)
+    (ascending id) pair choice must still match the oracle exactly.  Movers
+    between the cells leave the lists out of id order after the first step."""
+    cfg, parts = synthetic.rate_cell(n_e=n_e, n_t=n_t, Te_eV=Te, seed=5, coll_scale=scale, ncells=ncells)
     cfg.update(nz=2, nr=max(2, ncells))     # the library's grids are at least 2 x 2: a second, empty row
     sim, o = run_pair(pd, cfg, parts, xs, 3)
     gc, oc = sim.counters(), o.counters()
