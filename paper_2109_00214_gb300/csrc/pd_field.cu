@@ -47,6 +47,8 @@ constexpr int RED_BLOCKS = 64;
 constexpr int MAP_CHUNK = 256;         // items of one work-list entry
 constexpr int SP_TI = 16, SP_TJ = 32;  // smoother tile: interior rows x radial nodes
 constexpr int SP_H = 4;                // halo: four half-sweeps per launch
+constexpr int TAIL_NODES = 34 * 34;    // levels from the first one with at most this many nodes: k_mg_tail
+constexpr int TAIL_THREADS = 256;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -64,6 +66,22 @@ void level_dims(int nz, int nr, int* nzs, int* nrs, int& nlev) {
 
 // unknowns of the coarsest level (interior rows, all radial nodes)
 int coarse_unknowns(const int* a, const int* b, int n) { return (a[n - 1] - 1) * (b[n - 1] + 1); }
+
+// first level cycled by k_mg_tail (the coarsest level always qualifies: at
+// most 1024 nodes)
+int tail_level(const int* a, const int* b, int n) {
+    for (int l = 0; l < n; ++l)
+        if ((a[l] + 1) * (b[l] + 1) <= TAIL_NODES) return l;
+    return n - 1;
+}
+
+// k_mg_tail's shared memory for one run: e, f, r per node and ap, am, b,
+// dinv per radial node of each tail level
+size_t tail_floats(const int* a, const int* b, int n) {
+    size_t t = 0;
+    for (int l = tail_level(a, b, n); l < n; ++l) t += 3 * (size_t)(a[l] + 1) * (b[l] + 1) + 4 * (size_t)(b[l] + 1);
+    return t;
+}
 
 int chunks(long long n) { return (int)((n + MAP_CHUNK - 1) / MAP_CHUNK); }
 int tiles_of(int nz, int nr) { return ((nz - 1 + SP_TI - 1) / SP_TI) * ((nr + 1 + SP_TJ - 1) / SP_TJ); }
@@ -109,7 +127,7 @@ size_t field_workspace_bytes(const std::vector<int>& nz, const std::vector<int>&
         t += run_bytes(nz[r], nr[r]);
         tasks += run_tasks(nz[r], nr[r]);
     }
-    t += al(R * MG_MAX_LEVELS * sizeof(MGLevel)) + al(R * sizeof(MGTop)) + al(R * 4) * 2 +
+    t += al(R * MG_MAX_LEVELS * sizeof(MGLevel)) + al(R * sizeof(MGTop)) + al(R * 4) * 3 +
          al(R * RED_BLOCKS * 2 * 8) + al(R * 8) * 2 + al(R * sizeof(float*)) + al(tasks * sizeof(int2) + 8);
     return t;
 }
@@ -360,14 +378,14 @@ __global__ void k_restrict(const MGLevel* lev, const int* done, int l, const int
 }
 
 // correction from level l + 1: its values are in e2 after its post-smoothing,
-// in e on the run's coarsest level (solved directly)
-__global__ void k_prolong(const MGLevel* lev, const int* nlev, const int* done, int l, const int2* tasks) {
+// in e when level l + 1 is the run's first tail level (k_mg_tail)
+__global__ void k_prolong(const MGLevel* lev, const int* tail_lev, const int* done, int l, const int2* tasks) {
     const int2 tk = tasks[blockIdx.x];
     const int run = tk.x;
     if (done[run]) return;
     const MGLevel F = lev[run * MG_MAX_LEVELS + l];
     const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
-    const float* ce = l + 1 < nlev[run] - 1 ? Cl.e2 : Cl.e;
+    const float* ce = l + 1 < tail_lev[run] ? Cl.e2 : Cl.e;
     const int Wc = Cl.nr + 1, Wf = F.nr + 1;
     const int n = min((F.nz - 1) * Wf, tk.y + MAP_CHUNK);
     for (int q = tk.y + threadIdx.x; q < n; q += blockDim.x) {
@@ -379,50 +397,162 @@ __global__ void k_prolong(const MGLevel* lev, const int* nlev, const int* done, 
     }
 }
 
-// coarsest level of each run whose hierarchy ends at level l (blockIdx.x =
-// run): e = A^-1 f with the stored inverse (transposed: column v of A^-1 at
-// inv[v * m]), or Gauss-Seidel sweeps when the run has none.  A run whose
-// only level is level 0 adds the correction to phi here.
-__global__ void __launch_bounds__(256) k_coarse(const MGLevel* lev, const MGTop* top, const int* nlev,
-                                                const int* done, const float* const* inv, int l, int sweeps) {
-    const int run = blockIdx.x;
-    if (done[run] || l != nlev[run] - 1) return;
-    const MGLevel L = lev[run * MG_MAX_LEVELS + l];
+// The levels of one run from its first tail level T down to its coarsest,
+// one V(2,2) cycle by one block in shared memory (blockIdx.x = run): the
+// per-level kernels' operations in their order -- four red-black half-sweeps
+// (colors 0, 1, 0, 1), the residual, the full-weighting restriction, on the
+// coarsest level e = A^-1 f with the stored inverse (transposed: column v at
+// inv[v * m]) or `sweeps` Gauss-Seidel sweeps, then bilinear prolongation
+// and four half-sweeps (colors 1, 0, 1, 0) on the way up.  Input: f of level
+// T (its e is zero).  Output: the correction of level T in its e, or, when T
+// is level 0, added to phi.
+struct TailLevel {
+    float *e, *f, *r, *ap, *am, *b, *d;
+    int nz, nr;
+};
+
+__device__ __forceinline__ void tail_half_sweep(const TailLevel& L, int color) {
     const int W = L.nr + 1;
     const int n = (L.nz - 1) * W;
-    const float* Ai = inv[run];
-    if (Ai) {
-        __shared__ float f[MG_DIRECT_MAX];
-        for (int q = threadIdx.x; q < n; q += blockDim.x) f[q] = L.f[W + q];
-        __syncthreads();
-        for (int u = threadIdx.x; u < n; u += blockDim.x) {
-            float acc = 0.0f;
-#pragma unroll 4
-            for (int v = 0; v < n; ++v) acc += Ai[(size_t)v * n + u] * f[v];
-            L.e[W + u] = acc;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        const int i = 1 + q / W, j = q - (i - 1) * W;
+        if (((i + j) & 1) != color) continue;
+        const int k = i * W + j;
+        float v = L.f[k];
+        if (j < L.nr) v += L.ap[j] * L.e[k + 1];
+        if (j > 0) v += L.am[j] * L.e[k - 1];
+        if (i + 1 < L.nz) v += L.b[j] * L.e[k + W];
+        if (i - 1 > 0) v += L.b[j] * L.e[k - W];
+        L.e[k] = v * L.d[j];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const MGLevel* lev, const MGTop* top, const int* nlev,
+                                                          const int* tail_lev, const int* done,
+                                                          const float* const* inv, int sweeps) {
+    extern __shared__ float sm[];
+    __shared__ TailLevel tl[MG_MAX_LEVELS];
+    const int run = blockIdx.x;
+    if (done[run]) return;
+    const int n = nlev[run], T = tail_lev[run];
+    const MGLevel* Lg = lev + run * MG_MAX_LEVELS;
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int l = T; l < n; ++l) {
+            const int W = Lg[l].nr + 1, nodes = (Lg[l].nz + 1) * W;
+            TailLevel& t = tl[l];
+            t.nz = Lg[l].nz;
+            t.nr = Lg[l].nr;
+            t.e = sm + o;
+            t.f = t.e + nodes;
+            t.r = t.f + nodes;
+            t.ap = t.r + nodes;
+            t.am = t.ap + W;
+            t.b = t.am + W;
+            t.d = t.b + W;
+            o += 3 * nodes + 4 * W;
         }
-    } else {
-        for (int it = 0; it < sweeps; ++it) {
-            for (int color = 0; color < 2; ++color) {
-                for (int q = threadIdx.x; q < n; q += blockDim.x) {
-                    const int i = 1 + q / W, j = q - (i - 1) * W;
-                    if (((i + j) & 1) != color) continue;
-                    const int k = i * W + j;
-                    float s = L.f[k];
-                    if (j < L.nr) s += L.ap[j] * L.e[k + 1];
-                    if (j > 0) s += L.am[j] * L.e[k - 1];
-                    if (i + 1 < L.nz) s += L.b[j] * L.e[k + W];
-                    if (i - 1 > 0) s += L.b[j] * L.e[k - W];
-                    L.e[k] = s * L.dinv[j];
+    }
+    __syncthreads();
+    // inputs: f of level T, zero corrections, the coefficients
+    for (int l = T; l < n; ++l) {
+        const TailLevel t = tl[l];
+        const int W = t.nr + 1, nodes = (t.nz + 1) * W;
+        for (int k = threadIdx.x; k < nodes; k += blockDim.x) {
+            t.e[k] = 0.0f;
+            if (l == T) t.f[k] = Lg[l].f[k];
+        }
+        for (int j = threadIdx.x; j < W; j += blockDim.x) {
+            t.ap[j] = Lg[l].ap[j];
+            t.am[j] = Lg[l].am[j];
+            t.b[j] = Lg[l].b[j];
+            t.d[j] = Lg[l].dinv[j];
+        }
+    }
+    __syncthreads();
+    // down
+    for (int l = T; l + 1 < n; ++l) {
+        const TailLevel F = tl[l], Cl = tl[l + 1];
+        for (int k = 0; k < 4; ++k) tail_half_sweep(F, k & 1);
+        const int Wf = F.nr + 1, Wc = Cl.nr + 1;
+        for (int q = threadIdx.x; q < (F.nz - 1) * Wf; q += blockDim.x) {
+            const int i = 1 + q / Wf, j = q - (i - 1) * Wf;
+            const int k = i * Wf + j;
+            float s = (F.ap[j] + F.am[j] + 2.0f * F.b[j]) * F.e[k];
+            if (j < F.nr) s -= F.ap[j] * F.e[k + 1];
+            if (j > 0) s -= F.am[j] * F.e[k - 1];
+            if (i + 1 < F.nz) s -= F.b[j] * F.e[k + Wf];
+            if (i - 1 > 0) s -= F.b[j] * F.e[k - Wf];
+            F.r[k] = F.f[k] - s;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < (Cl.nz + 1) * Wc; k += blockDim.x) {
+            const int I = k / Wc, J = k - I * Wc;
+            if (I == 0 || I == Cl.nz) {
+                Cl.f[k] = 0.0f;
+                continue;
+            }
+            float s = 0.0f;
+            for (int di = -1; di <= 1; ++di) {
+                const int i = 2 * I + di;
+                if (i <= 0 || i >= F.nz) continue;
+                const float wi = di == 0 ? 1.0f : 0.5f;
+                for (int dj = -1; dj <= 1; ++dj) {
+                    const int j = 2 * J + dj;
+                    if (j < 0 || j > F.nr) continue;
+                    const float wj = dj == 0 ? 1.0f : 0.5f;
+                    s += wi * wj * F.r[i * Wf + j];
                 }
-                __syncthreads();
+            }
+            Cl.f[k] = s;
+        }
+        __syncthreads();
+    }
+    // coarsest
+    {
+        const TailLevel L = tl[n - 1];
+        const int W = L.nr + 1;
+        const int m = (L.nz - 1) * W;
+        const float* Ai = inv[run];
+        if (Ai) {
+            for (int u = threadIdx.x; u < m; u += blockDim.x) {
+                float acc = 0.0f;
+#pragma unroll 4
+                for (int v = 0; v < m; ++v) acc += Ai[(size_t)v * m + u] * L.f[W + v];
+                L.e[W + u] = acc;
+            }
+            __syncthreads();
+        } else {
+            for (int it = 0; it < sweeps; ++it) {
+                tail_half_sweep(L, 0);
+                tail_half_sweep(L, 1);
             }
         }
     }
-    if (l == 0) {
+    // up
+    for (int l = n - 2; l >= T; --l) {
+        const TailLevel F = tl[l], Cl = tl[l + 1];
+        const int Wf = F.nr + 1, Wc = Cl.nr + 1;
+        for (int q = threadIdx.x; q < (F.nz - 1) * Wf; q += blockDim.x) {
+            const int i = 1 + q / Wf, j = q - (i - 1) * Wf;
+            const int I0 = i >> 1, J0 = j >> 1;
+            const int I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
+            const float c = 0.25f * (Cl.e[I0 * Wc + J0] + Cl.e[I1 * Wc + J0] + Cl.e[I0 * Wc + J1] + Cl.e[I1 * Wc + J1]);
+            F.e[i * Wf + j] += c;
+        }
         __syncthreads();
+        for (int k = 0; k < 4; ++k) tail_half_sweep(F, 1 - (k & 1));
+    }
+    // output
+    const TailLevel t = tl[T];
+    const int W = t.nr + 1;
+    if (T == 0) {
         double* phi = top[run].phi;
-        for (int q = threadIdx.x; q < n; q += blockDim.x) phi[W + q] += (double)L.e[W + q];
+        for (int q = threadIdx.x; q < (t.nz - 1) * W; q += blockDim.x) phi[W + q] += (double)t.e[W + q];
+    } else {
+        float* e = Lg[T].e;
+        for (int k = threadIdx.x; k < (t.nz + 1) * W; k += blockDim.x) e[k] = t.e[k];
     }
 }
 
@@ -562,6 +692,9 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
     fs.host_lev.assign((size_t)R * MG_MAX_LEVELS, MGLevel{});
     fs.host_top.assign(R, MGTop{});
     fs.max_levels = 0;
+    fs.max_tail = 0;
+    fs.tail_smem = 0;
+    fs.tail_lev.assign(R, 0);
     fs.max_nodes0 = 0;
     fs.max_cycles = cfgs[0].poisson_max_cycles > 0 ? cfgs[0].poisson_max_cycles : 60;
     std::vector<double> tol(R);
@@ -572,6 +705,9 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
         level_dims(c.nz, c.nr, a, b, n);
         fs.nlev[r] = n;
         fs.max_levels = std::max(fs.max_levels, n);
+        fs.tail_lev[r] = tail_level(a, b, n);
+        fs.max_tail = std::max(fs.max_tail, fs.tail_lev[r]);
+        fs.tail_smem = std::max(fs.tail_smem, tail_floats(a, b, n) * sizeof(float));
         fs.max_nodes0 = std::max(fs.max_nodes0, (c.nz + 1) * (c.nr + 1));
         tol[r] = c.poisson_tol;
         // level 0 in double
@@ -648,12 +784,13 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
     fs.lev = (MGLevel*)take((size_t)R * MG_MAX_LEVELS * sizeof(MGLevel));
     fs.top = (MGTop*)take((size_t)R * sizeof(MGTop));
     fs.nlev_dev = (int*)take((size_t)R * 4);
+    fs.tail_lev_dev = (int*)take((size_t)R * 4);
     fs.done = (int*)take((size_t)R * 4);
     fs.red = (double*)take((size_t)R * RED_BLOCKS * 2 * 8);
     fs.bnorm = (double*)take((size_t)R * 8);
     fs.tol = (double*)take((size_t)R * 8);
     fs.inv = (float**)take((size_t)R * sizeof(float*));
-    // work lists, level by level
+    // work lists, level by level: the levels above each run's tail
     std::vector<int2> tasks;
     for (int l = 0; l < MG_MAX_LEVELS; ++l) {
         auto add = [&](int r, long long cnt, int step) {
@@ -661,32 +798,34 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
         };
         fs.fine_off[l] = (int)tasks.size();
         for (int r = 0; r < R; ++r)
-            if (l + 1 < fs.nlev[r]) {
+            if (l < fs.tail_lev[r]) {
                 const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
                 add(r, (long long)(L.nz - 1) * (L.nr + 1), MAP_CHUNK);
             }
         fs.fine_len[l] = (int)tasks.size() - fs.fine_off[l];
         fs.coarse_off[l] = (int)tasks.size();
         for (int r = 0; r < R; ++r)
-            if (l + 1 < fs.nlev[r]) {
+            if (l < fs.tail_lev[r]) {
                 const MGLevel& C = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l + 1];
                 add(r, (long long)(C.nz + 1) * (C.nr + 1), MAP_CHUNK);
             }
         fs.coarse_len[l] = (int)tasks.size() - fs.coarse_off[l];
         fs.tile_off[l] = (int)tasks.size();
         for (int r = 0; r < R; ++r)
-            if (l + 1 < fs.nlev[r]) {
+            if (l < fs.tail_lev[r]) {
                 const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
                 add(r, tiles_of(L.nz, L.nr), 1);
             }
         fs.tile_len[l] = (int)tasks.size() - fs.tile_off[l];
     }
+    if (fs.tail_smem > 48 * 1024) return 1;          // cannot happen: tail levels hold at most 34 x 34 nodes
     fs.tasks = (int2*)take(tasks.size() * sizeof(int2) + 8);
     if (o > bytes) return 1;
     upload(fs.tasks, tasks, s);
     upload(fs.lev, fs.host_lev, s);
     upload(fs.top, fs.host_top, s);
     upload(fs.nlev_dev, fs.nlev, s);
+    upload(fs.tail_lev_dev, fs.tail_lev, s);
     upload(fs.tol, tol, s);
     upload(fs.inv, inv, s);
     if (!fs.host_done && cudaMallocHost(&fs.host_done, (size_t)R * 4) != cudaSuccess) return 1;
@@ -715,21 +854,23 @@ static int vcycle(FieldSolver& fs, cudaStream_t s) {
     const int R = fs.nruns;
     const int th = fs.threads;
     int nk = 0;
-    // down: smooth, residual, restrict; the coarsest level of each run is solved directly
-    for (int l = 0; l < fs.max_levels; ++l) {
+    // down to each run's tail: smooth, residual, restrict
+    for (int l = 0; l < fs.max_tail; ++l) {
         nk += smooth4(fs, l, 0, false, s);
         if (fs.fine_len[l]) {
             k_residual_tasks<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.fine_off[l]);
             k_restrict<<<fs.coarse_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.coarse_off[l]);
             nk += 2;
         }
-        k_coarse<<<R, 256, 0, s>>>(fs.lev, fs.top, fs.nlev_dev, fs.done, fs.inv, l, 200);
-        ++nk;
     }
+    // the tail levels of every run, one block each
+    k_mg_tail<<<R, TAIL_THREADS, fs.tail_smem, s>>>(fs.lev, fs.top, fs.nlev_dev, fs.tail_lev_dev, fs.done, fs.inv,
+                                                    200);
+    ++nk;
     // up: prolong, smooth; level 0's last smoothing adds the correction to phi
-    for (int l = fs.max_levels - 2; l >= 0; --l) {
+    for (int l = fs.max_tail - 1; l >= 0; --l) {
         if (!fs.fine_len[l]) continue;
-        k_prolong<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.nlev_dev, fs.done, l, fs.tasks + fs.fine_off[l]);
+        k_prolong<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.tail_lev_dev, fs.done, l, fs.tasks + fs.fine_off[l]);
         ++nk;
         nk += smooth4(fs, l, 1, l == 0, s);
     }

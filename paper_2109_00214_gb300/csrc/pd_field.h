@@ -54,6 +54,12 @@ struct FieldSolver {
     int fine_off[MG_MAX_LEVELS] = {}, fine_len[MG_MAX_LEVELS] = {};       // interior nodes of level l
     int coarse_off[MG_MAX_LEVELS] = {}, coarse_len[MG_MAX_LEVELS] = {};   // all nodes of level l + 1
     int tile_off[MG_MAX_LEVELS] = {}, tile_len[MG_MAX_LEVELS] = {};       // smoother tiles of level l
+    // levels from tail_lev[run] down are cycled by one block per run in
+    // shared memory (k_mg_tail); the level lists hold only the levels above
+    std::vector<int> tail_lev;
+    int* tail_lev_dev = nullptr;        // [nruns]
+    int max_tail = 0;                   // largest tail_lev over the runs
+    size_t tail_smem = 0;               // dynamic shared memory of k_mg_tail
     int threads = 256;                  // threads per block of the level kernels (64..1024, a multiple of 32)
     int max_blocks = 1216;              // cap on blocks per run of the once-per-solve node kernels
 };

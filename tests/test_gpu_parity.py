@@ -149,6 +149,8 @@ def test_rz_external_field_with_injection_bit_exact(pd, xs):
     (64, 64),      # coarsest level 8 x 8 cells: solved by its stored inverse
     (96, 96),      # 6 x 6
     (64, 320),     # R = 5 L: coarsest 8 x 40 cells, 287 unknowns: Gauss-Seidel sweeps
+    (32, 32),      # every level in the one-block tail, the correction added to phi there
+    (16, 48),      # two levels, both in the tail
 ])
 def test_rz_poisson_matches_oracle(pd, xs, n, nr):
     """Self-consistent field: multigrid (GPU) vs conjugate gradients (CPU) on
