@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="ensemble: skip the one-simulation-per-run arm")
     p.add_argument("--ens-seeds", type=int, default=8, help="ensemble: seeds (runs = seeds x 8 voltages)")
+    p.add_argument("--ens-warm", default="extrapolate", help="ensemble: Poisson starting point of every arm "
+                   "(previous, extrapolate, cold)")
     p.add_argument("--ws-sizes", default="256,512", help="grid sizes of the warm-start runs")
     p.add_argument("--ws-runs", type=int, default=10, help="runs per grid size (the last one is held out)")
     p.add_argument("--ws-pairs", type=int, default=500, help="pairs per run, one every 2 steps")
@@ -305,6 +307,7 @@ def run_ensemble(args, ws, rank, local):
     if sims is not None:
         for cfg, parts in runs:
             sm = pd.Simulation(cfg, xs, device=dev)
+            sm.set_warm_start(args.ens_warm)
             sm.load_device({k: torch.from_numpy(parts[k]).to(dev) for k in keys})
             sims.append(sm)
         for sm in sims:
@@ -323,6 +326,7 @@ def run_ensemble(args, ws, rank, local):
 
     # ---- batched ensemble ---------------------------------------------------
     ens = pd.Ensemble(cfgs, xs, device=dev)
+    ens.set_warm_start(args.ens_warm)
     for r, (_, parts) in enumerate(runs):
         ens.load_run_device(r, {k: torch.from_numpy(parts[k]).to(dev) for k in keys})
     tuning = None
@@ -370,6 +374,7 @@ def run_ensemble(args, ws, rank, local):
     e2e = None
     if not args.no_e2e:
         ens2 = pd.Ensemble(cfgs, xs, device=dev)
+        ens2.set_warm_start(args.ens_warm)
         if tuning:
             ens2.set_tuning(**tuning)
         ens2.set_graph_mode(1, cycles)
@@ -402,7 +407,8 @@ def run_ensemble(args, ws, rank, local):
                 "config": {"workload": f"batched breakdown ensemble: {len(all_runs)} r-z runs (8 seeds x "
                                        f"{len(synthetic.ENSEMBLE_VOLTS_KV)} gap voltages 2-10 kV), grids "
                                        f"{sorted(grids)} cells per side, 1e5..2e6 particles per run, "
-                                       f"Poisson to relres <= {tol:g}, plume start without cathode emission, dt = 1 fs",
+                                       f"Poisson to relres <= {tol:g} from the {args.ens_warm} start, plume start without cathode "
+                                       f"emission, dt = 1 fs",
                            "runs_per_gpu": R, "grid_histogram": grids, "particles_per_gpu": nparts,
                            "parallelism": f"runs split over {ws} replicas" if ws > 1 else "single",
                            "l2": "particle store larger than L2; no flush"},

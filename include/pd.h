@@ -351,8 +351,12 @@ pd_status pd_warmstart_pairs(pd_sim* sim, int kind, float* x, float* t);
  * V z / L), PD_WARM_LEARNED or PD_WARM_LEARNED_DELTA (phi_0 from `net`,
  * which must stay alive and hold at least the simulation's node count; the
  * delta form falls back to the previous potential on the first solve after
- * create or load).  r-z Poisson mode only.  Drops a captured graph. */
-enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2, PD_WARM_LEARNED_DELTA = 3 };
+ * create or load), PD_WARM_EXTRAPOLATE (linear in time through the two
+ * previous solutions, 2 phi_{n-1} - phi_{n-2}, on the interior rows; the
+ * previous potential until two solves have been made since create or
+ * load).  r-z Poisson mode only.  Drops a captured graph. */
+enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2, PD_WARM_LEARNED_DELTA = 3,
+       PD_WARM_EXTRAPOLATE = 4 };
 pd_status pd_set_warm_start(pd_sim* sim, int mode, pd_net* net);
 
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle

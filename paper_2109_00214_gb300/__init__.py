@@ -426,7 +426,7 @@ def pd_get_rho_phi(h, nodes):
 
 
 PD_NET_NPARAMS = 37601
-WARM_MODES = {"previous": 0, "cold": 1, "learned": 2, "learned_delta": 3}
+WARM_MODES = {"previous": 0, "cold": 1, "learned": 2, "learned_delta": 3, "extrapolate": 4}
 PAIR_KINDS = {"absolute": 0, "delta": 1}
 
 

@@ -474,9 +474,11 @@ void apply_tuning(pd_sim* s, const pd_tuning& t) {
 size_t total_nodes(const pd_sim* s) { return (size_t)s->L.nodes; }
 
 // before each Poisson solve: the solve history, then the starting point
-// (PD_WARM_PREVIOUS: phi as it is)
+// (PD_WARM_PREVIOUS: phi as it is; PD_WARM_EXTRAPOLATE: set with the history
+// shift once two solutions exist)
 pd_status warm_start(pd_sim* s, int* kernels) {
-    warm_history(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rs, s->phi, s->whist, s->stream);
+    const bool extrapolate = s->warm_mode == PD_WARM_EXTRAPOLATE && s->solves >= 2;
+    warm_history(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rs, s->phi, s->whist, extrapolate, s->stream);
     *kernels += 1;
     const bool delta = s->warm_mode == PD_WARM_LEARNED_DELTA;
     if (s->warm_mode == PD_WARM_COLD) {
@@ -1368,7 +1370,8 @@ pd_status pd_warmstart_pairs(pd_sim* s, int kind, float* x, float* t) {
 
 pd_status pd_set_warm_start(pd_sim* s, int mode, pd_net* net) {
     if (!s) return PD_ERR_ARG;
-    if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED && mode != PD_WARM_LEARNED_DELTA)
+    if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED && mode != PD_WARM_LEARNED_DELTA &&
+        mode != PD_WARM_EXTRAPOLATE)
         return fail(s, PD_ERR_ARG, "bad warm-start mode");
     if (mode != PD_WARM_PREVIOUS && s->cfgs[0].field_mode != PD_FIELD_POISSON)
         return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");

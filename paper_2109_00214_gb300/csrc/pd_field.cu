@@ -102,7 +102,7 @@ size_t run_bytes(int nz, int nr) {
     int a[MG_MAX_LEVELS], b[MG_MAX_LEVELS], n;
     level_dims(nz, nr, a, b, n);
     const size_t W0 = (size_t)nr + 1, nodes0 = ((size_t)nz + 1) * W0;
-    size_t t = al(nodes0 * 8) + 5 * al(W0 * 8);            // b, and ap, am, b, cr, iv of level 0 in double
+    size_t t = al(nodes0 * 8) + 6 * al(W0 * 8);            // b, and ap, am, b, dg, cr, iv of level 0 in double
     for (int l = 0; l < n; ++l) {
         const size_t W = (size_t)b[l] + 1, nodes = ((size_t)a[l] + 1) * W;
         t += 4 * al(nodes * 4) + 4 * al(W * 4);             // e, e2, f, r; ap, am, b, dinv in float
@@ -157,18 +157,6 @@ __global__ void k_rhs(const long long* rho_e, const long long* rho_h, const MGTo
     }
 }
 
-// (A x)_ij on an interior node, double
-__device__ __forceinline__ double apply_A(const MGTop& T, const double* x, int i, int j) {
-    const int W = T.nr + 1;
-    const int k = i * W + j;
-    double s = (T.ap[j] + T.am[j] + 2.0 * T.b[j]) * x[k];
-    if (j < T.nr) s -= T.ap[j] * x[k + 1];
-    if (j > 0) s -= T.am[j] * x[k - 1];
-    if (i + 1 < T.nz) s -= T.b[j] * x[k + W];
-    if (i - 1 > 0) s -= T.b[j] * x[k - W];
-    return s;
-}
-
 // (A x)_ij on an interior node of a correction level, float
 __device__ __forceinline__ float apply_Af(const MGLevel& L, const float* x, int i, int j) {
     const int W = L.nr + 1;
@@ -182,26 +170,37 @@ __device__ __forceinline__ float apply_Af(const MGLevel& L, const float* x, int 
 }
 
 // The residual r = b - A phi of every run in double, per-block partial sums
-// of r^2 and b^2 for its norm, and the start of the next correction: level
-// 0's right-hand side f = r (float) and e = 0.  blockIdx.y = run; a fixed
-// launch shape, so the summation order (and the cycle count) never depends
-// on tuning.
-__global__ void k_residual_norms(const MGTop* top, const MGLevel* lev, const int* nlev, double* red) {
+// of r^2 (and, with with_b, of b^2) for its norm, and the start of the next
+// correction: level 0's right-hand side f = r (float) and e = 0.
+// blockIdx.y = run; block x takes the interior rows x, x + RED_BLOCKS, ...
+// with the threads along the row.  A fixed launch shape, so the summation
+// order (and the cycle count) never depends on tuning.
+__global__ void __launch_bounds__(256) k_residual_norms(const MGTop* top, const MGLevel* lev, const int* nlev,
+                                                        double* red, int with_b) {
     const int run = blockIdx.y;
     double acc = 0.0, accb = 0.0;
     if (nlev[run] > 0) {
         const MGTop T = top[run];
         const MGLevel L = lev[run * MG_MAX_LEVELS];
         const int W = T.nr + 1;
-        const int n = (T.nz - 1) * W;
-        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-            const int i = 1 + q / W, j = q - (i - 1) * W;
-            const int k = i * W + j;
-            const double r = T.bf[k] - apply_A(T, T.phi, i, j);
-            L.f[k] = (float)r;
-            L.e[k] = 0.0f;
-            acc += r * r;
-            accb += T.bf[k] * T.bf[k];
+        const double* x = T.phi;
+        for (int i = 1 + blockIdx.x; i < T.nz; i += RED_BLOCKS) {
+            for (int j = threadIdx.x; j < W; j += blockDim.x) {
+                const int k = i * W + j;
+                const double xp = j < T.nr ? x[k + 1] : 0.0;
+                const double xm = j > 0 ? x[k - 1] : 0.0;
+                const double xu = i + 1 < T.nz ? x[k + W] : 0.0;     // the anode row is in b
+                const double xd = i - 1 > 0 ? x[k - W] : 0.0;
+                const double bk = T.bf[k];
+                double r = bk - T.dg[j] * x[k];
+                r += T.ap[j] * xp;
+                r += T.am[j] * xm;
+                r += T.b[j] * (xu + xd);
+                L.f[k] = (float)r;
+                L.e[k] = 0.0f;
+                acc += r * r;
+                if (with_b) accb += bk * bk;
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -222,24 +221,33 @@ __global__ void k_residual_norms(const MGTop* top, const MGLevel* lev, const int
             tb += sb[q];
         }
         red[(run * RED_BLOCKS + blockIdx.x) * 2] = t;
-        red[(run * RED_BLOCKS + blockIdx.x) * 2 + 1] = tb;
+        if (with_b) red[(run * RED_BLOCKS + blockIdx.x) * 2 + 1] = tb;
     }
 }
 
-// per run: relres = |r| / |b|, converged flag, bookkeeping
+// per run (one warp each): relres = |r| / |b| (|b| from the first call of
+// the solve), converged flag, bookkeeping
 __global__ void k_norms(const double* red, double* bnorm, int* done, const double* tol, RunState* rs, int nruns,
                         int cycle, int first) {
-    const int run = blockIdx.x * blockDim.x + threadIdx.x;
+    const int run = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (run >= nruns) return;
     double a = 0, b = 0;
-    for (int q = 0; q < RED_BLOCKS; ++q) {
+    for (int q = lane; q < RED_BLOCKS; q += 32) {
         a += red[(run * RED_BLOCKS + q) * 2];
-        b += red[(run * RED_BLOCKS + q) * 2 + 1];
+        if (first) b += red[(run * RED_BLOCKS + q) * 2 + 1];
     }
-    const double rn = sqrt(a), bn = sqrt(b);
-    if (first) done[run] = 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    if (lane != 0) return;
+    const double rn = sqrt(a);
+    if (first) {
+        done[run] = 0;
+        bnorm[run] = sqrt(b);
+    }
     if (done[run]) return;
-    bnorm[run] = bn;
+    const double bn = bnorm[run];
     const double rel = bn > 0 ? rn / bn : 0.0;
     rs[run].relres = rel;
     rs[run].cycles = (double)cycle;
@@ -720,6 +728,7 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
         T.ap = (double*)take(W0 * 8);
         T.am = (double*)take(W0 * 8);
         T.b = (double*)take(W0 * 8);
+        T.dg = (double*)take(W0 * 8);
         T.cr = (double*)take(W0 * 8);
         T.iv = (double*)take(W0 * 8);
         T.idz = 1.0 / c.dz;
@@ -741,6 +750,9 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
         upload(T.ap, ap, s);
         upload(T.am, am, s);
         upload(T.b, bb, s);
+        std::vector<double> dg(W0);
+        for (size_t j = 0; j < W0; ++j) dg[j] = ap[j] + am[j] + 2.0 * bb[j];
+        upload(T.dg, dg, s);
         upload(T.cr, cr, s);
         upload(T.iv, iv, s);
         cudaStreamSynchronize(s);          // the host vectors above go out of scope
@@ -880,8 +892,8 @@ static int vcycle(FieldSolver& fs, cudaStream_t s) {
 static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStream_t s) {
     const int R = fs.nruns;
     const dim3 g(RED_BLOCKS, R);
-    k_residual_norms<<<g, 256, 0, s>>>(fs.top, fs.lev, fs.nlev_dev, fs.red);
-    k_norms<<<(R + 127) / 128, 128, 0, s>>>(fs.red, fs.bnorm, fs.done, fs.tol, rs, R, cycle, first);
+    k_residual_norms<<<g, 256, 0, s>>>(fs.top, fs.lev, fs.nlev_dev, fs.red, first);
+    k_norms<<<(R + 3) / 4, 128, 0, s>>>(fs.red, fs.bnorm, fs.done, fs.tol, rs, R, cycle, first);
 }
 
 int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
@@ -937,7 +949,7 @@ __device__ __forceinline__ double node_rho(const long long* rho_e, const long lo
 // history shift at the start of a solve: rho_prev := rho_last, phi_prev :=
 // phi, V_prev := V_last; then rho_last := current density, V_last := V
 __global__ void k_warm_history(const long long* rho_e, const long long* rho_h, const MGTop* top,
-                               const RunInfo* runs, const RunState* rs, WarmHistory h) {
+                               const RunInfo* runs, const RunState* rs, WarmHistory h, int extrapolate) {
     const int run = blockIdx.y;
     const MGTop T = top[run];
     const RunInfo& RI = runs[run];
@@ -947,7 +959,9 @@ __global__ void k_warm_history(const long long* rho_e, const long long* rho_h, c
         const int i = k / W, j = k - i * W;
         const uint32_t g = RI.node_base + (uint32_t)k;
         h.rho_prev[g] = h.rho_last[g];
-        h.phi_prev[g] = T.phi[k];
+        const double p = T.phi[k];
+        if (extrapolate && i > 0 && i < T.nz) T.phi[k] = 2.0 * p - h.phi_prev[g];
+        h.phi_prev[g] = p;
         h.rho_last[g] = node_rho(rho_e, rho_h, T, qw, i, j, g);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1026,10 +1040,10 @@ __global__ void k_warm_targets(const double* phi, const MGTop* top, const RunInf
 }
 
 void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
-                  const RunState* rs, const double* phi, const WarmHistory& h, cudaStream_t s) {
+                  const RunState* rs, double* phi, const WarmHistory& h, bool extrapolate, cudaStream_t s) {
     (void)phi;
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    k_warm_history<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.top, runs, rs, h);
+    k_warm_history<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.top, runs, rs, h, extrapolate ? 1 : 0);
 }
 
 void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,

@@ -26,6 +26,7 @@ struct MGTop {
     double* phi;             // the run's potential (the simulation's phi at the run's node base)
     double* bf;              // right-hand side b of the discrete Eq. (8) (nodes)
     double *ap, *am, *b;     // coefficients per radial node
+    double* dg;              // diagonal ap + am + 2 b per radial node
     double* cr;              // b = (rho_e + rho_h) cr[j] on interior rows (plus the anode row's b V)
     double* iv;              // 1 / Verboncoeur volume of an interior node at j
     double idz, i2dz, i2dr;  // 1 / dz, 1 / (2 dz), 1 / (2 dr)
@@ -96,9 +97,11 @@ struct WarmHistory {
     double* V_prev;     // [runs] of the one before
 };
 // at the start of every solve: shift the history and record the current
-// density (Verboncoeur volumes, halved on the electrode rows) and voltage
+// density (Verboncoeur volumes, halved on the electrode rows) and voltage;
+// with `extrapolate`, phi := 2 phi - phi_prev on the interior rows (phi_prev
+// taken before the shift)
 void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
-                  const RunState* rs, const double* phi, const WarmHistory& h, cudaStream_t s);
+                  const RunState* rs, double* phi, const WarmHistory& h, bool extrapolate, cudaStream_t s);
 // d = rho_last (- rho_prev when delta); rmax[run] = max |d|; x = d / rmax
 void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,
                  cudaStream_t s);
