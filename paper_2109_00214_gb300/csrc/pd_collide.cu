@@ -164,11 +164,71 @@ constexpr uint32_t SENTINEL = 0xFFFFFFFFu;
 struct IdList {
     uint32_t ids[RC];
     const uint32_t* table;           // rank -> position, or null
+    const uint32_t* base;            // the ids in global memory (select8)
+    uint32_t* cnt;                   // the warp's 256 shared counters (select8)
     uint32_t n;
     int top;                         // highest set bit of any id (0 if none)
     bool cached;
     bool sorted;                     // ids ascend with the position: rank = position
+    bool sel8;                       // a long list with few lookups: select8 per lookup
 };
+
+// lookups up to which a list longer than 32 * RC ids is searched per lookup
+// (select8) instead of being sorted into a rank table
+constexpr uint32_t SELECT_LOOKUPS = 4;
+
+// Position of the rank-th smallest of the n (unique) ids at ids[0, n) by
+// one warp: four passes over 8-bit digits from the top, each counting, in
+// the warp's 256 shared counters, the ids that share the digits found so
+// far; SENTINEL if rank >= n.
+__device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, uint32_t* cnt, int lane) {
+    uint32_t prefix = 0, want = rank;
+    for (int sh = 24; sh >= 0; sh -= 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
+        __syncwarp();
+        const uint32_t hm = sh == 24 ? 0u : (0xFFFFFFFFu << (sh + 8));
+        for (uint32_t q = lane; q < n; q += 32) {
+            const uint32_t x = ids[q];
+            if ((x & hm) == prefix) atomicAdd(&cnt[(x >> sh) & 255u], 1u);
+        }
+        __syncwarp();
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = cnt[lane * 8 + k];
+            sum += c[k];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t before = x - sum;
+        const bool mine = want >= before && want < x;
+        uint32_t d = 0, rest = 0, run = before;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (mine && want >= run && want < run + c[k]) {
+                d = (uint32_t)(lane * 8 + k);
+                rest = want - run;
+            }
+            run += c[k];
+        }
+        const unsigned b = __ballot_sync(FULL, mine);
+        __syncwarp();
+        if (!b) return SENTINEL;
+        const int src = __ffs(b) - 1;
+        d = __shfl_sync(FULL, d, src);
+        want = __shfl_sync(FULL, rest, src);
+        prefix |= d << sh;
+    }
+    uint32_t pos = SENTINEL;
+    for (uint32_t q = lane; q < n; q += 32)
+        if (ids[q] == prefix) pos = q;
+    return __reduce_min_sync(FULL, pos);
+}
 
 // Scratch of the rank tables, arrays indexed by slot: two (key, value) pair
 // buffers and the tables.  They are the sort's other buffer, unused between
@@ -349,9 +409,16 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
     const uint32_t* base = ids + slot0;
     L.n = n;
     L.table = nullptr;
+    L.base = base;
+    L.cnt = sbuf + 4 * RANK_WARP_MAX;
     L.cached = n <= 32u * RC;
     L.sorted = false;
+    L.sel8 = false;
     L.top = 0;
+    if (!L.cached && lookups <= SELECT_LOOKUPS) {
+        L.sel8 = true;
+        return;
+    }
     if (n > RANK_WARP_MAX) {         // table built by k_rank_tables
         L.table = S.table + slot0;
         return;
@@ -411,6 +478,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
     if (L.sorted) return rank;
     if (L.table) return L.table[rank];
+    if (L.sel8) return select8(L.base, L.n, rank, L.cnt, lane);
     // register-cached list: bitwise radix select
     uint32_t prefix = 0, want = rank;
     for (int bit = L.top; bit >= 0; --bit) {
@@ -481,10 +549,12 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         if (heavy) active[bh + __popc(mh & lt)] = c;
         else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
         if (act) {
-            // the lists k_collide will rank that need a block's sort
+            // the lists k_collide will rank that need a block's sort (long,
+            // with more lookups than select8 serves)
             const uint32_t len[3] = {Ne, n0 > 0 ? Ncu : 0u, n1 > 0 ? Ni : 0u};
+            const uint32_t look[3] = {n0 + n1, n0, n1};
             for (uint32_t k = 0; k < 3; ++k) {
-                if (len[k] <= RANK_WARP_MAX) continue;
+                if (len[k] <= RANK_WARP_MAX || look[k] <= SELECT_LOOKUPS) continue;
                 const bool large = len[k] > RANK_MID_MAX;
                 const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
                 if (x < rank_queue_max(P.capacity, large ? RANK_MID_MAX : RANK_WARP_MAX))
@@ -639,13 +709,26 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
     const uint32_t C = P.ncell;
     const uint32_t n_heavy = st->n_heavy, n_light = st->n_light;
     const uint32_t n_alive = off[nbins];
+    // heavy cells first, taken one at a time from a shared cursor by the
+    // first min(n_heavy, warps) warps; then the light cells, warp-strided
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    bool heavy_phase = warp0 < n_heavy;
+    uint32_t wl = warp0;
     for (;;) {
-        // the next active cell, heavy ones first
-        uint32_t w = 0;
-        if (lane == 0) w = atomicAdd(&st->collide_next, 1u);
-        w = __shfl_sync(FULL, w, 0);
-        if (w >= n_heavy + n_light) break;
-        const uint32_t c = w < n_heavy ? active[w] : active[C - 1u - (w - n_heavy)];
+        uint32_t c = 0;
+        if (heavy_phase) {
+            uint32_t w = 0;
+            if (lane == 0) w = atomicAdd(&st->collide_next, 1u);
+            w = __shfl_sync(FULL, w, 0);
+            if (w < n_heavy) c = active[w];
+            else heavy_phase = false;
+        }
+        if (!heavy_phase) {
+            if (wl >= n_light) break;
+            c = active[C - 1u - wl];
+            wl += nwarps;
+        }
         const uint2 n = nc[c];
         const int r = run_of(P, c);
         const RunInfo* RI = &P.runs[r];

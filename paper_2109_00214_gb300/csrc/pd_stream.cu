@@ -81,7 +81,7 @@ __device__ __forceinline__ float spc(const float (&a)[NSP], int sp) {
 }
 
 template <bool RZ, bool FIELD, bool MULTI>
-__global__ void __launch_bounds__(256, 4) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
+__global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
                                                uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
                                                DevState* st, KParams P) {
