@@ -174,23 +174,50 @@ struct IdList {
 };
 
 // lookups up to which a list longer than 32 * RC ids is searched per lookup
-// (select8) instead of being sorted into a rank table
+// (select8) instead of being sorted into a rank table: a select costs a few
+// sweeps of the list by one warp, a table a few sweeps by a whole block
 constexpr uint32_t SELECT_LOOKUPS = 4;
 
+// The lanes of the warp whose 8-bit digit d equals this lane's (v: the
+// lane holds a digit at all; lanes without one group with none), from nine
+// ballots (a warp multisplit).
+__device__ __forceinline__ unsigned digit_peers(uint32_t d, bool v) {
+    unsigned peers = __ballot_sync(FULL, v);
+    peers = v ? peers : ~peers;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bb = __ballot_sync(FULL, bit);
+        peers &= bit ? bb : ~bb;
+    }
+    return peers;
+}
+
 // Position of the rank-th smallest of the n (unique) ids at ids[0, n) by
-// one warp: four passes over 8-bit digits from the top, each counting, in
-// the warp's 256 shared counters, the ids that share the digits found so
-// far; SENTINEL if rank >= n.
-__device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, uint32_t* cnt, int lane) {
+// one warp: passes over 8-bit digits from the one holding bit `top` (every id
+// is below 2^(top + 1)) down, each counting, in the warp's 256 shared
+// counters, the ids that share the digits found so far; SENTINEL if
+// rank >= n.  Each lane keeps eight loads in flight.
+__device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, int top, uint32_t* cnt,
+                            int lane) {
     uint32_t prefix = 0, want = rank;
-    for (int sh = 24; sh >= 0; sh -= 8) {
+    for (int sh = (top / 8) * 8; sh >= 0; sh -= 8) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
         __syncwarp();
-        const uint32_t hm = sh == 24 ? 0u : (0xFFFFFFFFu << (sh + 8));
-        for (uint32_t q = lane; q < n; q += 32) {
-            const uint32_t x = ids[q];
-            if ((x & hm) == prefix) atomicAdd(&cnt[(x >> sh) & 255u], 1u);
+        const uint32_t hm = sh >= 24 ? 0u : (0xFFFFFFFFu << (sh + 8));
+        for (uint32_t q0 = 0; q0 < n; q0 += 256) {
+            uint32_t x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+                x[u] = q < n ? ids[q] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+                if (q < n && (x[u] & hm) == prefix) atomicAdd(&cnt[(x[u] >> sh) & 255u], 1u);
+            }
         }
         __syncwarp();
         uint32_t c[8], sum = 0;
@@ -199,14 +226,14 @@ __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32
             c[k] = cnt[lane * 8 + k];
             sum += c[k];
         }
-        uint32_t x = sum;
+        uint32_t xs = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += y;
+            const uint32_t y = __shfl_up_sync(FULL, xs, o);
+            if (lane >= o) xs += y;
         }
-        const uint32_t before = x - sum;
-        const bool mine = want >= before && want < x;
+        const uint32_t before = xs - sum;
+        const bool mine = want >= before && want < xs;
         uint32_t d = 0, rest = 0, run = before;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -225,8 +252,19 @@ __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32
         prefix |= d << sh;
     }
     uint32_t pos = SENTINEL;
-    for (uint32_t q = lane; q < n; q += 32)
-        if (ids[q] == prefix) pos = q;
+    for (uint32_t q0 = 0; q0 < n; q0 += 256) {
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+            x[u] = q < n ? ids[q] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+            if (q < n && x[u] == prefix && q < pos) pos = q;
+        }
+    }
     return __reduce_min_sync(FULL, pos);
 }
 
@@ -244,7 +282,7 @@ struct RankScratch {
 // pairs.  Keys come from sk, values from sv (null: the position itself);
 // the pairs go to (dk, dv) ordered by the digit (key >> sh) & 255, pairs of
 // equal digits keeping their order (dk null: values only).  Per 32 pairs,
-// __match_any_sync groups equal digits; a group's members take consecutive
+// digit_peers groups equal digits; a group's members take consecutive
 // places after the digit's running offset in lane order and the group's
 // highest lane advances it.  cnt: 256 counters per warp; tot: 256 (BLOCK).
 template <bool BLOCK>
@@ -259,7 +297,7 @@ __device__ void radix_pass(const uint32_t* sk, const uint32_t* sv, uint32_t* dk,
     for (uint32_t g = q0; g < q1; g += 32) {
         const uint32_t q = g + lane;
         const uint32_t d = q < q1 ? (sk[q] >> sh) & 255u : 256u;
-        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned peers = digit_peers(d, q < q1);
         if (q < q1 && lane == 31 - __clz((int)peers)) c[d] += (uint32_t)__popc(peers);
         __syncwarp();
     }
@@ -313,7 +351,7 @@ __device__ void radix_pass(const uint32_t* sk, const uint32_t* sv, uint32_t* dk,
         const bool in = q < q1;
         const uint32_t key = in ? sk[q] : 0u, val = in ? (sv ? sv[q] : q) : 0u;
         const uint32_t d = in ? (key >> sh) & 255u : 256u;
-        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned peers = digit_peers(d, in);
         const uint32_t b = in ? c[d] : 0u;
         __syncwarp();
         if (in) {
@@ -405,7 +443,8 @@ __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__
 // selections will follow.  sbuf: the warp's four arrays of RANK_WARP_MAX and
 // its 256 counters.
 __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
-                                         uint32_t lookups, const RankScratch& S, uint32_t* sbuf, int lane) {
+                                         uint32_t lookups, const RankScratch& S, uint32_t* sbuf, int lane,
+                                         int id_top) {
     const uint32_t* base = ids + slot0;
     L.n = n;
     L.table = nullptr;
@@ -417,6 +456,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
     L.top = 0;
     if (!L.cached && lookups <= SELECT_LOOKUPS) {
         L.sel8 = true;
+        L.top = id_top;
         return;
     }
     if (n > RANK_WARP_MAX) {         // table built by k_rank_tables
@@ -478,7 +518,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
     if (L.sorted) return rank;
     if (L.table) return L.table[rank];
-    if (L.sel8) return select8(L.base, L.n, rank, L.cnt, lane);
+    if (L.sel8) return select8(L.base, L.n, rank, L.top, L.cnt, lane);
     // register-cached list: bitwise radix select
     uint32_t prefix = 0, want = rank;
     for (int bit = L.top; bit >= 0; --bit) {
@@ -623,12 +663,15 @@ __device__ __forceinline__ PairEval evaluate_pair(int k, const V3& ve, const V3&
 
 // (tkey, ve, vt: the target's key and both velocities as they are now; ev:
 // evaluate_pair of ve, vt)
+// (accepted: the candidate is known to pass the target and acceptance
+// tests, already counted by the caller)
 __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
                                   uint32_t tkey, V3 ve, V3 vt, const PairEval& ev, float Racc, float Rch,
                                   const float* __restrict__ xsE, const float* __restrict__ xs,
-                                  const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h) {
+                                  const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h,
+                                  bool accepted) {
     const int ts = k == 0 ? SP_CU : SP_CUP;
-    if ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts) {   // target already ionized this step
+    if (!accepted && ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts)) {   // target already ionized this step
         ++cx.consumed;
         return;
     }
@@ -637,10 +680,12 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     const float* cum = ev.cum;
     const float sT = cum[nch - 1];
     const float sg = ev.sg;
-    if (sg > cc.sgmax[k]) ++cx.viol;
-    if (!(Racc * cc.sgmax[k] < sg)) {
-        ++cx.nulls;
-        return;
+    if (!accepted) {
+        if (sg > cc.sgmax[k]) ++cx.viol;
+        if (!(Racc * cc.sgmax[k] < sg)) {
+            ++cx.nulls;
+            return;
+        }
     }
     const float r = Rch * sT;
     int q = -1;
@@ -741,6 +786,9 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         cx.slot0 = (unsigned long long)n_alive + 2ull * cand_off[c];
         // ids: the run's next id plus twice the candidates of the run's earlier cells
         cx.id0 = P.rs[r].id_next + 2u * (cand_off[c] - cand_off[RI->cell_base]);
+        // every id in the cell's lists is below the run's next id
+        const uint32_t idn = P.rs[r].id_next;
+        const int id_top = idn > 1u ? 31 - __clz((int)(idn - 1u)) : 0;
         cx.s = 0;
         for (int q = 0; q < NCH; ++q) cx.ev[q] = 0;
         cx.nulls = cx.consumed = cx.thr = cx.viol = cx.fb = 0;
@@ -755,7 +803,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
         IdList el;
-        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, sbuf, lane);
+        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, sbuf, lane, id_top);
         for (int k = 0; k < 2; ++k) {
             const uint32_t tb = (k == 0 ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
@@ -763,7 +811,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             const uint32_t ncand = k == 0 ? n.x : n.y;
             if (ncand == 0) continue;
             IdList tl;
-            load_ids(tl, A.id, t_base, Nt, ncand, S, sbuf, lane);
+            load_ids(tl, A.id, t_base, Nt, ncand, S, sbuf, lane, id_top);
             // candidates in batches of 32: lane q draws candidate m0 + q's pair and
             // prefetches its particles; lane 0 then applies them in order,
             // re-reading a candidate whose particles an earlier candidate of
@@ -820,8 +868,27 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                     const uint32_t e2 = __shfl_sync(FULL, ie, (int)q), t2 = __shfl_sync(FULL, it, (int)q);
                     if (q < (uint32_t)lane && (e2 == ie || t2 == it)) dirty = true;
                 }
-                for (uint32_t q = 0; q < nb; ++q) {
-                    const bool okq = __shfl_sync(FULL, ok, (int)q);
+                // a candidate no earlier one of the batch touches sees the
+                // particles as prefetched: its lane takes the target and
+                // acceptance tests (the same float operations lane 0 would),
+                // and only accepted or touched candidates go through lane 0,
+                // in candidate order
+                const int ts = k == 0 ? SP_CU : SP_CUP;
+                const bool cons = (tkey & KEY_FLAG) || (int)key_species(tkey) != ts;
+                const bool acc = !cons && Racc * cc.sgmax[k] < ev.sg;
+                const bool clean = ok && !dirty;
+                const unsigned m_cons = __ballot_sync(FULL, clean && cons);
+                const unsigned m_viol = __ballot_sync(FULL, clean && !cons && ev.sg > cc.sgmax[k]);
+                const unsigned m_null = __ballot_sync(FULL, clean && !cons && !acc);
+                if (lane == 0) {
+                    cx.consumed += (uint32_t)__popc(m_cons);
+                    cx.viol += (uint32_t)__popc(m_viol);
+                    cx.nulls += (uint32_t)__popc(m_null);
+                }
+                const unsigned todo = __ballot_sync(FULL, ok && (dirty || acc));
+                for (unsigned mq = todo; mq; mq &= mq - 1u) {
+                    const uint32_t q = (uint32_t)(__ffs(mq) - 1);
+                    const bool okq = true;
                     const bool dq = __shfl_sync(FULL, dirty, (int)q);
                     const uint32_t ieq = __shfl_sync(FULL, ie, (int)q), itq = __shfl_sync(FULL, it, (int)q);
                     uint32_t tkq = __shfl_sync(FULL, tkey, (int)q);
@@ -846,7 +913,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                         rs.ctr.w = 1u;
                         rs.used = 4;
                         process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, evq, Ra, Rc, xsE, xs, cc, st,
-                                          rho_e, rho_h);
+                                          rho_e, rho_h, !dq);
                     }
                 }
                 __syncwarp();

@@ -72,8 +72,8 @@ def assert_same_counters(gc, oc, keys=None):
     (8200, 3000, 4, 1.0, 300.0),   # about 2050 e per cell (both sides of the mid-size / large block split)
     (24600, 6000, 2, 0.1, 300.0),  # about 12300 e per cell (both sides of the shared-memory limit)
     (800, 400, 4, 100.0, 300.0),   # 200 e / 100 Cu per cell, many lookups: tables of register-cached lists
-    (6000, 3000, 4, 0.2, 300.0),   # 1500 e / 750 Cu per cell, a few candidates: digit-by-digit selects
-    (20000, 9000, 1, 0.02, 30.0),  # 29000 particles in one cell, a few candidates
+    (6000, 3000, 4, 0.1, 300.0),   # 1500 e / 750 Cu per cell, about one candidate: digit-by-digit selects
+    (20000, 9000, 1, 0.0006, 30.0),  # 29000 particles in one cell, about one candidate
 ])
 def test_dense_cells_bit_exact(pd, xs, n_e, n_t, ncells, scale, Te):
     """Cells whose id lists exceed the register-cached length: the canonical
