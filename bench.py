@@ -490,7 +490,7 @@ def run_warmstart(args, ws, rank, local):
         train_info[k] = {"loss_history": hist, "train_ms": ms, "ms_per_iter": ms / max(args.ws_iters, 1),
                          "held_out": tl}
         nets["learned" if k == "absolute" else "learned_delta"] = net
-    modes = ("previous", "cold", "learned", "learned_delta")
+    modes = ("previous", "extrapolate", "cold", "learned", "learned_delta")
     results = {str(n): W.compare_starts(*evals[n], xs, nets, args.ws_eval_steps, modes=modes, device=dev)
                for n in sizes}
     # inference time on the largest grid
