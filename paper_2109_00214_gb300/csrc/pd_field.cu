@@ -92,8 +92,7 @@ size_t run_tasks(int nz, int nr) {
     level_dims(nz, nr, a, b, n);
     size_t t = 0;
     for (int l = 0; l + 1 < n; ++l)
-        t += chunks((long long)(a[l] - 1) * (b[l] + 1)) + chunks((long long)(a[l + 1] + 1) * (b[l + 1] + 1)) +
-             tiles_of(a[l], b[l]);
+        t += chunks((long long)(a[l + 1] + 1) * (b[l + 1] + 1)) + tiles_of(a[l], b[l]);
     return t;
 }
 
@@ -105,7 +104,7 @@ size_t run_bytes(int nz, int nr) {
     size_t t = al(nodes0 * 8) + 6 * al(W0 * 8);            // b, and ap, am, b, dg, cr, iv of level 0 in double
     for (int l = 0; l < n; ++l) {
         const size_t W = (size_t)b[l] + 1, nodes = ((size_t)a[l] + 1) * W;
-        t += 4 * al(nodes * 4) + 4 * al(W * 4);             // e, e2, f, r; ap, am, b, dinv in float
+        t += 3 * al(nodes * 4) + 4 * al(W * 4);             // e, e2, f; ap, am, b, dinv in float
     }
     const size_t m = (size_t)coarse_unknowns(a, b, n);
     if (m <= (size_t)MG_DIRECT_MAX) t += al(m * m * 4);
@@ -170,8 +169,8 @@ __device__ __forceinline__ float apply_Af(const MGLevel& L, const float* x, int 
 }
 
 // The residual r = b - A phi of every run in double, per-block partial sums
-// of r^2 (and, with with_b, of b^2) for its norm, and the start of the next
-// correction: level 0's right-hand side f = r (float) and e = 0.
+// of r^2 (and, with with_b, of b^2) for its norm, and the right-hand side of
+// the next correction: level 0's f = r (float).
 // blockIdx.y = run; block x takes the interior rows x, x + RED_BLOCKS, ...
 // with the threads along the row.  A fixed launch shape, so the summation
 // order (and the cycle count) never depends on tuning.
@@ -197,7 +196,6 @@ __global__ void __launch_bounds__(256) k_residual_norms(const MGTop* top, const 
                 r += T.am[j] * xm;
                 r += T.b[j] * (xu + xd);
                 L.f[k] = (float)r;
-                L.e[k] = 0.0f;
                 acc += r * r;
                 if (with_b) accb += bk * bk;
             }
@@ -261,13 +259,17 @@ __global__ void k_norms(const double* red, double* bnorm, int* done, const doubl
 // Four half-sweeps of red-black Gauss-Seidel on A e = f (colors c1, c2, c1,
 // c2: two iterations) in one launch, on a tile of SP_TI interior rows x SP_TJ
 // radial nodes in shared memory: the k-th half-sweep updates the tile grown
-// by 3 - k rings, so the tile's own nodes end exact.  Reads e, writes the
-// tile to e2 (no block reads a value another block has updated: the result
-// of four separate half-sweeps), or, with FINAL (level 0 after the cycle),
-// adds it to phi.  The work list gives each block its (run, tile).
-template <bool FINAL>
+// by 3 - k rings, so the tile's own nodes end exact (the result of four
+// separate half-sweeps).  The work list gives each block its (run, tile).
+// Pre-smoothing (POST false, colors 0, 1, 0, 1): starts from e = 0 (the
+// correction of a level is zero when its cycle begins) and writes e2.
+// Post-smoothing (POST true, colors 1, 0, 1, 0): starts from e2 plus the
+// bilinear prolongation of level l + 1's correction (its e), and writes e,
+// or, with FINAL (level 0), adds the tile to phi.  No block reads what
+// another block of the same launch writes.
+template <bool POST, bool FINAL>
 __global__ void __launch_bounds__(256) k_smooth4(const MGLevel* lev, const MGTop* top, const int* done, int l,
-                                                 int c1, const int2* tasks) {
+                                                 const int2* tasks) {
     constexpr int XR = SP_TI + 2 * SP_H, XC = SP_TJ + 2 * SP_H, FR = XR - 2, FC = XC - 2;
     __shared__ float xs[XR][XC + 1];
     __shared__ float fsm[FR][FC];
@@ -275,15 +277,31 @@ __global__ void __launch_bounds__(256) k_smooth4(const MGLevel* lev, const MGTop
     const int2 tk = tasks[blockIdx.x];
     const int run = tk.x;
     if (done[run]) return;
+    const int c1 = POST ? 1 : 0;
     const MGLevel L = lev[run * MG_MAX_LEVELS + l];
     const int W = L.nr + 1;
     const int tj = (W + SP_TJ - 1) / SP_TJ;
     const int i0 = 1 + (tk.y / tj) * SP_TI, j0 = (tk.y % tj) * SP_TJ;
-    for (int q = threadIdx.x; q < XR * XC; q += blockDim.x) {
-        const int a = q / XC, c = q % XC;
-        const int i = i0 - SP_H + a, j = j0 - SP_H + c;
-        // only interior rows are read by the update (the corrections vanish on the electrodes)
-        xs[a][c] = (i >= 1 && i <= L.nz - 1 && j >= 0 && j <= L.nr) ? L.e[i * W + j] : 0.0f;
+    if (POST) {
+        const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
+        const int Wc = Cl.nr + 1;
+        const float* ce = Cl.e;
+        for (int q = threadIdx.x; q < XR * XC; q += blockDim.x) {
+            const int a = q / XC, c = q % XC;
+            const int i = i0 - SP_H + a, j = j0 - SP_H + c;
+            float v = 0.0f;
+            // only interior rows are read by the update (the corrections vanish on the electrodes)
+            if (i >= 1 && i <= L.nz - 1 && j >= 0 && j <= L.nr) {
+                const int I0 = i >> 1, J0 = j >> 1;
+                const int I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
+                const float cc =
+                    0.25f * (ce[I0 * Wc + J0] + ce[I1 * Wc + J0] + ce[I0 * Wc + J1] + ce[I1 * Wc + J1]);
+                v = L.e2[i * W + j] + cc;
+            }
+            xs[a][c] = v;
+        }
+    } else {
+        for (int q = threadIdx.x; q < XR * (XC + 1); q += blockDim.x) (&xs[0][0])[q] = 0.0f;
     }
     for (int q = threadIdx.x; q < FR * FC; q += blockDim.x) {
         const int a = q / FC, c = q % FC;
@@ -327,33 +345,18 @@ __global__ void __launch_bounds__(256) k_smooth4(const MGLevel* lev, const MGTop
             if (i <= L.nz - 1 && j <= L.nr) phi[i * W + j] += (double)xs[i - i0 + SP_H][j - j0 + SP_H];
         }
     } else {
+        float* out = POST ? L.e : L.e2;
         for (int q = threadIdx.x; q < SP_TI * SP_TJ; q += blockDim.x) {
             const int i = i0 + q / SP_TJ, j = j0 + q % SP_TJ;
-            if (i <= L.nz - 1 && j <= L.nr) L.e2[i * W + j] = xs[i - i0 + SP_H][j - j0 + SP_H];
+            if (i <= L.nz - 1 && j <= L.nr) out[i * W + j] = xs[i - i0 + SP_H][j - j0 + SP_H];
         }
     }
 }
 
-// residual of level l after its pre-smoothing: the smoothed correction is in
-// e2; the residual is taken there and e2 is copied back to e (work list of
-// the level)
-__global__ void k_residual_tasks(const MGLevel* lev, const int* done, int l, const int2* tasks) {
-    const int2 tk = tasks[blockIdx.x];
-    const int run = tk.x;
-    if (done[run]) return;
-    const MGLevel L = lev[run * MG_MAX_LEVELS + l];
-    const int W = L.nr + 1;
-    const int n = min((L.nz - 1) * W, tk.y + MAP_CHUNK);
-    for (int q = tk.y + threadIdx.x; q < n; q += blockDim.x) {
-        const int i = 1 + q / W, j = q - (i - 1) * W;
-        const int k = i * W + j;
-        L.r[k] = L.f[k] - apply_Af(L, L.e2, i, j);
-        L.e[k] = L.e2[k];
-    }
-}
-
-// coarse right-hand side = sum of the fine integrated residuals over the
-// coarse control volume (full weighting scaled by 4); zero coarse correction
+// Coarse right-hand side of level l + 1 = the sum of the fine residuals
+// r = f - A e2 (e2: level l's pre-smoothed correction, r computed here)
+// over the coarse control volume (full weighting scaled by 4); zero coarse
+// correction.  Work list of the coarse level's nodes.
 __global__ void k_restrict(const MGLevel* lev, const int* done, int l, const int2* tasks) {
     const int2 tk = tasks[blockIdx.x];
     const int run = tk.x;
@@ -364,7 +367,6 @@ __global__ void k_restrict(const MGLevel* lev, const int* done, int l, const int
     const int n = min((Cl.nz + 1) * Wc, tk.y + MAP_CHUNK);
     for (int k = tk.y + threadIdx.x; k < n; k += blockDim.x) {
         const int I = k / Wc, J = k - I * Wc;
-        Cl.e[k] = 0.0f;
         if (I == 0 || I == Cl.nz) {
             Cl.f[k] = 0.0f;
             continue;
@@ -378,30 +380,10 @@ __global__ void k_restrict(const MGLevel* lev, const int* done, int l, const int
                 const int j = 2 * J + dj;
                 if (j < 0 || j > F.nr) continue;
                 const float wj = dj == 0 ? 1.0f : 0.5f;
-                s += wi * wj * F.r[i * Wf + j];
+                s += wi * wj * (F.f[i * Wf + j] - apply_Af(F, F.e2, i, j));
             }
         }
         Cl.f[k] = s;
-    }
-}
-
-// correction from level l + 1: its values are in e2 after its post-smoothing,
-// in e when level l + 1 is the run's first tail level (k_mg_tail)
-__global__ void k_prolong(const MGLevel* lev, const int* tail_lev, const int* done, int l, const int2* tasks) {
-    const int2 tk = tasks[blockIdx.x];
-    const int run = tk.x;
-    if (done[run]) return;
-    const MGLevel F = lev[run * MG_MAX_LEVELS + l];
-    const MGLevel Cl = lev[run * MG_MAX_LEVELS + l + 1];
-    const float* ce = l + 1 < tail_lev[run] ? Cl.e2 : Cl.e;
-    const int Wc = Cl.nr + 1, Wf = F.nr + 1;
-    const int n = min((F.nz - 1) * Wf, tk.y + MAP_CHUNK);
-    for (int q = tk.y + threadIdx.x; q < n; q += blockDim.x) {
-        const int i = 1 + q / Wf, j = q - (i - 1) * Wf;
-        const int I0 = i >> 1, J0 = j >> 1;
-        const int I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
-        const float c = 0.25f * (ce[I0 * Wc + J0] + ce[I1 * Wc + J0] + ce[I0 * Wc + J1] + ce[I1 * Wc + J1]);
-        F.e[i * Wf + j] += c;
     }
 }
 
@@ -766,7 +748,6 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
             L.e = (float*)take(nodes * 4);
             L.e2 = (float*)take(nodes * 4);
             L.f = (float*)take(nodes * 4);
-            L.r = (float*)take(nodes * 4);
             L.ap = (float*)take(W * 4);
             L.am = (float*)take(W * 4);
             L.b = (float*)take(W * 4);
@@ -808,13 +789,6 @@ int field_init(FieldSolver& fs, const std::vector<pd_config>& cfgs, const std::v
         auto add = [&](int r, long long cnt, int step) {
             for (long long q = 0; q < cnt; q += step) tasks.push_back(make_int2(r, (int)q));
         };
-        fs.fine_off[l] = (int)tasks.size();
-        for (int r = 0; r < R; ++r)
-            if (l < fs.tail_lev[r]) {
-                const MGLevel& L = fs.host_lev[(size_t)r * MG_MAX_LEVELS + l];
-                add(r, (long long)(L.nz - 1) * (L.nr + 1), MAP_CHUNK);
-            }
-        fs.fine_len[l] = (int)tasks.size() - fs.fine_off[l];
         fs.coarse_off[l] = (int)tasks.size();
         for (int r = 0; r < R; ++r)
             if (l < fs.tail_lev[r]) {
@@ -849,13 +823,15 @@ void field_free(FieldSolver& fs) {
     fs.host_done = nullptr;
 }
 
-// two red-black iterations (four half-sweeps) in one launch: e -> e2, or
-// e -> phi (+=) for level 0 after the cycle
-static int smooth4(FieldSolver& fs, int l, int c1, bool final_, cudaStream_t s) {
+// two red-black iterations (four half-sweeps) in one launch: pre-smoothing
+// from zero into e2, or post-smoothing from e2 plus the prolongated
+// correction of level l + 1 into e (level 0: into phi)
+static int smooth4(FieldSolver& fs, int l, bool post, cudaStream_t s) {
     if (!fs.tile_len[l]) return 0;
     const int2* t = fs.tasks + fs.tile_off[l];
-    if (final_) k_smooth4<true><<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.top, fs.done, l, c1, t);
-    else k_smooth4<false><<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.top, fs.done, l, c1, t);
+    if (!post) k_smooth4<false, false><<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.top, fs.done, l, t);
+    else if (l == 0) k_smooth4<true, true><<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.top, fs.done, l, t);
+    else k_smooth4<true, false><<<fs.tile_len[l], 256, 0, s>>>(fs.lev, fs.top, fs.done, l, t);
     return 1;
 }
 
@@ -866,26 +842,20 @@ static int vcycle(FieldSolver& fs, cudaStream_t s) {
     const int R = fs.nruns;
     const int th = fs.threads;
     int nk = 0;
-    // down to each run's tail: smooth, residual, restrict
+    // down to each run's tail: pre-smooth, residual and restriction
     for (int l = 0; l < fs.max_tail; ++l) {
-        nk += smooth4(fs, l, 0, false, s);
-        if (fs.fine_len[l]) {
-            k_residual_tasks<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.fine_off[l]);
+        nk += smooth4(fs, l, false, s);
+        if (fs.coarse_len[l]) {
             k_restrict<<<fs.coarse_len[l], th, 0, s>>>(fs.lev, fs.done, l, fs.tasks + fs.coarse_off[l]);
-            nk += 2;
+            ++nk;
         }
     }
     // the tail levels of every run, one block each
     k_mg_tail<<<R, TAIL_THREADS, fs.tail_smem, s>>>(fs.lev, fs.top, fs.nlev_dev, fs.tail_lev_dev, fs.done, fs.inv,
                                                     200);
     ++nk;
-    // up: prolong, smooth; level 0's last smoothing adds the correction to phi
-    for (int l = fs.max_tail - 1; l >= 0; --l) {
-        if (!fs.fine_len[l]) continue;
-        k_prolong<<<fs.fine_len[l], th, 0, s>>>(fs.lev, fs.tail_lev_dev, fs.done, l, fs.tasks + fs.fine_off[l]);
-        ++nk;
-        nk += smooth4(fs, l, 1, l == 0, s);
-    }
+    // up: prolongation and post-smoothing in one launch per level; level 0's adds the correction to phi
+    for (int l = fs.max_tail - 1; l >= 0; --l) nk += smooth4(fs, l, true, s);
     return nk;
 }
 

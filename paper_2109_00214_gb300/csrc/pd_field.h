@@ -15,7 +15,7 @@ constexpr int MG_DIRECT_MAX = 256;      // coarsest levels up to this many unkno
 // one level of one run's correction multigrid (float)
 struct MGLevel {
     int nz, nr;              // cells
-    float *e, *e2, *f, *r;   // correction, the smoother's second buffer, right-hand side, residual (nodes)
+    float *e, *e2, *f;       // correction (post-smoothed), pre-smoothed correction, right-hand side (nodes)
     float *ap, *am, *b;      // per radial node j: radial face and axial coefficients
     float* dinv;             // 1 / (ap + am + 2 b)
 };
@@ -50,9 +50,8 @@ struct FieldSolver {
     int max_nodes0 = 0;                 // largest level-0 node count
     float** inv = nullptr;              // [nruns] inverse of the coarsest operator (transposed), or null
     // work lists of the per-cycle kernels: (run, first item) of each block,
-    // for every level l the runs that smooth there (l < levels - 1)
+    // for every level l the runs whose tail level lies below l
     int2* tasks = nullptr;              // device copy of all lists
-    int fine_off[MG_MAX_LEVELS] = {}, fine_len[MG_MAX_LEVELS] = {};       // interior nodes of level l
     int coarse_off[MG_MAX_LEVELS] = {}, coarse_len[MG_MAX_LEVELS] = {};   // all nodes of level l + 1
     int tile_off[MG_MAX_LEVELS] = {}, tile_len[MG_MAX_LEVELS] = {};       // smoother tiles of level l
     // levels from tail_lev[run] down are cycled by one block per run in
