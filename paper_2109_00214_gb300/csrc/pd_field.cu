@@ -45,10 +45,10 @@ constexpr double EPS0_ = 8.8541878128e-12;
 constexpr double PI_ = 3.14159265358979323846;
 constexpr int RED_BLOCKS = 64;
 constexpr int MAP_CHUNK = 256;         // items of one work-list entry
-constexpr int SP_TI = 16, SP_TJ = 32;  // smoother tile: interior rows x radial nodes
+constexpr int SP_TI = 32, SP_TJ = 32;  // smoother tile: interior rows x radial nodes
 constexpr int SP_H = 4;                // halo: four half-sweeps per launch
 constexpr int TAIL_NODES = 34 * 34;    // levels from the first one with at most this many nodes: k_mg_tail
-constexpr int TAIL_THREADS = 256;
+constexpr int TAIL_THREADS = 512;
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
