@@ -48,7 +48,7 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, cntb, mv, mvx, partial, nc, cand, cand_off, active, mid, big, rho_e, rho_h, diag, E,
+    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, cand, cand_off, active, mid, big, rho_e, rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
@@ -90,6 +90,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.off2 = take(((size_t)L.nbins_pad + 1) * 4);
     L.outc = take((size_t)L.nbins_pad * 4);                // movers out of each bin
     L.stay = take((size_t)L.nbins_pad * 4);                // particles that stay in each bin
+    L.dlt = take((size_t)L.nbins_pad * 4);                 // stayers' slot offset of each bin
     L.cntb = take((size_t)L.nbins_pad * 4);                // new bin counts (scan input)
     L.mv = take((size_t)L.words_pad * 4);                  // mover bit mask of the sorted slots
     L.mvx = take(((size_t)L.words_pad + 1) * 4);           // its popcount prefix
@@ -148,7 +149,7 @@ struct pd_sim {
     char* ws;
     int sms;
     Particles A, B;
-    uint32_t *count, *off, *off2, *outc, *stay, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
+    uint32_t *count, *off, *off2, *outc, *stay, *dlt, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
     bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
     uint2* nc;
     long long *rho_e, *rho_h, *diag;
@@ -544,15 +545,19 @@ pd_status issue_step(pd_sim* s, bool capturing) {
                     s->stream);
     }
     {
-        Timed t(s, K_SCAN_BINS, capturing, P.use_prev ? 7 : 4);
+        Timed t(s, K_SCAN_BINS, capturing, P.use_prev ? 8 : 4);
         launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
                         grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
         launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
-        if (P.use_prev) launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
+        if (P.use_prev) {
+            launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
+            launch_bin_delta(s->off, s->off2, s->mv, s->mvx, s->dlt, nbins,
+                             grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
+        }
     }
     {
         Timed t(s, K_SCATTER, capturing, 1);
-        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->count, s->mv, s->mvx, nbins, s->st, P,
+        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->dlt, s->count, s->mv, s->mvx, nbins, s->st, P,
                        grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
     }
     std::swap(s->A, s->B);
@@ -768,6 +773,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->off2 = P32(L.off2);
     s->outc = P32(L.outc);
     s->stay = P32(L.stay);
+    s->dlt = P32(L.dlt);
     s->cntb = P32(L.cntb);
     s->mv = P32(L.mv);
     s->mvx = P32(L.mvx);

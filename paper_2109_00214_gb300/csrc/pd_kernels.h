@@ -29,9 +29,12 @@ void launch_push(const Particles& A, const float2* E, long long* rho_e, long lon
                  const KParams& P, int grid, cudaStream_t s);
 void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
                      uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s);
+// per bin: dlt = new_off - old_off + movers before old_off (after both scans)
+void launch_bin_delta(const uint32_t* old_off, const uint32_t* new_off, const uint32_t* mv, const uint32_t* mvx,
+                      uint32_t* dlt, uint32_t nbins, int grid, cudaStream_t s);
 void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
-                    const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
-                    DevState* st, const KParams& P, int grid, cudaStream_t s);
+                    const uint32_t* stay, const uint32_t* dlt, uint32_t* in_cnt, const uint32_t* mv,
+                    const uint32_t* mvx, uint32_t nbins, DevState* st, const KParams& P, int grid, cudaStream_t s);
 void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
                     int grid, cudaStream_t s);
 // exclusive scan of n_padded (multiple of SCAN_TILE) u32; out has n_padded + 1

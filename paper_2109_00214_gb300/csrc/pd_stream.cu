@@ -309,11 +309,23 @@ __global__ void __launch_bounds__(256) k_bincount(const uint32_t* __restrict__ o
     }
 }
 
-// movers strictly before slot p (p < n_sorted)
+// movers strictly before slot p (p <= n_sorted)
 __device__ __forceinline__ uint32_t movers_before(const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
                                                   uint32_t p) {
     const uint32_t w = p >> 5;
     return mvx[w] + (uint32_t)__popc(mv[w] & ((1u << (p & 31u)) - 1u));
+}
+
+// dlt[b] = new_off[b] - old_off[b] + (movers before old_off[b]): a stayer of
+// bin b at old slot i goes to dlt[b] + i - (movers before i)
+__global__ void __launch_bounds__(256) k_bin_delta(const uint32_t* __restrict__ old_off,
+                                                   const uint32_t* __restrict__ new_off,
+                                                   const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
+                                                   uint32_t* dlt, uint32_t nbins) {
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        const uint32_t o = old_off[b];
+        dlt[b] = new_off[b] - o + movers_before(mv, mvx, o);
+    }
 }
 
 // Staging window of the scatter: a block's stayers land on a nearly
@@ -326,7 +338,8 @@ constexpr uint32_t SCATTER_WIN = 1536;
 __global__ void __launch_bounds__(SCATTER_THREADS, 4) k_scatter4(Particles A, Particles B,
                                                               const uint32_t* __restrict__ old_off,
                                                               const uint32_t* __restrict__ new_off,
-                                                              const uint32_t* __restrict__ stay, uint32_t* in_cnt,
+                                                              const uint32_t* __restrict__ stay,
+                                                              const uint32_t* __restrict__ dlt, uint32_t* in_cnt,
                                                               const uint32_t* __restrict__ mv,
                                                               const uint32_t* __restrict__ mvx, uint32_t nbins,
                                                               DevState* st, KParams P) {
@@ -372,11 +385,11 @@ __global__ void __launch_bounds__(SCATTER_THREADS, 4) k_scatter4(Particles A, Pa
             any_mover |= mover[q];
             slot[q] = 0;
             if (stayer) {
-                const uint32_t o = old_off[bin[q]];
+                // slot = new_off - old_off + (movers before old_off) + i - (movers before i), the
+                // bin's part precomputed in dlt
                 const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
-                const uint32_t r = (i - o) - (before - movers_before(mv, mvx, o));
-                if (r >= stay[bin[q]]) set_error(st, ERR_BOUNDS);   // stayer outside its bin's range
-                slot[q] = new_off[bin[q]] + r;
+                slot[q] = dlt[bin[q]] + i - before;
+                if (slot[q] - new_off[bin[q]] >= stay[bin[q]]) set_error(st, ERR_BOUNDS);   // outside its bin's range
             }
         }
         if (any_mover) {            // claim slots after the stayers, one atomic per run of one bin
@@ -476,10 +489,15 @@ void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t*
     k_bincount<<<grid, 256, 0, s>>>(old_off, out_cnt, in_cnt, cnt, stay, nbins_pad, use_prev);
 }
 
+void launch_bin_delta(const uint32_t* old_off, const uint32_t* new_off, const uint32_t* mv, const uint32_t* mvx,
+                      uint32_t* dlt, uint32_t nbins, int grid, cudaStream_t s) {
+    k_bin_delta<<<grid, 256, 0, s>>>(old_off, new_off, mv, mvx, dlt, nbins);
+}
+
 void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
-                    const uint32_t* stay, uint32_t* in_cnt, const uint32_t* mv, const uint32_t* mvx, uint32_t nbins,
-                    DevState* st, const KParams& P, int grid, cudaStream_t s) {
-    k_scatter4<<<grid, SCATTER_THREADS, 0, s>>>(A, B, old_off, new_off, stay, in_cnt, mv, mvx, nbins, st, P);
+                    const uint32_t* stay, const uint32_t* dlt, uint32_t* in_cnt, const uint32_t* mv,
+                    const uint32_t* mvx, uint32_t nbins, DevState* st, const KParams& P, int grid, cudaStream_t s) {
+    k_scatter4<<<grid, SCATTER_THREADS, 0, s>>>(A, B, old_off, new_off, stay, dlt, in_cnt, mv, mvx, nbins, st, P);
 }
 
 }  // namespace pd
