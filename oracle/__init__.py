@@ -46,7 +46,7 @@ class _Cfg(C.Structure):
         ("V0", C.c_double), ("R_ohm", C.c_double), ("C_farad", C.c_double),
         ("beta", C.c_double), ("tip_radius", C.c_double), ("work_function", C.c_double),
         ("neutral_ratio", C.c_double), ("neutral_T", C.c_double),
-        ("poisson_tol", C.c_double), ("capacity", C.c_int64),
+        ("poisson_tol", C.c_double), ("capacity", C.c_int64), ("heavy_coll", C.c_int32),
     ]
 
 
@@ -108,7 +108,8 @@ def _dptr(a):
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
-                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")])
+                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")]
+                 + ["ev_cx", "ev_nn"])
 SCALAR_NAMES = ["t", "V", "I_gap", "gamma", "Qbar", "erosion", "mass", "charge", "sgmax0",
                 "sgmax1", "poisson_relres", "poisson_iters", "E_abs_cathode", "E_abs_anode",
                 "E_abs_wall"]
@@ -150,6 +151,7 @@ class Oracle:
         c.neutral_ratio, c.neutral_T = cfg["neutral_ratio"], cfg["neutral_T"]
         c.poisson_tol = cfg.get("oracle_poisson_tol", 1e-11)
         c.capacity = cfg["capacity"]
+        c.heavy_coll = cfg.get("heavy_coll", 0)
         self._c = c
         self.h = self.L.or_create(C.byref(c))
         rz = c.geom == 0

@@ -61,7 +61,10 @@ static const double KB = 1.380649e-23;
 static const double PI = 3.14159265358979323846;
 
 enum { SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4, NSP = 5 };
-enum { CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, NCH = 5 };
+/* channels 5 and 6 are the heavy-particle collisions the paper lists     */
+/* besides ionization (Sec. 2.3): charge exchange Cu+ + Cu and elastic    */
+/* Cu + Cu; off unless heavy_coll is set                                  */
+enum { CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6, NCH = 7 };
 static const int ZQ[NSP] = {-1, 0, 1, 2, 2};
 
 /* cross-section grid (must be the grid the inputs are tabulated on) */
@@ -87,6 +90,7 @@ typedef struct {
     double beta, tip_radius, work_function, neutral_ratio, neutral_T;
     double poisson_tol;
     int64_t capacity;
+    int32_t heavy_coll;    /* heavy-particle pair classes (charge exchange, Cu-Cu elastic) on */
 } or_cfg;
 
 typedef struct {
@@ -109,7 +113,7 @@ typedef struct {
     float xsE[XS_N];
     real xs[NCH][XS_N];
     double eth[NCH];
-    real sgmax[2];
+    real sgmax[4];
     /* counters */
     uint64_t events[NCH], nulls, consumed, thr_rej, ratio_viol, iso_fallback, cand_total;
     uint64_t absorbed[3][NSP];   /* cathode, anode, outer wall */
@@ -244,20 +248,24 @@ static real xs_lookup(const or_sim* S, int ch, real eps) {
     return S->xs[ch][k] + t * (S->xs[ch][k + 1] - S->xs[ch][k]);
 }
 
-static const int CLASS_CH0[2] = {CH_EL, CH_SW};
-static const int CLASS_NCH[2] = {4, 1};
-static const int CLASS_TARGET[2] = {SP_CU, SP_CUP};
+/* pair classes: (e, Cu), (e, Cu+), then, on heavy steps with heavy_coll,
+ * (Cu, Cu+) charge exchange and (Cu, Cu) elastic */
+static const int CLASS_CH0[4] = {CH_EL, CH_SW, CH_CX, CH_NN};
+static const int CLASS_NCH[4] = {4, 1, 1, 1};
+static const int CLASS_TARGET[4] = {SP_CU, SP_CUP, SP_CUP, SP_CU};
 
 static double mr_class(void) { return ME * M_CU / (ME + M_CU); }
 static real kmr(void) { return R_(0.5 * mr_class() / QE); } /* eps[eV] = g^2 * kmr */
+/* heavy pairs: equal masses, m_r = M/2 */
+static real kmr_heavy(void) { return R_(0.5 * (0.5 * M_CU) / QE); }
 
 /* NTC majorant (sigma g)_max of one pair class: on each grid segment the
  * interpolant is at most the larger end value and g is largest at the upper
  * end, so max_k max(sT_k, sT_k+1) * g(E_k+1) bounds sigma_T(eps) g(eps); a
  * relative margin of 1e-6 covers float rounding. */
 static void compute_sgmax(or_sim* S) {
-    double kd = (double)kmr();
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {
+        double kd = (double)(k < 2 ? kmr() : kmr_heavy());
         double best = 0.0;
         real sT_prev = 0;
         for (int q = 0; q < XS_N; ++q) {
@@ -708,7 +716,7 @@ static int cmp_id(const void* a, const void* b) {
     return x < y ? -1 : (x > y ? 1 : 0);
 }
 
-static int collide_all(or_sim* S) {
+static int collide_all(or_sim* S, int heavy_step) {
     int64_t C = (int64_t)S->c.nz * S->c.nr;
     int64_t nb = C * NSP;
     int64_t* cnt = (int64_t*)calloc(nb + 1, 8);
@@ -732,41 +740,60 @@ static int collide_all(or_sim* S) {
     for (int64_t b = 0; b < nb; ++b)
         if (cnt[b + 1] - cnt[b] > 1) qsort(rec + cnt[b], cnt[b + 1] - cnt[b], sizeof(idrec), cmp_id);
 
-    /* candidate counts per cell and their prefix sum (spawn id slots) */
-    uint32_t* nc = (uint32_t*)calloc(2 * C, 4);
-    uint64_t total = 0;
+    /* candidate counts per cell and their prefix sum (spawn id slots: the
+     * electron classes only; heavy pairs spawn nothing) */
+    uint32_t* nc = (uint32_t*)calloc(4 * C, 4);
+    uint64_t total = 0, heavy_total = 0;
     uint64_t* pre = (uint64_t*)malloc((C + 1) * 8);
     double dtc = S->c.dt * S->c.coll_dt_scale;
+    double dth = dtc * S->c.heavy_subcycle;                 /* heavy pairs collide on heavy steps */
+    int heavy = S->c.heavy_coll && heavy_step;
     for (int64_t c = 0; c < C; ++c) {
         int j = (int)(c % S->c.nr);
         pre[c] = total;
         stream_t st;
         stream_init(&st, S, (uint32_t)c, S->step, SID_NCAND);
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
+        uint32_t Ncu = (uint32_t)(cnt[SP_CU * C + c + 1] - cnt[SP_CU * C + c]);
+        uint32_t Ni = (uint32_t)(cnt[SP_CUP * C + c + 1] - cnt[SP_CUP * C + c]);
         for (int k = 0; k < 2; ++k) {
             int ts = CLASS_TARGET[k];
             uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
             real ck = R_(S->c.weight * (double)S->sgmax[k] * dtc / cell_volume(S, j));
             real R = u01(&st);
             real x = ((real)Ne * (real)Nt) * ck + R;
-            nc[2 * c + k] = (uint32_t)OR_FLOOR(x);
+            nc[4 * c + k] = (uint32_t)OR_FLOOR(x);
         }
-        total += nc[2 * c] + nc[2 * c + 1];
+        if (heavy) {
+            /* N_cu N_cu+ pairs for charge exchange, N_cu (N_cu - 1) / 2 for Cu-Cu */
+            real ck2 = R_(S->c.weight * (double)S->sgmax[2] * dth / cell_volume(S, j));
+            real ck3 = R_(0.5 * S->c.weight * (double)S->sgmax[3] * dth / cell_volume(S, j));
+            real R2 = u01(&st), R3 = u01(&st);
+            real x2 = ((real)Ncu * (real)Ni) * ck2 + R2;
+            real x3 = ((real)Ncu * (real)(Ncu > 0 ? Ncu - 1 : 0)) * ck3 + R3;
+            nc[4 * c + 2] = (uint32_t)OR_FLOOR(x2);
+            nc[4 * c + 3] = (uint32_t)OR_FLOOR(x3);
+            if (Ncu < 2) nc[4 * c + 3] = 0;
+            heavy_total += nc[4 * c + 2] + nc[4 * c + 3];
+        }
+        total += nc[4 * c] + nc[4 * c + 1];
     }
     pre[C] = total;
-    S->cand_total += total;
+    S->cand_total += total + heavy_total;
     uint32_t id_base = S->id_next;
-    real km = kmr();
+    real km = kmr(), kmh = kmr_heavy();
     int err = 0;
     for (int64_t c = 0; c < C && !err; ++c) {
         uint32_t next_id = id_base + (uint32_t)(2 * pre[c]);
         const idrec* el = rec + cnt[SP_E * C + c];
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
+        const idrec* cul = rec + cnt[SP_CU * C + c];
+        uint32_t Ncu = (uint32_t)(cnt[SP_CU * C + c + 1] - cnt[SP_CU * C + c]);
         for (int k = 0; k < 2 && !err; ++k) {
             int ts = CLASS_TARGET[k];
             const idrec* tl = rec + cnt[ts * C + c];
             uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
-            for (uint32_t m = 0; m < nc[2 * c + k]; ++m) {
+            for (uint32_t m = 0; m < nc[4 * c + k]; ++m) {
                 stream_t st;
                 stream_init(&st, S, (uint32_t)c, S->step, SID_CAND(k, m));
                 uint32_t i = pick(&st, Ne), jt = pick(&st, Nt);
@@ -799,6 +826,51 @@ static int collide_all(or_sim* S) {
                 if (r == -2) { err = 1; break; }
                 if (r < 0) { S->thr_rej++; continue; }
                 S->events[ch]++;
+            }
+        }
+        /* heavy pairs, classes 2 (Cu from the Cu list, Cu+ from the Cu+ list) and
+         * 3 (two different Cu of the Cu list); a particle whose species changed
+         * this step (ionized) is consumed */
+        for (int k = 2; k < 4 && heavy && !err; ++k) {
+            int ts = CLASS_TARGET[k];
+            const idrec* tl = rec + cnt[ts * C + c];
+            uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
+            for (uint32_t m = 0; m < nc[4 * c + k]; ++m) {
+                stream_t st;
+                stream_init(&st, S, (uint32_t)c, S->step, SID_CAND(k, m));
+                uint32_t i = pick(&st, Ncu), jt;
+                if (k == 2) jt = pick(&st, Nt);
+                else {          /* a second, different Cu */
+                    jt = pick(&st, Ncu - 1);
+                    if (jt >= i) jt++;
+                }
+                real Racc = u01(&st);
+                (void)u01(&st);     /* fourth draw of the candidate, unused by one-channel classes */
+                int64_t ia = cul[i].idx, ib = tl[jt].idx;
+                if (S->sp[ia] != SP_CU || S->sp[ib] != ts) { S->consumed++; continue; }
+                real ux = S->vz[ia] - S->vz[ib], uy = S->vr[ia] - S->vr[ib], uz = S->vt[ia] - S->vt[ib];
+                real g2 = (ux * ux + uy * uy) + uz * uz;
+                real g = OR_SQRT(g2);
+                real sg = xs_lookup(S, CLASS_CH0[k], g2 * kmh) * g;
+                if (sg > S->sgmax[k]) S->ratio_viol++;
+                if (!(Racc * S->sgmax[k] < sg)) { S->nulls++; continue; }
+                if (k == 2) {
+                    /* resonant charge exchange: the electron moves to the ion, the
+                     * velocities stay with the atoms: the Cu+ slot takes the Cu's
+                     * velocity and the Cu slot the ion's */
+                    real t;
+                    t = S->vz[ia]; S->vz[ia] = S->vz[ib]; S->vz[ib] = t;
+                    t = S->vr[ia]; S->vr[ia] = S->vr[ib]; S->vr[ib] = t;
+                    t = S->vt[ia]; S->vt[ia] = S->vt[ib]; S->vt[ib] = t;
+                } else {
+                    /* elastic, equal masses (m_r/m = 1/2), isotropic in the centre of mass */
+                    vec3 va = {S->vz[ia], S->vr[ia], S->vt[ia]};
+                    vec3 vb = {S->vz[ib], S->vr[ib], S->vt[ib]};
+                    binary_scatter(S, &st, &va, &vb, R_(0), R_(0.5), R_(0.5));
+                    S->vz[ia] = va.x; S->vr[ia] = va.y; S->vt[ia] = va.z;
+                    S->vz[ib] = vb.x; S->vr[ib] = vb.y; S->vt[ib] = vb.z;
+                }
+                S->events[CLASS_CH0[k]]++;
             }
         }
     }
@@ -1027,7 +1099,7 @@ int or_step(or_sim* S, int nsteps) {
         if (inject(S)) return 2;
         push_all(S, heavy_step);
         deposit_all(S, heavy_step);
-        if (collide_all(S)) return 3;
+        if (collide_all(S, heavy_step)) return 3;
         if (S->c.geom == 0) {
             /* RC circuit: C dV/dt = (V0 - V)/R - I_gap (anode fed through R) */
             S->V += S->c.dt / S->c.C_farad * ((S->c.V0 - S->V) / S->c.R_ohm - S->I_gap);
@@ -1081,15 +1153,17 @@ void or_get_field(const or_sim* S, double* Ez, double* Er) {
     for (int64_t k = 0; k < nn; ++k) { Ez[k] = S->Ez[k]; Er[k] = S->Er[k]; }
 }
 
-/* counters: events[5], nulls, consumed, thr_rej, ratio_viol, iso_fallback,
- * cand_total, emitted_e, emitted_cu, absorbed[3][5] */
+/* counters: events[5] of the electron channels, nulls, consumed, thr_rej,
+ * ratio_viol, iso_fallback, cand_total, emitted_e, emitted_cu,
+ * absorbed[3][5], then events of charge exchange and Cu-Cu elastic */
 void or_get_counters(const or_sim* S, uint64_t* out) {
     int k = 0;
-    for (int c = 0; c < NCH; ++c) out[k++] = S->events[c];
+    for (int c = 0; c < CH_CX; ++c) out[k++] = S->events[c];
     out[k++] = S->nulls; out[k++] = S->consumed; out[k++] = S->thr_rej;
     out[k++] = S->ratio_viol; out[k++] = S->iso_fallback; out[k++] = S->cand_total;
     out[k++] = S->emitted_e; out[k++] = S->emitted_cu;
     for (int e = 0; e < 3; ++e) for (int s = 0; s < NSP; ++s) out[k++] = S->absorbed[e][s];
+    out[k++] = S->events[CH_CX]; out[k++] = S->events[CH_NN];
 }
 
 /* scalars: t, V, I_gap, gamma, Qbar, erosion (kg/C), mass ledger (kg),

@@ -38,7 +38,8 @@ def xs_grid():
     return np.ldexp(1.0 + j / XS_SUB, e)
 
 
-def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.0):
+def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.0, s_cx=6e-19, k_cx=0.06,
+                           d_cu=2.6e-10):
     """Closed-form stand-ins for the paper's cross sections (its Fig. 1 data
     from refs. [28-30] is not available).  Ionization and excitation use the
     Lotz form with b = 0, sigma = s_max * e * ln(E/I) / (E/I) for E > I (peak
@@ -47,7 +48,11 @@ def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.
     the table grid.
 
     Channels: 0 elastic e-Cu, 1 excitation e-Cu, 2 single ionization Cu->Cu+,
-    3 double ionization Cu->Cu2+, 4 step-wise Cu+->Cu2+.
+    3 double ionization Cu->Cu2+, 4 step-wise Cu+->Cu2+, and the heavy pairs
+    the paper lists without data: 5 resonant charge exchange Cu+ + Cu,
+    sigma = s_cx (1 - k ln(E / 1 eV))^2 (the Rapp-Francis shape), and 6
+    elastic Cu + Cu, a hard sphere pi d^2 (E: relative energy in the centre
+    of mass, eV).
     Thresholds: DI about 28 eV and Cu+->Cu2+ 20.3 eV are the paper's (Sec. 3.2);
     7.726 eV (first ionization energy of Cu) and 3.8 eV (excitation) are not
     given by the paper.
@@ -67,6 +72,8 @@ def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.
         x = E / I
         s = np.where(x > 1.0, pk[c] * math.e * np.log(np.maximum(x, 1.0)) / x, 0.0)
         out[c] = (E, s, I)
+    out[5] = (E, s_cx * np.maximum(1.0 - k_cx * np.log(E), 0.0) ** 2, 0.0)
+    out[6] = (E, np.full_like(E, math.pi * d_cu * d_cu), 0.0)
     return out
 
 
