@@ -53,7 +53,11 @@ typedef enum {
 enum { PD_GEOM_RZ = 0, PD_GEOM_XY_PERIODIC = 1 };
 enum { PD_FIELD_NONE = 0, PD_FIELD_POISSON = 1, PD_FIELD_EXTERNAL = 2 };
 enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI = 4, PD_NSP = 5 };
-enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4, PD_NCH = 5 };
+/* channels 5 and 6: the heavy pairs the paper lists besides ionization
+ * (Sec. 2.3, no data given): resonant charge exchange Cu+ + Cu and elastic
+ * Cu + Cu, with E the relative energy in the centre of mass */
+enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4,
+       PD_CH_CX = 5, PD_CH_NN = 6, PD_NCH = 7 };
 
 #define PD_CONFIG_VERSION 1u
 
@@ -80,7 +84,9 @@ typedef struct pd_config {
     double beta, tip_radius, work_function, neutral_ratio, neutral_T;
     double poisson_tol;        /* relative residual |b - A phi| / |b| */
     int32_t poisson_max_cycles;
-    int32_t reserved0;
+    int32_t heavy_coll;        /* 1: on heavy steps, the heavy pair classes (Cu+, Cu)
+                                  charge exchange and (Cu, Cu) elastic, NTC with the
+                                  heavy step; 0 (default): off */
     int64_t capacity;          /* particle slots */
 } pd_config;
 
@@ -106,11 +112,13 @@ typedef struct pd_scalars {
     int64_t step;              /* electron steps taken */
 } pd_scalars;
 
-/* counters: events per channel [5], null candidates, candidates whose target
- * was already ionized this step, accepted candidates below threshold, NTC
- * majorant violations, isotropic-sampling fallbacks, candidates in total,
- * electrons emitted, neutrals emitted, absorbed [electrode 3][species 5]. */
-#define PD_NCOUNTERS 28
+/* counters: events per electron-impact channel [5], null candidates,
+ * candidates whose target (or, for heavy pairs, either particle) was already
+ * ionized this step, accepted candidates below threshold, NTC majorant
+ * violations, isotropic-sampling fallbacks, candidates in total, electrons
+ * emitted, neutrals emitted, absorbed [electrode 3][species 5], charge
+ * exchange events, Cu-Cu elastic events. */
+#define PD_NCOUNTERS 30
 
 typedef struct pd_sim pd_sim;
 

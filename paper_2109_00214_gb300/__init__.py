@@ -30,13 +30,14 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
-PD_NCOUNTERS = 28
+PD_NCOUNTERS = 30
 PD_NKERNELS = 12
 GEOM = {"rz": 0, "xy_periodic": 1}
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
-                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")])
+                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")]
+                 + ["ev_cx", "ev_nn"])
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CAPACITY", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
           5: "PD_ERR_NONFINITE", 6: "PD_ERR_STATE"}
 
@@ -52,7 +53,7 @@ class PdConfig(C.Structure):
         ("R_ohm", C.c_double), ("C_farad", C.c_double), ("beta", C.c_double),
         ("tip_radius", C.c_double), ("work_function", C.c_double), ("neutral_ratio", C.c_double),
         ("neutral_T", C.c_double), ("poisson_tol", C.c_double), ("poisson_max_cycles", C.c_int32),
-        ("reserved0", C.c_int32), ("capacity", C.c_int64),
+        ("heavy_coll", C.c_int32), ("capacity", C.c_int64),
     ]
 
 
@@ -208,6 +209,7 @@ def config_from_dict(d):
     c.neutral_ratio, c.neutral_T = d["neutral_ratio"], d["neutral_T"]
     c.poisson_tol = d.get("poisson_tol", 1e-8)
     c.poisson_max_cycles = d.get("poisson_max_cycles", 60)
+    c.heavy_coll = d.get("heavy_coll", 0)
     c.capacity = d["capacity"]
     return c
 

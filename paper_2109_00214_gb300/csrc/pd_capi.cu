@@ -23,6 +23,9 @@
 #include "pd_kernels.h"
 #include "pd_net.h"
 
+static_assert(PD_NCOUNTERS == pd::NCOUNTERS, "counter layout of the C ABI and the kernels differ");
+static_assert(PD_NCH == pd::NCH, "channel count of the C ABI and the kernels differ");
+
 using namespace pd;
 
 namespace {
@@ -71,7 +74,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
         cap += (uint64_t)cf[r].capacity;
         ncell += (uint64_t)cf[r].nz * cf[r].nr;
         nodes += run_nodes(cf[r]);
-        ckl += 2ull * cf[r].nr;
+        ckl += 4ull * cf[r].nr;
         nz[r] = cf[r].nz;
         nr[r] = cf[r].nr;
     }
@@ -96,7 +99,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.mvx = take(((size_t)L.words_pad + 1) * 4);           // its popcount prefix
     const size_t npart = (size_t)std::max(std::max(L.nbins_pad, L.ncell_pad), L.words_pad) / SCAN_TILE + 1;
     L.partial = take(npart * 4);
-    L.nc = take(ncell * 8);
+    L.nc = take(ncell * 16);
     L.cand = take((size_t)L.ncell_pad * 4);
     L.cand_off = take(((size_t)L.ncell_pad + 1) * 4);
     L.active = take(ncell * 4);
@@ -151,7 +154,7 @@ struct pd_sim {
     Particles A, B;
     uint32_t *count, *off, *off2, *outc, *stay, *dlt, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
     bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
-    uint2* nc;
+    uint4* nc;
     long long *rho_e, *rho_h, *diag;
     float2* E;
     double* phi;
@@ -270,6 +273,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.ncell = (uint32_t)s->L.ncell;
     P.step = (uint32_t)s->step;
     P.heavy_step = heavy_step;
+    P.heavy_coll = s->cfgs[0].heavy_coll;
     P.field_on = c.field_mode != PD_FIELD_NONE;
     P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
@@ -306,13 +310,14 @@ void update_collision_consts(pd_sim* s) {
     const double mr = mr_class();
     CollConsts& cc = s->cc;
     cc.kmr = (float)(0.5 * mr / QE);
+    cc.kmr_h = (float)(0.5 * (0.5 * M_CU) / QE);
     cc.a_e = (float)(mr / ME);
     cc.a_t = (float)(mr / M_CU);
     for (int ch = 0; ch < NCH; ++ch) cc.kth[ch] = (float)(2.0 * s->eth[ch] * QE / mr);
     cc.di_split_mode = s->cfgs[0].di_split_mode;
-    const double kd = (double)cc.kmr;
-    const int ch0[2] = {CH_EL, CH_SW}, nch[2] = {4, 1};
-    for (int k = 0; k < 2; ++k) {
+    const int ch0[4] = {CH_EL, CH_SW, CH_CX, CH_NN}, nch[4] = {4, 1, 1, 1};
+    for (int k = 0; k < 4; ++k) {
+        const double kd = (double)(k < 2 ? cc.kmr : cc.kmr_h);
         double best = 0.0;
         float prev = 0.0f;
         for (int q = 0; q < XS_N; ++q) {
@@ -343,6 +348,14 @@ pd_status upload_ck(pd_sim* s) {
         for (int k = 0; k < 2; ++k)
             for (int j = 0; j < c.nr; ++j)
                 ck[base + (size_t)k * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[k] * dtc / cell_volume(c, j));
+        // heavy pairs collide on heavy steps with the heavy step; (Cu, Cu) pairs
+        // number N (N - 1) / 2
+        const double dth = dtc * c.heavy_subcycle;
+        for (int j = 0; j < c.nr; ++j) {
+            ck[base + (size_t)2 * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[2] * dth / cell_volume(c, j));
+            ck[base + (size_t)3 * c.nr + j] =
+                (float)(0.5 * c.weight * (double)s->cc.sgmax[3] * dth / cell_volume(c, j));
+        }
     }
     CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -392,6 +405,7 @@ pd_status validate_one(const pd_config* c, std::string& msg) {
     if (c->field_mode == PD_FIELD_POISSON && c->geometry != PD_GEOM_RZ) { msg = "Poisson field needs r-z"; return PD_ERR_ARG; }
     if (c->field_mode == PD_FIELD_POISSON && !field_grid_ok(c->nz, c->nr)) { msg = "Poisson multigrid needs nz, nr = m * 2^k with m <= 8"; return PD_ERR_ARG; }
     if (!(c->coll_dt_scale >= 0)) { msg = "coll_dt_scale must be >= 0"; return PD_ERR_ARG; }
+    if (c->heavy_coll != 0 && c->heavy_coll != 1) { msg = "heavy_coll must be 0 or 1"; return PD_ERR_ARG; }
     if (c->geometry == PD_GEOM_RZ && c->inject_on) {
         if (!(c->tip_radius > 0) || c->tip_radius / c->dr > 63) { msg = "tip must span 1..63 cells"; return PD_ERR_ARG; }
     }
@@ -409,8 +423,9 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         const pd_config &a = cfgs[0], &b = cfgs[r];
         if (b.geometry != a.geometry || b.dt != a.dt || b.heavy_subcycle != a.heavy_subcycle ||
             b.field_mode != a.field_mode || b.coll_dt_scale != a.coll_dt_scale || b.di_on != a.di_on ||
-            b.di_split_mode != a.di_split_mode) {
-            msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale or double-ionization settings";
+            b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll) {
+            msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale, double-ionization "
+                  "or heavy-collision settings";
             return PD_ERR_ARG;
         }
         cells += (uint64_t)b.nz * b.nr;
@@ -629,7 +644,7 @@ bool same_config(const pd_config& a, const pd_config& b) {
            a.R_ohm == b.R_ohm && a.C_farad == b.C_farad && a.beta == b.beta && a.tip_radius == b.tip_radius &&
            a.work_function == b.work_function && a.neutral_ratio == b.neutral_ratio &&
            a.neutral_T == b.neutral_T && a.poisson_tol == b.poisson_tol &&
-           a.poisson_max_cycles == b.poisson_max_cycles && a.capacity == b.capacity;
+           a.poisson_max_cycles == b.poisson_max_cycles && a.heavy_coll == b.heavy_coll && a.capacity == b.capacity;
 }
 
 struct File {
@@ -779,7 +794,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->mvx = P32(L.mvx);
     s->sorted_valid = false;
     s->partial = P32(L.partial);
-    s->nc = (uint2*)(w + L.nc);
+    s->nc = (uint4*)(w + L.nc);
     s->cand = P32(L.cand);
     s->cand_off = P32(L.cand_off);
     s->active = P32(L.active);
@@ -856,7 +871,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
         s->node_base[r] = nb;
         cb += RI.ncell;
         nb += (uint32_t)run_nodes(c);
-        kb += 2u * (uint32_t)c.nr;
+        kb += 4u * (uint32_t)c.nr;
         circ[r] = RunCircuit{c.V0, c.R_ohm, c.C_farad};
         std::memset(&rs[r], 0, sizeof(RunState));
         rs[r].V = c.V0;

@@ -548,36 +548,67 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
 // front of `active`, the others to its back, so that k_collide starts them
 // first.
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
-                                               uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+                                               uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
                                                uint32_t* big, DevState* st, KParams P) {
     const uint32_t C = P.ncell;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
+    const bool heavy_pairs = P.heavy_coll && P.heavy_step;
     for (uint32_t c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); c0 < C; c0 += stride) {
         const uint32_t c = c0 + lane;
-        uint32_t n0 = 0, n1 = 0, Ne = 0, Ncu = 0, Ni = 0;
+        uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, Ne = 0, Ncu = 0, Ni = 0;
+        int r = -1;
         if (c < C) {
             Ne = off[c + 1] - off[c];
             Ncu = off[C + c + 1] - off[C + c];
             Ni = off[2 * C + c + 1] - off[2 * C + c];
-            if (Ne > 0 && (Ncu > 0 || Ni > 0)) {
-                const RunInfo& RI = P.runs[run_of(P, c)];
+            const bool ecls = Ne > 0 && (Ncu > 0 || Ni > 0);
+            const bool hcls = heavy_pairs && Ncu > 0;
+            if (ecls || hcls) {
+                r = run_of(P, c);
+                const RunInfo& RI = P.runs[r];
                 const uint32_t lc = c - RI.cell_base;
                 const uint32_t j = lc % (uint32_t)RI.nr;
                 Stream s(lc, st->step, SID_NCAND, RI.seed, RI.run);
                 const float R0 = s.u01();
                 const float R1 = s.u01();
-                const float x0 = ((float)Ne * (float)Ncu) * ck[RI.ck_base + j] + R0;
-                const float x1 = ((float)Ne * (float)Ni) * ck[RI.ck_base + RI.nr + j] + R1;
-                n0 = (uint32_t)floorf(x0);
-                n1 = (uint32_t)floorf(x1);
+                if (ecls) {
+                    const float x0 = ((float)Ne * (float)Ncu) * ck[RI.ck_base + j] + R0;
+                    const float x1 = ((float)Ne * (float)Ni) * ck[RI.ck_base + RI.nr + j] + R1;
+                    n0 = (uint32_t)floorf(x0);
+                    n1 = (uint32_t)floorf(x1);
+                }
+                if (hcls) {
+                    // N_cu N_cu+ charge-exchange pairs, N_cu (N_cu - 1) / 2 Cu-Cu
+                    // pairs (the 1/2 is in the row factor)
+                    const float R2 = s.u01();
+                    const float R3 = s.u01();
+                    const float x2 = ((float)Ncu * (float)Ni) * ck[RI.ck_base + 2 * RI.nr + j] + R2;
+                    const float x3 = ((float)Ncu * (float)(Ncu - 1u)) * ck[RI.ck_base + 3 * RI.nr + j] + R3;
+                    n2 = (uint32_t)floorf(x2);
+                    n3 = Ncu >= 2 ? (uint32_t)floorf(x3) : 0u;
+                }
             }
-            nc[c] = make_uint2(n0, n1);
-            cand[c] = n0 + n1;
+            nc[c] = make_uint4(n0, n1, n2, n3);
+            cand[c] = n0 + n1;         // the electron classes reserve spawn slots
         }
-        const bool act = c < C && (n0 + n1) > 0;
+        // heavy candidates join the run's candidate count here (the electron
+        // classes' are summed from the spawn-slot scan)
+        const uint32_t nh = n2 + n3;
+        if (__any_sync(FULL, nh > 0)) {
+            const int r0 = __shfl_sync(FULL, r, 0);
+            if (__all_sync(FULL, nh == 0 || r == r0)) {
+                const uint32_t t = __reduce_add_sync(FULL, nh);
+                if (lane == 0) atomicAdd(&P.rs[r0].ctr[C_CAND], (unsigned long long)t);
+            } else if (nh > 0) {
+                atomicAdd(&P.rs[r].ctr[C_CAND], (unsigned long long)nh);
+            }
+        }
+        const uint32_t look_e = n0 + n1, look_cu = n0 + n2 + 2u * n3, look_ci = n1 + n2;
+        const bool act = c < C && (n0 + n1 + nh) > 0;
         const uint32_t RL = 32u * RC;
-        const bool heavy = act && (n0 + n1 > 32u || Ne > RL || (n0 > 0 && Ncu > RL) || (n1 > 0 && Ni > RL));
+        const bool heavy = act && (n0 + n1 + nh > 32u || (look_e > 0 && Ne > RL) || (look_cu > 0 && Ncu > RL) ||
+                                   (look_ci > 0 && Ni > RL));
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
         const unsigned mh = __ballot_sync(FULL, heavy), ml = __ballot_sync(FULL, act && !heavy);
@@ -590,11 +621,12 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
         if (act) {
             // the lists k_collide will rank that need a block's sort (long,
-            // with more lookups than select8 serves)
-            const uint32_t len[3] = {Ne, n0 > 0 ? Ncu : 0u, n1 > 0 ? Ni : 0u};
-            const uint32_t look[3] = {n0 + n1, n0, n1};
+            // with more lookups than select8 serves); the lookups of a list are
+            // those of every class that draws from it
+            const uint32_t len[3] = {Ne, Ncu, Ni};
+            const uint32_t look[3] = {look_e, look_cu, look_ci};
             for (uint32_t k = 0; k < 3; ++k) {
-                if (len[k] <= RANK_WARP_MAX || look[k] <= SELECT_LOOKUPS) continue;
+                if (look[k] == 0 || len[k] <= RANK_WARP_MAX || look[k] <= SELECT_LOOKUPS) continue;
                 const bool large = len[k] > RANK_MID_MAX;
                 const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
                 if (x < rank_queue_max(P.capacity, large ? RANK_MID_MAX : RANK_WARP_MAX))
@@ -649,8 +681,8 @@ __device__ __forceinline__ PairEval evaluate_pair(int k, const V3& ve, const V3&
     const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
     const float g2 = (ux * ux + uy * uy) + uz * uz;
     const float g = sqrtf(g2);
-    const float eps = g2 * cc.kmr;
-    const int ch0 = k == 0 ? CH_EL : CH_SW;
+    const float eps = g2 * (k < 2 ? cc.kmr : cc.kmr_h);
+    const int ch0 = k == 0 ? CH_EL : (k == 1 ? CH_SW : (k == 2 ? CH_CX : CH_NN));
     const int nch = k == 0 ? 4 : 1;
     float sT = 0.0f;
     for (int q = 0; q < 4; ++q) {
@@ -742,8 +774,48 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     ++cx.ev[ch];
 }
 
+// a pair whose particles are no longer what its class draws: a target
+// ionized earlier this step or, for the heavy classes, a Cu that was
+__device__ __forceinline__ bool consumed_pair(int k, uint32_t akey, uint32_t tkey) {
+    const int ts = (k == 0 || k == 3) ? SP_CU : SP_CUP;
+    const bool t_gone = (tkey & KEY_FLAG) || (int)key_species(tkey) != ts;
+    if (k < 2) return t_gone;
+    return t_gone || (akey & KEY_FLAG) || (int)key_species(akey) != SP_CU;
+}
+
+// lane-0 part of one heavy-pair candidate (classes 2 and 3: one channel
+// each, nothing spawned), the counterpart of process_candidate.  Charge
+// exchange Cu + Cu+ -> Cu+ + Cu moves the electron, not the atoms: each slot
+// keeps its species and takes the other's velocity.  Cu + Cu is elastic and
+// isotropic in the centre of mass, equal masses.
+__device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ia, uint32_t ib,
+                                   uint32_t akey, uint32_t bkey, V3 va, V3 vb, const PairEval& ev, float Racc,
+                                   const CollConsts& cc, bool accepted) {
+    if (!accepted) {
+        if (consumed_pair(k, akey, bkey)) {
+            ++cx.consumed;
+            return;
+        }
+        if (ev.sg > cc.sgmax[k]) ++cx.viol;
+        if (!(Racc * cc.sgmax[k] < ev.sg)) {
+            ++cx.nulls;
+            return;
+        }
+    }
+    if (k == 2) {
+        A.vz[ia] = vb.x; A.vr[ia] = vb.y; A.vt[ia] = vb.z;
+        A.vz[ib] = va.x; A.vr[ib] = va.y; A.vt[ib] = va.z;
+        ++cx.ev[CH_CX];
+        return;
+    }
+    binary_scatter(rs, va, vb, 0.0f, 0.5f, 0.5f, cx.fb);
+    A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
+    A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
+    ++cx.ev[CH_NN];
+}
+
 __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
-                                                 const uint2* __restrict__ nc, const uint32_t* __restrict__ cand_off,
+                                                 const uint4* __restrict__ nc, const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
                                                  long long* rho_h, const float* __restrict__ xsE,
                                                  const float* __restrict__ xs, KParams P, CollConsts cc,
@@ -774,7 +846,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             c = active[C - 1u - wl];
             wl += nwarps;
         }
-        const uint2 n = nc[c];
+        const uint4 n = nc[c];         // candidates of the classes (e,Cu), (e,Cu+), (Cu,Cu+), (Cu,Cu)
         const int r = run_of(P, c);
         const RunInfo* RI = &P.runs[r];
         const uint32_t lc = c - RI->cell_base;
@@ -802,16 +874,30 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         }
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
+        // lookups of each list over all classes (the rank-table decisions of
+        // k_ncand use the same totals)
+        const uint32_t look_e = n.x + n.y, look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
+        // the first list of a pair: electrons for the electron classes, Cu for
+        // the heavy classes (loaded over the electrons' list once those are done)
         IdList el;
-        load_ids(el, A.id, e_base, Ne, n.x + n.y, S, sbuf, lane, id_top);
-        for (int k = 0; k < 2; ++k) {
-            const uint32_t tb = (k == 0 ? C : 2 * C) + c;
+        uint32_t a_base = e_base, Na = Ne;
+        bool cu_first = false;
+        if (look_e) load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t ncand = k == 0 ? n.x : (k == 1 ? n.y : (k == 2 ? n.z : n.w));
+            if (ncand == 0) continue;
+            if (k >= 2 && !cu_first) {
+                cu_first = true;
+                a_base = off[C + c];
+                Na = off[C + c + 1] - a_base;
+                load_ids(el, A.id, a_base, Na, look_cu, S, sbuf, lane, id_top);
+            }
+            const bool cu_target = k == 0 || k == 3;
+            const uint32_t tb = (cu_target ? C : 2 * C) + c;
             const uint32_t t_base = off[tb];
             const uint32_t Nt = off[tb + 1] - t_base;
-            const uint32_t ncand = k == 0 ? n.x : n.y;
-            if (ncand == 0) continue;
             IdList tl;
-            load_ids(tl, A.id, t_base, Nt, ncand, S, sbuf, lane, id_top);
+            load_ids(tl, A.id, t_base, Nt, cu_target ? look_cu : look_ci, S, sbuf, lane, id_top);
             // candidates in batches of 32: lane q draws candidate m0 + q's pair and
             // prefetches its particles; lane 0 then applies them in order,
             // re-reading a candidate whose particles an earlier candidate of
@@ -823,8 +909,13 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 float Racc = 0.0f, Rch = 0.0f;
                 if (has) {
                     Stream rs(lc, st->step, sid_cand(k, m0 + lane), RI->seed, RI->run);
-                    i = rs.pick(Ne);
-                    j = rs.pick(Nt);
+                    i = rs.pick(Na);
+                    if (k == 3) {           // a second, different Cu
+                        j = rs.pick(Na - 1u);
+                        if (j >= i) ++j;
+                    } else {
+                        j = rs.pick(Nt);
+                    }
                     Racc = rs.u01();
                     Rch = rs.u01();
                 }
@@ -849,13 +940,14 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                         if ((uint32_t)lane == q) pt = p;
                     }
                 }
-                const bool ok = has && pe < Ne && pt < Nt;   // ids not unique: corrupt state, never index with it
+                const bool ok = has && pe < Na && pt < Nt;   // ids not unique: corrupt state, never index with it
                 if (has && !ok) set_error(st, ERR_BOUNDS);
-                const uint32_t ie = e_base + (ok ? pe : 0u), it = t_base + (ok ? pt : 0u);
-                uint32_t tkey = 0;
+                const uint32_t ie = a_base + (ok ? pe : 0u), it = t_base + (ok ? pt : 0u);
+                uint32_t tkey = 0, akey = 0;
                 V3 ve{0.0f, 0.0f, 0.0f}, vt{0.0f, 0.0f, 0.0f};
                 if (ok) {
                     tkey = A.key[it];
+                    if (k >= 2) akey = A.key[ie];
                     ve = V3{A.vz[ie], A.vr[ie], A.vt[ie]};
                     vt = V3{A.vz[it], A.vr[it], A.vt[it]};
                 }
@@ -863,18 +955,19 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 // lane 0 for a pair an earlier candidate may have changed)
                 const PairEval ev = evaluate_pair(k, ve, vt, xsE, xs, cc);
                 // dirty: shares a particle with an earlier candidate of the batch
+                // (the two particles of a (Cu, Cu) pair come from one list)
                 bool dirty = false;
                 for (uint32_t q = 0; q + 1 < nb; ++q) {
                     const uint32_t e2 = __shfl_sync(FULL, ie, (int)q), t2 = __shfl_sync(FULL, it, (int)q);
-                    if (q < (uint32_t)lane && (e2 == ie || t2 == it)) dirty = true;
+                    if (q < (uint32_t)lane && (e2 == ie || t2 == it || (k == 3 && (e2 == it || t2 == ie))))
+                        dirty = true;
                 }
                 // a candidate no earlier one of the batch touches sees the
                 // particles as prefetched: its lane takes the target and
                 // acceptance tests (the same float operations lane 0 would),
                 // and only accepted or touched candidates go through lane 0,
                 // in candidate order
-                const int ts = k == 0 ? SP_CU : SP_CUP;
-                const bool cons = (tkey & KEY_FLAG) || (int)key_species(tkey) != ts;
+                const bool cons = consumed_pair(k, akey, tkey);
                 const bool acc = !cons && Racc * cc.sgmax[k] < ev.sg;
                 const bool clean = ok && !dirty;
                 const unsigned m_cons = __ballot_sync(FULL, clean && cons);
@@ -888,10 +981,9 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 const unsigned todo = __ballot_sync(FULL, ok && (dirty || acc));
                 for (unsigned mq = todo; mq; mq &= mq - 1u) {
                     const uint32_t q = (uint32_t)(__ffs(mq) - 1);
-                    const bool okq = true;
                     const bool dq = __shfl_sync(FULL, dirty, (int)q);
                     const uint32_t ieq = __shfl_sync(FULL, ie, (int)q), itq = __shfl_sync(FULL, it, (int)q);
-                    uint32_t tkq = __shfl_sync(FULL, tkey, (int)q);
+                    uint32_t tkq = __shfl_sync(FULL, tkey, (int)q), akq = __shfl_sync(FULL, akey, (int)q);
                     V3 veq{__shfl_sync(FULL, ve.x, (int)q), __shfl_sync(FULL, ve.y, (int)q),
                            __shfl_sync(FULL, ve.z, (int)q)};
                     V3 vtq{__shfl_sync(FULL, vt.x, (int)q), __shfl_sync(FULL, vt.y, (int)q),
@@ -901,9 +993,10 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
 #pragma unroll
                     for (int e = 0; e < 4; ++e) evq.cum[e] = __shfl_sync(FULL, ev.cum[e], (int)q);
                     evq.sg = __shfl_sync(FULL, ev.sg, (int)q);
-                    if (lane == 0 && okq) {
+                    if (lane == 0) {
                         if (dq) {
                             tkq = A.key[itq];
+                            if (k >= 2) akq = A.key[ieq];
                             veq = V3{A.vz[ieq], A.vr[ieq], A.vt[ieq]};
                             vtq = V3{A.vz[itq], A.vr[itq], A.vt[itq]};
                             evq = evaluate_pair(k, veq, vtq, xsE, xs, cc);
@@ -912,8 +1005,11 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                         Stream rs(lc, st->step, sid_cand(k, m0 + q), RI->seed, RI->run);
                         rs.ctr.w = 1u;
                         rs.used = 4;
-                        process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, evq, Ra, Rc, xsE, xs, cc, st,
-                                          rho_e, rho_h, !dq);
+                        if (k < 2)
+                            process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, evq, Ra, Rc, xsE, xs, cc, st,
+                                              rho_e, rho_h, !dq);
+                        else
+                            process_heavy_pair(A, cx, rs, k, ieq, itq, akq, tkq, veq, vtq, evq, Ra, cc, !dq);
                     }
                 }
                 __syncwarp();
@@ -924,7 +1020,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         if (lane == 0) {
             RunState& rsv = P.rs[r];
             for (int q = 0; q < NCH; ++q)
-                if (cx.ev[q]) atomicAdd(&rsv.ctr[C_EV + q], (unsigned long long)cx.ev[q]);
+                if (cx.ev[q]) atomicAdd(&rsv.ctr[c_event(q)], (unsigned long long)cx.ev[q]);
             if (cx.nulls) atomicAdd(&rsv.ctr[C_NULL], (unsigned long long)cx.nulls);
             if (cx.consumed) atomicAdd(&rsv.ctr[C_CONSUMED], (unsigned long long)cx.consumed);
             if (cx.thr) atomicAdd(&rsv.ctr[C_THR], (unsigned long long)cx.thr);
@@ -1084,11 +1180,11 @@ cudaError_t collide_setup() {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_MID_SMEM);
     return e;
 }
-void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
                   uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
     k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, mid, big, st, P);
 }
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s) {

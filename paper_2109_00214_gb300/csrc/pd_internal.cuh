@@ -15,9 +15,11 @@ namespace pd {
 
 constexpr uint32_t DEAD = 0xFFFFFFFFu;
 constexpr int NSP = 5;
-constexpr int NCH = 5;
+constexpr int NCH = 7;
 constexpr int SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4;
-constexpr int CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4;
+// electron-impact channels, then the heavy pairs of heavy steps (charge
+// exchange Cu+ + Cu, elastic Cu + Cu; with heavy_coll)
+constexpr int CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6;
 
 // cross-section grid: 64 points per octave from 2^-10 eV over 25 octaves
 constexpr int XS_EMIN_EXP = -10;
@@ -30,7 +32,9 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 
 // counter slots (see PD_NCOUNTERS in pd.h)
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
-              C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, NCOUNTERS = 28;
+              C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 28, C_EV_NN = 29, NCOUNTERS = 30;
+// counter of the events of channel ch
+__host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : (ch == CH_CX ? C_EV_CX : C_EV_NN); }
 
 // Device-resident scalars shared by all runs of a simulation.
 struct DevState {
@@ -74,10 +78,11 @@ struct RunInfo {
 
 // Collision constants (float; see the host's derivation).
 struct CollConsts {
-    float kmr;                       // eps[eV] = g^2 * kmr
+    float kmr;                       // eps[eV] = g^2 * kmr (electron-heavy pairs)
+    float kmr_h;                     // the same for heavy pairs (m_r = M / 2)
     float a_e, a_t;                  // m_r / m_e, m_r / M
     float kth[NCH];                  // 2 E_th e / m_r
-    float sgmax[2];                  // NTC majorants of the two pair classes
+    float sgmax[4];                  // NTC majorants of the pair classes (e,Cu), (e,Cu+), (Cu,Cu+), (Cu,Cu)
     int di_split_mode;
 };
 
@@ -94,6 +99,7 @@ struct KParams {
     uint32_t ncell;                  // cells of all runs
     uint32_t step;
     int heavy_step;
+    int heavy_coll;                  // heavy pair classes on heavy steps
     int field_on;                    // gather E in the push
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;

@@ -67,11 +67,11 @@ constexpr uint32_t RANK_MID_MAX = 2048;
 __host__ __device__ inline uint32_t rank_queue_max(uint64_t cap, uint32_t len) { return (uint32_t)(cap / (len + 1) + 4); }
 // shared-memory attribute of the rank-table kernels (once per process and device)
 cudaError_t collide_setup();
-void launch_ncand(const uint32_t* off, const float* ck, uint2* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
                   uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s);
 // B: the other particle buffer, used as scratch (free until the next scatter)
 // the two rank-table kernels, then k_collide (three launches)
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint2* nc,
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s);

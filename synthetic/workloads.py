@@ -237,6 +237,28 @@ def rate_cell(n_e=200000, n_t=100000, Te_eV=10.0, seed=3, depth=1e-6, dt=1e-15,
     return cfg, concat_loads([le, lt])
 
 
+def heavy_cells(n_e=3000, n_cu=6000, n_cup=1500, ncells=4, Te_eV=30.0, T_heavy=2000.0, seed=9,
+                coll_scale=1.0, heavy_coll=1, depth=1e-6, dt=1e-15, capacity=1 << 21):
+    """Dense Cartesian cells (a 2 x ncells grid, the second row empty) of
+    Maxwellian electrons at Te and Maxwellian Cu and Cu+ at T_heavy, spread
+    uniformly over the first row's cells: every step is a heavy step, so the
+    heavy-particle pair classes run beside the electron ones.  The capacity
+    leaves room for the slots that candidates of the electron classes reserve
+    (two each, per step)."""
+    rng = np.random.default_rng(seed)
+    d = 50e-9
+    ve = math.sqrt(Te_eV * _QE / _ME)
+    vh = math.sqrt(_KB * T_heavy / _MCU)
+    loads = []
+    for sp, n, vs in ((0, n_e, ve), (1, n_cu, vh), (2, n_cup, vh)):
+        loads.append(_load(np.zeros(n, np.int64), rng.integers(0, ncells, n), rng, vs, sp))
+    cfg = base_config(geometry="xy_periodic", nz=2, nr=max(2, ncells), dz=d, dr=d, depth=depth,
+                      dt=dt, heavy_subcycle=1, weight=100.0, seed=seed, field_on=0,
+                      inject_on=0, coll_dt_scale=coll_scale, heavy_coll=heavy_coll,
+                      capacity=capacity, max_cand_per_step=1 << 22)
+    return cfg, concat_loads(loads)
+
+
 ENSEMBLE_GRIDS = (64, 96, 128, 192, 256)
 ENSEMBLE_VOLTS_KV = (2.0, 3.0, 4.0, 5.0, 6.0, 7.0, 8.0, 10.0)
 

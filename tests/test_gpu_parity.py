@@ -117,6 +117,48 @@ def test_microbench_di_off(pd, xs):
     assert_same_particles(sim.particles(), o.particles())
 
 
+@pytest.mark.parametrize("kw,steps", [
+    # about 1500 Cu / 375 Cu+ per cell: block-sorted Cu tables, warp-sorted Cu+ tables
+    (dict(n_e=3000, n_cu=6000, n_cup=1500, ncells=4, coll_scale=3000.0), 3),
+    # one cell of 20000 Cu: the Cu table sorted by a block in the scratch buffers
+    (dict(n_e=1000, n_cu=20000, n_cup=2000, ncells=1, coll_scale=100.0), 3),
+    # 200 Cu per cell and many (Cu, Cu) candidates: register-cached lists,
+    # candidates of one batch sharing particles
+    (dict(n_e=200, n_cu=800, n_cup=200, ncells=4, coll_scale=30000.0), 3),
+    # no electrons, a couple of heavy candidates per step: digit-by-digit selects
+    (dict(n_e=0, n_cu=20000, n_cup=2000, ncells=1, coll_scale=0.003), 6),
+    (dict(n_e=0, n_cu=6000, n_cup=1500, ncells=4, coll_scale=3.0), 4),
+])
+def test_heavy_pairs_bit_exact(pd, xs, kw, steps):
+    """The heavy-particle pair classes (charge exchange Cu + Cu+, elastic
+    Cu + Cu) beside the electron classes, on every step: the same pairs,
+    acceptances and post-collision velocities as the oracle."""
+    cfg, parts = synthetic.heavy_cells(**kw)
+    sim, o = run_pair(pd, cfg, parts, xs, steps)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["cand_total"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
+@pytest.mark.parametrize("nz,nr,total,scale,steps", [
+    (64, 64, 2e5, 3000.0, 4),
+    (32, 32, 1e5, 3e5, 3),         # about a thousand candidates per cell and step
+])
+def test_microbench_heavy_pairs_bit_exact(pd, xs, nz, nr, total, scale, steps):
+    cfg, parts = synthetic.microbench(nz=nz, nr=nr, total=total, coll_scale=scale, seed=11)
+    cfg["heavy_coll"] = 1
+    cfg["capacity"] = max(cfg["capacity"], 1 << 22)   # two spawn slots per electron-class candidate
+    sim, o = run_pair(pd, cfg, parts, xs, steps)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["ev_cx"] > 0 and gc["ev_nn"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+    ge, gh = sim.rho()
+    oe, oh = o.rho()
+    assert np.array_equal(ge, oe) and np.array_equal(gh, oh)
+
+
 def _rz_field(n, V0, seed=3):
     rng = np.random.default_rng(seed)
     Ez = np.full((n + 1, n + 1), -V0 / 6e-6) * (1 + 0.3 * rng.uniform(-1, 1, (n + 1, n + 1)))
