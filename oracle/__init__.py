@@ -47,6 +47,7 @@ class _Cfg(C.Structure):
         ("beta", C.c_double), ("tip_radius", C.c_double), ("work_function", C.c_double),
         ("neutral_ratio", C.c_double), ("neutral_T", C.c_double),
         ("poisson_tol", C.c_double), ("capacity", C.c_int64), ("heavy_coll", C.c_int32),
+        ("charge_max", C.c_int32),
     ]
 
 
@@ -108,8 +109,8 @@ def _dptr(a):
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
-                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI")]
-                 + ["ev_cx", "ev_nn"])
+                    for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4"])
 SCALAR_NAMES = ["t", "V", "I_gap", "gamma", "Qbar", "erosion", "mass", "charge", "sgmax0",
                 "sgmax1", "poisson_relres", "poisson_iters", "E_abs_cathode", "E_abs_anode",
                 "E_abs_wall"]
@@ -152,6 +153,7 @@ class Oracle:
         c.poisson_tol = cfg.get("oracle_poisson_tol", 1e-11)
         c.capacity = cfg["capacity"]
         c.heavy_coll = cfg.get("heavy_coll", 0)
+        c.charge_max = cfg.get("charge_max", 2)
         self._c = c
         self.h = self.L.or_create(C.byref(c))
         rz = c.geom == 0
@@ -177,6 +179,8 @@ class Oracle:
         ir = np.ascontiguousarray(parts["ir"], np.int32)
         arr = [np.ascontiguousarray(parts[k], np.float64) for k in ("pz", "pr", "vz", "vr", "vt")]
         r = self.L.or_load(self.h, n, _ptr(sp), _ptr(iz), _ptr(ir), *[_dptr(a) for a in arr])
+        if r == -2:
+            raise ValueError("species code above the configured highest charge")
         if r < 0:
             raise RuntimeError("oracle capacity exceeded")
 

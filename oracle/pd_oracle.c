@@ -60,12 +60,17 @@ static const double KB = 1.380649e-23;
 #define M_CU (63.546 * AMU)
 static const double PI = 3.14159265358979323846;
 
-enum { SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4, NSP = 5 };
+/* Cu3+ and Cu4+ are the higher charge states Sec. 2.3 tracks; they exist   */
+/* only with charge_max 3 or 4                                             */
+enum { SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4, SP_CU3 = 5, SP_CU4 = 6, NSP = 7 };
 /* channels 5 and 6 are the heavy-particle collisions the paper lists     */
 /* besides ionization (Sec. 2.3): charge exchange Cu+ + Cu and elastic    */
-/* Cu + Cu; off unless heavy_coll is set                                  */
-enum { CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6, NCH = 7 };
-static const int ZQ[NSP] = {-1, 0, 1, 2, 2};
+/* Cu + Cu; off unless heavy_coll is set.  Channels 7 and 8 are the       */
+/* step-wise ionizations Cu2+ -> Cu3+ and Cu3+ -> Cu4+ (Sec. 2.3), on      */
+/* with charge_max >= 3 and 4                                             */
+enum { CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6, CH_S3 = 7, CH_S4 = 8,
+       NCH = 9 };
+static const int ZQ[NSP] = {-1, 0, 1, 2, 2, 3, 4};
 
 /* cross-section grid (must be the grid the inputs are tabulated on) */
 #define XS_EMIN_EXP (-10)
@@ -91,6 +96,7 @@ typedef struct {
     double poisson_tol;
     int64_t capacity;
     int32_t heavy_coll;    /* heavy-particle pair classes (charge exchange, Cu-Cu elastic) on */
+    int32_t charge_max;    /* highest ion charge: 2 (Cu2+), 3 (+ Cu2+ -> Cu3+), 4 (+ Cu3+ -> Cu4+) */
 } or_cfg;
 
 typedef struct {
@@ -113,7 +119,7 @@ typedef struct {
     float xsE[XS_N];
     real xs[NCH][XS_N];
     double eth[NCH];
-    real sgmax[4];
+    real sgmax[7];
     /* counters */
     uint64_t events[NCH], nulls, consumed, thr_rej, ratio_viol, iso_fallback, cand_total;
     uint64_t absorbed[3][NSP];   /* cathode, anode, outer wall */
@@ -248,11 +254,17 @@ static real xs_lookup(const or_sim* S, int ch, real eps) {
     return S->xs[ch][k] + t * (S->xs[ch][k + 1] - S->xs[ch][k]);
 }
 
-/* pair classes: (e, Cu), (e, Cu+), then, on heavy steps with heavy_coll,
+/* pair classes, in the order a cell applies them: the electron classes
+ * (e, Cu), (e, Cu+), (e, Cu2+ SW), (e, Cu2+ DI), (e, Cu3+) (the last three
+ * with charge_max >= 3, 3, 4), then, on heavy steps with heavy_coll,
  * (Cu, Cu+) charge exchange and (Cu, Cu) elastic */
-static const int CLASS_CH0[4] = {CH_EL, CH_SW, CH_CX, CH_NN};
-static const int CLASS_NCH[4] = {4, 1, 1, 1};
-static const int CLASS_TARGET[4] = {SP_CU, SP_CUP, SP_CUP, SP_CU};
+#define NCLS 7
+#define NECLS 5
+static const int CLASS_CH0[NCLS] = {CH_EL, CH_SW, CH_S3, CH_S3, CH_S4, CH_CX, CH_NN};
+static const int CLASS_NCH[NCLS] = {4, 1, 1, 1, 1, 1, 1};
+static const int CLASS_TARGET[NCLS] = {SP_CU, SP_CUP, SP_CU2_SW, SP_CU2_DI, SP_CU3, SP_CUP, SP_CU};
+/* highest ion charge a class needs */
+static const int CLASS_QMAX[NCLS] = {2, 2, 3, 3, 4, 2, 2};
 
 static double mr_class(void) { return ME * M_CU / (ME + M_CU); }
 static real kmr(void) { return R_(0.5 * mr_class() / QE); } /* eps[eV] = g^2 * kmr */
@@ -264,8 +276,8 @@ static real kmr_heavy(void) { return R_(0.5 * (0.5 * M_CU) / QE); }
  * end, so max_k max(sT_k, sT_k+1) * g(E_k+1) bounds sigma_T(eps) g(eps); a
  * relative margin of 1e-6 covers float rounding. */
 static void compute_sgmax(or_sim* S) {
-    for (int k = 0; k < 4; ++k) {
-        double kd = (double)(k < 2 ? kmr() : kmr_heavy());
+    for (int k = 0; k < NCLS; ++k) {
+        double kd = (double)(k < NECLS ? kmr() : kmr_heavy());
         double best = 0.0;
         real sT_prev = 0;
         for (int q = 0; q < XS_N; ++q) {
@@ -354,6 +366,9 @@ int or_set_xs(or_sim* S, int ch, const double* E, const double* sig, int n, doub
 int64_t or_load(or_sim* S, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
                 const double* pz, const double* pr, const double* vz, const double* vr, const double* vt) {
     if (S->n + n > S->cap) return -1;
+    /* species codes beyond the configured highest charge are refused */
+    for (int64_t q = 0; q < n; ++q)
+        if (sp[q] >= NSP || ZQ[sp[q]] > S->c.charge_max) return -2;
     for (int64_t q = 0; q < n; ++q) {
         int64_t p = S->n + q;
         S->sp[p] = sp[q]; S->iz[p] = iz[q]; S->ir[p] = ir[q];
@@ -627,7 +642,10 @@ static int collide_event(or_sim* S, stream_t* st, int ch, int64_t ie, int64_t it
     vec3 e2 = vt;
     /* Stage 3, Eq. (14): e1 + e2 elastic, equal masses (m_r/m = 1/2) */
     binary_scatter(S, st, &ve, &e2, R_(0), R_(0.5), R_(0.5));
-    int new_sp = ch == CH_SI ? SP_CUP : (ch == CH_SW ? SP_CU2_SW : SP_CU2_DI);
+    int new_sp = ch == CH_SI ? SP_CUP
+               : ch == CH_SW ? SP_CU2_SW
+               : ch == CH_DI ? SP_CU2_DI
+               : ch == CH_S3 ? SP_CU3 : SP_CU4;
     int dz = ZQ[new_sp] - ZQ[S->sp[it]];
     int nspawn = 0;
     vec3 e_keep = ve;
@@ -741,8 +759,9 @@ static int collide_all(or_sim* S, int heavy_step) {
         if (cnt[b + 1] - cnt[b] > 1) qsort(rec + cnt[b], cnt[b + 1] - cnt[b], sizeof(idrec), cmp_id);
 
     /* candidate counts per cell and their prefix sum (spawn id slots: the
-     * electron classes only; heavy pairs spawn nothing) */
-    uint32_t* nc = (uint32_t*)calloc(4 * C, 4);
+     * electron classes only; heavy pairs spawn nothing).  The cell's stream
+     * gives R_k to class k, k = 0..6, whether the class is on or not. */
+    uint32_t* nc = (uint32_t*)calloc(NCLS * C, 4);
     uint64_t total = 0, heavy_total = 0;
     uint64_t* pre = (uint64_t*)malloc((C + 1) * 8);
     double dtc = S->c.dt * S->c.coll_dt_scale;
@@ -756,27 +775,28 @@ static int collide_all(or_sim* S, int heavy_step) {
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
         uint32_t Ncu = (uint32_t)(cnt[SP_CU * C + c + 1] - cnt[SP_CU * C + c]);
         uint32_t Ni = (uint32_t)(cnt[SP_CUP * C + c + 1] - cnt[SP_CUP * C + c]);
-        for (int k = 0; k < 2; ++k) {
+        real R[NCLS];
+        for (int k = 0; k < NCLS; ++k) R[k] = u01(&st);
+        for (int k = 0; k < NECLS; ++k) {
+            if (CLASS_QMAX[k] > S->c.charge_max) continue;
             int ts = CLASS_TARGET[k];
             uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
             real ck = R_(S->c.weight * (double)S->sgmax[k] * dtc / cell_volume(S, j));
-            real R = u01(&st);
-            real x = ((real)Ne * (real)Nt) * ck + R;
-            nc[4 * c + k] = (uint32_t)OR_FLOOR(x);
+            real x = ((real)Ne * (real)Nt) * ck + R[k];
+            nc[NCLS * c + k] = (uint32_t)OR_FLOOR(x);
+            total += nc[NCLS * c + k];
         }
         if (heavy) {
             /* N_cu N_cu+ pairs for charge exchange, N_cu (N_cu - 1) / 2 for Cu-Cu */
-            real ck2 = R_(S->c.weight * (double)S->sgmax[2] * dth / cell_volume(S, j));
-            real ck3 = R_(0.5 * S->c.weight * (double)S->sgmax[3] * dth / cell_volume(S, j));
-            real R2 = u01(&st), R3 = u01(&st);
-            real x2 = ((real)Ncu * (real)Ni) * ck2 + R2;
-            real x3 = ((real)Ncu * (real)(Ncu > 0 ? Ncu - 1 : 0)) * ck3 + R3;
-            nc[4 * c + 2] = (uint32_t)OR_FLOOR(x2);
-            nc[4 * c + 3] = (uint32_t)OR_FLOOR(x3);
-            if (Ncu < 2) nc[4 * c + 3] = 0;
-            heavy_total += nc[4 * c + 2] + nc[4 * c + 3];
+            real ck5 = R_(S->c.weight * (double)S->sgmax[5] * dth / cell_volume(S, j));
+            real ck6 = R_(0.5 * S->c.weight * (double)S->sgmax[6] * dth / cell_volume(S, j));
+            real x5 = ((real)Ncu * (real)Ni) * ck5 + R[5];
+            real x6 = ((real)Ncu * (real)(Ncu > 0 ? Ncu - 1 : 0)) * ck6 + R[6];
+            nc[NCLS * c + 5] = (uint32_t)OR_FLOOR(x5);
+            nc[NCLS * c + 6] = (uint32_t)OR_FLOOR(x6);
+            if (Ncu < 2) nc[NCLS * c + 6] = 0;
+            heavy_total += nc[NCLS * c + 5] + nc[NCLS * c + 6];
         }
-        total += nc[4 * c] + nc[4 * c + 1];
     }
     pre[C] = total;
     S->cand_total += total + heavy_total;
@@ -789,11 +809,11 @@ static int collide_all(or_sim* S, int heavy_step) {
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
         const idrec* cul = rec + cnt[SP_CU * C + c];
         uint32_t Ncu = (uint32_t)(cnt[SP_CU * C + c + 1] - cnt[SP_CU * C + c]);
-        for (int k = 0; k < 2 && !err; ++k) {
+        for (int k = 0; k < NECLS && !err; ++k) {
             int ts = CLASS_TARGET[k];
             const idrec* tl = rec + cnt[ts * C + c];
             uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
-            for (uint32_t m = 0; m < nc[4 * c + k]; ++m) {
+            for (uint32_t m = 0; m < nc[NCLS * c + k]; ++m) {
                 stream_t st;
                 stream_init(&st, S, (uint32_t)c, S->step, SID_CAND(k, m));
                 uint32_t i = pick(&st, Ne), jt = pick(&st, Nt);
@@ -828,18 +848,18 @@ static int collide_all(or_sim* S, int heavy_step) {
                 S->events[ch]++;
             }
         }
-        /* heavy pairs, classes 2 (Cu from the Cu list, Cu+ from the Cu+ list) and
-         * 3 (two different Cu of the Cu list); a particle whose species changed
+        /* heavy pairs, classes 5 (Cu from the Cu list, Cu+ from the Cu+ list) and
+         * 6 (two different Cu of the Cu list); a particle whose species changed
          * this step (ionized) is consumed */
-        for (int k = 2; k < 4 && heavy && !err; ++k) {
+        for (int k = NECLS; k < NCLS && heavy && !err; ++k) {
             int ts = CLASS_TARGET[k];
             const idrec* tl = rec + cnt[ts * C + c];
             uint32_t Nt = (uint32_t)(cnt[ts * C + c + 1] - cnt[ts * C + c]);
-            for (uint32_t m = 0; m < nc[4 * c + k]; ++m) {
+            for (uint32_t m = 0; m < nc[NCLS * c + k]; ++m) {
                 stream_t st;
                 stream_init(&st, S, (uint32_t)c, S->step, SID_CAND(k, m));
                 uint32_t i = pick(&st, Ncu), jt;
-                if (k == 2) jt = pick(&st, Nt);
+                if (k == 5) jt = pick(&st, Nt);
                 else {          /* a second, different Cu */
                     jt = pick(&st, Ncu - 1);
                     if (jt >= i) jt++;
@@ -854,7 +874,7 @@ static int collide_all(or_sim* S, int heavy_step) {
                 real sg = xs_lookup(S, CLASS_CH0[k], g2 * kmh) * g;
                 if (sg > S->sgmax[k]) S->ratio_viol++;
                 if (!(Racc * S->sgmax[k] < sg)) { S->nulls++; continue; }
-                if (k == 2) {
+                if (k == 5) {
                     /* resonant charge exchange: the electron moves to the ion, the
                      * velocities stay with the atoms: the Cu+ slot takes the Cu's
                      * velocity and the Cu slot the ion's */
@@ -1153,9 +1173,10 @@ void or_get_field(const or_sim* S, double* Ez, double* Er) {
     for (int64_t k = 0; k < nn; ++k) { Ez[k] = S->Ez[k]; Er[k] = S->Er[k]; }
 }
 
-/* counters: events[5] of the electron channels, nulls, consumed, thr_rej,
+/* counters: events[5] of the channels 0-4, nulls, consumed, thr_rej,
  * ratio_viol, iso_fallback, cand_total, emitted_e, emitted_cu,
- * absorbed[3][5], then events of charge exchange and Cu-Cu elastic */
+ * absorbed[3][7], then events of charge exchange, Cu-Cu elastic,
+ * Cu2+ -> Cu3+ and Cu3+ -> Cu4+ */
 void or_get_counters(const or_sim* S, uint64_t* out) {
     int k = 0;
     for (int c = 0; c < CH_CX; ++c) out[k++] = S->events[c];
@@ -1164,6 +1185,7 @@ void or_get_counters(const or_sim* S, uint64_t* out) {
     out[k++] = S->emitted_e; out[k++] = S->emitted_cu;
     for (int e = 0; e < 3; ++e) for (int s = 0; s < NSP; ++s) out[k++] = S->absorbed[e][s];
     out[k++] = S->events[CH_CX]; out[k++] = S->events[CH_NN];
+    out[k++] = S->events[CH_S3]; out[k++] = S->events[CH_S4];
 }
 
 /* scalars: t, V, I_gap, gamma, Qbar, erosion (kg/C), mass ledger (kg),
@@ -1171,10 +1193,15 @@ void or_get_counters(const or_sim* S, uint64_t* out) {
 void or_get_scalars(const or_sim* S, double* out) {
     uint64_t N[NSP] = {0};
     for (int64_t p = 0; p < S->n; ++p) N[S->sp[p]]++;
-    double Nq[3] = {(double)N[SP_CU], (double)N[SP_CUP], (double)(N[SP_CU2_SW] + N[SP_CU2_DI])};
-    double ions = Nq[1] + Nq[2], all = Nq[0] + ions;
-    double gamma = all > 0 ? ions / all : 0.0;               /* Eq. (21) */
-    double qbar = ions > 0 ? (Nq[1] + 2.0 * Nq[2]) / ions : 0.0;
+    /* Eq. (21) over the heavy species: ionization degree and mean ion charge */
+    double ions = 0, qsum = 0;
+    for (int s = SP_CUP; s < NSP; ++s) {
+        ions += (double)N[s];
+        qsum += (double)ZQ[s] * (double)N[s];
+    }
+    double all = (double)N[SP_CU] + ions;
+    double gamma = all > 0 ? ions / all : 0.0;
+    double qbar = ions > 0 ? qsum / ions : 0.0;
     double heavy_back = 0;
     for (int s = 1; s < NSP; ++s) heavy_back += (double)S->absorbed[0][s];
     double mass = M_CU * S->c.weight * ((double)S->emitted_cu - heavy_back);

@@ -52,13 +52,15 @@ def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.
     the paper lists without data: 5 resonant charge exchange Cu+ + Cu,
     sigma = s_cx (1 - k ln(E / 1 eV))^2 (the Rapp-Francis shape), and 6
     elastic Cu + Cu, a hard sphere pi d^2 (E: relative energy in the centre
-    of mass, eV).
+    of mass, eV); 7 step-wise Cu2+ -> Cu3+ and 8 Cu3+ -> Cu4+ (Lotz, with the
+    third and fourth ionization energies of Cu, 36.841 and 57.38 eV, which
+    the paper does not give).
     Thresholds: DI about 28 eV and Cu+->Cu2+ 20.3 eV are the paper's (Sec. 3.2);
     7.726 eV (first ionization energy of Cu) and 3.8 eV (excitation) are not
     given by the paper.
     """
-    th = {1: 3.8, 2: 7.726, 3: 28.0, 4: 20.3}
-    pk = {1: 1.0e-20, 2: 3.0e-20, 3: 1.0e-21, 4: 1.5e-20}
+    th = {1: 3.8, 2: 7.726, 3: 28.0, 4: 20.3, 7: 36.841, 8: 57.38}
+    pk = {1: 1.0e-20, 2: 3.0e-20, 3: 1.0e-21, 4: 1.5e-20, 7: 8.0e-21, 8: 5.0e-21}
     if thresholds:
         th.update(thresholds)
     if peaks:
@@ -67,7 +69,7 @@ def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.
     out = {}
     s_el = np.where(E <= e_el, sigma_el, sigma_el * np.sqrt(e_el / np.maximum(E, 1e-300)))
     out[0] = (E, s_el, 0.0)
-    for c in (1, 2, 3, 4):
+    for c in (1, 2, 3, 4, 7, 8):
         I = th[c]
         x = E / I
         s = np.where(x > 1.0, pk[c] * math.e * np.log(np.maximum(x, 1.0)) / x, 0.0)

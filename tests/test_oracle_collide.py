@@ -25,7 +25,7 @@ QE = 1.602176634e-19
 ME = 9.1093837015e-31
 MCU = 63.546 * 1.66053906660e-27
 MR = ME * MCU / (ME + MCU)
-TH = {0: 0.0, 1: 3.8, 2: 7.726, 3: 28.0, 4: 20.3}
+TH = {0: 0.0, 1: 3.8, 2: 7.726, 3: 28.0, 4: 20.3, 7: 36.841, 8: 57.38}
 
 
 @pytest.fixture(scope="module")
@@ -40,12 +40,12 @@ def _ke(m, v):
     return 0.5 * m * float(np.dot(v, v))
 
 
-@pytest.mark.parametrize("ch", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("ch", [0, 1, 2, 3, 4, 7, 8])
 def test_event_conservation(o64, ch):
     rng = np.random.default_rng(10 + ch)
     ok = 0
     for trial in range(400):
-        ve = rng.normal(0, 4e6, 3)
+        ve = rng.normal(0, 6e6 if ch in (7, 8) else 4e6, 3)
         vt = rng.normal(0, 800.0, 3)
         r = o64.event(ch, ve, vt, subject=trial, step=7, sid=ch)
         if r is None:
@@ -130,24 +130,28 @@ def test_mcc_reduction_rates_match_closed_form(xs):
     N_e n_t <sigma v> dt_coll.  Each trial is a fresh Maxwellian load (so the
     electron distribution does not drift), with a per-electron collision
     probability of a few percent."""
-    params = dict(sigma_el=5e-20, e_el=10.0, peaks={1: 1e-20, 2: 3e-20, 3: 1e-21, 4: 1.5e-20})
+    params = dict(sigma_el=5e-20, e_el=10.0, peaks={1: 1e-20, 2: 3e-20, 3: 1e-21, 4: 1.5e-20, 7: 8e-21, 8: 5e-21})
     Te = 25.0
     n_e, n_t = 100000, 200000
     trials = 12
-    counts = np.zeros(5)
-    expect = np.zeros(5)
+    counts = np.zeros(9)
+    expect = np.zeros(9)
     # each pair class on its own (within one step the (e, Cu+) class sees the
-    # electrons the (e, Cu) class has already scattered)
-    for target, chans in ((1, (0, 1, 2, 3)), (2, (4,))):
-        for tr in range(trials):
+    # electrons the (e, Cu) class has already scattered); the step-wise
+    # classes of Cu2+ (either label) and Cu3+ with charge_max = 4
+    for target, chans in ((1, (0, 1, 2, 3)), (2, (4,)), (3, (7,)), (4, (7,)), (5, (8,))):
+        for tr in range(trials if target < 3 else trials // 2):
             cfg, parts = synthetic.rate_cell(n_e=n_e, n_t=n_t, Te_eV=Te, seed=100 + tr + 50 * target,
-                                             depth=1e-4, coll_scale=4.0, target_species=target)
+                                             depth=1e-4, coll_scale=4.0 if target < 3 else 16.0,
+                                             target_species=target)
+            cfg["charge_max"] = 4
             o = oracle.Oracle(cfg, fp64=True)
             o.set_cross_sections(xs)
             o.load(parts)
             o.step(1)
             c = o.counters()
-            ev = [c["ev_el"], c["ev_exc"], c["ev_si"], c["ev_di"], c["ev_sw"]]
+            ev = [c["ev_el"], c["ev_exc"], c["ev_si"], c["ev_di"], c["ev_sw"], c["ev_cx"], c["ev_nn"],
+                  c["ev_s3"], c["ev_s4"]]
             V = o.cell_volume(0)
             dtc = cfg["dt"] * cfg["coll_dt_scale"]
             nt = n_t * cfg["weight"] / V
@@ -155,7 +159,7 @@ def test_mcc_reduction_rates_match_closed_form(xs):
                 counts[ch] += ev[ch]
                 expect[ch] += n_e * nt * _maxwell_rate(ch, Te, params) * dtc
             assert c["ratio_viol"] == 0
-    for ch in range(5):
+    for ch in (0, 1, 2, 3, 4, 7, 8):
         sig = math.sqrt(expect[ch])
         # 3 sigma Poisson band plus 1 % for the in-step depletion of targets
         # and the few electrons that collide twice in a step
@@ -241,3 +245,51 @@ def test_ncand_mean_matches_ntc_formula(xs):
     got = o.counters()["cand_total"]
     # floor(x + R) - x is uniform on (-1, 1] per cell: variance <= 1/4 per term
     assert abs(got - mean) < 4 * math.sqrt(2 * ncell / 4)
+
+
+@pytest.mark.parametrize("charge_max", [2, 3, 4])
+def test_stepwise_charge_states_balance(xs, charge_max):
+    """The step-wise channels Cu2+ -> Cu3+ and Cu3+ -> Cu4+ (Sec. 2.3): charge
+    conserved exactly, each event moves one ion up one charge state and adds
+    one electron, and the channels beyond charge_max never fire."""
+    cfg, parts = synthetic.microbench(nz=16, nr=16, total=3e4, coll_scale=20000.0, seed=3)
+    cfg["charge_max"] = charge_max
+    rng = np.random.default_rng(2)
+    sp = parts["species"].copy()
+    pick = rng.permutation(np.flatnonzero(sp == 2))[: int((sp == 2).sum()) // 2]
+    sp[pick[0::3]] = 3
+    sp[pick[1::3]] = 4
+    if charge_max >= 3:
+        sp[pick[2::3]] = 5
+    parts = dict(parts, species=sp)
+    o = oracle.Oracle(cfg, fp64=False)
+    o.set_cross_sections(xs)
+    o.load(parts)
+    o.prime()
+    zq = np.array([-1, 0, 1, 2, 2, 3, 4])
+    q0 = int(zq[sp].sum())
+    o.step(4)
+    p = o.particles()
+    c = o.counters()
+    assert int(zq[p["species"]].sum()) == q0
+    n0 = np.bincount(sp, minlength=7)
+    n1 = np.bincount(p["species"], minlength=7)
+    assert n1[6] - n0[6] == c["ev_s4"]
+    assert n1[5] - n0[5] == c["ev_s3"] - c["ev_s4"]
+    assert (n1[3] + n1[4]) - (n0[3] + n0[4]) == c["ev_sw"] + c["ev_di"] - c["ev_s3"]
+    assert n1[0] - n0[0] == c["ev_si"] + c["ev_sw"] + 2 * c["ev_di"] + c["ev_s3"] + c["ev_s4"]
+    assert c["ev_s3"] == 0 if charge_max < 3 else c["ev_s3"] > 0
+    assert c["ev_s4"] == 0 if charge_max < 4 else c["ev_s4"] > 0
+    re, rh = o.rho()
+    assert int(re.sum() + rh.sum()) == q0 * 2 ** 32
+    sc = o.scalars()
+    ions = n1[2:].sum()
+    assert sc["Qbar"] == pytest.approx((zq[2:] * n1[2:]).sum() / ions, rel=1e-15)   # Eq. (21)
+    assert sc["gamma"] == pytest.approx(ions / n1[1:].sum(), rel=1e-15)
+
+
+def test_species_above_charge_max_refused(xs):
+    cfg, parts = synthetic.rate_cell(n_e=10, n_t=10, target_species=5)
+    o = oracle.Oracle(cfg, fp64=True)
+    with pytest.raises(ValueError):
+        o.load(parts)
