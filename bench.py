@@ -286,7 +286,7 @@ def run_ensemble(args, ws, rank, local):
     keys = ("species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
 
     def counts(get):
-        c = np.zeros(5)
+        c = np.zeros(7)
         for r in range(R):
             c += np.array(get(r)["count"], dtype=np.float64)
         return c

@@ -52,14 +52,19 @@ typedef enum {
 
 enum { PD_GEOM_RZ = 0, PD_GEOM_XY_PERIODIC = 1 };
 enum { PD_FIELD_NONE = 0, PD_FIELD_POISSON = 1, PD_FIELD_EXTERNAL = 2 };
-enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI = 4, PD_NSP = 5 };
+/* species: Cu2+ carries the label of its route (step-wise or double
+ * ionization, Sec. 2.3); Cu3+ and Cu4+ exist only with charge_max 3 and 4 */
+enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI = 4, PD_SP_CU3 = 5,
+       PD_SP_CU4 = 6, PD_NSP = 7 };
 /* channels 5 and 6: the heavy pairs the paper lists besides ionization
  * (Sec. 2.3, no data given): resonant charge exchange Cu+ + Cu and elastic
- * Cu + Cu, with E the relative energy in the centre of mass */
+ * Cu + Cu, with E the relative energy in the centre of mass; channels 7 and
+ * 8: the step-wise ionizations Cu2+ -> Cu3+ (either Cu2+ label) and
+ * Cu3+ -> Cu4+ (Sec. 2.3) */
 enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4,
-       PD_CH_CX = 5, PD_CH_NN = 6, PD_NCH = 7 };
+       PD_CH_CX = 5, PD_CH_NN = 6, PD_CH_S3 = 7, PD_CH_S4 = 8, PD_NCH = 9 };
 
-#define PD_CONFIG_VERSION 1u
+#define PD_CONFIG_VERSION 2u
 
 /* Run parameters (Sec. 2.3 gives: 50 nm cells, 1 fs electron step, heavy step
  * ten times longer, W = 100, 2.9 kV through R = 1 kOhm with C = 1 pF, a 200 nm
@@ -87,6 +92,10 @@ typedef struct pd_config {
     int32_t heavy_coll;        /* 1: on heavy steps, the heavy pair classes (Cu+, Cu)
                                   charge exchange and (Cu, Cu) elastic, NTC with the
                                   heavy step; 0 (default): off */
+    int32_t charge_max;        /* highest ion charge: 2 (default), 3 (adds the pair
+                                  classes (e, Cu2+) -> Cu3+), 4 (and (e, Cu3+) -> Cu4+);
+                                  species above it are refused on load */
+    int32_t reserved0;         /* 0 */
     int64_t capacity;          /* particle slots */
 } pd_config;
 
@@ -96,7 +105,7 @@ typedef struct pd_scalars {
     double t;                  /* simulated time (s) */
     double V;                  /* anode voltage (V) */
     double I_gap;              /* gap current of the last step (A) */
-    double gamma;              /* ionization degree, Eq. (21), q <= 2 */
+    double gamma;              /* ionization degree, Eq. (21), all ion charges */
     double Qbar;               /* mean ion charge, Eq. (21) */
     double erosion;            /* cathode erosion: net Cu mass / charge (kg/C) */
     double mass;               /* net Cu mass leaving the cathode (kg) */
@@ -112,13 +121,13 @@ typedef struct pd_scalars {
     int64_t step;              /* electron steps taken */
 } pd_scalars;
 
-/* counters: events per electron-impact channel [5], null candidates,
- * candidates whose target (or, for heavy pairs, either particle) was already
- * ionized this step, accepted candidates below threshold, NTC majorant
- * violations, isotropic-sampling fallbacks, candidates in total, electrons
- * emitted, neutrals emitted, absorbed [electrode 3][species 5], charge
- * exchange events, Cu-Cu elastic events. */
-#define PD_NCOUNTERS 30
+/* counters: events of channels 0-4 [5], null candidates, candidates whose
+ * target (or, for heavy pairs, either particle) was already ionized this
+ * step, accepted candidates below threshold, NTC majorant violations,
+ * isotropic-sampling fallbacks, candidates in total, electrons emitted,
+ * neutrals emitted, absorbed [electrode 3][species 7], then events of charge
+ * exchange, Cu-Cu elastic, Cu2+ -> Cu3+ and Cu3+ -> Cu4+. */
+#define PD_NCOUNTERS 38
 
 typedef struct pd_sim pd_sim;
 

@@ -37,7 +37,7 @@ constexpr double AMU = 1.66053906660e-27;
 constexpr double M_CU = 63.546 * AMU;
 constexpr double KB = 1.380649e-23;
 constexpr double PI = 3.14159265358979323846;
-constexpr int ZQ[NSP] = {-1, 0, 1, 2, 2};
+constexpr int ZQ[NSP] = {-1, 0, 1, 2, 2, 3, 4};
 constexpr int MAX_RUNS = MAX_RUNS_SMEM;
 
 double species_mass(int s) { return s == SP_E ? ME : M_CU; }
@@ -51,10 +51,12 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, cand, cand_off, active, mid, big, rho_e, rho_h, diag, E,
+    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cand, cand_off, active, mid, big, rho_e,
+        rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
+    int nsp;                         // species with bins
     uint64_t cap, ncell, nodes, ck_len;
     size_t field_bytes;
 };
@@ -74,7 +76,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
         cap += (uint64_t)cf[r].capacity;
         ncell += (uint64_t)cf[r].nz * cf[r].nr;
         nodes += run_nodes(cf[r]);
-        ckl += 4ull * cf[r].nr;
+        ckl += (uint64_t)NCLS * cf[r].nr;
         nz[r] = cf[r].nz;
         nr[r] = cf[r].nr;
     }
@@ -85,7 +87,9 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.ck_len = ckl;
     for (int k = 0; k < 7; ++k) L.A[k] = take(cap * 4);
     for (int k = 0; k < 7; ++k) L.B[k] = take(cap * 4);
-    L.nbins_pad = scan_padded(ncell * NSP);
+    // bins for Cu3+ and Cu4+ only when they can exist
+    L.nsp = cf[0].charge_max >= 3 ? NSP : 5;
+    L.nbins_pad = scan_padded(ncell * (uint64_t)L.nsp);
     L.ncell_pad = scan_padded(ncell);
     L.words_pad = scan_padded(cap / 32 + 1);
     L.count = take((size_t)L.nbins_pad * 4);               // movers into each bin (cursor in the scatter)
@@ -99,7 +103,8 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.mvx = take(((size_t)L.words_pad + 1) * 4);           // its popcount prefix
     const size_t npart = (size_t)std::max(std::max(L.nbins_pad, L.ncell_pad), L.words_pad) / SCAN_TILE + 1;
     L.partial = take(npart * 4);
-    L.nc = take(ncell * 16);
+    L.nc = take(ncell * 16);                               // candidates of classes 0, 1, 5, 6
+    L.nc2 = take(L.nsp == NSP ? ncell * 16 : 16);          // classes 2, 3, 4 (step-wise)
     L.cand = take((size_t)L.ncell_pad * 4);
     L.cand_off = take(((size_t)L.ncell_pad + 1) * 4);
     L.active = take(ncell * 4);
@@ -155,6 +160,7 @@ struct pd_sim {
     uint32_t *count, *off, *off2, *outc, *stay, *dlt, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
     bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
     uint4* nc;
+    uint4* nc2;
     long long *rho_e, *rho_h, *diag;
     float2* E;
     double* phi;
@@ -274,6 +280,8 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.step = (uint32_t)s->step;
     P.heavy_step = heavy_step;
     P.heavy_coll = s->cfgs[0].heavy_coll;
+    P.charge_max = s->cfgs[0].charge_max;
+    P.nsp = s->L.nsp;
     P.field_on = c.field_mode != PD_FIELD_NONE;
     P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
@@ -315,9 +323,9 @@ void update_collision_consts(pd_sim* s) {
     cc.a_t = (float)(mr / M_CU);
     for (int ch = 0; ch < NCH; ++ch) cc.kth[ch] = (float)(2.0 * s->eth[ch] * QE / mr);
     cc.di_split_mode = s->cfgs[0].di_split_mode;
-    const int ch0[4] = {CH_EL, CH_SW, CH_CX, CH_NN}, nch[4] = {4, 1, 1, 1};
-    for (int k = 0; k < 4; ++k) {
-        const double kd = (double)(k < 2 ? cc.kmr : cc.kmr_h);
+    const int ch0[NCLS] = {CH_EL, CH_SW, CH_S3, CH_S3, CH_S4, CH_CX, CH_NN}, nch[NCLS] = {4, 1, 1, 1, 1, 1, 1};
+    for (int k = 0; k < NCLS; ++k) {
+        const double kd = (double)(k < NECLS ? cc.kmr : cc.kmr_h);
         double best = 0.0;
         float prev = 0.0f;
         for (int q = 0; q < XS_N; ++q) {
@@ -345,16 +353,16 @@ pd_status upload_ck(pd_sim* s) {
         const pd_config& c = s->cfgs[r];
         const double dtc = c.dt * c.coll_dt_scale;
         const uint32_t base = s->runs[r].ck_base;
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < NECLS; ++k)
             for (int j = 0; j < c.nr; ++j)
                 ck[base + (size_t)k * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[k] * dtc / cell_volume(c, j));
         // heavy pairs collide on heavy steps with the heavy step; (Cu, Cu) pairs
         // number N (N - 1) / 2
         const double dth = dtc * c.heavy_subcycle;
         for (int j = 0; j < c.nr; ++j) {
-            ck[base + (size_t)2 * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[2] * dth / cell_volume(c, j));
-            ck[base + (size_t)3 * c.nr + j] =
-                (float)(0.5 * c.weight * (double)s->cc.sgmax[3] * dth / cell_volume(c, j));
+            ck[base + (size_t)5 * c.nr + j] = (float)(c.weight * (double)s->cc.sgmax[5] * dth / cell_volume(c, j));
+            ck[base + (size_t)6 * c.nr + j] =
+                (float)(0.5 * c.weight * (double)s->cc.sgmax[6] * dth / cell_volume(c, j));
         }
     }
     CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
@@ -406,6 +414,8 @@ pd_status validate_one(const pd_config* c, std::string& msg) {
     if (c->field_mode == PD_FIELD_POISSON && !field_grid_ok(c->nz, c->nr)) { msg = "Poisson multigrid needs nz, nr = m * 2^k with m <= 8"; return PD_ERR_ARG; }
     if (!(c->coll_dt_scale >= 0)) { msg = "coll_dt_scale must be >= 0"; return PD_ERR_ARG; }
     if (c->heavy_coll != 0 && c->heavy_coll != 1) { msg = "heavy_coll must be 0 or 1"; return PD_ERR_ARG; }
+    if (c->charge_max < 2 || c->charge_max > 4) { msg = "charge_max must be 2, 3 or 4"; return PD_ERR_ARG; }
+    if (c->reserved0 != 0) { msg = "reserved0 must be 0"; return PD_ERR_ARG; }
     if (c->geometry == PD_GEOM_RZ && c->inject_on) {
         if (!(c->tip_radius > 0) || c->tip_radius / c->dr > 63) { msg = "tip must span 1..63 cells"; return PD_ERR_ARG; }
     }
@@ -423,7 +433,7 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         const pd_config &a = cfgs[0], &b = cfgs[r];
         if (b.geometry != a.geometry || b.dt != a.dt || b.heavy_subcycle != a.heavy_subcycle ||
             b.field_mode != a.field_mode || b.coll_dt_scale != a.coll_dt_scale || b.di_on != a.di_on ||
-            b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll) {
+            b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll || b.charge_max != a.charge_max) {
             msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale, double-ionization "
                   "or heavy-collision settings";
             return PD_ERR_ARG;
@@ -540,7 +550,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     const pd_config& c = s->cfgs[0];
     const int heavy = (s->step % c.heavy_subcycle) == 0;
     const KParams P = kparams(s, heavy);
-    const uint32_t nbins = (uint32_t)s->L.ncell * NSP;
+    const uint32_t nbins = (uint32_t)s->L.ncell * (uint32_t)s->L.nsp;
     const int gpart = grid_for(s, s->tune.push_blocks_per_sm);
     const size_t nodes = total_nodes(s);
     if (s->any_inject) {
@@ -580,7 +590,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     s->sorted_valid = true;
     {
         Timed t(s, K_NCAND, capturing, 1);
-        launch_ncand(s->off, s->ck, s->nc, s->cand, s->active, s->mid, s->big, s->st, P,
+        launch_ncand(s->off, s->ck, s->nc, s->nc2, s->cand, s->active, s->mid, s->big, s->st, P,
                      grid_for(s, s->tune.ncand_blocks_per_sm), s->stream);
     }
     {
@@ -589,7 +599,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     }
     {
         Timed t(s, K_COLLIDE, capturing, 3);
-        launch_collide(s->A, s->B, s->off, s->nc, s->cand_off, s->active, s->mid, s->big, s->st, s->rho_e, s->rho_h,
+        launch_collide(s->A, s->B, s->off, s->nc, s->nc2, s->cand_off, s->active, s->mid, s->big, s->st, s->rho_e, s->rho_h,
                        s->xsE, s->xs, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
                        s->stream);
     }
@@ -644,7 +654,8 @@ bool same_config(const pd_config& a, const pd_config& b) {
            a.R_ohm == b.R_ohm && a.C_farad == b.C_farad && a.beta == b.beta && a.tip_radius == b.tip_radius &&
            a.work_function == b.work_function && a.neutral_ratio == b.neutral_ratio &&
            a.neutral_T == b.neutral_T && a.poisson_tol == b.poisson_tol &&
-           a.poisson_max_cycles == b.poisson_max_cycles && a.heavy_coll == b.heavy_coll && a.capacity == b.capacity;
+           a.poisson_max_cycles == b.poisson_max_cycles && a.heavy_coll == b.heavy_coll &&
+           a.charge_max == b.charge_max && a.capacity == b.capacity;
 }
 
 struct File {
@@ -795,6 +806,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->sorted_valid = false;
     s->partial = P32(L.partial);
     s->nc = (uint4*)(w + L.nc);
+    s->nc2 = (uint4*)(w + L.nc2);
     s->cand = P32(L.cand);
     s->cand_off = P32(L.cand_off);
     s->active = P32(L.active);
@@ -871,7 +883,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
         s->node_base[r] = nb;
         cb += RI.ncell;
         nb += (uint32_t)run_nodes(c);
-        kb += 4u * (uint32_t)c.nr;
+        kb += (uint32_t)NCLS * (uint32_t)c.nr;
         circ[r] = RunCircuit{c.V0, c.R_ohm, c.C_farad};
         std::memset(&rs[r], 0, sizeof(RunState));
         rs[r].V = c.V0;
@@ -981,8 +993,10 @@ pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const in
     unsigned int bad = 0;
     unsigned int* dbad = &s->st->load_bad;
     CK(cudaMemsetAsync(dbad, 0, 4, s->stream));
-    launch_pack_keys(sp, iz, ir, pz, pr, n, RI.nz, RI.nr, RI.cell_base, rs.id_next, s->A.key + o, s->A.id + o, dbad,
-                     grid_for(s, 8), s->stream);
+    // species codes up to the configured highest charge (Cu2+ DI is 4, Cu3+ 5, Cu4+ 6)
+    const uint32_t sp_max = (uint32_t)s->cfgs[0].charge_max + 2u;
+    launch_pack_keys(sp, iz, ir, pz, pr, n, RI.nz, RI.nr, RI.cell_base, rs.id_next, sp_max, s->A.key + o,
+                     s->A.id + o, dbad, grid_for(s, 8), s->stream);
     CK(cudaGetLastError());
     const float* src[5] = {pz, pr, vz, vr, vt};
     float* dst[5] = {s->A.pz + o, s->A.pr + o, s->A.vz + o, s->A.vr + o, s->A.vt + o};
@@ -1021,10 +1035,15 @@ pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
     out->t = (double)s->step * c.dt;
     out->V = d.V;
     out->I_gap = d.I_gap;
-    const double n0 = (double)cnt[SP_CU], n1 = (double)cnt[SP_CUP], n2 = (double)(cnt[SP_CU2_SW] + cnt[SP_CU2_DI]);
-    const double ions = n1 + n2, all = n0 + ions;
+    // Eq. (21) over the heavy species: ionization degree and mean ion charge
+    double ions = 0.0, qsum = 0.0;
+    for (int sp = SP_CUP; sp < NSP; ++sp) {
+        ions += (double)cnt[sp];
+        qsum += (double)ZQ[sp] * (double)cnt[sp];
+    }
+    const double all = (double)cnt[SP_CU] + ions;
     out->gamma = all > 0 ? ions / all : 0.0;
-    out->Qbar = ions > 0 ? (n1 + 2.0 * n2) / ions : 0.0;
+    out->Qbar = ions > 0 ? qsum / ions : 0.0;
     double heavy_back = 0;
     for (int sp = 1; sp < NSP; ++sp) heavy_back += (double)d.ctr[C_ABS + 0 * NSP + sp];
     out->mass = M_CU * c.weight * ((double)d.ctr[C_EMIT_CU] - heavy_back);
@@ -1113,6 +1132,9 @@ pd_status pd_config_default(pd_config* c) {
     c->neutral_T = 2000.0;
     c->poisson_tol = 1e-8;
     c->poisson_max_cycles = 60;
+    c->heavy_coll = 0;
+    c->charge_max = 2;
+    c->reserved0 = 0;
     c->capacity = 1 << 16;
     return PD_OK;
 }

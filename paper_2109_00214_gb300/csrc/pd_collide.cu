@@ -385,7 +385,7 @@ __device__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uin
 }
 
 // Rank tables of the lists that k_collide will use and k_ncand queued for
-// this kernel (entries cell << 2 | species bin 0..2; *nq of them, at most
+// this kernel (entries cell << 3 | species bin 0..5; *nq of them, at most
 // max_q): one list per block at a time, NT threads, sorted in shared memory
 // up to MAXN ids and in the scratch buffers above that.  A list already in
 // ascending id order gets the identity.
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__
     __syncthreads();
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const uint32_t e = q[b];
-        const uint32_t bin = (e & 3u) * C + (e >> 2);
+        const uint32_t bin = (e & 7u) * C + (e >> 3);
         const uint32_t slot0 = off[bin], n = off[bin + 1] - slot0;
         const uint32_t* base = ids + slot0;
         const bool in_smem = n <= MAXN;
@@ -548,53 +548,65 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
 // front of `active`, the others to its back, so that k_collide starts them
 // first.
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
-                                               uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
+                                               uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active, uint32_t* mid,
                                                uint32_t* big, DevState* st, KParams P) {
     const uint32_t C = P.ncell;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
     const bool heavy_pairs = P.heavy_coll && P.heavy_step;
+    const bool q3 = P.charge_max >= 3, q4 = P.charge_max >= 4;
     for (uint32_t c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); c0 < C; c0 += stride) {
         const uint32_t c = c0 + lane;
-        uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0, Ne = 0, Ncu = 0, Ni = 0;
+        // n[k]: candidates of class k (electron classes 0-4, heavy pairs 5, 6)
+        uint32_t n[NCLS] = {0, 0, 0, 0, 0, 0, 0};
+        uint32_t N[NSP] = {0, 0, 0, 0, 0, 0, 0};
         int r = -1;
         if (c < C) {
-            Ne = off[c + 1] - off[c];
-            Ncu = off[C + c + 1] - off[C + c];
-            Ni = off[2 * C + c + 1] - off[2 * C + c];
-            const bool ecls = Ne > 0 && (Ncu > 0 || Ni > 0);
-            const bool hcls = heavy_pairs && Ncu > 0;
+            // list lengths (Cu4+ is drawn by no class; Cu3+ has bins with charge_max >= 3)
+#pragma unroll
+            for (int sp = 0; sp < 6; ++sp)
+                if (sp < 5 || q3) N[sp] = off[sp * C + c + 1] - off[sp * C + c];
+            const uint32_t Nt[NECLS] = {N[SP_CU], N[SP_CUP], N[SP_CU2_SW], N[SP_CU2_DI], N[SP_CU3]};
+            bool ecls = false;
+            for (int k = 0; k < NECLS; ++k) ecls |= Nt[k] > 0;
+            ecls = ecls && N[SP_E] > 0;
+            const bool hcls = heavy_pairs && N[SP_CU] > 0;
             if (ecls || hcls) {
                 r = run_of(P, c);
                 const RunInfo& RI = P.runs[r];
                 const uint32_t lc = c - RI.cell_base;
                 const uint32_t j = lc % (uint32_t)RI.nr;
+                // the cell's stream gives R_k to class k whether the class is on or not
                 Stream s(lc, st->step, SID_NCAND, RI.seed, RI.run);
-                const float R0 = s.u01();
-                const float R1 = s.u01();
+                float R[NCLS];
+#pragma unroll
+                for (int k = 0; k < NCLS; ++k) R[k] = s.u01();
                 if (ecls) {
-                    const float x0 = ((float)Ne * (float)Ncu) * ck[RI.ck_base + j] + R0;
-                    const float x1 = ((float)Ne * (float)Ni) * ck[RI.ck_base + RI.nr + j] + R1;
-                    n0 = (uint32_t)floorf(x0);
-                    n1 = (uint32_t)floorf(x1);
+#pragma unroll
+                    for (int k = 0; k < NECLS; ++k) {
+                        if (k >= 2 && !q3) break;
+                        if (k == 4 && !q4) break;
+                        const float x = ((float)N[SP_E] * (float)Nt[k]) * ck[RI.ck_base + k * RI.nr + j] + R[k];
+                        n[k] = (uint32_t)floorf(x);
+                    }
                 }
                 if (hcls) {
                     // N_cu N_cu+ charge-exchange pairs, N_cu (N_cu - 1) / 2 Cu-Cu
                     // pairs (the 1/2 is in the row factor)
-                    const float R2 = s.u01();
-                    const float R3 = s.u01();
-                    const float x2 = ((float)Ncu * (float)Ni) * ck[RI.ck_base + 2 * RI.nr + j] + R2;
-                    const float x3 = ((float)Ncu * (float)(Ncu - 1u)) * ck[RI.ck_base + 3 * RI.nr + j] + R3;
-                    n2 = (uint32_t)floorf(x2);
-                    n3 = Ncu >= 2 ? (uint32_t)floorf(x3) : 0u;
+                    const uint32_t Ncu = N[SP_CU], Ni = N[SP_CUP];
+                    const float x5 = ((float)Ncu * (float)Ni) * ck[RI.ck_base + 5 * RI.nr + j] + R[5];
+                    const float x6 = ((float)Ncu * (float)(Ncu - 1u)) * ck[RI.ck_base + 6 * RI.nr + j] + R[6];
+                    n[5] = (uint32_t)floorf(x5);
+                    n[6] = Ncu >= 2 ? (uint32_t)floorf(x6) : 0u;
                 }
             }
-            nc[c] = make_uint4(n0, n1, n2, n3);
-            cand[c] = n0 + n1;         // the electron classes reserve spawn slots
+            nc[c] = make_uint4(n[0], n[1], n[5], n[6]);
+            if (q3) nc2[c] = make_uint4(n[2], n[3], n[4], 0u);
+            cand[c] = n[0] + n[1] + n[2] + n[3] + n[4];    // the electron classes reserve spawn slots
         }
         // heavy candidates join the run's candidate count here (the electron
         // classes' are summed from the spawn-slot scan)
-        const uint32_t nh = n2 + n3;
+        const uint32_t nh = n[5] + n[6];
         if (__any_sync(FULL, nh > 0)) {
             const int r0 = __shfl_sync(FULL, r, 0);
             if (__all_sync(FULL, nh == 0 || r == r0)) {
@@ -604,11 +616,21 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
                 atomicAdd(&P.rs[r].ctr[C_CAND], (unsigned long long)nh);
             }
         }
-        const uint32_t look_e = n0 + n1, look_cu = n0 + n2 + 2u * n3, look_ci = n1 + n2;
-        const bool act = c < C && (n0 + n1 + nh) > 0;
+        // lookups of each species' list over the classes that draw from it
+        uint32_t look[6];
+        look[SP_E] = n[0] + n[1] + n[2] + n[3] + n[4];
+        look[SP_CU] = n[0] + n[5] + 2u * n[6];
+        look[SP_CUP] = n[1] + n[5];
+        look[SP_CU2_SW] = n[2];
+        look[SP_CU2_DI] = n[3];
+        look[SP_CU3] = n[4];
+        const uint32_t ntot = look[SP_E] + nh;
+        const bool act = c < C && ntot > 0;
         const uint32_t RL = 32u * RC;
-        const bool heavy = act && (n0 + n1 + nh > 32u || (look_e > 0 && Ne > RL) || (look_cu > 0 && Ncu > RL) ||
-                                   (look_ci > 0 && Ni > RL));
+        bool long_list = false;
+#pragma unroll
+        for (int sp = 0; sp < 6; ++sp) long_list |= look[sp] > 0 && N[sp] > RL;
+        const bool heavy = act && (ntot > 32u || long_list);
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
         const unsigned mh = __ballot_sync(FULL, heavy), ml = __ballot_sync(FULL, act && !heavy);
@@ -621,16 +643,13 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
         if (act) {
             // the lists k_collide will rank that need a block's sort (long,
-            // with more lookups than select8 serves); the lookups of a list are
-            // those of every class that draws from it
-            const uint32_t len[3] = {Ne, Ncu, Ni};
-            const uint32_t look[3] = {look_e, look_cu, look_ci};
-            for (uint32_t k = 0; k < 3; ++k) {
-                if (look[k] == 0 || len[k] <= RANK_WARP_MAX || look[k] <= SELECT_LOOKUPS) continue;
-                const bool large = len[k] > RANK_MID_MAX;
+            // with more lookups than select8 serves)
+            for (uint32_t sp = 0; sp < 6; ++sp) {
+                if (look[sp] == 0 || N[sp] <= RANK_WARP_MAX || look[sp] <= SELECT_LOOKUPS) continue;
+                const bool large = N[sp] > RANK_MID_MAX;
                 const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
                 if (x < rank_queue_max(P.capacity, large ? RANK_MID_MAX : RANK_WARP_MAX))
-                    (large ? big : mid)[x] = (c << 2) | k;
+                    (large ? big : mid)[x] = (c << 3) | sp;
                 else set_error(st, ERR_BOUNDS);
             }
         }
@@ -675,14 +694,24 @@ struct PairEval {
     float sg;
 };
 
+// pair classes: first channel and target species of class k (the electron
+// classes draw an electron as the first particle, the heavy pairs a Cu)
+__device__ __forceinline__ int class_ch0(int k) {
+    return k == 0 ? CH_EL : k == 1 ? CH_SW : k <= 3 ? CH_S3 : k == 4 ? CH_S4 : k == 5 ? CH_CX : CH_NN;
+}
+__device__ __forceinline__ int class_target(int k) {
+    return k == 0 ? SP_CU : k == 1 ? SP_CUP : k == 2 ? SP_CU2_SW : k == 3 ? SP_CU2_DI : k == 4 ? SP_CU3
+         : k == 5 ? SP_CUP : SP_CU;
+}
+
 __device__ __forceinline__ PairEval evaluate_pair(int k, const V3& ve, const V3& vt, const float* __restrict__ xsE,
                                                   const float* __restrict__ xs, const CollConsts& cc) {
     PairEval e;
     const float ux = ve.x - vt.x, uy = ve.y - vt.y, uz = ve.z - vt.z;
     const float g2 = (ux * ux + uy * uy) + uz * uz;
     const float g = sqrtf(g2);
-    const float eps = g2 * (k < 2 ? cc.kmr : cc.kmr_h);
-    const int ch0 = k == 0 ? CH_EL : (k == 1 ? CH_SW : (k == 2 ? CH_CX : CH_NN));
+    const float eps = g2 * (k < NECLS ? cc.kmr : cc.kmr_h);
+    const int ch0 = class_ch0(k);
     const int nch = k == 0 ? 4 : 1;
     float sT = 0.0f;
     for (int q = 0; q < 4; ++q) {
@@ -702,12 +731,12 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
                                   const float* __restrict__ xsE, const float* __restrict__ xs,
                                   const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h,
                                   bool accepted) {
-    const int ts = k == 0 ? SP_CU : SP_CUP;
+    const int ts = class_target(k);
     if (!accepted && ((tkey & KEY_FLAG) || (int)key_species(tkey) != ts)) {   // target already ionized this step
         ++cx.consumed;
         return;
     }
-    const int ch0 = k == 0 ? CH_EL : CH_SW;
+    const int ch0 = class_ch0(k);
     const int nch = k == 0 ? 4 : 1;
     const float* cum = ev.cum;
     const float sT = cum[nch - 1];
@@ -754,7 +783,8 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
     V3 e2 = vt;
     // Stage 3, Eq. (14): e1 + e2 elastic, equal masses
     binary_scatter(rs, ve, e2, 0.0f, 0.5f, 0.5f, cx.fb);
-    const int new_sp = ch == CH_SI ? SP_CUP : (ch == CH_SW ? SP_CU2_SW : SP_CU2_DI);
+    const int new_sp = ch == CH_SI ? SP_CUP : ch == CH_SW ? SP_CU2_SW : ch == CH_DI ? SP_CU2_DI
+                     : ch == CH_S3 ? SP_CU3 : SP_CU4;
     const int dq = charge_of(new_sp) - charge_of(ts);
     V3 keep = ve, e6{0.0f, 0.0f, 0.0f};
     if (ch == CH_DI) {
@@ -777,13 +807,13 @@ __device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, 
 // a pair whose particles are no longer what its class draws: a target
 // ionized earlier this step or, for the heavy classes, a Cu that was
 __device__ __forceinline__ bool consumed_pair(int k, uint32_t akey, uint32_t tkey) {
-    const int ts = (k == 0 || k == 3) ? SP_CU : SP_CUP;
+    const int ts = class_target(k);
     const bool t_gone = (tkey & KEY_FLAG) || (int)key_species(tkey) != ts;
-    if (k < 2) return t_gone;
+    if (k < NECLS) return t_gone;
     return t_gone || (akey & KEY_FLAG) || (int)key_species(akey) != SP_CU;
 }
 
-// lane-0 part of one heavy-pair candidate (classes 2 and 3: one channel
+// lane-0 part of one heavy-pair candidate (classes 5 and 6: one channel
 // each, nothing spawned), the counterpart of process_candidate.  Charge
 // exchange Cu + Cu+ -> Cu+ + Cu moves the electron, not the atoms: each slot
 // keeps its species and takes the other's velocity.  Cu + Cu is elastic and
@@ -802,7 +832,7 @@ __device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k,
             return;
         }
     }
-    if (k == 2) {
+    if (k == 5) {
         A.vz[ia] = vb.x; A.vr[ia] = vb.y; A.vt[ia] = vb.z;
         A.vz[ib] = va.x; A.vr[ib] = va.y; A.vt[ib] = va.z;
         ++cx.ev[CH_CX];
@@ -815,7 +845,8 @@ __device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k,
 }
 
 __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
-                                                 const uint4* __restrict__ nc, const uint32_t* __restrict__ cand_off,
+                                                 const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
+                                                 const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
                                                  long long* rho_h, const float* __restrict__ xsE,
                                                  const float* __restrict__ xs, KParams P, CollConsts cc,
@@ -847,6 +878,8 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             wl += nwarps;
         }
         const uint4 n = nc[c];         // candidates of the classes (e,Cu), (e,Cu+), (Cu,Cu+), (Cu,Cu)
+        // and of (e,Cu2+ SW), (e,Cu2+ DI), (e,Cu3+)
+        const uint4 n2 = P.charge_max >= 3 ? nc2[c] : make_uint4(0u, 0u, 0u, 0u);
         const int r = run_of(P, c);
         const RunInfo* RI = &P.runs[r];
         const uint32_t lc = c - RI->cell_base;
@@ -854,7 +887,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         cx.cell = c;
         cx.RI = RI;
         cx.geom = P.geom;
-        cx.nres = 2u * (n.x + n.y);
+        cx.nres = 2u * (n.x + n.y + n2.x + n2.y + n2.z);
         cx.slot0 = (unsigned long long)n_alive + 2ull * cand_off[c];
         // ids: the run's next id plus twice the candidates of the run's earlier cells
         cx.id0 = P.rs[r].id_next + 2u * (cand_off[c] - cand_off[RI->cell_base]);
@@ -876,28 +909,32 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         const uint32_t Ne = off[c + 1] - e_base;
         // lookups of each list over all classes (the rank-table decisions of
         // k_ncand use the same totals)
-        const uint32_t look_e = n.x + n.y, look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
+        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z;
+        const uint32_t look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
         // the first list of a pair: electrons for the electron classes, Cu for
         // the heavy classes (loaded over the electrons' list once those are done)
         IdList el;
         uint32_t a_base = e_base, Na = Ne;
         bool cu_first = false;
         if (look_e) load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t ncand = k == 0 ? n.x : (k == 1 ? n.y : (k == 2 ? n.z : n.w));
+        for (int k = 0; k < NCLS; ++k) {
+            const uint32_t ncand = k == 0 ? n.x : k == 1 ? n.y : k == 2 ? n2.x : k == 3 ? n2.y : k == 4 ? n2.z
+                                 : k == 5 ? n.z : n.w;
             if (ncand == 0) continue;
-            if (k >= 2 && !cu_first) {
+            if (k >= NECLS && !cu_first) {
                 cu_first = true;
                 a_base = off[C + c];
                 Na = off[C + c + 1] - a_base;
                 load_ids(el, A.id, a_base, Na, look_cu, S, sbuf, lane, id_top);
             }
-            const bool cu_target = k == 0 || k == 3;
-            const uint32_t tb = (cu_target ? C : 2 * C) + c;
+            const int ts = class_target(k);
+            const uint32_t tb = (uint32_t)ts * C + c;
             const uint32_t t_base = off[tb];
             const uint32_t Nt = off[tb + 1] - t_base;
+            // the target list's lookups over every class that draws from it
+            const uint32_t t_look = ts == SP_CU ? look_cu : ts == SP_CUP ? look_ci : ncand;
             IdList tl;
-            load_ids(tl, A.id, t_base, Nt, cu_target ? look_cu : look_ci, S, sbuf, lane, id_top);
+            load_ids(tl, A.id, t_base, Nt, t_look, S, sbuf, lane, id_top);
             // candidates in batches of 32: lane q draws candidate m0 + q's pair and
             // prefetches its particles; lane 0 then applies them in order,
             // re-reading a candidate whose particles an earlier candidate of
@@ -910,7 +947,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 if (has) {
                     Stream rs(lc, st->step, sid_cand(k, m0 + lane), RI->seed, RI->run);
                     i = rs.pick(Na);
-                    if (k == 3) {           // a second, different Cu
+                    if (k == 6) {           // a second, different Cu
                         j = rs.pick(Na - 1u);
                         if (j >= i) ++j;
                     } else {
@@ -947,7 +984,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 V3 ve{0.0f, 0.0f, 0.0f}, vt{0.0f, 0.0f, 0.0f};
                 if (ok) {
                     tkey = A.key[it];
-                    if (k >= 2) akey = A.key[ie];
+                    if (k >= NECLS) akey = A.key[ie];
                     ve = V3{A.vz[ie], A.vr[ie], A.vt[ie]};
                     vt = V3{A.vz[it], A.vr[it], A.vt[it]};
                 }
@@ -959,7 +996,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 bool dirty = false;
                 for (uint32_t q = 0; q + 1 < nb; ++q) {
                     const uint32_t e2 = __shfl_sync(FULL, ie, (int)q), t2 = __shfl_sync(FULL, it, (int)q);
-                    if (q < (uint32_t)lane && (e2 == ie || t2 == it || (k == 3 && (e2 == it || t2 == ie))))
+                    if (q < (uint32_t)lane && (e2 == ie || t2 == it || (k == 6 && (e2 == it || t2 == ie))))
                         dirty = true;
                 }
                 // a candidate no earlier one of the batch touches sees the
@@ -996,7 +1033,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                     if (lane == 0) {
                         if (dq) {
                             tkq = A.key[itq];
-                            if (k >= 2) akq = A.key[ieq];
+                            if (k >= NECLS) akq = A.key[ieq];
                             veq = V3{A.vz[ieq], A.vr[ieq], A.vt[ieq]};
                             vtq = V3{A.vz[itq], A.vr[itq], A.vt[itq]};
                             evq = evaluate_pair(k, veq, vtq, xsE, xs, cc);
@@ -1005,7 +1042,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                         Stream rs(lc, st->step, sid_cand(k, m0 + q), RI->seed, RI->run);
                         rs.ctr.w = 1u;
                         rs.used = 4;
-                        if (k < 2)
+                        if (k < NECLS)
                             process_candidate(A, cx, rs, k, ieq, itq, tkq, veq, vtq, evq, Ra, Rc, xsE, xs, cc, st,
                                               rho_e, rho_h, !dq);
                         else
@@ -1180,11 +1217,11 @@ cudaError_t collide_setup() {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_MID_SMEM);
     return e;
 }
-void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
-                  uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
-    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, cand, active, mid, big, st, P);
+void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
+                  uint32_t* mid, uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
+    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
 }
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc,
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s) {
@@ -1194,7 +1231,7 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
         A.id, S, off, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
     k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
         A.id, S, off, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
-    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
+    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {

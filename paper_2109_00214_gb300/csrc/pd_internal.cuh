@@ -14,12 +14,17 @@
 namespace pd {
 
 constexpr uint32_t DEAD = 0xFFFFFFFFu;
-constexpr int NSP = 5;
-constexpr int NCH = 7;
-constexpr int SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4;
-// electron-impact channels, then the heavy pairs of heavy steps (charge
-// exchange Cu+ + Cu, elastic Cu + Cu; with heavy_coll)
-constexpr int CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6;
+constexpr int NSP = 7;              // species codes; bins exist for the first KParams::nsp
+constexpr int NCH = 9;
+constexpr int SP_E = 0, SP_CU = 1, SP_CUP = 2, SP_CU2_SW = 3, SP_CU2_DI = 4, SP_CU3 = 5, SP_CU4 = 6;
+// electron-impact channels, the heavy pairs of heavy steps (charge exchange
+// Cu+ + Cu, elastic Cu + Cu; with heavy_coll), then the step-wise
+// ionizations Cu2+ -> Cu3+ and Cu3+ -> Cu4+ (with charge_max 3 and 4)
+constexpr int CH_EL = 0, CH_EXC = 1, CH_SI = 2, CH_DI = 3, CH_SW = 4, CH_CX = 5, CH_NN = 6, CH_S3 = 7, CH_S4 = 8;
+// pair classes in the order a cell applies them: electron classes (e, Cu),
+// (e, Cu+), (e, Cu2+ SW), (e, Cu2+ DI), (e, Cu3+), then the heavy pairs
+// (Cu, Cu+) and (Cu, Cu)
+constexpr int NCLS = 7, NECLS = 5;
 
 // cross-section grid: 64 points per octave from 2^-10 eV over 25 octaves
 constexpr int XS_EMIN_EXP = -10;
@@ -32,9 +37,10 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 
 // counter slots (see PD_NCOUNTERS in pd.h)
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
-              C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 28, C_EV_NN = 29, NCOUNTERS = 30;
-// counter of the events of channel ch
-__host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : (ch == CH_CX ? C_EV_CX : C_EV_NN); }
+              C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 34, C_EV_NN = 35, C_EV_S3 = 36, C_EV_S4 = 37,
+              NCOUNTERS = 38;
+// counter of the events of channel ch (channels 5-8 follow the absorption block)
+__host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : C_EV_CX + (ch - CH_CX); }
 
 // Device-resident scalars shared by all runs of a simulation.
 struct DevState {
@@ -82,7 +88,7 @@ struct CollConsts {
     float kmr_h;                     // the same for heavy pairs (m_r = M / 2)
     float a_e, a_t;                  // m_r / m_e, m_r / M
     float kth[NCH];                  // 2 E_th e / m_r
-    float sgmax[4];                  // NTC majorants of the pair classes (e,Cu), (e,Cu+), (Cu,Cu+), (Cu,Cu)
+    float sgmax[NCLS];               // NTC majorants of the pair classes, in class order
     int di_split_mode;
 };
 
@@ -100,6 +106,8 @@ struct KParams {
     uint32_t step;
     int heavy_step;
     int heavy_coll;                  // heavy pair classes on heavy steps
+    int charge_max;                  // highest ion charge (2, 3 or 4): step-wise classes on
+    int nsp;                         // species with bins: 5, or 7 with charge_max >= 3
     int field_on;                    // gather E in the push
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
@@ -173,7 +181,9 @@ __device__ __forceinline__ uint32_t converted_key(uint32_t new_sp, uint32_t old_
     return KEY_FLAG | (old_sp << 27) | (new_sp << 24) | cell;
 }
 
-__device__ __forceinline__ int charge_of(int sp) { return sp == SP_E ? -1 : (sp == SP_CU ? 0 : (sp == SP_CUP ? 1 : 2)); }
+// charge number: e -1, Cu 0, Cu+ 1, Cu2+ (both labels) 2, Cu3+ 3, Cu4+ 4
+// (charge + 1 of species sp in nibble sp)
+__host__ __device__ __forceinline__ int charge_of(int sp) { return (int)((0x5433210u >> (4 * sp)) & 15u) - 1; }
 
 // global node index of local node (i, j) of a run; periodic wrap in the
 // Cartesian mode

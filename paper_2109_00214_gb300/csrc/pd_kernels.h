@@ -53,8 +53,8 @@ void launch_spectrum(const Particles& A, DevState* st, const KParams& P, int run
 
 // device-array load: keys and ids of n new particles of one run; *bad set on a bad input
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
-                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t* key, uint32_t* id,
-                      unsigned int* bad, int grid, cudaStream_t s);
+                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t sp_max, uint32_t* key,
+                      uint32_t* id, unsigned int* bad, int grid, cudaStream_t s);
 
 // collisions.  The rank table of an id list of more than RANK_WARP_MAX ids
 // that the candidates of an active cell use is built before k_collide, by a
@@ -67,11 +67,12 @@ constexpr uint32_t RANK_MID_MAX = 2048;
 __host__ __device__ inline uint32_t rank_queue_max(uint64_t cap, uint32_t len) { return (uint32_t)(cap / (len + 1) + 4); }
 // shared-memory attribute of the rank-table kernels (once per process and device)
 cudaError_t collide_setup();
-void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint32_t* cand, uint32_t* active, uint32_t* mid,
-                  uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s);
+// nc: candidates of classes 0, 1, 5, 6; nc2: classes 2, 3, 4 (written with charge_max >= 3)
+void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
+                  uint32_t* mid, uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s);
 // B: the other particle buffer, used as scratch (free until the next scatter)
 // the two rank-table kernels, then k_collide (three launches)
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc,
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s);

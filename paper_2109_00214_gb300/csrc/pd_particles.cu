@@ -219,12 +219,12 @@ __global__ void k_spectrum(Particles A, DevState* st, KParams P, int run, int sp
 __global__ void k_pack_keys(const uint8_t* __restrict__ sp, const int32_t* __restrict__ iz,
                             const int32_t* __restrict__ ir, const float* __restrict__ pz,
                             const float* __restrict__ pr, long long n, int nz, int nr, uint32_t cell_base, uint32_t id0,
-                            uint32_t* key, uint32_t* id, unsigned int* bad) {
+                            uint32_t sp_max, uint32_t* key, uint32_t* id, unsigned int* bad) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const int a = iz[q], b = ir[q];
         const uint32_t s = sp[q];
         const float fz = pz[q], fr = pr[q];
-        const bool ok = s < NSP && a >= 0 && a < nz && b >= 0 && b < nr && fz >= 0.0f && fz < 1.0f && fr >= 0.0f &&
+        const bool ok = s <= sp_max && a >= 0 && a < nz && b >= 0 && b < nr && fz >= 0.0f && fz < 1.0f && fr >= 0.0f &&
                         fr < 1.0f;
         if (!ok) atomicOr(bad, 1u);
         key[q] = ok ? make_key(s, cell_base + (uint32_t)a * (uint32_t)nr + (uint32_t)b) : DEAD;
@@ -252,9 +252,9 @@ void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint
     k_scan_down<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
 }
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
-                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t* key, uint32_t* id,
-                      unsigned int* bad, int grid, cudaStream_t s) {
-    k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, cell_base, id0, key, id, bad);
+                      int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t sp_max, uint32_t* key,
+                      uint32_t* id, unsigned int* bad, int grid, cudaStream_t s) {
+    k_pack_keys<<<grid, 256, 0, s>>>(sp, iz, ir, pz, pr, (long long)n, nz, nr, cell_base, id0, sp_max, key, id, bad);
 }
 void launch_species_count_all(const Particles& A, DevState* st, const KParams& P, unsigned long long* out, int grid,
                               cudaStream_t s) {

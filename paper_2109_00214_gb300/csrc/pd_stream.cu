@@ -30,9 +30,13 @@
 
 namespace pd {
 
+// a[sp] without dynamic indexing (kernel parameters)
 template <typename T>
-__device__ __forceinline__ T pick5(const T (&a)[NSP], int sp) {
-    return sp == 0 ? a[0] : sp == 1 ? a[1] : sp == 2 ? a[2] : sp == 3 ? a[3] : a[4];
+__device__ __forceinline__ T pick_sp(const T (&a)[NSP], int sp) {
+    T r = a[0];
+#pragma unroll
+    for (int k = 1; k < NSP; ++k) r = sp == k ? a[k] : r;
+    return r;
 }
 
 __device__ __forceinline__ float lane_of(const float4& v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
@@ -77,7 +81,13 @@ constexpr uint32_t NOBIN = 0xFFFFFFFFu;
 // (one run, selected without dynamic indexing)
 template <bool MULTI>
 __device__ __forceinline__ float spc(const float (&a)[NSP], int sp) {
-    return MULTI ? a[sp] : pick5(a, sp);
+    return MULTI ? a[sp] : pick_sp(a, sp);
+}
+// a constant that depends only on electron vs heavy (the time step ratios:
+// every heavy species moves with the heavy step)
+template <bool MULTI>
+__device__ __forceinline__ float spc_eh(const float (&a)[NSP], int sp) {
+    return MULTI ? a[sp] : (sp == SP_E ? a[0] : a[1]);
 }
 
 template <bool RZ, bool FIELD, bool MULTI>
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             const uint32_t lcell = move ? gcell_in - RI.cell_base : 0u;   // dead lanes read a valid node
             int iz, ir;
             decode_cell(lcell, RI.nr, RI.inv_nr, iz, ir);
-            const float qmdt = spc<MULTI>(RI.qmdt, sp), dtz = spc<MULTI>(RI.dtz, sp), dtr = spc<MULTI>(RI.dtr, sp);
+            const float qmdt = spc<MULTI>(RI.qmdt, sp), dtz = spc_eh<MULTI>(RI.dtz, sp), dtr = spc_eh<MULTI>(RI.dtr, sp);
             if (FIELD) {
                 const float gz = 1.0f - pz, gr = 1.0f - pr;
                 const float w00 = gz * gr, w10 = pz * gr, w01 = gz * pr, w11 = pz * pr;
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 RunState& rs = P.rs[run_[q]];
                 const double v2 = (double)vzo[q] * vzo[q] + (double)vro[q] * vro[q] + (double)vto[q] * vto[q];
                 const double w = MULTI ? s_runs[run_[q]].weight : P.run0.weight;
-                const double ke = w * (0.5 * pick5(P.masses, sp) * v2);
+                const double ke = w * (0.5 * pick_sp(P.masses, sp) * v2);
                 atomicAdd(&rs.ctr[C_ABS + electrode * NSP + sp], 1ull);
                 atomicAdd(&rs.absorbed_energy[electrode], ke);
                 const double qw = (double)charge_of(sp) * 1.602176634e-19 * w;

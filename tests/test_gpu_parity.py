@@ -159,6 +159,72 @@ def test_microbench_heavy_pairs_bit_exact(pd, xs, nz, nr, total, scale, steps):
     assert np.array_equal(ge, oe) and np.array_equal(gh, oh)
 
 
+def _with_charge_states(parts, charge_max, seed=2):
+    """Half of the Cu+ relabelled as Cu2+ (both labels) and, with charge_max
+    >= 3, Cu3+: targets for the step-wise classes from the first step."""
+    rng = np.random.default_rng(seed)
+    sp = parts["species"].copy()
+    pick = rng.permutation(np.flatnonzero(sp == 2))[: int((sp == 2).sum()) // 2]
+    sp[pick[0::3]] = 3
+    sp[pick[1::3]] = 4
+    if charge_max >= 3:
+        sp[pick[2::3]] = 5
+    return dict(parts, species=sp)
+
+
+@pytest.mark.parametrize("charge_max,heavy_coll,scale,steps", [
+    (4, 0, 20000.0, 4),
+    (3, 0, 20000.0, 3),
+    (4, 1, 3000.0, 4),             # the step-wise classes before the heavy pairs of each cell
+])
+def test_microbench_charge_states_bit_exact(pd, xs, charge_max, heavy_coll, scale, steps):
+    # hotter electrons than the default recipe, so that Cu3+ -> Cu4+ (57 eV) fires
+    cfg, parts = synthetic.microbench(nz=32, nr=48, total=6e4, coll_scale=scale, seed=3, Te_range=(40.0, 120.0))
+    cfg.update(charge_max=charge_max, heavy_coll=heavy_coll, capacity=max(cfg["capacity"], 1 << 21))
+    parts = _with_charge_states(parts, charge_max)
+    sim, o = run_pair(pd, cfg, parts, xs, steps)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["ev_s3"] > 0
+    if charge_max < 4:
+        assert gc["ev_s4"] == 0
+    elif not heavy_coll:
+        assert gc["ev_s4"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+    ge, gh = sim.rho()
+    oe, oh = o.rho()
+    assert np.array_equal(ge, oe) and np.array_equal(gh, oh)
+    gs, os_ = sim.scalars(), o.scalars()
+    assert gs["Qbar"] == pytest.approx(os_["Qbar"], rel=1e-14)
+    assert gs["gamma"] == pytest.approx(os_["gamma"], rel=1e-14)
+    assert list(gs["count"]) == [int(x) for x in np.bincount(o.particles()["species"], minlength=7)]
+
+
+@pytest.mark.parametrize("target,n_t,scale", [
+    (3, 9000, 0.3),                # one cell of 9000 Cu2+ (SW): the list sorted by a block
+    (5, 20000, 0.5),               # 20000 Cu3+: sorted in the scratch buffers
+    (4, 700, 20.0),                # 700 Cu2+ (DI): the cell's warp sorts it
+    (5, 6000, 0.1),                # a few candidates: digit-by-digit selects
+])
+def test_dense_charge_state_cells_bit_exact(pd, xs, target, n_t, scale):
+    cfg, parts = synthetic.rate_cell(n_e=3000, n_t=n_t, Te_eV=60.0, seed=8, coll_scale=scale, target_species=target)
+    cfg.update(nz=2, nr=2, charge_max=4)
+    sim, o = run_pair(pd, cfg, parts, xs, 3)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["cand_total"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
+def test_species_above_charge_max_refused_gpu(pd, xs):
+    cfg, parts = synthetic.rate_cell(n_e=10, n_t=10, target_species=5)
+    cfg.update(nz=2, nr=2)
+    sim = pd.Simulation(cfg, xs)
+    with pytest.raises(pd.PdError):
+        sim.load(parts)
+        sim.synchronize()
+
+
 def _rz_field(n, V0, seed=3):
     rng = np.random.default_rng(seed)
     Ez = np.full((n + 1, n + 1), -V0 / 6e-6) * (1 + 0.3 * rng.uniform(-1, 1, (n + 1, n + 1)))
