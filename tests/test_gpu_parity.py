@@ -261,6 +261,7 @@ def test_rz_external_field_with_injection_bit_exact(pd, xs):
     (64, 320),     # R = 5 L: coarsest 8 x 40 cells, 287 unknowns: Gauss-Seidel sweeps
     (32, 32),      # every level in the one-block tail, the correction added to phi there
     (16, 48),      # two levels, both in the tail
+    (120, 480),    # the paper's domain (Sec. 2.3): 6 x 24 um in 50 nm cells
 ])
 def test_rz_poisson_matches_oracle(pd, xs, n, nr):
     """Self-consistent field: multigrid (GPU) vs conjugate gradients (CPU) on
@@ -280,12 +281,13 @@ def test_rz_poisson_matches_oracle(pd, xs, n, nr):
     assert np.allclose(gEr, oEr, rtol=1e-6, atol=1e-6 * np.abs(oEz).max())
 
 
-def test_rz_self_consistent_steps_track_oracle(pd, xs):
+@pytest.mark.parametrize("n,nr", [(64, 64), (120, 480)])
+def test_rz_self_consistent_steps_track_oracle(pd, xs, n, nr):
     """A few self-consistent steps: the two field solves agree to ~1e-9, so
-    particle states agree to FP32 rounding and the counters stay equal."""
-    n = 64
+    particle states agree to FP32 rounding and the counters stay equal.  The
+    second case is the paper's domain, 120 x 480 cells of 50 nm (Sec. 2.3)."""
     cfg, parts = synthetic.rz_plume(n=n, total=3e4, seed=6)
-    cfg.update(field_on=1, inject_on=1, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
+    cfg.update(nr=nr, field_on=1, inject_on=1, poisson_tol=1e-10, oracle_poisson_tol=1e-12)
     sim, o = run_pair(pd, cfg, parts, xs, 5)
     gc, oc = sim.counters(), o.counters()
     for k in ("ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "emitted_e", "emitted_cu"):
