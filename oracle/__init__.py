@@ -47,7 +47,7 @@ class _Cfg(C.Structure):
         ("beta", C.c_double), ("tip_radius", C.c_double), ("work_function", C.c_double),
         ("neutral_ratio", C.c_double), ("neutral_T", C.c_double),
         ("poisson_tol", C.c_double), ("capacity", C.c_int64), ("heavy_coll", C.c_int32),
-        ("charge_max", C.c_int32),
+        ("charge_max", C.c_int32), ("coulomb", C.c_int32), ("coulomb_lnl", C.c_double),
     ]
 
 
@@ -94,6 +94,10 @@ def _lib(fp64):
         L.or_event_kinematics.argtypes = [P, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D, P]
         L.or_rectangle_split.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D]
         L.or_deposit_weights.argtypes = [C.c_double, C.c_double, P, P]
+        L.or_coulomb_kinematics.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, C.c_double, C.c_double,
+                                            C.c_double]
+        L.or_perm_index.restype = C.c_uint32
+        L.or_perm_index.argtypes = [C.c_uint32, C.c_uint32, P]
         _LIBS[key] = L
     return _LIBS[key]
 
@@ -110,7 +114,7 @@ COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consum
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
                     for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
-                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4"])
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei"])
 SCALAR_NAMES = ["t", "V", "I_gap", "gamma", "Qbar", "erosion", "mass", "charge", "sgmax0",
                 "sgmax1", "poisson_relres", "poisson_iters", "E_abs_cathode", "E_abs_anode",
                 "E_abs_wall"]
@@ -154,6 +158,8 @@ class Oracle:
         c.capacity = cfg["capacity"]
         c.heavy_coll = cfg.get("heavy_coll", 0)
         c.charge_max = cfg.get("charge_max", 2)
+        c.coulomb = cfg.get("coulomb", 0)
+        c.coulomb_lnl = cfg.get("coulomb_lnl", 10.0)
         self._c = c
         self.h = self.L.or_create(C.byref(c))
         rz = c.geom == 0
@@ -281,12 +287,27 @@ class Oracle:
             return None
         return ve, vt, [en[0:3].copy(), en[3:6].copy()][: ns.value]
 
+    def coulomb(self, va, vb, Kn, fa, fb, subject=0, step=0, sid=0):
+        """One Coulomb pair collision (binary collision model); None if the
+        relative velocity is zero."""
+        va = np.array(va, np.float64)
+        vb = np.array(vb, np.float64)
+        r = self.L.or_coulomb_kinematics(self.h, subject, step, sid, _dptr(va), _dptr(vb), float(Kn), float(fa),
+                                         float(fb))
+        return (va, vb) if r else None
+
     def rectangle_split(self, v, subject=0, step=0, sid=0):
         v = np.array(v, np.float64)
         a = np.zeros(3)
         b = np.zeros(3)
         self.L.or_rectangle_split(self.h, subject, step, sid, _dptr(v), _dptr(a), _dptr(b))
         return a, b
+
+
+def perm_index(x, n, key):
+    """Element x of the keyed pseudo-random permutation of [0, n)."""
+    k = np.asarray(key, np.uint32)
+    return int(_lib(False).or_perm_index(int(x), int(n), _ptr(k)))
 
 
 def deposit_weights(pz, pr, fp64=False):

@@ -97,6 +97,8 @@ typedef struct {
     int64_t capacity;
     int32_t heavy_coll;    /* heavy-particle pair classes (charge exchange, Cu-Cu elastic) on */
     int32_t charge_max;    /* highest ion charge: 2 (Cu2+), 3 (+ Cu2+ -> Cu3+), 4 (+ Cu3+ -> Cu4+) */
+    int32_t coulomb;       /* Coulomb collisions e-e and e-ion (binary collision model) on */
+    double coulomb_lnl;    /* Coulomb logarithm */
 } or_cfg;
 
 typedef struct {
@@ -122,6 +124,7 @@ typedef struct {
     real sgmax[7];
     /* counters */
     uint64_t events[NCH], nulls, consumed, thr_rej, ratio_viol, iso_fallback, cand_total;
+    uint64_t coul_ee, coul_ei;   /* Coulomb pair collisions applied */
     uint64_t absorbed[3][NSP];   /* cathode, anode, outer wall */
     double absorbed_energy[3];   /* J (physical, includes W) */
     uint64_t emitted_e, emitted_cu;
@@ -190,6 +193,10 @@ static uint32_t pick(stream_t* s, uint32_t n) { return (uint32_t)(((uint64_t)nex
 /* stream ids (third counter word) */
 #define SID_CAND(k, m) (((uint32_t)(k) << 28) | (uint32_t)(m))
 #define SID_NCAND 0xE0000000u
+/* Coulomb classes 0 (e-e) and 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+):
+ * pair k of class c, and the permutation keys of class c */
+#define SID_COUL(c, k) ((((uint32_t)(c) + 8u) << 28) | (uint32_t)(k))
+#define SID_COUL_PERM(c) (0xE1000000u | (uint32_t)(c))
 #define SID_INJ_COUNT 0xD0000000u
 #define SID_INJ_E(p) (0xD1000000u | (uint32_t)(p))
 #define SID_INJ_CU(p) (0xD2000000u | (uint32_t)(p))
@@ -590,6 +597,106 @@ static int binary_scatter(or_sim* S, stream_t* st, vec3* v1, vec3* v2, real kth,
     return 1;
 }
 
+/* ------------------------------------------------------------------ */
+/* Coulomb collisions (the paper lists them among the collisions of its  */
+/* model, Sec. 2.3, without a method): the binary collision model of     */
+/* Takizuka and Abe (J. Comput. Phys. 25, 205, 1977).  A pair (a, b)      */
+/* with relative velocity u is deflected by theta, tan(theta/2) = delta,  */
+/* delta normal with variance <delta^2> = (q_a q_b)^2 n_L lnL dt /        */
+/* (8 pi eps0^2 m_ab^2 u^3), about a uniform azimuth; |u| is kept and      */
+/* the change of u is shared by the reduced mass, so momentum and energy  */
+/* are conserved.  Kn = (q_a q_b)^2 n_L lnL dt / (8 pi eps0^2 m_ab^2) is   */
+/* the pair's factor; fa = m_ab / m_a, fb = m_ab / m_b.                   */
+/* ------------------------------------------------------------------ */
+/* normal deviate approximated by the Irwin-Hall sum of twelve uniforms   */
+/* (mean 0, variance 1, support [-6, 6])                                  */
+static real irwin_hall12(stream_t* st) {
+    real z = R_(0);
+    for (int i = 0; i < 12; ++i) z = z + u01(st);
+    return z - R_(6);
+}
+
+static int coulomb_kin(or_sim* S, stream_t* st, vec3* va, vec3* vb, real Kn, real fa, real fb) {
+    real ux = va->x - vb->x, uy = va->y - vb->y, uz = va->z - vb->z;
+    real u2 = (ux * ux + uy * uy) + uz * uz;
+    if (!(u2 > R_(0))) return 0;
+    real u = OR_SQRT(u2);
+    real var = Kn / (u2 * u);
+    var = var < R_(1e30) ? var : R_(1e30);          /* u -> 0: keep delta finite */
+    real z = irwin_hall12(st);
+    real d = OR_SQRT(var) * z;
+    /* sin(theta) = 2 delta / (1 + delta^2), 1 - cos(theta) = 2 delta^2 / (1 + delta^2),
+     * in 1/delta when |delta| > 1 */
+    real sth, omc;
+    real ad = d < R_(0) ? -d : d;
+    if (ad <= R_(1)) {
+        real d2 = d * d, den = R_(1) + d2;
+        sth = (R_(2) * d) / den;
+        omc = (R_(2) * d2) / den;
+    } else {
+        real r = R_(1) / d, r2 = r * r, den = R_(1) + r2;
+        sth = (R_(2) * r) / den;
+        omc = R_(2) / den;
+    }
+    real cph, sph;
+    azimuth(S, st, &cph, &sph);
+    real sc = sth * cph, ss = sth * sph;
+    real up = OR_SQRT(ux * ux + uy * uy);
+    real dx, dy, dz;
+    if (up > R_(0)) {
+        real a1 = ux / up, a2 = uy / up;
+        dx = ((a1 * uz) * sc - (a2 * u) * ss) - ux * omc;
+        dy = ((a2 * uz) * sc + (a1 * u) * ss) - uy * omc;
+        dz = -(up * sc) - uz * omc;
+    } else {            /* u along the third axis: rotate about it */
+        dx = uz * sc;
+        dy = uz * ss;
+        dz = -(uz * omc);
+    }
+    va->x = va->x + fa * dx; va->y = va->y + fa * dy; va->z = va->z + fa * dz;
+    vb->x = vb->x - fb * dx; vb->y = vb->y - fb * dy; vb->z = vb->z - fb * dz;
+    return 1;
+}
+
+static int coulomb_pair(or_sim* S, stream_t* st, int64_t ia, int64_t ib, real Kn, real fa, real fb) {
+    vec3 va = {S->vz[ia], S->vr[ia], S->vt[ia]}, vb = {S->vz[ib], S->vr[ib], S->vt[ib]};
+    if (!coulomb_kin(S, st, &va, &vb, Kn, fa, fb)) return 0;
+    S->vz[ia] = va.x; S->vr[ia] = va.y; S->vt[ia] = va.z;
+    S->vz[ib] = vb.x; S->vr[ib] = vb.y; S->vt[ib] = vb.z;
+    return 1;
+}
+
+/* Pseudo-random permutation of [0, n): a four-round Feistel network
+ * (Luby and Rackoff) on 2h bits, 4^h >= n, with an integer mixing round
+ * function, walked back into [0, n) by cycle walking (Black and Rogaway,
+ * 2002); the walk ends within 4^h steps because x itself lies in [0, n). */
+static uint32_t fe_round(uint32_t x, uint32_t k) {
+    uint32_t t = (x ^ k) * 0x9E3779B1u;
+    t ^= t >> 15;
+    t *= 0x85EBCA77u;
+    t ^= t >> 13;
+    return t;
+}
+static uint32_t perm_index(uint32_t x, uint32_t n, const uint32_t* key) {
+    int h = 1;
+    while ((1ull << (2 * h)) < (uint64_t)n) ++h;
+    uint32_t mask = (1u << h) - 1u;
+    uint64_t lim = 1ull << (2 * h);
+    uint32_t y = x;
+    for (uint64_t it = 0; it < lim; ++it) {
+        uint32_t L = y >> h, R = y & mask;
+        for (int r = 0; r < 4; ++r) {
+            uint32_t F = fe_round(R, key[r]) & mask;
+            uint32_t t = L ^ F;
+            L = R;
+            R = t;
+        }
+        y = (L << h) | R;
+        if (y < n) return y;
+    }
+    return x;
+}
+
 /* Stage 4 of the double-ionization scheme, Eq. (15)-(20): the velocity v of
  * e3 is the diagonal of a rectangle whose edges are v5 and v6.  v5 =
  * R^-1(theta,phi) R^-1(chi,psi) R(theta,phi) (cos chi v), with R of Eq. (20),
@@ -709,6 +816,21 @@ int or_event_kinematics(or_sim* S, int ch, uint32_t subject, uint32_t step, uint
     return 0;
 }
 
+/* exported for the pins of the Coulomb model: one pair collision of
+ * velocities va, vb with factor Kn and mass fractions fa, fb, drawing from
+ * stream (subject, step, sid); the permutation of [0, n) under key[4] */
+int or_coulomb_kinematics(or_sim* S, uint32_t subject, uint32_t step, uint32_t sid, double* va_io, double* vb_io,
+                          double Kn, double fa, double fb) {
+    stream_t st;
+    stream_init(&st, S, subject, step, sid);
+    vec3 va = {R_(va_io[0]), R_(va_io[1]), R_(va_io[2])}, vb = {R_(vb_io[0]), R_(vb_io[1]), R_(vb_io[2])};
+    int r = coulomb_kin(S, &st, &va, &vb, R_(Kn), R_(fa), R_(fb));
+    va_io[0] = va.x; va_io[1] = va.y; va_io[2] = va.z;
+    vb_io[0] = vb.x; vb_io[1] = vb.y; vb_io[2] = vb.z;
+    return r;
+}
+uint32_t or_perm_index(uint32_t x, uint32_t n, const uint32_t* key) { return perm_index(x, n, key); }
+
 int or_rectangle_split(or_sim* S, uint32_t subject, uint32_t step, uint32_t sid, const double* v,
                        double* v5, double* v6) {
     stream_t st;
@@ -732,6 +854,76 @@ typedef struct { uint32_t id; int64_t idx; } idrec;
 static int cmp_id(const void* a, const void* b) {
     uint32_t x = ((const idrec*)a)->id, y = ((const idrec*)b)->id;
     return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* Pairing of one cell (Takizuka-Abe): class 0 pairs the electrons two by
+ * two in a random order (an odd count ends with a triple whose three pairs
+ * collide with half the time step); class 1 + i (ion species i = Cu+, Cu2+
+ * SW, Cu2+ DI, Cu3+, Cu4+) pairs each particle of the more numerous of the
+ * electrons and the ions once, k-th of that species in a random order with
+ * the (k mod N_fewer)-th of the other in a random order, so that a particle
+ * of the fewer species collides several times in sequence; n_L is the
+ * density of the fewer (the lower density). */
+static double coulomb_k(int za, int zb, double mab, double lnl) {
+    double qq = (double)za * (double)zb * QE * QE;
+    return qq * qq * lnl / (8.0 * PI * EPS0 * EPS0 * mab * mab);
+}
+
+static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* cnt, int64_t C, double dtc) {
+    int j = (int)(c % S->c.nr);
+    double wv = S->c.weight * dtc / cell_volume(S, j);          /* W dt / V: n dt per particle */
+    double lnl = S->c.coulomb_lnl;
+    const idrec* el = rec + cnt[SP_E * C + c];
+    uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
+    if (Ne >= 2) {
+        stream_t ps;
+        stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(0));
+        uint32_t key[4];
+        for (int q = 0; q < 4; ++q) key[q] = next_u32(&ps);
+        real Kn = R_(coulomb_k(-1, -1, 0.5 * ME, lnl) * (double)Ne * wv);
+        real h = R_(0.5);
+        uint32_t P = Ne / 2 - (Ne % 2);                          /* regular pairs */
+        for (uint32_t k = 0; k < P; ++k) {
+            stream_t st;
+            stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(0, k));
+            int64_t ia = el[perm_index(2 * k, Ne, key)].idx, ib = el[perm_index(2 * k + 1, Ne, key)].idx;
+            S->coul_ee += (uint64_t)coulomb_pair(S, &st, ia, ib, Kn, h, h);
+        }
+        if (Ne % 2) {                                            /* the last three: a triple */
+            int64_t t[3];
+            for (int q = 0; q < 3; ++q) t[q] = el[perm_index(Ne - 3 + q, Ne, key)].idx;
+            for (int q = 0; q < 3; ++q) {
+                stream_t st;
+                stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(0, P + (uint32_t)q));
+                S->coul_ee += (uint64_t)coulomb_pair(S, &st, t[q], t[(q + 1) % 3], Kn * h, h, h);
+            }
+        }
+    }
+    double mr = mr_class();
+    real fe = R_(mr / ME), fi = R_(mr / M_CU);
+    for (int i = 0; i < 5 && Ne > 0; ++i) {
+        int sp = SP_CUP + i;
+        const idrec* il = rec + cnt[sp * C + c];
+        uint32_t Ni = (uint32_t)(cnt[sp * C + c + 1] - cnt[sp * C + c]);
+        if (Ni == 0) continue;
+        int e_many = Ne >= Ni;
+        uint32_t Na = e_many ? Ne : Ni, Nb = e_many ? Ni : Ne;
+        stream_t ps;
+        stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(1 + i));
+        uint32_t ka[4], kb[4];
+        for (int q = 0; q < 4; ++q) ka[q] = next_u32(&ps);
+        for (int q = 0; q < 4; ++q) kb[q] = next_u32(&ps);
+        real Kn = R_(coulomb_k(-1, ZQ[sp], mr, lnl) * (double)Nb * wv);
+        for (uint32_t k = 0; k < Na; ++k) {
+            uint32_t a = perm_index(k, Na, ka), b = perm_index(k % Nb, Nb, kb);
+            int64_t ie = e_many ? el[a].idx : el[b].idx;
+            int64_t ii = e_many ? il[b].idx : il[a].idx;
+            if (S->sp[ii] != sp) continue;                       /* ionized this step */
+            stream_t st;
+            stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(1 + i, k));
+            S->coul_ei += (uint64_t)coulomb_pair(S, &st, ie, ii, Kn, fe, fi);
+        }
+    }
 }
 
 static int collide_all(or_sim* S, int heavy_step) {
@@ -893,6 +1085,11 @@ static int collide_all(or_sim* S, int heavy_step) {
                 S->events[CLASS_CH0[k]]++;
             }
         }
+        /* Coulomb collisions of the cell's charged particles, after its DSMC
+         * classes: e-e, then e with each ion species.  The lists are those of
+         * the step's start (newborn electrons wait for the next step); an ion
+         * ionized earlier this step is left out. */
+        if (S->c.coulomb && !err) coulomb_cell(S, c, rec, cnt, C, dtc);
     }
     S->id_next = id_base + (uint32_t)(2 * total);
     free(cnt); free(rec); free(cur); free(nc); free(pre);
@@ -1176,7 +1373,8 @@ void or_get_field(const or_sim* S, double* Ez, double* Er) {
 /* counters: events[5] of the channels 0-4, nulls, consumed, thr_rej,
  * ratio_viol, iso_fallback, cand_total, emitted_e, emitted_cu,
  * absorbed[3][7], then events of charge exchange, Cu-Cu elastic,
- * Cu2+ -> Cu3+ and Cu3+ -> Cu4+ */
+ * Cu2+ -> Cu3+ and Cu3+ -> Cu4+, and the Coulomb pair collisions e-e and
+ * e-ion */
 void or_get_counters(const or_sim* S, uint64_t* out) {
     int k = 0;
     for (int c = 0; c < CH_CX; ++c) out[k++] = S->events[c];
@@ -1186,6 +1384,7 @@ void or_get_counters(const or_sim* S, uint64_t* out) {
     for (int e = 0; e < 3; ++e) for (int s = 0; s < NSP; ++s) out[k++] = S->absorbed[e][s];
     out[k++] = S->events[CH_CX]; out[k++] = S->events[CH_NN];
     out[k++] = S->events[CH_S3]; out[k++] = S->events[CH_S4];
+    out[k++] = S->coul_ee; out[k++] = S->coul_ei;
 }
 
 /* scalars: t, V, I_gap, gamma, Qbar, erosion (kg/C), mass ledger (kg),
