@@ -51,11 +51,12 @@ UNIT = "particle-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_desc(nz, nr, total, heavy_coll=0):
+def workload_desc(nz, nr, total, heavy_coll=0, coulomb=0):
     return (f"DSMC collision microbench: {nz}x{nr} Cartesian cells (50 nm, periodic, no field), "
             f"{total:.3g} super-particles (Cu lognormal(ln 1e23 m^-3, 1), Cu+ 10% of Cu, e = Cu+, "
             f"Te U[5,50] eV, heavies 2000 K), 5 channels incl. double ionization"
             + (" + charge exchange and Cu-Cu elastic pairs" if heavy_coll else "")
+            + (" + Coulomb e-e and e-ion pairs" if coulomb else "")
             + ", FP32 state, dt = 1 fs")
 
 
@@ -76,6 +77,7 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--heavy-coll", action="store_true",
                    help="microbench: add the heavy-particle pair classes (charge exchange, Cu-Cu elastic)")
+    p.add_argument("--coulomb", action="store_true", help="microbench: add the Coulomb pair collisions")
     p.add_argument("--no-plain", action="store_true", help="ensemble: skip the one-simulation-per-run arm")
     p.add_argument("--ens-seeds", type=int, default=8, help="ensemble: seeds (runs = seeds x 8 voltages)")
     p.add_argument("--ens-warm", default="extrapolate", help="ensemble: Poisson starting point of every arm "
@@ -222,6 +224,7 @@ def cpu_baseline(args, cfg_full, seed):
     total = args.total * rows / args.nz
     cfg, parts = synthetic.microbench(nz=rows, nr=args.nr, total=total, seed=seed)
     cfg["heavy_coll"] = int(args.heavy_coll)
+    cfg["coulomb"] = int(args.coulomb)
     o = oracle.Oracle(cfg, fp64=False)
     o.set_cross_sections(synthetic.standin_cross_sections())
     o.load(parts)
@@ -244,7 +247,8 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.cpu_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll) + " (bounded CPU sample)",
+            "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb)
+                       + " (bounded CPU sample)",
                        "nz": args.cpu_rows, "nr": args.nr},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -554,6 +558,7 @@ def main():
     seed = 1 + rank
     cfg, parts = synthetic.microbench(nz=args.nz, nr=args.nr, total=args.total, seed=seed)
     cfg["heavy_coll"] = int(args.heavy_coll)
+    cfg["coulomb"] = int(args.coulomb)
     xs = synthetic.standin_cross_sections()
     n_in = len(parts["species"])
 
@@ -653,7 +658,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll),
+                "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb),
                            "nz": args.nz, "nr": args.nr,
                            "particles_per_gpu": int(n0), "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                            "tuning": tuning,
@@ -661,7 +666,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,
                 "events": {k: counters[k] for k in ("ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "ev_cx", "ev_nn",
-                                                    "cand_total")}}
+                                                    "coul_ee", "coul_ei", "cand_total")}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

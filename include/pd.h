@@ -64,7 +64,7 @@ enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI 
 enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4,
        PD_CH_CX = 5, PD_CH_NN = 6, PD_CH_S3 = 7, PD_CH_S4 = 8, PD_NCH = 9 };
 
-#define PD_CONFIG_VERSION 2u
+#define PD_CONFIG_VERSION 3u
 
 /* Run parameters (Sec. 2.3 gives: 50 nm cells, 1 fs electron step, heavy step
  * ten times longer, W = 100, 2.9 kV through R = 1 kOhm with C = 1 pF, a 200 nm
@@ -95,8 +95,11 @@ typedef struct pd_config {
     int32_t charge_max;        /* highest ion charge: 2 (default), 3 (adds the pair
                                   classes (e, Cu2+) -> Cu3+), 4 (and (e, Cu3+) -> Cu4+);
                                   species above it are refused on load */
-    int32_t reserved0;         /* 0 */
+    int32_t coulomb;           /* 1: Coulomb collisions of the e-e and e-ion pairs of
+                                  each cell after its DSMC classes (binary collision
+                                  model of Takizuka and Abe); 0 (default): off */
     int64_t capacity;          /* particle slots */
+    double coulomb_lnl;        /* Coulomb logarithm (default 10) */
 } pd_config;
 
 /* Scalars of the current state (Sec. 3: arc current and voltage, Eq. (21)
@@ -126,8 +129,9 @@ typedef struct pd_scalars {
  * step, accepted candidates below threshold, NTC majorant violations,
  * isotropic-sampling fallbacks, candidates in total, electrons emitted,
  * neutrals emitted, absorbed [electrode 3][species 7], then events of charge
- * exchange, Cu-Cu elastic, Cu2+ -> Cu3+ and Cu3+ -> Cu4+. */
-#define PD_NCOUNTERS 38
+ * exchange, Cu-Cu elastic, Cu2+ -> Cu3+ and Cu3+ -> Cu4+, then Coulomb pair
+ * collisions e-e and e-ion. */
+#define PD_NCOUNTERS 40
 
 typedef struct pd_sim pd_sim;
 

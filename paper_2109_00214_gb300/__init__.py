@@ -30,14 +30,14 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
-PD_NCOUNTERS = 38
+PD_NCOUNTERS = 40
 PD_NKERNELS = 12
 GEOM = {"rz": 0, "xy_periodic": 1}
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
                     for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
-                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4"])
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei"])
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CAPACITY", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
           5: "PD_ERR_NONFINITE", 6: "PD_ERR_STATE"}
 
@@ -53,8 +53,8 @@ class PdConfig(C.Structure):
         ("R_ohm", C.c_double), ("C_farad", C.c_double), ("beta", C.c_double),
         ("tip_radius", C.c_double), ("work_function", C.c_double), ("neutral_ratio", C.c_double),
         ("neutral_T", C.c_double), ("poisson_tol", C.c_double), ("poisson_max_cycles", C.c_int32),
-        ("heavy_coll", C.c_int32), ("charge_max", C.c_int32), ("reserved0", C.c_int32),
-        ("capacity", C.c_int64),
+        ("heavy_coll", C.c_int32), ("charge_max", C.c_int32), ("coulomb", C.c_int32),
+        ("capacity", C.c_int64), ("coulomb_lnl", C.c_double),
     ]
 
 
@@ -212,6 +212,8 @@ def config_from_dict(d):
     c.poisson_max_cycles = d.get("poisson_max_cycles", 60)
     c.heavy_coll = d.get("heavy_coll", 0)
     c.charge_max = d.get("charge_max", 2)
+    c.coulomb = d.get("coulomb", 0)
+    c.coulomb_lnl = d.get("coulomb_lnl", 10.0)
     c.capacity = d["capacity"]
     return c
 

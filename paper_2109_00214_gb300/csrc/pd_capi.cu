@@ -33,6 +33,7 @@ namespace {
 // CODATA 2018
 constexpr double QE = 1.602176634e-19;
 constexpr double ME = 9.1093837015e-31;
+constexpr double EPS0_C = 8.8541878128e-12;
 constexpr double AMU = 1.66053906660e-27;
 constexpr double M_CU = 63.546 * AMU;
 constexpr double KB = 1.380649e-23;
@@ -51,13 +52,13 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cand, cand_off, active, mid, big, rho_e,
+    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cw, cand, cand_off, active, mid, big, rho_e,
         rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
     int nsp;                         // species with bins
-    uint64_t cap, ncell, nodes, ck_len;
+    uint64_t cap, ncell, nodes, ck_len, rows;
     size_t field_bytes;
 };
 
@@ -70,13 +71,14 @@ Layout make_layout(const std::vector<pd_config>& cf) {
         return r;
     };
     const int R = (int)cf.size();
-    uint64_t cap = 0, ncell = 0, nodes = 0, ckl = 0;
+    uint64_t cap = 0, ncell = 0, nodes = 0, ckl = 0, rows = 0;
     std::vector<int> nz(R), nr(R);
     for (int r = 0; r < R; ++r) {
         cap += (uint64_t)cf[r].capacity;
         ncell += (uint64_t)cf[r].nz * cf[r].nr;
         nodes += run_nodes(cf[r]);
         ckl += (uint64_t)NCLS * cf[r].nr;
+        rows += (uint64_t)cf[r].nr;
         nz[r] = cf[r].nz;
         nr[r] = cf[r].nr;
     }
@@ -85,6 +87,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.ncell = ncell;
     L.nodes = nodes;
     L.ck_len = ckl;
+    L.rows = rows;
     for (int k = 0; k < 7; ++k) L.A[k] = take(cap * 4);
     for (int k = 0; k < 7; ++k) L.B[k] = take(cap * 4);
     // bins for Cu3+ and Cu4+ only when they can exist
@@ -118,6 +121,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.xsE = take(XS_N * 4);
     L.xs = take(NCH * XS_N * 4);
     L.ck = take(ckl * 4);
+    L.cw = take(rows * 8);                                 // W dt_coll / V_cell per row (Coulomb densities)
     L.ray = take(1024 * 4);
     L.hist = take(4096 * 8);
     L.spc = take((size_t)R * NSP * 8);                     // live particles per run and species
@@ -165,6 +169,7 @@ struct pd_sim {
     float2* E;
     double* phi;
     float *xsE, *xs, *ck, *ray;
+    double* cw;
     unsigned long long *hist, *spc;
     DevState* st;
     RunState* rs;
@@ -282,6 +287,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.heavy_coll = s->cfgs[0].heavy_coll;
     P.charge_max = s->cfgs[0].charge_max;
     P.nsp = s->L.nsp;
+    P.coulomb = s->cfgs[0].coulomb;
     P.field_on = c.field_mode != PD_FIELD_NONE;
     P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
@@ -323,6 +329,17 @@ void update_collision_consts(pd_sim* s) {
     cc.a_t = (float)(mr / M_CU);
     for (int ch = 0; ch < NCH; ++ch) cc.kth[ch] = (float)(2.0 * s->eth[ch] * QE / mr);
     cc.di_split_mode = s->cfgs[0].di_split_mode;
+    // Coulomb pair factors (q_a q_b)^2 lnL / (8 pi eps0^2 m_ab^2): e-e (m_ab = m_e / 2),
+    // then e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+ (m_ab = m_r)
+    {
+        const double lnl = s->cfgs[0].coulomb_lnl;
+        for (int q = 0; q < 6; ++q) {
+            const int zb = q == 0 ? -1 : ZQ[SP_CUP + q - 1];
+            const double mab = q == 0 ? 0.5 * ME : mr;
+            const double qq = (double)(-1) * (double)zb * QE * QE;
+            cc.kc[q] = qq * qq * lnl / (8.0 * PI * EPS0_C * EPS0_C * mab * mab);
+        }
+    }
     const int ch0[NCLS] = {CH_EL, CH_SW, CH_S3, CH_S3, CH_S4, CH_CX, CH_NN}, nch[NCLS] = {4, 1, 1, 1, 1, 1, 1};
     for (int k = 0; k < NCLS; ++k) {
         const double kd = (double)(k < NECLS ? cc.kmr : cc.kmr_h);
@@ -365,7 +382,15 @@ pd_status upload_ck(pd_sim* s) {
                 (float)(0.5 * c.weight * (double)s->cc.sgmax[6] * dth / cell_volume(c, j));
         }
     }
+    // W dt_coll / V_cell(j) per row: a cell's density times dt_coll per particle
+    std::vector<double> cw(s->L.rows);
+    for (int r = 0; r < s->R; ++r) {
+        const pd_config& c = s->cfgs[r];
+        const double dtc = c.dt * c.coll_dt_scale;
+        for (int j = 0; j < c.nr; ++j) cw[s->runs[r].row_base + j] = c.weight * dtc / cell_volume(c, j);
+    }
     CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->cw, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return PD_OK;
 }
@@ -415,7 +440,11 @@ pd_status validate_one(const pd_config* c, std::string& msg) {
     if (!(c->coll_dt_scale >= 0)) { msg = "coll_dt_scale must be >= 0"; return PD_ERR_ARG; }
     if (c->heavy_coll != 0 && c->heavy_coll != 1) { msg = "heavy_coll must be 0 or 1"; return PD_ERR_ARG; }
     if (c->charge_max < 2 || c->charge_max > 4) { msg = "charge_max must be 2, 3 or 4"; return PD_ERR_ARG; }
-    if (c->reserved0 != 0) { msg = "reserved0 must be 0"; return PD_ERR_ARG; }
+    if (c->coulomb != 0 && c->coulomb != 1) { msg = "coulomb must be 0 or 1"; return PD_ERR_ARG; }
+    if (c->coulomb && !(c->coulomb_lnl > 0.0 && std::isfinite(c->coulomb_lnl))) {
+        msg = "coulomb_lnl must be positive";
+        return PD_ERR_ARG;
+    }
     if (c->geometry == PD_GEOM_RZ && c->inject_on) {
         if (!(c->tip_radius > 0) || c->tip_radius / c->dr > 63) { msg = "tip must span 1..63 cells"; return PD_ERR_ARG; }
     }
@@ -433,7 +462,8 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         const pd_config &a = cfgs[0], &b = cfgs[r];
         if (b.geometry != a.geometry || b.dt != a.dt || b.heavy_subcycle != a.heavy_subcycle ||
             b.field_mode != a.field_mode || b.coll_dt_scale != a.coll_dt_scale || b.di_on != a.di_on ||
-            b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll || b.charge_max != a.charge_max) {
+            b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll || b.charge_max != a.charge_max ||
+            b.coulomb != a.coulomb || b.coulomb_lnl != a.coulomb_lnl) {
             msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale, double-ionization "
                   "or heavy-collision settings";
             return PD_ERR_ARG;
@@ -600,7 +630,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     {
         Timed t(s, K_COLLIDE, capturing, 3);
         launch_collide(s->A, s->B, s->off, s->nc, s->nc2, s->cand_off, s->active, s->mid, s->big, s->st, s->rho_e, s->rho_h,
-                       s->xsE, s->xs, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
+                       s->xsE, s->xs, s->cw, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
                        s->stream);
     }
     {
@@ -655,7 +685,8 @@ bool same_config(const pd_config& a, const pd_config& b) {
            a.work_function == b.work_function && a.neutral_ratio == b.neutral_ratio &&
            a.neutral_T == b.neutral_T && a.poisson_tol == b.poisson_tol &&
            a.poisson_max_cycles == b.poisson_max_cycles && a.heavy_coll == b.heavy_coll &&
-           a.charge_max == b.charge_max && a.capacity == b.capacity;
+           a.charge_max == b.charge_max && a.coulomb == b.coulomb && a.coulomb_lnl == b.coulomb_lnl &&
+           a.capacity == b.capacity;
 }
 
 struct File {
@@ -820,6 +851,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->xsE = PF(L.xsE);
     s->xs = PF(L.xs);
     s->ck = PF(L.ck);
+    s->cw = (double*)(w + L.cw);
     s->ray = PF(L.ray);
     s->hist = (unsigned long long*)(w + L.hist);
     s->spc = (unsigned long long*)(w + L.spc);
@@ -855,7 +887,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     std::vector<uint16_t> cell_run(L.ncell);
     std::vector<RunState> rs(n);
     s->ic.resize(n);
-    uint32_t cb = 0, nb = 0, kb = 0;
+    uint32_t cb = 0, nb = 0, kb = 0, rb = 0;
     for (int r = 0; r < n; ++r) {
         const pd_config& c = cf[r];
         RunInfo& RI = s->runs[r];
@@ -871,6 +903,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
         RI.seed = c.seed;
         RI.run = c.run;
         RI.ck_base = kb;
+        RI.row_base = rb;
         const double dte = c.dt, dth = c.dt * c.heavy_subcycle;
         for (int sp = 0; sp < NSP; ++sp) {
             const double dts = sp == SP_E ? dte : dth;
@@ -884,6 +917,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
         cb += RI.ncell;
         nb += (uint32_t)run_nodes(c);
         kb += (uint32_t)NCLS * (uint32_t)c.nr;
+        rb += (uint32_t)c.nr;
         circ[r] = RunCircuit{c.V0, c.R_ohm, c.C_farad};
         std::memset(&rs[r], 0, sizeof(RunState));
         rs[r].V = c.V0;
@@ -1134,7 +1168,8 @@ pd_status pd_config_default(pd_config* c) {
     c->poisson_max_cycles = 60;
     c->heavy_coll = 0;
     c->charge_max = 2;
-    c->reserved0 = 0;
+    c->coulomb = 0;
+    c->coulomb_lnl = 10.0;
     c->capacity = 1 << 16;
     return PD_OK;
 }

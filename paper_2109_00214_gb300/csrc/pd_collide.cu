@@ -385,7 +385,7 @@ __device__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uin
 }
 
 // Rank tables of the lists that k_collide will use and k_ncand queued for
-// this kernel (entries cell << 3 | species bin 0..5; *nq of them, at most
+// this kernel (entries cell << 3 | species bin 0..6; *nq of them, at most
 // max_q): one list per block at a time, NT threads, sorted in shared memory
 // up to MAXN ids and in the scratch buffers above that.  A list already in
 // ascending id order gets the identity.
@@ -562,10 +562,11 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         uint32_t N[NSP] = {0, 0, 0, 0, 0, 0, 0};
         int r = -1;
         if (c < C) {
-            // list lengths (Cu4+ is drawn by no class; Cu3+ has bins with charge_max >= 3)
+            // list lengths (Cu3+ and Cu4+ have bins with charge_max >= 3; Cu4+ is
+            // drawn only by the Coulomb pairs)
 #pragma unroll
-            for (int sp = 0; sp < 6; ++sp)
-                if (sp < 5 || q3) N[sp] = off[sp * C + c + 1] - off[sp * C + c];
+            for (int sp = 0; sp < NSP; ++sp)
+                if ((sp < 5 || q3) && (sp < 6 || P.coulomb)) N[sp] = off[sp * C + c + 1] - off[sp * C + c];
             const uint32_t Nt[NECLS] = {N[SP_CU], N[SP_CUP], N[SP_CU2_SW], N[SP_CU2_DI], N[SP_CU3]};
             bool ecls = false;
             for (int k = 0; k < NECLS; ++k) ecls |= Nt[k] > 0;
@@ -616,20 +617,33 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
                 atomicAdd(&P.rs[r].ctr[C_CAND], (unsigned long long)nh);
             }
         }
-        // lookups of each species' list over the classes that draw from it
-        uint32_t look[6];
+        // lookups of each species' list over the classes that draw from it;
+        // the Coulomb pairs look up every electron and every ion of a cell
+        // with electrons (k_collide counts the same)
+        uint32_t look[NSP];
         look[SP_E] = n[0] + n[1] + n[2] + n[3] + n[4];
         look[SP_CU] = n[0] + n[5] + 2u * n[6];
         look[SP_CUP] = n[1] + n[5];
         look[SP_CU2_SW] = n[2];
         look[SP_CU2_DI] = n[3];
         look[SP_CU3] = n[4];
-        const uint32_t ntot = look[SP_E] + nh;
+        look[SP_CU4] = 0;
+        uint32_t ncoul = 0;          // Coulomb pairs of the cell
+        if (P.coulomb && N[SP_E] > 0) {
+            look[SP_E] += N[SP_E];
+            ncoul = N[SP_E] / 2u;
+#pragma unroll
+            for (int sp = SP_CUP; sp < NSP; ++sp) {
+                look[sp] += N[sp];
+                ncoul += N[sp] > 0 ? max(N[SP_E], N[sp]) : 0u;
+            }
+        }
+        const uint32_t ntot = n[0] + n[1] + n[2] + n[3] + n[4] + nh + ncoul;
         const bool act = c < C && ntot > 0;
         const uint32_t RL = 32u * RC;
         bool long_list = false;
 #pragma unroll
-        for (int sp = 0; sp < 6; ++sp) long_list |= look[sp] > 0 && N[sp] > RL;
+        for (int sp = 0; sp < NSP; ++sp) long_list |= look[sp] > 0 && N[sp] > RL;
         const bool heavy = act && (ntot > 32u || long_list);
         unsigned lt;
         asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
@@ -644,7 +658,7 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         if (act) {
             // the lists k_collide will rank that need a block's sort (long,
             // with more lookups than select8 serves)
-            for (uint32_t sp = 0; sp < 6; ++sp) {
+            for (uint32_t sp = 0; sp < (uint32_t)NSP; ++sp) {
                 if (look[sp] == 0 || N[sp] <= RANK_WARP_MAX || look[sp] <= SELECT_LOOKUPS) continue;
                 const bool large = N[sp] > RANK_MID_MAX;
                 const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
@@ -665,6 +679,7 @@ struct CellCtx {
     uint32_t id0;                    // id of the first reserved slot
     uint32_t s;                      // spawned so far
     uint32_t ev[NCH], nulls, consumed, thr, viol, fb;
+    uint32_t coul_ee, coul_ei;       // Coulomb pair collisions applied
 };
 
 __device__ bool spawn_electron(Particles& A, CellCtx& cx, DevState* st, long long* rho_e, uint32_t gcell, float pz,
@@ -844,13 +859,238 @@ __device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k,
     ++cx.ev[CH_NN];
 }
 
+// ---------------------------------------------------------------------
+// Coulomb collisions (listed by Sec. 2.3 without a method): the binary
+// collision model of Takizuka and Abe (1977).  A pair with relative velocity
+// u turns by theta, tan(theta / 2) = delta, delta = sqrt(Kn / u^3) Z with Z
+// normal (here the Irwin-Hall sum of twelve uniforms), about a uniform
+// azimuth; |u| is kept and the change is shared by the reduced mass.  Kn =
+// (q_a q_b)^2 n_L lnL dt / (8 pi eps0^2 m_ab^2).  The float operations are
+// those of the oracle's float build, in the same order.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float irwin_hall12(Stream& st) {
+    float z = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) z = z + st.u01();
+    return z - 6.0f;
+}
+
+__device__ bool coulomb_kin(Stream& st, V3& va, V3& vb, float Kn, float fa, float fb_, uint32_t& fb) {
+    const float ux = va.x - vb.x, uy = va.y - vb.y, uz = va.z - vb.z;
+    const float u2 = (ux * ux + uy * uy) + uz * uz;
+    if (!(u2 > 0.0f)) return false;
+    const float u = sqrtf(u2);
+    float var = Kn / (u2 * u);
+    var = var < 1e30f ? var : 1e30f;                // u -> 0: keep delta finite
+    const float z = irwin_hall12(st);
+    const float d = sqrtf(var) * z;
+    // sin(theta) = 2 delta / (1 + delta^2), 1 - cos(theta) = 2 delta^2 / (1 + delta^2)
+    float sth, omc;
+    const float ad = d < 0.0f ? -d : d;
+    if (ad <= 1.0f) {
+        const float d2 = d * d, den = 1.0f + d2;
+        sth = (2.0f * d) / den;
+        omc = (2.0f * d2) / den;
+    } else {
+        const float rr = 1.0f / d, r2 = rr * rr, den = 1.0f + r2;
+        sth = (2.0f * rr) / den;
+        omc = 2.0f / den;
+    }
+    float cph, sph;
+    azimuth(st, cph, sph, fb);
+    const float sc = sth * cph, ss = sth * sph;
+    const float up = sqrtf(ux * ux + uy * uy);
+    float dx, dy, dz;
+    if (up > 0.0f) {
+        const float a1 = ux / up, a2 = uy / up;
+        dx = ((a1 * uz) * sc - (a2 * u) * ss) - ux * omc;
+        dy = ((a2 * uz) * sc + (a1 * u) * ss) - uy * omc;
+        dz = -(up * sc) - uz * omc;
+    } else {                                         // u along the third axis
+        dx = uz * sc;
+        dy = uz * ss;
+        dz = -(uz * omc);
+    }
+    va.x = va.x + fa * dx; va.y = va.y + fa * dy; va.z = va.z + fa * dz;
+    vb.x = vb.x - fb_ * dx; vb.y = vb.y - fb_ * dy; vb.z = vb.z - fb_ * dz;
+    return true;
+}
+
+// Pseudo-random permutation of [0, n): four Feistel rounds (Luby and Rackoff)
+// on 2h bits, 4^h >= n, with an integer mixing round function, walked back
+// into [0, n) by cycle walking (Black and Rogaway, 2002).  The walk ends
+// within 4^h steps because x itself lies in [0, n).
+__device__ __forceinline__ uint32_t fe_round(uint32_t x, uint32_t k) {
+    uint32_t t = (x ^ k) * 0x9E3779B1u;
+    t ^= t >> 15;
+    t *= 0x85EBCA77u;
+    t ^= t >> 13;
+    return t;
+}
+__device__ uint32_t perm_index(uint32_t x, uint32_t n, const uint4& key) {
+    int h = 1;
+    while ((1ull << (2 * h)) < (unsigned long long)n) ++h;
+    const uint32_t mask = (1u << h) - 1u;
+    const unsigned long long lim = 1ull << (2 * h);
+    uint32_t y = x;
+    for (unsigned long long it = 0; it < lim; ++it) {
+        uint32_t L = y >> h, R = y & mask;
+        const uint32_t k4[4] = {key.x, key.y, key.z, key.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t F = fe_round(R, k4[r]) & mask;
+            const uint32_t t = L ^ F;
+            L = R;
+            R = t;
+        }
+        y = (L << h) | R;
+        if (y < n) return y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint4 stream_key(Stream& st) {
+    const uint32_t a = st.next(), b = st.next(), c = st.next(), d = st.next();
+    return make_uint4(a, b, c, d);
+}
+
+// position of each lane's rank in list L (has: the lane has one; nb: lanes
+// 0..nb-1 may have one); called by the whole warp
+__device__ __forceinline__ uint32_t rank_position(const IdList& L, uint32_t rank, bool has, uint32_t nb, int lane) {
+    if (L.sorted) return rank;
+    if (L.table) return has ? L.table[rank] : 0u;
+    uint32_t pos = 0;
+    for (uint32_t q = 0; q < nb; ++q) {
+        const uint32_t p = select_rank_list(L, __shfl_sync(FULL, rank, (int)q), lane);
+        if ((uint32_t)lane == q) pos = p;
+    }
+    return pos;
+}
+
+// The Coulomb pairs of one cell (after its DSMC classes), by its warp:
+// class 0 pairs the electrons two by two in a random order (an odd count
+// ends with a triple of three pairs at half the time step); class 1 + i pairs
+// each particle of the more numerous of the electrons and ion species i
+// (Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+) once, the k-th in a random order with
+// the (k mod N_fewer)-th of the other species in a random order, in rounds of
+// N_fewer disjoint pairs; n_L is the density of the fewer.  The lists are
+// those of the step's start; an ion ionized earlier this step is left out.
+// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts);
+// el_dsmc: the electron list as the DSMC classes left it, or null.
+__device__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
+                             const uint32_t* __restrict__ off, uint32_t C, uint32_t c, uint32_t lc, uint32_t look_e,
+                             const uint32_t (&look_ion)[5], int nsp, int id_top, int lane, DevState* st,
+                             const CollConsts& cc, const double* __restrict__ cw, const IdList* el_dsmc) {
+    const RunInfo* RI = cx.RI;
+    const uint32_t e_base = off[c], Ne = off[c + 1] - e_base;
+    const double wv = cw[RI->row_base + lc % (uint32_t)RI->nr];
+    IdList el;
+    if (el_dsmc) el = *el_dsmc;
+    else load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
+    if (Ne >= 2) {
+        Stream ps(lc, st->step, SID_COUL_PERM | 0u, RI->seed, RI->run);
+        const uint4 key = stream_key(ps);
+        const float Kn = (float)(cc.kc[0] * (double)Ne * wv);
+        const uint32_t P = Ne / 2u - (Ne % 2u);      // regular pairs
+        for (uint32_t m0 = 0; m0 < P; m0 += 32) {
+            const uint32_t nb = min(32u, P - m0);
+            const uint32_t k = m0 + (uint32_t)lane;
+            const bool has = (uint32_t)lane < nb;
+            const uint32_t ra = has ? perm_index(2u * k, Ne, key) : 0u;
+            const uint32_t rb = has ? perm_index(2u * k + 1u, Ne, key) : 0u;
+            const uint32_t pa = rank_position(el, ra, has, nb, lane);
+            const uint32_t pb = rank_position(el, rb, has, nb, lane);
+            if (has && pa < Ne && pb < Ne) {
+                const uint32_t ia = e_base + pa, ib = e_base + pb;
+                V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
+                Stream rs(lc, st->step, sid_coul(0, k), RI->seed, RI->run);
+                if (coulomb_kin(rs, va, vb, Kn, 0.5f, 0.5f, cx.fb)) {
+                    A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
+                    A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
+                    ++cx.coul_ee;
+                }
+            } else if (has) {
+                set_error(st, ERR_BOUNDS);
+            }
+        }
+        __syncwarp();
+        if (Ne % 2u) {                               // the last three: a triple, in order
+            const bool has = lane < 3;
+            const uint32_t rk = has ? perm_index(Ne - 3u + (uint32_t)lane, Ne, key) : 0u;
+            const uint32_t pk = rank_position(el, rk, has, 3u, lane);
+            const uint32_t p0 = __shfl_sync(FULL, pk, 0), p1 = __shfl_sync(FULL, pk, 1), p2 = __shfl_sync(FULL, pk, 2);
+            if (lane == 0) {
+                if (p0 < Ne && p1 < Ne && p2 < Ne) {
+                    const uint32_t t[3] = {e_base + p0, e_base + p1, e_base + p2};
+                    const float Kh = Kn * 0.5f;
+                    for (int q = 0; q < 3; ++q) {
+                        const uint32_t ia = t[q], ib = t[(q + 1) % 3];
+                        V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
+                        Stream rs(lc, st->step, sid_coul(0, P + (uint32_t)q), RI->seed, RI->run);
+                        if (coulomb_kin(rs, va, vb, Kh, 0.5f, 0.5f, cx.fb)) {
+                            A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
+                            A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
+                            ++cx.coul_ee;
+                        }
+                    }
+                } else {
+                    set_error(st, ERR_BOUNDS);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (int i = 0; i < 5 && Ne > 0; ++i) {
+        const int sp = SP_CUP + i;
+        if (sp >= nsp) break;
+        const uint32_t i_base = off[(uint32_t)sp * C + c], Ni = off[(uint32_t)sp * C + c + 1] - i_base;
+        if (Ni == 0) continue;
+        IdList il;
+        load_ids(il, A.id, i_base, Ni, look_ion[i], S, sbuf, lane, id_top);
+        const bool e_many = Ne >= Ni;
+        const uint32_t Na = e_many ? Ne : Ni, Nb = e_many ? Ni : Ne;
+        Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)(1 + i), RI->seed, RI->run);
+        const uint4 ka = stream_key(ps), kb = stream_key(ps);
+        const float Kn = (float)(cc.kc[1 + i] * (double)Nb * wv);
+        // rounds of Nb pairs: within a round no particle appears twice
+        for (uint32_t r0 = 0; r0 < Na; r0 += Nb) {
+            const uint32_t re = min(r0 + Nb, Na);
+            for (uint32_t m0 = r0; m0 < re; m0 += 32) {
+                const uint32_t nb = min(32u, re - m0);
+                const uint32_t k = m0 + (uint32_t)lane;
+                const bool has = (uint32_t)lane < nb;
+                const uint32_t a = has ? perm_index(k, Na, ka) : 0u;
+                const uint32_t b = has ? perm_index(k - r0, Nb, kb) : 0u;
+                const uint32_t pe = rank_position(el, e_many ? a : b, has, nb, lane);
+                const uint32_t pi = rank_position(il, e_many ? b : a, has, nb, lane);
+                if (has && pe < Ne && pi < Ni) {
+                    const uint32_t ie = e_base + pe, ii = i_base + pi;
+                    const uint32_t ikey = A.key[ii];
+                    if (!(ikey & KEY_FLAG) && (int)key_species(ikey) == sp) {
+                        V3 ve{A.vz[ie], A.vr[ie], A.vt[ie]}, vi{A.vz[ii], A.vr[ii], A.vt[ii]};
+                        Stream rs(lc, st->step, sid_coul(1 + i, k), RI->seed, RI->run);
+                        if (coulomb_kin(rs, ve, vi, Kn, cc.a_e, cc.a_t, cx.fb)) {
+                            A.vz[ie] = ve.x; A.vr[ie] = ve.y; A.vt[ie] = ve.z;
+                            A.vz[ii] = vi.x; A.vr[ii] = vi.y; A.vt[ii] = vi.z;
+                            ++cx.coul_ei;
+                        }
+                    }
+                } else if (has) {
+                    set_error(st, ERR_BOUNDS);
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                  const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
                                                  const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
                                                  long long* rho_h, const float* __restrict__ xsE,
-                                                 const float* __restrict__ xs, KParams P, CollConsts cc,
-                                                 uint32_t nbins) {
+                                                 const float* __restrict__ xs, const double* __restrict__ cw,
+                                                 KParams P, CollConsts cc, uint32_t nbins) {
     __shared__ uint32_t s_sort[4][4 * RANK_WARP_MAX + 256];   // per-warp rank-table sort
     const int lane = threadIdx.x & 31;
     uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
@@ -897,6 +1137,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         cx.s = 0;
         for (int q = 0; q < NCH; ++q) cx.ev[q] = 0;
         cx.nulls = cx.consumed = cx.thr = cx.viol = cx.fb = 0;
+        cx.coul_ee = cx.coul_ei = 0;
         if (cx.slot0 + cx.nres > P.capacity) {
             // no room for this cell's spawns: report, and leave its reserved
             // slots (those that exist) dead
@@ -908,8 +1149,10 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         const uint32_t e_base = off[c];
         const uint32_t Ne = off[c + 1] - e_base;
         // lookups of each list over all classes (the rank-table decisions of
-        // k_ncand use the same totals)
-        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z;
+        // k_ncand use the same totals): the Coulomb pairs look up every
+        // electron and every ion of a cell with electrons
+        const bool coul = P.coulomb && Ne > 0;
+        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (coul ? Ne : 0u);
         const uint32_t look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
         // the first list of a pair: electrons for the electron classes, Cu for
         // the heavy classes (loaded over the electrons' list once those are done)
@@ -932,7 +1175,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             const uint32_t t_base = off[tb];
             const uint32_t Nt = off[tb + 1] - t_base;
             // the target list's lookups over every class that draws from it
-            const uint32_t t_look = ts == SP_CU ? look_cu : ts == SP_CUP ? look_ci : ncand;
+            const uint32_t t_look = ts == SP_CU ? look_cu : (ts == SP_CUP ? look_ci : ncand) + (coul ? Nt : 0u);
             IdList tl;
             load_ids(tl, A.id, t_base, Nt, t_look, S, sbuf, lane, id_top);
             // candidates in batches of 32: lane q draws candidate m0 + q's pair and
@@ -1052,8 +1295,22 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 __syncwarp();
             }
         }
+        if (coul) {
+            // ion lists' lookups: the DSMC classes' plus one per ion
+            const uint32_t look_ion[5] = {look_ci, n2.x, n2.y, n2.z, 0u};
+            uint32_t look_all[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
+                look_all[i] = look_ion[i] + (SP_CUP + i < P.nsp ? off[b + 1] - off[b] : 0u);
+            }
+            // the electrons' list is still loaded unless a heavy class replaced it
+            coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, id_top, lane, st, cc, cw,
+                         cu_first ? nullptr : &el);
+        }
         const uint32_t s = __shfl_sync(FULL, cx.s, 0);
         for (uint32_t q = s + lane; q < cx.nres; q += 32) A.key[cx.slot0 + q] = DEAD;
+        cx.fb = __reduce_add_sync(FULL, cx.fb);      // the Coulomb pairs sample on every lane
         if (lane == 0) {
             RunState& rsv = P.rs[r];
             for (int q = 0; q < NCH; ++q)
@@ -1063,6 +1320,14 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             if (cx.thr) atomicAdd(&rsv.ctr[C_THR], (unsigned long long)cx.thr);
             if (cx.viol) atomicAdd(&rsv.ctr[C_VIOL], (unsigned long long)cx.viol);
             if (cx.fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)cx.fb);
+        }
+        if (coul) {
+            // every lane applied pairs: sum the warp's counts
+            const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
+            if (lane == 0) {
+                if (ee) atomicAdd(&P.rs[r].ctr[C_COUL_EE], (unsigned long long)ee);
+                if (ei) atomicAdd(&P.rs[r].ctr[C_COUL_EI], (unsigned long long)ei);
+            }
         }
     }
 }
@@ -1224,14 +1489,16 @@ void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, u
 void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
-                    const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s) {
+                    const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
+                    cudaStream_t s) {
     const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
                         reinterpret_cast<uint32_t*>(B.vz), B.id};
     k_rank_tables<RT_MID_THREADS, RANK_MID_MAX><<<sms * RT_MID_BLOCKS_PER_SM, RT_MID_THREADS, RT_MID_SMEM, s>>>(
         A.id, S, off, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
     k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
         A.id, S, off, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
-    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, P, cc, nbins);
+    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P, cc,
+                                   nbins);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {

@@ -38,7 +38,7 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 // counter slots (see PD_NCOUNTERS in pd.h)
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
               C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 34, C_EV_NN = 35, C_EV_S3 = 36, C_EV_S4 = 37,
-              NCOUNTERS = 38;
+              C_COUL_EE = 38, C_COUL_EI = 39, NCOUNTERS = 40;
 // counter of the events of channel ch (channels 5-8 follow the absorption block)
 __host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : C_EV_CX + (ch - CH_CX); }
 
@@ -77,6 +77,7 @@ struct RunInfo {
     uint32_t cell_base, node_base, ncell;
     uint32_t seed, run;              // Philox key of the run
     uint32_t ck_base;                // c_k(j) of the run at ck[ck_base + k * nr + j]
+    uint32_t row_base;               // W dt_coll / V_cell(j) of the run at cw[row_base + j]
     float qmdt[NSP];                 // z e / m * dt_s
     float dtz[NSP], dtr[NSP];        // dt_s / dz, dt_s / dr
     double weight;
@@ -89,6 +90,7 @@ struct CollConsts {
     float a_e, a_t;                  // m_r / m_e, m_r / M
     float kth[NCH];                  // 2 E_th e / m_r
     float sgmax[NCLS];               // NTC majorants of the pair classes, in class order
+    double kc[6];                    // Coulomb (q_a q_b)^2 lnL / (8 pi eps0^2 m_ab^2): e-e, e with Cu+ .. Cu4+
     int di_split_mode;
 };
 
@@ -108,6 +110,7 @@ struct KParams {
     int heavy_coll;                  // heavy pair classes on heavy steps
     int charge_max;                  // highest ion charge (2, 3 or 4): step-wise classes on
     int nsp;                         // species with bins: 5, or 7 with charge_max >= 3
+    int coulomb;                     // Coulomb pair collisions after the DSMC classes
     int field_on;                    // gather E in the push
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
@@ -163,6 +166,10 @@ struct Stream {
 
 __host__ __device__ constexpr uint32_t sid_cand(int k, uint32_t m) { return ((uint32_t)k << 28) | m; }
 constexpr uint32_t SID_NCAND = 0xE0000000u;
+// Coulomb classes 0 (e-e) and 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+):
+// pair k of class c, and the permutation keys of class c (SID_COUL_PERM | c)
+__host__ __device__ constexpr uint32_t sid_coul(int c, uint32_t k) { return ((uint32_t)(c + 8) << 28) | k; }
+constexpr uint32_t SID_COUL_PERM = 0xE1000000u;
 constexpr uint32_t SID_INJ_COUNT = 0xD0000000u;
 __host__ __device__ constexpr uint32_t sid_inj_e(uint32_t p) { return 0xD1000000u | p; }
 __host__ __device__ constexpr uint32_t sid_inj_cu(uint32_t p) { return 0xD2000000u | p; }

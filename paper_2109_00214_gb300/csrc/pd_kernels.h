@@ -74,8 +74,10 @@ void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, u
 // the two rank-table kernels, then k_collide (three launches)
 void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
+// cw: W dt_coll / V_cell per row (Coulomb pairs)
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
-                    const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid, cudaStream_t s);
+                    const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
+                    cudaStream_t s);
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 

@@ -225,6 +225,42 @@ def test_species_above_charge_max_refused_gpu(pd, xs):
         sim.synchronize()
 
 
+@pytest.mark.parametrize("charge_max,heavy_coll,scale,steps", [
+    (2, 0, 1.0, 3),
+    (4, 1, 3000.0, 3),             # every ion species, after the step-wise and heavy classes
+])
+def test_microbench_coulomb_bit_exact(pd, xs, charge_max, heavy_coll, scale, steps):
+    cfg, parts = synthetic.microbench(nz=32, nr=48, total=6e4, coll_scale=scale, seed=5)
+    cfg.update(coulomb=1, charge_max=charge_max, heavy_coll=heavy_coll, capacity=max(cfg["capacity"], 1 << 21))
+    if charge_max > 2:
+        parts = _with_charge_states(parts, charge_max)
+        sp = parts["species"].copy()
+        sp[np.flatnonzero(sp == 5)[::2]] = 6           # some Cu4+ as well
+        parts = dict(parts, species=sp)
+    sim, o = run_pair(pd, cfg, parts, xs, steps)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["coul_ee"] > 0 and gc["coul_ei"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
+@pytest.mark.parametrize("n_e,n_t,ncells", [
+    (20000, 9000, 1),              # 20000 electrons: rank tables in the scratch buffers
+    (300, 3000, 1),                # more ions than electrons: each electron in ten rounds
+    (2000, 1, 1),                  # one ion: 2000 rounds of one pair
+    (701, 300, 2),                 # about 350 electrons per cell, odd counts: triples
+])
+def test_dense_coulomb_cells_bit_exact(pd, xs, n_e, n_t, ncells):
+    cfg, parts = synthetic.rate_cell(n_e=n_e, n_t=n_t, Te_eV=5.0, seed=12, coll_scale=1.0, target_species=2,
+                                     ncells=ncells)
+    cfg.update(nz=2, nr=max(2, ncells), coulomb=1)
+    sim, o = run_pair(pd, cfg, parts, xs, 2)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["coul_ee"] > 0 and gc["coul_ei"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
 def _rz_field(n, V0, seed=3):
     rng = np.random.default_rng(seed)
     Ez = np.full((n + 1, n + 1), -V0 / 6e-6) * (1 + 0.3 * rng.uniform(-1, 1, (n + 1, n + 1)))
