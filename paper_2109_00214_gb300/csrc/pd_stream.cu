@@ -276,21 +276,55 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 if (link[q])
 #pragma unroll
                     for (int c = 0; c < 4; ++c) W[q - 1][c] += W[q][c];
+            // r-z plumes hold cells of thousands of particles: when all 128
+            // particles of the warp deposit into one cell, the warp sums the
+            // four corner weights and issues four atomics instead of 128
+            bool one_cell_warp = false;
+            if constexpr (RZ) {
+                const uint32_t k0 = __shfl_sync(FULL_MASK, key[0], 0);
+                const bool one_cell = dep[0] && dep[1] && dep[2] && dep[3] && key[0] == k0 && key[1] == k0 &&
+                                      key[2] == k0 && key[3] == k0;
+                one_cell_warp = __all_sync(FULL_MASK, one_cell);
+            }
+            if (one_cell_warp) {
+                unsigned long long Ws[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!len[q]) continue;
-                const long long zq = charge_of(sp_[q]);
-                long long* rho = sp_[q] == SP_E ? rho_e : rho_h;
-                const RunInfo& RI = MULTI ? s_runs[run_[q]] : P.run0;
-                const int iz = iz_[q], ir = ir_[q];
-                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)],
-                          (unsigned long long)(zq * (long long)W[q][0]));
-                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir)],
-                          (unsigned long long)(zq * (long long)W[q][1]));
-                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir + 1)],
-                          (unsigned long long)(zq * (long long)W[q][2]));
-                atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir + 1)],
-                          (unsigned long long)(zq * (long long)W[q][3]));
+                for (int c = 0; c < 4; ++c) {
+                    Ws[c] = W[0][c];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) Ws[c] += __shfl_down_sync(FULL_MASK, Ws[c], o);
+                }
+                if ((threadIdx.x & 31u) == 0) {
+                    const long long zq = charge_of(sp_[0]);
+                    long long* rho = sp_[0] == SP_E ? rho_e : rho_h;
+                    const RunInfo& RI = MULTI ? s_runs[run_[0]] : P.run0;
+                    const int iz = iz_[0], ir = ir_[0];
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)],
+                              (unsigned long long)(zq * (long long)Ws[0]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir)],
+                              (unsigned long long)(zq * (long long)Ws[1]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir + 1)],
+                              (unsigned long long)(zq * (long long)Ws[2]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir + 1)],
+                              (unsigned long long)(zq * (long long)Ws[3]));
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!len[q]) continue;
+                    const long long zq = charge_of(sp_[q]);
+                    long long* rho = sp_[q] == SP_E ? rho_e : rho_h;
+                    const RunInfo& RI = MULTI ? s_runs[run_[q]] : P.run0;
+                    const int iz = iz_[q], ir = ir_[q];
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir)],
+                              (unsigned long long)(zq * (long long)W[q][0]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir)],
+                              (unsigned long long)(zq * (long long)W[q][1]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz, ir + 1)],
+                              (unsigned long long)(zq * (long long)W[q][2]));
+                    atomicAdd((unsigned long long*)&rho[node_of(RI, geom, iz + 1, ir + 1)],
+                              (unsigned long long)(zq * (long long)W[q][3]));
+                }
             }
         }
         if (gv && (flags & 16u)) {
