@@ -48,6 +48,7 @@ class _Cfg(C.Structure):
         ("neutral_ratio", C.c_double), ("neutral_T", C.c_double),
         ("poisson_tol", C.c_double), ("capacity", C.c_int64), ("heavy_coll", C.c_int32),
         ("charge_max", C.c_int32), ("coulomb", C.c_int32), ("coulomb_lnl", C.c_double),
+        ("sputter", C.c_int32), ("sputter_T", C.c_double),
     ]
 
 
@@ -65,6 +66,7 @@ def _lib(fp64):
         L.or_create.argtypes = [C.POINTER(_Cfg)]
         L.or_destroy.argtypes = [P]
         L.or_set_xs.argtypes = [P, C.c_int, D, D, C.c_int, C.c_double]
+        L.or_set_yield.argtypes = [P, D, D, C.c_int]
         L.or_load.restype = C.c_int64
         L.or_load.argtypes = [P, C.c_int64, P, P, P, D, D, D, D, D]
         L.or_set_field.argtypes = [P, D, D]
@@ -114,7 +116,7 @@ COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consum
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
                     for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
-                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei"])
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei", "sput_cathode", "sput_anode"])
 SCALAR_NAMES = ["t", "V", "I_gap", "gamma", "Qbar", "erosion", "mass", "charge", "sgmax0",
                 "sgmax1", "poisson_relres", "poisson_iters", "E_abs_cathode", "E_abs_anode",
                 "E_abs_wall"]
@@ -160,6 +162,8 @@ class Oracle:
         c.charge_max = cfg.get("charge_max", 2)
         c.coulomb = cfg.get("coulomb", 0)
         c.coulomb_lnl = cfg.get("coulomb_lnl", 10.0)
+        c.sputter = cfg.get("sputter", 0)
+        c.sputter_T = cfg.get("sputter_T", 23209.0)
         self._c = c
         self.h = self.L.or_create(C.byref(c))
         rz = c.geom == 0
@@ -177,6 +181,13 @@ class Oracle:
             E = np.ascontiguousarray(E, np.float64)
             s = np.ascontiguousarray(s, np.float64)
             self.L.or_set_xs(self.h, int(ch), _dptr(E), _dptr(s), len(E), float(th))
+
+    def set_sputter_yield(self, E, Y):
+        """Sputtering yield (atoms per ion) against impact energy (eV)."""
+        E = np.ascontiguousarray(E, np.float64)
+        Y = np.ascontiguousarray(Y, np.float64)
+        if self.L.or_set_yield(self.h, _dptr(E), _dptr(Y), len(E)):
+            raise ValueError("yield table needs at least two points")
 
     def load(self, parts):
         n = len(parts["species"])

@@ -99,6 +99,8 @@ typedef struct {
     int32_t charge_max;    /* highest ion charge: 2 (Cu2+), 3 (+ Cu2+ -> Cu3+), 4 (+ Cu3+ -> Cu4+) */
     int32_t coulomb;       /* Coulomb collisions e-e and e-ion (binary collision model) on */
     double coulomb_lnl;    /* Coulomb logarithm */
+    int32_t sputter;       /* ion-impact sputtering at the electrodes on */
+    double sputter_T;      /* temperature (K) of the sputtered atoms' effusive flux */
 } or_cfg;
 
 typedef struct {
@@ -125,6 +127,10 @@ typedef struct {
     /* counters */
     uint64_t events[NCH], nulls, consumed, thr_rej, ratio_viol, iso_fallback, cand_total;
     uint64_t coul_ee, coul_ei;   /* Coulomb pair collisions applied */
+    uint64_t sput[2];            /* atoms sputtered from the cathode, the anode */
+    real ytab[XS_N];             /* sputtering yield Y(E) on the cross-section grid */
+    struct sput_rec* srec;       /* this step's ion impacts on the electrodes */
+    int64_t nsrec, srec_cap;
     uint64_t absorbed[3][NSP];   /* cathode, anode, outer wall */
     double absorbed_energy[3];   /* J (physical, includes W) */
     uint64_t emitted_e, emitted_cu;
@@ -200,6 +206,9 @@ static uint32_t pick(stream_t* s, uint32_t n) { return (uint32_t)(((uint64_t)nex
 #define SID_INJ_COUNT 0xD0000000u
 #define SID_INJ_E(p) (0xD1000000u | (uint32_t)(p))
 #define SID_INJ_CU(p) (0xD2000000u | (uint32_t)(p))
+/* sputtering: the count of an ion impact, the j-th sputtered atom (subject: the ion's id) */
+#define SID_SPUT 0xD3000000u
+#define SID_SPUT_ATOM(j) (0xD4000000u | (uint32_t)(j))
 
 /* ------------------------------------------------------------------ */
 /* geometry                                                             */
@@ -244,7 +253,9 @@ static void xs_build_grid(or_sim* S) {
 }
 /* sigma_c(eps) by linear interpolation between the bracketing grid points;
  * below the first point the first value, at or above the last point zero. */
-static real xs_lookup(const or_sim* S, int ch, real eps) {
+/* linear interpolation of a table on the cross-section grid, 0 at or above
+ * the grid's end, the first value below its start */
+static real tab_lookup(const or_sim* S, const real* tab, real eps) {
     if (!(eps < (real)S->xsE[XS_N - 1])) return R_(0);
     int k;
     if (eps < (real)S->xsE[0]) {
@@ -258,8 +269,9 @@ static real xs_lookup(const or_sim* S, int ch, real eps) {
         k = lo;
     }
     real t = (eps - (real)S->xsE[k]) / ((real)S->xsE[k + 1] - (real)S->xsE[k]);
-    return S->xs[ch][k] + t * (S->xs[ch][k + 1] - S->xs[ch][k]);
+    return tab[k] + t * (tab[k + 1] - tab[k]);
 }
+static real xs_lookup(const or_sim* S, int ch, real eps) { return tab_lookup(S, S->xs[ch], eps); }
 
 /* pair classes, in the order a cell applies them: the electron classes
  * (e, Cu), (e, Cu+), (e, Cu2+ SW), (e, Cu2+ DI), (e, Cu3+) (the last three
@@ -342,12 +354,32 @@ void or_destroy(or_sim* S) {
     free(S->sp); free(S->iz); free(S->ir); free(S->pz); free(S->pr);
     free(S->vz); free(S->vr); free(S->vt); free(S->id);
     free(S->rho_e); free(S->rho_h); free(S->phi); free(S->Ez); free(S->Er);
+    free(S->srec);
     free(S);
 }
 
 /* Cross section of one channel, given as (E_eV, sigma_m2) pairs (ascending
  * E); resampled by linear interpolation onto the grid (identity when the
  * input already sits on the grid).  Zero below the threshold. */
+/* sputtering yield Y(E) (sputtered atoms per ion, E the impact energy in eV),
+ * resampled onto the cross-section grid like the cross sections */
+int or_set_yield(or_sim* S, const double* E, const double* Y, int n) {
+    if (n < 2) return 1;
+    for (int k = 0; k < XS_N; ++k) {
+        double e = (double)S->xsE[k], v;
+        if (e <= E[0]) v = Y[0];
+        else if (e >= E[n - 1]) v = Y[n - 1];
+        else {
+            int a = 0;
+            while (E[a + 1] <= e) ++a;
+            double t = (e - E[a]) / (E[a + 1] - E[a]);
+            v = Y[a] + t * (Y[a + 1] - Y[a]);
+        }
+        S->ytab[k] = R_(v);
+    }
+    return 0;
+}
+
 int or_set_xs(or_sim* S, int ch, const double* E, const double* sig, int n, double threshold) {
     if (ch < 0 || ch >= NCH || n < 2) return 1;
     for (int k = 0; k < XS_N; ++k) {
@@ -503,6 +535,70 @@ static double kinetic(const or_sim* S, int64_t p) {
     return 0.5 * species_mass(S->sp[p]) * v2;
 }
 
+/* ------------------------------------------------------------------ */
+/* Ion-impact sputtering (Sec. 2.3: energetic ions arriving at the        */
+/* electrodes sputter neutrals into the domain, yield of Yamamura and     */
+/* Tawara [32]; the yield is an input table here).  An ion super-particle */
+/* of impact energy E absorbed at the cathode or the anode yields         */
+/* floor(Y(E) + R) Cu super-particles of the same weight, emitted from the */
+/* impact point (same r, on the electrode surface) into the gap with an    */
+/* effusive flux at sputter_T: Rayleigh normal and transverse speeds,      */
+/* uniform azimuth.  Impacts are taken in ascending ion id, so the new     */
+/* atoms' ids do not depend on the order of the push.  An impact beyond    */
+/* the outer radius (a corner crossing) sputters nothing.                 */
+/* ------------------------------------------------------------------ */
+typedef struct sput_rec { uint32_t id; int el; int ir; real pr; real Y; } sput_rec;
+
+static int cmp_sput(const void* a, const void* b) {
+    uint32_t x = ((const sput_rec*)a)->id, y = ((const sput_rec*)b)->id;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+static void sputter_record(or_sim* S, int64_t p, int el) {
+    if (S->ir[p] >= S->c.nr) return;
+    if (S->nsrec == S->srec_cap) {
+        S->srec_cap = S->srec_cap ? 2 * S->srec_cap : 1024;
+        S->srec = (sput_rec*)realloc(S->srec, (size_t)S->srec_cap * sizeof(sput_rec));
+    }
+    sput_rec* r = &S->srec[S->nsrec++];
+    r->id = S->id[p];
+    r->el = el;
+    r->ir = S->ir[p];
+    r->pr = S->pr[p];
+    r->Y = tab_lookup(S, S->ytab, R_(kinetic(S, p) / QE));
+}
+
+static real rayleigh(const or_sim* S, real U);
+static void azimuth(or_sim* S, stream_t* st, real* c, real* s);
+
+static int sputter_emit(or_sim* S) {
+    if (S->nsrec > 1) qsort(S->srec, (size_t)S->nsrec, sizeof(sput_rec), cmp_sput);
+    real vth = R_(sqrt(KB * S->c.sputter_T / M_CU));
+    for (int64_t q = 0; q < S->nsrec; ++q) {
+        const sput_rec* r = &S->srec[q];
+        stream_t st;
+        stream_init(&st, S, r->id, S->step, SID_SPUT);
+        uint32_t n = (uint32_t)OR_FLOOR(r->Y + u01(&st));
+        for (uint32_t j = 0; j < n; ++j) {
+            stream_t sp;
+            stream_init(&sp, S, r->id, S->step, SID_SPUT_ATOM(j));
+            real U1 = u01(&sp), U2 = u01(&sp);
+            real vn = vth * rayleigh(S, U1);
+            real s = vth * rayleigh(S, U2);
+            real cp, sn;
+            azimuth(S, &sp, &cp, &sn);
+            int iz = r->el == 0 ? 0 : S->c.nz - 1;
+            real pz = r->el == 0 ? R_(0) : ONE_MINUS_ULP;
+            if (append_particle(S, SP_CU, iz, r->ir, pz, r->pr, r->el == 0 ? vn : -vn, s * cp, s * sn,
+                                S->id_next++) < 0)
+                return 1;
+            S->sput[r->el]++;
+        }
+    }
+    S->nsrec = 0;
+    return 0;
+}
+
 static void push_all(or_sim* S, int heavy_step) {
     double dte = S->c.dt, dth = S->c.dt * S->c.heavy_subcycle;
     double IgapQ = 0.0;
@@ -515,6 +611,7 @@ static void push_all(or_sim* S, int heavy_step) {
         int out = push_one(S, p, qmdt, dtz, dtr);
         if (out) {
             int el = out - 1;
+            if (S->c.sputter && el < 2 && ZQ[s] > 0) sputter_record(S, p, el);
             S->absorbed[el][s] += 1;
             S->absorbed_energy[el] += S->c.weight * kinetic(S, p);
             /* gap current leaves the anode node: an arriving charge z e W lowers it */
@@ -1315,6 +1412,7 @@ int or_step(or_sim* S, int nsteps) {
         int heavy_step = (S->step % (uint32_t)S->c.heavy_subcycle) == 0;
         if (inject(S)) return 2;
         push_all(S, heavy_step);
+        if (S->c.sputter && sputter_emit(S)) return 2;
         deposit_all(S, heavy_step);
         if (collide_all(S, heavy_step)) return 3;
         if (S->c.geom == 0) {
@@ -1385,6 +1483,7 @@ void or_get_counters(const or_sim* S, uint64_t* out) {
     out[k++] = S->events[CH_CX]; out[k++] = S->events[CH_NN];
     out[k++] = S->events[CH_S3]; out[k++] = S->events[CH_S4];
     out[k++] = S->coul_ee; out[k++] = S->coul_ei;
+    out[k++] = S->sput[0]; out[k++] = S->sput[1];
 }
 
 /* scalars: t, V, I_gap, gamma, Qbar, erosion (kg/C), mass ledger (kg),
@@ -1403,7 +1502,8 @@ void or_get_scalars(const or_sim* S, double* out) {
     double qbar = ions > 0 ? qsum / ions : 0.0;
     double heavy_back = 0;
     for (int s = 1; s < NSP; ++s) heavy_back += (double)S->absorbed[0][s];
-    double mass = M_CU * S->c.weight * ((double)S->emitted_cu - heavy_back);
+    /* net Cu leaving the cathode: injected and sputtered neutrals less the heavies it absorbed */
+    double mass = M_CU * S->c.weight * ((double)S->emitted_cu + (double)S->sput[0] - heavy_back);
     double charge = S->charge_cathode;
     out[0] = S->step * S->c.dt;
     out[1] = S->V;

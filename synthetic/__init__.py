@@ -8,5 +8,6 @@ library and the CPU oracle can be fed the very same arrays.
 from .workloads import (  # noqa: F401
     SPECIES, SPECIES_NAMES, xs_grid, standin_cross_sections, base_config,
     microbench, rz_breakdown, rz_plume, rate_cell, heavy_cells, concat_loads, ensemble_breakdown,
+    standin_sputter_yield,
     ENSEMBLE_GRIDS, ENSEMBLE_VOLTS_KV,
 )

@@ -13,8 +13,8 @@ that made it, Sec. 2.3):
 import math
 import numpy as np
 
-SPECIES = {"e": 0, "Cu": 1, "Cu+": 2, "Cu2+SW": 3, "Cu2+DI": 4}
-SPECIES_NAMES = ["e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI"]
+SPECIES = {"e": 0, "Cu": 1, "Cu+": 2, "Cu2+SW": 3, "Cu2+DI": 4, "Cu3+": 5, "Cu4+": 6}
+SPECIES_NAMES = ["e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+"]
 
 # CODATA values, used here only to draw thermal velocities of the inputs.
 _QE = 1.602176634e-19
@@ -77,6 +77,16 @@ def standin_cross_sections(thresholds=None, peaks=None, sigma_el=5e-20, e_el=10.
     out[5] = (E, s_cx * np.maximum(1.0 - k_cx * np.log(E), 0.0) ** 2, 0.0)
     out[6] = (E, np.full_like(E, math.pi * d_cu * d_cu), 0.0)
     return out
+
+
+def standin_sputter_yield(e_th=25.0, y0=2.0, power=2.5):
+    """A stand-in for the ion-impact sputtering yield of Cu on Cu (the paper
+    takes it from Yamamura and Tawara [32], whose formula and fitted
+    parameters are not available): Y(E) = y0 (1 - sqrt(e_th / E))^power above
+    the threshold e_th (eV), 0 below.  Returns (E_eV, Y) on the table grid."""
+    E = xs_grid()
+    Y = np.where(E > e_th, y0 * np.clip(1.0 - np.sqrt(e_th / E), 0.0, None) ** power, 0.0)
+    return E, Y
 
 
 def base_config(**kw):
