@@ -64,7 +64,7 @@ enum { PD_SP_E = 0, PD_SP_CU = 1, PD_SP_CUP = 2, PD_SP_CU2_SW = 3, PD_SP_CU2_DI 
 enum { PD_CH_ELASTIC = 0, PD_CH_EXCITATION = 1, PD_CH_SI = 2, PD_CH_DI = 3, PD_CH_SW = 4,
        PD_CH_CX = 5, PD_CH_NN = 6, PD_CH_S3 = 7, PD_CH_S4 = 8, PD_NCH = 9 };
 
-#define PD_CONFIG_VERSION 3u
+#define PD_CONFIG_VERSION 4u
 
 /* Run parameters (Sec. 2.3 gives: 50 nm cells, 1 fs electron step, heavy step
  * ten times longer, W = 100, 2.9 kV through R = 1 kOhm with C = 1 pF, a 200 nm
@@ -100,6 +100,11 @@ typedef struct pd_config {
                                   model of Takizuka and Abe); 0 (default): off */
     int64_t capacity;          /* particle slots */
     double coulomb_lnl;        /* Coulomb logarithm (default 10) */
+    int32_t sputter;           /* 1: ions absorbed at an electrode sputter Cu atoms into
+                                  the gap, floor(Y(E) + R) per ion super-particle (yield
+                                  from pd_set_sputter_yield); 0 (default): off */
+    int32_t reserved1;         /* 0 */
+    double sputter_T;          /* temperature (K) of the sputtered atoms' effusive flux */
 } pd_config;
 
 /* Scalars of the current state (Sec. 3: arc current and voltage, Eq. (21)
@@ -130,8 +135,9 @@ typedef struct pd_scalars {
  * isotropic-sampling fallbacks, candidates in total, electrons emitted,
  * neutrals emitted, absorbed [electrode 3][species 7], then events of charge
  * exchange, Cu-Cu elastic, Cu2+ -> Cu3+ and Cu3+ -> Cu4+, then Coulomb pair
- * collisions e-e and e-ion. */
-#define PD_NCOUNTERS 40
+ * collisions e-e and e-ion, then atoms sputtered from the cathode and from
+ * the anode. */
+#define PD_NCOUNTERS 42
 
 typedef struct pd_sim pd_sim;
 
@@ -158,6 +164,14 @@ pd_status pd_create(const pd_config* cfg, void* dev_workspace, size_t bytes, voi
  * NTC majorants.  Synchronous with respect to the host. */
 pd_status pd_set_cross_section(pd_sim* sim, int channel, const double* E_eV, const double* sigma_m2,
                                int n, double threshold_eV);
+
+/* Ion-impact sputtering yield (Sec. 2.3; the paper's yield is that of
+ * Yamamura and Tawara): Y(E) sputtered Cu atoms per ion arriving at an
+ * electrode with kinetic energy E, as n >= 2 points (E_eV ascending, Y) in
+ * host memory, copied and resampled like a cross section (no threshold: the
+ * table carries its own).  Used when pd_config.sputter is 1; the default
+ * table is zero.  Synchronous with respect to the host. */
+pd_status pd_set_sputter_yield(pd_sim* sim, const double* E_eV, const double* Y, int n);
 
 /* Append n particles given on the host in cell-relative form: species code,
  * cell indices iz, ir, offsets pz, pr in [0, 1) inside the cell, velocities

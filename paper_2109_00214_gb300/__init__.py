@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "config_from_dict",
-           "pd_config_default", "pd_workspace_size", "pd_create", "pd_set_cross_section",
+           "pd_config_default", "pd_workspace_size", "pd_create", "pd_set_cross_section", "pd_set_sputter_yield",
            "pd_load_particles", "pd_load_particles_device", "pd_set_field", "pd_inject_cathode",
            "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots",
            "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
@@ -30,14 +30,14 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
-PD_NCOUNTERS = 40
+PD_NCOUNTERS = 42
 PD_NKERNELS = 12
 GEOM = {"rz": 0, "xy_periodic": 1}
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
                     for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
-                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei"])
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei", "sput_cathode", "sput_anode"])
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CAPACITY", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
           5: "PD_ERR_NONFINITE", 6: "PD_ERR_STATE"}
 
@@ -54,7 +54,8 @@ class PdConfig(C.Structure):
         ("tip_radius", C.c_double), ("work_function", C.c_double), ("neutral_ratio", C.c_double),
         ("neutral_T", C.c_double), ("poisson_tol", C.c_double), ("poisson_max_cycles", C.c_int32),
         ("heavy_coll", C.c_int32), ("charge_max", C.c_int32), ("coulomb", C.c_int32),
-        ("capacity", C.c_int64), ("coulomb_lnl", C.c_double),
+        ("capacity", C.c_int64), ("coulomb_lnl", C.c_double), ("sputter", C.c_int32), ("reserved1", C.c_int32),
+        ("sputter_T", C.c_double),
     ]
 
 
@@ -100,6 +101,7 @@ _SIGS = {
     "pd_workspace_size": (C.c_int, [C.POINTER(PdConfig), C.POINTER(C.c_size_t)]),
     "pd_create": (C.c_int, [C.POINTER(PdConfig), P, C.c_size_t, P, C.POINTER(P)]),
     "pd_set_cross_section": (C.c_int, [P, C.c_int, Dp, Dp, C.c_int, C.c_double]),
+    "pd_set_sputter_yield": (C.c_int, [P, Dp, Dp, C.c_int]),
     "pd_load_particles": (C.c_int, [P, C.c_int64, P, P, P, P, P, P, P, P]),
     "pd_load_particles_device": (C.c_int, [P, C.c_int64, P, P, P, P, P, P, P, P]),
     "pd_set_field": (C.c_int, [P, Dp, Dp]),
@@ -214,6 +216,8 @@ def config_from_dict(d):
     c.charge_max = d.get("charge_max", 2)
     c.coulomb = d.get("coulomb", 0)
     c.coulomb_lnl = d.get("coulomb_lnl", 10.0)
+    c.sputter = d.get("sputter", 0)
+    c.sputter_T = d.get("sputter_T", 23209.0)
     c.capacity = d["capacity"]
     return c
 
@@ -236,6 +240,12 @@ def pd_create(cfg, workspace_ptr, nbytes, stream_ptr):
     _check(None, _lib().pd_create(C.byref(cfg), P(workspace_ptr), nbytes, P(stream_ptr), C.byref(h)),
            "pd_create")
     return h
+
+
+def pd_set_sputter_yield(h, E, Y):
+    E = np.ascontiguousarray(E, np.float64)
+    Y = np.ascontiguousarray(Y, np.float64)
+    _check(h, _lib().pd_set_sputter_yield(h, _dp(E), _dp(Y), len(E)), "pd_set_sputter_yield")
 
 
 def pd_set_cross_section(h, ch, E, sig, threshold):
@@ -642,6 +652,9 @@ class Simulation:
     def set_cross_sections(self, xs):
         for ch, (E, s, th) in xs.items():
             pd_set_cross_section(self.h, ch, E, s, th)
+
+    def set_sputter_yield(self, E, Y):
+        pd_set_sputter_yield(self.h, E, Y)
 
     def load(self, parts):
         pd_load_particles(self.h, parts)

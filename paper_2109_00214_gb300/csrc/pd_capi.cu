@@ -52,12 +52,14 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cw, cand, cand_off, active, mid, big, rho_e,
+    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cw, ytab, squeue, cand, cand_off, active,
+        mid, big, rho_e,
         rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
     uint32_t nbins_pad, ncell_pad, words_pad;
     int nsp;                         // species with bins
+    uint32_t squeue_cap;             // sputtering impacts per step
     uint64_t cap, ncell, nodes, ck_len, rows;
     size_t field_bytes;
 };
@@ -123,6 +125,9 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.ck = take(ckl * 4);
     L.cw = take(rows * 8);                                 // W dt_coll / V_cell per row (Coulomb densities)
     L.ray = take(1024 * 4);
+    L.ytab = take(XS_N * 4);                               // sputtering yield on the table grid
+    L.squeue_cap = cf[0].sputter ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>(cap / 16, 4096), 1u << 20) : 16u;
+    L.squeue = take((size_t)L.squeue_cap * sizeof(SputRec));
     L.hist = take(4096 * 8);
     L.spc = take((size_t)R * NSP * 8);                     // live particles per run and species
     L.state = take(sizeof(DevState));
@@ -168,8 +173,10 @@ struct pd_sim {
     long long *rho_e, *rho_h, *diag;
     float2* E;
     double* phi;
-    float *xsE, *xs, *ck, *ray;
+    float *xsE, *xs, *ck, *ray, *ytab;
     double* cw;
+    SputRec* squeue;
+    float h_ytab[XS_N];
     unsigned long long *hist, *spc;
     DevState* st;
     RunState* rs;
@@ -288,6 +295,12 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.charge_max = s->cfgs[0].charge_max;
     P.nsp = s->L.nsp;
     P.coulomb = s->cfgs[0].coulomb;
+    P.sputter = s->cfgs[0].sputter;
+    P.sput_vth = (float)std::sqrt(KB * s->cfgs[0].sputter_T / M_CU);
+    P.xsE = s->xsE;
+    P.ytab = s->ytab;
+    P.squeue = s->squeue;
+    P.squeue_cap = s->L.squeue_cap;
     P.field_on = c.field_mode != PD_FIELD_NONE;
     P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
@@ -441,6 +454,12 @@ pd_status validate_one(const pd_config* c, std::string& msg) {
     if (c->heavy_coll != 0 && c->heavy_coll != 1) { msg = "heavy_coll must be 0 or 1"; return PD_ERR_ARG; }
     if (c->charge_max < 2 || c->charge_max > 4) { msg = "charge_max must be 2, 3 or 4"; return PD_ERR_ARG; }
     if (c->coulomb != 0 && c->coulomb != 1) { msg = "coulomb must be 0 or 1"; return PD_ERR_ARG; }
+    if (c->sputter != 0 && c->sputter != 1) { msg = "sputter must be 0 or 1"; return PD_ERR_ARG; }
+    if (c->reserved1 != 0) { msg = "reserved1 must be 0"; return PD_ERR_ARG; }
+    if (c->sputter && !(c->sputter_T > 0.0 && std::isfinite(c->sputter_T))) {
+        msg = "sputter_T must be positive";
+        return PD_ERR_ARG;
+    }
     if (c->coulomb && !(c->coulomb_lnl > 0.0 && std::isfinite(c->coulomb_lnl))) {
         msg = "coulomb_lnl must be positive";
         return PD_ERR_ARG;
@@ -463,7 +482,8 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         if (b.geometry != a.geometry || b.dt != a.dt || b.heavy_subcycle != a.heavy_subcycle ||
             b.field_mode != a.field_mode || b.coll_dt_scale != a.coll_dt_scale || b.di_on != a.di_on ||
             b.di_split_mode != a.di_split_mode || b.heavy_coll != a.heavy_coll || b.charge_max != a.charge_max ||
-            b.coulomb != a.coulomb || b.coulomb_lnl != a.coulomb_lnl) {
+            b.coulomb != a.coulomb || b.coulomb_lnl != a.coulomb_lnl || b.sputter != a.sputter ||
+            b.sputter_T != a.sputter_T) {
             msg = "runs differ in geometry, dt, heavy_subcycle, field_mode, coll_dt_scale, double-ionization "
                   "or heavy-collision settings";
             return PD_ERR_ARG;
@@ -599,6 +619,11 @@ pd_status issue_step(pd_sim* s, bool capturing) {
         launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, gpart,
                     s->stream);
     }
+    if (c.sputter && heavy && c.geometry == PD_GEOM_RZ) {
+        // ions reach the electrodes on heavy steps: their sputtered atoms join this step's sort
+        Timed t(s, K_INJECT, capturing, 1);
+        launch_sputter(s->A, s->st, P, s->ray, s->count, s->stream);
+    }
     {
         Timed t(s, K_SCAN_BINS, capturing, P.use_prev ? 8 : 4);
         launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
@@ -664,7 +689,7 @@ int graph_period(const pd_sim* s) {
 
 // ---- checkpoint file: a header, then the sections in a fixed order ----
 constexpr char CKPT_MAGIC[8] = {'P', 'D', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr uint32_t CKPT_VERSION = 1;
+constexpr uint32_t CKPT_VERSION = 2;
 
 struct CkptHeader {
     char magic[8];
@@ -686,7 +711,7 @@ bool same_config(const pd_config& a, const pd_config& b) {
            a.neutral_T == b.neutral_T && a.poisson_tol == b.poisson_tol &&
            a.poisson_max_cycles == b.poisson_max_cycles && a.heavy_coll == b.heavy_coll &&
            a.charge_max == b.charge_max && a.coulomb == b.coulomb && a.coulomb_lnl == b.coulomb_lnl &&
-           a.capacity == b.capacity;
+           a.sputter == b.sputter && a.sputter_T == b.sputter_T && a.capacity == b.capacity;
 }
 
 struct File {
@@ -853,6 +878,8 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->ck = PF(L.ck);
     s->cw = (double*)(w + L.cw);
     s->ray = PF(L.ray);
+    s->ytab = PF(L.ytab);
+    s->squeue = (SputRec*)(w + L.squeue);
     s->hist = (unsigned long long*)(w + L.hist);
     s->spc = (unsigned long long*)(w + L.spc);
     s->st = (DevState*)(w + L.state);
@@ -877,6 +904,7 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
         s->h_xsE[k] = (float)std::ldexp(1.0 + (double)j / XS_SUB, ex);
     }
     std::memset(s->h_xs, 0, sizeof(s->h_xs));
+    std::memset(s->h_ytab, 0, sizeof(s->h_ytab));
     for (int k = 0; k < NCH; ++k) s->eth[k] = 0.0;
     update_collision_consts(s);
     for (int k = 0; k < 1024; ++k) s->h_ray[k] = (float)std::sqrt(-2.0 * std::log(1.0 - (double)k / 1024.0));
@@ -1080,7 +1108,8 @@ pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
     out->Qbar = ions > 0 ? qsum / ions : 0.0;
     double heavy_back = 0;
     for (int sp = 1; sp < NSP; ++sp) heavy_back += (double)d.ctr[C_ABS + 0 * NSP + sp];
-    out->mass = M_CU * c.weight * ((double)d.ctr[C_EMIT_CU] - heavy_back);
+    // net Cu leaving the cathode: injected and sputtered neutrals less the heavies it absorbed
+    out->mass = M_CU * c.weight * ((double)d.ctr[C_EMIT_CU] + (double)d.ctr[C_SPUT_C] - heavy_back);
     out->charge = d.charge_cathode;
     out->erosion = out->charge != 0 ? out->mass / out->charge : 0.0;
     out->sgmax[0] = s->cc.sgmax[0];
@@ -1170,6 +1199,9 @@ pd_status pd_config_default(pd_config* c) {
     c->charge_max = 2;
     c->coulomb = 0;
     c->coulomb_lnl = 10.0;
+    c->sputter = 0;
+    c->reserved1 = 0;
+    c->sputter_T = 23209.0;
     c->capacity = 1 << 16;
     return PD_OK;
 }
@@ -1231,6 +1263,30 @@ pd_status pd_set_cross_section(pd_sim* s, int ch, const double* E, const double*
     drop_graph(s);
     CK(cudaMemcpyAsync(s->xs + (size_t)ch * XS_N, s->h_xs[ch], XS_N * 4, cudaMemcpyHostToDevice, s->stream));
     return upload_ck(s);
+}
+
+pd_status pd_set_sputter_yield(pd_sim* s, const double* E, const double* Y, int n) {
+    if (!s) return PD_ERR_ARG;
+    if (n < 2 || !E || !Y) return fail(s, PD_ERR_ARG, "bad sputtering-yield arguments");
+    for (int a = 0; a + 1 < n; ++a)
+        if (!(E[a + 1] > E[a])) return fail(s, PD_ERR_ARG, "yield energies must ascend");
+    for (int k = 0; k < XS_N; ++k) {
+        const double e = (double)s->h_xsE[k];
+        double v;
+        if (e <= E[0]) v = Y[0];
+        else if (e >= E[n - 1]) v = Y[n - 1];
+        else {
+            int a = 0;
+            while (E[a + 1] <= e) ++a;
+            const double t = (e - E[a]) / (E[a + 1] - E[a]);
+            v = Y[a] + t * (Y[a + 1] - Y[a]);
+        }
+        s->h_ytab[k] = (float)v;
+    }
+    drop_graph(s);
+    CK(cudaMemcpyAsync(s->ytab, s->h_ytab, sizeof(s->h_ytab), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
 }
 
 pd_status pd_load_particles(pd_sim* s, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
@@ -1506,7 +1562,8 @@ pd_status pd_save(pd_sim* s, const char* path) {
     h.nodes = total_nodes(s);
     h.cap = s->L.cap;
     bool ok = F.put(&h, sizeof(h)) && F.put(s->cfgs.data(), s->cfgs.size() * sizeof(pd_config)) &&
-              F.put(s->h_xs, sizeof(s->h_xs)) && F.put(s->eth, sizeof(s->eth)) && F.put(&d, sizeof(d));
+              F.put(s->h_xs, sizeof(s->h_xs)) && F.put(s->eth, sizeof(s->eth)) &&
+              F.put(s->h_ytab, sizeof(s->h_ytab)) && F.put(&d, sizeof(d));
     if (!ok) return fail(s, PD_ERR_ARG, "checkpoint write failed");
     const size_t nodes = (size_t)h.nodes, n = (size_t)h.n_slots;
     const void* arrays[7] = {s->A.key, s->A.pz, s->A.pr, s->A.vz, s->A.vr, s->A.vt, s->A.id};
@@ -1544,8 +1601,9 @@ pd_status pd_load(pd_sim* s, const char* path) {
         if (!same_config(cf[k], s->cfgs[k])) return fail(s, PD_ERR_ARG, "checkpoint configs differ from this simulation's");
     float xs[NCH][XS_N];
     double eth[NCH];
+    float ytab[XS_N];
     DevState d;
-    if (!F.get(xs, sizeof(xs)) || !F.get(eth, sizeof(eth)) || !F.get(&d, sizeof(d)))
+    if (!F.get(xs, sizeof(xs)) || !F.get(eth, sizeof(eth)) || !F.get(ytab, sizeof(ytab)) || !F.get(&d, sizeof(d)))
         return fail(s, PD_ERR_ARG, "checkpoint file is truncated");
     if (d.n_slots != h.n_slots) return fail(s, PD_ERR_ARG, "inconsistent checkpoint");
     drop_graph(s);
@@ -1563,8 +1621,10 @@ pd_status pd_load(pd_sim* s, const char* path) {
     CK(cudaMemsetAsync(s->A.key + n, 0xFF, (size_t)(s->L.cap - n) * 4, s->stream));
     std::memcpy(s->h_xs, xs, sizeof(xs));
     std::memcpy(s->eth, eth, sizeof(eth));
+    std::memcpy(s->h_ytab, ytab, sizeof(ytab));
     update_collision_consts(s);
     CK(cudaMemcpyAsync(s->xs, s->h_xs, sizeof(s->h_xs), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->ytab, s->h_ytab, sizeof(s->h_ytab), cudaMemcpyHostToDevice, s->stream));
     d.error = 0;
     d.load_bad = 0;
     CK(cudaMemcpyAsync(s->st, &d, sizeof(d), cudaMemcpyHostToDevice, s->stream));

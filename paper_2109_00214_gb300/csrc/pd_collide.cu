@@ -26,22 +26,6 @@ struct V3 {
     float x, y, z;
 };
 
-// sigma(eps): linear interpolation on the grid E_k = 2^e (1 + j/64); the
-// bracketing index comes from the exponent and top six mantissa bits of eps.
-__device__ __forceinline__ float xs_lookup(const float* __restrict__ E, const float* __restrict__ s, float eps) {
-    if (!(eps < E[XS_N - 1])) return 0.0f;
-    int k;
-    if (eps < E[0]) {
-        k = 0;
-        eps = E[0];
-    } else {
-        const uint32_t b = __float_as_uint(eps);
-        k = ((int)(b >> 23) - 127 - XS_EMIN_EXP) * XS_SUB + (int)((b >> 17) & 63u);
-    }
-    const float t = (eps - E[k]) / (E[k + 1] - E[k]);
-    return s[k] + t * (s[k + 1] - s[k]);
-}
-
 // isotropic unit vector, Marsaglia (1972)
 __device__ V3 iso_dir(Stream& st, uint32_t& fb) {
     for (int a = 0; a < 64; ++a) {
@@ -1349,6 +1333,7 @@ __global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, con
         st->n_mid = 0;
         st->n_big = 0;
         st->collide_next = 0;
+        st->n_sput = 0;
     }
     // the step is over for every kernel that draws from it
     if (blockIdx.x == 0 && threadIdx.x == 0) st->step += 1u;
@@ -1474,12 +1459,146 @@ __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __res
 constexpr size_t RT_SMEM = (size_t)RANK_BLOCK_MAX * 4 * sizeof(uint32_t);
 constexpr size_t RT_MID_SMEM = (size_t)RANK_MID_MAX * 4 * sizeof(uint32_t);
 
+// ---------------------------------------------------------------------
+// Ion-impact sputtering (Sec. 2.3), after the push: each run's block takes
+// the impacts the push recorded for it, sorts them by the ion's id, and
+// appends their atoms after the slots in use (the sort that follows places
+// them), with ids from the run's next id in that order.  An atom leaves the
+// impact point on the electrode surface with an effusive flux at
+// sputter_T: Rayleigh normal and transverse speeds, uniform azimuth.
+// ---------------------------------------------------------------------
+constexpr int SPUT_THREADS = 1024;
+constexpr uint32_t SPUT_MAX = 8192;              // impacts per run and step
+constexpr size_t SPUT_SMEM = SPUT_MAX * sizeof(unsigned long long);
+
+__global__ void __launch_bounds__(SPUT_THREADS) k_sputter(Particles A, DevState* st, KParams P,
+                                                          const float* __restrict__ ray, uint32_t* in_cnt) {
+    extern __shared__ unsigned long long s_key[];    // ion id << 32 | record index
+    __shared__ uint32_t s_cnt, s_el[2], s_wsum[SPUT_THREADS / 32];
+    __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_id0, s_ok;
+    const int r = blockIdx.x;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t nq = min(st->n_sput, P.squeue_cap);
+    if (tid == 0) {
+        s_cnt = 0u;
+        s_el[0] = s_el[1] = 0u;
+    }
+    __syncthreads();
+    for (uint32_t x = tid; x < nq; x += SPUT_THREADS) {
+        const SputRec rec = P.squeue[x];
+        if ((int)(rec.meta >> 1) != r) continue;
+        const uint32_t k = atomicAdd(&s_cnt, 1u);
+        if (k < SPUT_MAX) s_key[k] = ((unsigned long long)rec.id << 32) | x;
+    }
+    __syncthreads();
+    const uint32_t m = s_cnt;
+    if (m == 0u) return;
+    if (m > SPUT_MAX) {
+        if (tid == 0) set_error(st, ERR_CAPACITY);
+        return;
+    }
+    // bitonic sort of the keys, padded with all-ones to a power of two
+    uint32_t np2 = 1u;
+    while (np2 < m) np2 <<= 1;
+    for (uint32_t x = m + tid; x < np2; x += SPUT_THREADS) s_key[x] = ~0ull;
+    __syncthreads();
+    for (uint32_t kk = 2u; kk <= np2; kk <<= 1)
+        for (uint32_t j = kk >> 1; j > 0u; j >>= 1) {
+            for (uint32_t x = tid; x < np2; x += SPUT_THREADS) {
+                const uint32_t y = x ^ j;
+                if (y > x) {
+                    const unsigned long long a = s_key[x], b = s_key[y];
+                    if ((a > b) == ((x & kk) == 0u)) {
+                        s_key[x] = b;
+                        s_key[y] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    // atoms per impact in id order: each thread a contiguous chunk, an
+    // exclusive scan of the chunk sums across the block
+    const uint32_t per = (m + SPUT_THREADS - 1u) / SPUT_THREADS;
+    const uint32_t c0 = min(tid * per, m), c1 = min(c0 + per, m);
+    uint32_t sum = 0;
+    for (uint32_t i = c0; i < c1; ++i) {
+        const SputRec rec = P.squeue[(uint32_t)s_key[i]];
+        sum += rec.n;
+        atomicAdd(&s_el[rec.meta & 1u], rec.n);
+    }
+    const int lane = (int)(tid & 31u), w = (int)(tid >> 5);
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) s_wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t v = s_wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += u;
+        }
+        s_wsum[lane] = v;                            // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t total = s_wsum[SPUT_THREADS / 32 - 1];
+    uint32_t off = (w > 0 ? s_wsum[w - 1] : 0u) + incl - sum;
+    if (tid == 0) {
+        const unsigned long long base = atomicAdd(&st->n_slots, (unsigned long long)total);
+        s_ok = base + total <= P.capacity ? 1u : 0u;
+        if (!s_ok) set_error(st, ERR_CAPACITY);
+        s_base = base;
+        RunState& rs = P.rs[r];
+        s_id0 = rs.id_next;
+        if ((unsigned long long)rs.id_next + total > 0xFFFFFFFFull) set_error(st, ERR_IDS);
+        rs.id_next += total;
+        if (s_el[0]) rs.ctr[C_SPUT_C] += s_el[0];
+        if (s_el[1]) rs.ctr[C_SPUT_A] += s_el[1];
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const RunInfo& RI = P.runs[r];
+    uint32_t fb = 0;
+    for (uint32_t i = c0; i < c1; ++i) {
+        const SputRec rec = P.squeue[(uint32_t)s_key[i]];
+        const uint32_t el = rec.meta & 1u;
+        const int iz = el == 0u ? 0 : RI.nz - 1;
+        const float pz = el == 0u ? 0.0f : 0x1.fffffep-1f;
+        const uint32_t gcell = RI.cell_base + (uint32_t)iz * (uint32_t)RI.nr + rec.ir;
+        for (uint32_t j = 0; j < rec.n; ++j, ++off) {
+            Stream sp(rec.id, st->step, sid_sput_atom(j), RI.seed, RI.run);
+            const float U1 = sp.u01(), U2 = sp.u01();
+            const float vn = P.sput_vth * rayleigh(ray, U1);
+            const float sv = P.sput_vth * rayleigh(ray, U2);
+            float cp, sn;
+            azimuth(sp, cp, sn, fb);
+            const unsigned long long slot = s_base + off;
+            A.key[slot] = make_key(SP_CU, gcell);
+            A.pz[slot] = pz;
+            A.pr[slot] = rec.pr;
+            A.vz[slot] = el == 0u ? vn : -vn;
+            A.vr[slot] = sv * cp;
+            A.vt[slot] = sv * sn;
+            A.id[slot] = s_id0 + off;
+            atomicAdd(&in_cnt[(uint32_t)SP_CU * P.ncell + gcell], 1u);
+        }
+    }
+    if (fb) atomicAdd(&P.rs[r].ctr[C_ISOFB], (unsigned long long)fb);
+}
+
 cudaError_t collide_setup() {
     cudaError_t e = cudaFuncSetAttribute(k_rank_tables<RT_THREADS, RANK_BLOCK_MAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_rank_tables<RT_MID_THREADS, RANK_MID_MAX>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_MID_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sputter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPUT_SMEM);
     return e;
 }
 void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
@@ -1504,6 +1623,11 @@ void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_o
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(off, nbins, cand_off, st, P, circ, dt, circuit);
 }
+void launch_sputter(const Particles& A, DevState* st, const KParams& P, const float* ray, uint32_t* in_cnt,
+                    cudaStream_t s) {
+    k_sputter<<<P.nruns, SPUT_THREADS, SPUT_SMEM, s>>>(A, st, P, ray, in_cnt);
+}
+
 void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts* ic,
                    const float* ray, cudaStream_t s) {
     k_inject<<<P.nruns, 256, 0, s>>>(A, E, st, P, ic, ray);

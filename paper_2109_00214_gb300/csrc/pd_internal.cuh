@@ -38,7 +38,7 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 // counter slots (see PD_NCOUNTERS in pd.h)
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
               C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 34, C_EV_NN = 35, C_EV_S3 = 36, C_EV_S4 = 37,
-              C_COUL_EE = 38, C_COUL_EI = 39, NCOUNTERS = 40;
+              C_COUL_EE = 38, C_COUL_EI = 39, C_SPUT_C = 40, C_SPUT_A = 41, NCOUNTERS = 42;
 // counter of the events of channel ch (channels 5-8 follow the absorption block)
 __host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : C_EV_CX + (ch - CH_CX); }
 
@@ -52,6 +52,17 @@ struct DevState {
     unsigned int step;               // electron step index (Philox counter word), advanced by finalize
     unsigned int n_mid, n_big;       // id lists queued for the two rank-table kernels this step
     unsigned int collide_next;       // next active cell for k_collide's warps
+    unsigned int n_sput;             // ion impacts recorded by the push for sputtering
+};
+
+// One ion impact on an electrode that sputters n atoms (recorded by the push,
+// emitted by k_sputter in the order of the ions' ids).
+struct SputRec {
+    uint32_t id;                     // the ion's id
+    uint32_t meta;                   // run << 1 | electrode (0 cathode, 1 anode)
+    uint32_t ir;                     // radial cell of the impact (local)
+    float pr;                        // radial offset of the impact in the cell
+    uint32_t n;                      // atoms sputtered
 };
 
 // Device-resident scalars of one run (an ensemble holds several runs).
@@ -111,6 +122,12 @@ struct KParams {
     int charge_max;                  // highest ion charge (2, 3 or 4): step-wise classes on
     int nsp;                         // species with bins: 5, or 7 with charge_max >= 3
     int coulomb;                     // Coulomb pair collisions after the DSMC classes
+    int sputter;                     // ions absorbed at the electrodes sputter atoms
+    float sput_vth;                  // sqrt(k T_sputter / M)
+    const float* xsE;                // the table grid (eV)
+    const float* ytab;               // sputtering yield on the grid
+    SputRec* squeue;                 // this step's impacts, at most squeue_cap
+    uint32_t squeue_cap;
     int field_on;                    // gather E in the push
     int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
     unsigned long long capacity;
@@ -173,6 +190,9 @@ constexpr uint32_t SID_COUL_PERM = 0xE1000000u;
 constexpr uint32_t SID_INJ_COUNT = 0xD0000000u;
 __host__ __device__ constexpr uint32_t sid_inj_e(uint32_t p) { return 0xD1000000u | p; }
 __host__ __device__ constexpr uint32_t sid_inj_cu(uint32_t p) { return 0xD2000000u | p; }
+// sputtering: an impact's count, and its j-th atom (subject: the ion's id)
+constexpr uint32_t SID_SPUT = 0xD3000000u;
+__host__ __device__ constexpr uint32_t sid_sput_atom(uint32_t j) { return 0xD4000000u | j; }
 
 // Key layout: bits 0-23 cell, 24-26 species, 27-29 species before a
 // conversion in this step's collisions, 31 "converted" flag (the sort needs
@@ -209,5 +229,22 @@ __device__ __forceinline__ int run_of(const KParams& P, uint32_t gcell) {
 }
 
 __device__ __forceinline__ void set_error(DevState* st, uint32_t bits) { atomicOr(&st->error, bits); }
+
+// sigma(eps): linear interpolation on the grid E_k = 2^e (1 + j/64); the
+// bracketing index comes from the exponent and top six mantissa bits of eps.
+__device__ __forceinline__ float xs_lookup(const float* __restrict__ E, const float* __restrict__ s, float eps) {
+    if (!(eps < E[XS_N - 1])) return 0.0f;
+    int k;
+    if (eps < E[0]) {
+        k = 0;
+        eps = E[0];
+    } else {
+        const uint32_t b = __float_as_uint(eps);
+        k = ((int)(b >> 23) - 127 - XS_EMIN_EXP) * XS_SUB + (int)((b >> 17) & 63u);
+    }
+    const float t = (eps - E[k]) / (E[k + 1] - E[k]);
+    return s[k] + t * (s[k + 1] - s[k]);
+}
+
 
 }  // namespace pd

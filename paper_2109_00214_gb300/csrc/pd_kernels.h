@@ -78,6 +78,10 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
                     cudaStream_t s);
+// ion-impact sputtering after the push (one block per run); in_cnt: the
+// movers-into-bin counts of the sort
+void launch_sputter(const Particles& A, DevState* st, const KParams& P, const float* ray, uint32_t* in_cnt,
+                    cudaStream_t s);
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 

@@ -208,14 +208,14 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             inmv[q] = inq;
             absd[q] = absorbed;
             zo[q] = mk ? npz : pz;
-            ro[q] = mk ? npr : pr;
+            ro[q] = (mk || absorbed) ? npr : pr;           // an absorbed particle keeps its impact r
             vzo[q] = move ? vz : lane_of(VZ, q);
             vro[q] = move ? vr : lane_of(VR, q);
             vto[q] = move ? vt : lane_of(VT, q);
             sp_[q] = sp;
             run_[q] = r;
             iz_[q] = mk ? niz : iz;
-            ir_[q] = mk ? nir : ir;
+            ir_[q] = (mk || absorbed) ? nir : ir;
             dep[q] = mk && charge_of(sp) != 0;
             flags |= (absorbed ? 1u : 0u) | (mvq ? 2u : 0u) | (inq ? 4u : 0u) | (dep[q] ? 8u : 0u) |
                      ((live && k != lane_of(K, q)) || mk ? 16u : 0u);
@@ -236,6 +236,24 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 const double qw = (double)charge_of(sp) * 1.602176634e-19 * w;
                 if (electrode == 1) atomicAdd(&rs.anode_charge_step, qw);
                 if (electrode == 0) atomicAdd(&rs.charge_cathode, qw);
+                // an ion arriving at an electrode inside the outer radius sputters
+                // floor(Y(E) + R) atoms (emitted by k_sputter)
+                const RunInfo& RI = MULTI ? s_runs[run_[q]] : P.run0;
+                if (P.sputter && electrode < 2 && charge_of(sp) > 0 && ir_[q] < RI.nr) {
+                    const float E = (float)((0.5 * pick_sp(P.masses, sp) * v2) / 1.602176634e-19);
+                    const float Y = xs_lookup(P.xsE, P.ytab, E);
+                    const uint32_t id = A.id[4u * g + (uint32_t)q];
+                    Stream rs_(id, st->step, SID_SPUT, RI.seed, RI.run);
+                    const uint32_t nsp = (uint32_t)floorf(Y + rs_.u01());
+                    if (nsp) {
+                        const uint32_t x = atomicAdd(&st->n_sput, 1u);
+                        if (x < P.squeue_cap)
+                            P.squeue[x] = SputRec{id, ((uint32_t)run_[q] << 1) | (uint32_t)electrode, (uint32_t)ir_[q],
+                                                  ro[q], nsp};
+                        else
+                            set_error(st, ERR_CAPACITY);
+                    }
+                }
             }
         }
         if (wflags & 2u) {          // movers out of their sorted bin

@@ -171,3 +171,40 @@ def test_graph_mode_reports_the_worst_residual(pd, xs):
     ens.step(10)
     for k in range(ens.R):
         assert ens.run_scalars(k)["poisson_relres_max"] <= tol
+
+
+def test_ensemble_sputtering_per_run_matches_oracle(pd, xs):
+    """Each run's block of the sputtering kernel takes that run's impacts:
+    counts, ids and atoms equal those of the run simulated alone."""
+    from test_gpu_parity import _electrode_beams
+    E, Y = synthetic.standin_sputter_yield()
+    runs = []
+    for c, parts in _runs(field_on=2):
+        c.update(sputter=1, heavy_subcycle=1)
+        n = c["nz"]
+        runs.append((c, synthetic.concat_loads([parts, _electrode_beams(n, c["nr"], 800, seed=n)])))
+    fields = [_field(c, 3 + k) for k, (c, _) in enumerate(runs)]
+    ens = _ensemble(pd, runs, xs, fields)
+    pd.pd_set_sputter_yield(ens.h, E, Y)
+    steps = 3
+    ens.step(steps)
+    per_run = _split(ens, ens.particles())
+    for k, (cfg, parts) in enumerate(runs):
+        o = oracle.Oracle(cfg, fp64=False)
+        o.set_cross_sections(xs)
+        o.set_sputter_yield(E, Y)
+        o.load(parts)
+        o.set_field(*fields[k])
+        o.prime()
+        o.step(steps)
+        op = o.particles()
+        g = per_run[k]
+        assert len(g["id"]) == len(op["id"]), k
+        for key in ("id", "species", "iz", "ir"):
+            assert np.array_equal(g[key], op[key]), (k, key)
+        for key in FLOATS:
+            assert np.array_equal(g[key].astype(np.float64), op[key]), (k, key)
+        gc, oc = ens.run_counters(k), o.counters()
+        for key in oc:
+            assert gc[key] == oc[key], (k, key, gc[key], oc[key])
+        assert gc["sput_cathode"] > 0

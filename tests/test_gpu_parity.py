@@ -291,6 +291,54 @@ def test_rz_external_field_with_injection_bit_exact(pd, xs):
     assert gs["charge"] == pytest.approx(os_["charge"], rel=1e-12)
 
 
+def _electrode_beams(n, nr, count, seed=21):
+    """Ions of random charge state and impact energy (20 eV .. 3 keV) one step
+    from the cathode or the anode, moving onto it, with some electrons and
+    neutrals doing the same."""
+    rng = np.random.default_rng(seed)
+    QE, MCU, ME = 1.602176634e-19, 63.546 * 1.66053906660e-27, 9.1093837015e-31
+    sp = rng.choice(np.array([0, 1, 2, 3, 4], np.uint8), count, p=[0.1, 0.1, 0.5, 0.2, 0.1])
+    E = 10 ** rng.uniform(np.log10(20.0), np.log10(3000.0), count)
+    v = np.sqrt(2 * E * QE / np.where(sp == 0, ME, MCU))
+    cat = rng.uniform(size=count) < 0.6
+    return dict(species=sp, iz=np.where(cat, 0, n - 1).astype(np.int32),
+                ir=rng.integers(0, nr, count).astype(np.int32),
+                pz=np.where(cat, 1e-6, 1 - 1e-6).astype(np.float32), pr=rng.uniform(0, 1, count).astype(np.float32),
+                vz=np.where(cat, -v, v).astype(np.float32),
+                vr=(0.1 * v * rng.standard_normal(count)).astype(np.float32),
+                vt=(0.1 * v * rng.standard_normal(count)).astype(np.float32))
+
+
+@pytest.mark.parametrize("heavy_subcycle", [1, 10])
+def test_rz_sputtering_bit_exact(pd, xs, heavy_subcycle):
+    """Ions arriving at either electrode sputter Cu atoms (stand-in yield):
+    the same counts, ids, positions and velocities as the oracle."""
+    n = 64
+    cfg, parts = synthetic.rz_plume(n=n, total=3e4, seed=4)
+    cfg.update(field_on=2, inject_on=1, beta=60.0, coll_dt_scale=50.0, sputter=1, heavy_subcycle=heavy_subcycle)
+    parts = synthetic.concat_loads([parts, _electrode_beams(n, n, 3000)])
+    E, Y = synthetic.standin_sputter_yield()
+    sim = pd.Simulation(cfg, xs)
+    o = oracle.Oracle(cfg, fp64=False)
+    o.set_cross_sections(xs)
+    sim.set_sputter_yield(E, Y)
+    o.set_sputter_yield(E, Y)
+    sim.load(parts)
+    o.load(parts)
+    field = _rz_field(n, cfg["V0"])
+    sim.set_field(*field)
+    o.set_field(*field)
+    o.prime()
+    sim.step(3)
+    o.step(3)
+    gc, oc = sim.counters(), o.counters()
+    assert gc["sput_cathode"] > 0 and gc["sput_anode"] > 0
+    assert_same_counters(gc, oc)
+    assert_same_particles(sim.particles(), o.particles())
+    gs, os_ = sim.scalars(), o.scalars()
+    assert gs["mass"] == pytest.approx(os_["mass"], rel=1e-12)
+
+
 @pytest.mark.parametrize("n,nr", [
     (64, 64),      # coarsest level 8 x 8 cells: solved by its stored inverse
     (96, 96),      # 6 x 6
