@@ -531,14 +531,17 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
 // Heavy cells (a list the warp must sort or many candidates) go to the
 // front of `active`, the others to its back, so that k_collide starts them
 // first.
+// EXT: any of the step-wise, heavy-pair or Coulomb extensions is on (the
+// plain variant counts the classes (e, Cu) and (e, Cu+) only)
+template <bool EXT>
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
                                                uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active, uint32_t* mid,
                                                uint32_t* big, DevState* st, KParams P) {
     const uint32_t C = P.ncell;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
-    const bool heavy_pairs = P.heavy_coll && P.heavy_step;
-    const bool q3 = P.charge_max >= 3, q4 = P.charge_max >= 4;
+    const bool heavy_pairs = EXT && P.heavy_coll && P.heavy_step;
+    const bool q3 = EXT && P.charge_max >= 3, q4 = EXT && P.charge_max >= 4;
     for (uint32_t c0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); c0 < C; c0 += stride) {
         const uint32_t c = c0 + lane;
         // n[k]: candidates of class k (electron classes 0-4, heavy pairs 5, 6)
@@ -613,7 +616,7 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         look[SP_CU3] = n[4];
         look[SP_CU4] = 0;
         uint32_t ncoul = 0;          // Coulomb pairs of the cell
-        if (P.coulomb && N[SP_E] > 0) {
+        if (EXT && P.coulomb && N[SP_E] > 0) {
             look[SP_E] += N[SP_E];
             ncoul = N[SP_E] / 2u;
 #pragma unroll
@@ -1068,6 +1071,7 @@ __device__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, ui
     }
 }
 
+template <bool EXT>
 __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                  const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
                                                  const uint32_t* __restrict__ cand_off,
@@ -1103,7 +1107,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         }
         const uint4 n = nc[c];         // candidates of the classes (e,Cu), (e,Cu+), (Cu,Cu+), (Cu,Cu)
         // and of (e,Cu2+ SW), (e,Cu2+ DI), (e,Cu3+)
-        const uint4 n2 = P.charge_max >= 3 ? nc2[c] : make_uint4(0u, 0u, 0u, 0u);
+        const uint4 n2 = EXT && P.charge_max >= 3 ? nc2[c] : make_uint4(0u, 0u, 0u, 0u);
         const int r = run_of(P, c);
         const RunInfo* RI = &P.runs[r];
         const uint32_t lc = c - RI->cell_base;
@@ -1135,7 +1139,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         // lookups of each list over all classes (the rank-table decisions of
         // k_ncand use the same totals): the Coulomb pairs look up every
         // electron and every ion of a cell with electrons
-        const bool coul = P.coulomb && Ne > 0;
+        const bool coul = EXT && P.coulomb && Ne > 0;
         const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (coul ? Ne : 0u);
         const uint32_t look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
         // the first list of a pair: electrons for the electron classes, Cu for
@@ -1144,7 +1148,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         uint32_t a_base = e_base, Na = Ne;
         bool cu_first = false;
         if (look_e) load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
-        for (int k = 0; k < NCLS; ++k) {
+        for (int k = 0; k < (EXT ? NCLS : 2); ++k) {
             const uint32_t ncand = k == 0 ? n.x : k == 1 ? n.y : k == 2 ? n2.x : k == 3 ? n2.y : k == 4 ? n2.z
                                  : k == 5 ? n.z : n.w;
             if (ncand == 0) continue;
@@ -1603,7 +1607,10 @@ cudaError_t collide_setup() {
 }
 void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
                   uint32_t* mid, uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
-    k_ncand<<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
+    if (P.charge_max >= 3 || P.heavy_coll || P.coulomb)
+        k_ncand<true><<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
+    else
+        k_ncand<false><<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
 }
 void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
@@ -1616,8 +1623,12 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
         A.id, S, off, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
     k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
         A.id, S, off, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
-    k_collide<<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P, cc,
-                                   nbins);
+    if (P.charge_max >= 3 || P.heavy_coll || P.coulomb)
+        k_collide<true><<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
+                                             cc, nbins);
+    else
+        k_collide<false><<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
+                                              cc, nbins);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {
