@@ -126,7 +126,7 @@ typedef struct {
     real sgmax[7];
     /* counters */
     uint64_t events[NCH], nulls, consumed, thr_rej, ratio_viol, iso_fallback, cand_total;
-    uint64_t coul_ee, coul_ei;   /* Coulomb pair collisions applied */
+    uint64_t coul_ee, coul_ei, coul_ii;   /* Coulomb pair collisions applied: e-e, e-ion, ion-ion */
     uint64_t sput[2];            /* atoms sputtered from the cathode, the anode */
     real ytab[XS_N];             /* sputtering yield Y(E) on the cross-section grid */
     struct sput_rec* srec;       /* this step's ion impacts on the electrodes */
@@ -199,9 +199,10 @@ static uint32_t pick(stream_t* s, uint32_t n) { return (uint32_t)(((uint64_t)nex
 /* stream ids (third counter word) */
 #define SID_CAND(k, m) (((uint32_t)(k) << 28) | (uint32_t)(m))
 #define SID_NCAND 0xE0000000u
-/* Coulomb classes 0 (e-e) and 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+):
- * pair k of class c, and the permutation keys of class c */
-#define SID_COUL(c, k) ((((uint32_t)(c) + 8u) << 28) | (uint32_t)(k))
+/* Coulomb classes 0 (e-e), 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+)
+ * and 6-20 (ion pairs): pair k < 2^24 of class c, and the permutation keys
+ * of class c (a range no other stream id uses) */
+#define SID_COUL(c, k) (((0x70u + (uint32_t)(c)) << 24) | (uint32_t)(k))
 #define SID_COUL_PERM(c) (0xE1000000u | (uint32_t)(c))
 #define SID_INJ_COUNT 0xD0000000u
 #define SID_INJ_E(p) (0xD1000000u | (uint32_t)(p))
@@ -953,74 +954,110 @@ static int cmp_id(const void* a, const void* b) {
     return x < y ? -1 : (x > y ? 1 : 0);
 }
 
-/* Pairing of one cell (Takizuka-Abe): class 0 pairs the electrons two by
- * two in a random order (an odd count ends with a triple whose three pairs
- * collide with half the time step); class 1 + i (ion species i = Cu+, Cu2+
- * SW, Cu2+ DI, Cu3+, Cu4+) pairs each particle of the more numerous of the
- * electrons and the ions once, k-th of that species in a random order with
- * the (k mod N_fewer)-th of the other in a random order, so that a particle
- * of the fewer species collides several times in sequence; n_L is the
- * density of the fewer (the lower density). */
+/* one species paired with itself: two by two in a random order, an odd
+ * count ending with a triple of three pairs at half the time step; a
+ * particle whose species changed this step is left out */
+static uint64_t pairs_same(or_sim* S, int64_t c, const idrec* l, uint32_t N, int sp, int cls, real Kn, real f) {
+    uint64_t done = 0;
+    if (N < 2) return 0;
+    stream_t ps;
+    stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(cls));
+    uint32_t key[4];
+    for (int q = 0; q < 4; ++q) key[q] = next_u32(&ps);
+    uint32_t P = N / 2 - (N % 2);                              /* regular pairs */
+    for (uint32_t k = 0; k < P; ++k) {
+        int64_t ia = l[perm_index(2 * k, N, key)].idx, ib = l[perm_index(2 * k + 1, N, key)].idx;
+        if (S->sp[ia] != sp || S->sp[ib] != sp) continue;
+        stream_t st;
+        stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(cls, k));
+        done += (uint64_t)coulomb_pair(S, &st, ia, ib, Kn, f, f);
+    }
+    if (N % 2) {                                               /* the last three: a triple */
+        int64_t t[3];
+        for (int q = 0; q < 3; ++q) t[q] = l[perm_index(N - 3 + q, N, key)].idx;
+        for (int q = 0; q < 3; ++q) {
+            int64_t ia = t[q], ib = t[(q + 1) % 3];
+            if (S->sp[ia] != sp || S->sp[ib] != sp) continue;
+            stream_t st;
+            stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(cls, P + (uint32_t)q));
+            done += (uint64_t)coulomb_pair(S, &st, ia, ib, Kn * R_(0.5), f, f);
+        }
+    }
+    return done;
+}
+
+/* two species A and B: each particle of the more numerous (A on a tie) once,
+ * the k-th of it in a random order with the (k mod N_fewer)-th of the other
+ * in a random order, so that a particle of the fewer collides several times
+ * in sequence; the first particle of every pair is A's */
+static uint64_t pairs_cross(or_sim* S, int64_t c, const idrec* la, uint32_t NA, int spa, const idrec* lb,
+                            uint32_t NB, int spb, int cls, real Kn, real fa, real fb) {
+    uint64_t done = 0;
+    if (NA == 0 || NB == 0) return 0;
+    int a_many = NA >= NB;
+    uint32_t Nm = a_many ? NA : NB, Nf = a_many ? NB : NA;
+    stream_t ps;
+    stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(cls));
+    uint32_t km[4], kf[4];
+    for (int q = 0; q < 4; ++q) km[q] = next_u32(&ps);
+    for (int q = 0; q < 4; ++q) kf[q] = next_u32(&ps);
+    for (uint32_t k = 0; k < Nm; ++k) {
+        uint32_t m = perm_index(k, Nm, km), f = perm_index(k % Nf, Nf, kf);
+        int64_t ia = a_many ? la[m].idx : la[f].idx;
+        int64_t ib = a_many ? lb[f].idx : lb[m].idx;
+        if (S->sp[ia] != spa || S->sp[ib] != spb) continue;   /* ionized this step */
+        stream_t st;
+        stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(cls, k));
+        done += (uint64_t)coulomb_pair(S, &st, ia, ib, Kn, fa, fb);
+    }
+    return done;
+}
+
+/* Pairing of one cell (Takizuka-Abe), on the lists of the step's start:
+ * class 0 pairs the electrons with themselves, class 1 + i the electrons
+ * with ion species i (Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+), both with the
+ * electron collision step; on heavy steps, classes 6.. pair the ion species
+ * with themselves and with each other (species a <= b in order), with the
+ * heavy step.  n_L is the density of the fewer of the two (of the species
+ * itself in a class of one species). */
 static double coulomb_k(int za, int zb, double mab, double lnl) {
     double qq = (double)za * (double)zb * QE * QE;
     return qq * qq * lnl / (8.0 * PI * EPS0 * EPS0 * mab * mab);
 }
 
-static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* cnt, int64_t C, double dtc) {
+static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* cnt, int64_t C, double dtc,
+                         int heavy_step) {
     int j = (int)(c % S->c.nr);
     double wv = S->c.weight * dtc / cell_volume(S, j);          /* W dt / V: n dt per particle */
     double lnl = S->c.coulomb_lnl;
     const idrec* el = rec + cnt[SP_E * C + c];
     uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
-    if (Ne >= 2) {
-        stream_t ps;
-        stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(0));
-        uint32_t key[4];
-        for (int q = 0; q < 4; ++q) key[q] = next_u32(&ps);
-        real Kn = R_(coulomb_k(-1, -1, 0.5 * ME, lnl) * (double)Ne * wv);
-        real h = R_(0.5);
-        uint32_t P = Ne / 2 - (Ne % 2);                          /* regular pairs */
-        for (uint32_t k = 0; k < P; ++k) {
-            stream_t st;
-            stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(0, k));
-            int64_t ia = el[perm_index(2 * k, Ne, key)].idx, ib = el[perm_index(2 * k + 1, Ne, key)].idx;
-            S->coul_ee += (uint64_t)coulomb_pair(S, &st, ia, ib, Kn, h, h);
-        }
-        if (Ne % 2) {                                            /* the last three: a triple */
-            int64_t t[3];
-            for (int q = 0; q < 3; ++q) t[q] = el[perm_index(Ne - 3 + q, Ne, key)].idx;
-            for (int q = 0; q < 3; ++q) {
-                stream_t st;
-                stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(0, P + (uint32_t)q));
-                S->coul_ee += (uint64_t)coulomb_pair(S, &st, t[q], t[(q + 1) % 3], Kn * h, h, h);
-            }
-        }
-    }
+    S->coul_ee += pairs_same(S, c, el, Ne, SP_E, 0, R_(coulomb_k(-1, -1, 0.5 * ME, lnl) * (double)Ne * wv), R_(0.5));
     double mr = mr_class();
     real fe = R_(mr / ME), fi = R_(mr / M_CU);
-    for (int i = 0; i < 5 && Ne > 0; ++i) {
+    const idrec* il[5];
+    uint32_t Ni[5];
+    for (int i = 0; i < 5; ++i) {
         int sp = SP_CUP + i;
-        const idrec* il = rec + cnt[sp * C + c];
-        uint32_t Ni = (uint32_t)(cnt[sp * C + c + 1] - cnt[sp * C + c]);
-        if (Ni == 0) continue;
-        int e_many = Ne >= Ni;
-        uint32_t Na = e_many ? Ne : Ni, Nb = e_many ? Ni : Ne;
-        stream_t ps;
-        stream_init(&ps, S, (uint32_t)c, S->step, SID_COUL_PERM(1 + i));
-        uint32_t ka[4], kb[4];
-        for (int q = 0; q < 4; ++q) ka[q] = next_u32(&ps);
-        for (int q = 0; q < 4; ++q) kb[q] = next_u32(&ps);
-        real Kn = R_(coulomb_k(-1, ZQ[sp], mr, lnl) * (double)Nb * wv);
-        for (uint32_t k = 0; k < Na; ++k) {
-            uint32_t a = perm_index(k, Na, ka), b = perm_index(k % Nb, Nb, kb);
-            int64_t ie = e_many ? el[a].idx : el[b].idx;
-            int64_t ii = e_many ? il[b].idx : il[a].idx;
-            if (S->sp[ii] != sp) continue;                       /* ionized this step */
-            stream_t st;
-            stream_init(&st, S, (uint32_t)c, S->step, SID_COUL(1 + i, k));
-            S->coul_ei += (uint64_t)coulomb_pair(S, &st, ie, ii, Kn, fe, fi);
-        }
+        il[i] = rec + cnt[sp * C + c];
+        Ni[i] = (uint32_t)(cnt[sp * C + c + 1] - cnt[sp * C + c]);
     }
+    for (int i = 0; i < 5; ++i) {
+        uint32_t Nf = Ne < Ni[i] ? Ne : Ni[i];
+        real Kn = R_(coulomb_k(-1, ZQ[SP_CUP + i], mr, lnl) * (double)Nf * wv);
+        S->coul_ei += pairs_cross(S, c, el, Ne, SP_E, il[i], Ni[i], SP_CUP + i, 1 + i, Kn, fe, fi);
+    }
+    if (!heavy_step) return;
+    double wvh = S->c.weight * (dtc * S->c.heavy_subcycle) / cell_volume(S, j);
+    int cls = 6;
+    for (int a = 0; a < 5; ++a)
+        for (int b = a; b < 5; ++b, ++cls) {
+            int sa = SP_CUP + a, sb = SP_CUP + b;
+            uint32_t Nf = a == b ? Ni[a] : (Ni[a] < Ni[b] ? Ni[a] : Ni[b]);
+            real Kn = R_(coulomb_k(ZQ[sa], ZQ[sb], 0.5 * M_CU, lnl) * (double)Nf * wvh);
+            if (a == b) S->coul_ii += pairs_same(S, c, il[a], Ni[a], sa, cls, Kn, R_(0.5));
+            else S->coul_ii += pairs_cross(S, c, il[a], Ni[a], sa, il[b], Ni[b], sb, cls, Kn, R_(0.5), R_(0.5));
+        }
 }
 
 static int collide_all(or_sim* S, int heavy_step) {
@@ -1186,7 +1223,7 @@ static int collide_all(or_sim* S, int heavy_step) {
          * classes: e-e, then e with each ion species.  The lists are those of
          * the step's start (newborn electrons wait for the next step); an ion
          * ionized earlier this step is left out. */
-        if (S->c.coulomb && !err) coulomb_cell(S, c, rec, cnt, C, dtc);
+        if (S->c.coulomb && !err) coulomb_cell(S, c, rec, cnt, C, dtc, heavy_step);
     }
     S->id_next = id_base + (uint32_t)(2 * total);
     free(cnt); free(rec); free(cur); free(nc); free(pre);
@@ -1484,6 +1521,7 @@ void or_get_counters(const or_sim* S, uint64_t* out) {
     out[k++] = S->events[CH_S3]; out[k++] = S->events[CH_S4];
     out[k++] = S->coul_ee; out[k++] = S->coul_ei;
     out[k++] = S->sput[0]; out[k++] = S->sput[1];
+    out[k++] = S->coul_ii;
 }
 
 /* scalars: t, V, I_gap, gamma, Qbar, erosion (kg/C), mass ledger (kg),

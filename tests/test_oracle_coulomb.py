@@ -1,6 +1,6 @@
 """Pins of the oracle's Coulomb collisions (the binary collision model of
-Takizuka and Abe, 1977, applied to the e-e and e-ion pairs of each cell),
-CPU only.
+Takizuka and Abe, 1977, applied to the e-e and e-ion pairs of each cell and,
+on heavy steps, to its ion pairs), CPU only.
 
 * a pair collision keeps |u| and shares the change of u by the reduced mass:
   momentum and kinetic energy are conserved exactly (FP64), on both branches
@@ -16,7 +16,10 @@ CPU only.
 * a cold-ion beam: after one step the mean electron velocity has lost the
   fraction fe E[1 - cos theta] with var from the cell's ion density, W, V,
   dt and the Coulomb logarithm (the constant of the model);
-* whole steps with Coulomb collisions alone conserve momentum and energy.
+* whole steps with Coulomb collisions alone conserve momentum and energy;
+* ion pairs: exact counts on heavy steps and none between them, and a Cu2+
+  beam through cold Cu+ slows at the model's rate with charges 2 and 1,
+  m_ab = M/2 and the heavy step.
 """
 import math
 
@@ -223,3 +226,72 @@ def test_off_by_default(xs):
     o.step(2)
     c = o.counters()
     assert c["coul_ee"] == 0 and c["coul_ei"] == 0
+
+
+def test_ion_pairs_on_heavy_steps_only(xs):
+    """Ion-ion pairs run on heavy steps: per species N/2 (even) or
+    (N-3)/2 + 3 (odd) pairs, per pair of species max(N_a, N_b)."""
+    cfg, parts = synthetic.microbench(nz=8, nr=8, total=3e4, seed=4)
+    cfg.update(coulomb=1, charge_max=3, heavy_subcycle=10)
+    sp = parts["species"].copy()
+    sp[np.flatnonzero(sp == 2)[::3]] = 3
+    sp[np.flatnonzero(sp == 2)[1::3]] = 5
+    parts = dict(parts, species=sp)
+    o = oracle.Oracle(cfg, fp64=True)
+    o.set_cross_sections(_zero_xs(xs))
+    o.load(parts)
+    o.step(1)                                 # step 0 is a heavy step: lists as loaded (heavies moved)
+    c1 = o.counters()
+    o2 = oracle.Oracle(dict(cfg, coulomb=0), fp64=True)
+    o2.set_cross_sections(_zero_xs(xs))
+    o2.load(parts)
+    o2.step(1)
+    p = o2.particles()
+    cell = p["iz"].astype(np.int64) * cfg["nr"] + p["ir"]
+    C = cfg["nz"] * cfg["nr"]
+    N = {s: np.bincount(cell[p["species"] == s], minlength=C) for s in (2, 3, 4, 5, 6)}
+    want = 0
+    ions = (2, 3, 4, 5, 6)
+    for ia, a in enumerate(ions):
+        Na = N[a]
+        want += np.where(Na % 2 == 0, Na // 2, np.where(Na >= 3, (Na - 3) // 2 + 3, 0)).sum()
+        for b in ions[ia + 1:]:
+            want += np.where((Na > 0) & (N[b] > 0), np.maximum(Na, N[b]), 0).sum()
+    assert c1["coul_ii"] == want and want > 0
+    o.step(5)                                 # steps 1-5: no heavy step
+    assert o.counters()["coul_ii"] == c1["coul_ii"]
+
+
+def test_ion_beam_through_cold_ions_at_the_model_rate(xs):
+    """One heavy step of a Cu2+ beam through cold Cu+ (more beam ions than
+    targets): var = (2 e^2)^2 n_Cu+ lnL dt_h / (8 pi eps0^2 (M/2)^2) / v0^3, and
+    the beam's mean velocity loses the fraction E[1 - cos theta] / 2 (equal
+    masses); the beam's own pairs keep its momentum."""
+    ncell, nb_c, nt_c = 64, 600, 100
+    lnl, W, dt, hs = 10.0, 100.0, 1e-15, 10
+    V = 50e-9 * 50e-9 * 1e-6
+    ni = nt_c * W / V
+    Kn = (2 * QE * QE) ** 2 * ni * lnl * dt * hs / (8 * math.pi * EPS0 ** 2 * (MCU / 2) ** 2)
+    v0 = (Kn / 0.01) ** (1 / 3)                  # var = 0.01
+    cfg = synthetic.base_config(geometry="xy_periodic", nz=8, nr=8, dz=50e-9, dr=50e-9, depth=1e-6, dt=dt,
+                                heavy_subcycle=hs, weight=W, seed=5, field_on=0, inject_on=0, coll_dt_scale=1.0,
+                                capacity=ncell * (nb_c + nt_c) + 1024, coulomb=1, coulomb_lnl=lnl)
+    rng = np.random.default_rng(3)
+    cells = np.repeat(np.arange(ncell), nb_c + nt_c)
+    sp = np.tile(np.r_[np.full(nb_c, 3, np.uint8), np.full(nt_c, 2, np.uint8)], ncell)
+    n = len(sp)
+    parts = dict(species=sp, iz=(cells // 8).astype(np.int32), ir=(cells % 8).astype(np.int32),
+                 pz=rng.uniform(0.2, 0.8, n).astype(np.float32), pr=rng.uniform(0.2, 0.8, n).astype(np.float32),
+                 vz=np.where(sp == 3, v0, 0.0).astype(np.float32), vr=np.zeros(n, np.float32),
+                 vt=np.zeros(n, np.float32))
+    o = oracle.Oracle(cfg, fp64=True)
+    o.set_cross_sections(_zero_xs(xs))
+    o.load(parts)
+    o.step(1)
+    p = o.particles()
+    beam = p["species"] == 3
+    loss = 1.0 - p["vz"][beam].mean() / float(np.float32(v0))
+    var = Kn / float(np.float32(v0)) ** 3
+    want = 0.5 * omc_mean(var)
+    sd = 0.5 * 2 * var * math.sqrt(1.9) / math.sqrt(beam.sum())
+    assert abs(loss - want) < 4 * sd + 2e-3 * want, (loss, want, sd)
