@@ -96,8 +96,9 @@ typedef struct pd_config {
                                   classes (e, Cu2+) -> Cu3+), 4 (and (e, Cu3+) -> Cu4+);
                                   species above it are refused on load */
     int32_t coulomb;           /* 1: Coulomb collisions of the e-e and e-ion pairs of
-                                  each cell after its DSMC classes (binary collision
-                                  model of Takizuka and Abe); 0 (default): off */
+                                  each cell after its DSMC classes, and of its ion
+                                  pairs on heavy steps (binary collision model of
+                                  Takizuka and Abe); 0 (default): off */
     int64_t capacity;          /* particle slots */
     double coulomb_lnl;        /* Coulomb logarithm (default 10) */
     int32_t sputter;           /* 1: ions absorbed at an electrode sputter Cu atoms into
@@ -136,8 +137,8 @@ typedef struct pd_scalars {
  * neutrals emitted, absorbed [electrode 3][species 7], then events of charge
  * exchange, Cu-Cu elastic, Cu2+ -> Cu3+ and Cu3+ -> Cu4+, then Coulomb pair
  * collisions e-e and e-ion, then atoms sputtered from the cathode and from
- * the anode. */
-#define PD_NCOUNTERS 42
+ * the anode, then Coulomb ion-ion pair collisions. */
+#define PD_NCOUNTERS 43
 
 typedef struct pd_sim pd_sim;
 

@@ -30,14 +30,15 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
-PD_NCOUNTERS = 42
+PD_NCOUNTERS = 43
 PD_NKERNELS = 12
 GEOM = {"rz": 0, "xy_periodic": 1}
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
                  + [f"abs_{e}_{s}" for e in ("cathode", "anode", "wall")
                     for s in ("e", "Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")]
-                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei", "sput_cathode", "sput_anode"])
+                 + ["ev_cx", "ev_nn", "ev_s3", "ev_s4", "coul_ee", "coul_ei", "sput_cathode", "sput_anode",
+                    "coul_ii"])
 STATUS = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_CAPACITY", 3: "PD_ERR_CUDA", 4: "PD_ERR_TIMEOUT",
           5: "PD_ERR_NONFINITE", 6: "PD_ERR_STATE"}
 

@@ -123,7 +123,7 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.xsE = take(XS_N * 4);
     L.xs = take(NCH * XS_N * 4);
     L.ck = take(ckl * 4);
-    L.cw = take(rows * 8);                                 // W dt_coll / V_cell per row (Coulomb densities)
+    L.cw = take(2 * rows * 8);                             // W dt / V_cell per row, electron then heavy step
     L.ray = take(1024 * 4);
     L.ytab = take(XS_N * 4);                               // sputtering yield on the table grid
     L.squeue_cap = cf[0].sputter ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>(cap / 16, 4096), 1u << 20) : 16u;
@@ -295,6 +295,7 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.charge_max = s->cfgs[0].charge_max;
     P.nsp = s->L.nsp;
     P.coulomb = s->cfgs[0].coulomb;
+    P.cw_heavy = (uint32_t)s->L.rows;
     P.sputter = s->cfgs[0].sputter;
     P.sput_vth = (float)std::sqrt(KB * s->cfgs[0].sputter_T / M_CU);
     P.xsE = s->xsE;
@@ -346,12 +347,16 @@ void update_collision_consts(pd_sim* s) {
     // then e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+ (m_ab = m_r)
     {
         const double lnl = s->cfgs[0].coulomb_lnl;
-        for (int q = 0; q < 6; ++q) {
-            const int zb = q == 0 ? -1 : ZQ[SP_CUP + q - 1];
-            const double mab = q == 0 ? 0.5 * ME : mr;
-            const double qq = (double)(-1) * (double)zb * QE * QE;
-            cc.kc[q] = qq * qq * lnl / (8.0 * PI * EPS0_C * EPS0_C * mab * mab);
-        }
+        auto kc = [&](int za, int zb, double mab) {
+            const double qq = (double)za * (double)zb * QE * QE;
+            return qq * qq * lnl / (8.0 * PI * EPS0_C * EPS0_C * mab * mab);
+        };
+        cc.kc[0] = kc(-1, -1, 0.5 * ME);
+        for (int q = 1; q < 6; ++q) cc.kc[q] = kc(-1, ZQ[SP_CUP + q - 1], mr);
+        // ion pairs (species a <= b in order), equal masses: m_ab = M / 2
+        int cls = 6;
+        for (int a = 0; a < 5; ++a)
+            for (int b = a; b < 5; ++b) cc.kc[cls++] = kc(ZQ[SP_CUP + a], ZQ[SP_CUP + b], 0.5 * M_CU);
     }
     const int ch0[NCLS] = {CH_EL, CH_SW, CH_S3, CH_S3, CH_S4, CH_CX, CH_NN}, nch[NCLS] = {4, 1, 1, 1, 1, 1, 1};
     for (int k = 0; k < NCLS; ++k) {
@@ -395,12 +400,16 @@ pd_status upload_ck(pd_sim* s) {
                 (float)(0.5 * c.weight * (double)s->cc.sgmax[6] * dth / cell_volume(c, j));
         }
     }
-    // W dt_coll / V_cell(j) per row: a cell's density times dt_coll per particle
-    std::vector<double> cw(s->L.rows);
+    // W dt / V_cell(j) per row, with dt_coll and with the heavy step: a
+    // cell's density times the time step per particle (Coulomb pairs)
+    std::vector<double> cw(2 * s->L.rows);
     for (int r = 0; r < s->R; ++r) {
         const pd_config& c = s->cfgs[r];
         const double dtc = c.dt * c.coll_dt_scale;
-        for (int j = 0; j < c.nr; ++j) cw[s->runs[r].row_base + j] = c.weight * dtc / cell_volume(c, j);
+        for (int j = 0; j < c.nr; ++j) {
+            cw[s->runs[r].row_base + j] = c.weight * dtc / cell_volume(c, j);
+            cw[s->L.rows + s->runs[r].row_base + j] = c.weight * (dtc * c.heavy_subcycle) / cell_volume(c, j);
+        }
     }
     CK(cudaMemcpyAsync(s->ck, ck.data(), ck.size() * 4, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->cw, cw.data(), cw.size() * 8, cudaMemcpyHostToDevice, s->stream));

@@ -615,14 +615,19 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         look[SP_CU2_DI] = n[3];
         look[SP_CU3] = n[4];
         look[SP_CU4] = 0;
-        uint32_t ncoul = 0;          // Coulomb pairs of the cell
+        uint32_t ncoul = 0;          // Coulomb pairs of the cell (about)
         if (EXT && P.coulomb && N[SP_E] > 0) {
             look[SP_E] += N[SP_E];
             ncoul = N[SP_E] / 2u;
 #pragma unroll
+            for (int sp = SP_CUP; sp < NSP; ++sp) ncoul += N[sp] > 0 ? max(N[SP_E], N[sp]) : 0u;
+        }
+        // the ion lists: with electrons, or on heavy steps (ion pairs)
+        if (EXT && P.coulomb && (N[SP_E] > 0 || P.heavy_step)) {
+#pragma unroll
             for (int sp = SP_CUP; sp < NSP; ++sp) {
                 look[sp] += N[sp];
-                ncoul += N[sp] > 0 ? max(N[SP_E], N[sp]) : 0u;
+                ncoul += P.heavy_step ? N[sp] : 0u;
             }
         }
         const uint32_t ntot = n[0] + n[1] + n[2] + n[3] + n[4] + nh + ncoul;
@@ -666,7 +671,7 @@ struct CellCtx {
     uint32_t id0;                    // id of the first reserved slot
     uint32_t s;                      // spawned so far
     uint32_t ev[NCH], nulls, consumed, thr, viol, fb;
-    uint32_t coul_ee, coul_ei;       // Coulomb pair collisions applied
+    uint32_t coul_ee, coul_ei, coul_ii;   // Coulomb pair collisions applied
 };
 
 __device__ bool spawn_electron(Particles& A, CellCtx& cx, DevState* st, long long* rho_e, uint32_t gcell, float pz,
@@ -954,121 +959,178 @@ __device__ __forceinline__ uint32_t rank_position(const IdList& L, uint32_t rank
     return pos;
 }
 
-// The Coulomb pairs of one cell (after its DSMC classes), by its warp:
-// class 0 pairs the electrons two by two in a random order (an odd count
-// ends with a triple of three pairs at half the time step); class 1 + i pairs
-// each particle of the more numerous of the electrons and ion species i
-// (Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+) once, the k-th in a random order with
-// the (k mod N_fewer)-th of the other species in a random order, in rounds of
-// N_fewer disjoint pairs; n_L is the density of the fewer.  The lists are
-// those of the step's start; an ion ionized earlier this step is left out.
-// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts);
-// el_dsmc: the electron list as the DSMC classes left it, or null.
-__device__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
-                             const uint32_t* __restrict__ off, uint32_t C, uint32_t c, uint32_t lc, uint32_t look_e,
-                             const uint32_t (&look_ion)[5], int nsp, int id_top, int lane, DevState* st,
-                             const CollConsts& cc, const double* __restrict__ cw, const IdList* el_dsmc) {
-    const RunInfo* RI = cx.RI;
-    const uint32_t e_base = off[c], Ne = off[c + 1] - e_base;
-    const double wv = cw[RI->row_base + lc % (uint32_t)RI->nr];
-    IdList el;
-    if (el_dsmc) el = *el_dsmc;
-    else load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
-    if (Ne >= 2) {
-        Stream ps(lc, st->step, SID_COUL_PERM | 0u, RI->seed, RI->run);
-        const uint4 key = stream_key(ps);
-        const float Kn = (float)(cc.kc[0] * (double)Ne * wv);
-        const uint32_t P = Ne / 2u - (Ne % 2u);      // regular pairs
-        for (uint32_t m0 = 0; m0 < P; m0 += 32) {
-            const uint32_t nb = min(32u, P - m0);
-            const uint32_t k = m0 + (uint32_t)lane;
-            const bool has = (uint32_t)lane < nb;
-            const uint32_t ra = has ? perm_index(2u * k, Ne, key) : 0u;
-            const uint32_t rb = has ? perm_index(2u * k + 1u, Ne, key) : 0u;
-            const uint32_t pa = rank_position(el, ra, has, nb, lane);
-            const uint32_t pb = rank_position(el, rb, has, nb, lane);
-            if (has && pa < Ne && pb < Ne) {
-                const uint32_t ia = e_base + pa, ib = e_base + pb;
+// One list paired with itself, by the cell's warp: two by two in a random
+// order (lanes take disjoint pairs), an odd count ending with a triple of
+// three pairs at half the time step (lane 0, in order); a particle whose
+// species changed this step is left out.  Returns the lane's applied pairs.
+__device__ uint32_t pairs_same(Particles& A, const IdList& L, uint32_t base, uint32_t N, int sp, int cls, float Kn,
+                               float f, uint32_t lc, const RunInfo* RI, DevState* st, int lane, uint32_t& fb) {
+    uint32_t done = 0;
+    if (N < 2u) return 0;
+    Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)cls, RI->seed, RI->run);
+    const uint4 key = stream_key(ps);
+    const uint32_t P = N / 2u - (N % 2u);            // regular pairs
+    for (uint32_t m0 = 0; m0 < P; m0 += 32) {
+        const uint32_t nb = min(32u, P - m0);
+        const uint32_t k = m0 + (uint32_t)lane;
+        const bool has = (uint32_t)lane < nb;
+        const uint32_t ra = has ? perm_index(2u * k, N, key) : 0u;
+        const uint32_t rb = has ? perm_index(2u * k + 1u, N, key) : 0u;
+        const uint32_t pa = rank_position(L, ra, has, nb, lane);
+        const uint32_t pb = rank_position(L, rb, has, nb, lane);
+        if (has && pa < N && pb < N) {
+            const uint32_t ia = base + pa, ib = base + pb;
+            const uint32_t ka = A.key[ia], kb = A.key[ib];
+            if (!(ka & KEY_FLAG) && (int)key_species(ka) == sp && !(kb & KEY_FLAG) && (int)key_species(kb) == sp) {
                 V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
-                Stream rs(lc, st->step, sid_coul(0, k), RI->seed, RI->run);
-                if (coulomb_kin(rs, va, vb, Kn, 0.5f, 0.5f, cx.fb)) {
+                Stream rs(lc, st->step, sid_coul(cls, k), RI->seed, RI->run);
+                if (coulomb_kin(rs, va, vb, Kn, f, f, fb)) {
                     A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
                     A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
-                    ++cx.coul_ee;
+                    ++done;
                 }
-            } else if (has) {
+            }
+        } else if (has) {
+            set_error(st, ERR_BOUNDS);
+        }
+    }
+    __syncwarp();
+    if (N % 2u) {                                    // the last three: a triple, in order
+        const bool has = lane < 3;
+        const uint32_t rk = has ? perm_index(N - 3u + (uint32_t)lane, N, key) : 0u;
+        const uint32_t pk = rank_position(L, rk, has, 3u, lane);
+        const uint32_t p0 = __shfl_sync(FULL, pk, 0), p1 = __shfl_sync(FULL, pk, 1), p2 = __shfl_sync(FULL, pk, 2);
+        if (lane == 0) {
+            if (p0 < N && p1 < N && p2 < N) {
+                const uint32_t t[3] = {base + p0, base + p1, base + p2};
+                const float Kh = Kn * 0.5f;
+                for (int q = 0; q < 3; ++q) {
+                    const uint32_t ia = t[q], ib = t[(q + 1) % 3];
+                    const uint32_t ka = A.key[ia], kb = A.key[ib];
+                    if ((ka & KEY_FLAG) || (int)key_species(ka) != sp || (kb & KEY_FLAG) || (int)key_species(kb) != sp)
+                        continue;
+                    V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
+                    Stream rs(lc, st->step, sid_coul(cls, P + (uint32_t)q), RI->seed, RI->run);
+                    if (coulomb_kin(rs, va, vb, Kh, f, f, fb)) {
+                        A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
+                        A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
+                        ++done;
+                    }
+                }
+            } else {
                 set_error(st, ERR_BOUNDS);
             }
         }
         __syncwarp();
-        if (Ne % 2u) {                               // the last three: a triple, in order
-            const bool has = lane < 3;
-            const uint32_t rk = has ? perm_index(Ne - 3u + (uint32_t)lane, Ne, key) : 0u;
-            const uint32_t pk = rank_position(el, rk, has, 3u, lane);
-            const uint32_t p0 = __shfl_sync(FULL, pk, 0), p1 = __shfl_sync(FULL, pk, 1), p2 = __shfl_sync(FULL, pk, 2);
-            if (lane == 0) {
-                if (p0 < Ne && p1 < Ne && p2 < Ne) {
-                    const uint32_t t[3] = {e_base + p0, e_base + p1, e_base + p2};
-                    const float Kh = Kn * 0.5f;
-                    for (int q = 0; q < 3; ++q) {
-                        const uint32_t ia = t[q], ib = t[(q + 1) % 3];
-                        V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
-                        Stream rs(lc, st->step, sid_coul(0, P + (uint32_t)q), RI->seed, RI->run);
-                        if (coulomb_kin(rs, va, vb, Kh, 0.5f, 0.5f, cx.fb)) {
-                            A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
-                            A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
-                            ++cx.coul_ee;
-                        }
+    }
+    return done;
+}
+
+// Two lists A and B: each particle of the more numerous (A on a tie) once,
+// the k-th of it in a random order with the (k mod N_fewer)-th of the other,
+// in rounds of N_fewer disjoint pairs (rounds in order); the first particle
+// of every pair is A's.  Returns the lane's applied pairs.
+__device__ uint32_t pairs_cross(Particles& A, const IdList& La, uint32_t baseA, uint32_t NA, int spa, const IdList& Lb,
+                                uint32_t baseB, uint32_t NB, int spb, int cls, float Kn, float fa, float fb_,
+                                uint32_t lc, const RunInfo* RI, DevState* st, int lane, uint32_t& fb) {
+    uint32_t done = 0;
+    if (NA == 0u || NB == 0u) return 0;
+    const bool a_many = NA >= NB;
+    const uint32_t Nm = a_many ? NA : NB, Nf = a_many ? NB : NA;
+    Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)cls, RI->seed, RI->run);
+    const uint4 km = stream_key(ps), kf = stream_key(ps);
+    for (uint32_t r0 = 0; r0 < Nm; r0 += Nf) {
+        const uint32_t re = min(r0 + Nf, Nm);
+        for (uint32_t m0 = r0; m0 < re; m0 += 32) {
+            const uint32_t nb = min(32u, re - m0);
+            const uint32_t k = m0 + (uint32_t)lane;
+            const bool has = (uint32_t)lane < nb;
+            const uint32_t m = has ? perm_index(k, Nm, km) : 0u;
+            const uint32_t f = has ? perm_index(k - r0, Nf, kf) : 0u;
+            const uint32_t pa = rank_position(La, a_many ? m : f, has, nb, lane);
+            const uint32_t pb = rank_position(Lb, a_many ? f : m, has, nb, lane);
+            if (has && pa < NA && pb < NB) {
+                const uint32_t ia = baseA + pa, ib = baseB + pb;
+                const uint32_t ka = A.key[ia], kb = A.key[ib];
+                if (!(ka & KEY_FLAG) && (int)key_species(ka) == spa && !(kb & KEY_FLAG) &&
+                    (int)key_species(kb) == spb) {
+                    V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
+                    Stream rs(lc, st->step, sid_coul(cls, k), RI->seed, RI->run);
+                    if (coulomb_kin(rs, va, vb, Kn, fa, fb_, fb)) {
+                        A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
+                        A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
+                        ++done;
                     }
-                } else {
-                    set_error(st, ERR_BOUNDS);
                 }
+            } else if (has) {
+                set_error(st, ERR_BOUNDS);
             }
             __syncwarp();
         }
     }
-    for (int i = 0; i < 5 && Ne > 0; ++i) {
-        const int sp = SP_CUP + i;
-        if (sp >= nsp) break;
-        const uint32_t i_base = off[(uint32_t)sp * C + c], Ni = off[(uint32_t)sp * C + c + 1] - i_base;
-        if (Ni == 0) continue;
-        IdList il;
-        load_ids(il, A.id, i_base, Ni, look_ion[i], S, sbuf, lane, id_top);
-        const bool e_many = Ne >= Ni;
-        const uint32_t Na = e_many ? Ne : Ni, Nb = e_many ? Ni : Ne;
-        Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)(1 + i), RI->seed, RI->run);
-        const uint4 ka = stream_key(ps), kb = stream_key(ps);
-        const float Kn = (float)(cc.kc[1 + i] * (double)Nb * wv);
-        // rounds of Nb pairs: within a round no particle appears twice
-        for (uint32_t r0 = 0; r0 < Na; r0 += Nb) {
-            const uint32_t re = min(r0 + Nb, Na);
-            for (uint32_t m0 = r0; m0 < re; m0 += 32) {
-                const uint32_t nb = min(32u, re - m0);
-                const uint32_t k = m0 + (uint32_t)lane;
-                const bool has = (uint32_t)lane < nb;
-                const uint32_t a = has ? perm_index(k, Na, ka) : 0u;
-                const uint32_t b = has ? perm_index(k - r0, Nb, kb) : 0u;
-                const uint32_t pe = rank_position(el, e_many ? a : b, has, nb, lane);
-                const uint32_t pi = rank_position(il, e_many ? b : a, has, nb, lane);
-                if (has && pe < Ne && pi < Ni) {
-                    const uint32_t ie = e_base + pe, ii = i_base + pi;
-                    const uint32_t ikey = A.key[ii];
-                    if (!(ikey & KEY_FLAG) && (int)key_species(ikey) == sp) {
-                        V3 ve{A.vz[ie], A.vr[ie], A.vt[ie]}, vi{A.vz[ii], A.vr[ii], A.vt[ii]};
-                        Stream rs(lc, st->step, sid_coul(1 + i, k), RI->seed, RI->run);
-                        if (coulomb_kin(rs, ve, vi, Kn, cc.a_e, cc.a_t, cx.fb)) {
-                            A.vz[ie] = ve.x; A.vr[ie] = ve.y; A.vt[ie] = ve.z;
-                            A.vz[ii] = vi.x; A.vr[ii] = vi.y; A.vt[ii] = vi.z;
-                            ++cx.coul_ei;
-                        }
-                    }
-                } else if (has) {
-                    set_error(st, ERR_BOUNDS);
-                }
-                __syncwarp();
-            }
+    return done;
+}
+
+// The Coulomb pairs of one cell (after its DSMC classes), by its warp, on
+// the lists of the step's start: class 0 pairs the electrons with
+// themselves, class 1 + i the electrons with ion species i (Cu+, Cu2+ SW,
+// Cu2+ DI, Cu3+, Cu4+), with the electron collision step; on heavy steps,
+// classes 6.. pair the ion species with themselves and each other (species
+// a <= b in order) with the heavy step.  n_L is the density of the fewer of
+// the two (of the species itself in a class of one species).
+// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts);
+// el_dsmc: the electron list as the DSMC classes left it, or null.
+__device__ __noinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
+                             const uint32_t* __restrict__ off, uint32_t C, uint32_t c, uint32_t lc, uint32_t look_e,
+                             const uint32_t (&look_ion)[5], int nsp, int heavy_step, int id_top, int lane,
+                             DevState* st, const CollConsts& cc, const double* __restrict__ cw, uint32_t cw_heavy,
+                             const IdList* el_dsmc) {
+    const RunInfo* RI = cx.RI;
+    const uint32_t e_base = off[c], Ne = off[c + 1] - e_base;
+    const uint32_t row = RI->row_base + lc % (uint32_t)RI->nr;
+    const double wv = cw[row];
+    uint32_t Ni[5], ib[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
+        const bool has = SP_CUP + i < nsp;
+        ib[i] = has ? off[b] : 0u;
+        Ni[i] = has ? off[b + 1] - ib[i] : 0u;
+    }
+    if (Ne > 0u) {
+        IdList el;
+        if (el_dsmc) el = *el_dsmc;
+        else load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
+        cx.coul_ee += pairs_same(A, el, e_base, Ne, SP_E, 0, (float)(cc.kc[0] * (double)Ne * wv), 0.5f, lc, RI, st,
+                                 lane, cx.fb);
+        for (int i = 0; i < 5; ++i) {
+            if (Ni[i] == 0u) continue;
+            IdList il;
+            load_ids(il, A.id, ib[i], Ni[i], look_ion[i], S, sbuf, lane, id_top);
+            const uint32_t Nf = min(Ne, Ni[i]);
+            cx.coul_ei += pairs_cross(A, el, e_base, Ne, SP_E, il, ib[i], Ni[i], SP_CUP + i, 1 + i,
+                                      (float)(cc.kc[1 + i] * (double)Nf * wv), cc.a_e, cc.a_t, lc, RI, st, lane, cx.fb);
         }
     }
+    if (!heavy_step) return;
+    const double wvh = cw[cw_heavy + row];
+    int cls = 6;
+    for (int a = 0; a < 5; ++a)
+        for (int b = a; b < 5; ++b, ++cls) {
+            if (Ni[a] == 0u || Ni[b] == 0u || (a == b && Ni[a] < 2u)) continue;
+            const uint32_t Nf = a == b ? Ni[a] : min(Ni[a], Ni[b]);
+            const float Kn = (float)(cc.kc[cls] * (double)Nf * wvh);
+            IdList la;
+            load_ids(la, A.id, ib[a], Ni[a], look_ion[a], S, sbuf, lane, id_top);
+            if (a == b) {
+                cx.coul_ii += pairs_same(A, la, ib[a], Ni[a], SP_CUP + a, cls, Kn, 0.5f, lc, RI, st, lane, cx.fb);
+            } else {
+                IdList lb;
+                load_ids(lb, A.id, ib[b], Ni[b], look_ion[b], S, sbuf, lane, id_top);
+                cx.coul_ii += pairs_cross(A, la, ib[a], Ni[a], SP_CUP + a, lb, ib[b], Ni[b], SP_CUP + b, cls, Kn, 0.5f,
+                                          0.5f, lc, RI, st, lane, cx.fb);
+            }
+        }
 }
 
 template <bool EXT>
@@ -1125,7 +1187,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         cx.s = 0;
         for (int q = 0; q < NCH; ++q) cx.ev[q] = 0;
         cx.nulls = cx.consumed = cx.thr = cx.viol = cx.fb = 0;
-        cx.coul_ee = cx.coul_ei = 0;
+        cx.coul_ee = cx.coul_ei = cx.coul_ii = 0;
         if (cx.slot0 + cx.nres > P.capacity) {
             // no room for this cell's spawns: report, and leave its reserved
             // slots (those that exist) dead
@@ -1139,8 +1201,10 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         // lookups of each list over all classes (the rank-table decisions of
         // k_ncand use the same totals): the Coulomb pairs look up every
         // electron and every ion of a cell with electrons
-        const bool coul = EXT && P.coulomb && Ne > 0;
-        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (coul ? Ne : 0u);
+        // (ion pairs collide on heavy steps even where there are no electrons)
+        const bool coul_e = EXT && P.coulomb && Ne > 0;
+        const bool coul = EXT && P.coulomb && (Ne > 0 || P.heavy_step);
+        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (coul_e ? Ne : 0u);
         const uint32_t look_cu = n.x + n.z + 2u * n.w, look_ci = n.y + n.z;
         // the first list of a pair: electrons for the electron classes, Cu for
         // the heavy classes (loaded over the electrons' list once those are done)
@@ -1293,7 +1357,8 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 look_all[i] = look_ion[i] + (SP_CUP + i < P.nsp ? off[b + 1] - off[b] : 0u);
             }
             // the electrons' list is still loaded unless a heavy class replaced it
-            coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, id_top, lane, st, cc, cw,
+            coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
+                         P.cw_heavy,
                          cu_first ? nullptr : &el);
         }
         const uint32_t s = __shfl_sync(FULL, cx.s, 0);
@@ -1312,9 +1377,11 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
         if (coul) {
             // every lane applied pairs: sum the warp's counts
             const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
+            const uint32_t ii = __reduce_add_sync(FULL, cx.coul_ii);
             if (lane == 0) {
                 if (ee) atomicAdd(&P.rs[r].ctr[C_COUL_EE], (unsigned long long)ee);
                 if (ei) atomicAdd(&P.rs[r].ctr[C_COUL_EI], (unsigned long long)ei);
+                if (ii) atomicAdd(&P.rs[r].ctr[C_COUL_II], (unsigned long long)ii);
             }
         }
     }

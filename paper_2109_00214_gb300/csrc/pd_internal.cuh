@@ -38,7 +38,7 @@ constexpr uint32_t ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u, ERR_NONFINITE = 4u, ERR_
 // counter slots (see PD_NCOUNTERS in pd.h)
 constexpr int C_EV = 0, C_NULL = 5, C_CONSUMED = 6, C_THR = 7, C_VIOL = 8, C_ISOFB = 9, C_CAND = 10,
               C_EMIT_E = 11, C_EMIT_CU = 12, C_ABS = 13, C_EV_CX = 34, C_EV_NN = 35, C_EV_S3 = 36, C_EV_S4 = 37,
-              C_COUL_EE = 38, C_COUL_EI = 39, C_SPUT_C = 40, C_SPUT_A = 41, NCOUNTERS = 42;
+              C_COUL_EE = 38, C_COUL_EI = 39, C_SPUT_C = 40, C_SPUT_A = 41, C_COUL_II = 42, NCOUNTERS = 43;
 // counter of the events of channel ch (channels 5-8 follow the absorption block)
 __host__ __device__ constexpr int c_event(int ch) { return ch < CH_CX ? C_EV + ch : C_EV_CX + (ch - CH_CX); }
 
@@ -101,7 +101,7 @@ struct CollConsts {
     float a_e, a_t;                  // m_r / m_e, m_r / M
     float kth[NCH];                  // 2 E_th e / m_r
     float sgmax[NCLS];               // NTC majorants of the pair classes, in class order
-    double kc[6];                    // Coulomb (q_a q_b)^2 lnL / (8 pi eps0^2 m_ab^2): e-e, e with Cu+ .. Cu4+
+    double kc[21];                   // Coulomb (q_a q_b)^2 lnL / (8 pi eps0^2 m_ab^2) of classes 0-20
     int di_split_mode;
 };
 
@@ -122,6 +122,7 @@ struct KParams {
     int charge_max;                  // highest ion charge (2, 3 or 4): step-wise classes on
     int nsp;                         // species with bins: 5, or 7 with charge_max >= 3
     int coulomb;                     // Coulomb pair collisions after the DSMC classes
+    uint32_t cw_heavy;               // heavy-step rows of cw follow the electron-step rows at this offset
     int sputter;                     // ions absorbed at the electrodes sputter atoms
     float sput_vth;                  // sqrt(k T_sputter / M)
     const float* xsE;                // the table grid (eV)
@@ -183,9 +184,10 @@ struct Stream {
 
 __host__ __device__ constexpr uint32_t sid_cand(int k, uint32_t m) { return ((uint32_t)k << 28) | m; }
 constexpr uint32_t SID_NCAND = 0xE0000000u;
-// Coulomb classes 0 (e-e) and 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+):
-// pair k of class c, and the permutation keys of class c (SID_COUL_PERM | c)
-__host__ __device__ constexpr uint32_t sid_coul(int c, uint32_t k) { return ((uint32_t)(c + 8) << 28) | k; }
+// Coulomb classes 0 (e-e), 1-5 (e with Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+) and
+// 6-20 (ion pairs): pair k < 2^24 of class c (a range no other stream id
+// uses), and the permutation keys of class c (SID_COUL_PERM | c)
+__host__ __device__ constexpr uint32_t sid_coul(int c, uint32_t k) { return ((0x70u + (uint32_t)c) << 24) | k; }
 constexpr uint32_t SID_COUL_PERM = 0xE1000000u;
 constexpr uint32_t SID_INJ_COUNT = 0xD0000000u;
 __host__ __device__ constexpr uint32_t sid_inj_e(uint32_t p) { return 0xD1000000u | p; }

@@ -225,13 +225,15 @@ def test_species_above_charge_max_refused_gpu(pd, xs):
         sim.synchronize()
 
 
-@pytest.mark.parametrize("charge_max,heavy_coll,scale,steps", [
-    (2, 0, 1.0, 3),
-    (4, 1, 3000.0, 3),             # every ion species, after the step-wise and heavy classes
+@pytest.mark.parametrize("charge_max,heavy_coll,scale,steps,hs", [
+    (2, 0, 1.0, 3, 1),
+    (4, 1, 3000.0, 3, 1),          # every ion species, after the step-wise and heavy classes
+    (4, 0, 1.0, 4, 2),             # ion pairs on every other step only
 ])
-def test_microbench_coulomb_bit_exact(pd, xs, charge_max, heavy_coll, scale, steps):
+def test_microbench_coulomb_bit_exact(pd, xs, charge_max, heavy_coll, scale, steps, hs):
     cfg, parts = synthetic.microbench(nz=32, nr=48, total=6e4, coll_scale=scale, seed=5)
-    cfg.update(coulomb=1, charge_max=charge_max, heavy_coll=heavy_coll, capacity=max(cfg["capacity"], 1 << 21))
+    cfg.update(coulomb=1, charge_max=charge_max, heavy_coll=heavy_coll, heavy_subcycle=hs,
+               capacity=max(cfg["capacity"], 1 << 21))
     if charge_max > 2:
         parts = _with_charge_states(parts, charge_max)
         sp = parts["species"].copy()
@@ -240,7 +242,19 @@ def test_microbench_coulomb_bit_exact(pd, xs, charge_max, heavy_coll, scale, ste
     sim, o = run_pair(pd, cfg, parts, xs, steps)
     gc, oc = sim.counters(), o.counters()
     assert_same_counters(gc, oc)
-    assert gc["coul_ee"] > 0 and gc["coul_ei"] > 0
+    assert gc["coul_ee"] > 0 and gc["coul_ei"] > 0 and gc["coul_ii"] > 0
+    assert_same_particles(sim.particles(), o.particles())
+
+
+@pytest.mark.parametrize("n_cup,ncells", [(3000, 1), (9, 4)])
+def test_ion_only_coulomb_cells_bit_exact(pd, xs, n_cup, ncells):
+    """Cells without electrons: only the ion pairs collide (heavy steps)."""
+    cfg, parts = synthetic.heavy_cells(n_e=0, n_cu=500, n_cup=n_cup, ncells=ncells, coll_scale=1.0, heavy_coll=0)
+    cfg.update(coulomb=1)
+    sim, o = run_pair(pd, cfg, parts, xs, 2)
+    gc, oc = sim.counters(), o.counters()
+    assert_same_counters(gc, oc)
+    assert gc["coul_ii"] > 0 and gc["coul_ee"] == 0
     assert_same_particles(sim.particles(), o.particles())
 
 
