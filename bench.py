@@ -215,12 +215,14 @@ BYTES_PER_PARTICLE = {
 TRAFFIC_PER_PARTICLE = {"push": 768.44e6 / 24898326, "scatter": 1365.81e6 / 24898326}
 
 
-def cpu_baseline(args, cfg_full, seed):
+def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
     """The oracle (float mirror, as it stands, one thread) on a bounded sample:
-    the first `cpu_rows` rows of cells of the same workload recipe."""
+    the first `rows` rows of cells of the same workload recipe, `warmup`
+    untimed steps, then `steps` timed ones."""
     import oracle
     import synthetic
-    rows = args.cpu_rows
+    rows = args.cpu_rows if rows is None else rows
+    steps = args.cpu_steps if steps is None else steps
     total = args.total * rows / args.nz
     cfg, parts = synthetic.microbench(nz=rows, nr=args.nr, total=total, seed=seed)
     cfg["heavy_coll"] = int(args.heavy_coll)
@@ -229,27 +231,32 @@ def cpu_baseline(args, cfg_full, seed):
     o.set_cross_sections(synthetic.standin_cross_sections())
     o.load(parts)
     o.prime()
+    if warmup:
+        o.step(warmup)
     n0 = o.count()
     t0 = time.perf_counter()
-    o.step(args.cpu_steps)
+    o.step(steps)
     dt = time.perf_counter() - t0
     n1 = o.count()
-    upd = args.cpu_steps * 0.5 * (n0 + n1)
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{rows}x{args.nr} cells of the same recipe ({n0} particles), {args.cpu_steps} steps, "
-                      f"{dt:.1f} s, single-threaded C oracle (float mirror)"}
+    upd = steps * 0.5 * (n0 + n1)
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "ms_per_step": 1e3 * dt / steps,
+            "sample": f"{rows}x{args.nr} cells of the same recipe ({n0} particles), {warmup} untimed and "
+                      f"{steps} timed steps, {dt:.1f} s, single-threaded C oracle (float mirror)"}
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    cb = cpu_baseline(args, None, seed=1)
+    # the K timed steps (after W untimed ones) run on a sample of rows sized
+    # for about ten 512-row steps of oracle time in all
+    rows = max(8, min(args.cpu_rows, (args.cpu_rows * args.cpu_steps // max(args.steps, 1)) // 8 * 8))
+    cb = cpu_baseline(args, None, seed=1, rows=rows, steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.cpu_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb)
                        + " (bounded CPU sample)",
-                       "nz": args.cpu_rows, "nr": args.nr},
+                       "nz": rows, "nr": args.nr},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
