@@ -630,7 +630,9 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
                 ncoul += P.heavy_step ? N[sp] : 0u;
             }
         }
-        const uint32_t ntot = n[0] + n[1] + n[2] + n[3] + n[4] + nh + ncoul;
+        // k_collide takes the cells with DSMC candidates; k_coulomb visits the
+        // others itself, but the rank tables it needs are queued here too
+        const uint32_t ntot = n[0] + n[1] + n[2] + n[3] + n[4] + nh;
         const bool act = c < C && ntot > 0;
         const uint32_t RL = 32u * RC;
         bool long_list = false;
@@ -647,9 +649,9 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
         if (ml) bl = __shfl_sync(FULL, bl, __ffs(ml) - 1);
         if (heavy) active[bh + __popc(mh & lt)] = c;
         else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
-        if (act) {
-            // the lists k_collide will rank that need a block's sort (long,
-            // with more lookups than select8 serves)
+        if (act || (c < C && ncoul > 0)) {
+            // the lists k_collide or k_coulomb will rank that need a block's
+            // sort (long, with more lookups than select8 serves)
             for (uint32_t sp = 0; sp < (uint32_t)NSP; ++sp) {
                 if (look[sp] == 0 || N[sp] <= RANK_WARP_MAX || look[sp] <= SELECT_LOOKUPS) continue;
                 const bool large = N[sp] > RANK_MID_MAX;
@@ -1078,13 +1080,11 @@ __device__ uint32_t pairs_cross(Particles& A, const IdList& La, uint32_t baseA, 
 // classes 6.. pair the ion species with themselves and each other (species
 // a <= b in order) with the heavy step.  n_L is the density of the fewer of
 // the two (of the species itself in a class of one species).
-// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts);
-// el_dsmc: the electron list as the DSMC classes left it, or null.
-__device__ __noinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
+// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts).
+__device__ __forceinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
                              const uint32_t* __restrict__ off, uint32_t C, uint32_t c, uint32_t lc, uint32_t look_e,
                              const uint32_t (&look_ion)[5], int nsp, int heavy_step, int id_top, int lane,
-                             DevState* st, const CollConsts& cc, const double* __restrict__ cw, uint32_t cw_heavy,
-                             const IdList* el_dsmc) {
+                             DevState* st, const CollConsts& cc, const double* __restrict__ cw, uint32_t cw_heavy) {
     const RunInfo* RI = cx.RI;
     const uint32_t e_base = off[c], Ne = off[c + 1] - e_base;
     const uint32_t row = RI->row_base + lc % (uint32_t)RI->nr;
@@ -1099,8 +1099,7 @@ __device__ __noinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankS
     }
     if (Ne > 0u) {
         IdList el;
-        if (el_dsmc) el = *el_dsmc;
-        else load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
+        load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
         cx.coul_ee += pairs_same(A, el, e_base, Ne, SP_E, 0, (float)(cc.kc[0] * (double)Ne * wv), 0.5f, lc, RI, st,
                                  lane, cx.fb);
         for (int i = 0; i < 5; ++i) {
@@ -1347,23 +1346,8 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                 __syncwarp();
             }
         }
-        if (coul) {
-            // ion lists' lookups: the DSMC classes' plus one per ion
-            const uint32_t look_ion[5] = {look_ci, n2.x, n2.y, n2.z, 0u};
-            uint32_t look_all[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
-                look_all[i] = look_ion[i] + (SP_CUP + i < P.nsp ? off[b + 1] - off[b] : 0u);
-            }
-            // the electrons' list is still loaded unless a heavy class replaced it
-            coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
-                         P.cw_heavy,
-                         cu_first ? nullptr : &el);
-        }
         const uint32_t s = __shfl_sync(FULL, cx.s, 0);
         for (uint32_t q = s + lane; q < cx.nres; q += 32) A.key[cx.slot0 + q] = DEAD;
-        cx.fb = __reduce_add_sync(FULL, cx.fb);      // the Coulomb pairs sample on every lane
         if (lane == 0) {
             RunState& rsv = P.rs[r];
             for (int q = 0; q < NCH; ++q)
@@ -1374,15 +1358,62 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             if (cx.viol) atomicAdd(&rsv.ctr[C_VIOL], (unsigned long long)cx.viol);
             if (cx.fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)cx.fb);
         }
-        if (coul) {
-            // every lane applied pairs: sum the warp's counts
-            const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
-            const uint32_t ii = __reduce_add_sync(FULL, cx.coul_ii);
-            if (lane == 0) {
-                if (ee) atomicAdd(&P.rs[r].ctr[C_COUL_EE], (unsigned long long)ee);
-                if (ei) atomicAdd(&P.rs[r].ctr[C_COUL_EI], (unsigned long long)ei);
-                if (ii) atomicAdd(&P.rs[r].ctr[C_COUL_II], (unsigned long long)ii);
-            }
+    }
+}
+
+// The Coulomb pairs (after all cells' DSMC classes: cells are independent,
+// so this is the order of cell-by-cell processing): one warp per cell with
+// charged particles, grid-stride over the cells.  The lists' lookups are
+// counted as k_ncand counted them, so the rank-table choices agree.
+__global__ void __launch_bounds__(128, 3) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+                                                   const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
+                                                   DevState* st, KParams P, CollConsts cc,
+                                                   const double* __restrict__ cw) {
+    __shared__ uint32_t s_sort[4][4 * RANK_WARP_MAX + 256];   // per-warp rank-table sort
+    const int lane = threadIdx.x & 31;
+    uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
+    const uint32_t C = P.ncell;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = warp0; c < C; c += nwarps) {
+        const uint32_t Ne = off[c + 1] - off[c];
+        if (Ne == 0u && !P.heavy_step) continue;
+        uint32_t Ni[5], nion = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
+            Ni[i] = SP_CUP + i < P.nsp ? off[b + 1] - off[b] : 0u;
+            nion += Ni[i];
+        }
+        if (Ne < 2u && nion == 0u) continue;         // nothing to pair
+        const int r = run_of(P, c);
+        CellCtx cx;
+        cx.cell = c;
+        cx.RI = &P.runs[r];
+        cx.geom = P.geom;
+        cx.fb = 0;
+        cx.coul_ee = cx.coul_ei = cx.coul_ii = 0;
+        const uint32_t lc = c - cx.RI->cell_base;
+        const uint4 n = nc[c];
+        const uint4 n2 = P.charge_max >= 3 ? nc2[c] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (Ne > 0u ? Ne : 0u);
+        const uint32_t look_ion[5] = {n.y + n.z, n2.x, n2.y, n2.z, 0u};
+        uint32_t look_all[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) look_all[i] = look_ion[i] + Ni[i];
+        const uint32_t idn = P.rs[r].id_next;
+        const int id_top = idn > 1u ? 31 - __clz((int)(idn - 1u)) : 0;
+        coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
+                     P.cw_heavy);
+        // every lane applied pairs: sum the warp's counts
+        const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
+        const uint32_t ii = __reduce_add_sync(FULL, cx.coul_ii), fb = __reduce_add_sync(FULL, cx.fb);
+        if (lane == 0) {
+            RunState& rsv = P.rs[r];
+            if (ee) atomicAdd(&rsv.ctr[C_COUL_EE], (unsigned long long)ee);
+            if (ei) atomicAdd(&rsv.ctr[C_COUL_EI], (unsigned long long)ei);
+            if (ii) atomicAdd(&rsv.ctr[C_COUL_II], (unsigned long long)ii);
+            if (fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)fb);
         }
     }
 }
@@ -1696,6 +1727,8 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
     else
         k_collide<false><<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
                                               cc, nbins);
+    // one wave of resident blocks (three per SM), grid-stride over the cells
+    if (P.coulomb) k_coulomb<<<sms * 3, 128, 0, s>>>(A, S, off, nc, nc2, st, P, cc, cw);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {

@@ -353,6 +353,29 @@ def test_rz_sputtering_bit_exact(pd, xs, heavy_subcycle):
     assert gs["mass"] == pytest.approx(os_["mass"], rel=1e-12)
 
 
+def test_sputter_queue_overflow_is_reported(pd, xs):
+    """More ion impacts in a step than the impact queue holds (4096 with this
+    capacity): the step reports a capacity error instead of writing past it."""
+    n = 64
+    cfg, _ = synthetic.rz_plume(n=n, total=2e3, seed=4)
+    cfg.update(field_on=2, inject_on=0, sputter=1, heavy_subcycle=1, capacity=60000)
+    rng = np.random.default_rng(5)
+    m = 6000
+    QE, MCU = 1.602176634e-19, 63.546 * 1.66053906660e-27
+    v = np.sqrt(2 * 500.0 * QE / MCU)
+    beam = dict(species=np.full(m, 2, np.uint8), iz=np.zeros(m, np.int32), ir=rng.integers(0, n, m).astype(np.int32),
+                pz=np.full(m, 1e-6, np.float32), pr=rng.uniform(0, 1, m).astype(np.float32),
+                vz=np.full(m, -v, np.float32), vr=np.zeros(m, np.float32), vt=np.zeros(m, np.float32))
+    sim = pd.Simulation(cfg, xs)
+    E = synthetic.xs_grid()
+    sim.set_sputter_yield(E, np.full_like(E, 2.0))
+    sim.load(beam)
+    sim.set_field(*_rz_field(n, cfg["V0"]))
+    sim.step(1)
+    with pytest.raises(pd.PdError, match="CAPACITY"):
+        sim.synchronize()
+
+
 @pytest.mark.parametrize("n,nr", [
     (64, 64),      # coarsest level 8 x 8 cells: solved by its stored inverse
     (96, 96),      # 6 x 6
