@@ -75,6 +75,7 @@ def parse():
     p.add_argument("--cpu-steps", type=int, default=10)
     p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble", "warmstart"])
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--log-dir", default=".", help="where the clock samples of the timed region are written")
     p.add_argument("--heavy-coll", action="store_true",
                    help="microbench: add the heavy-particle pair classes (charge exchange, Cu-Cu elastic)")
     p.add_argument("--coulomb", action="store_true", help="microbench: add the Coulomb pair collisions")
@@ -362,7 +363,7 @@ def run_ensemble(args, ws, rank, local):
     # steps reaches the tolerance
     cycles = int(cyc) + 1
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if ws == 1 else str(local)
-    out_dir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    out_dir = args.log_dir
     for attempt in range(4):
         ens.set_graph_mode(1, cycles)
         ens.step(G)                              # capture + one replay, untimed
@@ -588,8 +589,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if ws == 1 else str(local)
     sampler = ClockSampler(gpu_index if gpu_index.isdigit() else local,
-                           os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                                        else "", f"clocks_rank{rank}.csv"))
+                           os.path.join(args.log_dir, f"clocks_rank{rank}.csv"))
     barrier(ws)
     torch.cuda.synchronize()
     e0.record(stream)
