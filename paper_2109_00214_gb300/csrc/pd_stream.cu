@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(SCATTER_THREADS, 4) k_scatter4(Particles A, Pa
                 // bin's part precomputed in dlt
                 const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
                 slot[q] = dlt[bin[q]] + i - before;
-                if (slot[q] - new_off[bin[q]] >= stay[bin[q]]) set_error(st, ERR_BOUNDS);   // outside its bin's range
+
             }
         }
         if (any_mover) {            // claim slots after the stayers, one atomic per run of one bin
