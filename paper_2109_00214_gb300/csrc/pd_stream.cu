@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             iz_[q] = mk ? niz : iz;
             ir_[q] = (mk || absorbed) ? nir : ir;
             dep[q] = mk && charge_of(sp) != 0;
+            // 16: the particle moved (new position); 32: its key changed (new
+            // bin, absorbed, or converted in the last collisions)
             flags |= (absorbed ? 1u : 0u) | (mvq ? 2u : 0u) | (inq ? 4u : 0u) | (dep[q] ? 8u : 0u) |
-                     ((live && k != lane_of(K, q)) || mk ? 16u : 0u);
+                     (mk ? 16u : 0u) | ((live && k != lane_of(K, q)) ? 32u : 0u);
         }
         const uint32_t wflags = __reduce_or_sync(FULL_MASK, flags);
         if (RZ && (wflags & 1u)) {  // absorbed at an electrode or the outer wall: ledgers
@@ -345,8 +347,9 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 }
             }
         }
+        // write back only what changed: most keys do not change in a step
+        if (gv && (flags & 32u)) key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
         if (gv && (flags & 16u)) {
-            key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
             pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
             pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
             if (FIELD || RZ) {
