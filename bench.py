@@ -213,7 +213,7 @@ BYTES_PER_PARTICLE = {
 # DRAM bytes per particle of the same kernels from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of a 2.49e7-particle launch, profiles/push_scatter_512x512_2.5e7_ncu.md),
 # scaled to a launch by its particle count; to be set to None when the kernels change
-TRAFFIC_PER_PARTICLE = {"push": 776.08e6 / 24898326, "scatter": 1362.93e6 / 24898326}
+TRAFFIC_PER_PARTICLE = {"push": 693.56e6 / 24898326, "scatter": 1362.67e6 / 24898326}
 
 
 def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
