@@ -99,3 +99,33 @@ def test_rho_phi_pairs(pd, xs):
         dm = sum(a.run_density_map(k, sp) * q for sp, q in ((0, -1), (1, 0), (2, 1), (3, 2), (4, 2)))
         r = a.run_slice(rho, k).reshape(dm.shape)
         assert np.allclose(r, 1.602176634e-19 * dm, rtol=1e-9, atol=1e-9 * np.abs(r).max())
+
+
+def test_resume_with_the_extensions(pd, xs, tmp_path):
+    """Charge states up to Cu4+, heavy pairs, Coulomb pairs and sputtering
+    on: the restored simulation (which never saw the sputtering yield: it
+    comes from the checkpoint) continues bit for bit."""
+    from test_gpu_parity import _electrode_beams
+    n = 32
+    cfg, parts = synthetic.rz_plume(n=n, total=2e4, seed=44)
+    cfg.update(field_on=1, inject_on=1, beta=1.0, coll_dt_scale=50.0, poisson_tol=1e-10, charge_max=4,
+               heavy_coll=1, coulomb=1, sputter=1, heavy_subcycle=2, capacity=1 << 18)
+    parts = synthetic.concat_loads([parts, _electrode_beams(n, n, 600, seed=7)])
+    E, Y = synthetic.standin_sputter_yield()
+    path = str(tmp_path / "ext.pdck")
+    a = pd.Simulation(cfg, xs)
+    a.set_sputter_yield(E, Y)
+    a.load(parts)
+    a.step(3)
+    a.save(path)
+    a.step(4)
+    b = pd.Simulation(cfg, xs)
+    b.restore(path)
+    b.step(4)
+    ga, gb = a.particles(), b.particles()
+    oa, ob = np.argsort(ga["id"]), np.argsort(gb["id"])
+    for key in ("id", "species", "iz", "ir", "pz", "pr", "vz", "vr", "vt"):
+        assert np.array_equal(ga[key][oa], gb[key][ob]), key
+    ca, cb = a.counters(), b.counters()
+    assert ca == cb
+    assert ca["sput_cathode"] + ca["sput_anode"] > 0 and ca["coul_ee"] > 0
