@@ -19,17 +19,23 @@ _BUILD = os.path.join(_HERE, "_build")
 _SRC = os.path.join(_HERE, "pd_oracle.c")
 
 
+def compile_source(src, so, fp64):
+    """Compile the oracle source file `src` into the shared object `so` with
+    the flags of the regular builds."""
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", *(["-DOR_DOUBLE"] if fp64 else []), "-o", so, src, "-lm"]
+    subprocess.check_call(cmd)
+
+
 def build(force=False):
     """Compile both oracle builds with gcc (no fused multiply-add)."""
     os.makedirs(_BUILD, exist_ok=True)
     outs = {}
-    for name, extra in (("oracle32", []), ("oracle64", ["-DOR_DOUBLE"])):
+    for name, extra in (("oracle32", False), ("oracle64", True)):
         so = os.path.join(_BUILD, f"lib{name}.so")
         if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
             tmp = so + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                   "-shared", *extra, "-o", tmp, _SRC, "-lm"]
-            subprocess.check_call(cmd)
+            compile_source(_SRC, tmp, fp64=bool(extra))
             os.replace(tmp, so)
         outs[name] = so
     return outs
@@ -60,48 +66,53 @@ D = C.POINTER(C.c_double)
 def _lib(fp64):
     key = "oracle64" if fp64 else "oracle32"
     if key not in _LIBS:
-        so = build()[key]
-        L = C.CDLL(so)
-        L.or_create.restype = P
-        L.or_create.argtypes = [C.POINTER(_Cfg)]
-        L.or_destroy.argtypes = [P]
-        L.or_set_xs.argtypes = [P, C.c_int, D, D, C.c_int, C.c_double]
-        L.or_set_yield.argtypes = [P, D, D, C.c_int]
-        L.or_load.restype = C.c_int64
-        L.or_load.argtypes = [P, C.c_int64, P, P, P, D, D, D, D, D]
-        L.or_set_field.argtypes = [P, D, D]
-        L.or_step.argtypes = [P, C.c_int]
-        L.or_prime.argtypes = [P]
-        L.or_count.restype = C.c_int64
-        L.or_count.argtypes = [P]
-        L.or_get_particles.argtypes = [P, P, P, P, P, D, D, D, D, D]
-        L.or_get_rho.argtypes = [P, P, P]
-        L.or_get_phi.argtypes = [P, D]
-        L.or_get_field.argtypes = [P, D, D]
-        L.or_get_counters.argtypes = [P, P]
-        L.or_get_scalars.argtypes = [P, D]
-        L.or_density_map.argtypes = [P, C.c_int, D]
-        L.or_energy_spectrum.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_int, P]
-        L.or_poisson_solve.argtypes = [P, D, C.c_double, C.c_double, D]
-        L.or_efield.argtypes = [P, D, D, D]
-        L.or_node_volume.restype = C.c_double
-        L.or_node_volume.argtypes = [P, C.c_int, C.c_int]
-        L.or_cell_volume.restype = C.c_double
-        L.or_cell_volume.argtypes = [P, C.c_int]
-        L.or_xs_lookup_d.restype = C.c_double
-        L.or_xs_lookup_d.argtypes = [P, C.c_int, C.c_double]
-        L.or_fn_current.restype = C.c_double
-        L.or_fn_current.argtypes = [C.c_double, C.c_double]
-        L.or_philox.argtypes = [P, P, P]
-        L.or_event_kinematics.argtypes = [P, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D, P]
-        L.or_rectangle_split.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D]
-        L.or_deposit_weights.argtypes = [C.c_double, C.c_double, P, P]
-        L.or_coulomb_kinematics.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, C.c_double, C.c_double,
-                                            C.c_double]
-        L.or_perm_index.restype = C.c_uint32
-        L.or_perm_index.argtypes = [C.c_uint32, C.c_uint32, P]
-        _LIBS[key] = L
+        _LIBS[key] = bind(build()[key])
     return _LIBS[key]
+
+
+def bind(so):
+    """Load one build of the oracle from the shared object `so` and declare
+    its entry points (the tests also bind builds they compile themselves)."""
+    L = C.CDLL(so)
+    L.or_create.restype = P
+    L.or_create.argtypes = [C.POINTER(_Cfg)]
+    L.or_destroy.argtypes = [P]
+    L.or_set_xs.argtypes = [P, C.c_int, D, D, C.c_int, C.c_double]
+    L.or_set_yield.argtypes = [P, D, D, C.c_int]
+    L.or_load.restype = C.c_int64
+    L.or_load.argtypes = [P, C.c_int64, P, P, P, D, D, D, D, D]
+    L.or_set_field.argtypes = [P, D, D]
+    L.or_step.argtypes = [P, C.c_int]
+    L.or_prime.argtypes = [P]
+    L.or_count.restype = C.c_int64
+    L.or_count.argtypes = [P]
+    L.or_get_particles.argtypes = [P, P, P, P, P, D, D, D, D, D]
+    L.or_get_rho.argtypes = [P, P, P]
+    L.or_get_phi.argtypes = [P, D]
+    L.or_get_field.argtypes = [P, D, D]
+    L.or_get_counters.argtypes = [P, P]
+    L.or_get_scalars.argtypes = [P, D]
+    L.or_density_map.argtypes = [P, C.c_int, D]
+    L.or_energy_spectrum.argtypes = [P, C.c_int, C.c_double, C.c_double, C.c_int, P]
+    L.or_poisson_solve.argtypes = [P, D, C.c_double, C.c_double, D]
+    L.or_efield.argtypes = [P, D, D, D]
+    L.or_node_volume.restype = C.c_double
+    L.or_node_volume.argtypes = [P, C.c_int, C.c_int]
+    L.or_cell_volume.restype = C.c_double
+    L.or_cell_volume.argtypes = [P, C.c_int]
+    L.or_xs_lookup_d.restype = C.c_double
+    L.or_xs_lookup_d.argtypes = [P, C.c_int, C.c_double]
+    L.or_fn_current.restype = C.c_double
+    L.or_fn_current.argtypes = [C.c_double, C.c_double]
+    L.or_philox.argtypes = [P, P, P]
+    L.or_event_kinematics.argtypes = [P, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D, P]
+    L.or_rectangle_split.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, D]
+    L.or_deposit_weights.argtypes = [C.c_double, C.c_double, P, P]
+    L.or_coulomb_kinematics.argtypes = [P, C.c_uint32, C.c_uint32, C.c_uint32, D, D, C.c_double, C.c_double,
+                                        C.c_double]
+    L.or_perm_index.restype = C.c_uint32
+    L.or_perm_index.argtypes = [C.c_uint32, C.c_uint32, P]
+    return L
 
 
 def _ptr(a):
@@ -139,8 +150,8 @@ def fn_current(F, work):
 class Oracle:
     """One CPU simulation.  `cfg` is a :func:`synthetic.base_config` dict."""
 
-    def __init__(self, cfg, fp64=True, field_mode=None):
-        self.L = _lib(fp64)
+    def __init__(self, cfg, fp64=True, field_mode=None, lib=None):
+        self.L = _lib(fp64) if lib is None else lib
         self.fp64 = fp64
         self.cfg = dict(cfg)
         c = _Cfg()
