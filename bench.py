@@ -29,6 +29,15 @@ ensemble under a CUDA graph with autotuned launch shapes, against the plain
 method (the same 64 runs as separate simulations, one after another), both
 with every Poisson solve at or below the same relative residual.
 
+--workload stress is the microbench with the collision time step scaled
+(--coll-scale, default 3200) so that a cell draws about one NTC candidate per
+step: it exercises the collision, spawn and ordered candidate loop at full
+size.  --workload production is the production-size breakdown: a 512 x 512
+r-z plume of 2e7 particles (e, Cu, Cu2+ with SW/DI labels; 60 % ionized,
+mean charge 2), self-consistent Poisson field to relres 1e-8 every step,
+heavies on every 10th step.  Both report per-kernel times and algorithmic
+GB/s.
+
 --impl reference times the CPU oracle (the plain restatement of the method)
 on a bounded sample of the same workload on this machine's host cores.
 """
@@ -51,8 +60,10 @@ UNIT = "particle-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def workload_desc(nz, nr, total, heavy_coll=0, coulomb=0):
-    return (f"DSMC collision microbench: {nz}x{nr} Cartesian cells (50 nm, periodic, no field), "
+def workload_desc(nz, nr, total, heavy_coll=0, coulomb=0, coll_scale=1.0):
+    return (("DSMC collision microbench" if coll_scale == 1.0 else
+             f"DSMC collision stress (microbench with the collision step x{coll_scale:g})")
+            + f": {nz}x{nr} Cartesian cells (50 nm, periodic, no field), "
             f"{total:.3g} super-particles (Cu lognormal(ln 1e23 m^-3, 1), Cu+ 10% of Cu, e = Cu+, "
             f"Te U[5,50] eV, heavies 2000 K), 5 channels incl. double ionization"
             + (" + charge exchange and Cu-Cu elastic pairs" if heavy_coll else "")
@@ -73,7 +84,12 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rows", type=int, default=512, help="rows of cells in the CPU-baseline sample")
     p.add_argument("--cpu-steps", type=int, default=10)
-    p.add_argument("--workload", default="microbench", choices=["microbench", "ensemble", "warmstart"])
+    p.add_argument("--workload", default="microbench",
+                   choices=["microbench", "stress", "production", "ensemble", "warmstart"])
+    p.add_argument("--coll-scale", type=float, default=None,
+                   help="collision time step scale (stress: default 3200, about one candidate per cell)")
+    p.add_argument("--prod-n", type=int, default=512, help="production: cells per side")
+    p.add_argument("--prod-total", type=float, default=2e7, help="production: particles")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--log-dir", default=".", help="where the clock samples of the timed region are written")
     p.add_argument("--heavy-coll", action="store_true",
@@ -90,6 +106,10 @@ def parse():
     p.add_argument("--ws-iters", type=int, default=3000)
     p.add_argument("--ws-eval-steps", type=int, default=30)
     a = p.parse_args()
+    if a.coll_scale is None:
+        a.coll_scale = 3200.0 if a.workload == "stress" else 1.0
+    if a.workload == "production" and "--steps" not in sys.argv:
+        a.steps = 50
     if a.workload == "ensemble":
         if "--steps" not in sys.argv:
             a.steps = 40
@@ -210,10 +230,25 @@ BYTES_PER_PARTICLE = {
     "push": 32.0,      # read key, pz, pr, vz, vr (20 B); write key, pz, pr (12 B)
     "scatter": 56.0,   # read 7 x 4 B, write 7 x 4 B
 }
-# DRAM bytes per particle of the same kernels from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of a 2.49e7-particle launch, profiles/push_scatter_512x512_2.5e7_ncu.md),
-# scaled to a launch by its particle count; to be set to None when the kernels change
+# DRAM bytes per particle of the same kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a 2.49e7-particle launch of
+# the 512 x 512 microbench), scaled to a launch by its particle count.  The
+# figures hold only for the kernel source they were taken on: TRAFFIC_SOURCE_SHA
+# is the SHA-256 of csrc/pd_stream.cu at the capture, and `traffic` is null
+# for any other source.
 TRAFFIC_PER_PARTICLE = {"push": 693.56e6 / 24898326, "scatter": 1362.67e6 / 24898326}
+TRAFFIC_SOURCE_SHA = "8a4704a567a68ffcf67db5b6ebdbf4f1b6510f12961ba286da03c32931dff281"
+TRAFFIC_SOURCE = "ncu dram bytes per particle of a 2.49e7-particle launch, scaled"
+
+
+def traffic_per_particle(kernel):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2109_00214_gb300", "csrc", "pd_stream.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return TRAFFIC_PER_PARTICLE.get(kernel) if sha == TRAFFIC_SOURCE_SHA else None
 
 
 def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
@@ -225,7 +260,7 @@ def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
     rows = args.cpu_rows if rows is None else rows
     steps = args.cpu_steps if steps is None else steps
     total = args.total * rows / args.nz
-    cfg, parts = synthetic.microbench(nz=rows, nr=args.nr, total=total, seed=seed)
+    cfg, parts = synthetic.microbench(nz=rows, nr=args.nr, total=total, seed=seed, coll_scale=args.coll_scale)
     cfg["heavy_coll"] = int(args.heavy_coll)
     cfg["coulomb"] = int(args.coulomb)
     o = oracle.Oracle(cfg, fp64=False)
@@ -245,19 +280,55 @@ def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
                       f"{steps} timed steps, {dt:.1f} s, single-threaded C oracle (float mirror)"}
 
 
+def cpu_baseline_production(args, seed, n=128, steps=None, warmup=1):
+    """The oracle on a bounded sample of the production breakdown: the same
+    plume recipe on an n x n grid with the particle total scaled by area
+    (the oracle's conjugate-gradient solve of every step included)."""
+    import oracle
+    import synthetic
+    steps = args.cpu_steps if steps is None else steps
+    total = args.prod_total * (n / args.prod_n) ** 2
+    cfg, parts = synthetic.rz_plume(n=n, total=total, seed=seed)
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-8)
+    o = oracle.Oracle(cfg, fp64=False)
+    o.set_cross_sections(synthetic.standin_cross_sections())
+    o.load(parts)
+    o.prime()
+    if warmup:
+        o.step(warmup)
+
+    def counts():
+        return np.bincount(o.particles()["species"], minlength=7).astype(np.float64)
+
+    c0 = counts()
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    c1 = counts()
+    upd = step_updates(c0, c1, steps, cfg["heavy_subcycle"])
+    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "ms_per_step": 1e3 * dt / steps,
+            "sample": f"the production plume recipe on {n}x{n} cells ({int(c0.sum())} particles), {warmup} untimed "
+                      f"and {steps} timed steps, {dt:.1f} s, single-threaded C oracle (float mirror, CG field solve)"}
+
+
+def cpu_baseline_for(args, seed, steps=None, warmup=0, rows=None):
+    if args.workload == "production":
+        return cpu_baseline_production(args, seed, steps=steps, warmup=max(warmup, 1))
+    return cpu_baseline(args, None, seed=seed, rows=rows, steps=steps, warmup=warmup)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     # the K timed steps (after W untimed ones) run on a sample of rows sized
     # for about ten 512-row steps of oracle time in all
     rows = max(8, min(args.cpu_rows, (args.cpu_rows * args.cpu_steps // max(args.steps, 1)) // 8 * 8))
-    cb = cpu_baseline(args, None, seed=1, rows=rows, steps=args.steps, warmup=args.warmup)
+    cb = cpu_baseline_for(args, seed=1, rows=rows, steps=args.steps, warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb)
-                       + " (bounded CPU sample)",
-                       "nz": rows, "nr": args.nr},
+            "config": {"workload": single_workload_desc(args) + " (bounded CPU sample)",
+                       "sample": cb["sample"]},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -544,18 +615,62 @@ def run_warmstart(args, ws, rank, local):
         net.close()
 
 
-def main():
-    args = parse()
-    ws, rank, local = dist_setup(args)
-    if args.impl == "reference":
-        run_reference(args, ws, rank)
-        return
-    if args.workload in ("ensemble", "warmstart"):
-        (run_ensemble if args.workload == "ensemble" else run_warmstart)(args, ws, rank, local)
-        if ws > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
-        return
+def single_workload_desc(args):
+    if args.workload == "production":
+        return (f"production breakdown: {args.prod_n}x{args.prod_n} r-z cells over the 6 um gap, "
+                f"{args.prod_total:.3g} super-particles of a near-cathode Cu plume (e, Cu, Cu2+ SW/DI; 60 % "
+                f"ionized, mean charge 2, Te 5 eV, heavies 2000 K), self-consistent Poisson field to relres "
+                f"1e-8 every step (extrapolated start), heavies every 10th step, cathode emission off, FP32 "
+                f"cell-relative state, int64 deposit, dt = 1 fs")
+    return workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb, args.coll_scale)
+
+
+def single_workload(args, seed):
+    """(config, particles, description, warm-start mode) of the one-simulation workloads."""
+    import synthetic
+    if args.workload == "production":
+        cfg, parts = synthetic.rz_plume(n=args.prod_n, total=args.prod_total, seed=seed)
+        cfg.update(field_on=1, inject_on=0, poisson_tol=1e-8)
+        return cfg, parts, single_workload_desc(args), "extrapolate"
+    cfg, parts = synthetic.microbench(nz=args.nz, nr=args.nr, total=args.total, seed=seed,
+                                      coll_scale=args.coll_scale)
+    cfg["heavy_coll"] = int(args.heavy_coll)
+    cfg["coulomb"] = int(args.coulomb)
+    return cfg, parts, single_workload_desc(args), None
+
+
+def step_updates(c0, c1, steps, heavy_subcycle):
+    """Particle updates of `steps` steps from the species counts at their start
+    and end: electrons every step, heavies on their sub-cycle steps."""
+    return ensemble_updates(c0, c1, steps, heavy_subcycle)
+
+
+def kernel_table(prof, steps, n_live, n_moved_e, n_moved_h, cand, ncell, nbins, rz_field, peak):
+    """Per-kernel time per step and, where the kernel has a per-unit byte
+    model, its algorithmic GB/s and fraction of the HBM peak."""
+    push_bytes = (24.0 * n_live + 20.0 * (n_moved_e + n_moved_h)) if rz_field else BYTES_PER_PARTICLE["push"] * n_live
+    model = {
+        "push": push_bytes,
+        "scatter": BYTES_PER_PARTICLE["scatter"] * n_live,
+        "scan_bins": 12.0 * nbins,
+        "ncand": 24.0 * ncell,
+        "collide": 100.0 * cand,
+    }
+    out = {}
+    for k, (ms, n) in prof.items():
+        if not n:
+            continue
+        row = {"ms_per_step": ms / steps, "launches_per_step": n / steps}
+        if k in model and ms > 0:
+            gbs = model[k] / (ms / steps * 1e-3) / 1e9
+            row.update({"algorithmic_bytes_per_step": model[k], "GBs": gbs, "frac_of_peak": gbs / peak})
+        out[k] = row
+    return out
+
+
+def run_single(args, ws, rank, local):
+    """One simulation on one GPU (replicas: one per rank): the microbench, its
+    stress variant or the production breakdown."""
     import torch
     import paper_2109_00214_gb300 as pd
     import synthetic
@@ -564,26 +679,35 @@ def main():
     dev = torch.device("cuda", local)
     pd.load_library()
     seed = 1 + rank
-    cfg, parts = synthetic.microbench(nz=args.nz, nr=args.nr, total=args.total, seed=seed)
-    cfg["heavy_coll"] = int(args.heavy_coll)
-    cfg["coulomb"] = int(args.coulomb)
+    cfg, parts, desc, warm = single_workload(args, seed)
     xs = synthetic.standin_cross_sections()
     n_in = len(parts["species"])
+    hs = cfg["heavy_subcycle"]
+    rz_field = cfg["geometry"] == "rz" and cfg["field_on"] == 1
+    steps = args.steps
+    if hs > 1:                 # whole heavy cycles
+        steps = -(-steps // hs) * hs
 
     # ---- device-resident run (value) -------------------------------------
     sim = pd.Simulation(cfg, xs, device=dev)
+    if warm:
+        sim.set_warm_start(warm)
     keys = ("species", "iz", "ir", "pz", "pr", "vz", "vr", "vt")
     dtens = {k: torch.from_numpy(parts[k]).to(dev) for k in keys}
     sim.load_device(dtens)
     del dtens
     torch.cuda.synchronize()
     tuning = None if args.no_autotune else sim.autotune(2)   # its trial steps are untimed warm-up
-    sim.step(args.warmup)
+    done = int(sim.scalars()["step"])
+    warm_steps = args.warmup + ((hs - (done + args.warmup) % hs) % hs if hs > 1 else 0)
+    sim.step(warm_steps)
     sim.synchronize()
     pd.pd_profile_read(sim.h)              # discard warm-up launch records
     pd.pd_profile_enable(sim.h, 1)
     counters0 = sim.counters()
-    n0 = sim.scalars()["n_particles"]
+    sc0 = sim.scalars()
+    ss0 = sim.sort_stats()
+    n0 = sc0["n_particles"]
     stream = sim.stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -593,7 +717,7 @@ def main():
     barrier(ws)
     torch.cuda.synchronize()
     e0.record(stream)
-    sim.step(args.steps)
+    sim.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
@@ -601,40 +725,62 @@ def main():
     ms = e0.elapsed_time(e1)
     prof = pd.pd_profile_read(sim.h)
     pd.pd_profile_enable(sim.h, 0)
-    n1 = sim.scalars()["n_particles"]
+    sc1 = sim.scalars()
+    n1 = sc1["n_particles"]
     sim.synchronize()
     ms_max = max_over_ranks(ws, ms, dev)
-    updates = args.steps * 0.5 * (n0 + n1)
+    c0 = np.array(sc0["count"], dtype=np.float64)
+    c1 = np.array(sc1["count"], dtype=np.float64)
+    updates = step_updates(c0, c1, steps, hs)
     total_updates = sum_over_ranks(ws, updates, dev)
     value = total_updates / (ms_max * 1e-3)
     launches = int(sum(v[1] for v in prof.values()))
+    counters1 = sim.counters()
+    counters = {k: counters1[k] - counters0[k] for k in counters1}   # events of the timed steps
+    ss1 = sim.sort_stats()
+    sort = {"relayouts_in_timed_steps": ss1["relayouts"] - ss0["relayouts"],
+            "bin_slots_per_live_particle": ss1["bin_slots"] / max(ss1["live"], 1)}
 
     # roofline of the dominant kernel (largest time share in the timed region)
     peak, peak_kind = peaks()
-    dom = max(("push", "scatter"), key=lambda k: prof[k][0])
+    n_live = 0.5 * (n0 + n1)
+    ne = 0.5 * (c0[0] + c1[0])
+    nh = n_live - ne
+    ncell = cfg["nz"] * cfg["nr"]
+    nbins = ncell * (7 if cfg.get("charge_max", 2) >= 3 else 5)
+    table = kernel_table(prof, steps, n_live, ne, nh / hs, counters["cand_total"] / steps, ncell, nbins,
+                         rz_field, peak)
+    cands = [k for k in ("push", "scatter") if k in table and "GBs" in table[k]]
+    dom = max(cands, key=lambda k: table[k]["ms_per_step"])
     per_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
-    bytes_per_launch = BYTES_PER_PARTICLE[dom] * 0.5 * (n0 + n1)
+    bytes_per_launch = table[dom]["algorithmic_bytes_per_step"] / table[dom]["launches_per_step"]
     achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     total_kernel_ms = sum(v[0] for v in prof.values())
-    tpp = TRAFFIC_PER_PARTICLE.get(dom)
+    tpp = None if (rz_field or args.coll_scale != 1.0) else traffic_per_particle(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "traffic": tpp * 0.5 * (n0 + n1) if tpp else None,
-                "traffic_source": "ncu dram bytes per particle of a 2.49e7-particle launch, scaled" if tpp else None,
+                "traffic": tpp * n_live if tpp else None,
+                "traffic_source": TRAFFIC_SOURCE if tpp else None,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "launch_ms": per_launch_ms,
                 "share": prof[dom][0] / total_kernel_ms if total_kernel_ms > 0 else None,
-                "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]}}
-    counters1 = sim.counters()
-    counters = {k: counters1[k] - counters0[k] for k in counters1}   # events of the timed steps
+                "kernels_ms_per_step": {k: v["ms_per_step"] for k, v in table.items()}}
+    poisson = None
+    if rz_field:
+        poisson = {"cycles_last": sc1["poisson_cycles"], "relres_max": sc1["poisson_relres_max"],
+                   "tol": cfg["poisson_tol"], "warm_start": warm}
     sim.close()
     del sim
     torch.cuda.empty_cache()
 
     # ---- end-to-end through the public API with host buffers -------------
+    # the particle load is the run's input: it is copied host -> device once
+    # per timed run of `steps` steps, and the scalars are read back at its end
     e2e = None
     if not args.no_e2e:
         sim2 = pd.Simulation(cfg, xs, device=dev)
+        if warm:
+            sim2.set_warm_start(warm)
         if tuning:
             sim2.set_tuning(**tuning)
         # the inputs in pinned host memory (prepared outside the timed region)
@@ -643,38 +789,55 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pd.pd_load_particles_ptrs(sim2.h, n_in, [pinned[k].data_ptr() for k in keys])   # host -> device
-        sim2.step(args.steps)
+        sim2.step(steps)
         sc = sim2.scalars()                 # device -> host read of the result
         t1 = time.perf_counter()
         barrier(ws)
         wall = max_over_ranks(ws, t1 - t0, dev)
-        upd2 = sum_over_ranks(ws, args.steps * 0.5 * (n_in + sc["n_particles"]), dev)
+        ce = np.zeros(7)
+        for sp in range(7):
+            ce[sp] = float(np.count_nonzero(parts["species"] == sp))
+        upd2 = sum_over_ranks(ws, step_updates(ce, np.array(sc["count"], dtype=np.float64), steps, hs), dev)
         h2d = 29 * n_in                     # species 1 B, cell indices 2 x 4 B, offsets and velocities 5 x 4 B
         d2h = 1024 + 5 * 8
-        e2e = {"value": upd2 / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-               "d2h_bytes_per_step": d2h / args.steps}
+        e2e = {"value": upd2 / wall, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+               "d2h_bytes_per_step": d2h / steps,
+               "copies": "particle load host -> device once per timed run of `steps` steps (pinned), "
+                         "scalars device -> host at its end"}
         sim2.close()
         del sim2
         torch.cuda.empty_cache()
 
     cb = None
     if rank == 0 and not args.no_cpu and ws == 1:
-        cb = cpu_baseline(args, cfg, seed=1)
+        cb = cpu_baseline_for(args, seed=1)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+                "warmup": warm_steps, "ms_per_step": ms_max / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_desc(args.nz, args.nr, args.total, args.heavy_coll, args.coulomb),
-                           "nz": args.nz, "nr": args.nr,
+                "config": {"workload": desc, "nz": cfg["nz"], "nr": cfg["nr"],
                            "particles_per_gpu": int(n0), "parallelism": f"replicas x{ws}" if ws > 1 else "single",
                            "tuning": tuning,
                            "l2": "inputs larger than L2 (28 B x particles resident in HBM); no flush"},
-                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clocks,
+                "roofline": roofline, "kernels": table, "sort": sort, "poisson": poisson, "cpu_baseline": cb,
+                "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks,
                 "events": {k: counters[k] for k in ("ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "ev_cx", "ev_nn",
                                                     "coul_ee", "coul_ei", "cand_total")}}
         print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    if args.workload in ("ensemble", "warmstart"):
+        (run_ensemble if args.workload == "ensemble" else run_warmstart)(args, ws, rank, local)
+    else:
+        run_single(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

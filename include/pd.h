@@ -206,6 +206,26 @@ pd_status pd_get_scalars(pd_sim* sim, pd_scalars* out);
 pd_status pd_get_counters(pd_sim* sim, uint64_t* out /* PD_NCOUNTERS */);
 /* Slots in use (live + dead); size for pd_get_particles. */
 pd_status pd_particle_slots(pd_sim* sim, int64_t* slots);
+/* State of the cell sort (no counterpart in the paper: the particle store's
+ * bookkeeping).  Particles are kept in bins of one species and cell with
+ * slack slots after each bin's particles; a step moves only the particles
+ * that change bin, and lays all bins out anew (with slack sized from each
+ * bin's traffic) only when a bin runs out of slots.  Synchronises. */
+typedef struct pd_sort_stats {
+    uint64_t relayouts;        /* new layouts of the bins since create (or load) */
+    uint64_t bin_slots;        /* slots of all bins, live and slack */
+    uint64_t live;             /* particles in bins */
+    uint64_t steps_since;      /* steps since the last new layout */
+    uint64_t faults;           /* consistency checks of the sort that failed (a bit per check), 0 if none */
+} pd_sort_stats;
+pd_status pd_get_sort_stats(pd_sim* sim, pd_sort_stats* out);
+/* The bins of the sort (for tests and diagnostics): `start` (nbins + 1
+ * entries, host) receives the first slot of each bin and, last, the first
+ * slot of the tail; `count` (nbins entries, host) the particles of each bin.
+ * Bins are species-major: bin = species * cells + cell, for the species that
+ * have bins (5, or 7 with charge_max >= 3); *nbins receives their number when
+ * `start` and `count` are NULL.  Synchronises. */
+pd_status pd_get_bins(pd_sim* sim, uint32_t* start, uint32_t* count, int64_t* nbins);
 /* Copy every slot to host arrays of pd_particle_slots() entries; dead slots
  * have species 255 and run -1.  Order is the device order (cell-sorted, not
  * by id).  `run` (may be NULL) receives the run of each particle; iz, ir are

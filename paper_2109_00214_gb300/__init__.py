@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "config_from_dict",
            "pd_config_default", "pd_workspace_size", "pd_create", "pd_set_cross_section", "pd_set_sputter_yield",
            "pd_load_particles", "pd_load_particles_device", "pd_set_field", "pd_inject_cathode",
-           "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots",
+           "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots", "pd_get_sort_stats", "pd_get_bins",
            "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
            "pd_get_energy_spectrum", "pd_profile_enable", "pd_profile_read", "pd_kernel_name",
            "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "Ensemble", "pd_ensemble_workspace_size",
@@ -112,6 +112,8 @@ _SIGS = {
     "pd_get_scalars": (C.c_int, [P, C.POINTER(PdScalars)]),
     "pd_get_counters": (C.c_int, [P, P]),
     "pd_particle_slots": (C.c_int, [P, C.POINTER(C.c_int64)]),
+    "pd_get_sort_stats": (C.c_int, [P, P]),
+    "pd_get_bins": (C.c_int, [P, P, P, C.POINTER(C.c_int64)]),
     "pd_get_particles": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
     "pd_ensemble_workspace_size": (C.c_int, [C.POINTER(PdConfig), C.c_int, C.POINTER(C.c_size_t)]),
     "pd_ensemble_create": (C.c_int, [C.POINTER(PdConfig), C.c_int, P, C.c_size_t, P, C.POINTER(P)]),
@@ -308,6 +310,28 @@ def pd_get_counters(h):
     a = np.zeros(PD_NCOUNTERS, np.uint64)
     _check(h, _lib().pd_get_counters(h, _ptr(a)), "pd_get_counters")
     return dict(zip(COUNTER_NAMES, (int(x) for x in a)))
+
+
+class PdSortStats(C.Structure):
+    _fields_ = [("relayouts", C.c_uint64), ("bin_slots", C.c_uint64), ("live", C.c_uint64),
+                ("steps_since", C.c_uint64), ("faults", C.c_uint64)]
+
+
+def pd_get_sort_stats(h):
+    st = PdSortStats()
+    _check(h, _lib().pd_get_sort_stats(h, C.byref(st)), "pd_get_sort_stats")
+    return {name: int(getattr(st, name)) for name, _ in st._fields_}
+
+
+def pd_get_bins(h):
+    """(start, count) of the sort's bins: start has nbins + 1 entries (the
+    last is the first slot of the tail)."""
+    nb = C.c_int64(0)
+    _check(h, _lib().pd_get_bins(h, None, None, C.byref(nb)), "pd_get_bins")
+    start = np.zeros(nb.value + 1, np.uint32)
+    count = np.zeros(nb.value, np.uint32)
+    _check(h, _lib().pd_get_bins(h, _ptr(start), _ptr(count), C.byref(nb)), "pd_get_bins")
+    return start, count
 
 
 def pd_particle_slots(h):
@@ -714,6 +738,12 @@ class Simulation:
 
     def counters(self):
         return pd_get_counters(self.h)
+
+    def sort_stats(self):
+        return pd_get_sort_stats(self.h)
+
+    def bins(self):
+        return pd_get_bins(self.h)
 
     def particles(self, live_only=True):
         return pd_get_particles(self.h, live_only)

@@ -51,16 +51,19 @@ size_t run_nodes(const pd_config& c) {
 
 struct Layout {
     size_t total = 0;
-    size_t A[7], B[7];
-    size_t count, off, off2, outc, stay, dlt, cntb, mv, mvx, partial, nc, nc2, cw, ytab, squeue, cand, cand_off, active,
+    size_t A[7], B[7], M[7];
+    size_t count, off, off2, outc, bcnt, act, net, bigq, cntb, mv, mm, partial, nc, nc2, cw, ytab, squeue, cand,
+        cand_off, active,
         mid, big, rho_e,
         rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
         rho_last, rho_prev, phi_prev, V_last, V_prev;
-    uint32_t nbins_pad, ncell_pad, words_pad;
+    uint32_t nbins_pad, ncell_pad, words_pad, bigq_cap;
     int nsp;                         // species with bins
     uint32_t squeue_cap;             // sputtering impacts per step
-    uint64_t cap, ncell, nodes, ck_len, rows;
+    uint64_t cap;                    // physical slots: the configured capacity plus room for the bins' slack
+    uint64_t cap_user;               // the configured capacity (particles, live and reserved for spawns)
+    uint64_t ncell, nodes, ck_len, rows;
     size_t field_bytes;
 };
 
@@ -84,7 +87,12 @@ Layout make_layout(const std::vector<pd_config>& cf) {
         nz[r] = cf[r].nz;
         nr[r] = cf[r].nr;
     }
-    cap = (cap + 3) & ~3ull;   // slot arrays move in groups of four
+    L.cap_user = cap;
+    // slots beyond the capacity hold the slack of the bins (the capacity
+    // again, and one slot per bin); slot arrays move in groups of four and
+    // the mover masks in groups of 128
+    const uint64_t nbins_all = ncell * (uint64_t)(cf[0].charge_max >= 3 ? NSP : 5);
+    cap = (2 * cap + nbins_all + 2048 + 127) & ~127ull;
     L.cap = cap;
     L.ncell = ncell;
     L.nodes = nodes;
@@ -97,16 +105,20 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.nbins_pad = scan_padded(ncell * (uint64_t)L.nsp);
     L.ncell_pad = scan_padded(ncell);
     L.words_pad = scan_padded(cap / 32 + 1);
-    L.count = take((size_t)L.nbins_pad * 4);               // movers into each bin (cursor in the scatter)
-    L.off = take(((size_t)L.nbins_pad + 1) * 4);           // bin offsets, two copies (previous / new)
+    L.count = take((size_t)L.nbins_pad * 4);               // movers into each bin (cursor of the insertion)
+    L.off = take(((size_t)L.nbins_pad + 1) * 4);           // bin starts: the layout, and the next one
     L.off2 = take(((size_t)L.nbins_pad + 1) * 4);
-    L.outc = take((size_t)L.nbins_pad * 4);                // movers out of each bin
-    L.stay = take((size_t)L.nbins_pad * 4);                // particles that stay in each bin
-    L.dlt = take((size_t)L.nbins_pad * 4);                 // stayers' slot offset of each bin
-    L.cntb = take((size_t)L.nbins_pad * 4);                // new bin counts (scan input)
-    L.mv = take((size_t)L.words_pad * 4);                  // mover bit mask of the sorted slots
-    L.mvx = take(((size_t)L.words_pad + 1) * 4);           // its popcount prefix
-    const size_t npart = (size_t)std::max(std::max(L.nbins_pad, L.ncell_pad), L.words_pad) / SCAN_TILE + 1;
+    L.outc = take((size_t)L.nbins_pad * 4);                // particles leaving each bin
+    L.bcnt = take((size_t)L.nbins_pad * 4);                // live particles of each bin
+    L.act = take((size_t)L.nbins_pad * 4);                 // bin traffic since the last layout
+    L.net = take((size_t)L.nbins_pad * 4);
+    L.bigq_cap = bigq_max(cap);
+    L.bigq = take((size_t)L.bigq_cap * 16);                // long bins with holes
+    L.cntb = take((size_t)L.nbins_pad * 4);                // re-layout: bin capacities (scan input)
+    L.mv = take((size_t)L.words_pad * 4);                  // slots vacated in their bin
+    L.mm = take((size_t)L.words_pad * 4);                  // slots whose particle is in the mover records
+    for (int k = 0; k < 7; ++k) L.M[k] = take(cap * 4);  // movers at their slots' indices
+    const size_t npart = (size_t)std::max(L.nbins_pad, L.ncell_pad) / SCAN_TILE + 1;
     L.partial = take(npart * 4);
     L.nc = take(ncell * 16);                               // candidates of classes 0, 1, 5, 6
     L.nc2 = take(L.nsp == NSP ? ncell * 16 : 16);          // classes 2, 3, 4 (step-wise)
@@ -126,7 +138,8 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.cw = take(2 * rows * 8);                             // W dt / V_cell per row, electron then heavy step
     L.ray = take(1024 * 4);
     L.ytab = take(XS_N * 4);                               // sputtering yield on the table grid
-    L.squeue_cap = cf[0].sputter ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>(cap / 16, 4096), 1u << 20) : 16u;
+    L.squeue_cap =
+        cf[0].sputter ? (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.cap_user / 16, 4096), 1u << 20) : 16u;
     L.squeue = take((size_t)L.squeue_cap * sizeof(SputRec));
     L.hist = take(4096 * 8);
     L.spc = take((size_t)R * NSP * 8);                     // live particles per run and species
@@ -166,8 +179,11 @@ struct pd_sim {
     char* ws;
     int sms;
     Particles A, B;
-    uint32_t *count, *off, *off2, *outc, *stay, *dlt, *cntb, *mv, *mvx, *partial, *cand, *cand_off, *active, *mid, *big;
-    bool sorted_valid;      // slots [0, off[nbins]) of A hold the previous step's sorted order
+    uint32_t *count, *off, *off2, *outc, *bcnt, *act, *cntb, *mv, *mm, *partial, *cand, *cand_off, *active, *mid, *big;
+    int* net;
+    uint4* bigq;
+    Particles M;            // movers of the step, at their slots' indices
+    bool sorted_valid;      // the bins of A have a layout (after the first step)
     uint4* nc;
     uint4* nc2;
     long long *rho_e, *rho_h, *diag;
@@ -303,8 +319,8 @@ KParams kparams(const pd_sim* s, int heavy_step) {
     P.squeue = s->squeue;
     P.squeue_cap = s->L.squeue_cap;
     P.field_on = c.field_mode != PD_FIELD_NONE;
-    P.use_prev = s->sorted_valid ? 1 : 0;
     P.capacity = (unsigned long long)s->L.cap;
+    P.user_capacity = (unsigned long long)s->L.cap_user;
     for (int k = 0; k < NSP; ++k) P.masses[k] = species_mass(k);
     P.run0 = s->runs[0];
     P.runs = s->runs_dev;
@@ -501,7 +517,11 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         cap += (uint64_t)b.capacity;
     }
     if (cells >= (1u << 24)) { msg = "all runs together must have < 2^24 cells"; return PD_ERR_ARG; }
-    if (cap > 0xFFFFFFF0ull) { msg = "all runs together must have < 2^32 slots"; return PD_ERR_ARG; }
+    // the slot arrays hold the capacity twice (the bins' slack) and a slot per bin
+    if (2 * cap + 7 * cells + 4096 > 0xFFFFFFF0ull) {
+        msg = "all runs together must have a capacity below 2^31 particles";
+        return PD_ERR_ARG;
+    }
     return PD_OK;
 }
 
@@ -620,41 +640,65 @@ pd_status issue_step(pd_sim* s, bool capturing) {
         Timed t(s, K_MEMSET, capturing, 0);   // memsets, no kernels
         cudaMemsetAsync(s->rho_e, 0, nodes * 8, s->stream);
         if (heavy) cudaMemsetAsync(s->rho_h, 0, nodes * 8, s->stream);
-        // mover bits are OR-ed in by the push: start from zero
+        // vacated-slot and mover bits are OR-ed in by the push: start from zero
         cudaMemsetAsync(s->mv, 0, (size_t)s->L.words_pad * 4, s->stream);
+        cudaMemsetAsync(s->mm, 0, (size_t)s->L.words_pad * 4, s->stream);
     }
     {
         Timed t(s, K_PUSH, capturing, 1);
-        launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->off, nbins, s->st, P, gpart,
+        launch_push(s->A, s->E, s->rho_e, s->rho_h, s->outc, s->count, s->mv, s->mm, s->M, s->st, P, gpart,
                     s->stream);
     }
     if (c.sputter && heavy && c.geometry == PD_GEOM_RZ) {
         // ions reach the electrodes on heavy steps: their sputtered atoms join this step's sort
         Timed t(s, K_INJECT, capturing, 1);
-        launch_sputter(s->A, s->st, P, s->ray, s->count, s->stream);
+        launch_sputter(s->M, s->mm, s->st, P, s->ray, s->count, s->stream);
     }
     {
-        Timed t(s, K_SCAN_BINS, capturing, P.use_prev ? 8 : 4);
-        launch_bincount(s->off, s->outc, s->count, s->cntb, s->stay, s->L.nbins_pad, P.use_prev,
-                        grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
-        launch_scan(s->cntb, s->off2, s->partial, s->L.nbins_pad, s->stream);
-        if (P.use_prev) {
-            launch_scan_popc(s->mv, s->mvx, s->partial, s->L.words_pad, s->stream);
-            launch_bin_delta(s->off, s->off2, s->mv, s->mvx, s->dlt, nbins,
-                             grid_for(s, s->tune.bincount_blocks_per_sm), s->stream);
+        SortArgs a;
+        a.A = s->A;
+        a.B = s->B;
+        a.M = s->M;
+        a.mv = s->mv;
+        a.mm = s->mm;
+        a.off = s->off;
+        a.off2 = s->off2;
+        a.cnt = s->bcnt;
+        a.out_cnt = s->outc;
+        a.in_cnt = s->count;
+        a.cap = s->cntb;
+        a.act = s->act;
+        a.net = s->net;
+        a.bigq = s->bigq;
+        a.bigq_cap = s->L.bigq_cap;
+        a.partial = s->partial;
+        a.nbins = nbins;
+        a.nbins_pad = s->L.nbins_pad;
+        a.slots = s->L.cap;
+        a.ncell_pad = s->L.ncell_pad;
+        {
+            // heavy bins: counts, holes closed (k_bins, k_compact_big)
+            Timed t(s, K_SCATTER, capturing, 2);
+            launch_sort(a, s->st, P, s->sms, s->stream);
+        }
+        {
+            // the re-layout of the heavy bins (three kernels, a scan of three,
+            // and four more) returns at once unless a heavy bin overflowed
+            Timed t(s, K_SCAN_BINS, capturing, 10);
+            launch_relayout(a, s->st, P, grid_for(s, s->tune.bincount_blocks_per_sm),
+                            grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
+        }
+        {
+            // electron bins laid out (a scan of three, k_ebins), movers
+            // inserted (k_insert, k_insert_dense)
+            Timed t(s, K_SCATTER, capturing, 6);
+            launch_insert(a, s->st, P, grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
         }
     }
-    {
-        Timed t(s, K_SCATTER, capturing, 1);
-        launch_scatter(s->A, s->B, s->off, s->off2, s->stay, s->dlt, s->count, s->mv, s->mvx, nbins, s->st, P,
-                       grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
-    }
-    std::swap(s->A, s->B);
-    std::swap(s->off, s->off2);
     s->sorted_valid = true;
     {
         Timed t(s, K_NCAND, capturing, 1);
-        launch_ncand(s->off, s->ck, s->nc, s->nc2, s->cand, s->active, s->mid, s->big, s->st, P,
+        launch_ncand(s->bcnt, s->ck, s->nc, s->nc2, s->cand, s->active, s->mid, s->big, s->st, P,
                      grid_for(s, s->tune.ncand_blocks_per_sm), s->stream);
     }
     {
@@ -663,7 +707,8 @@ pd_status issue_step(pd_sim* s, bool capturing) {
     }
     {
         Timed t(s, K_COLLIDE, capturing, 3);
-        launch_collide(s->A, s->B, s->off, s->nc, s->nc2, s->cand_off, s->active, s->mid, s->big, s->st, s->rho_e, s->rho_h,
+        launch_collide(s->A, s->B, s->off, s->bcnt, s->nc, s->nc2, s->cand_off, s->active, s->mid, s->big, s->st,
+                       s->rho_e, s->rho_h,
                        s->xsE, s->xs, s->cw, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
                        s->stream);
     }
@@ -693,12 +738,12 @@ pd_status issue_step(pd_sim* s, bool capturing) {
 
 int graph_period(const pd_sim* s) {
     const int h = s->cfgs[0].heavy_subcycle;
-    return (h % 2 == 0) ? h : 2 * h;   // whole heavy cycles, even (buffers swap every step)
+    return (h % 2 == 0) ? h : 2 * h;   // whole heavy cycles, even
 }
 
 // ---- checkpoint file: a header, then the sections in a fixed order ----
 constexpr char CKPT_MAGIC[8] = {'P', 'D', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr uint32_t CKPT_VERSION = 2;
+constexpr uint32_t CKPT_VERSION = 3;
 
 struct CkptHeader {
     char magic[8];
@@ -863,11 +908,14 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->off = P32(L.off);
     s->off2 = P32(L.off2);
     s->outc = P32(L.outc);
-    s->stay = P32(L.stay);
-    s->dlt = P32(L.dlt);
+    s->bcnt = P32(L.bcnt);
+    s->act = P32(L.act);
+    s->net = (int*)(w + L.net);
+    s->bigq = (uint4*)(w + L.bigq);
     s->cntb = P32(L.cntb);
     s->mv = P32(L.mv);
-    s->mvx = P32(L.mvx);
+    s->mm = P32(L.mm);
+    s->M = Particles{P32(L.M[0]), PF(L.M[1]), PF(L.M[2]), PF(L.M[3]), PF(L.M[4]), PF(L.M[5]), P32(L.M[6])};
     s->sorted_valid = false;
     s->partial = P32(L.partial);
     s->nc = (uint4*)(w + L.nc);
@@ -1018,6 +1066,13 @@ pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const in
 // positions and velocities into their slots, species and cell indices into
 // the other particle buffer, free between steps -- and checked and packed
 // there by the device load
+
+// particles in bins plus the tail's slots (loaded or spawned, not yet
+// sorted) plus n more: above the configured capacity?
+bool load_exceeds(const pd_sim* s, const DevState& d, int64_t n) {
+    return d.n_live + d.n_e + (d.n_slots - d.tail_base) + (uint64_t)n > s->L.cap_user;
+}
+
 pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int32_t* iz, const int32_t* ir,
                     const float* pz, const float* pr, const float* vz, const float* vr, const float* vt) {
     if (!s) return PD_ERR_ARG;
@@ -1028,7 +1083,8 @@ pd_status load_host(pd_sim* s, int run, int64_t n, const uint8_t* sp, const int3
     DevState d;
     pd_status r = sync_check(s, &d);
     if (r != PD_OK) return r;
-    if (d.n_slots + (uint64_t)n > s->L.cap) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if (d.n_slots + (uint64_t)n > s->L.cap || load_exceeds(s, d, n))
+        return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
     const size_t o = d.n_slots, nb = (size_t)n * 4;
     int32_t* diz = reinterpret_cast<int32_t*>(s->B.key + o);
     int32_t* dir = reinterpret_cast<int32_t*>(s->B.id + o);
@@ -1057,7 +1113,8 @@ pd_status load_device(pd_sim* s, int run, int64_t n, const uint8_t* sp, const in
     RunState rs;
     r = read_run(s, run, &rs);
     if (r != PD_OK) return r;
-    if (d.n_slots + (uint64_t)n > s->L.cap) return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
+    if (d.n_slots + (uint64_t)n > s->L.cap || load_exceeds(s, d, n))
+        return fail(s, PD_ERR_CAPACITY, "load exceeds capacity");
     if ((uint64_t)rs.id_next + (uint64_t)n > 0xFFFFFFFFull) return fail(s, PD_ERR_CAPACITY, "id space exhausted");
     const RunInfo& RI = s->runs[run];
     const size_t o = d.n_slots;
@@ -1419,6 +1476,35 @@ pd_status pd_particle_slots(pd_sim* s, int64_t* slots) {
     return PD_OK;
 }
 
+pd_status pd_get_sort_stats(pd_sim* s, pd_sort_stats* out) {
+    if (!s || !out) return PD_ERR_ARG;
+    DevState d;
+    CK(cudaMemcpyAsync(&d, s->st, sizeof(d), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    // (read without the error check, so that it also reports a failed sort)
+    out->faults = d.sort_fault;
+    out->relayouts = d.n_relayout;
+    out->bin_slots = d.tail_base;   // heavy bins with their slack, then the electron bins
+    out->live = d.n_live + d.n_e;
+    out->steps_since = d.since;
+    return PD_OK;
+}
+
+pd_status pd_get_bins(pd_sim* s, uint32_t* start, uint32_t* count, int64_t* nbins) {
+    if (!s || !nbins) return PD_ERR_ARG;
+    const size_t nb = (size_t)s->L.ncell * (size_t)s->L.nsp;
+    *nbins = (int64_t)nb;
+    if (!start && !count) return PD_OK;
+    if (!start || !count) return PD_ERR_ARG;
+    DevState d;
+    pd_status r = sync_check(s, &d);
+    if (r != PD_OK) return r;
+    CK(cudaMemcpyAsync(start, s->off, (nb + 1) * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(count, s->bcnt, nb * 4, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return PD_OK;
+}
+
 pd_status pd_get_particles(pd_sim* s, uint32_t* id, int32_t* run, uint8_t* sp, int32_t* iz, int32_t* ir, float* pz,
                            float* pr, float* vz, float* vr, float* vt) {
     if (!s) return PD_ERR_ARG;
@@ -1578,6 +1664,7 @@ pd_status pd_save(pd_sim* s, const char* path) {
     const void* arrays[7] = {s->A.key, s->A.pz, s->A.pr, s->A.vz, s->A.vr, s->A.vt, s->A.id};
     if ((r = dev_to_file(s, F, s->rs, (size_t)s->R * sizeof(RunState))) != PD_OK) return r;
     if ((r = dev_to_file(s, F, s->off, (size_t)h.n_off * 4)) != PD_OK) return r;
+    if ((r = dev_to_file(s, F, s->bcnt, (size_t)(h.n_off - 1) * 4)) != PD_OK) return r;
     if ((r = dev_to_file(s, F, s->rho_e, nodes * 8)) != PD_OK) return r;
     if ((r = dev_to_file(s, F, s->rho_h, nodes * 8)) != PD_OK) return r;
     if ((r = dev_to_file(s, F, s->E, nodes * 8)) != PD_OK) return r;
@@ -1620,14 +1707,22 @@ pd_status pd_load(pd_sim* s, const char* path) {
     void* arrays[7] = {s->A.key, s->A.pz, s->A.pr, s->A.vz, s->A.vr, s->A.vt, s->A.id};
     if ((r = file_to_dev(s, F, s->rs, (size_t)s->R * sizeof(RunState))) != PD_OK) return r;
     if ((r = file_to_dev(s, F, s->off, (size_t)h.n_off * 4)) != PD_OK) return r;
+    if ((r = file_to_dev(s, F, s->bcnt, (size_t)(h.n_off - 1) * 4)) != PD_OK) return r;
     if ((r = file_to_dev(s, F, s->rho_e, nodes * 8)) != PD_OK) return r;
     if ((r = file_to_dev(s, F, s->rho_h, nodes * 8)) != PD_OK) return r;
     if ((r = file_to_dev(s, F, s->E, nodes * 8)) != PD_OK) return r;
     if ((r = file_to_dev(s, F, s->phi, nodes * 8)) != PD_OK) return r;
     for (int a = 0; a < 7; ++a)
         if ((r = file_to_dev(s, F, arrays[a], n * 4)) != PD_OK) return r;
-    // slots past the saved ones are free
+    // slots past the saved ones are free; a checkpoint is taken between
+    // steps, when no bin has traffic, no mover is pending and no slot is a hole
     CK(cudaMemsetAsync(s->A.key + n, 0xFF, (size_t)(s->L.cap - n) * 4, s->stream));
+    const size_t nbp = (size_t)s->L.nbins_pad;
+    CK(cudaMemsetAsync(s->count, 0, nbp * 4, s->stream));
+    CK(cudaMemsetAsync(s->outc, 0, nbp * 4, s->stream));
+    CK(cudaMemsetAsync(s->act, 0, nbp * 4, s->stream));
+    CK(cudaMemsetAsync(s->net, 0, nbp * 4, s->stream));
+    CK(cudaMemsetAsync(s->mm, 0, (size_t)s->L.words_pad * 4, s->stream));
     std::memcpy(s->h_xs, xs, sizeof(xs));
     std::memcpy(s->eth, eth, sizeof(eth));
     std::memcpy(s->h_ytab, ytab, sizeof(ytab));

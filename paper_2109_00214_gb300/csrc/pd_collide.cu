@@ -375,7 +375,8 @@ __device__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uin
 // ascending id order gets the identity.
 template <int NT, uint32_t MAXN>
 __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__ ids, RankScratch S,
-                                                    const uint32_t* __restrict__ off, const uint32_t* __restrict__ q,
+                                                    const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+                                                    const uint32_t* __restrict__ q,
                                                     const uint32_t* nq, uint32_t max_q, uint32_t C) {
     constexpr int NWARPS = NT / 32;
     extern __shared__ uint32_t s_buf[];                 // four arrays of MAXN
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
         const uint32_t e = q[b];
         const uint32_t bin = (e & 7u) * C + (e >> 3);
-        const uint32_t slot0 = off[bin], n = off[bin + 1] - slot0;
+        const uint32_t slot0 = off[bin], n = cnt[bin];
         const uint32_t* base = ids + slot0;
         const bool in_smem = n <= MAXN;
         uint32_t* xk = in_smem ? s_buf : S.xk + slot0;
@@ -534,7 +535,7 @@ __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t r
 // EXT: any of the step-wise, heavy-pair or Coulomb extensions is on (the
 // plain variant counts the classes (e, Cu) and (e, Cu+) only)
 template <bool EXT>
-__global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off, const float* __restrict__ ck,
+__global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ cnt, const float* __restrict__ ck,
                                                uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active, uint32_t* mid,
                                                uint32_t* big, DevState* st, KParams P) {
     const uint32_t C = P.ncell;
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ off,
             // drawn only by the Coulomb pairs)
 #pragma unroll
             for (int sp = 0; sp < NSP; ++sp)
-                if ((sp < 5 || q3) && (sp < 6 || P.coulomb)) N[sp] = off[sp * C + c + 1] - off[sp * C + c];
+                if ((sp < 5 || q3) && (sp < 6 || P.coulomb)) N[sp] = cnt[sp * C + c];
             const uint32_t Nt[NECLS] = {N[SP_CU], N[SP_CUP], N[SP_CU2_SW], N[SP_CU2_DI], N[SP_CU3]};
             bool ecls = false;
             for (int k = 0; k < NECLS; ++k) ecls |= Nt[k] > 0;
@@ -1082,11 +1083,12 @@ __device__ uint32_t pairs_cross(Particles& A, const IdList& La, uint32_t baseA, 
 // the two (of the species itself in a class of one species).
 // look_ion[i]: the ion list's lookups over all classes (as k_ncand counts).
 __device__ __forceinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
-                             const uint32_t* __restrict__ off, uint32_t C, uint32_t c, uint32_t lc, uint32_t look_e,
+                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt, uint32_t C,
+                             uint32_t c, uint32_t lc, uint32_t look_e,
                              const uint32_t (&look_ion)[5], int nsp, int heavy_step, int id_top, int lane,
                              DevState* st, const CollConsts& cc, const double* __restrict__ cw, uint32_t cw_heavy) {
     const RunInfo* RI = cx.RI;
-    const uint32_t e_base = off[c], Ne = off[c + 1] - e_base;
+    const uint32_t e_base = off[c], Ne = cnt[c];
     const uint32_t row = RI->row_base + lc % (uint32_t)RI->nr;
     const double wv = cw[row];
     uint32_t Ni[5], ib[5];
@@ -1095,7 +1097,7 @@ __device__ __forceinline__ void coulomb_cell(Particles& A, CellCtx& cx, const Ra
         const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
         const bool has = SP_CUP + i < nsp;
         ib[i] = has ? off[b] : 0u;
-        Ni[i] = has ? off[b + 1] - ib[i] : 0u;
+        Ni[i] = has ? cnt[b] : 0u;
     }
     if (Ne > 0u) {
         IdList el;
@@ -1134,6 +1136,7 @@ __device__ __forceinline__ void coulomb_cell(Particles& A, CellCtx& cx, const Ra
 
 template <bool EXT>
 __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+                                                 const uint32_t* __restrict__ cnt,
                                                  const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
                                                  const uint32_t* __restrict__ cand_off,
                                                  const uint32_t* __restrict__ active, DevState* st, long long* rho_e,
@@ -1145,7 +1148,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
     uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
     const uint32_t C = P.ncell;
     const uint32_t n_heavy = st->n_heavy, n_light = st->n_light;
-    const uint32_t n_alive = off[nbins];
+    const uint32_t n_alive = (uint32_t)st->tail_base;   // spawn slots follow the bins
     // heavy cells first, taken one at a time from a shared cursor by the
     // first min(n_heavy, warps) warps; then the light cells, warp-strided
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1196,7 +1199,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             continue;
         }
         const uint32_t e_base = off[c];
-        const uint32_t Ne = off[c + 1] - e_base;
+        const uint32_t Ne = cnt[c];
         // lookups of each list over all classes (the rank-table decisions of
         // k_ncand use the same totals): the Coulomb pairs look up every
         // electron and every ion of a cell with electrons
@@ -1218,13 +1221,13 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             if (k >= NECLS && !cu_first) {
                 cu_first = true;
                 a_base = off[C + c];
-                Na = off[C + c + 1] - a_base;
+                Na = cnt[C + c];
                 load_ids(el, A.id, a_base, Na, look_cu, S, sbuf, lane, id_top);
             }
             const int ts = class_target(k);
             const uint32_t tb = (uint32_t)ts * C + c;
             const uint32_t t_base = off[tb];
-            const uint32_t Nt = off[tb + 1] - t_base;
+            const uint32_t Nt = cnt[tb];
             // the target list's lookups over every class that draws from it
             const uint32_t t_look = ts == SP_CU ? look_cu : (ts == SP_CUP ? look_ci : ncand) + (coul ? Nt : 0u);
             IdList tl;
@@ -1366,6 +1369,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
 // charged particles, grid-stride over the cells.  The lists' lookups are
 // counted as k_ncand counted them, so the rank-table choices agree.
 __global__ void __launch_bounds__(128, 3) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+                                                   const uint32_t* __restrict__ cnt,
                                                    const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
                                                    DevState* st, KParams P, CollConsts cc,
                                                    const double* __restrict__ cw) {
@@ -1376,13 +1380,13 @@ __global__ void __launch_bounds__(128, 3) k_coulomb(Particles A, RankScratch S, 
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = warp0; c < C; c += nwarps) {
-        const uint32_t Ne = off[c + 1] - off[c];
+        const uint32_t Ne = cnt[c];
         if (Ne == 0u && !P.heavy_step) continue;
         uint32_t Ni[5], nion = 0;
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
-            Ni[i] = SP_CUP + i < P.nsp ? off[b + 1] - off[b] : 0u;
+            Ni[i] = SP_CUP + i < P.nsp ? cnt[b] : 0u;
             nion += Ni[i];
         }
         if (Ne < 2u && nion == 0u) continue;         // nothing to pair
@@ -1403,7 +1407,7 @@ __global__ void __launch_bounds__(128, 3) k_coulomb(Particles A, RankScratch S, 
         for (int i = 0; i < 5; ++i) look_all[i] = look_ion[i] + Ni[i];
         const uint32_t idn = P.rs[r].id_next;
         const int id_top = idn > 1u ? 31 - __clz((int)(idn - 1u)) : 0;
-        coulomb_cell(A, cx, S, sbuf, off, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
+        coulomb_cell(A, cx, S, sbuf, off, cnt, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
                      P.cw_heavy);
         // every lane applied pairs: sum the warp's counts
         const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
@@ -1424,12 +1428,17 @@ __global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, con
     const uint32_t C = P.ncell;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long T = cand_off[C];
-        unsigned long long ns = (unsigned long long)off[nbins] + 2ull * T;
+        unsigned long long ns = st->tail_base + 2ull * T;
         if (ns > P.capacity) {
             set_error(st, ERR_CAPACITY);
             ns = P.capacity;
         }
+        // the next step's particles (in bins and in the spawn slots) within
+        // the configured capacity
+        if (st->n_live + st->n_e + 2ull * T > P.user_capacity) set_error(st, ERR_CAPACITY);
         st->n_slots = ns;
+        st->n_bigc = 0;
+        st->since += 1u;
         st->n_heavy = 0;
         st->n_light = 0;
         st->n_mid = 0;
@@ -1564,8 +1573,8 @@ constexpr size_t RT_MID_SMEM = (size_t)RANK_MID_MAX * 4 * sizeof(uint32_t);
 // ---------------------------------------------------------------------
 // Ion-impact sputtering (Sec. 2.3), after the push: each run's block takes
 // the impacts the push recorded for it, sorts them by the ion's id, and
-// appends their atoms after the slots in use (the sort that follows places
-// them), with ids from the run's next id in that order.  An atom leaves the
+// appends their atoms after the slots in use, as movers that the sort which
+// follows places, with ids from the run's next id in that order.  An atom leaves the
 // impact point on the electrode surface with an effusive flux at
 // sputter_T: Rayleigh normal and transverse speeds, uniform azimuth.
 // ---------------------------------------------------------------------
@@ -1573,7 +1582,7 @@ constexpr int SPUT_THREADS = 1024;
 constexpr uint32_t SPUT_MAX = 8192;              // impacts per run and step
 constexpr size_t SPUT_SMEM = SPUT_MAX * sizeof(unsigned long long);
 
-__global__ void __launch_bounds__(SPUT_THREADS) k_sputter(Particles A, DevState* st, KParams P,
+__global__ void __launch_bounds__(SPUT_THREADS) k_sputter(Particles M, uint32_t* mm, DevState* st, KParams P,
                                                           const float* __restrict__ ray, uint32_t* in_cnt) {
     extern __shared__ unsigned long long s_key[];    // ion id << 32 | record index
     __shared__ uint32_t s_cnt, s_el[2], s_wsum[SPUT_THREADS / 32];
@@ -1679,14 +1688,16 @@ __global__ void __launch_bounds__(SPUT_THREADS) k_sputter(Particles A, DevState*
             const float sv = P.sput_vth * rayleigh(ray, U2);
             float cp, sn;
             azimuth(sp, cp, sn, fb);
+            // a tail slot after those in use: the atom joins this step's sort as a mover
             const unsigned long long slot = s_base + off;
-            A.key[slot] = make_key(SP_CU, gcell);
-            A.pz[slot] = pz;
-            A.pr[slot] = rec.pr;
-            A.vz[slot] = el == 0u ? vn : -vn;
-            A.vr[slot] = sv * cp;
-            A.vt[slot] = sv * sn;
-            A.id[slot] = s_id0 + off;
+            M.key[slot] = make_key(SP_CU, gcell);
+            M.pz[slot] = pz;
+            M.pr[slot] = rec.pr;
+            M.vz[slot] = el == 0u ? vn : -vn;
+            M.vr[slot] = sv * cp;
+            M.vt[slot] = sv * sn;
+            M.id[slot] = s_id0 + off;
+            atomicOr(&mm[slot >> 5], 1u << (slot & 31u));
             atomicAdd(&in_cnt[(uint32_t)SP_CU * P.ncell + gcell], 1u);
         }
     }
@@ -1703,14 +1714,15 @@ cudaError_t collide_setup() {
         e = cudaFuncSetAttribute(k_sputter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SPUT_SMEM);
     return e;
 }
-void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
+void launch_ncand(const uint32_t* cnt, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
                   uint32_t* mid, uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s) {
     if (P.charge_max >= 3 || P.heavy_coll || P.coulomb)
-        k_ncand<true><<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
+        k_ncand<true><<<grid, 256, 0, s>>>(cnt, ck, nc, nc2, cand, active, mid, big, st, P);
     else
-        k_ncand<false><<<grid, 256, 0, s>>>(off, ck, nc, nc2, cand, active, mid, big, st, P);
+        k_ncand<false><<<grid, 256, 0, s>>>(cnt, ck, nc, nc2, cand, active, mid, big, st, P);
 }
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint32_t* cnt, const uint4* nc,
+                    const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
@@ -1718,25 +1730,25 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
     const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
                         reinterpret_cast<uint32_t*>(B.vz), B.id};
     k_rank_tables<RT_MID_THREADS, RANK_MID_MAX><<<sms * RT_MID_BLOCKS_PER_SM, RT_MID_THREADS, RT_MID_SMEM, s>>>(
-        A.id, S, off, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
+        A.id, S, off, cnt, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
     k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
-        A.id, S, off, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
+        A.id, S, off, cnt, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
     if (P.charge_max >= 3 || P.heavy_coll || P.coulomb)
-        k_collide<true><<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
+        k_collide<true><<<grid, 128, 0, s>>>(A, S, off, cnt, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
                                              cc, nbins);
     else
-        k_collide<false><<<grid, 128, 0, s>>>(A, S, off, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
+        k_collide<false><<<grid, 128, 0, s>>>(A, S, off, cnt, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
                                               cc, nbins);
     // one wave of resident blocks (three per SM), grid-stride over the cells
-    if (P.coulomb) k_coulomb<<<sms * 3, 128, 0, s>>>(A, S, off, nc, nc2, st, P, cc, cw);
+    if (P.coulomb) k_coulomb<<<sms * 3, 128, 0, s>>>(A, S, off, cnt, nc, nc2, st, P, cc, cw);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {
     k_finalize<<<1, 256, 0, s>>>(off, nbins, cand_off, st, P, circ, dt, circuit);
 }
-void launch_sputter(const Particles& A, DevState* st, const KParams& P, const float* ray, uint32_t* in_cnt,
-                    cudaStream_t s) {
-    k_sputter<<<P.nruns, SPUT_THREADS, SPUT_SMEM, s>>>(A, st, P, ray, in_cnt);
+void launch_sputter(const Particles& M, uint32_t* mm, DevState* st, const KParams& P, const float* ray,
+                    uint32_t* in_cnt, cudaStream_t s) {
+    k_sputter<<<P.nruns, SPUT_THREADS, SPUT_SMEM, s>>>(M, mm, st, P, ray, in_cnt);
 }
 
 void launch_inject(Particles A, const float2* E, DevState* st, const KParams& P, const InjectConsts* ic,

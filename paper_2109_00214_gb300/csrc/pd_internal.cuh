@@ -5,8 +5,14 @@
 //   pz, pr    f32 offset inside the cell, in [0, 1)
 //   vz, vr, vt f32 velocity (m/s)
 //   id   u32  particle id (ascending id = canonical order inside a cell)
-// 28 bytes per particle.  Two copies (A, B): the counting sort scatters A
-// into B in (species, cell) order each step and the two are swapped.
+// 28 bytes per particle.  Slots are grouped in bins, one per (species,
+// cell), bin = species * cells + cell.  Heavy bins come first: heavy bin b
+// owns slots [off[b], off[b+1]) and its live particles fill the first cnt[b]
+// of them; the rest is slack (DEAD keys).  The electron bins follow, packed
+// (rebuilt every step), from off[nbins] on; then the tail: particles created
+// since the last sort (injected, spawned, sputtered, loaded).  A second copy
+// (B) is scratch for the collisions and the target of a re-layout; a third
+// (M) holds this step's movers at their slots' indices.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -53,7 +59,24 @@ struct DevState {
     unsigned int n_mid, n_big;       // id lists queued for the two rank-table kernels this step
     unsigned int collide_next;       // next active cell for k_collide's warps
     unsigned int n_sput;             // ion impacts recorded by the push for sputtering
+    unsigned int relayout;           // a bin overflowed its slots this step: re-lay the bins out
+    unsigned int since;              // steps since the last re-layout
+    unsigned int n_bigc;             // long bins queued for the warp compaction this step
+    unsigned int n_relayout;         // new layouts of the bins so far
+    unsigned int sort_fault;         // which consistency check of the sort failed (bits), 0 if none
+    unsigned int pad2;
+    unsigned long long n_live;       // heavy particles in bins (after this step's insertions)
+    unsigned long long tail_base;    // first slot of the tail (after the electron bins)
+    unsigned long long e_base;       // first slot of the electron bins (after the heavy bins' slots)
+    unsigned long long e_from;       // the electron bins' first slot when this step's push ran
+    unsigned long long n_e;          // electrons in bins
+    unsigned long long sum_cnt;      // re-layout: particles over all bins, and the sums that size the
+    double sum_s1, sum_s2;           // slack horizon (random-walk and drift terms)
+    unsigned long long sp_cnt[NSP];  // re-layout: particles and bin traffic (movers in + out since
+    unsigned long long sp_act[NSP];  // the last layout) of each species
 };
+
+
 
 // One ion impact on an electrode that sputters n atoms (recorded by the push,
 // emitted by k_sputter in the order of the ions' ids).
@@ -130,8 +153,8 @@ struct KParams {
     SputRec* squeue;                 // this step's impacts, at most squeue_cap
     uint32_t squeue_cap;
     int field_on;                    // gather E in the push
-    int use_prev;                    // slots [0, off[nbins]) are sorted from the previous step
-    unsigned long long capacity;
+    unsigned long long capacity;     // physical slots of the particle arrays
+    unsigned long long user_capacity;  // particles (live and reserved for spawns) the configuration allows
     double masses[NSP];
     RunInfo run0;                    // runs[0] by value (the one run of a single simulation)
     const RunInfo* runs;             // [nruns]

@@ -25,21 +25,43 @@ struct InjectConsts {
 
 // push + deposit + mover bookkeeping (see pd_stream.cu)
 void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
-                 uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
-                 const KParams& P, int grid, cudaStream_t s);
-void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
-                     uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s);
-// per bin: dlt = new_off - old_off + movers before old_off (after both scans)
-void launch_bin_delta(const uint32_t* old_off, const uint32_t* new_off, const uint32_t* mv, const uint32_t* mvx,
-                      uint32_t* dlt, uint32_t nbins, int grid, cudaStream_t s);
-void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
-                    const uint32_t* stay, const uint32_t* dlt, uint32_t* in_cnt, const uint32_t* mv,
-                    const uint32_t* mvx, uint32_t nbins, DevState* st, const KParams& P, int grid, cudaStream_t s);
+                 uint32_t* in_cnt, uint32_t* mv, uint32_t* mm, const Particles& M, DevState* st, const KParams& P,
+                 int grid, cudaStream_t s);
+// the sort after the push (see pd_stream.cu)
+struct SortArgs {
+    Particles A, B;                  // the particles; B: scratch of a re-layout
+    Particles M;                     // movers, at their slots' indices
+    uint32_t *mv, *mm;               // vacated slots; slots with a mover record
+    uint32_t *off, *off2;            // bin starts (nbins_pad + 1 entries), the next layout / scratch
+    uint32_t *cnt, *out_cnt, *in_cnt;  // live count, movers out, movers in (cursor) per bin
+    uint32_t* cap;                   // re-layout: heavy bin capacities (scan input)
+    uint32_t* act;                   // movers in + out per heavy bin since the last layout
+    int* net;                        // movers in - out per heavy bin since the last layout
+    uint4* bigq;                     // long heavy bins with holes
+    uint32_t bigq_cap;
+    uint32_t* partial;               // scan partials
+    uint32_t nbins, nbins_pad, ncell_pad;
+    uint64_t slots;                  // physical slots of the particle arrays
+};
+// heavy bins: counts, holes closed (two launches)
+void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cudaStream_t s);
+// a new layout of the heavy bins when one overflowed (every kernel returns at
+// once otherwise; ten launches)
+void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid_bins, int grid_slots,
+                     cudaStream_t s);
+// the electron bins packed after the heavy bins, then every mover into its
+// bin (six launches)
+void launch_insert(const SortArgs& a, DevState* st, const KParams& P, int grid_dense, cudaStream_t s);
+// queue entries that always suffice for bins longer than the warp-compaction
+// threshold (they hold disjoint slots)
+inline uint32_t bigq_max(uint64_t slots) { return (uint32_t)(slots / 96 + 16); }
 void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevState* st, const KParams& P,
                     int grid, cudaStream_t s);
 // exclusive scan of n_padded (multiple of SCAN_TILE) u32; out has n_padded + 1
 // entries, out[n_padded] = total; partial needs n_padded / SCAN_TILE + 1 entries
-void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
+// (cond: when not null, the scan runs only if *cond is nonzero)
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s,
+                 const uint32_t* cond = nullptr);
 // the same over the population counts of the input words
 void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s);
 // diagnostics of one run
@@ -68,20 +90,23 @@ __host__ __device__ inline uint32_t rank_queue_max(uint64_t cap, uint32_t len) {
 // shared-memory attribute of the rank-table kernels (once per process and device)
 cudaError_t collide_setup();
 // nc: candidates of classes 0, 1, 5, 6; nc2: classes 2, 3, 4 (written with charge_max >= 3)
-void launch_ncand(const uint32_t* off, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
+void launch_ncand(const uint32_t* cnt, const float* ck, uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active,
                   uint32_t* mid, uint32_t* big, DevState* st, const KParams& P, int grid, cudaStream_t s);
-// B: the other particle buffer, used as scratch (free until the next scatter)
-// the two rank-table kernels, then k_collide (three launches)
-void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint4* nc, const uint4* nc2,
+// B: the other particle buffer, used as scratch (free outside a re-layout);
+// off / cnt: bin starts and live counts.  The two rank-table kernels, then
+// k_collide (three launches)
+void launch_collide(const Particles& A, const Particles& B, const uint32_t* off, const uint32_t* cnt, const uint4* nc,
+                    const uint4* nc2,
                     const uint32_t* cand_off, const uint32_t* active, const uint32_t* mid, const uint32_t* big,
 // cw: W dt_coll / V_cell per row (Coulomb pairs)
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
                     cudaStream_t s);
-// ion-impact sputtering after the push (one block per run); in_cnt: the
-// movers-into-bin counts of the sort
-void launch_sputter(const Particles& A, DevState* st, const KParams& P, const float* ray, uint32_t* in_cnt,
-                    cudaStream_t s);
+// ion-impact sputtering after the push (one block per run): the atoms go to
+// the mover records M (mask mm) of tail slots; in_cnt: the movers-into-bin
+// counts of the sort
+void launch_sputter(const Particles& M, uint32_t* mm, DevState* st, const KParams& P, const float* ray,
+                    uint32_t* in_cnt, cudaStream_t s);
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s);
 

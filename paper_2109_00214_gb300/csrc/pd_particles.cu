@@ -86,7 +86,9 @@ __device__ __forceinline__ uint4 scan_tf(uint4 v) {
 }
 
 template <bool POPC>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, uint32_t* partial) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ in, uint32_t* partial,
+                                                              const uint32_t* cond) {
+    if (cond && !*cond) return;
     const uint4* p = reinterpret_cast<const uint4*>(in + (size_t)blockIdx.x * SCAN_TILE) + threadIdx.x * 2;
     const uint4 a = scan_tf<POPC>(p[0]), b = scan_tf<POPC>(p[1]);
     uint32_t s = (a.x + a.y + a.z + a.w) + (b.x + b.y + b.z + b.w);
@@ -102,7 +104,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __
 }
 
 // single block: exclusive scan of nb block sums in place, total to partial[nb]
-__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partial, uint32_t nb) {
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partial, uint32_t nb, const uint32_t* cond) {
+    if (cond && !*cond) return;
     uint32_t carry = 0;
     for (uint32_t base = 0; base < nb; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
@@ -118,7 +121,8 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partial, uint3
 template <bool POPC>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* __restrict__ in,
                                                             const uint32_t* __restrict__ partial, uint32_t* out,
-                                                            uint32_t n, uint32_t nb) {
+                                                            uint32_t n, uint32_t nb, const uint32_t* cond) {
+    if (cond && !*cond) return;
     const size_t base = (size_t)blockIdx.x * SCAN_TILE + threadIdx.x * 8;
     const uint4* p = reinterpret_cast<const uint4*>(in + base);
     const uint4 a = scan_tf<POPC>(p[0]), b = scan_tf<POPC>(p[1]);
@@ -239,17 +243,18 @@ void launch_deposit(const Particles& A, long long* rho_e, long long* rho_h, DevS
                     int grid, cudaStream_t s) {
     k_deposit<<<grid, 256, 0, s>>>(A, rho_e, rho_h, st, P);
 }
-void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
+void launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s,
+                 const uint32_t* cond) {
     const uint32_t nb = n_padded / SCAN_TILE;
-    k_scan_reduce<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial);
-    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb);
-    k_scan_down<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
+    k_scan_reduce<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial, cond);
+    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb, cond);
+    k_scan_down<false><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb, cond);
 }
 void launch_scan_popc(const uint32_t* in, uint32_t* out, uint32_t* partial, uint32_t n_padded, cudaStream_t s) {
     const uint32_t nb = n_padded / SCAN_TILE;
-    k_scan_reduce<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial);
-    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb);
-    k_scan_down<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb);
+    k_scan_reduce<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, nullptr);
+    k_scan_partials<<<1, 1024, 0, s>>>(partial, nb, nullptr);
+    k_scan_down<true><<<nb, SCAN_THREADS, 0, s>>>(in, partial, out, n_padded, nb, nullptr);
 }
 void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, const float* pz, const float* pr,
                       int64_t n, int nz, int nr, uint32_t cell_base, uint32_t id0, uint32_t sp_max, uint32_t* key,

@@ -1,26 +1,34 @@
 // pd_stream.cu -- the particle-streaming kernels of the step.
 //
-//   k_push4     Newton push (Sec. 2.1) with the field gathered by the CIC
-//               weights of Eq. (10), r-z rotation or periodic wrap, absorbing
-//               walls, fused with the fixed-point CIC deposit of Eq. (9)-(10)
-//               and the bookkeeping of the cell sort.
-//   k_bincount  new bin counts = sorted counts - movers out + movers in.
-//   k_scatter4  the sort itself, A -> B in (species, cell) order.
+//   k_push4       Newton push (Sec. 2.1) with the field gathered by the CIC
+//                 weights of Eq. (10), r-z rotation or periodic wrap,
+//                 absorbing walls, fused with the fixed-point CIC deposit of
+//                 Eq. (9)-(10) and the bookkeeping of the cell sort.
+//   k_bins        per bin: new count, overflow check, closing of the holes
+//                 the push left (short bins; long ones are queued for
+//                 k_compact_big, a warp per bin).
+//   k_insert      movers into their new bins.
+//   k_relayout_*  a new slot layout of all bins when a bin ran out of slots.
 //
 // The sort exploits that a step moves few particles out of their (species,
-// cell) bin.  Slots [0, n_sorted) hold the previous step's sorted order.  A
-// particle there that stays in its bin ("stayer") goes to
-//     new_off[b] + (p - old_off[b]) - (movers in [old_off[b], p)),
-// computed from a bit mask of movers and its popcount prefix: no atomics, and
-// the stayers of a warp land on consecutive slots.  Movers, spawned and
-// injected particles (slots >= n_sorted) take slots after the stayers of
-// their new bin through one atomic cursor per bin.  With no previous order
-// (after a load) everything is a mover and this is a plain counting sort.
+// cell) bin.  Every bin owns a fixed range of slots with slack after its live
+// particles.  A particle that stays in its bin ("stayer") stays in its slot:
+// the push writes it back in place.  A particle that leaves its bin, or one in
+// the tail (created since the last sort), is a mover: the push copies it into
+// the mover buffer at its slot's index and marks the slot it vacates.  The
+// holes of each bin are then filled by the bin's last live particles, and the
+// movers take the slots after the live ones of their new bin, one atomic
+// cursor per bin.  The order inside a bin is not canonical (ascending id is
+// found where it matters, in the collisions).  When a bin's particles
+// outgrow its slots the bins get a new layout (a counting sort into the
+// second buffer, copied back), with slack sized from each bin's traffic since
+// the previous layout.  Every kernel of the re-layout returns at once on the
+// steps that need none, so the step's launch sequence is fixed (CUDA graphs).
 //
-// Each thread moves four consecutive particles with 128-bit loads issued
-// before use.  Sorted input means the four usually share a cell, so counts,
-// slot claims and deposited charge are merged over runs of equal keys inside
-// the thread (no warp-wide collectives on the common path), and the push
+// The push moves four consecutive particles per thread with 128-bit loads
+// issued before use.  Sorted input means the four usually share a cell, so
+// counts and deposited charge are merged over runs of equal keys inside the
+// thread (no warp-wide collectives on the common path), and the push
 // arithmetic is done for all four and selected, without divergent branches.
 // Slot arrays are padded to a multiple of four.  Compiled with -fmad=false:
 // every float operation is rounded on its own, in the order written.
@@ -90,18 +98,25 @@ __device__ __forceinline__ float spc_eh(const float (&a)[NSP], int sp) {
     return MULTI ? a[sp] : (sp == SP_E ? a[0] : a[1]);
 }
 
+// the key of a particle converted by the last collisions (not a free slot)
+__device__ __forceinline__ bool flagged(uint32_t k) { return k != DEAD && (k & KEY_FLAG); }
+
+// mv: slots vacated in their heavy bin this step (bit per slot); mm: slots
+// whose particle is in the mover buffer M; out_cnt / in_cnt: particles
+// leaving / entering each bin.  Every electron is a mover (the electron bins
+// are rebuilt each step), and so is every particle of the tail.
 template <bool RZ, bool FIELD, bool MULTI>
 __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles A, const float2* __restrict__ E, long long* rho_e,
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
-                                               uint32_t* mv, const uint32_t* __restrict__ old_off, uint32_t nbins,
-                                               DevState* st, KParams P) {
+                                               uint32_t* mv, uint32_t* mm, Particles M, DevState* st, KParams P) {
     __shared__ RunInfo s_runs[MULTI ? MAX_RUNS_SMEM : 1];
     if (MULTI) {
         for (int r = threadIdx.x; r < P.nruns; r += blockDim.x) s_runs[r] = P.runs[r];
         __syncthreads();
     }
     const uint32_t n = (uint32_t)st->n_slots;
-    const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
+    const uint32_t n_sorted = (uint32_t)st->e_base;      // slots of the heavy bins; the electron bins follow
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->e_from = n_sorted;
     const uint32_t nv = (n + 3u) >> 2;
     const uint32_t stride = gridDim.x * blockDim.x;
     const int geom = RZ ? 0 : 1;
@@ -111,19 +126,30 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
     float4* vz4 = reinterpret_cast<float4*>(A.vz);
     float4* vr4 = reinterpret_cast<float4*>(A.vr);
     float4* vt4 = reinterpret_cast<float4*>(A.vt);
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x % 32u < nv; g += stride) {
+    const uint4 dead4 = make_uint4(DEAD, DEAD, DEAD, DEAD);
+    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    uint4 Kn = g < nv ? key4[g] : dead4;     // the keys of the thread's next group, loaded one group ahead
+    for (; g - threadIdx.x % 32u < nv; g += stride) {
         const bool gv = g < nv;
-        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD);
+        const uint4 K = Kn;
+        Kn = g + stride < nv ? key4[g + stride] : dead4;
         float4 Z = make_float4(0, 0, 0, 0), R4 = Z, VZ = Z, VR = Z, VT = Z;
-        if (gv) {
-            K = key4[g];
+        // groups of four free slots (the bins' slack) read only their keys;
+        // heavies move on heavy steps only, so on the other steps a group of
+        // the heavy bins needs work only where the last collisions converted
+        // a particle (it changes bin)
+        const bool need = gv && (K.x & K.y & K.z & K.w) != DEAD &&
+                          (P.heavy_step || 4u * g + 4u > n_sorted || flagged(K.x) || flagged(K.y) || flagged(K.z) ||
+                           flagged(K.w));
+        if (!__any_sync(FULL_MASK, need)) continue;
+        if (need) {
             Z = pz4[g];
             R4 = pr4[g];
             VZ = vz4[g];
             VR = vr4[g];
             if (RZ) VT = vt4[g];
         }
-        uint32_t ko[4], key[4], newbin[4], oldbin[4];
+        uint32_t key[4], newbin[4], oldbin[4];
         float zo[4], ro[4], vzo[4], vro[4], vto[4];
         int sp_[4], iz_[4], ir_[4], wall_[4], run_[4];
         bool mover[4], inmv[4], dep[4], absd[4];
@@ -201,7 +227,6 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             const bool mvq = in_sorted && nb != oldbin[q];
             const bool inq = kp && (!in_sorted || nb != oldbin[q]);
             const bool mk = move && kp;
-            ko[q] = live ? k : lane_of(K, q);
             key[q] = k;
             newbin[q] = nb;
             mover[q] = mvq;
@@ -217,10 +242,10 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             iz_[q] = mk ? niz : iz;
             ir_[q] = (mk || absorbed) ? nir : ir;
             dep[q] = mk && charge_of(sp) != 0;
-            // 16: the particle moved (new position); 32: its key changed (new
-            // bin, absorbed, or converted in the last collisions)
+            // 16: the particle moved and keeps its slot (written back); a
+            // mover's slot is refilled by the sort, an absorbed one's too
             flags |= (absorbed ? 1u : 0u) | (mvq ? 2u : 0u) | (inq ? 4u : 0u) | (dep[q] ? 8u : 0u) |
-                     (mk ? 16u : 0u) | ((live && k != lane_of(K, q)) ? 32u : 0u);
+                     ((mk && !inq) ? 16u : 0u);
         }
         const uint32_t wflags = __reduce_or_sync(FULL_MASK, flags);
         if (RZ && (wflags & 1u)) {  // absorbed at an electrode or the outer wall: ledgers
@@ -271,9 +296,25 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             bool link[4];
             uint32_t len[4];
             runs4(inmv, newbin, link, len);
+            uint32_t nib = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 4; ++q) {
                 if (len[q]) atomicAdd(&in_cnt[newbin[q]], len[q]);
+                nib |= (inmv[q] ? 1u : 0u) << q;
+            }
+            if (nib) {
+                // the group's new state into the mover buffer (lanes that are
+                // not movers are never read); the Cartesian push does not
+                // load v_theta, which it leaves unchanged
+                reinterpret_cast<uint4*>(M.key)[g] = make_uint4(key[0], key[1], key[2], key[3]);
+                reinterpret_cast<float4*>(M.pz)[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
+                reinterpret_cast<float4*>(M.pr)[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
+                reinterpret_cast<float4*>(M.vz)[g] = make_float4(vzo[0], vzo[1], vzo[2], vzo[3]);
+                reinterpret_cast<float4*>(M.vr)[g] = make_float4(vro[0], vro[1], vro[2], vro[3]);
+                reinterpret_cast<float4*>(M.vt)[g] = RZ ? make_float4(vto[0], vto[1], vto[2], vto[3]) : vt4[g];
+                reinterpret_cast<uint4*>(M.id)[g] = reinterpret_cast<const uint4*>(A.id)[g];
+                atomicOr(&mm[g >> 3], nib << (4u * (g & 7u)));
+            }
         }
         if (wflags & 8u) {          // fixed-point CIC deposit, merged over runs of one key
             bool link[4];
@@ -347,8 +388,8 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 }
             }
         }
-        // write back only what changed: most keys do not change in a step
-        if (gv && (flags & 32u)) key4[g] = make_uint4(ko[0], ko[1], ko[2], ko[3]);
+        // write back the particles that moved and keep their slot (keys do not
+        // change there)
         if (gv && (flags & 16u)) {
             pz4[g] = make_float4(zo[0], zo[1], zo[2], zo[3]);
             pr4[g] = make_float4(ro[0], ro[1], ro[2], ro[3]);
@@ -361,180 +402,535 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
     }
 }
 
-// cnt[b] = (sorted count of b) - out[b] + in[b]; stay[b] = sorted - out; out := 0
-__global__ void __launch_bounds__(256) k_bincount(const uint32_t* __restrict__ old_off, uint32_t* out_cnt,
-                                                  const uint32_t* __restrict__ in_cnt, uint32_t* cnt, uint32_t* stay,
-                                                  uint32_t nbins_pad, int use_prev) {
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins_pad; b += gridDim.x * blockDim.x) {
-        const uint32_t sorted = use_prev ? old_off[b + 1] - old_off[b] : 0u;
-        const uint32_t s = sorted - out_cnt[b];
-        stay[b] = s;
-        cnt[b] = s + in_cnt[b];
-        out_cnt[b] = 0u;
+// ---------------------------------------------------------------------
+// sort: holes, insertions, re-layout
+// ---------------------------------------------------------------------
+// a failed consistency check of the sort: the sticky bounds error and, for
+// diagnosis, which check (a bit per check site)
+__device__ __forceinline__ void sort_fault(DevState* st, uint32_t where) {
+    set_error(st, ERR_BOUNDS);
+    atomicOr(&st->sort_fault, where);
+}
+
+__device__ __forceinline__ bool bit_of(const uint32_t* __restrict__ w, uint32_t i) { return (w[i >> 5] >> (i & 31u)) & 1u; }
+
+// first slot in [from, to) whose bit is `want` (to if none)
+__device__ __forceinline__ uint32_t next_bit(const uint32_t* __restrict__ w, uint32_t from, uint32_t to, bool want) {
+    while (from < to) {
+        uint32_t x = w[from >> 5];
+        if (!want) x = ~x;
+        x &= ~0u << (from & 31u);
+        if (x) return min(to, (from & ~31u) + (uint32_t)(__ffs((int)x) - 1));
+        from = (from & ~31u) + 32u;
     }
+    return to;
 }
 
-// movers strictly before slot p (p <= n_sorted)
-__device__ __forceinline__ uint32_t movers_before(const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
-                                                  uint32_t p) {
-    const uint32_t w = p >> 5;
-    return mvx[w] + (uint32_t)__popc(mv[w] & ((1u << (p & 31u)) - 1u));
+__device__ __forceinline__ void move_slot(Particles& A, uint32_t from, uint32_t to) {
+    A.key[to] = A.key[from];
+    A.pz[to] = A.pz[from];
+    A.pr[to] = A.pr[from];
+    A.vz[to] = A.vz[from];
+    A.vr[to] = A.vr[from];
+    A.vt[to] = A.vt[from];
+    A.id[to] = A.id[from];
 }
 
-// dlt[b] = new_off[b] - old_off[b] + (movers before old_off[b]): a stayer of
-// bin b at old slot i goes to dlt[b] + i - (movers before i)
-__global__ void __launch_bounds__(256) k_bin_delta(const uint32_t* __restrict__ old_off,
-                                                   const uint32_t* __restrict__ new_off,
-                                                   const uint32_t* __restrict__ mv, const uint32_t* __restrict__ mvx,
-                                                   uint32_t* dlt, uint32_t nbins) {
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
-        const uint32_t o = old_off[b];
-        dlt[b] = new_off[b] - o + movers_before(mv, mvx, o);
-    }
-}
+// Bins of up to this many particles close their holes in k_bins (one
+// thread); longer ones are queued for k_compact_big (one warp).
+constexpr uint32_t COMPACT_THREAD_MAX = 96;
 
-// Staging window of the scatter: a block's stayers land on a nearly
-// contiguous range of slots (its own particles plus the movers other blocks
-// insert between its bins); stayers within SCATTER_WIN slots of the block's
-// first one go through shared memory and are written out in slot order.
-constexpr int SCATTER_THREADS = 256;
-constexpr uint32_t SCATTER_WIN = 1536;
-
-__global__ void __launch_bounds__(SCATTER_THREADS, 4) k_scatter4(Particles A, Particles B,
-                                                              const uint32_t* __restrict__ old_off,
-                                                              const uint32_t* __restrict__ new_off,
-                                                              const uint32_t* __restrict__ stay,
-                                                              const uint32_t* __restrict__ dlt, uint32_t* in_cnt,
-                                                              const uint32_t* __restrict__ mv,
-                                                              const uint32_t* __restrict__ mvx, uint32_t nbins,
-                                                              DevState* st, KParams P) {
-    __shared__ uint32_t s_key[SCATTER_WIN], s_id[SCATTER_WIN];
-    __shared__ float s_pz[SCATTER_WIN], s_pr[SCATTER_WIN], s_vz[SCATTER_WIN], s_vr[SCATTER_WIN], s_vt[SCATTER_WIN];
-    __shared__ uint32_t s_base;
-    const uint32_t n = (uint32_t)st->n_slots;
-    const uint32_t n_sorted = P.use_prev ? old_off[nbins] : 0u;
-    const uint32_t nv = (n + 3u) >> 2;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = threadIdx.x; k < SCATTER_WIN; k += blockDim.x) s_key[k] = DEAD;
-    if (threadIdx.x == 0) s_base = 0xFFFFFFFFu;
-    __syncthreads();
-    for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < nv; g0 += stride) {
-        const uint32_t g = g0 + threadIdx.x;
-        const bool gv = g < nv;
-        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
-        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
-        if (gv) {
-            K = reinterpret_cast<const uint4*>(A.key)[g];
-            Z = reinterpret_cast<const float4*>(A.pz)[g];
-            R = reinterpret_cast<const float4*>(A.pr)[g];
-            VZ = reinterpret_cast<const float4*>(A.vz)[g];
-            VR = reinterpret_cast<const float4*>(A.vr)[g];
-            VT = reinterpret_cast<const float4*>(A.vt)[g];
-            ID = reinterpret_cast<const uint4*>(A.id)[g];
+// Per heavy bin (b0 = the first) with traffic this step: the count after the movers out (c0) and in
+// (cnt), the overflow check against the bin's slots, and the holes of
+// [start, start + c) closed by moving the live particles of
+// [start + c0, start + c) into them; that range then reads DEAD.
+__global__ void __launch_bounds__(256) k_bins(Particles A, const uint32_t* __restrict__ off, uint32_t* cnt,
+                                              uint32_t* out_cnt, const uint32_t* __restrict__ in_cnt,
+                                              const uint32_t* __restrict__ mv, uint32_t* act, int* net, uint4* bigq,
+                                              uint32_t bigq_cap, uint32_t b0, uint32_t nbins, DevState* st) {
+    long long dlive = 0;
+    for (uint32_t b = b0 + blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        const uint32_t o = out_cnt[b], in = in_cnt[b];
+        if ((o | in) == 0u) continue;
+        const uint32_t c = cnt[b];
+        if (o > c) {                                   // inconsistent bookkeeping: report, move nothing
+            sort_fault(st, 1u);
+            continue;
         }
-        const bool sorted_part = gv && 4u * g < n_sorted;
-        const uint32_t mw = sorted_part ? mv[g >> 3] : 0u;
-        const uint32_t mx = sorted_part ? mvx[g >> 3] : 0u;
-        uint32_t key[4], bin[4], slot[4];
-        bool live[4], mover[4], stays[4];
-        bool any_mover = false;
+        const uint32_t c0 = c - o, cf = c0 + in;
+        const uint32_t start = off[b];
+        cnt[b] = cf;
+        act[b] += o + in;
+        net[b] += (int)in - (int)o;
+        dlive += (long long)in - (long long)o;
+        if (cf > off[b + 1] - start) st->relayout = 1u;
+        if (o == 0u) continue;
+        out_cnt[b] = 0u;
+        if (c > COMPACT_THREAD_MAX) {
+            const uint32_t q = atomicAdd(&st->n_bigc, 1u);
+            if (q < bigq_cap) bigq[q] = make_uint4(b, start, c, c0);
+            else sort_fault(st, 2u);
+            continue;
+        }
+        const uint32_t end0 = start + c0, end = start + c;
+        uint32_t h = start, j = end0;
+        for (;;) {
+            h = next_bit(mv, h, end0, true);           // a hole below the new count
+            if (h >= end0) break;
+            j = next_bit(mv, j, end, false);           // a live particle above it
+            if (j >= end) {                            // cannot happen with consistent counts
+                sort_fault(st, 4u);
+                break;
+            }
+            move_slot(A, j, h);
+            ++h;
+            ++j;
+        }
+        for (uint32_t k = end0; k < end; ++k) A.key[k] = DEAD;
+    }
+    // the change of the live count, one atomic per block
+    __shared__ long long s_d[8];
+    const long long w = warp_sum_ll(dlive);
+    if ((threadIdx.x & 31u) == 0u) s_d[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_d[k];
+        if (t) atomicAdd(&st->n_live, (unsigned long long)t);
+    }
+}
+
+// The same closing of holes for the queued long bins, a warp per bin: each
+// round takes the holes of the next 32 slots below the new count and pairs
+// them, in order, with the next live particles above it.
+__global__ void __launch_bounds__(256) k_compact_big(Particles A, const uint32_t* __restrict__ mv,
+                                                     const uint4* __restrict__ bigq, uint32_t bigq_cap,
+                                                     DevState* st) {
+    __shared__ uint32_t s_h[8][32];
+    const int lane = threadIdx.x & 31;
+    uint32_t* sh = s_h[threadIdx.x >> 5];
+    const uint32_t nq = min(st->n_bigc, bigq_cap);
+    const uint32_t lt = (1u << lane) - 1u;
+    for (uint32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += (gridDim.x * blockDim.x) >> 5) {
+        const uint4 e = bigq[q];
+        const uint32_t start = e.y, end = start + e.z, end0 = start + e.w;
+        uint32_t hc = start, lc = end0;
+        bool bad = false;
+        while (hc < end0 && !bad) {
+            const uint32_t sh_slot = hc + (uint32_t)lane;
+            const bool hole = sh_slot < end0 && bit_of(mv, sh_slot);
+            const uint32_t Hm = __ballot_sync(FULL_MASK, hole);
+            hc += 32u;
+            const uint32_t nh = (uint32_t)__popc(Hm);
+            if (nh == 0u) continue;
+            if (hole) sh[__popc(Hm & lt)] = sh_slot;
+            __syncwarp();
+            uint32_t got = 0;
+            while (got < nh) {
+                if (lc >= end) {                       // fewer live particles than holes: inconsistent counts
+                    bad = true;
+                    break;
+                }
+                const uint32_t sl = lc + (uint32_t)lane;
+                const bool live = sl < end && !bit_of(mv, sl);
+                const uint32_t Lm = __ballot_sync(FULL_MASK, live);
+                const uint32_t nl = (uint32_t)__popc(Lm);
+                const uint32_t take = min(nl, nh - got);
+                const uint32_t lr = (uint32_t)__popc(Lm & lt);
+                if (live && lr < take) move_slot(A, sl, sh[got + lr]);
+                if (take == nl) {
+                    lc += 32u;
+                } else {
+                    // past the take-th live slot of this chunk
+                    uint32_t m = Lm;
+                    for (uint32_t k = 1; k < take; ++k) m &= m - 1u;
+                    lc += (uint32_t)__ffs((int)m);
+                }
+                got += take;
+            }
+            __syncwarp();
+        }
+        __syncwarp();
+        if (bad) {
+            if (lane == 0) sort_fault(st, 8u);
+            continue;
+        }
+        for (uint32_t k = end0 + (uint32_t)lane; k < end; k += 32u) A.key[k] = DEAD;
+    }
+}
+
+// mover record i of M into slot s of D
+__device__ __forceinline__ void put(Particles& D, uint32_t s, const Particles& M, uint32_t i) {
+    D.key[s] = M.key[i];
+    D.pz[s] = M.pz[i];
+    D.pr[s] = M.pr[i];
+    D.vz[s] = M.vz[i];
+    D.vr[s] = M.vr[i];
+    D.vt[s] = M.vt[i];
+    D.id[s] = M.id[i];
+}
+
+// bin of a mover record's key (nbins if the key is not a particle's)
+__device__ __forceinline__ uint32_t mover_bin(uint32_t k, uint32_t ncell, uint32_t nbins) {
+    if (k == DEAD || key_cell(k) >= ncell) return nbins;
+    const uint32_t b = key_species(k) * ncell + key_cell(k);
+    return b < nbins ? b : nbins;
+}
+
+// The sparse movers of 128 slots (one uint4 of the mask) into bins laid out
+// by `off`, after the live ones (cnt: the count after the insertions,
+// in_cnt: the bin's cursor, back to zero when all its movers are in).
+// heavy_only: electrons are left in the mask for the electron pass.
+__device__ __forceinline__ void insert128(Particles& D, const Particles& M, uint32_t* mm, uint32_t g,
+                                          const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+                                          uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, bool heavy_only,
+                                          DevState* st) {
+    const uint4 w = reinterpret_cast<uint4*>(mm)[g];
+    if ((w.x | w.y | w.z | w.w) == 0u) return;
+    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+    uint32_t keep[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uint32_t bits = ws[k];
+        while (bits) {
+            const uint32_t bit = (uint32_t)(__ffs((int)bits) - 1);
+            bits &= bits - 1u;
+            const uint32_t i = 128u * g + 32u * (uint32_t)k + bit;
+            const uint32_t key = M.key[i];
+            if (heavy_only && key != DEAD && key_species(key) == SP_E) {
+                keep[k] |= 1u << bit;
+                continue;
+            }
+            const uint32_t bin = mover_bin(key, ncell, nbins);
+            if (bin >= nbins) {
+                sort_fault(st, 128u);
+                continue;
+            }
+            const uint32_t left = atomicSub(&in_cnt[bin], 1u);
+            const uint32_t s = off[bin] + cnt[bin] - left;
+            if (left == 0u || s >= off[bin] + cnt[bin]) {   // inconsistent bookkeeping: report, never write out of range
+                sort_fault(st, 16u);
+                continue;
+            }
+            put(D, s, M, i);
+        }
+    }
+    reinterpret_cast<uint4*>(mm)[g] = make_uint4(keep[0], keep[1], keep[2], keep[3]);
+}
+
+// heavy movers of the heavy bins' slots [0, e_from) (sparse: a thread per 128 slots)
+__global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32_t* mm,
+                                                const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
+                                                uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, DevState* st) {
+    const uint32_t ng = (uint32_t)((st->e_from + 127ull) >> 7);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        insert128(A, M, mm, g, off, cnt, in_cnt, ncell, nbins, false, st);
+}
+
+// The movers of the electron bins and the tail, [e_from, n_slots) (dense:
+// every electron moves): a thread per four slots, one atomic per bin and warp.
+__global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
+                                                      const uint32_t* __restrict__ off,
+                                                      const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
+                                                      uint32_t ncell, uint32_t nbins, DevState* st) {
+    const uint32_t g0 = (uint32_t)(st->e_from >> 2), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g - lane < g1; g += gridDim.x * blockDim.x) {
+        const uint32_t nib = g < g1 ? (mm[g >> 3] >> (4u * (g & 7u))) & 15u : 0u;
+        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD);
+        if (nib) K = reinterpret_cast<const uint4*>(M.key)[g];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t i = 4u * g + (uint32_t)q;
-            key[q] = (gv && i < n) ? lane_of(K, q) : DEAD;
-            live[q] = key[q] != DEAD;
-            bin[q] = live[q] ? key_species(key[q]) * P.ncell + key_cell(key[q]) : 0u;
-            const bool stayer = live[q] && i < n_sorted && !((mw >> (i & 31u)) & 1u);
-            mover[q] = live[q] && !stayer;
-            stays[q] = stayer;
-            any_mover |= mover[q];
-            slot[q] = 0;
-            if (stayer) {
-                // slot = new_off - old_off + (movers before old_off) + i - (movers before i), the
-                // bin's part precomputed in dlt
-                const uint32_t before = mx + (uint32_t)__popc(mw & ((1u << (i & 31u)) - 1u));
-                slot[q] = dlt[bin[q]] + i - before;
-
-            }
-        }
-        if (any_mover) {            // claim slots after the stayers, one atomic per run of one bin
-            bool link[4];
-            uint32_t len[4];
-            runs4(mover, bin, link, len);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (len[q]) {
-                    const uint32_t old = atomicSub(&in_cnt[bin[q]], len[q]);
-                    if (old < len[q]) set_error(st, ERR_BOUNDS);      // more movers than counted
-                    slot[q] = new_off[bin[q]] + stay[bin[q]] + old - len[q];
-                } else if (link[q]) {
-                    slot[q] = (q > 0 ? slot[q > 0 ? q - 1 : 0] : 0u) + 1u;
-                }
-            }
-        }
-        // the block's first stayer slot anchors the staging window
-        uint32_t my_min = 0xFFFFFFFFu;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (stays[q] && slot[q] < my_min) my_min = slot[q];
-        my_min = __reduce_min_sync(FULL_MASK, my_min);
-        if ((threadIdx.x & 31) == 0 && my_min != 0xFFFFFFFFu) atomicMin(&s_base, my_min);
-        __syncthreads();
-        const uint32_t base = s_base;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!live[q]) continue;
-            if (slot[q] >= n) {     // inconsistent bookkeeping: report, never write out of range
-                set_error(st, ERR_BOUNDS);
+            const bool on = ((nib >> q) & 1u) && i >= st->e_from;
+            const uint32_t bin = on ? mover_bin(lane_of(K, q), ncell, nbins) : nbins;
+            if (on && bin >= nbins) sort_fault(st, 128u);
+            const bool ok = on && bin < nbins;
+            // one atomic per bin among the warp's lanes
+            const unsigned peers = __match_any_sync(FULL_MASK, ok ? bin : 0xFFFFFFFFu);
+            const uint32_t leader = (uint32_t)(__ffs((int)peers) - 1);
+            uint32_t left = 0;
+            if (ok && lane == leader) left = atomicSub(&in_cnt[bin], (uint32_t)__popc(peers));
+            left = __shfl_sync(FULL_MASK, left, (int)leader);
+            if (!ok) continue;
+            const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            const uint32_t s = off[bin] + cnt[bin] - left + rank;
+            if (left < (uint32_t)__popc(peers) || s >= off[bin] + cnt[bin]) {
+                sort_fault(st, 256u);
                 continue;
             }
-            const uint32_t s = slot[q];
-            const uint32_t w = s - base;
-            if (stays[q] && w < SCATTER_WIN) {
-                s_key[w] = key[q];
-                s_pz[w] = lane_of(Z, q);
-                s_pr[w] = lane_of(R, q);
-                s_vz[w] = lane_of(VZ, q);
-                s_vr[w] = lane_of(VR, q);
-                s_vt[w] = lane_of(VT, q);
-                s_id[w] = lane_of(ID, q);
-            } else {
-                B.key[s] = key[q];
-                B.pz[s] = lane_of(Z, q);
-                B.pr[s] = lane_of(R, q);
-                B.vz[s] = lane_of(VZ, q);
-                B.vr[s] = lane_of(VR, q);
-                B.vt[s] = lane_of(VT, q);
-                B.id[s] = lane_of(ID, q);
-            }
+            put(A, s, M, i);
         }
-        __syncthreads();
-        // write the window out in slot order: consecutive threads, consecutive slots
-        if (base != 0xFFFFFFFFu) {
-            for (uint32_t e = threadIdx.x; e < SCATTER_WIN; e += blockDim.x) {
-                const uint32_t k = s_key[e];
-                if (k == DEAD) continue;
-                const uint32_t s = base + e;
-                B.key[s] = k;
-                B.pz[s] = s_pz[e];
-                B.pr[s] = s_pr[e];
-                B.vz[s] = s_vz[e];
-                B.vr[s] = s_vr[e];
-                B.vt[s] = s_vt[e];
-                B.id[s] = s_id[e];
-                s_key[e] = DEAD;
-            }
-        }
-        if (threadIdx.x == 0) s_base = 0xFFFFFFFFu;
-        __syncthreads();
     }
 }
 
+// The electron bins, packed after the heavy bins: count = the electrons
+// moving in (every electron), start = e_base + exclusive prefix of the counts
+// (scanned into pre[]); the tail starts after them.
+__global__ void __launch_bounds__(256) k_ebins(uint32_t* off, uint32_t* cnt, const uint32_t* __restrict__ in_cnt,
+                                               const uint32_t* __restrict__ pre, uint32_t ncell, DevState* st) {
+    const uint32_t eb = (uint32_t)st->e_base;
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        off[c] = eb + pre[c];
+        cnt[c] = in_cnt[c];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->n_e = pre[ncell];
+        st->tail_base = (unsigned long long)eb + pre[ncell];
+    }
+}
+
+// ---- re-layout (only on steps where a bin overflowed) ----------------
+// Slack of a bin: room for a random walk of its movers in and out and for
+// its drift over H steps, SLACK_SIGMAS standard deviations (a layout holds
+// about a million bins):
+//     slack = 1 + ceil(SLACK_SIGMAS sqrt(lambda H) + drift H).
+// lambda, a bin's traffic per step, is the larger of its own since the
+// previous layout and its species' traffic per particle times the larger of
+// its count and the species' mean count per bin (a short interval sees no
+// traffic in many bins that do have it, and particles flow into a bin from
+// its neighbours, empty or not).  H is the largest horizon up to
+// SLACK_HORIZON_MAX steps whose slack fits in the slots beyond the configured
+// capacity, so that the layout lasts about H steps.  Without history (the
+// first layout) the slack is a sixteenth of the count and two.
+constexpr float SLACK_HORIZON_MAX = 100.0f;
+constexpr float SLACK_SIGMAS = 5.3f;
+
+// per species: particles and traffic over the bins
+__global__ void __launch_bounds__(256) k_relayout_stats(const uint32_t* __restrict__ cnt,
+                                                        const uint32_t* __restrict__ act, uint32_t nbins,
+                                                        uint32_t ncell, int nsp, DevState* st) {
+    if (!st->relayout) return;
+    unsigned long long c_[NSP], a_[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) c_[k] = a_[k] = 0ull;
+    for (uint32_t b = ncell + blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        const uint32_t sp = b / ncell, c = cnt[b], a = act[b];
+#pragma unroll
+        for (int k = 0; k < NSP; ++k) {
+            c_[k] += sp == (uint32_t)k ? c : 0u;
+            a_[k] += sp == (uint32_t)k ? a : 0u;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        if (k >= nsp) break;
+        const unsigned long long wc = warp_sum_ull(c_[k]), wa = warp_sum_ull(a_[k]);
+        if ((threadIdx.x & 31u) == 0u) {
+            if (wc) atomicAdd(&st->sp_cnt[k], wc);
+            if (wa) atomicAdd(&st->sp_act[k], wa);
+        }
+    }
+}
+
+// a bin's traffic per step (lambda) and drift per step
+__device__ __forceinline__ void bin_traffic(uint32_t b, uint32_t c, uint32_t a, int nt, uint32_t since, uint32_t ncell,
+                                            const float* s_rate, const float* s_mean, float& lam, float& drift) {
+    const uint32_t sp = b / ncell;
+    const float own = (float)a / (float)since;
+    lam = fmaxf(own, s_rate[sp] * fmaxf((float)c, s_mean[sp]));
+    drift = fmaxf((float)nt, 0.0f) / (float)since;
+}
+
+__device__ __forceinline__ void species_rates(const DevState* st, uint32_t since, uint32_t ncell, float* s_rate,
+                                              float* s_mean) {
+    if (threadIdx.x < NSP) {
+        const unsigned long long c = st->sp_cnt[threadIdx.x];
+        s_rate[threadIdx.x] = (since > 0u && c > 0ull)
+                                  ? (float)((double)st->sp_act[threadIdx.x] / ((double)c * (double)since))
+                                  : 0.0f;
+        s_mean[threadIdx.x] = (float)((double)c / (double)ncell);
+    }
+    __syncthreads();
+}
+
+// sums over the heavy bins of the count, of SLACK_SIGMAS sqrt(lambda) and of the drift
+__global__ void __launch_bounds__(256) k_relayout_want(const uint32_t* __restrict__ cnt,
+                                                       const uint32_t* __restrict__ act, const int* __restrict__ net,
+                                                       uint32_t nbins, uint32_t ncell, DevState* st) {
+    if (!st->relayout) return;
+    const uint32_t since = st->since;
+    __shared__ float s_rate[NSP], s_mean[NSP];
+    species_rates(st, since, ncell, s_rate, s_mean);
+    unsigned long long sc = 0;
+    double s1 = 0.0, s2 = 0.0;
+    for (uint32_t b = ncell + blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[b];
+        sc += c;
+        if (since == 0u) continue;
+        float lam, drift;
+        bin_traffic(b, c, act[b], net[b], since, ncell, s_rate, s_mean, lam, drift);
+        s1 += (double)(SLACK_SIGMAS * sqrtf(lam));
+        s2 += (double)drift;
+    }
+    __shared__ unsigned long long s_c[8];
+    __shared__ double s_1[8], s_2[8];
+    sc = warp_sum_ull(sc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_xor_sync(FULL_MASK, s1, o);
+        s2 += __shfl_xor_sync(FULL_MASK, s2, o);
+    }
+    if ((threadIdx.x & 31u) == 0u) {
+        s_c[threadIdx.x >> 5] = sc;
+        s_1[threadIdx.x >> 5] = s1;
+        s_2[threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long tc = 0;
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            tc += s_c[k];
+            t1 += s_1[k];
+            t2 += s_2[k];
+        }
+        atomicAdd(&st->sum_cnt, tc);
+        atomicAdd(&st->sum_s1, t1);
+        atomicAdd(&st->sum_s2, t2);
+    }
+}
+
+// heavy bin capacities: count plus slack over the horizon that fits the
+// slots beyond the configured capacity (the electron bins get none: they are
+// packed after the heavy bins every step); history cleared
+__global__ void __launch_bounds__(256) k_relayout_caps(const uint32_t* __restrict__ cnt, uint32_t* cap,
+                                                       uint32_t* act, int* net, uint32_t nbins, uint32_t nbins_pad,
+                                                       uint32_t ncell, DevState* st, KParams P) {
+    if (!st->relayout) return;
+    const uint32_t since = st->since;
+    __shared__ float s_rate[NSP], s_mean[NSP];
+    species_rates(st, since, ncell, s_rate, s_mean);
+    // room for the slack: the slots beyond the capacity (or beyond the
+    // particles, if more), less two slots per bin (the one added and the
+    // rounding up)
+    const unsigned long long used = max(st->sum_cnt + st->n_e + 1024ull, P.user_capacity) + 2ull * nbins;
+    const double room = P.capacity > used ? (double)(P.capacity - used) : 0.0;
+    // largest H <= SLACK_HORIZON_MAX with s1 sqrt(H) + s2 H <= room
+    const double s1 = st->sum_s1, s2 = st->sum_s2;
+    double x;
+    if (s2 > 0.0) x = (-s1 + sqrt(s1 * s1 + 4.0 * s2 * room)) / (2.0 * s2);
+    else x = s1 > 0.0 ? room / s1 : 1e30;
+    const float H = (float)fmin((double)SLACK_HORIZON_MAX, x * x), sqH = sqrtf(H);
+    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins_pad; b += gridDim.x * blockDim.x) {
+        if (b >= nbins || b < ncell) {
+            cap[b] = 0u;
+            continue;
+        }
+        const uint32_t c = cnt[b];
+        uint32_t w;
+        if (since == 0u) {
+            w = 2u + (c >> 4);
+        } else {
+            float lam, drift;
+            bin_traffic(b, c, act[b], net[b], since, ncell, s_rate, s_mean, lam, drift);
+            w = 1u + (uint32_t)ceilf(SLACK_SIGMAS * sqrtf(lam) * sqH + drift * H);
+        }
+        cap[b] = c + w;
+        act[b] = 0u;
+        net[b] = 0;
+    }
+}
+
+// B's keys over the new bins: DEAD (slack slots stay so)
+__global__ void __launch_bounds__(256) k_relayout_clear(uint32_t* key, const uint32_t* __restrict__ off2,
+                                                        uint32_t nbins, DevState* st) {
+    if (!st->relayout) return;
+    const uint32_t nv = (off2[nbins] + 3u) >> 2;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+        reinterpret_cast<uint4*>(key)[v] = make_uint4(DEAD, DEAD, DEAD, DEAD);
+}
+
+// B := the heavy particles in the new layout off2: the live particles of
+// each heavy bin (its first cnt - in slots after the closing of holes) keep
+// their order, the heavy movers follow them.  Clears the heavy movers' bits
+// of the mover mask (the electrons are inserted after the electron bins are
+// laid out).
+__global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles B, Particles M,
+                                                          uint32_t* mm, const uint32_t* __restrict__ off,
+                                                          const uint32_t* __restrict__ off2,
+                                                          const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
+                                                          uint32_t nbins, DevState* st, KParams P) {
+    if (!st->relayout) return;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t tb = (uint32_t)st->e_from, nv = (tb + 3u) >> 2;
+    for (uint32_t v = tid; v < nv; v += stride) {
+        const uint4 K = reinterpret_cast<const uint4*>(A.key)[v];
+        if ((K.x & K.y & K.z & K.w) == DEAD) continue;
+        const float4 Z = reinterpret_cast<const float4*>(A.pz)[v], R = reinterpret_cast<const float4*>(A.pr)[v];
+        const float4 VZ = reinterpret_cast<const float4*>(A.vz)[v], VR = reinterpret_cast<const float4*>(A.vr)[v];
+        const float4 VT = reinterpret_cast<const float4*>(A.vt)[v];
+        const uint4 ID = reinterpret_cast<const uint4*>(A.id)[v];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            // (the last group may reach into the electron bins: they are movers)
+            const uint32_t k = lane_of(K, q), i = 4u * v + (uint32_t)q;
+            if (k == DEAD || i >= tb) continue;
+            const uint32_t b = key_species(k) * P.ncell + key_cell(k);
+            if (key_cell(k) >= P.ncell || b >= nbins || i < off[b] || i - off[b] >= cnt[b]) {
+                sort_fault(st, 64u);             // not a particle of its bin: never write out of range
+                continue;
+            }
+            const uint32_t s = off2[b] + (i - off[b]);
+            B.key[s] = k;
+            B.pz[s] = lane_of(Z, q);
+            B.pr[s] = lane_of(R, q);
+            B.vz[s] = lane_of(VZ, q);
+            B.vr[s] = lane_of(VR, q);
+            B.vt[s] = lane_of(VT, q);
+            B.id[s] = lane_of(ID, q);
+        }
+    }
+    const uint32_t ng = (uint32_t)((st->n_slots + 127ull) >> 7);
+    for (uint32_t g = tid; g < ng; g += stride) insert128(B, M, mm, g, off2, cnt, in_cnt, P.ncell, nbins, true, st);
+}
+
+// A := B over the new heavy bins (groups of four slack slots copy only
+// their keys), off := off2; the electron bins start after them
+__global__ void __launch_bounds__(256) k_relayout_copy(Particles A, Particles B, uint32_t* off,
+                                                       const uint32_t* __restrict__ off2, uint32_t nbins,
+                                                       uint32_t nbins_pad, DevState* st) {
+    if (!st->relayout) return;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t end = off2[nbins], nv = (end + 3u) >> 2;
+    for (uint32_t v = tid; v < nv; v += stride) {
+        uint4 K = reinterpret_cast<const uint4*>(B.key)[v];
+        if (4u * v + 4u > end) {       // the last group: slots past the bins read DEAD
+            if (4u * v + 1u > end) K.y = DEAD;
+            if (4u * v + 2u > end) K.z = DEAD;
+            if (4u * v + 3u > end) K.w = DEAD;
+        }
+        reinterpret_cast<uint4*>(A.key)[v] = K;
+        if ((K.x & K.y & K.z & K.w) == DEAD) continue;
+        reinterpret_cast<float4*>(A.pz)[v] = reinterpret_cast<const float4*>(B.pz)[v];
+        reinterpret_cast<float4*>(A.pr)[v] = reinterpret_cast<const float4*>(B.pr)[v];
+        reinterpret_cast<float4*>(A.vz)[v] = reinterpret_cast<const float4*>(B.vz)[v];
+        reinterpret_cast<float4*>(A.vr)[v] = reinterpret_cast<const float4*>(B.vr)[v];
+        reinterpret_cast<float4*>(A.vt)[v] = reinterpret_cast<const float4*>(B.vt)[v];
+        reinterpret_cast<uint4*>(A.id)[v] = reinterpret_cast<const uint4*>(B.id)[v];
+    }
+    for (uint32_t b = tid; b <= nbins_pad; b += stride) off[b] = off2[b];
+}
+
+// after the copy: the re-layout is done
+__global__ void k_relayout_done(const uint32_t* __restrict__ off, uint32_t nbins, DevState* st) {
+    if (!st->relayout) return;
+    st->e_base = off[nbins];
+    st->relayout = 0u;
+    st->since = 0u;
+    st->n_relayout += 1u;
+    st->sum_cnt = 0ull;
+    st->sum_s1 = st->sum_s2 = 0.0;
+    for (int k = 0; k < NSP; ++k) st->sp_cnt[k] = st->sp_act[k] = 0ull;
+}
+
 void launch_push(const Particles& A, const float2* E, long long* rho_e, long long* rho_h, uint32_t* out_cnt,
-                 uint32_t* in_cnt, uint32_t* mv, const uint32_t* old_off, uint32_t nbins, DevState* st,
-                 const KParams& P, int grid, cudaStream_t s) {
+                 uint32_t* in_cnt, uint32_t* mv, uint32_t* mm, const Particles& M, DevState* st, const KParams& P,
+                 int grid, cudaStream_t s) {
     const bool rz = P.geom == 0, field = P.field_on != 0;
-#define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, old_off, nbins, st, P
+#define PD_PUSH_ARGS A, E, rho_e, rho_h, out_cnt, in_cnt, mv, mm, M, st, P
     if (P.nruns > 1) {
         if (rz && field) k_push4<true, true, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
         else if (rz) k_push4<true, false, true><<<grid, 256, 0, s>>>(PD_PUSH_ARGS);
@@ -549,20 +945,37 @@ void launch_push(const Particles& A, const float2* E, long long* rho_e, long lon
 #undef PD_PUSH_ARGS
 }
 
-void launch_bincount(const uint32_t* old_off, uint32_t* out_cnt, const uint32_t* in_cnt, uint32_t* cnt,
-                     uint32_t* stay, uint32_t nbins_pad, int use_prev, int grid, cudaStream_t s) {
-    k_bincount<<<grid, 256, 0, s>>>(old_off, out_cnt, in_cnt, cnt, stay, nbins_pad, use_prev);
+void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cudaStream_t s) {
+    // one thread per heavy bin: the work of a thread is a chain of dependent
+    // loads, which many threads in flight hide
+    const uint32_t gb = (a.nbins - P.ncell + 255u) / 256u;
+    k_bins<<<gb, 256, 0, s>>>(a.A, a.off, a.cnt, a.out_cnt, a.in_cnt, a.mv, a.act, a.net, a.bigq, a.bigq_cap, P.ncell,
+                              a.nbins, st);
+    k_compact_big<<<sms * 4, 256, 0, s>>>(a.A, a.mv, a.bigq, a.bigq_cap, st);
 }
 
-void launch_bin_delta(const uint32_t* old_off, const uint32_t* new_off, const uint32_t* mv, const uint32_t* mvx,
-                      uint32_t* dlt, uint32_t nbins, int grid, cudaStream_t s) {
-    k_bin_delta<<<grid, 256, 0, s>>>(old_off, new_off, mv, mvx, dlt, nbins);
+void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid_bins, int grid_slots,
+                     cudaStream_t s) {
+    // each kernel returns at once unless a bin overflowed
+    k_relayout_stats<<<grid_bins, 256, 0, s>>>(a.cnt, a.act, a.nbins, P.ncell, P.nsp, st);
+    k_relayout_want<<<grid_bins, 256, 0, s>>>(a.cnt, a.act, a.net, a.nbins, P.ncell, st);
+    k_relayout_caps<<<grid_bins, 256, 0, s>>>(a.cnt, a.cap, a.act, a.net, a.nbins, a.nbins_pad, P.ncell, st, P);
+    launch_scan(a.cap, a.off2, a.partial, a.nbins_pad, s, &st->relayout);
+    k_relayout_clear<<<grid_slots, 256, 0, s>>>(a.B.key, a.off2, a.nbins, st);
+    k_relayout_scatter<<<grid_slots, 256, 0, s>>>(a.A, a.B, a.M, a.mm, a.off, a.off2, a.cnt, a.in_cnt, a.nbins, st,
+                                                  P);
+    k_relayout_copy<<<grid_slots, 256, 0, s>>>(a.A, a.B, a.off, a.off2, a.nbins, a.nbins_pad, st);
+    k_relayout_done<<<1, 1, 0, s>>>(a.off, a.nbins, st);
 }
 
-void launch_scatter(const Particles& A, const Particles& B, const uint32_t* old_off, const uint32_t* new_off,
-                    const uint32_t* stay, const uint32_t* dlt, uint32_t* in_cnt, const uint32_t* mv,
-                    const uint32_t* mvx, uint32_t nbins, DevState* st, const KParams& P, int grid, cudaStream_t s) {
-    k_scatter4<<<grid, SCATTER_THREADS, 0, s>>>(A, B, old_off, new_off, stay, dlt, in_cnt, mv, mvx, nbins, st, P);
+void launch_insert(const SortArgs& a, DevState* st, const KParams& P, int grid_dense, cudaStream_t s) {
+    // the electron bins: counts scanned (into off2, free after a re-layout), laid out after the heavy bins
+    launch_scan(a.in_cnt, a.off2, a.partial, a.ncell_pad, s);
+    k_ebins<<<(P.ncell + 255u) / 256u, 256, 0, s>>>(a.off, a.cnt, a.in_cnt, a.off2, P.ncell, st);
+    // heavy movers (a thread per 128 slots of the heavy bins), then the electrons and the tail
+    const uint32_t gs = (uint32_t)((a.slots / 128u + 255u) / 256u);
+    k_insert<<<gs, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins, st);
+    k_insert_dense<<<grid_dense, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins, st);
 }
 
 }  // namespace pd

@@ -12,6 +12,17 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
 // histogram increment with one atomic per distinct bin in the warp
 __device__ __forceinline__ void warp_count(uint32_t* count, uint32_t bin, bool on) {
     const unsigned m = __ballot_sync(FULL_MASK, on);
