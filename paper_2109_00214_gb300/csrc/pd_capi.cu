@@ -52,7 +52,7 @@ size_t run_nodes(const pd_config& c) {
 struct Layout {
     size_t total = 0;
     size_t A[7], B[7], M[7];
-    size_t count, off, off2, outc, bcnt, act, net, bigq, cntb, mv, mm, partial, nc, nc2, cw, ytab, squeue, cand,
+    size_t count, off, off2, outc, bcnt, act, net, bigq, ovq, ovbits, cntb, mv, mm, partial, nc, nc2, cw, ytab, squeue, cand,
         cand_off, active,
         mid, big, rho_e,
         rho_h, diag, E,
@@ -114,6 +114,8 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.net = take((size_t)L.nbins_pad * 4);
     L.bigq_cap = bigq_max(cap);
     L.bigq = take((size_t)L.bigq_cap * 16);                // long bins with holes
+    L.ovq = take((size_t)OVQ_CAP * 4);                     // full bins that borrow slots
+    L.ovbits = take(((size_t)L.nbins_pad / 32 + 1) * 4);
     L.cntb = take((size_t)L.nbins_pad * 4);                // re-layout: bin capacities (scan input)
     L.mv = take((size_t)L.words_pad * 4);                  // slots vacated in their bin
     L.mm = take((size_t)L.words_pad * 4);                  // slots whose particle is in the mover records
@@ -182,6 +184,7 @@ struct pd_sim {
     uint32_t *count, *off, *off2, *outc, *bcnt, *act, *cntb, *mv, *mm, *partial, *cand, *cand_off, *active, *mid, *big;
     int* net;
     uint4* bigq;
+    uint32_t *ovq, *ovbits;
     Particles M;            // movers of the step, at their slots' indices
     bool sorted_valid;      // the bins of A have a layout (after the first step)
     uint4* nc;
@@ -671,14 +674,16 @@ pd_status issue_step(pd_sim* s, bool capturing) {
         a.net = s->net;
         a.bigq = s->bigq;
         a.bigq_cap = s->L.bigq_cap;
+        a.ovq = s->ovq;
+        a.ovbits = s->ovbits;
         a.partial = s->partial;
         a.nbins = nbins;
         a.nbins_pad = s->L.nbins_pad;
         a.slots = s->L.cap;
         a.ncell_pad = s->L.ncell_pad;
         {
-            // heavy bins: counts, holes closed (k_bins, k_compact_big)
-            Timed t(s, K_SCATTER, capturing, 2);
+            // heavy bins: counts, holes closed, slots borrowed (k_bins, k_compact_big, k_borrow)
+            Timed t(s, K_SCATTER, capturing, 3);
             launch_sort(a, s->st, P, s->sms, s->stream);
         }
         {
@@ -912,6 +917,8 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->act = P32(L.act);
     s->net = (int*)(w + L.net);
     s->bigq = (uint4*)(w + L.bigq);
+    s->ovq = P32(L.ovq);
+    s->ovbits = P32(L.ovbits);
     s->cntb = P32(L.cntb);
     s->mv = P32(L.mv);
     s->mm = P32(L.mm);

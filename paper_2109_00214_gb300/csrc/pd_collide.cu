@@ -1438,6 +1438,7 @@ __global__ void k_finalize(const uint32_t* __restrict__ off, uint32_t nbins, con
         if (st->n_live + st->n_e + 2ull * T > P.user_capacity) set_error(st, ERR_CAPACITY);
         st->n_slots = ns;
         st->n_bigc = 0;
+        st->n_ovf = 0;
         st->since += 1u;
         st->n_heavy = 0;
         st->n_light = 0;

@@ -64,7 +64,7 @@ struct DevState {
     unsigned int n_bigc;             // long bins queued for the warp compaction this step
     unsigned int n_relayout;         // new layouts of the bins so far
     unsigned int sort_fault;         // which consistency check of the sort failed (bits), 0 if none
-    unsigned int pad2;
+    unsigned int n_ovf;              // heavy bins that outgrew their slots this step
     unsigned long long n_live;       // heavy particles in bins (after this step's insertions)
     unsigned long long tail_base;    // first slot of the tail (after the electron bins)
     unsigned long long e_base;       // first slot of the electron bins (after the heavy bins' slots)

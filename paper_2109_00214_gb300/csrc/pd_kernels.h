@@ -39,11 +39,13 @@ struct SortArgs {
     int* net;                        // movers in - out per heavy bin since the last layout
     uint4* bigq;                     // long heavy bins with holes
     uint32_t bigq_cap;
+    uint32_t* ovq;                   // heavy bins that outgrew their slots (OVQ_CAP entries)
+    uint32_t* ovbits;                // the same as a bit per bin (nbins / 32 + 1 words)
     uint32_t* partial;               // scan partials
     uint32_t nbins, nbins_pad, ncell_pad;
     uint64_t slots;                  // physical slots of the particle arrays
 };
-// heavy bins: counts, holes closed (two launches)
+// heavy bins: counts, holes closed, slots borrowed by full bins (three launches)
 void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cudaStream_t s);
 // a new layout of the heavy bins when one overflowed (every kernel returns at
 // once otherwise; ten launches)
@@ -52,6 +54,9 @@ void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid
 // the electron bins packed after the heavy bins, then every mover into its
 // bin (six launches)
 void launch_insert(const SortArgs& a, DevState* st, const KParams& P, int grid_dense, cudaStream_t s);
+// heavy bins that may borrow slots from their neighbours in one step (more
+// lay the bins out anew)
+constexpr uint32_t OVQ_CAP = 65536;
 // queue entries that always suffice for bins longer than the warp-compaction
 // threshold (they hold disjoint slots)
 inline uint32_t bigq_max(uint64_t slots) { return (uint32_t)(slots / 96 + 16); }

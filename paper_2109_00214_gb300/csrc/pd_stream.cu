@@ -447,7 +447,8 @@ constexpr uint32_t COMPACT_THREAD_MAX = 96;
 __global__ void __launch_bounds__(256) k_bins(Particles A, const uint32_t* __restrict__ off, uint32_t* cnt,
                                               uint32_t* out_cnt, const uint32_t* __restrict__ in_cnt,
                                               const uint32_t* __restrict__ mv, uint32_t* act, int* net, uint4* bigq,
-                                              uint32_t bigq_cap, uint32_t b0, uint32_t nbins, DevState* st) {
+                                              uint32_t bigq_cap, uint32_t* ovq, uint32_t* ovbits, uint32_t b0,
+                                              uint32_t nbins, DevState* st) {
     long long dlive = 0;
     for (uint32_t b = b0 + blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
         const uint32_t o = out_cnt[b], in = in_cnt[b];
@@ -463,7 +464,12 @@ __global__ void __launch_bounds__(256) k_bins(Particles A, const uint32_t* __res
         act[b] += o + in;
         net[b] += (int)in - (int)o;
         dlive += (long long)in - (long long)o;
-        if (cf > off[b + 1] - start) st->relayout = 1u;
+        if (cf > off[b + 1] - start) {             // full: borrow from the next bin, else a new layout
+            atomicOr(&ovbits[b >> 5], 1u << (b & 31u));
+            const uint32_t q = atomicAdd(&st->n_ovf, 1u);
+            if (q < OVQ_CAP) ovq[q] = b;
+            else st->relayout = 1u;
+        }
         if (o == 0u) continue;
         out_cnt[b] = 0u;
         if (c > COMPACT_THREAD_MAX) {
@@ -559,6 +565,46 @@ __global__ void __launch_bounds__(256) k_compact_big(Particles A, const uint32_t
     }
 }
 
+// A bin that outgrew its slots this step takes free slots from the next
+// bin (same memory order: the next cell's bin of the species, or the first
+// bin of the next species): the next bin's start moves up by `take` slots
+// and the first of its live particles move to just after the others, at
+// most `take` moves.  The next bin must not be full itself (its bit in
+// ovbits, set before any borrowing) and must fit with `take` fewer slots; it
+// lends half of what it can spare beyond the need.  A bin lends only to the
+// bin before it and a full bin never lends: the offsets and slots a thread
+// reads and writes are touched by no other thread.  Without such a
+// neighbour the bins are laid out anew.
+__global__ void __launch_bounds__(256) k_borrow(Particles A, uint32_t* off, const uint32_t* __restrict__ cnt,
+                                                const uint32_t* __restrict__ in_cnt, const uint32_t* __restrict__ ovq,
+                                                const uint32_t* __restrict__ ovbits, uint32_t nbins, DevState* st) {
+    const uint32_t nq = st->n_ovf;
+    if (nq > OVQ_CAP) return;                        // (the re-layout is already set)
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint32_t b = ovq[q], l = b + 1u;
+        const uint32_t need = cnt[b] - (off[b + 1] - off[b]);
+        if (l >= nbins || bit_of(ovbits, l)) {
+            st->relayout = 1u;
+            continue;
+        }
+        const uint32_t lo = off[l], lcap = off[l + 1] - lo, lf = cnt[l];
+        if (lf > lcap || lcap - lf < need) {
+            st->relayout = 1u;
+            continue;
+        }
+        const uint32_t take = need + (lcap - lf - need) / 2u;
+        const uint32_t c0 = lf - in_cnt[l];              // the lender's live particles before its movers
+        const uint32_t m = min(take, c0);
+        const uint32_t nlo = lo + take;
+        for (uint32_t j = 0; j < m; ++j) {
+            const uint32_t src = lo + j, dst = nlo + c0 - m + j;
+            move_slot(A, src, dst);
+            A.key[src] = DEAD;
+        }
+        off[l] = nlo;
+    }
+}
+
 // mover record i of M into slot s of D
 __device__ __forceinline__ void put(Particles& D, uint32_t s, const Particles& M, uint32_t i) {
     D.key[s] = M.key[i];
@@ -618,32 +664,44 @@ __device__ __forceinline__ void insert128(Particles& D, const Particles& M, uint
     reinterpret_cast<uint4*>(mm)[g] = make_uint4(keep[0], keep[1], keep[2], keep[3]);
 }
 
-// heavy movers of the heavy bins' slots [0, e_from) (sparse: a thread per 128 slots)
+// heavy movers of the heavy bins' slots, in whole chunks of 128 below
+// e_from (sparse: a thread per chunk)
 __global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32_t* mm,
                                                 const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
                                                 uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, DevState* st) {
-    const uint32_t ng = (uint32_t)((st->e_from + 127ull) >> 7);
+    const uint32_t ng = (uint32_t)(st->e_from >> 7);
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
         insert128(A, M, mm, g, off, cnt, in_cnt, ncell, nbins, false, st);
 }
 
-// The movers of the electron bins and the tail, [e_from, n_slots) (dense:
-// every electron moves): a thread per four slots, one atomic per bin and warp.
+// The movers from the first chunk of 128 that k_insert leaves (it ends below
+// e_from) to the end of the tail: the electron bins and the tail (dense:
+// every electron moves), and the last heavy slots before them.  A thread per
+// four slots, the group's records loaded whole, one atomic per bin and warp.
 __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
                                                       const uint32_t* __restrict__ off,
                                                       const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
                                                       uint32_t ncell, uint32_t nbins, DevState* st) {
-    const uint32_t g0 = (uint32_t)(st->e_from >> 2), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
+    const uint32_t g0 = (uint32_t)((st->e_from >> 7) << 5), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g - lane < g1; g += gridDim.x * blockDim.x) {
         const uint32_t nib = g < g1 ? (mm[g >> 3] >> (4u * (g & 7u))) & 15u : 0u;
-        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD);
-        if (nib) K = reinterpret_cast<const uint4*>(M.key)[g];
+        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
+        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
+        if (nib) {
+            K = reinterpret_cast<const uint4*>(M.key)[g];
+            Z = reinterpret_cast<const float4*>(M.pz)[g];
+            R = reinterpret_cast<const float4*>(M.pr)[g];
+            VZ = reinterpret_cast<const float4*>(M.vz)[g];
+            VR = reinterpret_cast<const float4*>(M.vr)[g];
+            VT = reinterpret_cast<const float4*>(M.vt)[g];
+            ID = reinterpret_cast<const uint4*>(M.id)[g];
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const uint32_t i = 4u * g + (uint32_t)q;
-            const bool on = ((nib >> q) & 1u) && i >= st->e_from;
-            const uint32_t bin = on ? mover_bin(lane_of(K, q), ncell, nbins) : nbins;
+            const bool on = (nib >> q) & 1u;
+            const uint32_t k = lane_of(K, q);
+            const uint32_t bin = on ? mover_bin(k, ncell, nbins) : nbins;
             if (on && bin >= nbins) sort_fault(st, 128u);
             const bool ok = on && bin < nbins;
             // one atomic per bin among the warp's lanes
@@ -659,7 +717,13 @@ __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, 
                 sort_fault(st, 256u);
                 continue;
             }
-            put(A, s, M, i);
+            A.key[s] = k;
+            A.pz[s] = lane_of(Z, q);
+            A.pr[s] = lane_of(R, q);
+            A.vz[s] = lane_of(VZ, q);
+            A.vr[s] = lane_of(VR, q);
+            A.vt[s] = lane_of(VT, q);
+            A.id[s] = lane_of(ID, q);
         }
     }
 }
@@ -684,7 +748,9 @@ __global__ void __launch_bounds__(256) k_ebins(uint32_t* off, uint32_t* cnt, con
 // Slack of a bin: room for a random walk of its movers in and out and for
 // its drift over H steps, SLACK_SIGMAS standard deviations (a layout holds
 // about a million bins):
-//     slack = 1 + ceil(SLACK_SIGMAS sqrt(lambda H) + drift H).
+//     slack = 3 + ceil(SLACK_SIGMAS sqrt(lambda H) + drift H)
+// (the constant covers the heavier tail of small counts: a bin's arrivals
+// are Poisson).
 // lambda, a bin's traffic per step, is the larger of its own since the
 // previous layout and its species' traffic per particle times the larger of
 // its count and the species' mean count per bin (a short interval sees no
@@ -802,9 +868,9 @@ __global__ void __launch_bounds__(256) k_relayout_caps(const uint32_t* __restric
     __shared__ float s_rate[NSP], s_mean[NSP];
     species_rates(st, since, ncell, s_rate, s_mean);
     // room for the slack: the slots beyond the capacity (or beyond the
-    // particles, if more), less two slots per bin (the one added and the
+    // particles, if more), less four slots per bin (the three added and the
     // rounding up)
-    const unsigned long long used = max(st->sum_cnt + st->n_e + 1024ull, P.user_capacity) + 2ull * nbins;
+    const unsigned long long used = max(st->sum_cnt + st->n_e + 1024ull, P.user_capacity) + 4ull * nbins;
     const double room = P.capacity > used ? (double)(P.capacity - used) : 0.0;
     // largest H <= SLACK_HORIZON_MAX with s1 sqrt(H) + s2 H <= room
     const double s1 = st->sum_s1, s2 = st->sum_s2;
@@ -824,7 +890,7 @@ __global__ void __launch_bounds__(256) k_relayout_caps(const uint32_t* __restric
         } else {
             float lam, drift;
             bin_traffic(b, c, act[b], net[b], since, ncell, s_rate, s_mean, lam, drift);
-            w = 1u + (uint32_t)ceilf(SLACK_SIGMAS * sqrtf(lam) * sqH + drift * H);
+            w = 3u + (uint32_t)ceilf(SLACK_SIGMAS * sqrtf(lam) * sqH + drift * H);
         }
         cap[b] = c + w;
         act[b] = 0u;
@@ -949,9 +1015,11 @@ void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cud
     // one thread per heavy bin: the work of a thread is a chain of dependent
     // loads, which many threads in flight hide
     const uint32_t gb = (a.nbins - P.ncell + 255u) / 256u;
-    k_bins<<<gb, 256, 0, s>>>(a.A, a.off, a.cnt, a.out_cnt, a.in_cnt, a.mv, a.act, a.net, a.bigq, a.bigq_cap, P.ncell,
-                              a.nbins, st);
+    cudaMemsetAsync(a.ovbits, 0, (size_t)(a.nbins / 32u + 1u) * 4u, s);
+    k_bins<<<gb, 256, 0, s>>>(a.A, a.off, a.cnt, a.out_cnt, a.in_cnt, a.mv, a.act, a.net, a.bigq, a.bigq_cap, a.ovq,
+                              a.ovbits, P.ncell, a.nbins, st);
     k_compact_big<<<sms * 4, 256, 0, s>>>(a.A, a.mv, a.bigq, a.bigq_cap, st);
+    k_borrow<<<(OVQ_CAP + 255u) / 256u, 256, 0, s>>>(a.A, a.off, a.cnt, a.in_cnt, a.ovq, a.ovbits, a.nbins, st);
 }
 
 void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid_bins, int grid_slots,
