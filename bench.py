@@ -261,6 +261,8 @@ def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
     steps = args.cpu_steps if steps is None else steps
     total = args.total * rows / args.nz
     cfg, parts = synthetic.microbench(nz=rows, nr=args.nr, total=total, seed=seed, coll_scale=args.coll_scale)
+    if args.coll_scale != 1.0:
+        cfg["capacity"] = int(2.0 * total) + 8 * rows * args.nr
     cfg["heavy_coll"] = int(args.heavy_coll)
     cfg["coulomb"] = int(args.coulomb)
     o = oracle.Oracle(cfg, fp64=False)
@@ -634,6 +636,11 @@ def single_workload(args, seed):
         return cfg, parts, single_workload_desc(args), "extrapolate"
     cfg, parts = synthetic.microbench(nz=args.nz, nr=args.nr, total=args.total, seed=seed,
                                       coll_scale=args.coll_scale)
+    if args.coll_scale != 1.0:
+        # about one candidate per cell reserves two spawn slots each per step,
+        # and the ionizations add particles (a few per cent of the electrons
+        # per step): room for both over the tuning, warm-up and timed steps
+        cfg["capacity"] = int(2.0 * args.total) + 8 * args.nz * args.nr
     cfg["heavy_coll"] = int(args.heavy_coll)
     cfg["coulomb"] = int(args.coulomb)
     return cfg, parts, single_workload_desc(args), None
@@ -645,14 +652,27 @@ def step_updates(c0, c1, steps, heavy_subcycle):
     return ensemble_updates(c0, c1, steps, heavy_subcycle)
 
 
-def kernel_table(prof, steps, n_live, n_moved_e, n_moved_h, cand, ncell, nbins, rz_field, peak):
+def kernel_table(prof, steps, n_live, n_e, n_h, hs, slots, cand, ncell, nbins_h, rz_field, peak):
     """Per-kernel time per step and, where the kernel has a per-unit byte
-    model, its algorithmic GB/s and fraction of the HBM peak."""
-    push_bytes = (24.0 * n_live + 20.0 * (n_moved_e + n_moved_h)) if rz_field else BYTES_PER_PARTICLE["push"] * n_live
+    model, its algorithmic GB/s and fraction of the HBM peak.
+
+    push: an electron is read (20 B Cartesian, 24 B r-z) and written to the
+    mover buffer (28 B) with its id (4 B; the Cartesian push also reads
+    v_theta, 4 B); a heavy particle on a heavy step is read and its new
+    position written back (20 + 8 B Cartesian; 24 + 20 B r-z), on the other
+    steps only its key is read (4 B); a slack slot reads its key (4 B).
+    scatter (the sort after the push): every electron is read from the mover
+    buffer and written to its bin (28 + 28 B); each heavy bin's in and out
+    counts are read (8 B); heavy movers are few."""
+    slack = max(slots - n_live, 0.0)
+    if rz_field:
+        heavy = n_h * (44.0 + 4.0 * (hs - 1)) / hs
+        push_bytes = 56.0 * n_e + heavy + 4.0 * slack
+    else:
+        push_bytes = 60.0 * n_e + 28.0 * n_h + 4.0 * slack
     model = {
         "push": push_bytes,
-        "scatter": BYTES_PER_PARTICLE["scatter"] * n_live,
-        "scan_bins": 12.0 * nbins,
+        "scatter": 56.0 * n_e + 8.0 * nbins_h,
         "ncand": 24.0 * ncell,
         "collide": 100.0 * cand,
     }
@@ -747,8 +767,9 @@ def run_single(args, ws, rank, local):
     ne = 0.5 * (c0[0] + c1[0])
     nh = n_live - ne
     ncell = cfg["nz"] * cfg["nr"]
-    nbins = ncell * (7 if cfg.get("charge_max", 2) >= 3 else 5)
-    table = kernel_table(prof, steps, n_live, ne, nh / hs, counters["cand_total"] / steps, ncell, nbins,
+    nbins_h = ncell * (6 if cfg.get("charge_max", 2) >= 3 else 4)
+    slots = float(ss1["bin_slots"])
+    table = kernel_table(prof, steps, n_live, ne, nh, hs, slots, counters["cand_total"] / steps, ncell, nbins_h,
                          rz_field, peak)
     cands = [k for k in ("push", "scatter") if k in table and "GBs" in table[k]]
     dom = max(cands, key=lambda k: table[k]["ms_per_step"])

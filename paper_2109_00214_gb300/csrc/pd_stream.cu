@@ -697,33 +697,44 @@ __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, 
             VT = reinterpret_cast<const float4*>(M.vt)[g];
             ID = reinterpret_cast<const uint4*>(M.id)[g];
         }
+        // the four lanes' bins, their warp peers and the cursor claims: the
+        // claims of the four are independent, so all are issued before any
+        // result is used
+        uint32_t bin[4], left[4];
+        unsigned peers[4];
+        bool ok[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const bool on = (nib >> q) & 1u;
-            const uint32_t k = lane_of(K, q);
-            const uint32_t bin = on ? mover_bin(k, ncell, nbins) : nbins;
-            if (on && bin >= nbins) sort_fault(st, 128u);
-            const bool ok = on && bin < nbins;
-            // one atomic per bin among the warp's lanes
-            const unsigned peers = __match_any_sync(FULL_MASK, ok ? bin : 0xFFFFFFFFu);
-            const uint32_t leader = (uint32_t)(__ffs((int)peers) - 1);
-            uint32_t left = 0;
-            if (ok && lane == leader) left = atomicSub(&in_cnt[bin], (uint32_t)__popc(peers));
-            left = __shfl_sync(FULL_MASK, left, (int)leader);
-            if (!ok) continue;
-            const uint32_t rank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            const uint32_t s = off[bin] + cnt[bin] - left + rank;
-            if (left < (uint32_t)__popc(peers) || s >= off[bin] + cnt[bin]) {
+            bin[q] = on ? mover_bin(lane_of(K, q), ncell, nbins) : nbins;
+            if (on && bin[q] >= nbins) sort_fault(st, 128u);
+            ok[q] = on && bin[q] < nbins;
+            peers[q] = __match_any_sync(FULL_MASK, ok[q] ? bin[q] : 0xFFFFFFFFu);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t leader = (uint32_t)(__ffs((int)peers[q]) - 1);
+            left[q] = (ok[q] && lane == leader) ? atomicSub(&in_cnt[bin[q]], (uint32_t)__popc(peers[q])) : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t leader = (uint32_t)(__ffs((int)peers[q]) - 1);
+            const uint32_t lq = __shfl_sync(FULL_MASK, left[q], (int)leader);
+            if (!ok[q]) continue;
+            const uint32_t b = bin[q];
+            const uint32_t rank = (uint32_t)__popc(peers[q] & ((1u << lane) - 1u));
+            const uint32_t sl = off[b] + cnt[b] - lq + rank;
+            if (lq < (uint32_t)__popc(peers[q]) || sl >= off[b] + cnt[b]) {
                 sort_fault(st, 256u);
                 continue;
             }
-            A.key[s] = k;
-            A.pz[s] = lane_of(Z, q);
-            A.pr[s] = lane_of(R, q);
-            A.vz[s] = lane_of(VZ, q);
-            A.vr[s] = lane_of(VR, q);
-            A.vt[s] = lane_of(VT, q);
-            A.id[s] = lane_of(ID, q);
+            A.key[sl] = lane_of(K, q);
+            A.pz[sl] = lane_of(Z, q);
+            A.pr[sl] = lane_of(R, q);
+            A.vz[sl] = lane_of(VZ, q);
+            A.vr[sl] = lane_of(VR, q);
+            A.vt[sl] = lane_of(VT, q);
+            A.id[sl] = lane_of(ID, q);
         }
     }
 }
