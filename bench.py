@@ -251,10 +251,32 @@ def traffic_per_particle(kernel):
     return TRAFFIC_PER_PARTICLE.get(kernel) if sha == TRAFFIC_SOURCE_SHA else None
 
 
+def host_cpu():
+    """Host cores the oracle uses and their model (lscpu's, else /proc/cpuinfo's)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model
+
+
 def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
-    """The oracle (float mirror, as it stands, one thread) on a bounded sample:
-    the first `rows` rows of cells of the same workload recipe, `warmup`
-    untimed steps, then `steps` timed ones."""
+    """The oracle (float mirror, as it stands, its OpenMP build on all host
+    cores) on a bounded sample: the first `rows` rows of cells of the same
+    workload recipe, `warmup` untimed steps, then `steps` timed ones."""
     import oracle
     import synthetic
     rows = args.cpu_rows if rows is None else rows
@@ -265,7 +287,7 @@ def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
         cfg["capacity"] = int(2.0 * total) + 8 * rows * args.nr
     cfg["heavy_coll"] = int(args.heavy_coll)
     cfg["coulomb"] = int(args.coulomb)
-    o = oracle.Oracle(cfg, fp64=False)
+    o = oracle.Oracle(cfg, fp64=False, omp=True)
     o.set_cross_sections(synthetic.standin_cross_sections())
     o.load(parts)
     o.prime()
@@ -277,9 +299,12 @@ def cpu_baseline(args, cfg_full, seed, rows=None, steps=None, warmup=0):
     dt = time.perf_counter() - t0
     n1 = o.count()
     upd = steps * 0.5 * (n0 + n1)
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "ms_per_step": 1e3 * dt / steps,
+    cores, model = host_cpu()
+    return {"value": upd / dt, "unit": UNIT, "cores": cores, "cpu_model": model, "kind": "oracle",
+            "ms_per_step": 1e3 * dt / steps,
             "sample": f"{rows}x{args.nr} cells of the same recipe ({n0} particles), {warmup} untimed and "
-                      f"{steps} timed steps, {dt:.1f} s, single-threaded C oracle (float mirror)"}
+                      f"{steps} timed steps, {dt:.1f} s, C oracle (float mirror), OpenMP build on {cores} "
+                      f"host cores"}
 
 
 def cpu_baseline_production(args, seed, n=128, steps=None, warmup=1):
@@ -292,7 +317,7 @@ def cpu_baseline_production(args, seed, n=128, steps=None, warmup=1):
     total = args.prod_total * (n / args.prod_n) ** 2
     cfg, parts = synthetic.rz_plume(n=n, total=total, seed=seed)
     cfg.update(field_on=1, inject_on=0, poisson_tol=1e-8)
-    o = oracle.Oracle(cfg, fp64=False)
+    o = oracle.Oracle(cfg, fp64=False, omp=True)
     o.set_cross_sections(synthetic.standin_cross_sections())
     o.load(parts)
     o.prime()
@@ -308,9 +333,12 @@ def cpu_baseline_production(args, seed, n=128, steps=None, warmup=1):
     dt = time.perf_counter() - t0
     c1 = counts()
     upd = step_updates(c0, c1, steps, cfg["heavy_subcycle"])
-    return {"value": upd / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "ms_per_step": 1e3 * dt / steps,
+    cores, model = host_cpu()
+    return {"value": upd / dt, "unit": UNIT, "cores": cores, "cpu_model": model, "kind": "oracle",
+            "ms_per_step": 1e3 * dt / steps,
             "sample": f"the production plume recipe on {n}x{n} cells ({int(c0.sum())} particles), {warmup} untimed "
-                      f"and {steps} timed steps, {dt:.1f} s, single-threaded C oracle (float mirror, CG field solve)"}
+                      f"and {steps} timed steps, {dt:.1f} s, C oracle (float mirror, CG field solve), OpenMP build "
+                      f"on {cores} host cores"}
 
 
 def cpu_baseline_for(args, seed, steps=None, warmup=0, rows=None):

@@ -19,23 +19,30 @@ _BUILD = os.path.join(_HERE, "_build")
 _SRC = os.path.join(_HERE, "pd_oracle.c")
 
 
-def compile_source(src, so, fp64):
+def compile_source(src, so, fp64, omp=False):
     """Compile the oracle source file `src` into the shared object `so` with
-    the flags of the regular builds."""
+    the flags of the regular builds (omp: the build that runs on all host
+    cores)."""
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", *(["-DOR_DOUBLE"] if fp64 else []), "-o", so, src, "-lm"]
+           "-shared", *(["-DOR_DOUBLE"] if fp64 else []), *(["-fopenmp", "-DOR_OMP"] if omp else []),
+           "-o", so, src, "-lm"]
     subprocess.check_call(cmd)
 
 
+BUILDS = (("oracle32", False, False), ("oracle64", True, False), ("oracle32_omp", False, True),
+          ("oracle64_omp", True, True))
+
+
 def build(force=False):
-    """Compile both oracle builds with gcc (no fused multiply-add)."""
+    """Compile the oracle builds with gcc (no fused multiply-add): double and
+    float, each single-threaded and on all cores (OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
     outs = {}
-    for name, extra in (("oracle32", False), ("oracle64", True)):
+    for name, fp64, omp in BUILDS:
         so = os.path.join(_BUILD, f"lib{name}.so")
         if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
             tmp = so + f".tmp{os.getpid()}"
-            compile_source(_SRC, tmp, fp64=bool(extra))
+            compile_source(_SRC, tmp, fp64=fp64, omp=omp)
             os.replace(tmp, so)
         outs[name] = so
     return outs
@@ -63,8 +70,8 @@ P = C.c_void_p
 D = C.POINTER(C.c_double)
 
 
-def _lib(fp64):
-    key = "oracle64" if fp64 else "oracle32"
+def _lib(fp64, omp=False):
+    key = ("oracle64" if fp64 else "oracle32") + ("_omp" if omp else "")
     if key not in _LIBS:
         _LIBS[key] = bind(build()[key])
     return _LIBS[key]
@@ -150,8 +157,8 @@ def fn_current(F, work):
 class Oracle:
     """One CPU simulation.  `cfg` is a :func:`synthetic.base_config` dict."""
 
-    def __init__(self, cfg, fp64=True, field_mode=None, lib=None):
-        self.L = _lib(fp64) if lib is None else lib
+    def __init__(self, cfg, fp64=True, field_mode=None, lib=None, omp=False):
+        self.L = _lib(fp64, omp) if lib is None else lib
         self.fp64 = fp64
         self.cfg = dict(cfg)
         c = _Cfg()

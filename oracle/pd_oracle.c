@@ -35,6 +35,19 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The OpenMP build (OR_OMP) runs the particle loops and the cells'
+ * collisions on all host cores.  It is deterministic and gives the serial
+ * build's particles, counts and charge: deposits are integer, a cell's
+ * collisions are ordered and touch only its particles, spawns take the
+ * slots their ids reserve and are compacted in order; only the FP64 ledger
+ * sums (energies, the gap current) are added in another order. */
+#ifdef OR_OMP
+#include <omp.h>
+#define OR_ATOMIC _Pragma("omp atomic")
+#else
+#define OR_ATOMIC
+#endif
+
 #ifdef OR_DOUBLE
 typedef double real;
 #define R_(x) ((double)(x))
@@ -138,6 +151,11 @@ typedef struct {
     float ray[1024];             /* Rayleigh inverse CDF in units of sigma */
     int poisson_iters;
     double poisson_relres;
+    /* collisions of cells in parallel: spawns go to the slot their id
+     * reserves, spawn_base + (id - spawn_id0) */
+    int spawn_mode;
+    int64_t spawn_base;
+    uint32_t spawn_id0;
 } or_sim;
 
 /* ------------------------------------------------------------------ */
@@ -506,10 +524,10 @@ static void deposit_one(const or_sim* S, int64_t* rho, int iz, int ir, real pz, 
     uint32_t wz = (uint32_t)nearbyint((double)(pz * R_(65536)));
     uint32_t wr = (uint32_t)nearbyint((double)(pr * R_(65536)));
     int64_t az = 65536 - (int64_t)wz, ar = 65536 - (int64_t)wr;
-    rho[node_index(S, iz, ir)] += zq * az * ar;
-    rho[node_index(S, iz + 1, ir)] += zq * (int64_t)wz * ar;
-    rho[node_index(S, iz, ir + 1)] += zq * az * (int64_t)wr;
-    rho[node_index(S, iz + 1, ir + 1)] += zq * (int64_t)wz * (int64_t)wr;
+    OR_ATOMIC rho[node_index(S, iz, ir)] += zq * az * ar;
+    OR_ATOMIC rho[node_index(S, iz + 1, ir)] += zq * (int64_t)wz * ar;
+    OR_ATOMIC rho[node_index(S, iz, ir + 1)] += zq * az * (int64_t)wr;
+    OR_ATOMIC rho[node_index(S, iz + 1, ir + 1)] += zq * (int64_t)wz * (int64_t)wr;
 }
 
 static void remove_particle(or_sim* S, int64_t p) {
@@ -525,6 +543,18 @@ static int64_t append_particle(or_sim* S, int sp, int iz, int ir, real pz, real 
                                real vz, real vr, real vt, uint32_t id) {
     if (S->n >= S->cap) return -1;
     int64_t p = S->n++;
+    S->sp[p] = (uint8_t)sp; S->iz[p] = iz; S->ir[p] = ir;
+    S->pz[p] = pz; S->pr[p] = pr; S->vz[p] = vz; S->vr[p] = vr; S->vt[p] = vt;
+    S->id[p] = id;
+    return p;
+}
+
+/* a particle made by a collision: appended, or (cells in parallel) put in
+ * the slot its id reserves */
+static int64_t spawn_particle(or_sim* S, int sp, int iz, int ir, real pz, real pr, real vz, real vr, real vt,
+                              uint32_t id) {
+    if (!S->spawn_mode) return append_particle(S, sp, iz, ir, pz, pr, vz, vr, vt, id);
+    int64_t p = S->spawn_base + (int64_t)(id - S->spawn_id0);
     S->sp[p] = (uint8_t)sp; S->iz[p] = iz; S->ir[p] = ir;
     S->pz[p] = pz; S->pr[p] = pr; S->vz[p] = vz; S->vr[p] = vr; S->vt[p] = vt;
     S->id[p] = id;
@@ -600,7 +630,55 @@ static int sputter_emit(or_sim* S) {
     return 0;
 }
 
+#ifdef OR_OMP
+/* the push on all cores: every particle is pushed on its own; then, in index
+ * order, the absorbed ones are tallied and the others kept (stable) */
+static void push_all_par(or_sim* S, int heavy_step) {
+    double dte = S->c.dt, dth = S->c.dt * S->c.heavy_subcycle;
+    int64_t n = S->n;
+    uint8_t* out = (uint8_t*)malloc(n > 0 ? (size_t)n : 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; ++p) {
+        int s = S->sp[p];
+        out[p] = 0;
+        if (s != SP_E && !heavy_step) continue;
+        double dts = (s == SP_E) ? dte : dth;
+        real qmdt = R_((double)ZQ[s] * QE / species_mass(s) * dts);
+        real dtz = R_(dts / S->c.dz), dtr = R_(dts / S->c.dr);
+        out[p] = (uint8_t)push_one(S, p, qmdt, dtz, dtr);
+    }
+    double IgapQ = 0.0;
+    int64_t w = 0;
+    for (int64_t p = 0; p < n; ++p) {
+        if (out[p]) {
+            int s = S->sp[p], el = out[p] - 1;
+            S->absorbed[el][s] += 1;
+            S->absorbed_energy[el] += S->c.weight * kinetic(S, p);
+            if (el == 1) IgapQ += -(double)ZQ[s] * QE * S->c.weight;
+            if (el == 0) S->charge_cathode += (double)ZQ[s] * QE * S->c.weight;
+            continue;
+        }
+        if (w != p) {
+            S->sp[w] = S->sp[p]; S->iz[w] = S->iz[p]; S->ir[w] = S->ir[p];
+            S->pz[w] = S->pz[p]; S->pr[w] = S->pr[p];
+            S->vz[w] = S->vz[p]; S->vr[w] = S->vr[p]; S->vt[w] = S->vt[p];
+            S->id[w] = S->id[p];
+        }
+        ++w;
+    }
+    S->n = w;
+    S->I_gap = IgapQ / dte;
+    free(out);
+}
+#endif
+
 static void push_all(or_sim* S, int heavy_step) {
+#ifdef OR_OMP
+    if (!S->c.sputter) {       /* (the impact records of sputtering are kept in the serial order) */
+        push_all_par(S, heavy_step);
+        return;
+    }
+#endif
     double dte = S->c.dt, dth = S->c.dt * S->c.heavy_subcycle;
     double IgapQ = 0.0;
     for (int64_t p = 0; p < S->n;) {
@@ -632,6 +710,9 @@ static void deposit_all(or_sim* S, int heavy_step) {
     int64_t nn = (int64_t)S->nzn * S->nrn;
     memset(S->rho_e, 0, nn * 8);
     if (heavy_step) memset(S->rho_h, 0, nn * 8);
+#ifdef OR_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t p = 0; p < S->n; ++p) {
         int s = S->sp[p];
         if (s == SP_E) deposit_one(S, S->rho_e, S->iz[p], S->ir[p], S->pz[p], S->pr[p], -1);
@@ -657,7 +738,7 @@ static vec3 iso_dir(or_sim* S, stream_t* st) {
             return n;
         }
     }
-    S->iso_fallback++;
+    OR_ATOMIC S->iso_fallback++;
     vec3 n = {0, 0, 1};
     return n;
 }
@@ -674,7 +755,7 @@ static void azimuth(or_sim* S, stream_t* st, real* c, real* s) {
             return;
         }
     }
-    S->iso_fallback++;
+    OR_ATOMIC S->iso_fallback++;
     *c = 1; *s = 0;
 }
 
@@ -867,13 +948,13 @@ static int collide_event(or_sim* S, stream_t* st, int ch, int64_t ie, int64_t it
     S->sp[it] = (uint8_t)new_sp;
     deposit_one(S, rho_h, S->iz[it], S->ir[it], S->pz[it], S->pr[it], dz);
     /* e2 (scattered into e4) at the position of A* */
-    int64_t q = append_particle(S, SP_E, S->iz[it], S->ir[it], S->pz[it], S->pr[it], e2.x, e2.y, e2.z, (*next_id)++);
+    int64_t q = spawn_particle(S, SP_E, S->iz[it], S->ir[it], S->pz[it], S->pr[it], e2.x, e2.y, e2.z, (*next_id)++);
     if (q < 0) return -2;
     deposit_one(S, rho_e, S->iz[it], S->ir[it], S->pz[it], S->pr[it], -1);
     ++nspawn;
     if (ch == CH_DI) {
         /* e6 at the position of e3 (the projectile) */
-        q = append_particle(S, SP_E, S->iz[ie], S->ir[ie], S->pz[ie], S->pr[ie], e6.x, e6.y, e6.z, (*next_id)++);
+        q = spawn_particle(S, SP_E, S->iz[ie], S->ir[ie], S->pz[ie], S->pr[ie], e6.x, e6.y, e6.z, (*next_id)++);
         if (q < 0) return -2;
         deposit_one(S, rho_e, S->iz[ie], S->ir[ie], S->pz[ie], S->pr[ie], -1);
         ++nspawn;
@@ -1032,7 +1113,8 @@ static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* 
     double lnl = S->c.coulomb_lnl;
     const idrec* el = rec + cnt[SP_E * C + c];
     uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
-    S->coul_ee += pairs_same(S, c, el, Ne, SP_E, 0, R_(coulomb_k(-1, -1, 0.5 * ME, lnl) * (double)Ne * wv), R_(0.5));
+    uint64_t ee_ = pairs_same(S, c, el, Ne, SP_E, 0, R_(coulomb_k(-1, -1, 0.5 * ME, lnl) * (double)Ne * wv), R_(0.5));
+    OR_ATOMIC S->coul_ee += ee_;
     double mr = mr_class();
     real fe = R_(mr / ME), fi = R_(mr / M_CU);
     const idrec* il[5];
@@ -1045,7 +1127,8 @@ static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* 
     for (int i = 0; i < 5; ++i) {
         uint32_t Nf = Ne < Ni[i] ? Ne : Ni[i];
         real Kn = R_(coulomb_k(-1, ZQ[SP_CUP + i], mr, lnl) * (double)Nf * wv);
-        S->coul_ei += pairs_cross(S, c, el, Ne, SP_E, il[i], Ni[i], SP_CUP + i, 1 + i, Kn, fe, fi);
+        uint64_t ei_ = pairs_cross(S, c, el, Ne, SP_E, il[i], Ni[i], SP_CUP + i, 1 + i, Kn, fe, fi);
+        OR_ATOMIC S->coul_ei += ei_;
     }
     if (!heavy_step) return;
     double wvh = S->c.weight * (dtc * S->c.heavy_subcycle) / cell_volume(S, j);
@@ -1055,8 +1138,9 @@ static void coulomb_cell(or_sim* S, int64_t c, const idrec* rec, const int64_t* 
             int sa = SP_CUP + a, sb = SP_CUP + b;
             uint32_t Nf = a == b ? Ni[a] : (Ni[a] < Ni[b] ? Ni[a] : Ni[b]);
             real Kn = R_(coulomb_k(ZQ[sa], ZQ[sb], 0.5 * M_CU, lnl) * (double)Nf * wvh);
-            if (a == b) S->coul_ii += pairs_same(S, c, il[a], Ni[a], sa, cls, Kn, R_(0.5));
-            else S->coul_ii += pairs_cross(S, c, il[a], Ni[a], sa, il[b], Ni[b], sb, cls, Kn, R_(0.5), R_(0.5));
+            uint64_t ii_ = a == b ? pairs_same(S, c, il[a], Ni[a], sa, cls, Kn, R_(0.5))
+                                  : pairs_cross(S, c, il[a], Ni[a], sa, il[b], Ni[b], sb, cls, Kn, R_(0.5), R_(0.5));
+            OR_ATOMIC S->coul_ii += ii_;
         }
 }
 
@@ -1065,22 +1149,35 @@ static int collide_all(or_sim* S, int heavy_step) {
     int64_t nb = C * NSP;
     int64_t* cnt = (int64_t*)calloc(nb + 1, 8);
     int64_t n0 = S->n;
+#ifdef OR_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t p = 0; p < n0; ++p) {
         int64_t cell = (int64_t)S->iz[p] * S->c.nr + S->ir[p];
-        cnt[(int64_t)S->sp[p] * C + cell + 1]++;
+        OR_ATOMIC cnt[(int64_t)S->sp[p] * C + cell + 1]++;
     }
     for (int64_t b = 0; b < nb; ++b) cnt[b + 1] += cnt[b];
     idrec* rec = (idrec*)malloc((n0 > 0 ? n0 : 1) * sizeof(idrec));
     int64_t* cur = (int64_t*)malloc((nb > 0 ? nb : 1) * 8);
     memcpy(cur, cnt, nb * 8);
+#ifdef OR_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t p = 0; p < n0; ++p) {
         int64_t cell = (int64_t)S->iz[p] * S->c.nr + S->ir[p];
         int64_t b = (int64_t)S->sp[p] * C + cell;
-        rec[cur[b]].id = S->id[p];
-        rec[cur[b]].idx = p;
-        cur[b]++;
+        int64_t at;
+#ifdef OR_OMP
+#pragma omp atomic capture
+#endif
+        at = cur[b]++;
+        rec[at].id = S->id[p];
+        rec[at].idx = p;
     }
     /* canonical order inside each (species, cell) bin: ascending id */
+#ifdef OR_OMP
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
     for (int64_t b = 0; b < nb; ++b)
         if (cnt[b + 1] - cnt[b] > 1) qsort(rec + cnt[b], cnt[b + 1] - cnt[b], sizeof(idrec), cmp_id);
 
@@ -1093,9 +1190,11 @@ static int collide_all(or_sim* S, int heavy_step) {
     double dtc = S->c.dt * S->c.coll_dt_scale;
     double dth = dtc * S->c.heavy_subcycle;                 /* heavy pairs collide on heavy steps */
     int heavy = S->c.heavy_coll && heavy_step;
+#ifdef OR_OMP
+#pragma omp parallel for schedule(static) reduction(+ : total, heavy_total)
+#endif
     for (int64_t c = 0; c < C; ++c) {
         int j = (int)(c % S->c.nr);
-        pre[c] = total;
         stream_t st;
         stream_init(&st, S, (uint32_t)c, S->step, SID_NCAND);
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
@@ -1124,12 +1223,33 @@ static int collide_all(or_sim* S, int heavy_step) {
             heavy_total += nc[NCLS * c + 5] + nc[NCLS * c + 6];
         }
     }
+    /* spawn id slots of each cell: prefix of its electron-class candidates */
+    {
+        uint64_t acc = 0;
+        for (int64_t c = 0; c < C; ++c) {
+            pre[c] = acc;
+            for (int k = 0; k < NECLS; ++k) acc += nc[NCLS * c + k];
+        }
+    }
     pre[C] = total;
     S->cand_total += total + heavy_total;
     uint32_t id_base = S->id_next;
     real km = kmr(), kmh = kmr_heavy();
     int err = 0;
-    for (int64_t c = 0; c < C && !err; ++c) {
+#ifdef OR_OMP
+    /* cells in parallel, each cell's spawns in the slots of its ids; only
+     * when the reserved slots fit (the serial order otherwise) */
+    const int par = S->n + 2 * (int64_t)total <= S->cap;
+    if (par) {
+        S->spawn_mode = 1;
+        S->spawn_base = S->n;
+        S->spawn_id0 = id_base;
+        for (int64_t q = S->n; q < S->n + 2 * (int64_t)total; ++q) S->sp[q] = 255;
+    }
+#pragma omp parallel for schedule(dynamic, 64) if (par)
+#endif
+    for (int64_t c = 0; c < C; ++c) {
+        if (err) continue;
         uint32_t next_id = id_base + (uint32_t)(2 * pre[c]);
         const idrec* el = rec + cnt[SP_E * C + c];
         uint32_t Ne = (uint32_t)(cnt[SP_E * C + c + 1] - cnt[SP_E * C + c]);
@@ -1145,7 +1265,7 @@ static int collide_all(or_sim* S, int heavy_step) {
                 uint32_t i = pick(&st, Ne), jt = pick(&st, Nt);
                 real Racc = u01(&st), Rch = u01(&st);
                 int64_t ie = el[i].idx, it = tl[jt].idx;
-                if (S->sp[it] != ts) { S->consumed++; continue; }   /* target already ionized this step */
+                if (S->sp[it] != ts) { OR_ATOMIC S->consumed++; continue; }   /* target already ionized this step */
                 real ux = S->vz[ie] - S->vz[it], uy = S->vr[ie] - S->vr[it], uz = S->vt[ie] - S->vt[it];
                 real g2 = (ux * ux + uy * uy) + uz * uz;
                 real g = OR_SQRT(g2);
@@ -1157,8 +1277,8 @@ static int collide_all(or_sim* S, int heavy_step) {
                     cum[q] = sT;
                 }
                 real sg = sT * g;
-                if (sg > S->sgmax[k]) S->ratio_viol++;
-                if (!(Racc * S->sgmax[k] < sg)) { S->nulls++; continue; }
+                if (sg > S->sgmax[k]) { OR_ATOMIC S->ratio_viol++; }
+                if (!(Racc * S->sgmax[k] < sg)) { OR_ATOMIC S->nulls++; continue; }
                 real rs = Rch * sT;
                 int q = -1;
                 for (int a = 0; a < CLASS_NCH[k]; ++a) if (rs < cum[a]) { q = a; break; }
@@ -1170,8 +1290,8 @@ static int collide_all(or_sim* S, int heavy_step) {
                 int ch = CLASS_CH0[k] + q;
                 int r = collide_event(S, &st, ch, ie, it, &next_id, S->rho_e, S->rho_h);
                 if (r == -2) { err = 1; break; }
-                if (r < 0) { S->thr_rej++; continue; }
-                S->events[ch]++;
+                if (r < 0) { OR_ATOMIC S->thr_rej++; continue; }
+                OR_ATOMIC S->events[ch]++;
             }
         }
         /* heavy pairs, classes 5 (Cu from the Cu list, Cu+ from the Cu+ list) and
@@ -1193,13 +1313,13 @@ static int collide_all(or_sim* S, int heavy_step) {
                 real Racc = u01(&st);
                 (void)u01(&st);     /* fourth draw of the candidate, unused by one-channel classes */
                 int64_t ia = cul[i].idx, ib = tl[jt].idx;
-                if (S->sp[ia] != SP_CU || S->sp[ib] != ts) { S->consumed++; continue; }
+                if (S->sp[ia] != SP_CU || S->sp[ib] != ts) { OR_ATOMIC S->consumed++; continue; }
                 real ux = S->vz[ia] - S->vz[ib], uy = S->vr[ia] - S->vr[ib], uz = S->vt[ia] - S->vt[ib];
                 real g2 = (ux * ux + uy * uy) + uz * uz;
                 real g = OR_SQRT(g2);
                 real sg = xs_lookup(S, CLASS_CH0[k], g2 * kmh) * g;
-                if (sg > S->sgmax[k]) S->ratio_viol++;
-                if (!(Racc * S->sgmax[k] < sg)) { S->nulls++; continue; }
+                if (sg > S->sgmax[k]) { OR_ATOMIC S->ratio_viol++; }
+                if (!(Racc * S->sgmax[k] < sg)) { OR_ATOMIC S->nulls++; continue; }
                 if (k == 5) {
                     /* resonant charge exchange: the electron moves to the ion, the
                      * velocities stay with the atoms: the Cu+ slot takes the Cu's
@@ -1216,7 +1336,7 @@ static int collide_all(or_sim* S, int heavy_step) {
                     S->vz[ia] = va.x; S->vr[ia] = va.y; S->vt[ia] = va.z;
                     S->vz[ib] = vb.x; S->vr[ib] = vb.y; S->vt[ib] = vb.z;
                 }
-                S->events[CLASS_CH0[k]]++;
+                OR_ATOMIC S->events[CLASS_CH0[k]]++;
             }
         }
         /* Coulomb collisions of the cell's charged particles, after its DSMC
@@ -1225,6 +1345,24 @@ static int collide_all(or_sim* S, int heavy_step) {
          * ionized earlier this step is left out. */
         if (S->c.coulomb && !err) coulomb_cell(S, c, rec, cnt, C, dtc, heavy_step);
     }
+#ifdef OR_OMP
+    if (par) {
+        /* the reserved slots, compacted in order: the serial build's appends */
+        int64_t w = S->n, end = S->n + 2 * (int64_t)total;
+        for (int64_t q = S->n; q < end; ++q) {
+            if (S->sp[q] == 255) continue;
+            if (q != w) {
+                S->sp[w] = S->sp[q]; S->iz[w] = S->iz[q]; S->ir[w] = S->ir[q];
+                S->pz[w] = S->pz[q]; S->pr[w] = S->pr[q];
+                S->vz[w] = S->vz[q]; S->vr[w] = S->vr[q]; S->vt[w] = S->vt[q];
+                S->id[w] = S->id[q];
+            }
+            ++w;
+        }
+        S->n = w;
+        S->spawn_mode = 0;
+    }
+#endif
     S->id_next = id_base + (uint32_t)(2 * total);
     free(cnt); free(rec); free(cur); free(nc); free(pre);
     return err;
