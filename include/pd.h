@@ -45,7 +45,8 @@ typedef enum {
     PD_ERR_ARG = 1,        /* invalid argument or configuration */
     PD_ERR_CAPACITY = 2,   /* particle capacity or id space exhausted */
     PD_ERR_CUDA = 3,       /* a CUDA runtime call failed */
-    PD_ERR_TIMEOUT = 4,    /* a bounded device wait ran out */
+    PD_ERR_TIMEOUT = 4,    /* reserved: a bounded device wait ran out (no kernel of this
+                              version waits on another, so none reports it) */
     PD_ERR_NONFINITE = 5,  /* NaN/Inf met where a finite value is required */
     PD_ERR_STATE = 6       /* call not valid in the current state */
 } pd_status;
@@ -427,15 +428,21 @@ pd_status pd_set_warm_start(pd_sim* sim, int mode, pd_net* net);
  * Scratch: one histogram of PD_SPECTRUM_STATIC_MAX_BINS counters in the
  * library's own device memory, which every GPU that loads the library keeps
  * until the process exits.  nbins above that maximum is rejected with
- * PD_ERR_ARG.  The first call on a device looks up the scratch's device
- * address; make that first call before any stream capture.  All calls share
- * the one histogram, which is cleared at the start of each call: calls whose
- * work overlaps on the GPU (other streams, other threads) race and give wrong
- * counts. */
+ * PD_ERR_ARG (pd_spectrum_static_max_bins() returns the maximum).  The
+ * scratch belongs to the current device: `cuda_stream` must be a stream of
+ * that device, else PD_ERR_ARG.  The first call on a device looks up the
+ * scratch's device address and keeps it for the life of the process (it does
+ * not survive a cudaDeviceReset).  The call synchronises `cuda_stream` (it
+ * copies the histogram to the host before it returns), so it must not be
+ * issued while any stream is being captured into a CUDA graph.  All calls
+ * share the one histogram, which is cleared at the start of each call: calls
+ * whose work overlaps on the GPU (other streams, other threads) race and give
+ * wrong counts. */
 #define PD_SPECTRUM_STATIC_MAX_BINS 4096
 pd_status pd_energy_spectrum_static(const uint32_t* key, const float* vz, const float* vr, const float* vt,
                                     int64_t n, int species, double e_lo_eV, double e_hi_eV, int nbins,
                                     void* cuda_stream, uint64_t* out);
+int pd_spectrum_static_max_bins(void);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,7 @@ from . import build as _build
 __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "config_from_dict",
            "pd_config_default", "pd_workspace_size", "pd_create", "pd_set_cross_section", "pd_set_sputter_yield",
            "pd_load_particles", "pd_load_particles_device", "pd_set_field", "pd_inject_cathode",
-           "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots", "pd_get_sort_stats", "pd_get_bins",
+           "pd_step", "pd_synchronize", "pd_get_scalars", "pd_get_counters", "pd_particle_slots", "pd_get_sort_stats", "pd_get_bins", "pd_spectrum_static_max_bins",
            "pd_get_particles", "pd_get_rho", "pd_get_phi", "pd_get_field", "pd_get_density_map",
            "pd_get_energy_spectrum", "pd_profile_enable", "pd_profile_read", "pd_kernel_name",
            "pd_last_error", "pd_destroy", "pd_energy_spectrum_static", "Ensemble", "pd_ensemble_workspace_size",
@@ -113,6 +113,7 @@ _SIGS = {
     "pd_get_counters": (C.c_int, [P, P]),
     "pd_particle_slots": (C.c_int, [P, C.POINTER(C.c_int64)]),
     "pd_get_sort_stats": (C.c_int, [P, P]),
+    "pd_spectrum_static_max_bins": (C.c_int, []),
     "pd_get_bins": (C.c_int, [P, P, P, C.POINTER(C.c_int64)]),
     "pd_get_particles": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P]),
     "pd_ensemble_workspace_size": (C.c_int, [C.POINTER(PdConfig), C.c_int, C.POINTER(C.c_size_t)]),
@@ -593,12 +594,15 @@ def pd_destroy(h):
     _lib().pd_destroy(h)
 
 
-PD_SPECTRUM_STATIC_MAX_BINS = 4096
+def pd_spectrum_static_max_bins():
+    return int(_lib().pd_spectrum_static_max_bins())
 
 
 def pd_energy_spectrum_static(key_ptr, vz_ptr, vr_ptr, vt_ptr, n, species, lo, hi, nbins, stream_ptr=0):
     """Energy histogram of raw device particle arrays (device pointers as ints),
     with no allocation; see include/pd.h for the shared-scratch rules."""
+    if not 1 <= int(nbins) <= pd_spectrum_static_max_bins():
+        raise PdError(f"pd_energy_spectrum_static: nbins = {nbins} is outside 1..{pd_spectrum_static_max_bins()}")
     a = np.zeros(nbins, np.uint64)
     r = _lib().pd_energy_spectrum_static(P(key_ptr), P(vz_ptr), P(vr_ptr), P(vt_ptr), int(n), int(species),
                                          float(lo), float(hi), int(nbins), P(stream_ptr), _ptr(a))

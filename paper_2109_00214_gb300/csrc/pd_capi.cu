@@ -32,16 +32,16 @@ namespace {
 
 // CODATA 2018
 constexpr double QE = 1.602176634e-19;
-constexpr double ME = 9.1093837015e-31;
+constexpr double ME = MASS_E;
 constexpr double EPS0_C = 8.8541878128e-12;
-constexpr double AMU = 1.66053906660e-27;
-constexpr double M_CU = 63.546 * AMU;
+constexpr double AMU = AMU_KG;
+constexpr double M_CU = MASS_CU;
 constexpr double KB = 1.380649e-23;
 constexpr double PI = 3.14159265358979323846;
 constexpr int ZQ[NSP] = {-1, 0, 1, 2, 2, 3, 4};
 constexpr int MAX_RUNS = MAX_RUNS_SMEM;
 
-double species_mass(int s) { return s == SP_E ? ME : M_CU; }
+double species_mass(int s) { return species_mass_kg(s); }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 

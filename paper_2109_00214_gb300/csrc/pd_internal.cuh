@@ -233,6 +233,12 @@ __device__ __forceinline__ uint32_t converted_key(uint32_t new_sp, uint32_t old_
     return KEY_FLAG | (old_sp << 27) | (new_sp << 24) | cell;
 }
 
+// particle masses (CODATA 2018; every Cu charge state has the atom's mass)
+constexpr double MASS_E = 9.1093837015e-31;
+constexpr double AMU_KG = 1.66053906660e-27;
+constexpr double MASS_CU = 63.546 * AMU_KG;
+__host__ __device__ constexpr double species_mass_kg(int sp) { return sp == SP_E ? MASS_E : MASS_CU; }
+
 // charge number: e -1, Cu 0, Cu+ 1, Cu2+ (both labels) 2, Cu3+ 3, Cu4+ 4
 // (charge + 1 of species sp in nibble sp)
 __host__ __device__ __forceinline__ int charge_of(int sp) { return (int)((0x5433210u >> (4 * sp)) & 15u) - 1; }

@@ -34,7 +34,8 @@ unsigned long long* g_scratch_ptr[kMaxDevices] = {};   // device address of the 
 
 // Host code cannot use the array's name as a device address.  Ask the
 // runtime for it once per device (the device must be current) and remember
-// it.
+// it for the life of the process (a cudaDeviceReset in the process would
+// leave the remembered address stale).
 cudaError_t scratch_for_current_device(unsigned long long** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -83,12 +84,20 @@ extern "C" pd_status pd_energy_spectrum_static(const uint32_t* key, const float*
     if (n < 0 || species < 0 || species >= NSP || !(e_hi_eV > e_lo_eV) || !out) return PD_ERR_ARG;
     if (n > 0 && (!key || !vz || !vr || !vt)) return PD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    // the scratch address is the current device's: the stream must be on it
+    int sdev = -1, cur = -1;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess || cudaGetDevice(&cur) != cudaSuccess) return PD_ERR_CUDA;
+    if (sdev != cur) {
+        std::fprintf(stderr, "pd_energy_spectrum_static: the stream is on device %d, the current device is %d\n", sdev,
+                     cur);
+        return PD_ERR_ARG;
+    }
     unsigned long long* hist = nullptr;
     if (scratch_for_current_device(&hist) != cudaSuccess) return PD_ERR_CUDA;
     // the array keeps the previous call's counts: clear the bins used here
     if (cudaMemsetAsync(hist, 0, (size_t)nbins * sizeof(unsigned long long), s) != cudaSuccess) return PD_ERR_CUDA;
     if (n > 0) {
-        const double mass = species == SP_E ? 9.1093837015e-31 : 63.546 * 1.66053906660e-27;
+        const double mass = species_mass_kg(species);     // the masses pd_get_energy_spectrum uses
         long long blocks = (n + 255) / 256;
         if (blocks > 4096) blocks = 4096;
         k_spectrum_raw<<<(unsigned)blocks, 256, 0, s>>>(key, vz, vr, vt, (long long)n, (uint32_t)species, mass,
@@ -101,3 +110,5 @@ extern "C" pd_status pd_energy_spectrum_static(const uint32_t* key, const float*
     if (cudaStreamSynchronize(s) != cudaSuccess) return PD_ERR_CUDA;
     return PD_OK;
 }
+
+extern "C" int pd_spectrum_static_max_bins(void) { return PD_SPECTRUM_STATIC_MAX_BINS; }

@@ -209,7 +209,7 @@ MUTANTS = {
 def _mutant(tmp_path, name):
     old, new = MUTANTS[name]
     src = open(os.path.join(os.path.dirname(oracle.__file__), "pd_oracle.c")).read()
-    assert src.count(old) == 1, name
+    assert src.count(old) >= 1, name          # (every copy: the serial and the OpenMP push)
     path = tmp_path / "mut.c"
     path.write_text(src.replace(old, new))
     so = str(tmp_path / "libmut.so")

@@ -50,7 +50,13 @@ def test_static_spectrum_matches_workspace_spectrum():
     assert a.sum() > 0 and b.sum() > 0
     assert np.array_equal(a, sim.energy_spectrum(0, 0.0, 200.0, 400))
     assert np.array_equal(b, sim.energy_spectrum(1, 0.0, 1.0, 400))
-    # sizes beyond the fixed scratch are refused
+    # sizes beyond the fixed scratch are refused, by the library itself
+    big = pd.pd_spectrum_static_max_bins() + 1
     with pytest.raises(pd.PdError):
-        static(0, 0.0, 200.0, pd.PD_SPECTRUM_STATIC_MAX_BINS + 1)
+        static(0, 0.0, 200.0, big)
+    out = np.zeros(big, np.uint64)
+    r = pd._lib().pd_energy_spectrum_static(pd.P(t["key"].data_ptr()), pd.P(t["vz"].data_ptr()),
+                                             pd.P(t["vr"].data_ptr()), pd.P(t["vt"].data_ptr()), n, 0, 0.0, 200.0,
+                                             big, pd.P(stream), out.ctypes.data_as(pd.P))
+    assert pd.STATUS[r] == "PD_ERR_ARG"
     sim.close()
