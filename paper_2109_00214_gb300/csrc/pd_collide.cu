@@ -472,6 +472,25 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
         L.sorted = __all_sync(FULL, asc);
         // a select sweeps the list once per significant bit, per lookup
         if (L.sorted || lookups * (uint32_t)(L.top + 1) <= 128u) return;
+        if (n <= 64u) {
+            // a short list's table by comparison: the rank of an id is the
+            // number of smaller ids (ids are unique), 32 exchanges per warp
+            uint32_t r0 = 0, r1 = 0;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const uint32_t a = __shfl_sync(FULL, L.ids[0], j), b = __shfl_sync(FULL, L.ids[1], j);
+                const bool va = (uint32_t)j < n, vb = 32u + (uint32_t)j < n;
+                r0 += (va && a < L.ids[0] ? 1u : 0u) + (vb && b < L.ids[0] ? 1u : 0u);
+                r1 += (va && a < L.ids[1] ? 1u : 0u) + (vb && b < L.ids[1] ? 1u : 0u);
+            }
+            uint32_t* table = S.table + slot0;
+            if ((uint32_t)lane < n) table[r0] = (uint32_t)lane;
+            if (32u + (uint32_t)lane < n) table[r1] = 32u + (uint32_t)lane;
+            __syncwarp();
+            L.table = table;
+            L.cached = false;
+            return;
+        }
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             const uint32_t q = (uint32_t)lane + 32u * k;
