@@ -253,7 +253,7 @@ pd_status pd_get_energy_spectrum(pd_sim* sim, int species, double e_lo_eV, doubl
  * measurement).  enable != 0 starts recording; pd_profile_read synchronises
  * and returns, per kernel id, total milliseconds and launch counts, then
  * clears.  Kernel ids: see pd_kernel_name. */
-#define PD_NKERNELS 12
+#define PD_NKERNELS 13
 pd_status pd_profile_enable(pd_sim* sim, int enable);
 pd_status pd_profile_read(pd_sim* sim, double* ms /* PD_NKERNELS */, uint64_t* launches /* PD_NKERNELS */);
 const char* pd_kernel_name(int kernel_id);

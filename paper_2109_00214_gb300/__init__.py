@@ -31,7 +31,7 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 43
-PD_NKERNELS = 12
+PD_NKERNELS = 13
 GEOM = {"rz": 0, "xy_periodic": 1}
 COUNTER_NAMES = (["ev_el", "ev_exc", "ev_si", "ev_di", "ev_sw", "nulls", "consumed", "thr_rej",
                   "ratio_viol", "iso_fallback", "cand_total", "emitted_e", "emitted_cu"]
@@ -583,7 +583,7 @@ def pd_kernel_name(k):
 
 
 KERNEL_NAMES = ["inject", "push", "scan_bins", "scatter", "ncand", "scan_cand", "collide", "finalize",
-                "poisson", "efield", "memset", "other"]
+                "poisson", "efield", "memset", "other", "coulomb"]
 
 
 def pd_last_error(h):

@@ -167,9 +167,10 @@ Layout make_layout(const std::vector<pd_config>& cf) {
 }
 
 const char* const KNAMES[PD_NKERNELS] = {"inject",  "push",     "scan_bins", "scatter", "ncand",  "scan_cand",
-                                         "collide", "finalize", "poisson",   "efield",  "memset", "other"};
+                                         "collide", "finalize", "poisson",   "efield",  "memset", "other",
+                                         "coulomb"};
 enum { K_INJECT, K_PUSH, K_SCAN_BINS, K_SCATTER, K_NCAND, K_SCAN_CAND, K_COLLIDE, K_FINALIZE, K_POISSON, K_EFIELD,
-       K_MEMSET, K_OTHER };
+       K_MEMSET, K_OTHER, K_COULOMB };
 
 }  // namespace
 
@@ -716,6 +717,10 @@ pd_status issue_step(pd_sim* s, bool capturing) {
                        s->rho_e, s->rho_h,
                        s->xsE, s->xs, s->cw, P, s->cc, nbins, s->sms, grid_for(s, s->tune.collide_blocks_per_sm),
                        s->stream);
+    }
+    if (P.coulomb) {
+        Timed t(s, K_COULOMB, capturing, 1);
+        launch_coulomb(s->A, s->B, s->off, s->bcnt, s->st, P, s->cc, s->cw, s->sms, s->stream);
     }
     {
         Timed t(s, K_FINALIZE, capturing, 1);

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__
 // its 256 counters.
 __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
                                          uint32_t lookups, const RankScratch& S, uint32_t* sbuf, int lane,
-                                         int id_top) {
+                                         int id_top, bool want_table = false) {
     const uint32_t* base = ids + slot0;
     L.n = n;
     L.table = nullptr;
@@ -439,7 +439,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
     L.sorted = false;
     L.sel8 = false;
     L.top = 0;
-    if (!L.cached && lookups <= SELECT_LOOKUPS) {
+    if (!want_table && !L.cached && lookups <= SELECT_LOOKUPS) {
         L.sel8 = true;
         L.top = id_top;
         return;
@@ -471,7 +471,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
         L.top = orv ? 31 - __clz((int)orv) : 0;
         L.sorted = __all_sync(FULL, asc);
         // a select sweeps the list once per significant bit, per lookup
-        if (L.sorted || lookups * (uint32_t)(L.top + 1) <= 128u) return;
+        if (L.sorted || (!want_table && lookups * (uint32_t)(L.top + 1) <= 128u)) return;
         if (n <= 64u) {
             // a short list's table by comparison: the rank of an id is the
             // number of smaller ids (ids are unique), 32 exchanges per warp
@@ -881,54 +881,16 @@ __device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k,
 // azimuth; |u| is kept and the change is shared by the reduced mass.  Kn =
 // (q_a q_b)^2 n_L lnL dt / (8 pi eps0^2 m_ab^2).  The float operations are
 // those of the oracle's float build, in the same order.
+//
+// A pair's particles and random numbers do not depend on any velocity: the
+// particles come from keyed permutations of the id ranks, and each pair
+// draws from a stream of its own (twelve uniforms for Z, then the azimuth).
+// So a cell's warp first derives them for 32 pairs at a time, flattened over
+// all the cell's classes, and then applies the pairs in waves that the
+// sequential definition allows to run side by side: the regular pairs of a
+// species with itself (disjoint), each pair of an odd count's closing triple
+// alone, and each round of N_fewer pairs of two species (disjoint) in turn.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ float irwin_hall12(Stream& st) {
-    float z = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 12; ++i) z = z + st.u01();
-    return z - 6.0f;
-}
-
-__device__ bool coulomb_kin(Stream& st, V3& va, V3& vb, float Kn, float fa, float fb_, uint32_t& fb) {
-    const float ux = va.x - vb.x, uy = va.y - vb.y, uz = va.z - vb.z;
-    const float u2 = (ux * ux + uy * uy) + uz * uz;
-    if (!(u2 > 0.0f)) return false;
-    const float u = sqrtf(u2);
-    float var = Kn / (u2 * u);
-    var = var < 1e30f ? var : 1e30f;                // u -> 0: keep delta finite
-    const float z = irwin_hall12(st);
-    const float d = sqrtf(var) * z;
-    // sin(theta) = 2 delta / (1 + delta^2), 1 - cos(theta) = 2 delta^2 / (1 + delta^2)
-    float sth, omc;
-    const float ad = d < 0.0f ? -d : d;
-    if (ad <= 1.0f) {
-        const float d2 = d * d, den = 1.0f + d2;
-        sth = (2.0f * d) / den;
-        omc = (2.0f * d2) / den;
-    } else {
-        const float rr = 1.0f / d, r2 = rr * rr, den = 1.0f + r2;
-        sth = (2.0f * rr) / den;
-        omc = 2.0f / den;
-    }
-    float cph, sph;
-    azimuth(st, cph, sph, fb);
-    const float sc = sth * cph, ss = sth * sph;
-    const float up = sqrtf(ux * ux + uy * uy);
-    float dx, dy, dz;
-    if (up > 0.0f) {
-        const float a1 = ux / up, a2 = uy / up;
-        dx = ((a1 * uz) * sc - (a2 * u) * ss) - ux * omc;
-        dy = ((a2 * uz) * sc + (a1 * u) * ss) - uy * omc;
-        dz = -(up * sc) - uz * omc;
-    } else {                                         // u along the third axis
-        dx = uz * sc;
-        dy = uz * ss;
-        dz = -(uz * omc);
-    }
-    va.x = va.x + fa * dx; va.y = va.y + fa * dy; va.z = va.z + fa * dz;
-    vb.x = vb.x - fb_ * dx; vb.y = vb.y - fb_ * dy; vb.z = vb.z - fb_ * dz;
-    return true;
-}
 
 // Pseudo-random permutation of [0, n): four Feistel rounds (Luby and Rackoff)
 // on 2h bits, 4^h >= n, with an integer mixing round function, walked back
@@ -941,9 +903,13 @@ __device__ __forceinline__ uint32_t fe_round(uint32_t x, uint32_t k) {
     t ^= t >> 13;
     return t;
 }
-__device__ uint32_t perm_index(uint32_t x, uint32_t n, const uint4& key) {
+// h of the permutation of [0, n): the least h >= 1 with 4^h >= n
+__device__ __forceinline__ int perm_bits(uint32_t n) {
     int h = 1;
     while ((1ull << (2 * h)) < (unsigned long long)n) ++h;
+    return h;
+}
+__device__ uint32_t perm_index(uint32_t x, uint32_t n, const uint4& key, int h) {
     const uint32_t mask = (1u << h) - 1u;
     const unsigned long long lim = 1ull << (2 * h);
     uint32_t y = x;
@@ -963,194 +929,378 @@ __device__ uint32_t perm_index(uint32_t x, uint32_t n, const uint4& key) {
     return x;
 }
 
-__device__ __forceinline__ uint4 stream_key(Stream& st) {
-    const uint32_t a = st.next(), b = st.next(), c = st.next(), d = st.next();
-    return make_uint4(a, b, c, d);
-}
+// uniform on [0, 1) from the top 24 bits of a draw (as Stream::u01)
+__device__ __forceinline__ float u01_of(uint32_t x) { return __fmul_rn((float)(x >> 8), 5.9604644775390625e-08f); }
 
-// position of each lane's rank in list L (has: the lane has one; nb: lanes
-// 0..nb-1 may have one); called by the whole warp
-__device__ __forceinline__ uint32_t rank_position(const IdList& L, uint32_t rank, bool has, uint32_t nb, int lane) {
-    if (L.sorted) return rank;
-    if (L.table) return has ? L.table[rank] : 0u;
-    uint32_t pos = 0;
-    for (uint32_t q = 0; q < nb; ++q) {
-        const uint32_t p = select_rank_list(L, __shfl_sync(FULL, rank, (int)q), lane);
-        if ((uint32_t)lane == q) pos = p;
+// The draws of one Coulomb pair from its stream: Z (the Irwin-Hall sum of
+// the first twelve uniforms, three Philox blocks) and the azimuth (points of
+// the square from the following blocks, two per block, until one falls in
+// the unit disc; fail after 64 tries, as azimuth()).
+__device__ void coul_draws(uint32_t subject, uint32_t step, uint32_t sid, uint32_t seed, uint32_t run, float& z,
+                           float& c, float& s, bool& fail) {
+    uint4 ctr = make_uint4(subject, step, sid, 0u);
+    const uint2 key = make_uint2(seed, run);
+    float zz = 0.0f;
+#pragma unroll 1
+    for (int b = 0; b < 3; ++b) {
+        const uint4 r = philox4x32_10(ctr, key);
+        ctr.w += 1u;
+        zz = zz + u01_of(r.x);
+        zz = zz + u01_of(r.y);
+        zz = zz + u01_of(r.z);
+        zz = zz + u01_of(r.w);
     }
-    return pos;
-}
-
-// One list paired with itself, by the cell's warp: two by two in a random
-// order (lanes take disjoint pairs), an odd count ending with a triple of
-// three pairs at half the time step (lane 0, in order); a particle whose
-// species changed this step is left out.  Returns the lane's applied pairs.
-__device__ uint32_t pairs_same(Particles& A, const IdList& L, uint32_t base, uint32_t N, int sp, int cls, float Kn,
-                               float f, uint32_t lc, const RunInfo* RI, DevState* st, int lane, uint32_t& fb) {
-    uint32_t done = 0;
-    if (N < 2u) return 0;
-    Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)cls, RI->seed, RI->run);
-    const uint4 key = stream_key(ps);
-    const uint32_t P = N / 2u - (N % 2u);            // regular pairs
-    for (uint32_t m0 = 0; m0 < P; m0 += 32) {
-        const uint32_t nb = min(32u, P - m0);
-        const uint32_t k = m0 + (uint32_t)lane;
-        const bool has = (uint32_t)lane < nb;
-        const uint32_t ra = has ? perm_index(2u * k, N, key) : 0u;
-        const uint32_t rb = has ? perm_index(2u * k + 1u, N, key) : 0u;
-        const uint32_t pa = rank_position(L, ra, has, nb, lane);
-        const uint32_t pb = rank_position(L, rb, has, nb, lane);
-        if (has && pa < N && pb < N) {
-            const uint32_t ia = base + pa, ib = base + pb;
-            const uint32_t ka = A.key[ia], kb = A.key[ib];
-            if (!(ka & KEY_FLAG) && (int)key_species(ka) == sp && !(kb & KEY_FLAG) && (int)key_species(kb) == sp) {
-                V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
-                Stream rs(lc, st->step, sid_coul(cls, k), RI->seed, RI->run);
-                if (coulomb_kin(rs, va, vb, Kn, f, f, fb)) {
-                    A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
-                    A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
-                    ++done;
-                }
+    z = zz - 6.0f;
+    fail = false;
+#pragma unroll 1
+    for (int b = 0; b < 32; ++b) {
+        const uint4 r = philox4x32_10(ctr, key);
+        ctr.w += 1u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float u1 = 2.0f * u01_of(h ? r.z : r.x) - 1.0f;
+            const float u2 = 2.0f * u01_of(h ? r.w : r.y) - 1.0f;
+            const float q = u1 * u1 + u2 * u2;
+            if (q < 1.0f && q > 0.0f) {
+                const float rq = sqrtf(q);
+                c = u1 / rq;
+                s = u2 / rq;
+                return;
             }
-        } else if (has) {
-            set_error(st, ERR_BOUNDS);
         }
     }
-    __syncwarp();
-    if (N % 2u) {                                    // the last three: a triple, in order
-        const bool has = lane < 3;
-        const uint32_t rk = has ? perm_index(N - 3u + (uint32_t)lane, N, key) : 0u;
-        const uint32_t pk = rank_position(L, rk, has, 3u, lane);
-        const uint32_t p0 = __shfl_sync(FULL, pk, 0), p1 = __shfl_sync(FULL, pk, 1), p2 = __shfl_sync(FULL, pk, 2);
-        if (lane == 0) {
-            if (p0 < N && p1 < N && p2 < N) {
-                const uint32_t t[3] = {base + p0, base + p1, base + p2};
-                const float Kh = Kn * 0.5f;
-                for (int q = 0; q < 3; ++q) {
-                    const uint32_t ia = t[q], ib = t[(q + 1) % 3];
-                    const uint32_t ka = A.key[ia], kb = A.key[ib];
-                    if ((ka & KEY_FLAG) || (int)key_species(ka) != sp || (kb & KEY_FLAG) || (int)key_species(kb) != sp)
-                        continue;
-                    V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
-                    Stream rs(lc, st->step, sid_coul(cls, P + (uint32_t)q), RI->seed, RI->run);
-                    if (coulomb_kin(rs, va, vb, Kh, f, f, fb)) {
-                        A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
-                        A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
-                        ++done;
-                    }
-                }
+    fail = true;
+    c = 1.0f;
+    s = 0.0f;
+}
+
+// One pair's turn (after its draws): false when u = 0 (nothing to turn).
+__device__ __forceinline__ bool coulomb_turn(V3& va, V3& vb, float Kn, float fa, float fb_, float z, float cph,
+                                             float sph) {
+    const float ux = va.x - vb.x, uy = va.y - vb.y, uz = va.z - vb.z;
+    const float u2 = (ux * ux + uy * uy) + uz * uz;
+    if (!(u2 > 0.0f)) return false;
+    const float u = sqrtf(u2);
+    float var = Kn / (u2 * u);
+    var = var < 1e30f ? var : 1e30f;                // u -> 0: keep delta finite
+    const float d = sqrtf(var) * z;
+    // sin(theta) = 2 delta / (1 + delta^2), 1 - cos(theta) = 2 delta^2 / (1 + delta^2)
+    float sth, omc;
+    const float ad = d < 0.0f ? -d : d;
+    if (ad <= 1.0f) {
+        const float d2 = d * d, den = 1.0f + d2;
+        sth = (2.0f * d) / den;
+        omc = (2.0f * d2) / den;
+    } else {
+        const float rr = 1.0f / d, r2 = rr * rr, den = 1.0f + r2;
+        sth = (2.0f * rr) / den;
+        omc = 2.0f / den;
+    }
+    const float sc = sth * cph, ss = sth * sph;
+    const float up = sqrtf(ux * ux + uy * uy);
+    float dx, dy, dz;
+    if (up > 0.0f) {
+        const float a1 = ux / up, a2 = uy / up;
+        dx = ((a1 * uz) * sc - (a2 * u) * ss) - ux * omc;
+        dy = ((a2 * uz) * sc + (a1 * u) * ss) - uy * omc;
+        dz = -(up * sc) - uz * omc;
+    } else {                                         // u along the third axis
+        dx = uz * sc;
+        dy = uz * ss;
+        dz = -(uz * omc);
+    }
+    va.x = va.x + fa * dx; va.y = va.y + fa * dy; va.z = va.z + fa * dz;
+    vb.x = vb.x - fb_ * dx; vb.y = vb.y - fb_ * dy; vb.z = vb.z - fb_ * dz;
+    return true;
+}
+
+// Classes of a cell: 0 the electrons with themselves, 1 + i the electrons
+// with ion species i (Cu+, Cu2+ SW, Cu2+ DI, Cu3+, Cu4+), on heavy steps
+// 6.. the ion species a <= b (in order).  Lists: 0 the electrons, 1 + i ion
+// species i.
+constexpr int COUL_NCLS = 21;
+constexpr int COUL_NLIST = 6;
+// charged particles of a cell whose velocities its warp holds in shared
+// memory (in the words of its rank-table sort buffer, free once the tables
+// are built)
+constexpr int COUL_CACHE = 512;
+constexpr int COUL_WARPS = 4;           // warps of a k_coulomb block
+constexpr int COUL_SBUF = 4 * RANK_WARP_MAX + 256;   // words of a warp's sort buffer
+static_assert(COUL_CACHE * 13 <= COUL_SBUF * 4, "velocity cache exceeds the sort buffer");
+
+struct CoulClass {
+    uint4 k1, k2;          // permutation keys: of the one species; or of the more and the fewer
+    float Kn, fa, fb;
+    uint32_t start;        // first pair in the cell's flattened order
+    uint32_t npairs;
+    uint32_t P;            // one species: regular pairs; two: the fewer's count (a round)
+    uint32_t N;            // one species: its count; two: the more numerous's
+    uint8_t la, lb;        // the lists of the pair's first and second particle
+    uint8_t cls, a_many;   // a_many: list la is the more numerous (la on a tie)
+};
+struct CoulWarp {
+    CoulClass cl[COUL_NCLS];
+    uint32_t base[COUL_NLIST], n[COUL_NLIST];
+    uint32_t coff[COUL_NLIST], cn[COUL_NLIST];   // a list's place and count in the velocity cache
+    uint32_t sorted;       // bit l: list l's ids ascend (rank = position)
+};
+
+__device__ __forceinline__ void class_lists(int t, int& la, int& lb) {
+    if (t == 0) {
+        la = lb = 0;
+    } else if (t < 6) {
+        la = 0;
+        lb = t;
+    } else {
+        int idx = t - 6, a = 0;
+        while (idx >= 5 - a) {
+            idx -= 5 - a;
+            ++a;
+        }
+        la = 1 + a;
+        lb = 1 + a + idx;
+    }
+}
+__device__ __forceinline__ int list_species(int l) { return l == 0 ? SP_E : SP_CUP + l - 1; }
+
+// The Coulomb pairs (after all cells' DSMC classes: cells are independent,
+// so this is the order of cell-by-cell processing): one warp per cell with
+// charged particles, grid-stride over the cells, on the lists of the step's
+// start; a particle whose species changed this step is left out.
+__global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+                                                   const uint32_t* __restrict__ cnt, DevState* st, KParams P,
+                                                   CollConsts cc, const double* __restrict__ cw) {
+    __shared__ uint32_t s_sort[COUL_WARPS][COUL_SBUF];   // per-warp rank-table sort, then velocity cache
+    __shared__ CoulWarp s_cw[COUL_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = (threadIdx.x >> 5) & (COUL_WARPS - 1);
+    uint32_t* sbuf = s_sort[wib];
+    CoulWarp& W = s_cw[wib];
+    const uint32_t C = P.ncell;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    for (uint32_t c = warp0; c < C; c += nwarps) {
+        // the cell's charged lists (lane l reads list l)
+        uint32_t nl = 0, bl = 0;
+        if (lane < COUL_NLIST) {
+            const int sp = list_species(lane);
+            if (sp < P.nsp) {
+                const uint32_t b = (uint32_t)sp * C + c;
+                nl = cnt[b];
+                bl = off[b];
+            }
+        }
+        const uint32_t Ne = __shfl_sync(FULL, nl, 0);
+        if (Ne == 0u && !P.heavy_step) continue;
+        // the class table: lane t takes class t
+        int la = 0, lb = 0;
+        if (lane < COUL_NCLS) class_lists(lane, la, lb);
+        const uint32_t Na = __shfl_sync(FULL, nl, la), Nb = __shfl_sync(FULL, nl, lb);
+        bool on = false;
+        uint32_t np = 0, Pk = 0, Nk = 0;
+        bool a_many = true;
+        if (lane < COUL_NCLS) {
+            if (la == lb) {
+                on = Na >= 2u && (lane == 0 || P.heavy_step);
+                Pk = Na / 2u - (Na % 2u);
+                np = Pk + (Na % 2u ? 3u : 0u);
+                Nk = Na;
             } else {
-                set_error(st, ERR_BOUNDS);
+                on = Na >= 1u && Nb >= 1u && (lane < 6 || P.heavy_step);
+                a_many = Na >= Nb;
+                Nk = a_many ? Na : Nb;
+                Pk = a_many ? Nb : Na;
+                np = Nk;
+            }
+        }
+        const unsigned mact = __ballot_sync(FULL, on);
+        if (mact == 0u) continue;
+        const int r = run_of(P, c);
+        const RunInfo* RI = &P.runs[r];
+        const uint32_t lc = c - RI->cell_base;
+        if (!on) np = 0;
+        uint32_t incl = np;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t T = __shfl_sync(FULL, incl, 31);
+        const int nact = __popc(mact);
+        if (on) {
+            const uint32_t row = RI->row_base + lc % (uint32_t)RI->nr;
+            const double w = lane < 6 ? cw[row] : cw[P.cw_heavy + row];
+            const uint32_t Nf = la == lb ? Na : min(Na, Nb);
+            CoulClass K;
+            Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)lane, RI->seed, RI->run);
+            K.k1 = make_uint4(ps.next(), ps.next(), ps.next(), ps.next());
+            K.k2 = make_uint4(0u, 0u, 0u, 0u);
+            if (la != lb) K.k2 = make_uint4(ps.next(), ps.next(), ps.next(), ps.next());
+            K.Kn = (float)(cc.kc[lane] * (double)Nf * w);
+            K.fa = lane >= 1 && lane < 6 ? cc.a_e : 0.5f;
+            K.fb = lane >= 1 && lane < 6 ? cc.a_t : 0.5f;
+            K.start = incl - np;
+            K.npairs = np;
+            K.P = Pk;
+            K.N = Nk;
+            K.la = (uint8_t)la;
+            K.lb = (uint8_t)lb;
+            K.cls = (uint8_t)lane;
+            K.a_many = a_many ? 1 : 0;
+            W.cl[__popc(mact & lt)] = K;
+        }
+        // lists any class uses: rank tables, then the velocities in shared
+        // memory when they fit
+        unsigned used = on ? ((1u << la) | (1u << lb)) : 0u;
+        used = __reduce_or_sync(FULL, used);
+        const uint32_t idn = P.rs[r].id_next;
+        const int id_top = idn > 1u ? 31 - __clz((int)(idn - 1u)) : 0;
+        uint32_t sorted = 0, tot = 0;
+        for (int l = 0; l < COUL_NLIST; ++l) {
+            const uint32_t n = __shfl_sync(FULL, nl, l), b = __shfl_sync(FULL, bl, l);
+            const bool u = (used >> l) & 1u;
+            if (lane == 0) {
+                W.base[l] = b;
+                W.n[l] = n;
+                W.coff[l] = tot;
+                W.cn[l] = u ? n : 0u;
+            }
+            if (!u) continue;
+            tot += n;
+            IdList L;
+            load_ids(L, A.id, b, n, n, S, sbuf, lane, id_top, true);
+            if (L.sorted) sorted |= 1u << l;
+        }
+        if (lane == 0) W.sorted = sorted;
+        const bool cached = tot <= (uint32_t)COUL_CACHE;
+        float* const cvz = reinterpret_cast<float*>(sbuf);
+        float* const cvr = cvz + COUL_CACHE;
+        float* const cvt = cvr + COUL_CACHE;
+        uint8_t* const touched = reinterpret_cast<uint8_t*>(cvt + COUL_CACHE);
+        __syncwarp();
+        if (cached) {
+            for (int l = 0; l < COUL_NLIST; ++l) {
+                const uint32_t n = W.cn[l], b = W.base[l], co = W.coff[l];
+                for (uint32_t q = (uint32_t)lane; q < n; q += 32) {
+                    cvz[co + q] = A.vz[b + q];
+                    cvr[co + q] = A.vr[b + q];
+                    cvt[co + q] = A.vt[b + q];
+                    touched[co + q] = 0;
+                }
             }
         }
         __syncwarp();
-    }
-    return done;
-}
-
-// Two lists A and B: each particle of the more numerous (A on a tie) once,
-// the k-th of it in a random order with the (k mod N_fewer)-th of the other,
-// in rounds of N_fewer disjoint pairs (rounds in order); the first particle
-// of every pair is A's.  Returns the lane's applied pairs.
-__device__ uint32_t pairs_cross(Particles& A, const IdList& La, uint32_t baseA, uint32_t NA, int spa, const IdList& Lb,
-                                uint32_t baseB, uint32_t NB, int spb, int cls, float Kn, float fa, float fb_,
-                                uint32_t lc, const RunInfo* RI, DevState* st, int lane, uint32_t& fb) {
-    uint32_t done = 0;
-    if (NA == 0u || NB == 0u) return 0;
-    const bool a_many = NA >= NB;
-    const uint32_t Nm = a_many ? NA : NB, Nf = a_many ? NB : NA;
-    Stream ps(lc, st->step, SID_COUL_PERM | (uint32_t)cls, RI->seed, RI->run);
-    const uint4 km = stream_key(ps), kf = stream_key(ps);
-    for (uint32_t r0 = 0; r0 < Nm; r0 += Nf) {
-        const uint32_t re = min(r0 + Nf, Nm);
-        for (uint32_t m0 = r0; m0 < re; m0 += 32) {
-            const uint32_t nb = min(32u, re - m0);
-            const uint32_t k = m0 + (uint32_t)lane;
-            const bool has = (uint32_t)lane < nb;
-            const uint32_t m = has ? perm_index(k, Nm, km) : 0u;
-            const uint32_t f = has ? perm_index(k - r0, Nf, kf) : 0u;
-            const uint32_t pa = rank_position(La, a_many ? m : f, has, nb, lane);
-            const uint32_t pb = rank_position(Lb, a_many ? f : m, has, nb, lane);
-            if (has && pa < NA && pb < NB) {
-                const uint32_t ia = baseA + pa, ib = baseB + pb;
-                const uint32_t ka = A.key[ia], kb = A.key[ib];
-                if (!(ka & KEY_FLAG) && (int)key_species(ka) == spa && !(kb & KEY_FLAG) &&
-                    (int)key_species(kb) == spb) {
-                    V3 va{A.vz[ia], A.vr[ia], A.vt[ia]}, vb{A.vz[ib], A.vr[ib], A.vt[ib]};
-                    Stream rs(lc, st->step, sid_coul(cls, k), RI->seed, RI->run);
-                    if (coulomb_kin(rs, va, vb, Kn, fa, fb_, fb)) {
-                        A.vz[ia] = va.x; A.vr[ia] = va.y; A.vt[ia] = va.z;
-                        A.vz[ib] = vb.x; A.vr[ib] = vb.y; A.vt[ib] = vb.z;
-                        ++done;
+        float* VZ = cached ? cvz : A.vz;
+        float* VR = cached ? cvr : A.vr;
+        float* VT = cached ? cvt : A.vt;
+        uint32_t n_ee = 0, n_ei = 0, n_ii = 0, n_fb = 0;
+        int jw = 0;                      // the class of the wave being applied
+        for (uint32_t c0 = 0; c0 < T; c0 += 32) {
+            // lane q: pair c0 + q's particles and draws
+            const uint32_t p = c0 + (uint32_t)lane;
+            uint32_t ia = 0, ib = 0;
+            float z = 0.0f, cph = 1.0f, sph = 0.0f, Kn = 0.0f;
+            bool valid = false, fail = false;
+            if (p < T) {
+                int j = 0;
+                while (j + 1 < nact && W.cl[j + 1].start <= p) ++j;
+                const CoulClass& K = W.cl[j];
+                const uint32_t k = p - K.start;
+                uint32_t ra, rb;
+                Kn = K.Kn;
+                if (K.la == K.lb) {
+                    const uint32_t N = K.N;
+                    const int h = perm_bits(N);
+                    if (k < K.P) {
+                        ra = perm_index(2u * k, N, K.k1, h);
+                        rb = perm_index(2u * k + 1u, N, K.k1, h);
+                    } else {                     // the closing triple: pair q joins q and q + 1 (mod 3)
+                        const uint32_t q = k - K.P;
+                        ra = perm_index(N - 3u + q, N, K.k1, h);
+                        rb = perm_index(N - 3u + (q + 1u) % 3u, N, K.k1, h);
+                        Kn = Kn * 0.5f;
+                    }
+                } else {
+                    const uint32_t m = perm_index(k, K.N, K.k1, perm_bits(K.N));
+                    const uint32_t f = perm_index(k % K.P, K.P, K.k2, perm_bits(K.P));
+                    ra = K.a_many ? m : f;
+                    rb = K.a_many ? f : m;
+                }
+                const int la_ = K.la, lb_ = K.lb;
+                const uint32_t na = W.n[la_], nb = W.n[lb_], ba = W.base[la_], bb = W.base[lb_];
+                const uint32_t pa = (W.sorted >> la_) & 1u ? ra : S.table[ba + ra];
+                const uint32_t pb = (W.sorted >> lb_) & 1u ? rb : S.table[bb + rb];
+                if (pa < na && pb < nb) {
+                    const uint32_t ka = A.key[ba + pa], kb = A.key[bb + pb];
+                    valid = !(ka & KEY_FLAG) && (int)key_species(ka) == list_species(la_) && !(kb & KEY_FLAG) &&
+                            (int)key_species(kb) == list_species(lb_);
+                    ia = cached ? W.coff[la_] + pa : ba + pa;
+                    ib = cached ? W.coff[lb_] + pb : bb + pb;
+                    if (valid)
+                        coul_draws(lc, st->step, sid_coul(K.cls, k), RI->seed, RI->run, z, cph, sph, fail);
+                } else {
+                    set_error(st, ERR_BOUNDS);   // ids not unique: corrupt state, never index with it
+                }
+            }
+            // the chunk's pairs in waves, in order
+            const uint32_t c1 = min(c0 + 32u, T);
+            for (uint32_t pw = c0; pw < c1;) {
+                while (pw >= W.cl[jw].start + W.cl[jw].npairs) ++jw;
+                const CoulClass& K = W.cl[jw];
+                const uint32_t k = pw - K.start;
+                uint32_t we;
+                if (K.la == K.lb) we = k < K.P ? K.start + K.P : pw + 1u;
+                else we = K.start + min((k / K.P + 1u) * K.P, K.N);
+                const uint32_t e = min(we, c1);
+                const int src = (int)(pw - c0) + lane;
+                const uint32_t wa = __shfl_sync(FULL, ia, src & 31), wb = __shfl_sync(FULL, ib, src & 31);
+                const float wz = __shfl_sync(FULL, z, src & 31), wc = __shfl_sync(FULL, cph, src & 31);
+                const float ws = __shfl_sync(FULL, sph, src & 31), wk = __shfl_sync(FULL, Kn, src & 31);
+                const bool wv = __shfl_sync(FULL, valid, src & 31), wf = __shfl_sync(FULL, fail, src & 31);
+                if (pw + (uint32_t)lane < e && wv) {
+                    V3 va{VZ[wa], VR[wa], VT[wa]}, vb{VZ[wb], VR[wb], VT[wb]};
+                    if (coulomb_turn(va, vb, wk, K.fa, K.fb, wz, wc, ws)) {
+                        VZ[wa] = va.x; VR[wa] = va.y; VT[wa] = va.z;
+                        VZ[wb] = vb.x; VR[wb] = vb.y; VT[wb] = vb.z;
+                        if (cached) {
+                            touched[wa] = 1;
+                            touched[wb] = 1;
+                        }
+                        if (K.cls == 0) ++n_ee;
+                        else if (K.cls < 6) ++n_ei;
+                        else ++n_ii;
+                        if (wf) ++n_fb;
                     }
                 }
-            } else if (has) {
-                set_error(st, ERR_BOUNDS);
-            }
-            __syncwarp();
-        }
-    }
-    return done;
-}
-
-// The Coulomb pairs of one cell (after its DSMC classes), by its warp, on
-// the lists of the step's start: class 0 pairs the electrons with
-// themselves, class 1 + i the electrons with ion species i (Cu+, Cu2+ SW,
-// Cu2+ DI, Cu3+, Cu4+), with the electron collision step; on heavy steps,
-// classes 6.. pair the ion species with themselves and each other (species
-// a <= b in order) with the heavy step.  n_L is the density of the fewer of
-// the two (of the species itself in a class of one species).
-// look_ion[i]: the ion list's lookups over all classes (as k_ncand counts).
-__device__ __forceinline__ void coulomb_cell(Particles& A, CellCtx& cx, const RankScratch& S, uint32_t* sbuf,
-                             const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt, uint32_t C,
-                             uint32_t c, uint32_t lc, uint32_t look_e,
-                             const uint32_t (&look_ion)[5], int nsp, int heavy_step, int id_top, int lane,
-                             DevState* st, const CollConsts& cc, const double* __restrict__ cw, uint32_t cw_heavy) {
-    const RunInfo* RI = cx.RI;
-    const uint32_t e_base = off[c], Ne = cnt[c];
-    const uint32_t row = RI->row_base + lc % (uint32_t)RI->nr;
-    const double wv = cw[row];
-    uint32_t Ni[5], ib[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
-        const bool has = SP_CUP + i < nsp;
-        ib[i] = has ? off[b] : 0u;
-        Ni[i] = has ? cnt[b] : 0u;
-    }
-    if (Ne > 0u) {
-        IdList el;
-        load_ids(el, A.id, e_base, Ne, look_e, S, sbuf, lane, id_top);
-        cx.coul_ee += pairs_same(A, el, e_base, Ne, SP_E, 0, (float)(cc.kc[0] * (double)Ne * wv), 0.5f, lc, RI, st,
-                                 lane, cx.fb);
-        for (int i = 0; i < 5; ++i) {
-            if (Ni[i] == 0u) continue;
-            IdList il;
-            load_ids(il, A.id, ib[i], Ni[i], look_ion[i], S, sbuf, lane, id_top);
-            const uint32_t Nf = min(Ne, Ni[i]);
-            cx.coul_ei += pairs_cross(A, el, e_base, Ne, SP_E, il, ib[i], Ni[i], SP_CUP + i, 1 + i,
-                                      (float)(cc.kc[1 + i] * (double)Nf * wv), cc.a_e, cc.a_t, lc, RI, st, lane, cx.fb);
-        }
-    }
-    if (!heavy_step) return;
-    const double wvh = cw[cw_heavy + row];
-    int cls = 6;
-    for (int a = 0; a < 5; ++a)
-        for (int b = a; b < 5; ++b, ++cls) {
-            if (Ni[a] == 0u || Ni[b] == 0u || (a == b && Ni[a] < 2u)) continue;
-            const uint32_t Nf = a == b ? Ni[a] : min(Ni[a], Ni[b]);
-            const float Kn = (float)(cc.kc[cls] * (double)Nf * wvh);
-            IdList la;
-            load_ids(la, A.id, ib[a], Ni[a], look_ion[a], S, sbuf, lane, id_top);
-            if (a == b) {
-                cx.coul_ii += pairs_same(A, la, ib[a], Ni[a], SP_CUP + a, cls, Kn, 0.5f, lc, RI, st, lane, cx.fb);
-            } else {
-                IdList lb;
-                load_ids(lb, A.id, ib[b], Ni[b], look_ion[b], S, sbuf, lane, id_top);
-                cx.coul_ii += pairs_cross(A, la, ib[a], Ni[a], SP_CUP + a, lb, ib[b], Ni[b], SP_CUP + b, cls, Kn, 0.5f,
-                                          0.5f, lc, RI, st, lane, cx.fb);
+                __syncwarp();
+                pw = e;
             }
         }
+        if (cached) {
+            // the velocities the pairs changed back to their slots
+            for (uint32_t i = (uint32_t)lane; i < tot; i += 32) {
+                if (!touched[i]) continue;
+                int l = 0;
+                while (i >= W.coff[l] + W.cn[l]) ++l;
+                const uint32_t slot = W.base[l] + (i - W.coff[l]);
+                A.vz[slot] = cvz[i];
+                A.vr[slot] = cvr[i];
+                A.vt[slot] = cvt[i];
+            }
+        }
+        __syncwarp();
+        const uint32_t ee = __reduce_add_sync(FULL, n_ee), ei = __reduce_add_sync(FULL, n_ei);
+        const uint32_t ii = __reduce_add_sync(FULL, n_ii), fb = __reduce_add_sync(FULL, n_fb);
+        if (lane == 0) {
+            RunState& rsv = P.rs[r];
+            if (ee) atomicAdd(&rsv.ctr[C_COUL_EE], (unsigned long long)ee);
+            if (ei) atomicAdd(&rsv.ctr[C_COUL_EI], (unsigned long long)ei);
+            if (ii) atomicAdd(&rsv.ctr[C_COUL_II], (unsigned long long)ii);
+            if (fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)fb);
+        }
+    }
 }
 
 template <bool EXT>
@@ -1379,64 +1529,6 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
             if (cx.thr) atomicAdd(&rsv.ctr[C_THR], (unsigned long long)cx.thr);
             if (cx.viol) atomicAdd(&rsv.ctr[C_VIOL], (unsigned long long)cx.viol);
             if (cx.fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)cx.fb);
-        }
-    }
-}
-
-// The Coulomb pairs (after all cells' DSMC classes: cells are independent,
-// so this is the order of cell-by-cell processing): one warp per cell with
-// charged particles, grid-stride over the cells.  The lists' lookups are
-// counted as k_ncand counted them, so the rank-table choices agree.
-__global__ void __launch_bounds__(128, 3) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
-                                                   const uint32_t* __restrict__ cnt,
-                                                   const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
-                                                   DevState* st, KParams P, CollConsts cc,
-                                                   const double* __restrict__ cw) {
-    __shared__ uint32_t s_sort[4][4 * RANK_WARP_MAX + 256];   // per-warp rank-table sort
-    const int lane = threadIdx.x & 31;
-    uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
-    const uint32_t C = P.ncell;
-    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = warp0; c < C; c += nwarps) {
-        const uint32_t Ne = cnt[c];
-        if (Ne == 0u && !P.heavy_step) continue;
-        uint32_t Ni[5], nion = 0;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const uint32_t b = (uint32_t)(SP_CUP + i) * C + c;
-            Ni[i] = SP_CUP + i < P.nsp ? cnt[b] : 0u;
-            nion += Ni[i];
-        }
-        if (Ne < 2u && nion == 0u) continue;         // nothing to pair
-        const int r = run_of(P, c);
-        CellCtx cx;
-        cx.cell = c;
-        cx.RI = &P.runs[r];
-        cx.geom = P.geom;
-        cx.fb = 0;
-        cx.coul_ee = cx.coul_ei = cx.coul_ii = 0;
-        const uint32_t lc = c - cx.RI->cell_base;
-        const uint4 n = nc[c];
-        const uint4 n2 = P.charge_max >= 3 ? nc2[c] : make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t look_e = n.x + n.y + n2.x + n2.y + n2.z + (Ne > 0u ? Ne : 0u);
-        const uint32_t look_ion[5] = {n.y + n.z, n2.x, n2.y, n2.z, 0u};
-        uint32_t look_all[5];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) look_all[i] = look_ion[i] + Ni[i];
-        const uint32_t idn = P.rs[r].id_next;
-        const int id_top = idn > 1u ? 31 - __clz((int)(idn - 1u)) : 0;
-        coulomb_cell(A, cx, S, sbuf, off, cnt, C, c, lc, look_e, look_all, P.nsp, P.heavy_step, id_top, lane, st, cc, cw,
-                     P.cw_heavy);
-        // every lane applied pairs: sum the warp's counts
-        const uint32_t ee = __reduce_add_sync(FULL, cx.coul_ee), ei = __reduce_add_sync(FULL, cx.coul_ei);
-        const uint32_t ii = __reduce_add_sync(FULL, cx.coul_ii), fb = __reduce_add_sync(FULL, cx.fb);
-        if (lane == 0) {
-            RunState& rsv = P.rs[r];
-            if (ee) atomicAdd(&rsv.ctr[C_COUL_EE], (unsigned long long)ee);
-            if (ei) atomicAdd(&rsv.ctr[C_COUL_EI], (unsigned long long)ei);
-            if (ii) atomicAdd(&rsv.ctr[C_COUL_II], (unsigned long long)ii);
-            if (fb) atomicAdd(&rsv.ctr[C_ISOFB], (unsigned long long)fb);
         }
     }
 }
@@ -1759,8 +1851,13 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
     else
         k_collide<false><<<grid, 128, 0, s>>>(A, S, off, cnt, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
                                               cc, nbins);
-    // one wave of resident blocks (three per SM), grid-stride over the cells
-    if (P.coulomb) k_coulomb<<<sms * 3, 128, 0, s>>>(A, S, off, cnt, nc, nc2, st, P, cc, cw);
+}
+void launch_coulomb(const Particles& A, const Particles& B, const uint32_t* off, const uint32_t* cnt, DevState* st,
+                    const KParams& P, const CollConsts& cc, const double* cw, int sms, cudaStream_t s) {
+    const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
+                        reinterpret_cast<uint32_t*>(B.vz), B.id};
+    // one wave of resident blocks, grid-stride over the cells
+    k_coulomb<<<sms * 4, 32 * COUL_WARPS, 0, s>>>(A, S, off, cnt, st, P, cc, cw);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {

@@ -107,6 +107,9 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
                     DevState* st, long long* rho_e, long long* rho_h, const float* xsE, const float* xs,
                     const double* cw, const KParams& P, const CollConsts& cc, uint32_t nbins, int sms, int grid,
                     cudaStream_t s);
+// Coulomb pairs (after launch_collide; one launch)
+void launch_coulomb(const Particles& A, const Particles& B, const uint32_t* off, const uint32_t* cnt, DevState* st,
+                    const KParams& P, const CollConsts& cc, const double* cw, int sms, cudaStream_t s);
 // ion-impact sputtering after the push (one block per run): the atoms go to
 // the mover records M (mask mm) of tail slots; in_cnt: the movers-into-bin
 // counts of the sort

@@ -4,26 +4,40 @@
 //                 weights of Eq. (10), r-z rotation or periodic wrap,
 //                 absorbing walls, fused with the fixed-point CIC deposit of
 //                 Eq. (9)-(10) and the bookkeeping of the cell sort.
-//   k_bins        per bin: new count, overflow check, closing of the holes
-//                 the push left (short bins; long ones are queued for
+//   k_bins        per heavy bin: new count, overflow check, closing of the
+//                 holes the push left (short bins; long ones are queued for
 //                 k_compact_big, a warp per bin).
-//   k_insert      movers into their new bins.
-//   k_relayout_*  a new slot layout of all bins when a bin ran out of slots.
+//   k_borrow      a full heavy bin takes free slots of the next bin.
+//   k_relayout_*  a new slot layout of the heavy bins when one ran out of
+//                 slots.
+//   k_ebins, k_insert, k_insert_dense
+//                 the electron bins packed after the heavy ones, and every
+//                 mover into its new bin.
 //
-// The sort exploits that a step moves few particles out of their (species,
-// cell) bin.  Every bin owns a fixed range of slots with slack after its live
-// particles.  A particle that stays in its bin ("stayer") stays in its slot:
-// the push writes it back in place.  A particle that leaves its bin, or one in
-// the tail (created since the last sort), is a mover: the push copies it into
-// the mover buffer at its slot's index and marks the slot it vacates.  The
-// holes of each bin are then filled by the bin's last live particles, and the
-// movers take the slots after the live ones of their new bin, one atomic
-// cursor per bin.  The order inside a bin is not canonical (ascending id is
-// found where it matters, in the collisions).  When a bin's particles
-// outgrow its slots the bins get a new layout (a counting sort into the
-// second buffer, copied back), with slack sized from each bin's traffic since
-// the previous layout.  Every kernel of the re-layout returns at once on the
-// steps that need none, so the step's launch sequence is fixed (CUDA graphs).
+// The sort exploits that a step moves few heavy particles out of their
+// (species, cell) bin.  Every heavy bin owns a fixed range of slots with
+// slack after its live particles.  A heavy particle that stays in its bin
+// ("stayer") stays in its slot: the push writes it back in place (on the
+// steps that move no heavies it is not touched at all).  A heavy particle
+// that leaves its bin or changed species in the collisions is a mover: the
+// push copies it into the mover buffer at its slot's index and marks the slot
+// it vacates.  The holes of each bin are then filled by the bin's last live
+// particles, and the movers take the slots after the live ones of their new
+// bin, one atomic cursor per bin.  A bin that receives more movers than it
+// has free slots borrows the free slots of the next bin when that one is not
+// full as of the counts; beyond that the heavy bins get a new layout (a
+// counting sort into the second buffer, copied back), with slack sized from
+// each bin's traffic since the previous layout.  Every kernel of the
+// re-layout returns at once on the steps that need none, so the step's
+// launch sequence is fixed (CUDA graphs).
+//
+// Electrons cross a cell in a few steps, so they are all movers: they sit in
+// bins packed after the heavy region, and every step the push copies each
+// one (with the particles created since the last sort, in the tail) into the
+// mover buffer; a scan of the movers-in counts gives the electron bins'
+// starts, and each mover takes its slot by the bin's atomic cursor.  The
+// order inside a bin is not canonical (ascending id is found where it
+// matters, in the collisions).
 //
 // The push moves four consecutive particles per thread with 128-bit loads
 // issued before use.  Sorted input means the four usually share a cell, so

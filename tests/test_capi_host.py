@@ -54,4 +54,4 @@ def test_workspace_size_and_validation():
 
 
 def test_kernel_names():
-    assert [pd.pd_kernel_name(k) for k in range(12)] == pd.KERNEL_NAMES
+    assert [pd.pd_kernel_name(k) for k in range(pd.PD_NKERNELS)] == pd.KERNEL_NAMES
