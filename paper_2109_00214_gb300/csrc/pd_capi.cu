@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -88,11 +89,13 @@ Layout make_layout(const std::vector<pd_config>& cf) {
         nr[r] = cf[r].nr;
     }
     L.cap_user = cap;
-    // slots beyond the capacity hold the slack of the bins (the capacity
-    // again, and one slot per bin); slot arrays move in groups of four and
-    // the mover masks in groups of 128
+    // slots beyond the capacity hold the slack of the bins: the capacity
+    // again, and the four slots per bin that every layout may give a bin
+    // whatever its traffic (its three and the rounding up; on a sparse grid
+    // the bins outnumber the particles); slot arrays move in groups of four
+    // and the mover masks in groups of 128
     const uint64_t nbins_all = ncell * (uint64_t)(cf[0].charge_max >= 3 ? NSP : 5);
-    cap = (2 * cap + nbins_all + 2048 + 127) & ~127ull;
+    cap = (2 * cap + 4 * nbins_all + 2048 + 127) & ~127ull;
     L.cap = cap;
     L.ncell = ncell;
     L.nodes = nodes;
@@ -228,6 +231,11 @@ struct pd_sim {
     std::vector<uint16_t> h_cell_run;
     // profiling
     bool prof;
+    // diagnosis (environment PD_DEBUG_SYNC=1): the stream is synchronised and
+    // the device error bits read after each stage of an eager step; the first
+    // failure is reported with the stage's name
+    bool debug_sync;
+    std::string debug_err;
     struct Rec {
         int k;
         cudaEvent_t a, b;
@@ -272,6 +280,19 @@ pd_status cuda_fail(pd_sim* s, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
     } while (0)
 
+// (diagnosis) after a stage: a CUDA error, or device error bits, named by the stage
+void debug_stage(pd_sim* s, int k) {
+    DevState d;
+    cudaError_t e = cudaMemcpyAsync(&d, s->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        s->debug_err = std::string("after ") + KNAMES[k] + ": " + cudaGetErrorString(e);
+    } else if (d.error) {
+        s->debug_err = std::string("after ") + KNAMES[k] + ": device error bits " + std::to_string(d.error) +
+                       ", sort checks " + std::to_string(d.sort_fault) + ", step " + std::to_string(s->step);
+    }
+}
+
 cudaEvent_t take_event(pd_sim* s) {
     if (s->pool.empty()) {
         cudaEvent_t e;
@@ -288,8 +309,9 @@ cudaEvent_t take_event(pd_sim* s) {
 struct Timed {
     pd_sim* s;
     int k;
+    bool capturing;
     cudaEvent_t b;
-    Timed(pd_sim* s_, int k_, bool capturing, int kernels) : s(s_), k(k_), b(nullptr) {
+    Timed(pd_sim* s_, int k_, bool capturing_, int kernels) : s(s_), k(k_), capturing(capturing_), b(nullptr) {
         s->launches[k] += (uint64_t)kernels;
         if (s->prof && !capturing) {
             cudaEvent_t a = take_event(s);
@@ -300,6 +322,7 @@ struct Timed {
     }
     ~Timed() {
         if (b) cudaEventRecord(b, s->stream);
+        if (s->debug_sync && !capturing && s->debug_err.empty()) debug_stage(s, k);
     }
 };
 
@@ -521,8 +544,8 @@ pd_status validate(const pd_config* cfgs, int n, std::string& msg) {
         cap += (uint64_t)b.capacity;
     }
     if (cells >= (1u << 24)) { msg = "all runs together must have < 2^24 cells"; return PD_ERR_ARG; }
-    // the slot arrays hold the capacity twice (the bins' slack) and a slot per bin
-    if (2 * cap + 7 * cells + 4096 > 0xFFFFFFF0ull) {
+    // the slot arrays hold the capacity twice (the bins' slack) and four slots per bin
+    if (2 * cap + 28 * cells + 4096 > 0xFFFFFFF0ull) {
         msg = "all runs together must have a capacity below 2^31 particles";
         return PD_ERR_ARG;
     }
@@ -618,8 +641,9 @@ pd_status prime(pd_sim* s) {
         Timed t(s, K_POISSON, false, 2);   // + the warm start's and the solve's kernels, counted below
         int nk = 0;
         if (warm_start(s, &nk) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
-        if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0, s->stream, &nk))
-            return fail(s, PD_ERR_CUDA, "field solve failed");
+        const cudaError_t fe = field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, 1, 0,
+                                           s->stream, &nk);
+        if (fe != cudaSuccess) return cuda_fail(s, fe, "field solve");
         s->launches[K_POISSON] += (uint64_t)nk;
         field_efield(s->field, s->phi, s->runs_dev, s->E, s->st, s->rs, s->stream);
     }
@@ -732,9 +756,9 @@ pd_status issue_step(pd_sim* s, bool capturing) {
             int nk = 0;
             if (warm_start(s, &nk) != PD_OK) return fail(s, PD_ERR_CUDA, "warm start failed");
             const bool host_check = !capturing && !s->graph_on;
-            if (field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs, host_check ? 1 : 0,
-                            s->graph_cycles, s->stream, &nk))
-                return fail(s, PD_ERR_CUDA, "field solve failed");
+            const cudaError_t fe = field_solve(s->field, s->rho_e, s->rho_h, s->phi, s->E, s->runs_dev, s->rs,
+                                               host_check ? 1 : 0, s->graph_cycles, s->stream, &nk);
+            if (fe != cudaSuccess) return cuda_fail(s, fe, "field solve");
             s->launches[K_POISSON] += (uint64_t)nk;
         }
         {
@@ -743,6 +767,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
         }
     }
     s->step += 1;
+    if (!s->debug_err.empty()) return fail(s, PD_ERR_CUDA, "PD_DEBUG_SYNC: " + s->debug_err);
     return PD_OK;
 }
 
@@ -1027,6 +1052,10 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->step = 0;
     s->primed = false;
     s->prof = false;
+    {
+        const char* d = std::getenv("PD_DEBUG_SYNC");
+        s->debug_sync = d && d[0] == '1';
+    }
     s->graph_on = false;
     s->graph_cycles = 4;
     s->tune = default_tuning();

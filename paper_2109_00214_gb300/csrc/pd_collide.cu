@@ -126,8 +126,10 @@ __device__ void deposit1(long long* rho, const RunInfo& RI, int geom, uint32_t l
 // scatter's atomics, so each list the candidates use is mapped rank ->
 // position by one of:
 //   * ids already ascending with the position (rank = position);
-//   * up to 32 * RC ids with few lookups: a radix select over the ids held
-//     in registers, per lookup;
+//   * up to 64 ids: a rank table by comparisons (the rank of an id is the
+//     number of smaller ids in the list);
+//   * up to 32 * RC ids with lookups that cost less than a table: a radix
+//     select over the ids held in registers, per lookup;
 //   * otherwise a rank table, position of the r-th smallest id at table[r],
 //     from a stable LSD radix sort of (id, position) pairs by 8-bit digits:
 //     by the cell's warp in its shared memory for lists up to RANK_WARP_MAX
@@ -377,7 +379,9 @@ template <int NT, uint32_t MAXN>
 __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__ ids, RankScratch S,
                                                     const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
                                                     const uint32_t* __restrict__ q,
-                                                    const uint32_t* nq, uint32_t max_q, uint32_t C) {
+                                                    const uint32_t* nq, uint32_t max_q, uint32_t C,
+                                                    const DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     constexpr int NWARPS = NT / 32;
     extern __shared__ uint32_t s_buf[];                 // four arrays of MAXN
     __shared__ uint32_t s_cnt[NWARPS * 256];
@@ -470,18 +474,25 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
         orv = __reduce_or_sync(FULL, orv);
         L.top = orv ? 31 - __clz((int)orv) : 0;
         L.sorted = __all_sync(FULL, asc);
-        // a select sweeps the list once per significant bit, per lookup
-        if (L.sorted || (!want_table && lookups * (uint32_t)(L.top + 1) <= 128u)) return;
+        if (L.sorted) return;
         if (n <= 64u) {
             // a short list's table by comparison: the rank of an id is the
-            // number of smaller ids (ids are unique), 32 exchanges per warp
+            // number of smaller ids (ids are unique), 32 exchanges per row
             uint32_t r0 = 0, r1 = 0;
+            if (n <= 32u) {
 #pragma unroll 8
-            for (int j = 0; j < 32; ++j) {
-                const uint32_t a = __shfl_sync(FULL, L.ids[0], j), b = __shfl_sync(FULL, L.ids[1], j);
-                const bool va = (uint32_t)j < n, vb = 32u + (uint32_t)j < n;
-                r0 += (va && a < L.ids[0] ? 1u : 0u) + (vb && b < L.ids[0] ? 1u : 0u);
-                r1 += (va && a < L.ids[1] ? 1u : 0u) + (vb && b < L.ids[1] ? 1u : 0u);
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t a = __shfl_sync(FULL, L.ids[0], j);
+                    r0 += ((uint32_t)j < n && a < L.ids[0]) ? 1u : 0u;
+                }
+            } else {
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    const uint32_t a = __shfl_sync(FULL, L.ids[0], j), b = __shfl_sync(FULL, L.ids[1], j);
+                    const bool vb = 32u + (uint32_t)j < n;
+                    r0 += (a < L.ids[0] ? 1u : 0u) + (vb && b < L.ids[0] ? 1u : 0u);
+                    r1 += (a < L.ids[1] ? 1u : 0u) + (vb && b < L.ids[1] ? 1u : 0u);
+                }
             }
             uint32_t* table = S.table + slot0;
             if ((uint32_t)lane < n) table[r0] = (uint32_t)lane;
@@ -491,6 +502,12 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
             L.cached = false;
             return;
         }
+        // a select sweeps the registers once per significant bit, per lookup
+        // (about 48 instructions a bit); the table takes a radix pass per
+        // 8-bit digit (about 96 plus 64 per 32 ids)
+        const uint32_t sel_cost = lookups * (uint32_t)(L.top + 1) * 48u;
+        const uint32_t tab_cost = (uint32_t)(L.top / 8 + 1) * (96u + ((n + 31u) / 32u) * 64u);
+        if (!want_table && sel_cost <= tab_cost) return;
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             const uint32_t q = (uint32_t)lane + 32u * k;
@@ -557,6 +574,7 @@ template <bool EXT>
 __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ cnt, const float* __restrict__ ck,
                                                uint4* nc, uint4* nc2, uint32_t* cand, uint32_t* active, uint32_t* mid,
                                                uint32_t* big, DevState* st, KParams P) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t C = P.ncell;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
@@ -1070,6 +1088,7 @@ __device__ __forceinline__ int list_species(int l) { return l == 0 ? SP_E : SP_C
 __global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                    const uint32_t* __restrict__ cnt, DevState* st, KParams P,
                                                    CollConsts cc, const double* __restrict__ cw) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     __shared__ uint32_t s_sort[COUL_WARPS][COUL_SBUF];   // per-warp rank-table sort, then velocity cache
     __shared__ CoulWarp s_cw[COUL_WARPS];
     const int lane = threadIdx.x & 31;
@@ -1312,6 +1331,7 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                                                  long long* rho_h, const float* __restrict__ xsE,
                                                  const float* __restrict__ xs, const double* __restrict__ cw,
                                                  KParams P, CollConsts cc, uint32_t nbins) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     __shared__ uint32_t s_sort[4][4 * RANK_WARP_MAX + 256];   // per-warp rank-table sort
     const int lane = threadIdx.x & 31;
     uint32_t* sbuf = s_sort[(threadIdx.x >> 5) & 3];
@@ -1590,6 +1610,7 @@ __device__ __forceinline__ float rayleigh(const float* __restrict__ ray, float U
 
 __global__ void __launch_bounds__(256) k_inject(Particles A, const float2* __restrict__ E, DevState* st, KParams P,
                                                 const InjectConsts* __restrict__ icv, const float* __restrict__ ray) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     __shared__ uint32_t ne_s[64], nn_s[64], pre_s[65];
     __shared__ unsigned long long slot0_s;
     const int run = blockIdx.x;
@@ -1696,6 +1717,7 @@ constexpr size_t SPUT_SMEM = SPUT_MAX * sizeof(unsigned long long);
 
 __global__ void __launch_bounds__(SPUT_THREADS) k_sputter(Particles M, uint32_t* mm, DevState* st, KParams P,
                                                           const float* __restrict__ ray, uint32_t* in_cnt) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     extern __shared__ unsigned long long s_key[];    // ion id << 32 | record index
     __shared__ uint32_t s_cnt, s_el[2], s_wsum[SPUT_THREADS / 32];
     __shared__ unsigned long long s_base;
@@ -1842,9 +1864,9 @@ void launch_collide(const Particles& A, const Particles& B, const uint32_t* off,
     const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
                         reinterpret_cast<uint32_t*>(B.vz), B.id};
     k_rank_tables<RT_MID_THREADS, RANK_MID_MAX><<<sms * RT_MID_BLOCKS_PER_SM, RT_MID_THREADS, RT_MID_SMEM, s>>>(
-        A.id, S, off, cnt, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell);
+        A.id, S, off, cnt, mid, &st->n_mid, rank_queue_max(P.capacity, RANK_WARP_MAX), P.ncell, st);
     k_rank_tables<RT_THREADS, RANK_BLOCK_MAX><<<sms, RT_THREADS, RT_SMEM, s>>>(
-        A.id, S, off, cnt, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell);
+        A.id, S, off, cnt, big, &st->n_big, rank_queue_max(P.capacity, RANK_MID_MAX), P.ncell, st);
     if (P.charge_max >= 3 || P.heavy_coll || P.coulomb)
         k_collide<true><<<grid, 128, 0, s>>>(A, S, off, cnt, nc, nc2, cand_off, active, st, rho_e, rho_h, xsE, xs, cw, P,
                                              cc, nbins);

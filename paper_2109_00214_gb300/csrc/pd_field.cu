@@ -866,7 +866,7 @@ static void norms(FieldSolver& fs, RunState* rs, int cycle, int first, cudaStrea
     k_norms<<<(R + 3) / 4, 128, 0, s>>>(fs.red, fs.bnorm, fs.done, fs.tol, rs, R, cycle, first);
 }
 
-int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
+cudaError_t field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
                 const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s, int* kernels) {
     (void)E;
     (void)phi;
@@ -877,9 +877,9 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
     if (kernels) *kernels += 3;
     if (host_check) {
         for (int cyc = 1; cyc <= fs.max_cycles; ++cyc) {
-            if (cudaMemcpyAsync(fs.host_done, fs.done, (size_t)R * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-                return 1;
-            if (cudaStreamSynchronize(s) != cudaSuccess) return 1;
+            cudaError_t e = cudaMemcpyAsync(fs.host_done, fs.done, (size_t)R * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return e;
             bool all = true;
             for (int r = 0; r < R; ++r) all = all && fs.host_done[r] != 0;
             if (all) break;
@@ -894,7 +894,7 @@ int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h,
             if (kernels) *kernels += nk + 2;
         }
     }
-    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+    return cudaGetLastError();
 }
 
 // E for every run (separate so the caller can time it)

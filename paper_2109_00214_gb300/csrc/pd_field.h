@@ -77,7 +77,7 @@ void field_free(FieldSolver& fs);
 // reads the flags between cycles); otherwise exactly `cycles` cycles are
 // issued with no host synchronisation (runs already converged skip them),
 // so the solve can be captured in a CUDA graph.  Records relres / cycles.
-int field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
+cudaError_t field_solve(FieldSolver& fs, const long long* rho_e, const long long* rho_h, double* phi, float2* E,
                 const RunInfo* runs, RunState* rs, int host_check, int cycles, cudaStream_t s,
                 int* kernels = nullptr);   // adds the number of kernels launched
 

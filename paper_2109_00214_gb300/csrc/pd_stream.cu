@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                                                long long* rho_h, uint32_t* out_cnt, uint32_t* in_cnt,
                                                uint32_t* mv, uint32_t* mm, Particles M, DevState* st, KParams P) {
     __shared__ RunInfo s_runs[MULTI ? MAX_RUNS_SMEM : 1];
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     if (MULTI) {
         for (int r = threadIdx.x; r < P.nruns; r += blockDim.x) s_runs[r] = P.runs[r];
         __syncthreads();
@@ -232,7 +233,11 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 niz = wrap1(niz, RI.nz);
                 nir = wrap1(nir, RI.nr);
             }
-            const bool absorbed = move && out;
+            // a non-finite position or velocity (a fault upstream) would index
+            // outside the grid: the particle is dropped and the error flagged
+            const bool bad = move && !(isfinite(z) && isfinite(npr) && isfinite(vz) && isfinite(vr) && isfinite(vt));
+            if (bad) set_error(st, ERR_NONFINITE);
+            const bool absorbed = move && (out || bad);
             const bool kp = live && !absorbed;
             const uint32_t gcell =
                 move ? RI.cell_base + (uint32_t)niz * (uint32_t)RI.nr + (uint32_t)nir : gcell_in;
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             newbin[q] = nb;
             mover[q] = mvq;
             inmv[q] = inq;
-            absd[q] = absorbed;
+            absd[q] = absorbed && !bad;                   // (ledgers and impacts of finite particles only)
             zo[q] = mk ? npz : pz;
             ro[q] = (mk || absorbed) ? npr : pr;           // an absorbed particle keeps its impact r
             vzo[q] = move ? vz : lane_of(VZ, q);
@@ -463,6 +468,7 @@ __global__ void __launch_bounds__(256) k_bins(Particles A, const uint32_t* __res
                                               const uint32_t* __restrict__ mv, uint32_t* act, int* net, uint4* bigq,
                                               uint32_t bigq_cap, uint32_t* ovq, uint32_t* ovbits, uint32_t b0,
                                               uint32_t nbins, DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     long long dlive = 0;
     for (uint32_t b = b0 + blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
         const uint32_t o = out_cnt[b], in = in_cnt[b];
@@ -526,6 +532,7 @@ __global__ void __launch_bounds__(256) k_bins(Particles A, const uint32_t* __res
 __global__ void __launch_bounds__(256) k_compact_big(Particles A, const uint32_t* __restrict__ mv,
                                                      const uint4* __restrict__ bigq, uint32_t bigq_cap,
                                                      DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     __shared__ uint32_t s_h[8][32];
     const int lane = threadIdx.x & 31;
     uint32_t* sh = s_h[threadIdx.x >> 5];
@@ -592,6 +599,7 @@ __global__ void __launch_bounds__(256) k_compact_big(Particles A, const uint32_t
 __global__ void __launch_bounds__(256) k_borrow(Particles A, uint32_t* off, const uint32_t* __restrict__ cnt,
                                                 const uint32_t* __restrict__ in_cnt, const uint32_t* __restrict__ ovq,
                                                 const uint32_t* __restrict__ ovbits, uint32_t nbins, DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t nq = st->n_ovf;
     if (nq > OVQ_CAP) return;                        // (the re-layout is already set)
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
@@ -643,8 +651,8 @@ __device__ __forceinline__ uint32_t mover_bin(uint32_t k, uint32_t ncell, uint32
 // heavy_only: electrons are left in the mask for the electron pass.
 __device__ __forceinline__ void insert128(Particles& D, const Particles& M, uint32_t* mm, uint32_t g,
                                           const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
-                                          uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, bool heavy_only,
-                                          DevState* st) {
+                                          uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, uint32_t nslots,
+                                          bool heavy_only, DevState* st) {
     const uint4 w = reinterpret_cast<uint4*>(mm)[g];
     if ((w.x | w.y | w.z | w.w) == 0u) return;
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
@@ -668,7 +676,7 @@ __device__ __forceinline__ void insert128(Particles& D, const Particles& M, uint
             }
             const uint32_t left = atomicSub(&in_cnt[bin], 1u);
             const uint32_t s = off[bin] + cnt[bin] - left;
-            if (left == 0u || s >= off[bin] + cnt[bin]) {   // inconsistent bookkeeping: report, never write out of range
+            if (left == 0u || s >= off[bin] + cnt[bin] || s >= nslots) {   // inconsistent: report, never write out of range
                 sort_fault(st, 16u);
                 continue;
             }
@@ -682,10 +690,12 @@ __device__ __forceinline__ void insert128(Particles& D, const Particles& M, uint
 // e_from (sparse: a thread per chunk)
 __global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32_t* mm,
                                                 const uint32_t* __restrict__ off, const uint32_t* __restrict__ cnt,
-                                                uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, DevState* st) {
+                                                uint32_t* in_cnt, uint32_t ncell, uint32_t nbins, uint32_t nslots,
+                                                DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t ng = (uint32_t)(st->e_from >> 7);
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
-        insert128(A, M, mm, g, off, cnt, in_cnt, ncell, nbins, false, st);
+        insert128(A, M, mm, g, off, cnt, in_cnt, ncell, nbins, nslots, false, st);
 }
 
 // The movers from the first chunk of 128 that k_insert leaves (it ends below
@@ -695,7 +705,8 @@ __global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32
 __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
                                                       const uint32_t* __restrict__ off,
                                                       const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
-                                                      uint32_t ncell, uint32_t nbins, DevState* st) {
+                                                      uint32_t ncell, uint32_t nbins, uint32_t nslots, DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t g0 = (uint32_t)((st->e_from >> 7) << 5), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
     const uint32_t lane = threadIdx.x & 31u;
     for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g - lane < g1; g += gridDim.x * blockDim.x) {
@@ -738,7 +749,7 @@ __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, 
             const uint32_t b = bin[q];
             const uint32_t rank = (uint32_t)__popc(peers[q] & ((1u << lane) - 1u));
             const uint32_t sl = off[b] + cnt[b] - lq + rank;
-            if (lq < (uint32_t)__popc(peers[q]) || sl >= off[b] + cnt[b]) {
+            if (lq < (uint32_t)__popc(peers[q]) || sl >= off[b] + cnt[b] || sl >= nslots) {
                 sort_fault(st, 256u);
                 continue;
             }
@@ -757,7 +768,9 @@ __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, 
 // moving in (every electron), start = e_base + exclusive prefix of the counts
 // (scanned into pre[]); the tail starts after them.
 __global__ void __launch_bounds__(256) k_ebins(uint32_t* off, uint32_t* cnt, const uint32_t* __restrict__ in_cnt,
-                                               const uint32_t* __restrict__ pre, uint32_t ncell, DevState* st) {
+                                               const uint32_t* __restrict__ pre, uint32_t ncell, uint32_t nslots,
+                                               DevState* st) {
+    if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t eb = (uint32_t)st->e_base;
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
         off[c] = eb + pre[c];
@@ -766,6 +779,7 @@ __global__ void __launch_bounds__(256) k_ebins(uint32_t* off, uint32_t* cnt, con
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->n_e = pre[ncell];
         st->tail_base = (unsigned long long)eb + pre[ncell];
+        if (st->tail_base > nslots) set_error(st, ERR_CAPACITY);   // the inserts then write nothing past the slots
     }
 }
 
@@ -791,7 +805,7 @@ constexpr float SLACK_SIGMAS = 5.3f;
 __global__ void __launch_bounds__(256) k_relayout_stats(const uint32_t* __restrict__ cnt,
                                                         const uint32_t* __restrict__ act, uint32_t nbins,
                                                         uint32_t ncell, int nsp, DevState* st) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     unsigned long long c_[NSP], a_[NSP];
 #pragma unroll
     for (int k = 0; k < NSP; ++k) c_[k] = a_[k] = 0ull;
@@ -839,7 +853,7 @@ __device__ __forceinline__ void species_rates(const DevState* st, uint32_t since
 __global__ void __launch_bounds__(256) k_relayout_want(const uint32_t* __restrict__ cnt,
                                                        const uint32_t* __restrict__ act, const int* __restrict__ net,
                                                        uint32_t nbins, uint32_t ncell, DevState* st) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     const uint32_t since = st->since;
     __shared__ float s_rate[NSP], s_mean[NSP];
     species_rates(st, since, ncell, s_rate, s_mean);
@@ -888,7 +902,7 @@ __global__ void __launch_bounds__(256) k_relayout_want(const uint32_t* __restric
 __global__ void __launch_bounds__(256) k_relayout_caps(const uint32_t* __restrict__ cnt, uint32_t* cap,
                                                        uint32_t* act, int* net, uint32_t nbins, uint32_t nbins_pad,
                                                        uint32_t ncell, DevState* st, KParams P) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     const uint32_t since = st->since;
     __shared__ float s_rate[NSP], s_mean[NSP];
     species_rates(st, since, ncell, s_rate, s_mean);
@@ -926,7 +940,7 @@ __global__ void __launch_bounds__(256) k_relayout_caps(const uint32_t* __restric
 // B's keys over the new bins: DEAD (slack slots stay so)
 __global__ void __launch_bounds__(256) k_relayout_clear(uint32_t* key, const uint32_t* __restrict__ off2,
                                                         uint32_t nbins, DevState* st) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     const uint32_t nv = (off2[nbins] + 3u) >> 2;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
         reinterpret_cast<uint4*>(key)[v] = make_uint4(DEAD, DEAD, DEAD, DEAD);
@@ -942,7 +956,7 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
                                                           const uint32_t* __restrict__ off2,
                                                           const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
                                                           uint32_t nbins, DevState* st, KParams P) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t tb = (uint32_t)st->e_from, nv = (tb + 3u) >> 2;
@@ -974,7 +988,8 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
         }
     }
     const uint32_t ng = (uint32_t)((st->n_slots + 127ull) >> 7);
-    for (uint32_t g = tid; g < ng; g += stride) insert128(B, M, mm, g, off2, cnt, in_cnt, P.ncell, nbins, true, st);
+    for (uint32_t g = tid; g < ng; g += stride)
+        insert128(B, M, mm, g, off2, cnt, in_cnt, P.ncell, nbins, (uint32_t)P.capacity, true, st);
 }
 
 // A := B over the new heavy bins (groups of four slack slots copy only
@@ -982,7 +997,7 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
 __global__ void __launch_bounds__(256) k_relayout_copy(Particles A, Particles B, uint32_t* off,
                                                        const uint32_t* __restrict__ off2, uint32_t nbins,
                                                        uint32_t nbins_pad, DevState* st) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t end = off2[nbins], nv = (end + 3u) >> 2;
@@ -1007,7 +1022,7 @@ __global__ void __launch_bounds__(256) k_relayout_copy(Particles A, Particles B,
 
 // after the copy: the re-layout is done
 __global__ void k_relayout_done(const uint32_t* __restrict__ off, uint32_t nbins, DevState* st) {
-    if (!st->relayout) return;
+    if (!st->relayout || st->error) return;
     st->e_base = off[nbins];
     st->relayout = 0u;
     st->since = 0u;
@@ -1064,11 +1079,12 @@ void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid
 void launch_insert(const SortArgs& a, DevState* st, const KParams& P, int grid_dense, cudaStream_t s) {
     // the electron bins: counts scanned (into off2, free after a re-layout), laid out after the heavy bins
     launch_scan(a.in_cnt, a.off2, a.partial, a.ncell_pad, s);
-    k_ebins<<<(P.ncell + 255u) / 256u, 256, 0, s>>>(a.off, a.cnt, a.in_cnt, a.off2, P.ncell, st);
+    k_ebins<<<(P.ncell + 255u) / 256u, 256, 0, s>>>(a.off, a.cnt, a.in_cnt, a.off2, P.ncell, (uint32_t)a.slots, st);
     // heavy movers (a thread per 128 slots of the heavy bins), then the electrons and the tail
     const uint32_t gs = (uint32_t)((a.slots / 128u + 255u) / 256u);
-    k_insert<<<gs, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins, st);
-    k_insert_dense<<<grid_dense, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins, st);
+    k_insert<<<gs, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins, (uint32_t)a.slots, st);
+    k_insert_dense<<<grid_dense, 256, 0, s>>>(a.A, a.M, a.mm, a.off, a.cnt, a.in_cnt, P.ncell, a.nbins,
+                                              (uint32_t)a.slots, st);
 }
 
 }  // namespace pd

@@ -26,7 +26,11 @@ from . import Simulation, load_library
 
 COLS = ["step", "t_ns", "wall_s", "particles", "n_e", "n_cu", "n_cup", "n_cu2_sw", "n_cu2_di", "n_cu3", "n_cu4",
         "V", "I_gap", "gamma", "Qbar", "erosion_ug_per_C", "poisson_relres_max", "emitted_e", "emitted_cu",
-        "sput_cathode", "ev_si", "ev_di", "ev_sw"]
+        "sput_cathode", "ev_si", "ev_di", "ev_sw", "abs_cathode_e", "abs_cathode_heavy", "abs_cathode_ion_charge",
+        "mass_kg", "charge_C"]
+
+HEAVY = ("Cu", "Cu+", "Cu2+SW", "Cu2+DI", "Cu3+", "Cu4+")
+CHARGE = {"Cu": 0, "Cu+": 1, "Cu2+SW": 2, "Cu2+DI": 2, "Cu3+": 3, "Cu4+": 4}
 
 
 def paper_config(nz=120, nr=480, capacity=1 << 23, charge_max=4, heavy_coll=1, sputter=1, coulomb=0, seed=1):
@@ -38,6 +42,24 @@ def paper_config(nz=120, nr=480, capacity=1 << 23, charge_max=4, heavy_coll=1, s
     cfg, parts = synthetic.rz_breakdown(n=nz, seed=seed, capacity=capacity)
     cfg.update(nr=nr, charge_max=charge_max, heavy_coll=heavy_coll, sputter=sputter, coulomb=coulomb)
     return cfg, parts
+
+
+def erosion_terms(row, weight):
+    """The cathode erosion rate of a sampled row split into its ledger terms:
+    net Cu mass M W (N_neutral + N_sputtered - N_heavy returned) over the net
+    charge through the cathode, e W (N_e emitted - N_e returned + sum of z N
+    of the ions it absorbed) (the charge ledger also counts the particles of
+    the initial load that leave through the cathode).  With no returns and no
+    sputtering the rate is 0.03 M / e = 19.76 ug/C; returning ions take mass
+    back and add charge, so they pull it below that floor."""
+    qe, mcu = 1.602176634e-19, 63.546 * 1.66053906660e-27
+    mass = mcu * weight * (row["emitted_cu"] + row["sput_cathode"] - row["abs_cathode_heavy"])
+    charge = qe * weight * (row["emitted_e"] - row["abs_cathode_e"] + row["abs_cathode_ion_charge"])
+    floor = mcu * weight * row["emitted_cu"] / (qe * weight * row["emitted_e"]) if row["emitted_e"] else 0.0
+    return dict(floor_ug_per_C=floor * 1e9, mass_kg=mass, charge_C=charge,
+                from_terms_ug_per_C=mass / charge * 1e9 if charge else 0.0,
+                returned_heavy=row["abs_cathode_heavy"], returned_ion_charge=row["abs_cathode_ion_charge"],
+                returned_e=row["abs_cathode_e"], sputtered=row["sput_cathode"])
 
 
 def run(steps, every, nz=120, nr=480, cycles=8, out=None, capacity=1 << 23, charge_max=4, heavy_coll=1,
@@ -68,7 +90,10 @@ def run(steps, every, nz=120, nr=480, cycles=8, out=None, capacity=1 << 23, char
                          Qbar=sc["Qbar"], erosion_ug_per_C=sc["erosion"] * 1e9,
                          poisson_relres_max=sc["poisson_relres_max"], emitted_e=c["emitted_e"],
                          emitted_cu=c["emitted_cu"], sput_cathode=c["sput_cathode"], ev_si=c["ev_si"],
-                         ev_di=c["ev_di"], ev_sw=c["ev_sw"]))
+                         ev_di=c["ev_di"], ev_sw=c["ev_sw"], abs_cathode_e=c["abs_cathode_e"],
+                         abs_cathode_heavy=sum(c[f"abs_cathode_{h}"] for h in HEAVY),
+                         abs_cathode_ion_charge=sum(CHARGE[h] * c[f"abs_cathode_{h}"] for h in HEAVY),
+                         mass_kg=sc["mass"], charge_C=sc["charge"]))
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if out:
@@ -78,7 +103,9 @@ def run(steps, every, nz=120, nr=480, cycles=8, out=None, capacity=1 << 23, char
             w.writerows(rows)
     summary = dict(steps=steps, simulated_ns=steps * cfg["dt"] * 1e9, wall_s=wall,
                    steps_per_s=steps / wall, grid=[nz, nr], poisson_cycles=cycles, warm_start=warm,
-                   final=rows[-1] if rows else None)
+                   worst_relres=max(r["poisson_relres_max"] for r in rows) if rows else None,
+                   final=rows[-1] if rows else None,
+                   erosion_terms=erosion_terms(rows[-1], cfg["weight"]) if rows else None)
     sim.close()
     return summary, rows
 
