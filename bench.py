@@ -226,12 +226,6 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-# algorithmic bytes per live particle (FP32 SoA, 28 B per particle), per
-# kernel, Cartesian field-free microbench
-BYTES_PER_PARTICLE = {
-    "push": 32.0,      # read key, pz, pr, vz, vr (20 B); write key, pz, pr (12 B)
-    "scatter": 56.0,   # read 7 x 4 B, write 7 x 4 B
-}
 # DRAM bytes per particle of the same kernels from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of a 2.49e7-particle launch of
 # the 512 x 512 microbench), scaled to a launch by its particle count.  The
@@ -711,11 +705,12 @@ def kernel_table(prof, steps, n_live, n_e, n_h, hs, slots, cand, ncell, nbins_h,
     """Per-kernel time per step and, where the kernel has a per-unit byte
     model, its algorithmic GB/s and fraction of the HBM peak.
 
-    push: an electron is read (20 B Cartesian, 24 B r-z) and written to the
-    mover buffer (28 B) with its id (4 B; the Cartesian push also reads
-    v_theta, 4 B); a heavy particle on a heavy step is read and its new
-    position written back (20 + 8 B Cartesian; 24 + 20 B r-z), on the other
-    steps only its key is read (4 B); a slack slot reads its key (4 B).
+    push: an electron's key, position and velocity are read (24 B, with
+    v_theta, which the Cartesian push reads only for the record) with its id
+    (4 B), and its record written to the mover buffer (28 B); a heavy
+    particle on a heavy step is read and its new position written back
+    (20 + 8 B Cartesian; 24 + 20 B r-z), on the other steps only its key is
+    read (4 B); a slack slot reads its key (4 B).
     scatter (the sort after the push): every electron is read from the mover
     buffer and written to its bin (28 + 28 B); each heavy bin's in and out
     counts are read (8 B); heavy movers are few."""
@@ -724,7 +719,7 @@ def kernel_table(prof, steps, n_live, n_e, n_h, hs, slots, cand, ncell, nbins_h,
         heavy = n_h * (44.0 + 4.0 * (hs - 1)) / hs
         push_bytes = 56.0 * n_e + heavy + 4.0 * slack
     else:
-        push_bytes = 60.0 * n_e + 28.0 * n_h + 4.0 * slack
+        push_bytes = 56.0 * n_e + 28.0 * n_h + 4.0 * slack
     model = {
         "push": push_bytes,
         "scatter": 56.0 * n_e + 8.0 * nbins_h,

@@ -80,12 +80,16 @@ def test_sparse_ensemble_run_layouts_fit(pd, xs):
     assert np.array_equal(made - absorbed, gn)
 
 
-def test_sparse_hot_heavies_bit_exact(pd, xs):
-    """128 x 128 Cartesian cells, 2e4 particles, heavies hot enough to cross
+@pytest.mark.parametrize("n,min_relayouts", [
+    (128, 1),      # 1.2 particles a cell: bins borrow from their empty neighbours
+    (48, 3),       # 8.7 a cell: borrowing falls short and the bins are laid out anew
+])
+def test_hot_heavies_bit_exact(pd, xs, n, min_relayouts):
+    """n x n Cartesian cells, 2e4 particles, heavies hot enough to cross
     about a cell a step, and a capacity of 25 000: every step moves most heavy
-    particles between bins of minimal slack, so bins borrow and the layout is
+    particles between bins of little slack, so bins borrow and the layout is
     redone; the particles must match the oracle bit for bit."""
-    cfg, parts = synthetic.microbench(nz=128, nr=128, total=2e4, seed=7, T_heavy=2e7)
+    cfg, parts = synthetic.microbench(nz=n, nr=n, total=2e4, seed=7, T_heavy=2e7)
     cfg.update(capacity=25000)
     sim = pd.Simulation(cfg, xs)
     o = oracle.Oracle(cfg, fp64=False)
@@ -97,10 +101,10 @@ def test_sparse_hot_heavies_bit_exact(pd, xs):
         sim.step(8)
         o.step(8)
         sim.synchronize()
-        check_bins(sim, 128 * 128)
+        check_bins(sim, n * n)
     st = sim.sort_stats()
     assert st["faults"] == 0
-    assert st["relayouts"] >= 3, st
+    assert st["relayouts"] >= min_relayouts, st
     gc, oc = sim.counters(), o.counters()
     for k in oc:
         assert gc[k] == oc[k], (k, gc[k], oc[k])
