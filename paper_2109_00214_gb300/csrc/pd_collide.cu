@@ -180,18 +180,24 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool v) {
 }
 
 // Position of the rank-th smallest of the n (unique) ids at ids[0, n) by
-// one warp: passes over 8-bit digits from the one holding bit `top` (every id
-// is below 2^(top + 1)) down, each counting, in the warp's 256 shared
-// counters, the ids that share the digits found so far; SENTINEL if
-// rank >= n.  Each lane keeps eight loads in flight.
+// one warp: passes over windows of 8 bits from bit `top` (every id is below
+// 2^(top + 1)) down, each counting, in the warp's 256 shared counters, the
+// ids that share the bits found so far; SENTINEL if rank >= n.  The first
+// window is the top 8 bits, so that its digits spread over the counters
+// (windows aligned to bit 0 would leave the first pass one or two digits:
+// every id's atomic on the same counters); the last window holds the bits
+// that remain.  Each lane keeps eight loads in flight.
 __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, int top, uint32_t* cnt,
                             int lane) {
     uint32_t prefix = 0, want = rank;
-    for (int sh = (top / 8) * 8; sh >= 0; sh -= 8) {
+    for (int lo = top - 7;; lo -= 8) {
+        const int sh = lo > 0 ? lo : 0;
+        const int width = lo >= 0 ? 8 : 8 + lo;        // bits of this window
+        const uint32_t dm = (1u << width) - 1u;
+        const uint32_t hm = sh + width >= 32 ? 0u : (0xFFFFFFFFu << (sh + width));
 #pragma unroll
         for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
         __syncwarp();
-        const uint32_t hm = sh >= 24 ? 0u : (0xFFFFFFFFu << (sh + 8));
         for (uint32_t q0 = 0; q0 < n; q0 += 256) {
             uint32_t x[8];
 #pragma unroll
@@ -202,7 +208,7 @@ __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint32_t q = q0 + 32u * u + (uint32_t)lane;
-                if (q < n && (x[u] & hm) == prefix) atomicAdd(&cnt[(x[u] >> sh) & 255u], 1u);
+                if (q < n && (x[u] & hm) == prefix) atomicAdd(&cnt[(x[u] >> sh) & dm], 1u);
             }
         }
         __syncwarp();
@@ -236,6 +242,7 @@ __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32
         d = __shfl_sync(FULL, d, src);
         want = __shfl_sync(FULL, rest, src);
         prefix |= d << sh;
+        if (sh == 0) break;
     }
     uint32_t pos = SENTINEL;
     for (uint32_t q0 = 0; q0 < n; q0 += 256) {

@@ -86,10 +86,12 @@ def test_sparse_ensemble_run_layouts_fit(pd, xs):
 ])
 def test_hot_heavies_bit_exact(pd, xs, n, min_relayouts):
     """n x n Cartesian cells, 2e4 particles, heavies hot enough to cross
-    about a cell a step, and a capacity of 25 000: every step moves most heavy
+    about a cell a step (2e13 K: 5e7 m/s, a 50 nm cell in a 1 fs step; the
+    sort does not care that no copper is that hot), and a capacity of
+    25 000: every step moves most heavy
     particles between bins of little slack, so bins borrow and the layout is
     redone; the particles must match the oracle bit for bit."""
-    cfg, parts = synthetic.microbench(nz=n, nr=n, total=2e4, seed=7, T_heavy=2e7)
+    cfg, parts = synthetic.microbench(nz=n, nr=n, total=2e4, seed=7, T_heavy=2e13)
     cfg.update(capacity=25000)
     sim = pd.Simulation(cfg, xs)
     o = oracle.Oracle(cfg, fp64=False)
