@@ -31,6 +31,26 @@ convolutions).  Parameter vector: for l = 1..6 in order, W_l as
 
 Loss: mean over the batch and the nodes of (y - t)^2.
 
+Extrapolated form, against the two previous solves (rho', phi', V') and
+(rho'', phi'', V''): the start is the potential extrapolated linearly in
+time, and the network corrects it from the charge that the extrapolation
+misses:
+    d = rho - (2 rho' - rho''),
+    base = 2 phi' - phi'' + (V - 2 V' + V'') z / L.
+Its training loss is the residual of Eq. (8) that the corrected start
+leaves, in the units of the finite-volume equations: on the interior rows
+(the electrode rows are Dirichlet, y = 0 there)
+    r = w x - S y,
+    (S y)_ij = (a+_j + a-_j + 2 w_j) y_ij - a+_j y_i,j+1 - a-_j y_i,j-1
+               - w_j (y_i+1,j + y_i-1,j),
+with, for dz = dr (radial node j = 0..nr, outer radius R = nr dr), the
+face coefficients and volumes of the finite-volume r-z Laplacian divided by
+2 pi dr: a+_j = j + 1/2 (0 at j = nr: Neumann), a-_j = j - 1/2 (0 on the
+axis), w_j = j, 1/8 on the axis, nr/2 - 1/8 at the outer radius (the node's
+finite volume over 2 pi dr^3).  S is symmetric; t of the pair satisfies
+S t = w x exactly when phi solves Eq. (8).  Loss: sum of r^2 over the
+interior nodes of the batch divided by their number.
+
 Adam (Kingma and Ba, ICLR 2015): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2)
 g^2, w -= lr (m / (1 - b1^k)) / (sqrt(v / (1 - b2^k)) + eps) at step k = 1, 2, ...
 
@@ -163,6 +183,98 @@ def loss_and_grad(params, x, t, bf16=False):
             gh += shift(g, -dy, -dx) @ Wr[tap]
         g = rnd(gh * (h > 0.0))                  # through the ReLU of layer l - 1
     return L, pack(grads)
+
+
+def rz_weights(W):
+    """(a+, a-, w) of the unit finite-volume r-z operator for W = nr + 1 radial nodes."""
+    nr = W - 1
+    j = np.arange(W, dtype=np.float64)
+    ap = j + 0.5
+    ap[nr] = 0.0
+    am = j - 0.5
+    am[0] = 0.0
+    w = j.copy()
+    w[0] = 1.0 / 8.0
+    w[nr] = nr / 2.0 - 1.0 / 8.0
+    return ap, am, w
+
+
+def rz_operator(y):
+    """S y on the interior rows of y [..., H, W] (rows 0 and H - 1 read as 0
+    and returned 0)."""
+    y = np.array(y, dtype=np.float64)
+    y[..., 0, :] = 0.0
+    y[..., -1, :] = 0.0
+    ap, am, w = rz_weights(y.shape[-1])
+    out = (ap + am + 2.0 * w) * y
+    out[..., :, :-1] -= ap[:-1] * y[..., :, 1:]
+    out[..., :, 1:] -= am[1:] * y[..., :, :-1]
+    out[..., 1:, :] -= w * y[..., :-1, :]
+    out[..., :-1, :] -= w * y[..., 1:, :]
+    out[..., 0, :] = 0.0
+    out[..., -1, :] = 0.0
+    return out
+
+
+def rz_residual(x, y):
+    """r = w x - S y on the interior rows (0 on the electrode rows)."""
+    x = np.asarray(x, dtype=np.float64)
+    _, _, w = rz_weights(x.shape[-1])
+    r = w * x - rz_operator(y)
+    r[..., 0, :] = 0.0
+    r[..., -1, :] = 0.0
+    return r
+
+
+def backprop(params, hs, g, bf16=False):
+    """Parameter gradient in the packed layout from dL/da_6 = g [B, H, W, 1]
+    and the layer inputs hs of forward()."""
+    layers = unpack(params)
+    rnd = round_bf16 if bf16 else (lambda v: v)
+    grads = [None] * 6
+    for l in range(5, -1, -1):
+        W, _ = layers[l]
+        Wr = rnd(W)
+        h = hs[l]
+        gW = np.zeros_like(W)
+        for tap, (dy, dx) in enumerate(TAPS):
+            gW[tap] = np.einsum("bijc,bijd->cd", g, shift(h, dy, dx))
+        gb = g.sum(axis=(0, 1, 2))
+        grads[l] = (gW, gb)
+        if l == 0:
+            break
+        gh = np.zeros(h.shape)
+        for tap, (dy, dx) in enumerate(TAPS):
+            gh += shift(g, -dy, -dx) @ Wr[tap]
+        g = rnd(gh * (h > 0.0))
+    return pack(grads)
+
+
+def resid_loss_and_grad(params, x, bf16=False):
+    """Residual loss of the extrapolated form and its gradient: L = sum of
+    r^2 over the interior nodes / their number; dL/dy = -(2 / N) S r."""
+    y, hs = forward(params, x, bf16)
+    r = rz_residual(x, y)
+    n_int = y.shape[0] * (y.shape[1] - 2) * y.shape[2]
+    L = float((r * r).sum() / n_int)
+    g = (-2.0 / n_int) * rz_operator(r)
+    return L, backprop(params, hs, g[..., None], bf16)
+
+
+def training_pair_extrap(rho, phi, V, dz, rho1, phi1, V1, rho2, phi2, V2):
+    """(x, t) of the extrapolated form from the solve (rho, phi, V) and the
+    two before it (1: the previous one, 2: the one before)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    phi = np.asarray(phi, dtype=np.float64)
+    nz = rho.shape[0] - 1
+    zL = (np.arange(nz + 1)[:, None] / nz) * np.ones_like(rho)
+    d = rho - (2.0 * np.asarray(rho1, dtype=np.float64) - np.asarray(rho2, dtype=np.float64))
+    base = 2.0 * np.asarray(phi1, dtype=np.float64) - np.asarray(phi2, dtype=np.float64) + \
+        (V - 2.0 * V1 + V2) * zL
+    m = np.abs(d).max()
+    if m == 0.0:
+        return np.zeros_like(rho), np.zeros_like(rho)
+    return d / m, (phi - base) * EPS0 / (m * dz * dz)
 
 
 def adam_step(params, grad, m, v, k, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -173,3 +173,110 @@ def test_training_pairs_follow_eq8_linearity(xs):
     assert np.allclose(xd, xa, rtol=1e-10, atol=1e-12)
     assert np.allclose(td, ta, rtol=1e-7, atol=1e-7 * np.abs(ta).max())
     assert np.allclose(cnn.warm_start(td, m, V, dz, phi_prev=phi_b, V_prev=1.7e3), phi, rtol=1e-12, atol=1e-9 * V)
+
+
+def test_rz_operator_is_the_solvers_finite_volume_equation(xs):
+    """Through the oracle's own Poisson solve (conjugate gradients on its
+    finite-volume equations): the target t of a pair satisfies S t = w x on
+    the interior rows, to the solve's tolerance; S is symmetric.  Planted
+    mistakes (Verboncoeur's 1/6 for the axis volume, a face past the outer
+    radius) break the identity."""
+    cfg, parts = synthetic.rz_plume(n=16, total=6e3, seed=9)
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-13, oracle_poisson_tol=1e-13)
+    rho, phi = _solved(cfg, xs, parts)
+    x, t = cnn.training_pair(rho, phi, cfg["V0"], cfg["dz"])
+    _, _, w = cnn.rz_weights(x.shape[1])
+    scale = np.abs(w * x).max()
+    r = cnn.rz_residual(x, t)
+    assert np.abs(r).max() <= 1e-9 * scale
+    # symmetric on the interior rows
+    rng = np.random.default_rng(3)
+    a, b = rng.standard_normal((2,) + t.shape)
+    a[[0, -1]] = 0.0
+    b[[0, -1]] = 0.0
+    assert np.vdot(a, cnn.rz_operator(b)) == pytest.approx(np.vdot(cnn.rz_operator(a), b), rel=1e-12)
+    saved = cnn.rz_weights
+
+    def axis_sixth(W):
+        ap, am, w_ = saved(W)
+        w_ = w_.copy()
+        w_[0] = 1.0 / 6.0
+        return ap, am, w_
+
+    def outer_face(W):
+        ap, am, w_ = saved(W)
+        ap = ap.copy()
+        ap[-1] = W - 0.5
+        return ap, am, w_
+
+    for bad in (axis_sixth, outer_face):
+        cnn.rz_weights = bad
+        try:
+            assert np.abs(cnn.rz_residual(x, t)).max() > 1e-6 * scale, bad.__name__
+        finally:
+            cnn.rz_weights = saved
+
+
+def test_extrapolated_pair_is_the_pair_of_the_second_difference(xs):
+    """Linearity of Eq. (8): the extrapolated pair of three states equals the
+    absolute pair of rho - 2 rho' + rho'' solved with the anode at
+    V - 2 V' + V''; with states linear in time (rho'' , rho', rho equally
+    spaced) x and t vanish."""
+    cfg, parts = synthetic.rz_plume(n=16, total=6e3, seed=9)
+    cfg.update(field_on=1, inject_on=0, poisson_tol=1e-13, oracle_poisson_tol=1e-13)
+    dz = cfg["dz"]
+    thirds = [{k: v[q::3] for k, v in parts.items()} for q in range(3)]
+    two = {k: np.concatenate([thirds[0][k], thirds[1][k]]) for k in parts}
+    # states: rho2 = A (V 1.5 kV), rho1 = A + B (2.1 kV), rho = all (2.9 kV)
+    s2 = _solved(cfg, xs, thirds[0], V=1.5e3)
+    s1 = _solved(cfg, xs, two, V=2.1e3)
+    s0 = _solved(cfg, xs, parts, V=2.9e3)
+    x, t = cnn.training_pair_extrap(s0[0], s0[1], 2.9e3, dz, s1[0], s1[1], 2.1e3, s2[0], s2[1], 1.5e3)
+    # rho - 2 rho1 + rho2 = C - B (integer deposits add exactly): solved with
+    # V - 2 V1 + V2 = 0.2 kV it gives the same pair
+    sB = _solved(cfg, xs, thirds[1], V=0.0)
+    sC = _solved(cfg, xs, thirds[2], V=0.2e3)
+    d = s0[0] - 2.0 * s1[0] + s2[0]
+    assert np.allclose(d, sC[0] - sB[0], rtol=1e-12, atol=1e-12 * np.abs(d).max())
+    xa, ta = cnn.training_pair(sC[0] - sB[0], sC[1] - sB[1], 0.2e3, dz)
+    assert np.allclose(x, xa, rtol=1e-10, atol=1e-12)
+    assert np.allclose(t, ta, rtol=1e-7, atol=1e-7 * np.abs(ta).max())
+    # the exact target leaves no residual
+    _, _, w = cnn.rz_weights(x.shape[1])
+    assert np.abs(cnn.rz_residual(x, t)).max() <= 1e-9 * np.abs(w * x).max()
+    # equally spaced states: nothing for the network to add
+    x0, t0 = cnn.training_pair_extrap(s0[0], s0[1], 2.9e3, dz, s0[0], s0[1], 2.9e3, s0[0], s0[1], 2.9e3)
+    assert not x0.any() and not t0.any()
+
+
+def test_residual_loss_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    B, H, W = 2, 6, 7
+    x = rng.standard_normal((B, H, W))
+    p = cnn.init_params(6)
+    p[cnn.n_params() - 1] = 0.2
+    L, g = cnn.resid_loss_and_grad(p, x)
+    y, _ = cnn.forward(p, x)
+    r = cnn.rz_residual(x, y)
+    assert L == pytest.approx((r * r).sum() / (B * (H - 2) * W), rel=1e-14)
+    idx, o = [], 0
+    for nw, nb in cnn.layer_sizes():
+        idx += list(rng.choice(nw, size=min(nw, 30), replace=False) + o)
+        idx += list(range(o + nw, o + nw + nb))
+        o += nw + nb
+
+    def loss_of(q):
+        yq, _ = cnn.forward(q, x)
+        rq = cnn.rz_residual(x, yq)
+        return (rq * rq).sum() / (B * (H - 2) * W)
+
+    h = 1e-6
+    bad = 0
+    for k in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (loss_of(pp) - loss_of(pm)) / (2 * h)
+        if abs(fd - g[k]) > 1e-6 * abs(g).max() + 1e-4 * abs(g[k]):
+            bad += 1                       # a ReLU kink inside [-h, h]
+    assert bad <= 0.02 * len(idx)
