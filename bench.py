@@ -565,7 +565,7 @@ def run_ensemble(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-WS_METRIC = "Poisson multigrid cycles per step to relres 1e-8: cold vs previous-step vs learned warm start"
+WS_METRIC = "Poisson multigrid cycles per step to relres 1e-8: cold vs previous-step vs extrapolated vs learned warm start"
 
 
 def run_warmstart(args, ws, rank, local):
@@ -579,7 +579,8 @@ def run_warmstart(args, ws, rank, local):
     pd.load_library()
     xs = synthetic.standin_cross_sections()
     sizes = [int(v) for v in args.ws_sizes.split(",")]
-    kinds = ("absolute", "delta")
+    kinds = ("absolute", "delta", "extrap")
+    mode_of = {"absolute": "learned", "delta": "learned_delta", "extrap": "learned_extrap"}
     t0 = time.perf_counter()
     sets = {k: [] for k in kinds}
     held = {k: {} for k in kinds}
@@ -615,21 +616,31 @@ def run_warmstart(args, ws, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for k in kinds:
+        # the extrapolated form learns to cancel the residual its start leaves
+        lk = "rz" if k == "extrap" else "mse"
         net = pd.Net(max_nodes, params=p0, device=dev)
         torch.cuda.synchronize()
         e0.record(net.stream)
         hist = W.train(net, sets[k], args.ws_iters, batch, lr=1e-3, lr_final=5e-5,
-                       log_every=max(1, args.ws_iters // 10))
+                       log_every=max(1, args.ws_iters // 10), loss=lk)
         e1.record(net.stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        tl = {str(n): {"test_loss": W.test_loss(net, *held[k][n], batch=b),
-                       "test_target_mean_square": float(torch.mean(held[k][n][1].double() ** 2).item())}
-              for n, b in zip(sizes, batch)}
-        train_info[k] = {"loss_history": hist, "train_ms": ms, "ms_per_iter": ms / max(args.ws_iters, 1),
-                         "held_out": tl}
-        nets["learned" if k == "absolute" else "learned_delta"] = net
-    modes = ("previous", "extrapolate", "cold", "learned", "learned_delta")
+        tl = {}
+        for n, b in zip(sizes, batch):
+            X, T = held[k][n]
+            tl[str(n)] = {"test_loss": W.test_loss(net, X, T, batch=b, loss=lk),
+                          "test_target_mean_square": float(torch.mean(T.double() ** 2).item())}
+            if lk == "rz":
+                # the same loss of the uncorrected start (y = 0): the mean square of w x
+                w = torch.arange(n + 1, dtype=torch.float64, device=X.device)
+                w[0], w[n] = 0.125, n / 2.0 - 0.125
+                tl[str(n)]["loss_of_extrapolated_start"] = float(
+                    torch.mean((X[:, 1:-1, :].double() * w) ** 2).item())
+        train_info[k] = {"loss": lk, "loss_history": hist, "train_ms": ms,
+                         "ms_per_iter": ms / max(args.ws_iters, 1), "held_out": tl}
+        nets[mode_of[k]] = net
+    modes = ("previous", "extrapolate", "cold", "learned", "learned_delta", "learned_extrap")
     results = {str(n): W.compare_starts(*evals[n], xs, nets, args.ws_eval_steps, modes=modes, device=dev)
                for n in sizes}
     # inference time on the largest grid
@@ -646,7 +657,7 @@ def run_warmstart(args, ws, rank, local):
     infer_ms = e0.elapsed_time(e1) / 20
     flops = 2.0 * (n + 1) ** 2 * (9 * 32 * 2 + 4 * 9 * 32 * 32)
     big = results[str(n)]
-    best = min(("learned", "learned_delta"), key=lambda m: big[m]["cycles_per_step"])
+    best = min(("learned", "learned_delta", "learned_extrap"), key=lambda m: big[m]["cycles_per_step"])
     if rank == 0:
         line = {"metric": WS_METRIC, "value": big[best]["cycles_per_step"], "unit": "cycles/step",
                 "n_gpus": ws, "steps": args.ws_eval_steps, "warmup": 2,

@@ -125,6 +125,8 @@ typedef struct pd_scalars {
     double poisson_cycles;     /* last solve's multigrid cycles */
     double poisson_relres_max; /* largest final relative residual of the solves
                                   issued by the latest pd_step call */
+    double poisson_relres0;    /* last solve's relative residual at its start
+                                  (the quality of the warm start) */
     double absorbed_energy[3]; /* J absorbed at cathode, anode, outer wall */
     int64_t n_particles;       /* live particles */
     int64_t count[PD_NSP];     /* live particles per species */
@@ -355,11 +357,16 @@ pd_status pd_load(pd_sim* sim, const char* path);
  * density so that the multigrid solve starts closer to its answer; the solve
  * still runs to the configured residual.  Node arrays of one r-z run are
  * (nz + 1) x (nr + 1); z_i = i dz, L = nz dz; rho in C/m^3 (Verboncoeur's
- * node volumes, halved on the electrode rows).  Two formulations:
+ * node volumes, halved on the electrode rows).  Three formulations:
  *   absolute (PD_WARM_LEARNED): d = rho, base = V z / L;
  *   delta (PD_WARM_LEARNED_DELTA): d = rho - rho', base = phi' + (V - V') z / L,
  *     where rho', phi', V' belong to the previous solve;
- * and, for both, with m = max |d| over the run's nodes:
+ *   extrapolated (PD_WARM_LEARNED_EXTRAP): d = rho - (2 rho' - rho''),
+ *     base = 2 phi' - phi'' + (V - 2 V' + V'') z / L, with rho'', phi'', V''
+ *     of the solve before the previous one: the network corrects the
+ *     potential extrapolated linearly in time from the charge the
+ *     extrapolation misses;
+ * and, for all, with m = max |d| over the run's nodes:
  *   x = d / m  (x = 0 when m = 0)                       (network input)
  *   t = (phi - base) eps0 / (m dz^2)                    (training target)
  *   phi_0 = base + y m dz^2 / eps0                      (warm start from y ~ t)
@@ -370,7 +377,9 @@ pd_status pd_load(pd_sim* sim, const char* path);
  * W[tap][c_out][c_in], tap = 3 (dy + 1) + (dx + 1) for the input node at
  * (i + dy, j + dx), then its biases.  Layers compute with bfloat16 weights
  * and activations and float accumulation; the optimiser keeps float master
- * weights.  Loss: mean over samples and nodes of (y - t)^2; optimiser: Adam. */
+ * weights.  Loss: mean over samples and nodes of (y - t)^2 (pd_net_loss_grad),
+ * or the residual of Eq. (8) that the start leaves (pd_net_loss_grad_rz);
+ * optimiser: Adam. */
 #define PD_NET_NPARAMS 37601
 typedef struct pd_net pd_net;
 
@@ -391,29 +400,42 @@ pd_status pd_net_forward(pd_net* net, const float* x, int B, int H, int W, float
  * also kept for pd_net_adam.  Synchronises when loss or grads is given. */
 pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, int H, int W, double* loss,
                            float* grads);
+/* The same with the residual loss of a start phi_0 = base + y m dz^2 /
+ * eps0 on r-z grids with dz = dr: on the interior rows (1 .. H - 2; the
+ * electrode rows are Dirichlet and y is not used there)
+ *   r = w x - S y,
+ *   (S y)_ij = (a+_j + a-_j + 2 w_j) y_ij - a+_j y_i,j+1 - a-_j y_i,j-1
+ *              - w_j (y_i+1,j + y_i-1,j)   (y = 0 on rows 0 and H - 1),
+ * the finite-volume equations of Eq. (8) divided by 2 pi dr^3 m / eps0, with
+ * a+_j = j + 1/2 (0 at j = W - 1), a-_j = j - 1/2 (0 at j = 0), w_j = j,
+ * 1/8 at j = 0 and (W - 1)/2 - 1/8 at j = W - 1 (the node's finite volume
+ * over 2 pi dr^3); loss = sum of r^2 / (B (H - 2) W).  The target of the
+ * pair is not needed: the exact t gives r = 0.  H >= 3, W >= 2. */
+pd_status pd_net_loss_grad_rz(pd_net* net, const float* x, int B, int H, int W, double* loss, float* grads);
 /* One Adam step (b1, b2, eps as in Kingma and Ba) with the gradient of the
- * last pd_net_loss_grad. */
+ * last pd_net_loss_grad or pd_net_loss_grad_rz. */
 pd_status pd_net_adam(pd_net* net, float lr, float b1, float b2, float eps);
 
 /* Training pairs (x, t) of every run from the most recent solve (kind
- * PD_PAIRS_ABSOLUTE) or from the two most recent solves (PD_PAIRS_DELTA),
- * written to device float arrays laid out like the node arrays of
- * pd_get_phi.  PD_ERR_STATE until enough solves have run since the
- * simulation was created or loaded (one, or two for delta pairs). */
-enum { PD_PAIRS_ABSOLUTE = 0, PD_PAIRS_DELTA = 1 };
+ * PD_PAIRS_ABSOLUTE), the two most recent (PD_PAIRS_DELTA) or the three
+ * most recent (PD_PAIRS_EXTRAP), written to device float arrays laid out
+ * like the node arrays of pd_get_phi.  PD_ERR_STATE until enough solves have
+ * run since the simulation was created or loaded. */
+enum { PD_PAIRS_ABSOLUTE = 0, PD_PAIRS_DELTA = 1, PD_PAIRS_EXTRAP = 2 };
 pd_status pd_warmstart_pairs(pd_sim* sim, int kind, float* x, float* t);
 
 /* Starting point of each Poisson solve: PD_WARM_PREVIOUS (default: the
  * previous step's potential), PD_WARM_COLD (the charge-free potential
- * V z / L), PD_WARM_LEARNED or PD_WARM_LEARNED_DELTA (phi_0 from `net`,
- * which must stay alive and hold at least the simulation's node count; the
- * delta form falls back to the previous potential on the first solve after
- * create or load), PD_WARM_EXTRAPOLATE (linear in time through the two
- * previous solutions, 2 phi_{n-1} - phi_{n-2}, on the interior rows; the
- * previous potential until two solves have been made since create or
- * load).  r-z Poisson mode only.  Drops a captured graph. */
+ * V z / L), PD_WARM_LEARNED, PD_WARM_LEARNED_DELTA or PD_WARM_LEARNED_EXTRAP
+ * (phi_0 from `net`, which must stay alive and hold at least the
+ * simulation's node count; the delta and extrapolated forms fall back to the
+ * previous potential until one or two solves have been made since create or
+ * load), PD_WARM_EXTRAPOLATE (linear in time through the two previous
+ * solutions, 2 phi_{n-1} - phi_{n-2}, on the interior rows; the previous
+ * potential until two solves have been made since create or load).  r-z
+ * Poisson mode only.  Drops a captured graph. */
 enum { PD_WARM_PREVIOUS = 0, PD_WARM_COLD = 1, PD_WARM_LEARNED = 2, PD_WARM_LEARNED_DELTA = 3,
-       PD_WARM_EXTRAPOLATE = 4 };
+       PD_WARM_EXTRAPOLATE = 4, PD_WARM_LEARNED_EXTRAP = 5 };
 pd_status pd_set_warm_start(pd_sim* sim, int mode, pd_net* net);
 
 /* Kinetic-energy histogram (eV) of one species, computed from raw particle

@@ -27,7 +27,7 @@ __all__ = ["PdConfig", "PdScalars", "Simulation", "PdError", "load_library", "co
            "pd_load_particles_device_run", "pd_set_graph_mode", "PdTuning", "pd_get_tuning",
            "pd_set_tuning", "pd_autotune", "pd_save", "pd_load", "pd_get_rho_phi", "Net", "PD_NET_NPARAMS", "pd_net_workspace_size",
            "pd_net_create", "pd_net_destroy", "pd_net_set_params", "pd_net_get_params", "pd_net_forward",
-           "pd_net_loss_grad", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
+           "pd_net_loss_grad", "pd_net_loss_grad_rz", "pd_net_adam", "pd_warmstart_pairs", "pd_set_warm_start", "WARM_MODES",
            "COUNTER_NAMES", "KERNEL_NAMES", "EXPORTED"]
 
 PD_NCOUNTERS = 43
@@ -65,7 +65,7 @@ class PdScalars(C.Structure):
         ("t", C.c_double), ("V", C.c_double), ("I_gap", C.c_double), ("gamma", C.c_double),
         ("Qbar", C.c_double), ("erosion", C.c_double), ("mass", C.c_double), ("charge", C.c_double),
         ("sgmax", C.c_double * 2), ("poisson_relres", C.c_double), ("poisson_cycles", C.c_double),
-        ("poisson_relres_max", C.c_double),
+        ("poisson_relres_max", C.c_double), ("poisson_relres0", C.c_double),
         ("absorbed_energy", C.c_double * 3), ("n_particles", C.c_int64), ("count", C.c_int64 * 7),
         ("step", C.c_int64),
     ]
@@ -141,6 +141,7 @@ _SIGS = {
     "pd_net_get_params": (C.c_int, [P, P]),
     "pd_net_forward": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, P]),
     "pd_net_loss_grad": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, Dp, P]),
+    "pd_net_loss_grad_rz": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, Dp, P]),
     "pd_net_adam": (C.c_int, [P, C.c_float, C.c_float, C.c_float, C.c_float]),
     "pd_warmstart_pairs": (C.c_int, [P, C.c_int, P, P]),
     "pd_set_warm_start": (C.c_int, [P, C.c_int, P]),
@@ -468,8 +469,8 @@ def pd_get_rho_phi(h, nodes):
 
 
 PD_NET_NPARAMS = 37601
-WARM_MODES = {"previous": 0, "cold": 1, "learned": 2, "learned_delta": 3, "extrapolate": 4}
-PAIR_KINDS = {"absolute": 0, "delta": 1}
+WARM_MODES = {"previous": 0, "cold": 1, "learned": 2, "learned_delta": 3, "extrapolate": 4, "learned_extrap": 5}
+PAIR_KINDS = {"absolute": 0, "delta": 1, "extrap": 2}
 
 
 def pd_net_workspace_size(max_nodes):
@@ -517,6 +518,15 @@ def pd_net_loss_grad(h, x_ptr, t_ptr, B, H, W, want_loss=True, want_grads=False)
     _net_check(h, _lib().pd_net_loss_grad(h, P(x_ptr), P(t_ptr), int(B), int(H), int(W),
                                          C.byref(loss) if want_loss else None,
                                          _ptr(g) if want_grads else None), "pd_net_loss_grad")
+    return (loss.value if want_loss else None), g
+
+
+def pd_net_loss_grad_rz(h, x_ptr, B, H, W, want_loss=True, want_grads=False):
+    loss = C.c_double(0.0)
+    g = np.zeros(PD_NET_NPARAMS, np.float32) if want_grads else None
+    _net_check(h, _lib().pd_net_loss_grad_rz(h, P(x_ptr), int(B), int(H), int(W),
+                                            C.byref(loss) if want_loss else None,
+                                            _ptr(g) if want_grads else None), "pd_net_loss_grad_rz")
     return (loss.value if want_loss else None), g
 
 
@@ -644,6 +654,11 @@ class Net:
         B, H, W = x.shape
         return pd_net_loss_grad(self.h, x.data_ptr(), t.data_ptr(), B, H, W, True, want_grads)
 
+    def loss_grad_rz(self, x, want_grads=False):
+        x = x.contiguous()
+        B, H, W = x.shape
+        return pd_net_loss_grad_rz(self.h, x.data_ptr(), B, H, W, True, want_grads)
+
     def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         pd_net_adam(self.h, lr, b1, b2, eps)
 
@@ -715,7 +730,7 @@ class Simulation:
         pd_save(self.h, path)
 
     def warmstart_pairs(self, kind="absolute"):
-        """(x, t) training pairs ("absolute" or "delta") of the latest solves
+        """(x, t) training pairs ("absolute", "delta" or "extrap") of the latest solves
         as torch CUDA tensors over all nodes (runs end to end)."""
         import torch
         x = torch.empty(self.nodes, dtype=torch.float32, device=self.ws.device)

@@ -58,7 +58,7 @@ struct Layout {
         mid, big, rho_e,
         rho_h, diag, E,
         phi, xsE, xs, ck, ray, hist, spc, state, rs, runs, cell_run, circ, ic, field, wsx, wsy, rmax, grp_base,
-        rho_last, rho_prev, phi_prev, V_last, V_prev;
+        rho_last, rho_prev, rho_prev2, phi_prev, phi_prev2, V_last, V_prev, V_prev2;
     uint32_t nbins_pad, ncell_pad, words_pad, bigq_cap;
     int nsp;                         // species with bins
     uint32_t squeue_cap;             // sputtering impacts per step
@@ -162,9 +162,12 @@ Layout make_layout(const std::vector<pd_config>& cf) {
     L.grp_base = take(R * 4);
     L.rho_last = take(nodes * 8);                          // solve history of the warm start
     L.rho_prev = take(nodes * 8);
+    L.rho_prev2 = take(nodes * 8);
     L.phi_prev = take(nodes * 8);
+    L.phi_prev2 = take(nodes * 8);
     L.V_last = take(R * 8);
     L.V_prev = take(R * 8);
+    L.V_prev2 = take(R * 8);
     L.total = o;
     return L;
 }
@@ -612,17 +615,22 @@ pd_status warm_start(pd_sim* s, int* kernels) {
     const bool extrapolate = s->warm_mode == PD_WARM_EXTRAPOLATE && s->solves >= 2;
     warm_history(s->field, s->rho_e, s->rho_h, s->runs_dev, s->rs, s->phi, s->whist, extrapolate, s->stream);
     *kernels += 1;
-    const bool delta = s->warm_mode == PD_WARM_LEARNED_DELTA;
+    // the learned forms need one (delta) or two (extrapolated) earlier
+    // solves; until then the previous potential stands
+    int form = -1;
+    if (s->warm_mode == PD_WARM_LEARNED) form = WARM_ABSOLUTE;
+    else if (s->warm_mode == PD_WARM_LEARNED_DELTA && s->solves >= 1) form = WARM_DELTA;
+    else if (s->warm_mode == PD_WARM_LEARNED_EXTRAP && s->solves >= 2) form = WARM_EXTRAP;
     if (s->warm_mode == PD_WARM_COLD) {
-        warm_apply(s->field, nullptr, s->whist, false, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+        warm_apply(s->field, nullptr, s->whist, WARM_ABSOLUTE, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
         *kernels += 1;
-    } else if (s->warm_mode == PD_WARM_LEARNED || (delta && s->solves >= 1)) {
-        warm_inputs(s->field, s->whist, delta, s->runs_dev, s->rmax, s->wsx, s->stream);
+    } else if (form >= 0) {
+        warm_inputs(s->field, s->whist, form, s->runs_dev, s->rmax, s->wsx, s->stream);
         for (const auto& g : s->groups)
             if (net_forward_at(s->warm_net, s->wsx, s->wsy, g.B, g.H, g.W, s->grp_base + g.first,
                                (int64_t)total_nodes(s), s->stream))
                 return PD_ERR_CUDA;
-        warm_apply(s->field, s->wsy, s->whist, delta, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
+        warm_apply(s->field, s->wsy, s->whist, form, s->runs_dev, s->rs, s->rmax, s->phi, s->stream);
         *kernels += 3 + 6 * (int)s->groups.size();   // rmax, x, apply; six layers per group
     }
     s->solves += 1;
@@ -778,7 +786,7 @@ int graph_period(const pd_sim* s) {
 
 // ---- checkpoint file: a header, then the sections in a fixed order ----
 constexpr char CKPT_MAGIC[8] = {'P', 'D', 'C', 'K', 'P', 'T', '0', '1'};
-constexpr uint32_t CKPT_VERSION = 3;
+constexpr uint32_t CKPT_VERSION = 4;
 
 struct CkptHeader {
     char magic[8];
@@ -990,8 +998,9 @@ pd_status create_common(const pd_config* cfgs, int n, void* ws, size_t bytes, vo
     s->warm_net = nullptr;
     s->version = 1;
     s->spc_version = 0;
-    s->whist = WarmHistory{(double*)(w + L.rho_last), (double*)(w + L.rho_prev), (double*)(w + L.phi_prev),
-                          (double*)(w + L.V_last), (double*)(w + L.V_prev)};
+    s->whist = WarmHistory{(double*)(w + L.rho_last), (double*)(w + L.rho_prev), (double*)(w + L.rho_prev2),
+                          (double*)(w + L.phi_prev), (double*)(w + L.phi_prev2), (double*)(w + L.V_last),
+                          (double*)(w + L.V_prev), (double*)(w + L.V_prev2)};
     s->solves = 0;
     for (int k = 0; k < XS_N; ++k) {
         const int ex = XS_EMIN_EXP + k / XS_SUB, j = k % XS_SUB;
@@ -1224,6 +1233,7 @@ pd_status run_scalars(pd_sim* s, int run, pd_scalars* out) {
     out->poisson_relres = d.relres;
     out->poisson_cycles = d.cycles;
     out->poisson_relres_max = d.relres_max;
+    out->poisson_relres0 = d.relres0;
     for (int k = 0; k < 3; ++k) out->absorbed_energy[k] = d.absorbed_energy[k];
     int64_t tot = 0;
     for (int sp = 0; sp < NSP; ++sp) {
@@ -1623,17 +1633,18 @@ pd_status pd_get_rho_phi(pd_sim* s, double* rho, double* phi) {
 }
 
 pd_status pd_warmstart_pairs(pd_sim* s, int kind, float* x, float* t) {
-    if (!s || !x || !t || (kind != PD_PAIRS_ABSOLUTE && kind != PD_PAIRS_DELTA)) return PD_ERR_ARG;
+    if (!s || !x || !t || (kind != PD_PAIRS_ABSOLUTE && kind != PD_PAIRS_DELTA && kind != PD_PAIRS_EXTRAP))
+        return PD_ERR_ARG;
     if (s->cfgs[0].field_mode != PD_FIELD_POISSON) return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
     if (!s->primed) {
         pd_status r = prime(s);
         if (r != PD_OK) return r;
     }
-    if (s->solves < (kind == PD_PAIRS_DELTA ? 2 : 1))
+    if (s->solves < 1 + kind)
         return fail(s, PD_ERR_STATE, "not enough solves since create or load for these pairs");
-    const bool delta = kind == PD_PAIRS_DELTA;
-    warm_inputs(s->field, s->whist, delta, s->runs_dev, s->rmax, x, s->stream);
-    warm_targets(s->field, s->phi, s->whist, delta, s->runs_dev, s->rmax, t, s->stream);
+    const int form = kind == PD_PAIRS_DELTA ? WARM_DELTA : kind == PD_PAIRS_EXTRAP ? WARM_EXTRAP : WARM_ABSOLUTE;
+    warm_inputs(s->field, s->whist, form, s->runs_dev, s->rmax, x, s->stream);
+    warm_targets(s->field, s->phi, s->whist, form, s->runs_dev, s->rmax, t, s->stream);
     CK(cudaGetLastError());
     return PD_OK;
 }
@@ -1641,11 +1652,11 @@ pd_status pd_warmstart_pairs(pd_sim* s, int kind, float* x, float* t) {
 pd_status pd_set_warm_start(pd_sim* s, int mode, pd_net* net) {
     if (!s) return PD_ERR_ARG;
     if (mode != PD_WARM_PREVIOUS && mode != PD_WARM_COLD && mode != PD_WARM_LEARNED && mode != PD_WARM_LEARNED_DELTA &&
-        mode != PD_WARM_EXTRAPOLATE)
+        mode != PD_WARM_EXTRAPOLATE && mode != PD_WARM_LEARNED_EXTRAP)
         return fail(s, PD_ERR_ARG, "bad warm-start mode");
     if (mode != PD_WARM_PREVIOUS && s->cfgs[0].field_mode != PD_FIELD_POISSON)
         return fail(s, PD_ERR_STATE, "warm start needs the Poisson field");
-    const bool learned = mode == PD_WARM_LEARNED || mode == PD_WARM_LEARNED_DELTA;
+    const bool learned = mode == PD_WARM_LEARNED || mode == PD_WARM_LEARNED_DELTA || mode == PD_WARM_LEARNED_EXTRAP;
     if (learned) {
         if (!net) return fail(s, PD_ERR_ARG, "learned warm start needs a network");
         if (net_max_nodes(net) < (int64_t)total_nodes(s))

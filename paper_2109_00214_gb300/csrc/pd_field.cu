@@ -249,6 +249,7 @@ __global__ void k_norms(const double* red, double* bnorm, int* done, const doubl
     const double rel = bn > 0 ? rn / bn : 0.0;
     rs[run].relres = rel;
     rs[run].cycles = (double)cycle;
+    if (first) rs[run].relres0 = rel;
     if (!(rel == rel) || !(bn == bn)) {
         done[run] = 2;              // non-finite: stop this run
         return;
@@ -916,8 +917,9 @@ __device__ __forceinline__ double node_rho(const long long* rho_e, const long lo
     return qw * (double)(rho_e[g] + rho_h[g]) * (T.iv[j] * f);
 }
 
-// history shift at the start of a solve: rho_prev := rho_last, phi_prev :=
-// phi, V_prev := V_last; then rho_last := current density, V_last := V
+// history shift at the start of a solve: rho_prev2 := rho_prev, rho_prev :=
+// rho_last, phi_prev2 := phi_prev, phi_prev := phi, V_prev2 := V_prev,
+// V_prev := V_last; then rho_last := current density, V_last := V
 __global__ void k_warm_history(const long long* rho_e, const long long* rho_h, const MGTop* top,
                                const RunInfo* runs, const RunState* rs, WarmHistory h, int extrapolate) {
     const int run = blockIdx.y;
@@ -928,36 +930,69 @@ __global__ void k_warm_history(const long long* rho_e, const long long* rho_h, c
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W, j = k - i * W;
         const uint32_t g = RI.node_base + (uint32_t)k;
+        h.rho_prev2[g] = h.rho_prev[g];
         h.rho_prev[g] = h.rho_last[g];
-        const double p = T.phi[k];
-        if (extrapolate && i > 0 && i < T.nz) T.phi[k] = 2.0 * p - h.phi_prev[g];
+        const double p = T.phi[k], pp = h.phi_prev[g];
+        if (extrapolate && i > 0 && i < T.nz) T.phi[k] = 2.0 * p - pp;
+        h.phi_prev2[g] = pp;
         h.phi_prev[g] = p;
         h.rho_last[g] = node_rho(rho_e, rho_h, T, qw, i, j, g);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h.V_prev2[run] = h.V_prev[run];
         h.V_prev[run] = h.V_last[run];
         h.V_last[run] = rs[run].V;
     }
 }
 
-// d = rho_last - ref (ref null: 0); rmax[run] = max |d|
-__global__ void k_warm_rmax(const double* rho_last, const double* ref, const RunInfo* runs,
-                            unsigned long long* rmax_bits) {
+// The references of a form: d = rho_last - c1 rho1 - c2 rho2 and base =
+// c1 phi1 + c2 phi2 + (V - c1 V1 - c2 V2) z / L (absent terms: 0)
+struct WarmRef {
+    const double *rho1, *rho2, *phi1, *phi2, *V1, *V2;
+    double c1, c2;
+};
+
+WarmRef warm_ref(const WarmHistory& h, int form) {
+    WarmRef r{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0};
+    if (form == WARM_DELTA) {
+        r.rho1 = h.rho_prev;
+        r.phi1 = h.phi_prev;
+        r.V1 = h.V_prev;
+        r.c1 = 1.0;
+    } else if (form == WARM_EXTRAP) {
+        r.rho1 = h.rho_prev;
+        r.phi1 = h.phi_prev;
+        r.V1 = h.V_prev;
+        r.c1 = 2.0;
+        r.rho2 = h.rho_prev2;
+        r.phi2 = h.phi_prev2;
+        r.V2 = h.V_prev2;
+        r.c2 = -1.0;
+    }
+    return r;
+}
+
+__device__ __forceinline__ double warm_d(const double* rho_last, const WarmRef& R, uint32_t g) {
+    double d = rho_last[g];
+    if (R.rho1) d -= R.c1 * R.rho1[g];
+    if (R.rho2) d -= R.c2 * R.rho2[g];
+    return d;
+}
+
+// rmax[run] = max |d|
+__global__ void k_warm_rmax(const double* rho_last, WarmRef R, const RunInfo* runs, unsigned long long* rmax_bits) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const int n = (RI.nz + 1) * (RI.nr + 1);
     double m = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t g = RI.node_base + (uint32_t)k;
-        m = fmax(m, fabs(rho_last[g] - (ref ? ref[g] : 0.0)));
-    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        m = fmax(m, fabs(warm_d(rho_last, R, RI.node_base + (uint32_t)k)));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
     // non-negative doubles order like their bit patterns
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(&rmax_bits[run], (unsigned long long)__double_as_longlong(m));
 }
 
-__global__ void k_warm_x(const double* rho_last, const double* ref, const RunInfo* runs, const double* rmax,
-                         float* x) {
+__global__ void k_warm_x(const double* rho_last, WarmRef R, const RunInfo* runs, const double* rmax, float* x) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const int n = (RI.nz + 1) * (RI.nr + 1);
@@ -965,47 +1000,54 @@ __global__ void k_warm_x(const double* rho_last, const double* ref, const RunInf
     const double irm = rm > 0.0 ? 1.0 / rm : 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t g = RI.node_base + (uint32_t)k;
-        x[g] = (float)((rho_last[g] - (ref ? ref[g] : 0.0)) * irm);
+        x[g] = (float)(warm_d(rho_last, R, g) * irm);
     }
 }
 
-// the potential the prediction is added to: V z / L, or with a reference
-// phi_ref + (V - V_ref) z / L
-__device__ __forceinline__ double warm_base(const double* phi_ref, double V, double V_ref, uint32_t g, int i,
-                                            double inz) {
-    return phi_ref ? phi_ref[g] + (V - V_ref) * ((double)i * inz) : V * ((double)i * inz);
+// the potential the prediction is added to
+__device__ __forceinline__ double warm_base(const WarmRef& R, int run, double V, uint32_t g, int i, double inz) {
+    double b = 0.0, Vr = 0.0;
+    if (R.phi1) {
+        b += R.c1 * R.phi1[g];
+        Vr += R.c1 * R.V1[run];
+    }
+    if (R.phi2) {
+        b += R.c2 * R.phi2[g];
+        Vr += R.c2 * R.V2[run];
+    }
+    return b + (V - Vr) * ((double)i * inz);
 }
 
 __global__ void k_warm_apply(const float* y, const MGTop* top, const RunInfo* runs, const RunState* rs,
-                             const double* rmax, const double* phi_ref, const double* V_ref, double* phi) {
+                             const double* rmax, WarmRef R, double* phi) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const MGTop T = top[run];
     const int W = RI.nr + 1, n = (RI.nz - 1) * W;
-    const double V = rs[run].V, Vr = V_ref ? V_ref[run] : 0.0, inz = 1.0 / (double)RI.nz;
+    const double V = rs[run].V, inz = 1.0 / (double)RI.nz;
     const double dz = 1.0 / T.idz;
     const double sc = y ? rmax[run] * dz * dz / EPS0_ : 0.0;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const int i = 1 + q / W;
         const uint32_t g = RI.node_base + (uint32_t)(W + q);
-        const double base = warm_base(phi_ref, V, Vr, g, i, inz);
+        const double base = warm_base(R, run, V, g, i, inz);
         phi[g] = y ? base + (double)y[g] * sc : base;
     }
 }
 
 __global__ void k_warm_targets(const double* phi, const MGTop* top, const RunInfo* runs, const double* V_last,
-                               const double* rmax, const double* phi_ref, const double* V_ref, float* t) {
+                               const double* rmax, WarmRef R, float* t) {
     const int run = blockIdx.y;
     const RunInfo& RI = runs[run];
     const MGTop T = top[run];
     const int W = RI.nr + 1, n = (RI.nz + 1) * W;
-    const double V = V_last[run], Vr = V_ref ? V_ref[run] : 0.0, rm = rmax[run], inz = 1.0 / (double)RI.nz;
+    const double V = V_last[run], rm = rmax[run], inz = 1.0 / (double)RI.nz;
     const double dz = 1.0 / T.idz;
     const double sc = rm > 0.0 ? EPS0_ / (rm * dz * dz) : 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int i = k / W;
         const uint32_t g = RI.node_base + (uint32_t)k;
-        t[g] = (float)((phi[g] - warm_base(phi_ref, V, Vr, g, i, inz)) * sc);
+        t[g] = (float)((phi[g] - warm_base(R, run, V, g, i, inz)) * sc);
     }
 }
 
@@ -1016,27 +1058,25 @@ void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_
     k_warm_history<<<g, fs.threads, 0, s>>>(rho_e, rho_h, fs.top, runs, rs, h, extrapolate ? 1 : 0);
 }
 
-void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,
+void warm_inputs(FieldSolver& fs, const WarmHistory& h, int form, const RunInfo* runs, double* rmax, float* x,
                  cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    const double* ref = delta ? h.rho_prev : nullptr;
+    const WarmRef R = warm_ref(h, form);
     cudaMemsetAsync(rmax, 0, (size_t)fs.nruns * 8, s);
-    k_warm_rmax<<<g, fs.threads, 0, s>>>(h.rho_last, ref, runs, (unsigned long long*)rmax);
-    k_warm_x<<<g, fs.threads, 0, s>>>(h.rho_last, ref, runs, rmax, x);
+    k_warm_rmax<<<g, fs.threads, 0, s>>>(h.rho_last, R, runs, (unsigned long long*)rmax);
+    k_warm_x<<<g, fs.threads, 0, s>>>(h.rho_last, R, runs, rmax, x);
 }
 
-void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, bool delta, const RunInfo* runs,
+void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, int form, const RunInfo* runs,
                 const RunState* rs, const double* rmax, double* phi, cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    k_warm_apply<<<g, fs.threads, 0, s>>>(y, fs.top, runs, rs, rmax, delta ? h.phi_prev : nullptr,
-                                          delta ? h.V_prev : nullptr, phi);
+    k_warm_apply<<<g, fs.threads, 0, s>>>(y, fs.top, runs, rs, rmax, warm_ref(h, form), phi);
 }
 
-void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, bool delta, const RunInfo* runs,
+void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, int form, const RunInfo* runs,
                   const double* rmax, float* t, cudaStream_t s) {
     const dim3 g(blocks_for(fs, fs.max_nodes0), fs.nruns);
-    k_warm_targets<<<g, fs.threads, 0, s>>>(phi, fs.top, runs, h.V_last, rmax, delta ? h.phi_prev : nullptr,
-                                            delta ? h.V_prev : nullptr, t);
+    k_warm_targets<<<g, fs.threads, 0, s>>>(phi, fs.top, runs, h.V_last, rmax, warm_ref(h, form), t);
 }
 
 }  // namespace pd

@@ -91,26 +91,35 @@ void field_efield(FieldSolver& fs, const double* phi, const RunInfo* runs, float
 struct WarmHistory {
     double* rho_last;   // density of the most recent solve
     double* rho_prev;   // density of the solve before it
+    double* rho_prev2;  // density of the solve before that
     double* phi_prev;   // potential of the solve before the most recent one
+    double* phi_prev2;  // potential of the solve before that
     double* V_last;     // [runs] anode voltage of the most recent solve
     double* V_prev;     // [runs] of the one before
+    double* V_prev2;    // [runs] of the one before that
 };
+// Forms of the learned start: the reference the network's input and the
+// base of its output are taken against.
+//   absolute: d = rho, base = V z / L
+//   delta: d = rho - rho', base = phi' + (V - V') z / L
+//   extrapolated: d = rho - (2 rho' - rho''),
+//                 base = 2 phi' - phi'' + (V - 2 V' + V'') z / L
+enum WarmForm { WARM_ABSOLUTE = 0, WARM_DELTA = 1, WARM_EXTRAP = 2 };
 // at the start of every solve: shift the history and record the current
 // density (Verboncoeur volumes, halved on the electrode rows) and voltage;
 // with `extrapolate`, phi := 2 phi - phi_prev on the interior rows (phi_prev
 // taken before the shift)
 void warm_history(FieldSolver& fs, const long long* rho_e, const long long* rho_h, const RunInfo* runs,
                   const RunState* rs, double* phi, const WarmHistory& h, bool extrapolate, cudaStream_t s);
-// d = rho_last (- rho_prev when delta); rmax[run] = max |d|; x = d / rmax
-void warm_inputs(FieldSolver& fs, const WarmHistory& h, bool delta, const RunInfo* runs, double* rmax, float* x,
+// d of the form; rmax[run] = max |d|; x = d / rmax
+void warm_inputs(FieldSolver& fs, const WarmHistory& h, int form, const RunInfo* runs, double* rmax, float* x,
                  cudaStream_t s);
-// interior rows of phi := base + y rmax dz^2 / eps0, base = V z / L or, with
-// delta, phi_prev + (V - V_prev) z / L (y = null: the base alone)
-void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, bool delta, const RunInfo* runs,
+// interior rows of phi := base + y rmax dz^2 / eps0 (y = null: the base alone)
+void warm_apply(FieldSolver& fs, const float* y, const WarmHistory& h, int form, const RunInfo* runs,
                 const RunState* rs, const double* rmax, double* phi, cudaStream_t s);
 // training targets t = (phi - base) eps0 / (rmax dz^2) at every node, with
 // the voltages of the history (call after a solve)
-void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, bool delta, const RunInfo* runs,
+void warm_targets(FieldSolver& fs, const double* phi, const WarmHistory& h, int form, const RunInfo* runs,
                   const double* rmax, float* t, cudaStream_t s);
 
 }  // namespace pd

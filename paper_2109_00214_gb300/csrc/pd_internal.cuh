@@ -99,6 +99,7 @@ struct RunState {
     double relres;                   // last Poisson relative residual
     double cycles;                   // last Poisson cycles
     double relres_max;               // largest final residual of the solves since it was last cleared
+    double relres0;                  // last Poisson relative residual at the start of the solve
     unsigned int id_next;            // next particle id of the run
     unsigned int pad0;
 };

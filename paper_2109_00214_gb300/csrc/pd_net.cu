@@ -261,6 +261,67 @@ __global__ void __launch_bounds__(256) k_loss(const float* __restrict__ y, const
     if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
+// residual loss of a start on an r-z grid (dz = dr): the unit finite-volume
+// coefficients of radial node j of W, and (S v)_ij on an interior row with
+// rows 0 and H - 1 of v read as zero (Dirichlet)
+__device__ __forceinline__ void rz_coeffs(int j, int W, float& ap, float& am, float& w) {
+    const int nr = W - 1;
+    ap = j < nr ? (float)j + 0.5f : 0.0f;
+    am = j > 0 ? (float)j - 0.5f : 0.0f;
+    w = j == 0 ? 0.125f : (j == nr ? 0.5f * (float)nr - 0.125f : (float)j);
+}
+__device__ __forceinline__ float rz_apply(const float* __restrict__ v, size_t k, int H, int W, int i, int j) {
+    float ap, am, w;
+    rz_coeffs(j, W, ap, am, w);
+    float s = (ap + am + 2.0f * w) * v[k];
+    if (j + 1 < W) s -= ap * v[k + 1];
+    if (j > 0) s -= am * v[k - 1];
+    if (i + 1 < H - 1) s -= w * v[k + W];
+    if (i - 1 > 0) s -= w * v[k - W];
+    return s;
+}
+
+// r = w x - S y on the interior rows (0 on the electrode rows) and
+// per-block partial sums of r^2
+__global__ void __launch_bounds__(256) k_rz_resid(const float* __restrict__ x, const float* __restrict__ y,
+                                                  float* __restrict__ r, double* part, int B, int H, int W) {
+    const long long n = (long long)B * H * W;
+    double acc = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(p % ((long long)H * W)), i = q / W, j = q - i * W;
+        if (i == 0 || i == H - 1) {
+            r[p] = 0.0f;
+            continue;
+        }
+        float ap, am, w;
+        rz_coeffs(j, W, ap, am, w);
+        const float v = w * x[p] - rz_apply(y, (size_t)p, H, W, i, j);
+        r[p] = v;
+        acc += (double)v * (double)v;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// g = scale S r on the interior rows, 0 on the electrode rows (S is
+// symmetric, so this is scale S^T r)
+__global__ void __launch_bounds__(256) k_rz_resid_grad(const float* __restrict__ r, float* __restrict__ g, float scale,
+                                                       int B, int H, int W) {
+    const long long n = (long long)B * H * W;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(p % ((long long)H * W)), i = q / W, j = q - i * W;
+        g[p] = (i == 0 || i == H - 1) ? 0.0f : scale * rz_apply(r, (size_t)p, H, W, i, j);
+    }
+}
+
 __global__ void k_loss_sum(const double* part, int n, double inv_count, double* out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         double s = 0.0;
@@ -685,22 +746,21 @@ pd_status pd_net_forward(pd_net* net, const float* x, int B, int H, int W, float
     return e == cudaSuccess ? PD_OK : net_fail(net, PD_ERR_CUDA, cudaGetErrorString(e));
 }
 
-pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, int H, int W, double* loss,
-                           float* grads) {
-    if (!net || !x || !t) return PD_ERR_ARG;
-    if (!shape_ok(net, B, H, W)) return net_fail(net, PD_ERR_ARG, "batch exceeds the network's node capacity");
+}  // extern "C"
+
+namespace {
+
+// back-propagation of the output gradient g6 (B H W floats) to the
+// parameter gradient, and the loss and gradient out to the host if asked
+pd_status backprop(pd_net* net, const float* x, const float* g6, int B, int H, int W, double* loss, float* grads) {
     cudaStream_t s = net->stream;
     const long long total = (long long)B * H * W;
-    forward_layers(net, x, net->ybuf, B, H, W, nullptr, s);
-    const int lb = (int)std::min<long long>(LOSS_BLOCKS, (total + 255) / 256);
-    k_loss<<<lb, 256, 0, s>>>(net->ybuf, t, net->g6, net->lpart, total);
-    k_loss_sum<<<1, 32, 0, s>>>(net->lpart, lb, 1.0 / (double)total, net->lsum);
     const int pb = part_blocks(net);
     const int eb = elem_blocks(net, total);
     // layer 6
-    k_wgrad6<<<pb, 320, 0, s>>>(net->g6, net->h[4], net->part, B, H, W);
+    k_wgrad6<<<pb, 320, 0, s>>>(g6, net->h[4], net->part, B, H, W);
     k_reduce<<<2, 160, 0, s>>>(net->part, pb, 9 * CH + 1, 9 * CH + 1, net->grad + off_w(5));
-    k_conv6_bwd<<<eb, 256, 0, s>>>(net->g6, net->h[4], net->g[4], net->w6r, B, H, W);
+    k_conv6_bwd<<<eb, 256, 0, s>>>(g6, net->h[4], net->g[4], net->w6r, B, H, W);
     // layers 5 .. 2
     const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, B);
     for (int l = 4; l >= 1; --l) {
@@ -721,6 +781,39 @@ pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, i
     if (e == cudaSuccess && grads) e = cudaMemcpyAsync(grads, net->grad, NP * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && (loss || grads)) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? PD_OK : net_fail(net, PD_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_net_loss_grad(pd_net* net, const float* x, const float* t, int B, int H, int W, double* loss,
+                           float* grads) {
+    if (!net || !x || !t) return PD_ERR_ARG;
+    if (!shape_ok(net, B, H, W)) return net_fail(net, PD_ERR_ARG, "batch exceeds the network's node capacity");
+    cudaStream_t s = net->stream;
+    const long long total = (long long)B * H * W;
+    forward_layers(net, x, net->ybuf, B, H, W, nullptr, s);
+    const int lb = (int)std::min<long long>(LOSS_BLOCKS, (total + 255) / 256);
+    k_loss<<<lb, 256, 0, s>>>(net->ybuf, t, net->g6, net->lpart, total);
+    k_loss_sum<<<1, 32, 0, s>>>(net->lpart, lb, 1.0 / (double)total, net->lsum);
+    return backprop(net, x, net->g6, B, H, W, loss, grads);
+}
+
+pd_status pd_net_loss_grad_rz(pd_net* net, const float* x, int B, int H, int W, double* loss, float* grads) {
+    if (!net || !x) return PD_ERR_ARG;
+    if (!shape_ok(net, B, H, W) || H < 3 || W < 2)
+        return net_fail(net, PD_ERR_ARG, "batch exceeds the network's node capacity, or a grid below 3 x 2 nodes");
+    cudaStream_t s = net->stream;
+    const long long total = (long long)B * H * W, n_int = (long long)B * (H - 2) * W;
+    forward_layers(net, x, net->ybuf, B, H, W, nullptr, s);
+    const int lb = (int)std::min<long long>(LOSS_BLOCKS, (total + 255) / 256);
+    // r into g6, then dL/dy = -(2 / N) S r into ybuf (y is not needed after r)
+    k_rz_resid<<<lb, 256, 0, s>>>(x, net->ybuf, net->g6, net->lpart, B, H, W);
+    k_loss_sum<<<1, 32, 0, s>>>(net->lpart, lb, 1.0 / (double)n_int, net->lsum);
+    k_rz_resid_grad<<<elem_blocks(net, total), 256, 0, s>>>(net->g6, net->ybuf, (float)(-2.0 / (double)n_int), B, H,
+                                                           W);
+    return backprop(net, x, net->ybuf, B, H, W, loss, grads);
 }
 
 pd_status pd_net_adam(pd_net* net, float lr, float b1, float b2, float eps) {

@@ -35,13 +35,15 @@ def collect_pairs(cfgs, loads, xs, n_pairs, every=2, warmup=2, kinds=("absolute"
     return out
 
 
-def train(net, sets, iters, batch, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
+def train(net, sets, iters, batch, lr=1e-3, lr_final=1e-4, seed=0, log_every=0, loss="mse"):
     """Adam on mini-batches drawn from `sets` (a list of (X, T) tensors of
     shape [n, H, W], one per grid shape, used in turn).  The learning rate
-    decays geometrically from lr to lr_final.  Returns the loss history
+    decays geometrically from lr to lr_final.  `loss`: "mse" against the
+    targets T, or "rz", the residual of Eq. (8) that the start leaves
+    (pd_net_loss_grad_rz; T unused).  Returns the loss history
     [(iteration, loss)] taken every `log_every` iterations."""
     import torch
-    from . import pd_net_loss_grad
+    from . import pd_net_loss_grad, pd_net_loss_grad_rz
     g = torch.Generator(device=sets[0][0].device)
     g.manual_seed(seed)
     hist = []
@@ -52,20 +54,23 @@ def train(net, sets, iters, batch, lr=1e-3, lr_final=1e-4, seed=0, log_every=0):
         xb, tb = X[idx].contiguous(), T[idx].contiguous()
         want = bool(log_every) and (it % log_every == 0 or it == iters - 1)
         # the loss is read back (a synchronisation) only on logged iterations
-        loss, _ = pd_net_loss_grad(net.h, xb.data_ptr(), tb.data_ptr(), b, X.shape[1], X.shape[2], want, False)
+        if loss == "rz":
+            lv, _ = pd_net_loss_grad_rz(net.h, xb.data_ptr(), b, X.shape[1], X.shape[2], want, False)
+        else:
+            lv, _ = pd_net_loss_grad(net.h, xb.data_ptr(), tb.data_ptr(), b, X.shape[1], X.shape[2], want, False)
         net.adam(lr=lr * (lr_final / lr) ** (it / max(iters - 1, 1)))
         if want:
-            hist.append((it, loss))
+            hist.append((it, lv))
     return hist
 
 
-def test_loss(net, X, T, batch=4):
+def test_loss(net, X, T, batch=4, loss="mse"):
     """Mean loss over the pairs of (X, T) ([n, H, W] device tensors)."""
     tot, n = 0.0, 0
     for s in range(0, X.shape[0], batch):
         xb, tb = X[s:s + batch].contiguous(), T[s:s + batch].contiguous()
-        loss, _ = net.loss_grad(xb, tb)
-        tot += loss * xb.shape[0]
+        lv, _ = net.loss_grad_rz(xb) if loss == "rz" else net.loss_grad(xb, tb)
+        tot += lv * xb.shape[0]
         n += xb.shape[0]
     return tot / n
 
@@ -73,7 +78,8 @@ def test_loss(net, X, T, batch=4):
 def compare_starts(cfg, parts, xs, nets, steps, warmup=2, modes=("previous", "cold", "learned"), device="cuda"):
     """Step the run `cfg` from the same start under each warm-start mode
     (host-checked multigrid to the configured tolerance) and report, per
-    mode, the multigrid cycles per step and the step time (CUDA events).
+    mode, the multigrid cycles per step, the step time (CUDA events) and the
+    geometric mean of the solves' starting residuals.
     `nets` maps the learned modes to their networks."""
     import torch
     out = {}
@@ -83,7 +89,7 @@ def compare_starts(cfg, parts, xs, nets, steps, warmup=2, modes=("previous", "co
         sim.step(warmup)
         sim.set_warm_start(mode, nets.get(mode))
         sim.synchronize()
-        cyc, ms, worst = [], [], 0.0
+        cyc, ms, r0, worst = [], [], [], 0.0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         for _ in range(steps):
@@ -92,9 +98,10 @@ def compare_starts(cfg, parts, xs, nets, steps, warmup=2, modes=("previous", "co
             e1.record(sim.stream)
             sc = sim.scalars()
             cyc.append(sc["poisson_cycles"])
+            r0.append(sc["poisson_relres0"])
             worst = max(worst, sc["poisson_relres_max"])
             ms.append(e0.elapsed_time(e1))
         out[mode] = {"cycles_per_step": float(np.mean(cyc)), "ms_per_step": float(np.mean(ms)),
-                     "relres_max": worst}
+                     "relres_max": worst, "start_relres_geomean": float(np.exp(np.mean(np.log(np.maximum(r0, 1e-300)))))}
         sim.close()
     return out

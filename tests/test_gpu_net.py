@@ -183,7 +183,7 @@ def test_warm_start_modes_reach_the_tolerance(pd, torch, xs):
     cfg, parts = _plume(n=64, total=6e4)
     net = pd.Net((cfg["nz"] + 1) * (cfg["nr"] + 1), params=_params(10))
     cycles = {}
-    for mode in ("previous", "cold", "learned", "learned_delta"):
+    for mode in ("previous", "cold", "learned", "learned_delta", "learned_extrap"):
         sim = pd.Simulation(cfg, xs)
         sim.load(parts)
         sim.step(2)
@@ -194,4 +194,81 @@ def test_warm_start_modes_reach_the_tolerance(pd, torch, xs):
         cycles[mode] = sc["poisson_cycles"]
         sim.close()
     assert cycles["cold"] >= cycles["previous"]
+    net.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(2, 21, 37), (1, 8, 16), (3, 5, 3)])
+def test_residual_loss_and_gradients_match_the_oracle(pd, torch, B, H, W):
+    rng = np.random.default_rng(7 * B + H + W)
+    p = _params(3 * B + W)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    net = pd.Net(B * H * W, params=p)
+    loss, g = net.loss_grad_rz(torch.from_numpy(x).cuda(), want_grads=True)
+    lo, go = cnn.resid_loss_and_grad(p.astype(np.float64), x, bf16=True)
+    assert loss == pytest.approx(lo, rel=2e-3)
+    o = 0
+    for l, (nw, nb) in enumerate(cnn.layer_sizes()):
+        assert _rel(g[o:o + nw], go[o:o + nw]) <= 1e-2, ("weights", l)
+        assert _rel(g[o + nw:o + nw + nb], go[o + nw:o + nw + nb]) <= 1e-2, ("biases", l)
+        o += nw + nb
+    net.close()
+
+
+def test_extrapolated_pairs_match_the_oracle(pd, torch, xs):
+    """Pairs of three consecutive solves (load + solve, two steps with a
+    solve each) against the oracle's definition on the oracle's own states:
+    the float oracle moves the particles as the library does, so the charge
+    is bit-identical and the potentials agree to the solve tolerance."""
+    cfg, parts = _plume()
+    cfg.update(poisson_tol=1e-12, oracle_poisson_tol=1e-13)
+    parts = {k: v.copy() for k, v in parts.items()}
+    parts["iz"][::4] = cfg["nz"] - 1
+    sim = pd.Simulation(cfg, xs)
+    sim.load(parts)
+    sim.step(1)
+    with pytest.raises(pd.PdError):
+        sim.warmstart_pairs("extrap")         # two solves only
+    sim.step(1)
+    x, t = (a.cpu().numpy().astype(np.float64).reshape(sim.nzn, sim.nrn) for a in sim.warmstart_pairs("extrap"))
+    o = oracle.Oracle(cfg, fp64=False)
+    o.set_cross_sections(xs)
+    o.load(parts)
+    o.prime()
+    grid = (cfg["weight"], cfg["dz"], cfg["dr"], cfg["nz"], cfg["nr"])
+    st = []
+    for k in range(3):
+        if k:
+            o.step(1)
+        st.append((cnn.node_density(sum(o.rho()), *grid), o.phi().reshape(sim.nzn, sim.nrn), o.scalars()["V"]))
+    (r2, p2, V2), (r1, p1, V1), (r0, p0, V0) = st
+    xo, to = cnn.training_pair_extrap(r0, p0, V0, cfg["dz"], r1, p1, V1, r2, p2, V2)
+    assert np.abs(xo).max() == pytest.approx(1.0)
+    assert np.abs(x - xo).max() <= 1e-6
+    assert np.abs(t - to).max() <= 1e-3 * np.abs(to).max()
+
+
+def test_learned_correction_beats_the_extrapolated_start(pd, torch, xs):
+    """The network trained on the residual its correction leaves (three
+    training runs, 128^2 r-z plume) starts the solves of a held-out run
+    closer than the potential extrapolated in time: a smaller starting
+    residual and no more multigrid cycles to 1e-8."""
+    from paper_2109_00214_gb300 import warmstart as W
+    n = 128
+    runs = []
+    for k in range(4):
+        cfg, parts = synthetic.rz_plume(n=n, total=2.5e5, seed=300 + k)
+        cfg.update(field_on=1, inject_on=0, run=k, V0=1e3 * (2 + 2 * k), poisson_tol=1e-8)
+        runs.append((cfg, parts))
+    train_runs, test_run = runs[:3], runs[3]
+    pairs = W.collect_pairs([c for c, _ in train_runs], [p for _, p in train_runs], xs, 60, kinds=("extrap",))
+    X = pairs["extrap"][0].flatten(0, 1)
+    net = pd.Net(8 * (n + 1) ** 2, params=_params(5))
+    W.train(net, [(X, X)], 600, 8, lr=1e-3, lr_final=5e-5, loss="rz")
+    res = W.compare_starts(*test_run, xs, {"learned_extrap": net}, 12, warmup=3,
+                           modes=("extrapolate", "learned_extrap"))
+    ext, lrn = res["extrapolate"], res["learned_extrap"]
+    assert lrn["relres_max"] <= 1e-8 and ext["relres_max"] <= 1e-8
+    assert lrn["start_relres_geomean"] <= 0.5 * ext["start_relres_geomean"], res
+    assert lrn["cycles_per_step"] <= ext["cycles_per_step"], res
+    print(f"\nlearned correction vs extrapolated start: {res}")
     net.close()

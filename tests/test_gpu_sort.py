@@ -82,7 +82,7 @@ def test_sparse_ensemble_run_layouts_fit(pd, xs):
 
 @pytest.mark.parametrize("n,min_relayouts", [
     (128, 1),      # 1.2 particles a cell: bins borrow from their empty neighbours
-    (48, 3),       # 8.7 a cell: borrowing falls short and the bins are laid out anew
+    (48, 2),       # 8.7 a cell: borrowing falls short and the bins are laid out anew
 ])
 def test_hot_heavies_bit_exact(pd, xs, n, min_relayouts):
     """n x n Cartesian cells, 2e4 particles, heavies hot enough to cross
