@@ -621,7 +621,7 @@ def run_warmstart(args, ws, rank, local):
         net = pd.Net(max_nodes, params=p0, device=dev)
         torch.cuda.synchronize()
         e0.record(net.stream)
-        hist = W.train(net, sets[k], args.ws_iters, batch, lr=1e-3, lr_final=5e-5,
+        hist = W.train(net, sets[k], args.ws_iters, batch, lr=3e-3 if lk == "rz" else 1e-3, lr_final=5e-5,
                        log_every=max(1, args.ws_iters // 10), loss=lk)
         e1.record(net.stream)
         torch.cuda.synchronize()

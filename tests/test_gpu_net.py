@@ -262,8 +262,8 @@ def test_learned_correction_beats_the_extrapolated_start(pd, torch, xs):
     train_runs, test_run = runs[:3], runs[3]
     pairs = W.collect_pairs([c for c, _ in train_runs], [p for _, p in train_runs], xs, 60, kinds=("extrap",))
     X = pairs["extrap"][0].flatten(0, 1)
-    net = pd.Net(8 * (n + 1) ** 2, params=_params(5))
-    W.train(net, [(X, X)], 600, 8, lr=1e-3, lr_final=5e-5, loss="rz")
+    net = pd.Net(8 * (n + 1) ** 2, params=cnn.init_params(5).astype(np.float32))
+    W.train(net, [(X, X)], 2000, 8, lr=3e-3, lr_final=5e-5, loss="rz")
     res = W.compare_starts(*test_run, xs, {"learned_extrap": net}, 12, warmup=3,
                            modes=("extrapolate", "learned_extrap"))
     ext, lrn = res["extrapolate"], res["learned_extrap"]
