@@ -261,114 +261,6 @@ __device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32
     return __reduce_min_sync(FULL, pos);
 }
 
-// The same selection for the ranks held by lanes 0 .. m - 1 (m <= 8) at once:
-// each pass sweeps the list once for all of them (their counters side by
-// side, m x 256 in cnt), and one last sweep finds their positions.  Returns,
-// in lane q < m, the position of rank q's id (SENTINEL in the other lanes or
-// for a rank >= n).
-constexpr uint32_t SELECT_MULTI_MAX = 8;
-__device__ uint32_t select8_multi(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, uint32_t m, int top,
-                                  uint32_t* cnt, int lane) {
-    uint32_t prefix = 0, want = rank;
-    bool found = true;
-    for (int lo = top - 7;; lo -= 8) {
-        const int sh = lo > 0 ? lo : 0;
-        const int width = lo >= 0 ? 8 : 8 + lo;        // bits of this window
-        const uint32_t dm = (1u << width) - 1u;
-        const uint32_t hm = sh + width >= 32 ? 0u : (0xFFFFFFFFu << (sh + width));
-        for (uint32_t k = (uint32_t)lane; k < 256u * m; k += 32u) cnt[k] = 0u;
-        uint32_t pf[SELECT_MULTI_MAX];
-#pragma unroll
-        for (int l = 0; l < (int)SELECT_MULTI_MAX; ++l) pf[l] = __shfl_sync(FULL, prefix, l);
-        __syncwarp();
-        for (uint32_t q0 = 0; q0 < n; q0 += 256) {
-            uint32_t x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
-                x[u] = q < n ? ids[q] : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
-                if (q >= n) continue;
-                const uint32_t hx = x[u] & hm, d = (x[u] >> sh) & dm;
-#pragma unroll
-                for (int l = 0; l < (int)SELECT_MULTI_MAX; ++l)
-                    if ((uint32_t)l < m && hx == pf[l]) atomicAdd(&cnt[256u * (uint32_t)l + d], 1u);
-            }
-        }
-        __syncwarp();
-        for (uint32_t l = 0; l < m; ++l) {
-            const uint32_t wl = __shfl_sync(FULL, want, (int)l);
-            uint32_t c[8], sum = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                c[k] = cnt[256u * l + (uint32_t)lane * 8u + (uint32_t)k];
-                sum += c[k];
-            }
-            uint32_t xs = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, xs, o);
-                if (lane >= o) xs += y;
-            }
-            const uint32_t before = xs - sum;
-            const bool mine = wl >= before && wl < xs;
-            uint32_t d = 0, rest = 0, run = before;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (mine && wl >= run && wl < run + c[k]) {
-                    d = (uint32_t)(lane * 8 + k);
-                    rest = wl - run;
-                }
-                run += c[k];
-            }
-            const unsigned b = __ballot_sync(FULL, mine);
-            if (b) {
-                const int src = __ffs(b) - 1;
-                d = __shfl_sync(FULL, d, src);
-                rest = __shfl_sync(FULL, rest, src);
-            }
-            if ((uint32_t)lane == l) {
-                if (b) {
-                    prefix |= d << sh;
-                    want = rest;
-                } else {
-                    found = false;                       // rank >= n
-                }
-            }
-        }
-        __syncwarp();
-        if (sh == 0) break;
-    }
-    uint32_t pf[SELECT_MULTI_MAX];
-#pragma unroll
-    for (int l = 0; l < (int)SELECT_MULTI_MAX; ++l) pf[l] = __shfl_sync(FULL, prefix, l);
-    if ((uint32_t)lane < m) cnt[lane] = SENTINEL;
-    __syncwarp();
-    for (uint32_t q0 = 0; q0 < n; q0 += 256) {
-        uint32_t x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
-            x[u] = q < n ? ids[q] : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
-            if (q >= n) continue;
-#pragma unroll
-            for (int l = 0; l < (int)SELECT_MULTI_MAX; ++l)
-                if ((uint32_t)l < m && x[u] == pf[l]) atomicMin(&cnt[l], q);
-        }
-    }
-    __syncwarp();
-    const uint32_t pos = (uint32_t)lane < m && found ? cnt[lane] : SENTINEL;
-    __syncwarp();
-    return pos;
-}
-
 // Scratch of the rank tables, arrays indexed by slot: two (key, value) pair
 // buffers and the tables.  They are the sort's other buffer, unused between
 // the scatter and the next step's scatter; a list at slots [b, b + n) uses
@@ -1562,8 +1454,6 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                     pe = i;
                 } else if (el.table) {
                     if (has) pe = el.table[i];
-                } else if (el.sel8 && nb <= SELECT_MULTI_MAX) {
-                    pe = select8_multi(el.base, el.n, i, nb, el.top, sbuf, lane);
                 } else {
                     for (uint32_t q = 0; q < nb; ++q) {
                         const uint32_t p = select_rank_list(el, __shfl_sync(FULL, i, (int)q), lane);
@@ -1574,8 +1464,6 @@ __global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, 
                     pt = j;
                 } else if (tl.table) {
                     if (has) pt = tl.table[j];
-                } else if (tl.sel8 && nb <= SELECT_MULTI_MAX) {
-                    pt = select8_multi(tl.base, tl.n, j, nb, tl.top, sbuf, lane);
                 } else {
                     for (uint32_t q = 0; q < nb; ++q) {
                         const uint32_t p = select_rank_list(tl, __shfl_sync(FULL, j, (int)q), lane);

@@ -702,42 +702,26 @@ __global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32
 // e_from) to the end of the tail: the electron bins and the tail (dense:
 // every electron moves), and the last heavy slots before them.  A thread per
 // four slots, the group's records loaded whole, one atomic per bin and warp.
-// The records of the thread's next group are loaded while the current one's
-// cursor claims are in flight (the claims' results gate the stores).
-struct Group4 {
-    uint32_t nib;
-    uint4 K, ID;
-    float4 Z, R, VZ, VR, VT;
-};
-__device__ __forceinline__ void load_group(Group4& G, const Particles& M, const uint32_t* __restrict__ mm, uint32_t g,
-                                           uint32_t g1) {
-    G.nib = g < g1 ? (mm[g >> 3] >> (4u * (g & 7u))) & 15u : 0u;
-    G.K = G.ID = make_uint4(DEAD, DEAD, DEAD, DEAD);
-    G.Z = G.R = G.VZ = G.VR = G.VT = make_float4(0, 0, 0, 0);
-    if (G.nib) {
-        G.K = reinterpret_cast<const uint4*>(M.key)[g];
-        G.Z = reinterpret_cast<const float4*>(M.pz)[g];
-        G.R = reinterpret_cast<const float4*>(M.pr)[g];
-        G.VZ = reinterpret_cast<const float4*>(M.vz)[g];
-        G.VR = reinterpret_cast<const float4*>(M.vr)[g];
-        G.VT = reinterpret_cast<const float4*>(M.vt)[g];
-        G.ID = reinterpret_cast<const uint4*>(M.id)[g];
-    }
-}
-__global__ void __launch_bounds__(256, 3) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
+__global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
                                                       const uint32_t* __restrict__ off,
                                                       const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
                                                       uint32_t ncell, uint32_t nbins, uint32_t nslots, DevState* st) {
     if (st->error) return;                           // a fault was flagged: the state is not stepped further
     const uint32_t g0 = (uint32_t)((st->e_from >> 7) << 5), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
     const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x;
-    Group4 Gn;
-    load_group(Gn, M, mm, g, g1);
-    for (; g - lane < g1; g += stride) {
-        const Group4 G = Gn;
-        load_group(Gn, M, mm, g + stride, g1);
+    for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g - lane < g1; g += gridDim.x * blockDim.x) {
+        const uint32_t nib = g < g1 ? (mm[g >> 3] >> (4u * (g & 7u))) & 15u : 0u;
+        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
+        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
+        if (nib) {
+            K = reinterpret_cast<const uint4*>(M.key)[g];
+            Z = reinterpret_cast<const float4*>(M.pz)[g];
+            R = reinterpret_cast<const float4*>(M.pr)[g];
+            VZ = reinterpret_cast<const float4*>(M.vz)[g];
+            VR = reinterpret_cast<const float4*>(M.vr)[g];
+            VT = reinterpret_cast<const float4*>(M.vt)[g];
+            ID = reinterpret_cast<const uint4*>(M.id)[g];
+        }
         // the four lanes' bins, their warp peers and the cursor claims: the
         // claims of the four are independent, so all are issued before any
         // result is used
@@ -746,8 +730,8 @@ __global__ void __launch_bounds__(256, 3) k_insert_dense(Particles A, Particles 
         bool ok[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const bool on = (G.nib >> q) & 1u;
-            bin[q] = on ? mover_bin(lane_of(G.K, q), ncell, nbins) : nbins;
+            const bool on = (nib >> q) & 1u;
+            bin[q] = on ? mover_bin(lane_of(K, q), ncell, nbins) : nbins;
             if (on && bin[q] >= nbins) sort_fault(st, 128u);
             ok[q] = on && bin[q] < nbins;
             peers[q] = __match_any_sync(FULL_MASK, ok[q] ? bin[q] : 0xFFFFFFFFu);
@@ -769,13 +753,13 @@ __global__ void __launch_bounds__(256, 3) k_insert_dense(Particles A, Particles 
                 sort_fault(st, 256u);
                 continue;
             }
-            A.key[sl] = lane_of(G.K, q);
-            A.pz[sl] = lane_of(G.Z, q);
-            A.pr[sl] = lane_of(G.R, q);
-            A.vz[sl] = lane_of(G.VZ, q);
-            A.vr[sl] = lane_of(G.VR, q);
-            A.vt[sl] = lane_of(G.VT, q);
-            A.id[sl] = lane_of(G.ID, q);
+            A.key[sl] = lane_of(K, q);
+            A.pz[sl] = lane_of(Z, q);
+            A.pr[sl] = lane_of(R, q);
+            A.vz[sl] = lane_of(VZ, q);
+            A.vr[sl] = lane_of(VR, q);
+            A.vt[sl] = lane_of(VT, q);
+            A.id[sl] = lane_of(ID, q);
         }
     }
 }
