@@ -468,7 +468,7 @@ def run_ensemble(args, ws, rank, local):
         ens.load_run_device(r, {k: torch.from_numpy(parts[k]).to(dev) for k in keys})
     tuning = None
     if not args.no_autotune:
-        tuning = ens.autotune(2)
+        tuning = ens.autotune(4)
     # eager warm-up with host-checked solves; per-kernel times of the last G steps
     done = int(ens.run_scalars(0)["step"])      # steps the autotuner took
     ens.step(W + (G - (done + W) % G) % G)      # end on a multiple of the graph period
@@ -778,7 +778,7 @@ def run_single(args, ws, rank, local):
     sim.load_device(dtens)
     del dtens
     torch.cuda.synchronize()
-    tuning = None if args.no_autotune else sim.autotune(2)   # its trial steps are untimed warm-up
+    tuning = None if args.no_autotune else sim.autotune(4)   # its trial steps are untimed warm-up
     done = int(sim.scalars()["step"])
     warm_steps = args.warmup + ((hs - (done + args.warmup) % hs) % hs if hs > 1 else 0)
     sim.step(warm_steps)
