@@ -226,14 +226,14 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-# DRAM bytes per particle of the same kernels from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of a 2.49e7-particle launch of
-# the 512 x 512 microbench), scaled to a launch by its particle count.  The
-# figures hold only for the kernel source they were taken on: TRAFFIC_SOURCE_SHA
-# is the SHA-256 of csrc/pd_stream.cu at the capture, and `traffic` is null
-# for any other source.
-TRAFFIC_PER_PARTICLE = {"push": 693.56e6 / 24898326, "scatter": 1362.67e6 / 24898326}
-TRAFFIC_SOURCE_SHA = "8a4704a567a68ffcf67db5b6ebdbf4f1b6510f12961ba286da03c32931dff281"
+# DRAM bytes per live particle of the push from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a launch of the 512 x 512
+# microbench, 2.49e7 particles, the recipe of the 1024 x 1024 one), scaled to
+# a launch by its particle count.  The figure holds only for the kernel source
+# it was taken on: TRAFFIC_SOURCE_SHA is the SHA-256 of csrc/pd_stream.cu at
+# the capture, and `traffic` is null for any other source.
+TRAFFIC_PER_PARTICLE = {"push": 798.69e6 / 24898326}
+TRAFFIC_SOURCE_SHA = "21d0de9f2c8493a92a85575e8cbc178917d6f25a81375de66173108901aa23d6"
 TRAFFIC_SOURCE = "ncu dram bytes per particle of a 2.49e7-particle launch, scaled"
 
 

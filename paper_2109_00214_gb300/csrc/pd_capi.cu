@@ -1873,7 +1873,7 @@ pd_status pd_autotune(pd_sim* s, int steps_per_trial, pd_tuning* out) {
     };
     pd_tuning t = s->tune;
     std::vector<Knob> knobs = {
-        {&t.push_blocks_per_sm, K_PUSH, {2, 3, 4, 6, 8, 12, 16, 24}},
+        {&t.push_blocks_per_sm, K_PUSH, {3, 4, 6, 8, 12, 16}},
         {&t.bincount_blocks_per_sm, K_SCAN_BINS, {2, 4, 8, 16}},
         {&t.scatter_blocks_per_sm, K_SCATTER, {2, 3, 4, 6, 8, 12, 16}},
         {&t.ncand_blocks_per_sm, K_NCAND, {2, 4, 8, 16}},
