@@ -187,7 +187,7 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool v) {
 // (windows aligned to bit 0 would leave the first pass one or two digits:
 // every id's atomic on the same counters); the last window holds the bits
 // that remain.  Each lane keeps eight loads in flight.
-__device__ __noinline__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, int top, uint32_t* cnt,
+__device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, int top, uint32_t* cnt,
                             int lane) {
     uint32_t prefix = 0, want = rank;
     for (int lo = top - 7;; lo -= 8) {
@@ -363,7 +363,7 @@ __device__ void radix_pass(const uint32_t* sk, const uint32_t* sv, uint32_t* dk,
 // the digits up to `top`, passes alternating between (yk, yv) and (xk, xv),
 // the last one writing the positions to table.
 template <bool BLOCK>
-__device__ __noinline__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uint32_t* yk, uint32_t* yv,
+__device__ void radix_table(uint32_t n, int top, uint32_t* xk, uint32_t* xv, uint32_t* yk, uint32_t* yv,
                             uint32_t* table, int nw, uint32_t* cnt, uint32_t* tot, uint32_t tid, int lane, int w) {
     const int passes = top / 8 + 1;
     const uint32_t *sk = xk, *sv = nullptr;
@@ -780,7 +780,7 @@ __device__ __forceinline__ PairEval evaluate_pair(int k, const V3& ve, const V3&
 // evaluate_pair of ve, vt)
 // (accepted: the candidate is known to pass the target and acceptance
 // tests, already counted by the caller)
-__device__ __noinline__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
+__device__ void process_candidate(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ie, uint32_t it,
                                   uint32_t tkey, V3 ve, V3 vt, const PairEval& ev, float Racc, float Rch,
                                   const float* __restrict__ xsE, const float* __restrict__ xs,
                                   const CollConsts& cc, DevState* st, long long* rho_e, long long* rho_h,
@@ -872,7 +872,7 @@ __device__ __forceinline__ bool consumed_pair(int k, uint32_t akey, uint32_t tke
 // exchange Cu + Cu+ -> Cu+ + Cu moves the electron, not the atoms: each slot
 // keeps its species and takes the other's velocity.  Cu + Cu is elastic and
 // isotropic in the centre of mass, equal masses.
-__device__ __noinline__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ia, uint32_t ib,
+__device__ void process_heavy_pair(Particles& A, CellCtx& cx, Stream& rs, int k, uint32_t ia, uint32_t ib,
                                    uint32_t akey, uint32_t bkey, V3 va, V3 vb, const PairEval& ev, float Racc,
                                    const CollConsts& cc, bool accepted) {
     if (!accepted) {
@@ -1330,7 +1330,7 @@ __global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, 
 }
 
 template <bool EXT>
-__global__ void __launch_bounds__(128, 4) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(128, 3) k_collide(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                  const uint32_t* __restrict__ cnt,
                                                  const uint4* __restrict__ nc, const uint4* __restrict__ nc2,
                                                  const uint32_t* __restrict__ cand_off,
