@@ -473,7 +473,7 @@ pd_status check_device_error(pd_sim* s, const DevState& d) {
     if (d.error & ERR_CAPACITY) return fail(s, PD_ERR_CAPACITY, "particle capacity exhausted");
     if (d.error & ERR_IDS) return fail(s, PD_ERR_CAPACITY, "particle id space exhausted");
     if (d.error & ERR_TIMEOUT) return fail(s, PD_ERR_TIMEOUT, "a bounded device wait ran out");
-    if (d.error & ERR_NONFINITE) return fail(s, PD_ERR_NONFINITE, "non-finite value in the field solve");
+    if (d.error & ERR_NONFINITE) return fail(s, PD_ERR_NONFINITE, "non-finite value in the field solve or a particle's step");
     if (d.error & ERR_BOUNDS) return fail(s, PD_ERR_CAPACITY, "inconsistent slot bookkeeping (reported, not written)");
     return PD_OK;
 }

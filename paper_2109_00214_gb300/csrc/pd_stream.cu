@@ -205,10 +205,12 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             int nir;
             float npr;
             bool out = false;
+            bool fin;        // the new position is finite (a fault upstream makes it NaN or infinite)
             if (RZ) {
                 const float x = ((float)ir + pr) + vr * dtr;
                 const float y = vt * dtr;
                 const float rr = sqrtf(x * x + y * y);
+                fin = isfinite(z) && isfinite(rr);
                 const bool pos = rr > 0.0f;
                 const float c = pos ? x / rr : 1.0f, s = pos ? y / rr : 0.0f;
                 const float nvr = c * vr + s * vt;
@@ -232,10 +234,12 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
                 // a particle crosses at most one period per step (|v dt| < one domain)
                 niz = wrap1(niz, RI.nz);
                 nir = wrap1(nir, RI.nr);
+                // a finite step stays within one period, so the indices are in range
+                fin = (unsigned)niz < (unsigned)RI.nz && (unsigned)nir < (unsigned)RI.nr;
             }
-            // a non-finite position or velocity (a fault upstream) would index
-            // outside the grid: the particle is dropped and the error flagged
-            const bool bad = move && !(isfinite(z) && isfinite(npr) && isfinite(vz) && isfinite(vr) && isfinite(vt));
+            // a non-finite position (a fault upstream) would index outside the
+            // grid: the particle is dropped and the error flagged
+            const bool bad = move && !fin;
             if (bad) set_error(st, ERR_NONFINITE);
             const bool absorbed = move && (out || bad);
             const bool kp = live && !absorbed;
