@@ -84,12 +84,12 @@ void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, c
                       uint32_t* id, unsigned int* bad, int grid, cudaStream_t s);
 
 // collisions.  The rank table of an id list of more than RANK_WARP_MAX ids
-// that the candidates of an active cell use is built before k_collide, by a
-// block of its own: lists up to RANK_MID_MAX ids by the mid-size kernel,
-// longer ones by the large one.  k_ncand queues them in `mid` and `big`;
-// rank_queue_max(cap, len) entries always suffice for lists longer than len
-// (the lists hold disjoint particles).
-constexpr uint32_t RANK_WARP_MAX = 512;
+// (beyond a warp's register cache) that the candidates of an active cell use
+// is built before k_collide, by a block of its own: lists up to RANK_MID_MAX
+// ids by the mid-size kernel, longer ones by the large one.  k_ncand queues
+// them in `mid` and `big`; rank_queue_max(cap, len) entries always suffice
+// for lists longer than len (the lists hold disjoint particles).
+constexpr uint32_t RANK_WARP_MAX = 256;
 constexpr uint32_t RANK_MID_MAX = 2048;
 __host__ __device__ inline uint32_t rank_queue_max(uint64_t cap, uint32_t len) { return (uint32_t)(cap / (len + 1) + 4); }
 // shared-memory attribute of the rank-table kernels (once per process and device)
