@@ -130,14 +130,14 @@ __device__ void deposit1(long long* rho, const RunInfo& RI, int geom, uint32_t l
 //     number of smaller ids in the list);
 //   * up to 32 * RC ids with lookups that cost less than a table: a radix
 //     select over the ids held in registers, per lookup;
+//   * longer lists with at most SELECT_LOOKUPS lookups: a select per lookup
+//     over the list in global memory (select8);
 //   * otherwise a rank table, position of the r-th smallest id at table[r],
 //     from a stable LSD radix sort of (id, position) pairs by 8-bit digits:
 //     by the cell's warp in its shared memory for the register-cached lists
 //     (up to RANK_WARP_MAX = 32 * RC ids), by a block of k_rank_tables
-//     (before k_collide) for every longer list that has a lookup, in shared
-//     memory up to RANK_BLOCK_MAX ids and in the scratch buffers above that
-//     (a block's sort of a long list costs less than the warp of a cell
-//     searching the list even once per lookup).
+//     (before k_collide) for longer lists, in shared memory up to
+//     RANK_BLOCK_MAX ids and in the scratch buffers above that.
 // The table of the list at slots [b, b + n) is written to table[b, b + n).
 
 // Register-cached id list of one cell and species: element lane + 32 k in
@@ -152,12 +152,19 @@ constexpr uint32_t SENTINEL = 0xFFFFFFFFu;
 struct IdList {
     uint32_t ids[RC];
     const uint32_t* table;           // rank -> position, or null
+    const uint32_t* base;            // the ids in global memory (select8)
+    uint32_t* cnt;                   // the warp's 256 shared counters (select8)
     uint32_t n;
     int top;                         // highest set bit of any id (0 if none)
     bool cached;
     bool sorted;                     // ids ascend with the position: rank = position
+    bool sel8;                       // a long list with few lookups: select8 per lookup
 };
-static_assert(RANK_WARP_MAX == 32u * RC, "lists beyond the register cache are sorted by k_rank_tables");
+
+// lookups up to which a list longer than 32 * RC ids is searched per lookup
+// (select8) instead of being sorted into a rank table: a select costs a few
+// sweeps of the list by one warp, a table a few sweeps by a whole block
+constexpr uint32_t SELECT_LOOKUPS = 4;
 
 // The lanes of the warp whose 8-bit digit d equals this lane's (v: the
 // lane holds a digit at all; lanes without one group with none), from nine
@@ -172,6 +179,88 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, bool v) {
         peers &= bit ? bb : ~bb;
     }
     return peers;
+}
+
+// Position of the rank-th smallest of the n (unique) ids at ids[0, n) by
+// one warp: passes over windows of 8 bits from bit `top` (every id is below
+// 2^(top + 1)) down, each counting, in the warp's 256 shared counters, the
+// ids that share the bits found so far; SENTINEL if rank >= n.  The first
+// window is the top 8 bits, so that its digits spread over the counters
+// (windows aligned to bit 0 would leave the first pass one or two digits:
+// every id's atomic on the same counters); the last window holds the bits
+// that remain.  Each lane keeps eight loads in flight.
+__device__ uint32_t select8(const uint32_t* __restrict__ ids, uint32_t n, uint32_t rank, int top, uint32_t* cnt,
+                            int lane) {
+    uint32_t prefix = 0, want = rank;
+    for (int lo = top - 7;; lo -= 8) {
+        const int sh = lo > 0 ? lo : 0;
+        const int width = lo >= 0 ? 8 : 8 + lo;        // bits of this window
+        const uint32_t dm = (1u << width) - 1u;
+        const uint32_t hm = sh + width >= 32 ? 0u : (0xFFFFFFFFu << (sh + width));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cnt[lane * 8 + k] = 0u;
+        __syncwarp();
+        for (uint32_t q0 = 0; q0 < n; q0 += 256) {
+            uint32_t x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+                x[u] = q < n ? ids[q] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+                if (q < n && (x[u] & hm) == prefix) atomicAdd(&cnt[(x[u] >> sh) & dm], 1u);
+            }
+        }
+        __syncwarp();
+        uint32_t c[8], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = cnt[lane * 8 + k];
+            sum += c[k];
+        }
+        uint32_t xs = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, xs, o);
+            if (lane >= o) xs += y;
+        }
+        const uint32_t before = xs - sum;
+        const bool mine = want >= before && want < xs;
+        uint32_t d = 0, rest = 0, run = before;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (mine && want >= run && want < run + c[k]) {
+                d = (uint32_t)(lane * 8 + k);
+                rest = want - run;
+            }
+            run += c[k];
+        }
+        const unsigned b = __ballot_sync(FULL, mine);
+        __syncwarp();
+        if (!b) return SENTINEL;
+        const int src = __ffs(b) - 1;
+        d = __shfl_sync(FULL, d, src);
+        want = __shfl_sync(FULL, rest, src);
+        prefix |= d << sh;
+        if (sh == 0) break;
+    }
+    uint32_t pos = SENTINEL;
+    for (uint32_t q0 = 0; q0 < n; q0 += 256) {
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+            x[u] = q < n ? ids[q] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t q = q0 + 32u * u + (uint32_t)lane;
+            if (q < n && x[u] == prefix && q < pos) pos = q;
+        }
+    }
+    return __reduce_min_sync(FULL, pos);
 }
 
 // Scratch of the rank tables, arrays indexed by slot: two (key, value) pair
@@ -354,13 +443,20 @@ __global__ void __launch_bounds__(NT) k_rank_tables(const uint32_t* __restrict__
 __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__ ids, uint32_t slot0, uint32_t n,
                                          uint32_t lookups, const RankScratch& S, uint32_t* sbuf, int lane,
                                          int id_top, bool want_table = false) {
-    (void)id_top;
     const uint32_t* base = ids + slot0;
     L.n = n;
     L.table = nullptr;
+    L.base = base;
+    L.cnt = sbuf + 4 * RANK_WARP_MAX;
     L.cached = n <= 32u * RC;
     L.sorted = false;
+    L.sel8 = false;
     L.top = 0;
+    if (!want_table && !L.cached && lookups <= SELECT_LOOKUPS) {
+        L.sel8 = true;
+        L.top = id_top;
+        return;
+    }
     if (!L.cached) {                 // table built by k_rank_tables
         L.table = S.table + slot0;
         return;
@@ -368,7 +464,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
     uint32_t* xk = sbuf;
     bool asc = true;
     uint32_t orv = 0;
-    {
+    if (L.cached) {
 #pragma unroll
         for (int k = 0; k < RC; ++k) {
             const uint32_t q = (uint32_t)lane + 32u * k;
@@ -439,6 +535,7 @@ __device__ __forceinline__ void load_ids(IdList& L, const uint32_t* __restrict__
 __device__ __forceinline__ uint32_t select_rank_list(const IdList& L, uint32_t rank, int lane) {
     if (L.sorted) return rank;
     if (L.table) return L.table[rank];
+    if (L.sel8) return select8(L.base, L.n, rank, L.top, L.cnt, lane);
     // register-cached list: bitwise radix select
     uint32_t prefix = 0, want = rank;
     for (int bit = L.top; bit >= 0; --bit) {
@@ -588,9 +685,9 @@ __global__ void __launch_bounds__(256) k_ncand(const uint32_t* __restrict__ cnt,
         else if (act) active[C - 1u - (bl + __popc(ml & lt))] = c;
         if (act || (c < C && ncoul > 0)) {
             // the lists k_collide or k_coulomb will rank that need a block's
-            // sort (beyond the register cache, with a lookup)
+            // sort (long, with more lookups than select8 serves)
             for (uint32_t sp = 0; sp < (uint32_t)NSP; ++sp) {
-                if (look[sp] == 0 || N[sp] <= RANK_WARP_MAX) continue;
+                if (look[sp] == 0 || N[sp] <= RANK_WARP_MAX || look[sp] <= SELECT_LOOKUPS) continue;
                 const bool large = N[sp] > RANK_MID_MAX;
                 const uint32_t x = atomicAdd(large ? &st->n_big : &st->n_mid, 1u);
                 if (x < rank_queue_max(P.capacity, large ? RANK_MID_MAX : RANK_WARP_MAX))

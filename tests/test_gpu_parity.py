@@ -72,7 +72,7 @@ def assert_same_counters(gc, oc, keys=None):
     (8200, 3000, 4, 1.0, 300.0),   # about 2050 e per cell (both sides of the mid-size / large block split)
     (24600, 6000, 2, 0.1, 300.0),  # about 12300 e per cell (both sides of the shared-memory limit)
     (800, 400, 4, 100.0, 300.0),   # 200 e / 100 Cu per cell, many lookups: tables of register-cached lists
-    (6000, 3000, 4, 0.1, 300.0),   # 1500 e / 750 Cu per cell, about one candidate: block-sorted tables all the same
+    (6000, 3000, 4, 0.1, 300.0),   # 1500 e / 750 Cu per cell, about one candidate: digit-by-digit selects
     (20000, 9000, 1, 0.0006, 30.0),  # 29000 particles in one cell, about one candidate
 ])
 def test_dense_cells_bit_exact(pd, xs, n_e, n_t, ncells, scale, Te):
@@ -125,7 +125,7 @@ def test_microbench_di_off(pd, xs):
     # 200 Cu per cell and many (Cu, Cu) candidates: register-cached lists,
     # candidates of one batch sharing particles
     (dict(n_e=200, n_cu=800, n_cup=200, ncells=4, coll_scale=30000.0), 3),
-    # no electrons, a couple of heavy candidates per step: block-sorted Cu tables
+    # no electrons, a couple of heavy candidates per step: digit-by-digit selects
     (dict(n_e=0, n_cu=20000, n_cup=2000, ncells=1, coll_scale=0.003), 6),
     (dict(n_e=0, n_cu=6000, n_cup=1500, ncells=4, coll_scale=3.0), 4),
 ])
@@ -204,7 +204,7 @@ def test_microbench_charge_states_bit_exact(pd, xs, charge_max, heavy_coll, scal
     (3, 9000, 0.3),                # one cell of 9000 Cu2+ (SW): the list sorted by a block
     (5, 20000, 0.5),               # 20000 Cu3+: sorted in the scratch buffers
     (4, 700, 20.0),                # 700 Cu2+ (DI): the cell's warp sorts it
-    (5, 6000, 0.1),                # a few candidates on long lists: block-sorted tables
+    (5, 6000, 0.1),                # a few candidates: digit-by-digit selects
 ])
 def test_dense_charge_state_cells_bit_exact(pd, xs, target, n_t, scale):
     cfg, parts = synthetic.rate_cell(n_e=3000, n_t=n_t, Te_eV=60.0, seed=8, coll_scale=scale, target_species=target)
