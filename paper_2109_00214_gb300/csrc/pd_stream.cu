@@ -704,40 +704,44 @@ __global__ void __launch_bounds__(256) k_insert(Particles A, Particles M, uint32
 
 // The movers from the first chunk of 128 that k_insert leaves (it ends below
 // e_from) to the end of the tail: the electron bins and the tail (dense:
-// every electron moves), and the last heavy slots before them.  A thread per
-// four slots, the group's records loaded whole, one atomic per bin and warp.
+// every electron moves), and the last heavy slots before them.  A warp per
+// chunk of 128 slots, as four rows of 32 consecutive slots, lane l taking
+// slot l of each row: a row's records load in coalesced 128-byte lines, and
+// the movers of a row that share a bin (consecutive slots of one old cell,
+// mostly) take consecutive slots of it in lane order, so that each store
+// writes runs of neighbouring words instead of one word per 32-byte sector.
+// One atomic per bin and row claims the slots; the four rows' claims are
+// issued before any result is used, beside the loads of the bins' ends.
 __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, const uint32_t* __restrict__ mm,
                                                       const uint32_t* __restrict__ off,
                                                       const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
                                                       uint32_t ncell, uint32_t nbins, uint32_t nslots, DevState* st) {
     if (st->error) return;                           // a fault was flagged: the state is not stepped further
-    const uint32_t g0 = (uint32_t)((st->e_from >> 7) << 5), g1 = (uint32_t)((st->n_slots + 3ull) >> 2);
+    const uint32_t n = (uint32_t)st->n_slots;
+    const uint32_t c0 = (uint32_t)(st->e_from >> 7), c1 = (n + 127u) >> 7;
     const uint32_t lane = threadIdx.x & 31u;
-    for (uint32_t g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g - lane < g1; g += gridDim.x * blockDim.x) {
-        const uint32_t nib = g < g1 ? (mm[g >> 3] >> (4u * (g & 7u))) & 15u : 0u;
-        uint4 K = make_uint4(DEAD, DEAD, DEAD, DEAD), ID = K;
-        float4 Z = make_float4(0, 0, 0, 0), R = Z, VZ = Z, VR = Z, VT = Z;
-        if (nib) {
-            K = reinterpret_cast<const uint4*>(M.key)[g];
-            Z = reinterpret_cast<const float4*>(M.pz)[g];
-            R = reinterpret_cast<const float4*>(M.pr)[g];
-            VZ = reinterpret_cast<const float4*>(M.vz)[g];
-            VR = reinterpret_cast<const float4*>(M.vr)[g];
-            VT = reinterpret_cast<const float4*>(M.vt)[g];
-            ID = reinterpret_cast<const uint4*>(M.id)[g];
-        }
-        // the four lanes' bins, their warp peers and the cursor claims: the
-        // claims of the four are independent, so all are issued before any
-        // result is used
-        uint32_t bin[4], left[4];
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < c1; c += nwarps) {
+        uint32_t K[4], ID[4];
+        float Z[4], R[4], VZ[4], VR[4], VT[4];
+        uint32_t bin[4], end[4], left[4];
         unsigned peers[4];
         bool ok[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const bool on = (nib >> q) & 1u;
-            bin[q] = on ? mover_bin(lane_of(K, q), ncell, nbins) : nbins;
+            const uint32_t i = 128u * c + 32u * (uint32_t)q + lane;   // < 128 c1 <= the slot arrays' length
+            const bool on = ((mm[4u * c + (uint32_t)q] >> lane) & 1u) && i < n;
+            K[q] = M.key[i];
+            Z[q] = M.pz[i];
+            R[q] = M.pr[i];
+            VZ[q] = M.vz[i];
+            VR[q] = M.vr[i];
+            VT[q] = M.vt[i];
+            ID[q] = M.id[i];
+            bin[q] = on ? mover_bin(K[q], ncell, nbins) : nbins;
             if (on && bin[q] >= nbins) sort_fault(st, 128u);
             ok[q] = on && bin[q] < nbins;
+            end[q] = ok[q] ? off[bin[q]] + cnt[bin[q]] : 0u;
             peers[q] = __match_any_sync(FULL_MASK, ok[q] ? bin[q] : 0xFFFFFFFFu);
         }
 #pragma unroll
@@ -750,20 +754,19 @@ __global__ void __launch_bounds__(256) k_insert_dense(Particles A, Particles M, 
             const uint32_t leader = (uint32_t)(__ffs((int)peers[q]) - 1);
             const uint32_t lq = __shfl_sync(FULL_MASK, left[q], (int)leader);
             if (!ok[q]) continue;
-            const uint32_t b = bin[q];
             const uint32_t rank = (uint32_t)__popc(peers[q] & ((1u << lane) - 1u));
-            const uint32_t sl = off[b] + cnt[b] - lq + rank;
-            if (lq < (uint32_t)__popc(peers[q]) || sl >= off[b] + cnt[b] || sl >= nslots) {
+            const uint32_t sl = end[q] - lq + rank;
+            if (lq < (uint32_t)__popc(peers[q]) || sl >= end[q] || sl >= nslots) {
                 sort_fault(st, 256u);
                 continue;
             }
-            A.key[sl] = lane_of(K, q);
-            A.pz[sl] = lane_of(Z, q);
-            A.pr[sl] = lane_of(R, q);
-            A.vz[sl] = lane_of(VZ, q);
-            A.vr[sl] = lane_of(VR, q);
-            A.vt[sl] = lane_of(VT, q);
-            A.id[sl] = lane_of(ID, q);
+            A.key[sl] = K[q];
+            A.pz[sl] = Z[q];
+            A.pr[sl] = R[q];
+            A.vz[sl] = VZ[q];
+            A.vr[sl] = VR[q];
+            A.vt[sl] = VT[q];
+            A.id[sl] = ID[q];
         }
     }
 }
