@@ -923,24 +923,53 @@ __device__ __forceinline__ int perm_bits(uint32_t n) {
     while ((1ull << (2 * h)) < (unsigned long long)n) ++h;
     return h;
 }
-__device__ uint32_t perm_index(uint32_t x, uint32_t n, const uint4& key, int h) {
+// one pass of the four Feistel rounds on 2h bits
+__device__ __forceinline__ uint32_t feistel4(uint32_t y, const uint4& key, int h) {
     const uint32_t mask = (1u << h) - 1u;
-    const unsigned long long lim = 1ull << (2 * h);
-    uint32_t y = x;
-    for (unsigned long long it = 0; it < lim; ++it) {
-        uint32_t L = y >> h, R = y & mask;
-        const uint32_t k4[4] = {key.x, key.y, key.z, key.w};
+    uint32_t L = y >> h, R = y & mask;
+    const uint32_t k4[4] = {key.x, key.y, key.z, key.w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const uint32_t F = fe_round(R, k4[r]) & mask;
-            const uint32_t t = L ^ F;
-            L = R;
-            R = t;
-        }
-        y = (L << h) | R;
-        if (y < n) return y;
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t F = fe_round(R, k4[r]) & mask;
+        const uint32_t t = L ^ F;
+        L = R;
+        R = t;
     }
-    return x;
+    return (L << h) | R;
+}
+// Indices x0 and x1 under two permutations (or the same one twice), each
+// walked back into its range [0, n) by repeating the rounds until the value
+// falls in it; the two walks advance side by side.  A walk ends within 4^h
+// steps, x lying in [0, n) itself (x is returned after 4^h, which it never
+// reaches).
+__device__ void perm_index2(uint32_t x0, uint32_t n0, const uint4& key0, int h0, uint32_t x1, uint32_t n1,
+                            const uint4& key1, int h1, uint32_t& out0, uint32_t& out1) {
+    const unsigned long long lim0 = 1ull << (2 * h0), lim1 = 1ull << (2 * h1);
+    const unsigned long long lim = lim0 > lim1 ? lim0 : lim1;
+    uint32_t y0 = x0, y1 = x1;
+    bool d0 = false, d1 = false;
+    out0 = x0;
+    out1 = x1;
+    for (unsigned long long it = 0; it < lim && !(d0 && d1); ++it) {
+        if (!d0) {
+            y0 = feistel4(y0, key0, h0);
+            if (y0 < n0) {
+                out0 = y0;
+                d0 = true;
+            } else if (it + 1 >= lim0) {
+                d0 = true;
+            }
+        }
+        if (!d1) {
+            y1 = feistel4(y1, key1, h1);
+            if (y1 < n1) {
+                out1 = y1;
+                d1 = true;
+            } else if (it + 1 >= lim1) {
+                d1 = true;
+            }
+        }
+    }
 }
 
 // uniform on [0, 1) from the top 24 bits of a draw (as Stream::u01)
@@ -949,27 +978,34 @@ __device__ __forceinline__ float u01_of(uint32_t x) { return __fmul_rn((float)(x
 // The draws of one Coulomb pair from its stream: Z (the Irwin-Hall sum of
 // the first twelve uniforms, three Philox blocks) and the azimuth (points of
 // the square from the following blocks, two per block, until one falls in
-// the unit disc; fail after 64 tries, as azimuth()).
+// the unit disc; fail after 64 tries, as azimuth()).  The three blocks of Z
+// and the first block of the azimuth (which serves all but about one pair in
+// twenty) are independent chains of rounds, computed side by side.
 __device__ void coul_draws(uint32_t subject, uint32_t step, uint32_t sid, uint32_t seed, uint32_t run, float& z,
                            float& c, float& s, bool& fail) {
-    uint4 ctr = make_uint4(subject, step, sid, 0u);
     const uint2 key = make_uint2(seed, run);
+    const uint4 r0 = philox4x32_10(make_uint4(subject, step, sid, 0u), key);
+    const uint4 r1 = philox4x32_10(make_uint4(subject, step, sid, 1u), key);
+    const uint4 r2 = philox4x32_10(make_uint4(subject, step, sid, 2u), key);
+    uint4 r = philox4x32_10(make_uint4(subject, step, sid, 3u), key);
     float zz = 0.0f;
-#pragma unroll 1
-    for (int b = 0; b < 3; ++b) {
-        const uint4 r = philox4x32_10(ctr, key);
-        ctr.w += 1u;
-        zz = zz + u01_of(r.x);
-        zz = zz + u01_of(r.y);
-        zz = zz + u01_of(r.z);
-        zz = zz + u01_of(r.w);
-    }
+    zz = zz + u01_of(r0.x);
+    zz = zz + u01_of(r0.y);
+    zz = zz + u01_of(r0.z);
+    zz = zz + u01_of(r0.w);
+    zz = zz + u01_of(r1.x);
+    zz = zz + u01_of(r1.y);
+    zz = zz + u01_of(r1.z);
+    zz = zz + u01_of(r1.w);
+    zz = zz + u01_of(r2.x);
+    zz = zz + u01_of(r2.y);
+    zz = zz + u01_of(r2.z);
+    zz = zz + u01_of(r2.w);
     z = zz - 6.0f;
     fail = false;
 #pragma unroll 1
-    for (int b = 0; b < 32; ++b) {
-        const uint4 r = philox4x32_10(ctr, key);
-        ctr.w += 1u;
+    for (uint32_t b = 0; b < 32u; ++b) {
+        if (b > 0u) r = philox4x32_10(make_uint4(subject, step, sid, 3u + b), key);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const float u1 = 2.0f * u01_of(h ? r.z : r.x) - 1.0f;
@@ -1230,18 +1266,17 @@ __global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, 
                 if (K.la == K.lb) {
                     const uint32_t N = K.N;
                     const int h = perm_bits(N);
-                    if (k < K.P) {
-                        ra = perm_index(2u * k, N, K.k1, h);
-                        rb = perm_index(2u * k + 1u, N, K.k1, h);
-                    } else {                     // the closing triple: pair q joins q and q + 1 (mod 3)
+                    uint32_t xa = 2u * k, xb = 2u * k + 1u;
+                    if (k >= K.P) {              // the closing triple: pair q joins q and q + 1 (mod 3)
                         const uint32_t q = k - K.P;
-                        ra = perm_index(N - 3u + q, N, K.k1, h);
-                        rb = perm_index(N - 3u + (q + 1u) % 3u, N, K.k1, h);
+                        xa = N - 3u + q;
+                        xb = N - 3u + (q + 1u) % 3u;
                         Kn = Kn * 0.5f;
                     }
+                    perm_index2(xa, N, K.k1, h, xb, N, K.k1, h, ra, rb);
                 } else {
-                    const uint32_t m = perm_index(k, K.N, K.k1, perm_bits(K.N));
-                    const uint32_t f = perm_index(k % K.P, K.P, K.k2, perm_bits(K.P));
+                    uint32_t m, f;
+                    perm_index2(k, K.N, K.k1, perm_bits(K.N), k % K.P, K.P, K.k2, perm_bits(K.P), m, f);
                     ra = K.a_many ? m : f;
                     rb = K.a_many ? f : m;
                 }
@@ -1249,17 +1284,20 @@ __global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, 
                 const uint32_t na = W.n[la_], nb = W.n[lb_], ba = W.base[la_], bb = W.base[lb_];
                 const uint32_t pa = (W.sorted >> la_) & 1u ? ra : S.table[ba + ra];
                 const uint32_t pb = (W.sorted >> lb_) & 1u ? rb : S.table[bb + rb];
+                // the draws do not depend on the particles: they are computed
+                // while the rank lookups are in flight (and dropped for a pair
+                // that does not take place)
+                coul_draws(lc, st->step, sid_coul(K.cls, k), RI->seed, RI->run, z, cph, sph, fail);
                 if (pa < na && pb < nb) {
                     const uint32_t ka = A.key[ba + pa], kb = A.key[bb + pb];
                     valid = !(ka & KEY_FLAG) && (int)key_species(ka) == list_species(la_) && !(kb & KEY_FLAG) &&
                             (int)key_species(kb) == list_species(lb_);
                     ia = cached ? W.coff[la_] + pa : ba + pa;
                     ib = cached ? W.coff[lb_] + pb : bb + pb;
-                    if (valid)
-                        coul_draws(lc, st->step, sid_coul(K.cls, k), RI->seed, RI->run, z, cph, sph, fail);
                 } else {
                     set_error(st, ERR_BOUNDS);   // ids not unique: corrupt state, never index with it
                 }
+                if (!valid) fail = false;
             }
             // the chunk's pairs in waves, in order
             const uint32_t c1 = min(c0 + 32u, T);

@@ -164,6 +164,42 @@ __global__ void __launch_bounds__(256, (RZ || FIELD) ? 3 : 4) k_push4(Particles 
             VR = vr4[g];
             if (RZ) VT = vt4[g];
         }
+        if constexpr (!RZ && !FIELD && !MULTI) {
+            // Neutral copper staying in its cell.  On a heavy step, when every
+            // live particle of the warp's groups is a neutral copper atom of
+            // the heavy bins (its key carries no conversion) whose new
+            // position stays inside its cell, the step below reduces to the new
+            // positions written back in place: it keeps the key, the bin and
+            // the velocity, deposits nothing, and its position update is the
+            // same float operations (z - floor(z) is z + 0 when floor(z) is
+            // zero, which also turns -0 into +0 as the subtraction does).
+            if (P.heavy_step) {
+                const float dtz = P.run0.dtz[1], dtr = P.run0.dtr[1];
+                bool fast = true, anyl = false;
+                float zs[4], rs[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t i = 4u * g + (uint32_t)q;
+                    const uint32_t key_in = (gv && i < n) ? lane_of(K, q) : DEAD;
+                    const float pz = lane_of(Z, q), pr = lane_of(R4, q);
+                    const float z = pz + lane_of(VZ, q) * dtz;
+                    const float rr = pr + lane_of(VR, q) * dtr;
+                    const bool live = key_in != DEAD;
+                    const bool stay = z >= 0.0f && z < 1.0f && rr >= 0.0f && rr < 1.0f;
+                    fast = fast && (!live || ((key_in >> 24) == (uint32_t)SP_CU && i < n_sorted && stay));
+                    anyl = anyl || live;
+                    zs[q] = live ? z + 0.0f : pz;
+                    rs[q] = live ? rr + 0.0f : pr;
+                }
+                if (__all_sync(FULL_MASK, fast || !need)) {
+                    if (need && anyl) {
+                        pz4[g] = make_float4(zs[0], zs[1], zs[2], zs[3]);
+                        pr4[g] = make_float4(rs[0], rs[1], rs[2], rs[3]);
+                    }
+                    continue;
+                }
+            }
+        }
         uint32_t key[4], newbin[4], oldbin[4];
         float zo[4], ro[4], vzo[4], vro[4], vto[4];
         int sp_[4], iz_[4], ir_[4], wall_[4], run_[4];
