@@ -92,7 +92,7 @@ def parse():
     p.add_argument("--prod-total", type=float, default=2e7, help="production: particles")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--eager", action="store_true",
-                   help="field-on workloads: time the eager steps (host-checked multigrid), no CUDA graph")
+                   help="time the eager steps only (the multigrid residual checked on the host), no CUDA graph")
     p.add_argument("--log-dir", default=".", help="where the clock samples of the timed region are written")
     p.add_argument("--heavy-coll", action="store_true",
                    help="microbench: add the heavy-particle pair classes (charge exchange, Cu-Cu elastic)")
