@@ -232,8 +232,8 @@ def peaks():
 # a launch by its particle count.  The figure holds only for the kernel source
 # it was taken on: TRAFFIC_SOURCE_SHA is the SHA-256 of csrc/pd_stream.cu at
 # the capture, and `traffic` is null for any other source.
-TRAFFIC_PER_PARTICLE = {"push": 797.566e6 / 24898326}
-TRAFFIC_SOURCE_SHA = "6347f9de1505663f03aa1dde8e6c5dbd6db47e100a5b1d654f8f16bf2e57ff67"
+TRAFFIC_PER_PARTICLE = {"push": 796.619e6 / 24898326}
+TRAFFIC_SOURCE_SHA = "84e6a9a9a5699bf1b351c8a73133535810d0b553c3882c11f1e4d64d8497aa23"
 TRAFFIC_SOURCE = "ncu dram bytes per particle of a 2.49e7-particle launch, scaled"
 
 

@@ -993,7 +993,9 @@ __global__ void __launch_bounds__(256) k_relayout_clear(uint32_t* key, const uin
 // each heavy bin (its first cnt - in slots after the closing of holes) keep
 // their order, the heavy movers follow them.  Clears the heavy movers' bits
 // of the mover mask (the electrons are inserted after the electron bins are
-// laid out).
+// laid out).  A warp per 128 slots, lane l taking slot l of each row of 32:
+// the loads and the stores of a row are runs of consecutive words (a bin
+// keeps its order and moves by one offset).
 __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles B, Particles M,
                                                           uint32_t* mm, const uint32_t* __restrict__ off,
                                                           const uint32_t* __restrict__ off2,
@@ -1002,19 +1004,16 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
     if (!st->relayout || st->error) return;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t tb = (uint32_t)st->e_from, nv = (tb + 3u) >> 2;
-    for (uint32_t v = tid; v < nv; v += stride) {
-        const uint4 K = reinterpret_cast<const uint4*>(A.key)[v];
-        if ((K.x & K.y & K.z & K.w) == DEAD) continue;
-        const float4 Z = reinterpret_cast<const float4*>(A.pz)[v], R = reinterpret_cast<const float4*>(A.pr)[v];
-        const float4 VZ = reinterpret_cast<const float4*>(A.vz)[v], VR = reinterpret_cast<const float4*>(A.vr)[v];
-        const float4 VT = reinterpret_cast<const float4*>(A.vt)[v];
-        const uint4 ID = reinterpret_cast<const uint4*>(A.id)[v];
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t tb = (uint32_t)st->e_from, nch = (tb + 127u) >> 7;
+    for (uint32_t c = tid >> 5; c < nch; c += stride >> 5) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            // (the last group may reach into the electron bins: they are movers)
-            const uint32_t k = lane_of(K, q), i = 4u * v + (uint32_t)q;
-            if (k == DEAD || i >= tb) continue;
+            // (the last chunk may reach into the electron bins: they are movers)
+            const uint32_t i = 128u * c + 32u * (uint32_t)q + lane;
+            if (i >= tb) continue;
+            const uint32_t k = A.key[i];
+            if (k == DEAD) continue;
             const uint32_t b = key_species(k) * P.ncell + key_cell(k);
             if (key_cell(k) >= P.ncell || b >= nbins || i < off[b] || i - off[b] >= cnt[b]) {
                 sort_fault(st, 64u);             // not a particle of its bin: never write out of range
@@ -1022,12 +1021,12 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
             }
             const uint32_t s = off2[b] + (i - off[b]);
             B.key[s] = k;
-            B.pz[s] = lane_of(Z, q);
-            B.pr[s] = lane_of(R, q);
-            B.vz[s] = lane_of(VZ, q);
-            B.vr[s] = lane_of(VR, q);
-            B.vt[s] = lane_of(VT, q);
-            B.id[s] = lane_of(ID, q);
+            B.pz[s] = A.pz[i];
+            B.pr[s] = A.pr[i];
+            B.vz[s] = A.vz[i];
+            B.vr[s] = A.vr[i];
+            B.vt[s] = A.vt[i];
+            B.id[s] = A.id[i];
         }
     }
     const uint32_t ng = (uint32_t)((st->n_slots + 127ull) >> 7);
