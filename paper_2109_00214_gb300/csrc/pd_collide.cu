@@ -1073,7 +1073,7 @@ constexpr int COUL_NLIST = 6;
 // charged particles of a cell whose velocities its warp holds in shared
 // memory (in the words of its rank-table sort buffer, free once the tables
 // are built)
-constexpr int COUL_CACHE = 512;
+constexpr int COUL_CACHE = 384;
 constexpr int COUL_WARPS = 4;           // warps of a k_coulomb block
 // words of a warp's buffer: the rank-table sort of a register-cached list,
 // then the velocity cache (three floats and a flag byte per particle)
@@ -1119,7 +1119,7 @@ __device__ __forceinline__ int list_species(int l) { return l == 0 ? SP_E : SP_C
 // so this is the order of cell-by-cell processing): one warp per cell with
 // charged particles, grid-stride over the cells, on the lists of the step's
 // start; a particle whose species changed this step is left out.
-__global__ void __launch_bounds__(128, 4) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(128, 6) k_coulomb(Particles A, RankScratch S, const uint32_t* __restrict__ off,
                                                    const uint32_t* __restrict__ cnt, DevState* st, KParams P,
                                                    CollConsts cc, const double* __restrict__ cw) {
     if (st->error) return;                           // a fault was flagged: the state is not stepped further
@@ -1915,7 +1915,7 @@ void launch_coulomb(const Particles& A, const Particles& B, const uint32_t* off,
     const RankScratch S{B.key, reinterpret_cast<uint32_t*>(B.pz), reinterpret_cast<uint32_t*>(B.pr),
                         reinterpret_cast<uint32_t*>(B.vz), B.id};
     // one wave of resident blocks, grid-stride over the cells
-    k_coulomb<<<sms * 4, 32 * COUL_WARPS, 0, s>>>(A, S, off, cnt, st, P, cc, cw);
+    k_coulomb<<<sms * 6, 32 * COUL_WARPS, 0, s>>>(A, S, off, cnt, st, P, cc, cw);
 }
 void launch_finalize(const uint32_t* off, uint32_t nbins, const uint32_t* cand_off, DevState* st, const KParams& P,
                      const RunCircuit* circ, double dt, int circuit, cudaStream_t s) {
