@@ -43,7 +43,7 @@ namespace {
 constexpr double QE_ = 1.602176634e-19;
 constexpr double EPS0_ = 8.8541878128e-12;
 constexpr double PI_ = 3.14159265358979323846;
-constexpr int RED_BLOCKS = 64;
+constexpr int RED_BLOCKS = 256;      // blocks of a run's residual (a fixed shape: the summation order is fixed)
 constexpr int MAP_CHUNK = 256;         // items of one work-list entry
 constexpr int SP_TI = 32, SP_TJ = 32;  // smoother tile: interior rows x radial nodes
 constexpr int SP_H = 4;                // halo: four half-sweeps per launch
@@ -507,11 +507,19 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(const MGLevel* lev, co
         const int m = (L.nz - 1) * W;
         const float* Ai = inv[run];
         if (Ai) {
-            for (int u = threadIdx.x; u < m; u += blockDim.x) {
+            // e = A^-1 f: P threads per unknown, each summing every P-th
+            // term (their loads in flight together), then a shuffle sum
+            const int P = m <= 64 ? 8 : (m <= 128 ? 4 : (m <= 256 ? 2 : 1));
+            const int per = (int)blockDim.x / P;
+            for (int u0 = 0; u0 < m; u0 += per) {        // the same trip count in every thread
+                const int u = u0 + (int)threadIdx.x / P, part = (int)threadIdx.x % P;
                 float acc = 0.0f;
-#pragma unroll 4
-                for (int v = 0; v < m; ++v) acc += Ai[(size_t)v * m + u] * L.f[W + v];
-                L.e[W + u] = acc;
+                if (u < m) {
+#pragma unroll 8
+                    for (int v = part; v < m; v += P) acc += Ai[(size_t)v * m + u] * L.f[W + v];
+                }
+                for (int o = P >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o, P);
+                if (part == 0 && u < m) L.e[W + u] = acc;
             }
             __syncthreads();
         } else {
