@@ -1029,9 +1029,69 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
             B.id[s] = A.id[i];
         }
     }
+    // The heavy movers, a warp per 128 slots of the mover mask (lane l takes
+    // slot l of each row of 32).  After a load every particle is a mover, so
+    // the rows are dense: the movers of a row bound for one bin claim their
+    // slots with one atomic, and the records' loads of the four rows are in
+    // flight together.  Electrons stay in the mask for the electron pass.
     const uint32_t ng = (uint32_t)((st->n_slots + 127ull) >> 7);
-    for (uint32_t g = tid; g < ng; g += stride)
-        insert128(B, M, mm, g, off2, cnt, in_cnt, P.ncell, nbins, (uint32_t)P.capacity, true, st);
+    const uint32_t nslots = (uint32_t)P.capacity;
+    for (uint32_t g = tid >> 5; g < ng; g += stride >> 5) {
+        const uint4 w = reinterpret_cast<const uint4*>(mm)[g];
+        if ((w.x | w.y | w.z | w.w) == 0u) continue;          // the same chunk in every lane
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+        uint32_t K[4], bin[4], end[4], left[4];
+        unsigned peers[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = 128u * g + 32u * (uint32_t)q + lane;    // < 128 ng <= the slot arrays' length
+            const bool on = (ws[q] >> lane) & 1u;
+            K[q] = on ? M.key[i] : DEAD;
+            const bool elec = on && K[q] != DEAD && key_species(K[q]) == SP_E;
+            const bool heavy = on && !elec;
+            bin[q] = heavy ? mover_bin(K[q], P.ncell, nbins) : nbins;
+            if (heavy && bin[q] >= nbins) sort_fault(st, 128u);
+            ok[q] = heavy && bin[q] < nbins;
+            end[q] = ok[q] ? off2[bin[q]] + cnt[bin[q]] : 0u;
+            peers[q] = __match_any_sync(FULL_MASK, ok[q] ? bin[q] : 0xFFFFFFFFu);
+            const unsigned keep = __ballot_sync(FULL_MASK, elec);
+            if (lane == 0u) mm[4u * g + (uint32_t)q] = keep;
+        }
+        float Z[4], R[4], VZ[4], VR[4], VT[4];
+        uint32_t ID[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t i = 128u * g + 32u * (uint32_t)q + lane;
+            const uint32_t leader = (uint32_t)(__ffs((int)peers[q]) - 1);
+            left[q] = (ok[q] && lane == leader) ? atomicSub(&in_cnt[bin[q]], (uint32_t)__popc(peers[q])) : 0u;
+            Z[q] = ok[q] ? M.pz[i] : 0.0f;
+            R[q] = ok[q] ? M.pr[i] : 0.0f;
+            VZ[q] = ok[q] ? M.vz[i] : 0.0f;
+            VR[q] = ok[q] ? M.vr[i] : 0.0f;
+            VT[q] = ok[q] ? M.vt[i] : 0.0f;
+            ID[q] = ok[q] ? M.id[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t leader = (uint32_t)(__ffs((int)peers[q]) - 1);
+            const uint32_t lq = __shfl_sync(FULL_MASK, left[q], (int)leader);
+            if (!ok[q]) continue;
+            const uint32_t rank = (uint32_t)__popc(peers[q] & ((1u << lane) - 1u));
+            const uint32_t s = end[q] - lq + rank;
+            if (lq < (uint32_t)__popc(peers[q]) || s >= end[q] || s >= nslots) {   // inconsistent: never write out of range
+                sort_fault(st, 16u);
+                continue;
+            }
+            B.key[s] = K[q];
+            B.pz[s] = Z[q];
+            B.pr[s] = R[q];
+            B.vz[s] = VZ[q];
+            B.vr[s] = VR[q];
+            B.vt[s] = VT[q];
+            B.id[s] = ID[q];
+        }
+    }
 }
 
 // A := B over the new heavy bins (groups of four slack slots copy only
