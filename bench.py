@@ -230,18 +230,43 @@ def peaks():
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch of the 512 x 512
 # microbench, 2.49e7 particles, the recipe of the 1024 x 1024 one), scaled to
 # a launch by its particle count.  The figure holds only for the kernel source
-# it was taken on: TRAFFIC_SOURCE_SHA is the SHA-256 of csrc/pd_stream.cu at
-# the capture, and `traffic` is null for any other source.
+# it was taken on: TRAFFIC_SOURCE_SHA is the push_source_digest() of the
+# source at the capture, and `traffic` is null for any other source.
 TRAFFIC_PER_PARTICLE = {"push": 796.619e6 / 24898326}
-TRAFFIC_SOURCE_SHA = "84e6a9a9a5699bf1b351c8a73133535810d0b553c3882c11f1e4d64d8497aa23"
+TRAFFIC_SOURCE_SHA = "1cbcc20d3a105d4a06e37ae47d56c9ab8d5972cb0c65a2061d1102138765a1ef"
 TRAFFIC_SOURCE = "ncu dram bytes per particle of a 2.49e7-particle launch, scaled"
+PUSH_SECTION_END = "// sort: holes, insertions, re-layout"
+
+
+def push_source_digest(read=None):
+    """SHA-256 over the source the push kernel compiles from: csrc/pd_stream.cu
+    up to its sort section (the push kernel and its helpers), its launcher
+    launch_push, and the three headers it includes.  Edits elsewhere in the
+    file (the sort kernels) leave it unchanged.  `read(relpath) -> str`
+    supplies the files (default: the working tree)."""
+    import hashlib
+    csrc = "paper_2109_00214_gb300/csrc/"
+    if read is None:
+        def read(rel):
+            with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+                return f.read()
+    stream = read(csrc + "pd_stream.cu")
+    cut = stream.find(PUSH_SECTION_END)
+    start = stream.find("void launch_push(")
+    end = stream.find("\n}\n", start)
+    if cut < 0 or start < 0 or end < 0:
+        return None
+    h = hashlib.sha256()
+    h.update(stream[:cut].encode())
+    h.update(stream[start:end + 3].encode())
+    for name in ("pd_internal.cuh", "pd_warp.cuh", "pd_kernels.h"):
+        h.update(read(csrc + name).encode())
+    return h.hexdigest()
 
 
 def traffic_per_particle(kernel):
-    import hashlib
-    src = os.path.join(ROOT, "paper_2109_00214_gb300", "csrc", "pd_stream.cu")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = push_source_digest()
     except OSError:
         return None
     return TRAFFIC_PER_PARTICLE.get(kernel) if sha == TRAFFIC_SOURCE_SHA else None
