@@ -233,7 +233,7 @@ def peaks():
 # it was taken on: TRAFFIC_SOURCE_SHA is the push_source_digest() of the
 # source at the capture, and `traffic` is null for any other source.
 TRAFFIC_PER_PARTICLE = {"push": 796.619e6 / 24898326}
-TRAFFIC_SOURCE_SHA = "1cbcc20d3a105d4a06e37ae47d56c9ab8d5972cb0c65a2061d1102138765a1ef"
+TRAFFIC_SOURCE_SHA = "4ea56a37e679cd6915a1f10f3105171b5066fd3f77c9b4c9d07c6f56dc5efaa0"
 TRAFFIC_SOURCE = "ncu dram bytes per particle of a 2.49e7-particle launch, scaled"
 PUSH_SECTION_END = "// sort: holes, insertions, re-layout"
 
@@ -241,9 +241,10 @@ PUSH_SECTION_END = "// sort: holes, insertions, re-layout"
 def push_source_digest(read=None):
     """SHA-256 over the source the push kernel compiles from: csrc/pd_stream.cu
     up to its sort section (the push kernel and its helpers), its launcher
-    launch_push, and the three headers it includes.  Edits elsewhere in the
-    file (the sort kernels) leave it unchanged.  `read(relpath) -> str`
-    supplies the files (default: the working tree)."""
+    launch_push, and the two headers its device code uses.  Edits elsewhere in
+    the file (the sort kernels) and in the launchers' declarations leave it
+    unchanged.  `read(relpath) -> str` supplies the files (default: the
+    working tree)."""
     import hashlib
     csrc = "paper_2109_00214_gb300/csrc/"
     if read is None:
@@ -259,7 +260,7 @@ def push_source_digest(read=None):
     h = hashlib.sha256()
     h.update(stream[:cut].encode())
     h.update(stream[start:end + 3].encode())
-    for name in ("pd_internal.cuh", "pd_warp.cuh", "pd_kernels.h"):
+    for name in ("pd_internal.cuh", "pd_warp.cuh"):
         h.update(read(csrc + name).encode())
     return h.hexdigest()
 

@@ -724,7 +724,7 @@ pd_status issue_step(pd_sim* s, bool capturing) {
             // and four more) returns at once unless a heavy bin overflowed
             Timed t(s, K_SCAN_BINS, capturing, 10);
             launch_relayout(a, s->st, P, grid_for(s, s->tune.bincount_blocks_per_sm),
-                            grid_for(s, s->tune.scatter_blocks_per_sm), s->stream);
+                            grid_for(s, s->tune.scatter_blocks_per_sm), s->stream, !s->sorted_valid);
         }
         {
             // electron bins laid out (a scan of three, k_ebins), movers

@@ -48,9 +48,10 @@ struct SortArgs {
 // heavy bins: counts, holes closed, slots borrowed by full bins (three launches)
 void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cudaStream_t s);
 // a new layout of the heavy bins when one overflowed (every kernel returns at
-// once otherwise; ten launches)
+// once otherwise; ten launches).  first: no particle is in a bin yet (the
+// first step after the loads), so the layout is written into A directly
 void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid_bins, int grid_slots,
-                     cudaStream_t s);
+                     cudaStream_t s, bool first);
 // the electron bins packed after the heavy bins, then every mover into its
 // bin (six launches)
 void launch_insert(const SortArgs& a, DevState* st, const KParams& P, int grid_dense, cudaStream_t s);

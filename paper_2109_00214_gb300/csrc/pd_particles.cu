@@ -154,8 +154,46 @@ __device__ __forceinline__ bool in_run(uint32_t key, const RunInfo& RI) {
     return c >= RI.cell_base && c < RI.cell_base + RI.ncell;
 }
 
-// live particles of one run per species: per-warp ballot counts, one atomic
-// per warp and species at the end
+// live particles per species of a single run, out[species]: each thread
+// counts its slots in registers, four groups of four keys loaded before any
+// is used (independent loads in flight), then a warp sum and one atomic per
+// warp and species
+__global__ void __launch_bounds__(256) k_species_count1(Particles A, DevState* st, unsigned long long* out) {
+    const unsigned long long n = st->n_slots;
+    const unsigned long long nv = (n + 3ull) >> 2;           // the slot arrays are padded to four
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const uint4* key4 = reinterpret_cast<const uint4*>(A.key);
+    unsigned int c[NSP];
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) c[k] = 0u;
+    for (unsigned long long v0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; v0 < nv;
+         v0 += 4ull * stride) {
+        uint4 K[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned long long v = v0 + (unsigned long long)u * stride;
+            K[u] = v < nv ? key4[v] : make_uint4(DEAD, DEAD, DEAD, DEAD);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned long long j0 = 4ull * (v0 + (unsigned long long)u * stride);
+            const uint32_t ks[4] = {K[u].x, K[u].y, K[u].z, K[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool live = j0 + (unsigned long long)q < n && ks[q] != DEAD;
+                const uint32_t sp = key_species(ks[q]);
+#pragma unroll
+                for (int k = 0; k < NSP; ++k) c[k] += (live && sp == (uint32_t)k) ? 1u : 0u;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+        const unsigned int w = __reduce_add_sync(FULL, c[k]);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&out[k], (unsigned long long)w);
+    }
+}
+
 // live particles per run and species, all runs in one pass: out[run * NSP + species]
 // (warp-aggregated shared-memory counters, one flush per block)
 __global__ void k_species_count_all(Particles A, DevState* st, KParams P, unsigned long long* out) {
@@ -263,7 +301,8 @@ void launch_pack_keys(const uint8_t* sp, const int32_t* iz, const int32_t* ir, c
 }
 void launch_species_count_all(const Particles& A, DevState* st, const KParams& P, unsigned long long* out, int grid,
                               cudaStream_t s) {
-    k_species_count_all<<<grid, 256, 0, s>>>(A, st, P, out);
+    if (P.nruns == 1) k_species_count1<<<grid, 256, 0, s>>>(A, st, out);
+    else k_species_count_all<<<grid, 256, 0, s>>>(A, st, P, out);
 }
 void launch_density(const Particles& A, DevState* st, const KParams& P, int run, int species, long long* acc,
                     int grid, cudaStream_t s) {

@@ -1000,12 +1000,16 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
                                                           uint32_t* mm, const uint32_t* __restrict__ off,
                                                           const uint32_t* __restrict__ off2,
                                                           const uint32_t* __restrict__ cnt, uint32_t* in_cnt,
-                                                          uint32_t nbins, DevState* st, KParams P) {
+                                                          uint32_t nbins, DevState* st, KParams P, bool in_place) {
     if (!st->relayout || st->error) return;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t tb = (uint32_t)st->e_from, nch = (tb + 127u) >> 7;
+    if (in_place && tb != 0u) {        // B is A: only valid while no particle sits in a bin
+        sort_fault(st, 512u);
+        return;
+    }
     for (uint32_t c = tid >> 5; c < nch; c += stride >> 5) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1095,14 +1099,15 @@ __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles
 }
 
 // A := B over the new heavy bins (groups of four slack slots copy only
-// their keys), off := off2; the electron bins start after them
+// their keys), off := off2; the electron bins start after them.  in_place:
+// the re-layout was written into A itself (nothing to copy)
 __global__ void __launch_bounds__(256) k_relayout_copy(Particles A, Particles B, uint32_t* off,
                                                        const uint32_t* __restrict__ off2, uint32_t nbins,
-                                                       uint32_t nbins_pad, DevState* st) {
+                                                       uint32_t nbins_pad, DevState* st, bool in_place) {
     if (!st->relayout || st->error) return;
     const uint32_t stride = gridDim.x * blockDim.x;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t end = off2[nbins], nv = (end + 3u) >> 2;
+    const uint32_t end = off2[nbins], nv = in_place ? 0u : (end + 3u) >> 2;
     for (uint32_t v = tid; v < nv; v += stride) {
         uint4 K = reinterpret_cast<const uint4*>(B.key)[v];
         if (4u * v + 4u > end) {       // the last group: slots past the bins read DEAD
@@ -1165,16 +1170,19 @@ void launch_sort(const SortArgs& a, DevState* st, const KParams& P, int sms, cud
 }
 
 void launch_relayout(const SortArgs& a, DevState* st, const KParams& P, int grid_bins, int grid_slots,
-                     cudaStream_t s) {
-    // each kernel returns at once unless a bin overflowed
+                     cudaStream_t s, bool first) {
+    // each kernel returns at once unless a bin overflowed.  The first layout
+    // (no particle in any bin yet: every loaded particle is a mover) is
+    // written straight into A, and nothing is copied back.
+    const Particles& D = first ? a.A : a.B;
     k_relayout_stats<<<grid_bins, 256, 0, s>>>(a.cnt, a.act, a.nbins, P.ncell, P.nsp, st);
     k_relayout_want<<<grid_bins, 256, 0, s>>>(a.cnt, a.act, a.net, a.nbins, P.ncell, st);
     k_relayout_caps<<<grid_bins, 256, 0, s>>>(a.cnt, a.cap, a.act, a.net, a.nbins, a.nbins_pad, P.ncell, st, P);
     launch_scan(a.cap, a.off2, a.partial, a.nbins_pad, s, &st->relayout);
-    k_relayout_clear<<<grid_slots, 256, 0, s>>>(a.B.key, a.off2, a.nbins, st);
-    k_relayout_scatter<<<grid_slots, 256, 0, s>>>(a.A, a.B, a.M, a.mm, a.off, a.off2, a.cnt, a.in_cnt, a.nbins, st,
-                                                  P);
-    k_relayout_copy<<<grid_slots, 256, 0, s>>>(a.A, a.B, a.off, a.off2, a.nbins, a.nbins_pad, st);
+    k_relayout_clear<<<grid_slots, 256, 0, s>>>(D.key, a.off2, a.nbins, st);
+    k_relayout_scatter<<<grid_slots, 256, 0, s>>>(a.A, D, a.M, a.mm, a.off, a.off2, a.cnt, a.in_cnt, a.nbins, st,
+                                                  P, first);
+    k_relayout_copy<<<grid_slots, 256, 0, s>>>(a.A, D, a.off, a.off2, a.nbins, a.nbins_pad, st, first);
     k_relayout_done<<<1, 1, 0, s>>>(a.off, a.nbins, st);
 }
 
