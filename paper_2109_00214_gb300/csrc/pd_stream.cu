@@ -995,7 +995,9 @@ __global__ void __launch_bounds__(256) k_relayout_clear(uint32_t* key, const uin
 // of the mover mask (the electrons are inserted after the electron bins are
 // laid out).  A warp per 128 slots, lane l taking slot l of each row of 32:
 // the loads and the stores of a row are runs of consecutive words (a bin
-// keeps its order and moves by one offset).
+// keeps its order and moves by one offset).  in_place: B is A itself, which
+// holds only while no particle sits in a bin (the first layout after the
+// loads, every particle a mover).
 __global__ void __launch_bounds__(256) k_relayout_scatter(Particles A, Particles B, Particles M,
                                                           uint32_t* mm, const uint32_t* __restrict__ off,
                                                           const uint32_t* __restrict__ off2,
